@@ -1,0 +1,171 @@
+"""Seeded synthetic filterbank inputs for the dedispersion tests and benchmark.
+
+This module only *makes inputs*.  It holds none of the dedispersion
+arithmetic (no phasors, no transforms, no shift-and-sum) and imports neither
+the oracle nor the CUDA package, so both can be fed from it.
+
+A filterbank is a [n_t, n_chan] time-major array (the 8-bit or float32
+dynamic spectrum of Sect. 3 of the paper) of Gaussian noise, with boxcar
+pulses injected along a dispersion sweep.  The sweep uses this module's own
+sky model: a pulse emitted at sample t0 arrives in channel c at
+    t0 + round(DM * K_DM_SKY * (nu_c^-2 - nu_top^-2) / t_samp),
+with nu_c the channel centre and nu_top the highest channel centre, and
+K_DM_SKY = 4.148808e3 MHz^2 pc^-1 cm^3 s (the value the 64-channel workload
+states; the dedisperser's own constant is a plan parameter).
+
+The workloads stand in for the simulated SUPERB-like survey data of the paper
+(Sect. 4: 1024 channels, 64 us sampling), which is not available; their
+shapes follow the paper's parameter space.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+K_DM_SKY = 4.148808e3
+
+
+@dataclass
+class Pulse:
+    t0: int          # emission sample at the top channel
+    dm: float
+    amp: float
+    width: int
+
+
+@dataclass
+class Workload:
+    name: str
+    n_chan: int
+    band_lo_mhz: float   # lower band edge
+    band_hi_mhz: float   # upper band edge
+    t_samp_s: float
+    n_t: int
+    dtype: str           # "u8" or "f32"
+    dm0: float
+    ddm: float
+    n_dm: int
+    chunk_len: int       # 0 = whole series zero padded to a power of two
+    n_beams: int = 1
+    output: str = "time"  # "time" | "spectra" | "power"
+    pulses_per_beam: int = 1
+    fixed_pulse: Pulse | None = None
+    noise_mean: float = 0.0
+    noise_sigma: float = 1.0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dnu_mhz(self) -> float:
+        return (self.band_hi_mhz - self.band_lo_mhz) / self.n_chan
+
+    @property
+    def nu_lo_mhz(self) -> float:
+        """Centre of channel 0."""
+        return self.band_lo_mhz + 0.5 * self.dnu_mhz
+
+    def channel_centres(self) -> np.ndarray:
+        return self.nu_lo_mhz + self.dnu_mhz * np.arange(self.n_chan, dtype=np.float64)
+
+    def dms(self) -> np.ndarray:
+        return self.dm0 + self.ddm * np.arange(self.n_dm, dtype=np.float64)
+
+    def scaled(self, **kw) -> "Workload":
+        d = dict(self.__dict__)
+        d.update(kw)
+        return Workload(**d)
+
+
+# The workloads, named by what they are.  Sizes as stated for each.
+WORKLOADS = {
+    # 64 channels of 4.6875 MHz over 1250-1550 MHz, 0.25 ms, 4096 float32
+    # samples of N(0,1), one boxcar (amp 2, width 4) at t=1000, DM 57.3;
+    # 128 trials 0..127; whole series, time-domain output.
+    "fdd_64ch_4096t_128dm": Workload(
+        name="fdd_64ch_4096t_128dm", n_chan=64, band_lo_mhz=1250.0, band_hi_mhz=1550.0,
+        t_samp_s=0.25e-3, n_t=4096, dtype="f32", dm0=0.0, ddm=1.0, n_dm=128, chunk_len=0,
+        fixed_pulse=Pulse(t0=1000, dm=57.3, amp=2.0, width=4)),
+    # survey-shaped: 1024 channels over 1210-1520 MHz, 64 us, 2^20 uint8
+    # samples N(128,16) clipped, 5 pulses; 2048 trials 0..1023.5; 2^18 chunks.
+    "fdd_1024ch_2p20t_2048dm": Workload(
+        name="fdd_1024ch_2p20t_2048dm", n_chan=1024, band_lo_mhz=1210.0, band_hi_mhz=1520.0,
+        t_samp_s=64e-6, n_t=1 << 20, dtype="u8", dm0=0.0, ddm=0.5, n_dm=2048,
+        chunk_len=1 << 18, pulses_per_beam=5, noise_mean=128.0, noise_sigma=16.0),
+    # 32 beams sharing the bins: 1024 channels over 1250-1550 MHz, 0.25 ms,
+    # 2^19 float32 samples per beam; 4096 trials 0..2047.5; whole series.
+    "fdd_32beam_1024ch_2p19t_4096dm": Workload(
+        name="fdd_32beam_1024ch_2p19t_4096dm", n_chan=1024, band_lo_mhz=1250.0,
+        band_hi_mhz=1550.0, t_samp_s=0.25e-3, n_t=1 << 19, dtype="f32", dm0=0.0, ddm=0.5,
+        n_dm=4096, chunk_len=0, n_beams=32, pulses_per_beam=1),
+    # low frequency, long delays: 4096 channels over 110-190 MHz, 491.52 us,
+    # 2^21 float32 samples, 8192 trials 0..409.55; power spectra out; 16 beams.
+    "fdd_16beam_4096ch_2p21t_8192dm_power": Workload(
+        name="fdd_16beam_4096ch_2p21t_8192dm_power", n_chan=4096, band_lo_mhz=110.0,
+        band_hi_mhz=190.0, t_samp_s=491.52e-6, n_t=1 << 21, dtype="f32", dm0=0.0, ddm=0.05,
+        n_dm=8192, chunk_len=1 << 19, n_beams=16, output="power", pulses_per_beam=1),
+}
+
+
+def sky_delay_samples(w: Workload, dm: float) -> np.ndarray:
+    """Sky-model arrival offsets (samples, rounded) of each channel for one DM."""
+    nu = w.channel_centres()
+    top = nu.max()
+    return np.rint(dm * K_DM_SKY * (nu ** -2 - top ** -2) / w.t_samp_s).astype(np.int64)
+
+
+def draw_pulses(w: Workload, rng: np.random.Generator) -> list[Pulse]:
+    if w.fixed_pulse is not None:
+        return [w.fixed_pulse]
+    dms = w.dms()
+    lo, hi = float(dms.min()), float(dms.max())
+    out = []
+    for _ in range(w.pulses_per_beam):
+        dm = float(rng.uniform(lo, hi))
+        sweep = int(sky_delay_samples(w, dm).max())
+        t_hi = max(1, w.n_t - sweep - 4)
+        out.append(Pulse(t0=int(rng.integers(0, t_hi)), dm=dm, amp=2.0 * w.noise_sigma, width=4))
+    return out
+
+
+def _noise_block(rng: np.random.Generator, w: Workload, rows: int) -> np.ndarray:
+    z = rng.standard_normal((rows, w.n_chan), dtype=np.float32)
+    if w.noise_sigma != 1.0:
+        z *= np.float32(w.noise_sigma)
+    if w.noise_mean != 0.0:
+        z += np.float32(w.noise_mean)
+    return z
+
+
+def filterbank(w: Workload, seed: int, beam: int = 0, block_rows: int = 1 << 16):
+    """One beam's [n_t, n_chan] time-major filterbank and its pulses.
+
+    Noise is drawn block by block (bounded host memory) from PCG64 seeded by
+    (seed, beam); u8 workloads are rounded and clipped to 0..255 after the
+    pulses are added.
+    """
+    rng = np.random.default_rng([seed, beam])
+    pulses = draw_pulses(w, rng)
+    out = np.empty((w.n_t, w.n_chan), dtype=np.uint8 if w.dtype == "u8" else np.float32)
+    sweeps = [(p, sky_delay_samples(w, p.dm)) for p in pulses]
+    for r0 in range(0, w.n_t, block_rows):
+        r1 = min(w.n_t, r0 + block_rows)
+        blk = _noise_block(rng, w, r1 - r0)
+        for p, off in sweeps:
+            for c in range(w.n_chan):
+                s = p.t0 + int(off[c])
+                a, b = max(s, r0), min(s + p.width, r1)
+                if a < b:
+                    blk[a - r0: b - r0, c] += np.float32(p.amp)
+        if w.dtype == "u8":
+            out[r0:r1] = np.clip(np.rint(blk), 0, 255).astype(np.uint8)
+        else:
+            out[r0:r1] = blk
+    return out, pulses
+
+
+def log_uniform_lengths(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """n integers drawn log-uniformly in [lo, hi] (uneven beam lengths)."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(math.log(lo), math.log(hi), size=n)
+    return np.floor(np.exp(u)).astype(np.int64)
