@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the Fourier-domain dedispersion path on GB300.
+
+One step is the whole path over one batch of synthetic input resident in HBM:
+unpack/transpose and chunking, channel R2C transforms (Eq. 3), the
+phase-rotate-and-sum over channels for every trial DM (Eqs. 4, 7), the
+inverse transforms with 1/L scaling (Eq. 6) and the valid-sample placement.
+
+Default workload: survey-shaped plain FDD, one beam -- 1024 channels over
+1210-1520 MHz, 64 us sampling, 2^20 uint8 samples (Gaussian mean 128, sigma 16,
+clipped, five dispersed pulses), 2048 trials 0..1023.5 step 0.5, overlap-save
+chunks of 2^18 samples, FP32 phasors and accumulation.
+
+The metric counts DM x channel x bin phasor-MACs (8 flops each).  Prints one
+JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample
+of the same workload instead (the reference arm of this benchmark).
+
+Multi-GPU (torchrun): every rank processes its own beam of the same shape
+(independent problems, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "DM·channel·bin phasor-MACs/s and % of FP32/tensor peak, batched TC vs plain FP32"
+UNIT = "phasor-MAC/s"
+DEFAULT_WORKLOAD = "fdd_1024ch_2p20t_2048dm"
+FLOPS_PER_MAC = 8
+MAC_SOURCE = os.path.join(ROOT, "paper_2110_03482_gb300", "csrc", "fdd_mac_fp32.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "mac_fp32_survey_1024ch_2048dm.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fdd", "reference"], default="fdd")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--seed", type=int, default=20211007)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def plan_params(w: synth.Workload, fdd) -> dict:
+    return dict(n_chan=w.n_chan, nu_lo_mhz=w.nu_lo_mhz, dnu_mhz=w.dnu_mhz, t_samp_s=w.t_samp_s,
+                n_t=w.n_t, dm_list=w.dms(), chunk_len=w.chunk_len, n_beams=1,
+                in_dtype=fdd.FDD_IN_U8 if w.dtype == "u8" else fdd.FDD_IN_F32,
+                output={"time": fdd.FDD_OUT_TIME, "spectra": fdd.FDD_OUT_SPECTRA,
+                        "power": fdd.FDD_OUT_POWER}[w.output])
+
+
+def workload_config(w: synth.Workload, info: dict | None) -> dict:
+    cfg = {"workload": w.name, "n_chan": w.n_chan, "band_mhz": [w.band_lo_mhz, w.band_hi_mhz],
+           "t_samp_s": w.t_samp_s, "n_t": w.n_t, "in_dtype": w.dtype, "n_dm": w.n_dm,
+           "dm_range": [w.dm0, w.dm0 + w.ddm * (w.n_dm - 1)], "chunk_len": w.chunk_len,
+           "beams_per_gpu": 1, "output": w.output,
+           "l2": "no flush: inputs, spectra and outputs (GBs) exceed the 129 MB L2"}
+    if info:
+        cfg.update({"fft_len": info["fft_len"], "n_bins": info["n_bins"],
+                    "n_chunks": info["n_chunks"], "d_max": info["d_max"]})
+    return cfg
+
+
+def macs_per_beam(w: synth.Workload, info: dict) -> int:
+    return int(info["n_chunks"]) * w.n_dm * w.n_chan * int(info["n_bins"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [r.strip().split(",") for r in f if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, pw, reasons = [], [], [], set()
+        for r in rows:
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                pw.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, r[4:8]):
+                if v.strip() == "Active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def read_traffic_summary() -> float | None:
+    """Per-launch DRAM bytes of the MAC kernel from the committed ncu summary,
+    only if that summary was taken on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            text = f.read()
+        with open(MAC_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+# ------------------------------------------------------------------ CPU legs
+def oracle_sample_setup(w: synth.Workload, seed: int):
+    """Spectra of chunk 0 (all channels) by the oracle FFT, outside any timing."""
+    import oracle
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    geo = oracle.geometry(w.n_t, w.chunk_len, d)
+    fb, _ = synth.filterbank(w, seed=seed, rows=geo.L)
+    X = oracle.spectra(fb.T.astype(np.float64), geo, 0)
+    return d, geo, X
+
+
+def oracle_rate(d, geo, X, n_bins: int, rng: np.random.Generator):
+    """Time the oracle's phase-rotate-and-sum on n_bins sampled bins x all DMs x all
+    channels; returns (MACs, seconds)."""
+    import oracle
+    fixed = [0, 1, geo.K - 1]
+    extra = rng.choice(np.arange(2, geo.K - 1), size=max(0, n_bins - 3), replace=False)
+    bins = np.unique(np.concatenate([fixed, extra]).astype(np.int64))
+    t0 = time.perf_counter()
+    oracle.fdd_bins(X[:, bins], bins, geo.L, d)
+    dt = time.perf_counter() - t0
+    return d.shape[0] * d.shape[1] * bins.size, dt
+
+
+def cpu_baseline(w: synth.Workload, seed: int, target_s: float) -> dict:
+    import oracle
+    d, geo, X = oracle_sample_setup(w, seed)
+    rng = np.random.default_rng(seed)
+    macs, dt = oracle_rate(d, geo, X, 16, rng)
+    nb = int(min(geo.K, max(16, 16 * target_s / max(dt, 1e-3))))
+    macs, dt = oracle_rate(d, geo, X, nb, rng)
+    return {"value": macs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle phase-rotate-and-sum of {nb} sampled bins (incl. DC, 1, "
+                      f"Nyquist) x {w.n_dm} DMs x {w.n_chan} channels of chunk 0 "
+                      f"({macs:.3g} MACs in {dt:.1f} s; oracle FFT of the chunk untimed)",
+            "seconds": dt}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    import oracle
+    w = synth.WORKLOADS[args.workload]
+    d, geo, X = oracle_sample_setup(w, args.seed)
+    rng = np.random.default_rng(args.seed)
+    nb = 64
+    for _ in range(args.warmup):
+        oracle_rate(d, geo, X, nb, rng)
+    tot_macs, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        m, s = oracle_rate(d, geo, X, nb, rng)
+        tot_macs += m
+        tot_s += s
+    value = tot_macs / tot_s
+    sample = (f"each step: FP64 oracle phase-rotate-and-sum of {nb} sampled bins x {w.n_dm} DMs x "
+              f"{w.n_chan} channels of chunk 0 ({tot_macs // args.steps:.3g} MACs)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded survey-shaped filterbank)",
+            "config": workload_config(w, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_fdd(args, rank: int, world: int, dist) -> None:
+    import torch
+
+    import paper_2110_03482_gb300 as fdd
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    fdd.build()
+    w = synth.WORKLOADS[args.workload]
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    gpu_id = str(getattr(props, "uuid", "")) or str(local)
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+
+    fb, _ = synth.filterbank(w, seed=args.seed, beam=rank)
+    plan = fdd.Plan(**plan_params(w, fdd))
+    info = plan.info
+    stream = torch.cuda.current_stream()
+    d_in = torch.from_numpy(fb.reshape(-1)).cuda()
+    out_dtype = torch.float32
+    n_out = info["out_elems"] * (2 if w.output == "spectra" else 1)
+    d_out = torch.empty(n_out, dtype=out_dtype, device="cuda")
+    macs_step = macs_per_beam(w, info)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        plan.execute(d_in, d_out, stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    plan.profile_enable(True)
+    clocks = Clocks(gpu_id)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(d_in, d_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile_read()
+    plan.profile_enable(False)
+
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    total_macs = macs_step * args.steps * world
+    value = total_macs / (ms_max / 1e3)
+
+    # dominant kernel: the phasor-MAC
+    mac_n = prof["launches"]["mac"]
+    mac_ms = prof["ms"]["mac"] / max(mac_n, 1)
+    flops_launch = FLOPS_PER_MAC * min(info["dm_batch"], w.n_dm) * w.n_chan * info["n_bins"]
+    achieved = flops_launch / (mac_ms / 1e3) / 1e12
+    peaks = load_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    traffic = read_traffic_summary()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "mac_fp32_kernel (phase-rotate-and-sum, Eqs. 4 and 7)",
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x "
+                               f"{max_mhz:.0f} MHz max SM clock (FP32 FFMA; "
+                               "MEASURED_PEAKS.json has no FP32 figure)",
+                "algorithmic_flops_per_launch": flops_launch,
+                "mac_ms_per_launch": mac_ms, "mac_launches_timed": mac_n}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (peak * clk["sm_mhz"] / max_mhz)
+    stage_share = {k: v / max(sum(prof["ms"].values()), 1e-9) for k, v in prof["ms"].items()}
+    own_launches = prof["launches"]["unpack"] + prof["launches"]["mac"] + \
+        prof["launches"]["scatter"]
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(fb.reshape(-1)).pin_memory()
+        h_out = torch.empty(n_out, dtype=out_dtype, pin_memory=True)
+        plan.execute_host(h_in, h_out, stream)
+        torch.cuda.synchronize()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            plan.execute_host(h_in, h_out, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = f0.elapsed_time(f1)
+        if dist is not None:
+            t = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": macs_step * args.e2e_steps * world / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
+               "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
+               "ms_per_step": e_ms / args.e2e_steps}
+        del h_in, h_out
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.seed, args.cpu_seconds)
+    plan.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded survey-shaped filterbank)",
+                "config": dict(workload_config(w, info), parallelism=f"beam-replicas x{world}"),
+                "gpu_launches": own_launches,
+                "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "stage_ms_share": stage_share,
+                "fp32_frac_whole_step": value * FLOPS_PER_MAC / 1e12 / (peak * world),
+                "macs_per_step": macs_step * world}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_fdd(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * fdd.h -- C ABI of the GB300 (sm_103a) Fourier-domain dedispersion library.
+ *
+ * Fourier-domain dedispersion (FDD; Bassa et al., arXiv 2110.03482) replaces
+ * the per-channel time shifts of brute-force dedispersion (Sect. 2.1, Eq. 2)
+ * by phase rotations of each channel's Fourier transform (Sect. 2.2):
+ *
+ *   X[nu][k]  = sum_n x_nu[n] exp(-2 pi i k n / L)                  (Eq. 3)
+ *   d(nu, DM) = DM k_DM (nu^-2 - nu_ref^-2) / t_samp  [samples]      (Eq. 1)
+ *   Y[DM][k]  = sum_nu exp(+2 pi i k d(nu, DM) / L) X[nu][k]          (Eqs. 4, 7)
+ *   y[DM][n]  = (1/L) inverse real transform of Y[DM][.]             (Eq. 6)
+ *
+ * The phasor sign is the one that ADVANCES low channels so that a dispersed
+ * pulse lines up at its arrival time at nu_ref (the discard rule of Sect. 2.2
+ * puts the wrapped-around samples at the end of each series).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers (memory of the current CUDA
+ *    device); h_* are host pointers.  The caller owns every buffer it passes
+ *    and the stream; the plan owns its workspace, its FFT plans and tables.
+ *  - Streams are CUDA runtime streams (cudaStream_t); NULL means the legacy
+ *    default stream.  Execute calls are asynchronous on that stream, launch
+ *    only, never synchronise and never allocate.
+ *  - Every call returns an fdd_status.  Nothing aborts.  On failure a message
+ *    is kept per thread and returned by fdd_last_error().
+ *  - A plan must not be executed concurrently from two streams or threads.
+ *  - All complex data are interleaved single-precision (re, im) pairs.
+ */
+#ifndef FDD_H_
+#define FDD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDD_ABI_VERSION 1
+
+struct CUstream_st;
+typedef struct CUstream_st* fdd_stream_t; /* same type as cudaStream_t */
+
+typedef struct fdd_plan_s* fdd_plan_t;
+
+typedef enum fdd_status {
+  FDD_OK = 0,
+  FDD_ERR_INVALID_ARG = 1, /* a parameter or pointer is out of its domain   */
+  FDD_ERR_UNSUPPORTED = 2, /* valid, but not implemented by this library    */
+  FDD_ERR_ALLOC = 3,       /* device or host allocation failed (plan time)  */
+  FDD_ERR_CUDA = 4,        /* a CUDA runtime call failed                    */
+  FDD_ERR_CUFFT = 5,       /* a cuFFT call failed                           */
+  FDD_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up            */
+  FDD_ERR_DEVICE = 7       /* a kernel reported an error in its status word */
+} fdd_status;
+
+/* fdd_params.in_dtype: sample type of the input dynamic spectrum (Sect. 3:
+ * packed 8-bit data; float32 also accepted). */
+#define FDD_IN_U8 0
+#define FDD_IN_F32 1
+
+/* fdd_params.in_layout */
+#define FDD_LAYOUT_TIME_MAJOR 0 /* [beam][n_t][n_chan], filterbank order (Sect. 3) */
+#define FDD_LAYOUT_CHAN_MAJOR 1 /* [beam][n_chan][n_t]                              */
+
+/* fdd_params.output */
+#define FDD_OUT_TIME 0    /* float  [beam][n_dm][out_len]: back to time (Eq. 6) */
+#define FDD_OUT_SPECTRA 1 /* complex[beam][chunk][n_dm][n_bins]: Y of Eq. 7     */
+#define FDD_OUT_POWER 2   /* float  [beam][chunk][n_dm][n_bins]: |Y|^2 for
+                             periodicity searches (Sect. 5)                     */
+
+/* fdd_params.precision */
+#define FDD_PREC_FP32 0      /* FP32 phasors and accumulation (CUDA cores)       */
+#define FDD_PREC_BF16_HILO 1 /* tensor cores, BF16 hi+lo phasors (Sect. 5 future
+                                work); reserved, returns FDD_ERR_UNSUPPORTED     */
+
+typedef struct fdd_params {
+  int32_t n_chan;         /* observing channels N_nu, >= 1                          */
+  int32_t n_beams;        /* independent beams sharing the setup, >= 1              */
+  double nu_lo_mhz;       /* centre frequency of channel 0, MHz, > 0                */
+  double dnu_mhz;         /* channel spacing, MHz, nonzero, may be negative         */
+  double t_samp_s;        /* sampling time, s, > 0                                  */
+  int64_t n_t;            /* samples per channel and beam, >= 2                     */
+  const double* dm_list;  /* host array of n_dm trial DMs (pc cm^-3), >= 0; copied  */
+  int32_t n_dm;           /* number of trial DMs, >= 1                              */
+  int32_t in_dtype;       /* FDD_IN_U8 | FDD_IN_F32                                  */
+  int64_t chunk_len;      /* 0: whole series zero padded to a power of two (Sect. 3);
+                             L > 0: overlap-save chunks of L samples, even          */
+  double k_dm;            /* dispersion constant, MHz^2 pc^-1 cm^3 s; 0 selects the
+                             paper's (2.41e-4)^-1 (Sect. 2.1)                       */
+  double nu_ref_mhz;      /* reference frequency nu_0 of Eq. 1; 0 selects the
+                             highest channel centre; must be >= every channel centre */
+  int32_t in_layout;      /* FDD_LAYOUT_*                                            */
+  int32_t output;         /* FDD_OUT_*                                               */
+  int32_t precision;      /* FDD_PREC_*                                              */
+  int32_t reserved0;      /* must be 0                                               */
+  size_t workspace_limit; /* device bytes the plan may hold; 0 = library default    */
+} fdd_params;
+
+typedef struct fdd_info {
+  int64_t fft_len;         /* L, transform length                                  */
+  int64_t n_bins;          /* L/2 + 1                                              */
+  int64_t bin_pitch;       /* complex elements between spectra rows in workspace   */
+  int64_t n_chunks;        /* chunks per beam                                      */
+  int64_t hop;             /* output samples kept per chunk                        */
+  int64_t d_max;           /* ceil(largest delay) in samples (Sect. 2.2)           */
+  int64_t out_len;         /* time samples per DM in FDD_OUT_TIME output           */
+  int64_t valid_len;       /* leading output samples free of wrap-around           */
+  int64_t in_elems;        /* elements of the input buffer                         */
+  int64_t out_elems;       /* elements (float or complex) of a full output buffer  */
+  int64_t out_bytes;       /* bytes of a full output buffer                        */
+  int64_t workspace_bytes; /* device bytes held by the plan                        */
+  double dm0;              /* first trial DM                                       */
+  double ddm;              /* DM step of the (uniform) trial list                  */
+  int32_t dm_uniform;      /* 1 when the list is an arithmetic progression         */
+  int32_t dm_batch;        /* trials per internal batch (bounded by workspace)     */
+  int32_t mac_variant;     /* phasor-MAC kernel tile chosen for this plan          */
+  int32_t reserved1;
+} fdd_info;
+
+/* ABI version of the loaded library (FDD_ABI_VERSION at build time). */
+int32_t fdd_abi_version(void);
+
+/* Human-readable name of a status code.  Never NULL. */
+const char* fdd_status_string(fdd_status s);
+
+/* Last error message of the calling thread ("" if none).  Never NULL; valid
+ * until the next failing call on this thread. */
+const char* fdd_last_error(void);
+
+/* Fill *p with defaults: one beam, FP32, time-major u8 input, time output,
+ * paper k_DM, nu_ref at the top channel, no chunking.  Sizes stay zero. */
+void fdd_params_init(fdd_params* p);
+
+/*
+ * Host-only plan geometry (no CUDA call): validates *p and fills *out with
+ * the transform length, chunking (hop, d_max, out_len), DM-grid description
+ * and buffer sizes, exactly as fdd_plan would.  The chunking follows
+ * Sect. 2.2 (discard the last Delta t_max samples) and Sect. 3 (zero pad to
+ * a power of two): chunk_len == 0 gives one circular transform of
+ * L = next power of two >= n_t and out_len = n_t, of which the first
+ * valid_len = n_t - d_max are free of wrap-around; chunk_len == L gives
+ * hop = L - d_max, out_len = n_t - d_max and ceil(out_len / hop) chunks.
+ * Errors: FDD_ERR_INVALID_ARG (bad parameter), FDD_ERR_UNSUPPORTED.
+ */
+fdd_status fdd_plan_geometry(const fdd_params* p, fdd_info* out);
+
+/*
+ * Create a plan on the current CUDA device (Algorithm 1, initialisation:
+ * delay table, spin-frequency grid, FFT plans, device buffers).  Computes in
+ * FP64 the per-channel delay rate of Eq. 1 and, for a uniform DM list, the
+ * exact 64-bit fixed-point phase rates used by the kernels.  Allocates all
+ * device workspace here; execute calls never allocate.
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_UNSUPPORTED (non-uniform DM list,
+ * unsupported precision), FDD_ERR_ALLOC, FDD_ERR_CUDA, FDD_ERR_CUFFT.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out);
+
+/* Copy the plan's geometry into *out.  Also reports (FDD_ERR_DEVICE or
+ * FDD_ERR_TIMEOUT) a status word left by an earlier kernel; this call
+ * synchronises the plan's status read with the device. */
+fdd_status fdd_query(fdd_plan_t plan, fdd_info* out);
+
+/*
+ * Whole path for every trial DM (Algorithm 1 on device-resident data):
+ * unpack and transpose the input to channel-major float, zero pad / cut the
+ * overlap-save chunks, forward real FFT per channel (Eq. 3), phase-rotate-
+ * and-sum over channels (Eqs. 4, 7), then per the plan's output either the
+ * inverse real FFT scaled by 1/L with the valid samples of each chunk placed
+ * in order (Eq. 6), the spectra Y, or |Y|^2.
+ *   d_in : input, layout and type per the plan, info.in_elems elements.
+ *   d_out: output, info.out_elems elements of the output type:
+ *          TIME    float [beam][n_dm][out_len]
+ *          SPECTRA complex float [beam][chunk][n_dm][n_bins]
+ *          POWER   float [beam][chunk][n_dm][n_bins]
+ * Errors: FDD_ERR_INVALID_ARG (NULL plan or pointer), FDD_ERR_CUDA,
+ * FDD_ERR_CUFFT.
+ */
+fdd_status fdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream);
+
+/*
+ * The same for the trial DMs dm_first .. dm_first + n_dm - 1 only (the
+ * DM-outer batching of Sect. 3 / Algorithm 1).  d_out has the layout of
+ * fdd_execute with n_dm in place of the plan's trial count.
+ * Errors: as fdd_execute; FDD_ERR_INVALID_ARG for a range outside the list.
+ */
+fdd_status fdd_execute_dm_range(fdd_plan_t plan, const void* d_in, int32_t dm_first,
+                                int32_t n_dm, void* d_out, fdd_stream_t stream);
+
+/*
+ * End-to-end call with HOST buffers: copies h_in to the device, runs
+ * fdd_execute and copies the result back into h_out, all on the stream
+ * (page-locked host buffers make the copies asynchronous; the call returns
+ * after enqueueing them).  The device staging buffers are allocated on the
+ * first call of this function for the plan and reused afterwards.
+ * Errors: as fdd_execute, plus FDD_ERR_ALLOC on the first call.
+ */
+fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_stream_t stream);
+
+/*
+ * The hot path alone: phase-rotate-and-sum (Eqs. 4, 7) of given spectra.
+ *   d_X      : complex float [n_series][n_chan][x_pitch], bins 0 .. n_bins-1
+ *              of each row used (n_bins from the plan; x_pitch >= n_bins).
+ *   n_series : independent spectra sets (beams x chunks), >= 1.
+ *   dm_first, n_dm : trial range of the plan's DM list.
+ *   d_Y      : out_kind FDD_OUT_SPECTRA: complex float [n_series][n_dm][y_pitch];
+ *              out_kind FDD_OUT_POWER:   float [n_series][n_dm][y_pitch] (|Y|^2).
+ * No scaling is applied (Y is the plain sum of Eq. 7).
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA.
+ */
+fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pitch,
+                                  int32_t n_series, int32_t dm_first, int32_t n_dm,
+                                  void* d_Y, int64_t y_pitch, int32_t out_kind,
+                                  fdd_stream_t stream);
+
+/* Stages of the path timed by the profiling calls below. */
+#define FDD_STAGE_UNPACK 0  /* transpose_and_unpack + zero_pad (Algorithm 1)   */
+#define FDD_STAGE_R2C 1     /* channel transforms, Eq. 3 (cuFFT)                */
+#define FDD_STAGE_MAC 2     /* phase-rotate-and-sum, Eqs. 4 and 7               */
+#define FDD_STAGE_C2R 3     /* inverse transforms, Eq. 6 (cuFFT)                */
+#define FDD_STAGE_SCATTER 4 /* 1/L scaling and valid-sample placement           */
+#define FDD_STAGE_COUNT 5
+
+typedef struct fdd_profile {
+  int64_t launches[FDD_STAGE_COUNT]; /* timed launches per stage               */
+  double ms[FDD_STAGE_COUNT];        /* summed device time per stage, ms        */
+  int64_t dropped;                   /* launches not timed (event ring full)    */
+} fdd_profile;
+
+/*
+ * Profiling (no counterpart in the paper beyond its per-component runtime
+ * breakdown, Sect. 4.1): when enabled, execute calls record a CUDA event pair
+ * on the launching stream around every stage launch.  on != 0 creates the
+ * events (host-side, at this call), clears the counters and starts
+ * recording; on == 0 stops recording.  Up to 8192 launches are kept per
+ * reset; later ones are counted as dropped.
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA.
+ */
+fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on);
+
+/* Sum the recorded event pairs into *out.  Waits for the last recorded event
+ * (host synchronisation), so call it outside timed regions.
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA. */
+fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out);
+
+/* Release the plan and everything it owns (synchronises the device first).
+ * NULL is accepted and ignored. */
+fdd_status fdd_destroy(fdd_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDD_H_ */

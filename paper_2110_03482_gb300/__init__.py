@@ -1,0 +1,331 @@
+"""GB300 (sm_103a) Fourier-domain dedispersion -- Python binding of the C ABI.
+
+A thin ctypes layer over ``_lib/libfdd.so`` (declared in ``include/fdd.h``).
+Functions carry the C names and only marshal arguments; every step of the
+path runs in the library's CUDA kernels (and cuFFT for the channel
+transforms).  There is no CPU fallback: importing works without the library,
+but every call raises ``FddError`` until ``build()`` has produced it.
+
+Device memory and streams come from PyTorch tensors
+(``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``); plain
+integers (raw pointers) are accepted as well.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+LIB_PATH = _build_mod.LIB_PATH
+
+# Constants of include/fdd.h
+FDD_OK = 0
+FDD_ERR_INVALID_ARG = 1
+FDD_ERR_UNSUPPORTED = 2
+FDD_ERR_ALLOC = 3
+FDD_ERR_CUDA = 4
+FDD_ERR_CUFFT = 5
+FDD_ERR_TIMEOUT = 6
+FDD_ERR_DEVICE = 7
+FDD_IN_U8 = 0
+FDD_IN_F32 = 1
+FDD_LAYOUT_TIME_MAJOR = 0
+FDD_LAYOUT_CHAN_MAJOR = 1
+FDD_OUT_TIME = 0
+FDD_OUT_SPECTRA = 1
+FDD_OUT_POWER = 2
+FDD_PREC_FP32 = 0
+FDD_PREC_BF16_HILO = 1
+
+# Every symbol include/fdd.h declares.
+EXPORTS = [
+    "fdd_abi_version", "fdd_status_string", "fdd_last_error", "fdd_params_init",
+    "fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute", "fdd_execute_dm_range",
+    "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
+    "fdd_destroy",
+]
+
+FDD_STAGE_UNPACK = 0
+FDD_STAGE_R2C = 1
+FDD_STAGE_MAC = 2
+FDD_STAGE_C2R = 3
+FDD_STAGE_SCATTER = 4
+FDD_STAGE_COUNT = 5
+STAGE_NAMES = ["unpack", "r2c", "mac", "c2r", "scatter"]
+
+
+class fdd_params(ctypes.Structure):
+    _fields_ = [
+        ("n_chan", ctypes.c_int32),
+        ("n_beams", ctypes.c_int32),
+        ("nu_lo_mhz", ctypes.c_double),
+        ("dnu_mhz", ctypes.c_double),
+        ("t_samp_s", ctypes.c_double),
+        ("n_t", ctypes.c_int64),
+        ("dm_list", ctypes.POINTER(ctypes.c_double)),
+        ("n_dm", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int32),
+        ("chunk_len", ctypes.c_int64),
+        ("k_dm", ctypes.c_double),
+        ("nu_ref_mhz", ctypes.c_double),
+        ("in_layout", ctypes.c_int32),
+        ("output", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("workspace_limit", ctypes.c_size_t),
+    ]
+
+
+class fdd_info(ctypes.Structure):
+    _fields_ = [
+        ("fft_len", ctypes.c_int64),
+        ("n_bins", ctypes.c_int64),
+        ("bin_pitch", ctypes.c_int64),
+        ("n_chunks", ctypes.c_int64),
+        ("hop", ctypes.c_int64),
+        ("d_max", ctypes.c_int64),
+        ("out_len", ctypes.c_int64),
+        ("valid_len", ctypes.c_int64),
+        ("in_elems", ctypes.c_int64),
+        ("out_elems", ctypes.c_int64),
+        ("out_bytes", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64),
+        ("dm0", ctypes.c_double),
+        ("ddm", ctypes.c_double),
+        ("dm_uniform", ctypes.c_int32),
+        ("dm_batch", ctypes.c_int32),
+        ("mac_variant", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class fdd_profile(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64 * FDD_STAGE_COUNT),
+        ("ms", ctypes.c_double * FDD_STAGE_COUNT),
+        ("dropped", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {"launches": {STAGE_NAMES[i]: int(self.launches[i]) for i in range(FDD_STAGE_COUNT)},
+                "ms": {STAGE_NAMES[i]: float(self.ms[i]) for i in range(FDD_STAGE_COUNT)},
+                "dropped": int(self.dropped)}
+
+
+class FddError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a in-tree (nvcc)."""
+    return _build_mod.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises FddError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FddError(-1, f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_2110_03482_gb300.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.fdd_abi_version.restype = i32
+        L.fdd_status_string.restype = ctypes.c_char_p
+        L.fdd_status_string.argtypes = [ctypes.c_int]
+        L.fdd_last_error.restype = ctypes.c_char_p
+        L.fdd_params_init.argtypes = [ctypes.POINTER(fdd_params)]
+        L.fdd_params_init.restype = None
+        L.fdd_plan_geometry.argtypes = [ctypes.POINTER(fdd_params), ctypes.POINTER(fdd_info)]
+        L.fdd_plan.argtypes = [ctypes.POINTER(fdd_params), ctypes.POINTER(vp)]
+        L.fdd_query.argtypes = [vp, ctypes.POINTER(fdd_info)]
+        L.fdd_execute.argtypes = [vp, vp, vp, vp]
+        L.fdd_execute_dm_range.argtypes = [vp, vp, i32, i32, vp, vp]
+        L.fdd_execute_host.argtypes = [vp, vp, vp, vp]
+        L.fdd_dedisperse_spectra.argtypes = [vp, vp, i64, i32, i32, i32, vp, i64, i32, vp]
+        L.fdd_destroy.argtypes = [vp]
+        L.fdd_profile_enable.argtypes = [vp, i32]
+        L.fdd_profile_read.argtypes = [vp, ctypes.POINTER(fdd_profile)]
+        for name in ["fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute",
+                     "fdd_execute_dm_range", "fdd_execute_host", "fdd_dedisperse_spectra",
+                     "fdd_profile_enable", "fdd_profile_read", "fdd_destroy"]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != FDD_OK:
+        L = lib()
+        raise FddError(status, f"{L.fdd_status_string(status).decode()}: "
+                               f"{L.fdd_last_error().decode()}")
+
+
+def _ptr(x) -> int | None:
+    """Device/host address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+def fdd_abi_version() -> int:
+    return int(lib().fdd_abi_version())
+
+
+def fdd_status_string(status: int) -> str:
+    return lib().fdd_status_string(status).decode()
+
+
+def fdd_last_error() -> str:
+    return lib().fdd_last_error().decode()
+
+
+class Params:
+    """Owns an fdd_params and the DM array it points at."""
+
+    def __init__(self, **kw):
+        self.c = fdd_params()
+        lib().fdd_params_init(ctypes.byref(self.c))
+        dms = kw.pop("dm_list")
+        self.dms = np.ascontiguousarray(dms, dtype=np.float64)
+        self.c.dm_list = self.dms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.c.n_dm = int(self.dms.size)
+        for k, v in kw.items():
+            if not hasattr(self.c, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(self.c, k, v)
+
+
+def fdd_params_init(**kw) -> Params:
+    return Params(**kw)
+
+
+def fdd_plan_geometry(params: Params) -> dict:
+    info = fdd_info()
+    _check(lib().fdd_plan_geometry(ctypes.byref(params.c), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def fdd_plan(params: Params) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fdd_plan(ctypes.byref(params.c), ctypes.byref(h)))
+    return h.value
+
+
+def fdd_query(plan: int) -> dict:
+    info = fdd_info()
+    _check(lib().fdd_query(plan, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def fdd_execute(plan: int, d_in, d_out, stream=None) -> None:
+    _check(lib().fdd_execute(plan, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+
+def fdd_execute_dm_range(plan: int, d_in, dm_first: int, n_dm: int, d_out, stream=None) -> None:
+    _check(lib().fdd_execute_dm_range(plan, _ptr(d_in), dm_first, n_dm, _ptr(d_out),
+                                      _stream(stream)))
+
+
+def fdd_execute_host(plan: int, h_in, h_out, stream=None) -> None:
+    _check(lib().fdd_execute_host(plan, _ptr(h_in), _ptr(h_out), _stream(stream)))
+
+
+def fdd_dedisperse_spectra(plan: int, d_X, x_pitch: int, n_series: int, dm_first: int,
+                           n_dm: int, d_Y, y_pitch: int, out_kind: int = FDD_OUT_SPECTRA,
+                           stream=None) -> None:
+    _check(lib().fdd_dedisperse_spectra(plan, _ptr(d_X), x_pitch, n_series, dm_first, n_dm,
+                                        _ptr(d_Y), y_pitch, out_kind, _stream(stream)))
+
+
+def fdd_profile_enable(plan: int, on: bool = True) -> None:
+    _check(lib().fdd_profile_enable(plan, 1 if on else 0))
+
+
+def fdd_profile_read(plan: int) -> dict:
+    prof = fdd_profile()
+    _check(lib().fdd_profile_read(plan, ctypes.byref(prof)))
+    return prof.as_dict()
+
+
+def fdd_destroy(plan: int) -> None:
+    _check(lib().fdd_destroy(plan))
+
+
+# ------------------------------------------------------------------ convenience
+class Plan:
+    """RAII wrapper: Plan(**params) -> .execute(d_in, d_out) ... .close()."""
+
+    def __init__(self, **kw):
+        self.params = Params(**kw)
+        self.handle = fdd_plan(self.params)
+        self.info = fdd_query(self.handle)
+
+    def execute(self, d_in, d_out, stream=None):
+        fdd_execute(self.handle, d_in, d_out, stream)
+
+    def execute_dm_range(self, d_in, dm_first, n_dm, d_out, stream=None):
+        fdd_execute_dm_range(self.handle, d_in, dm_first, n_dm, d_out, stream)
+
+    def execute_host(self, h_in, h_out, stream=None):
+        fdd_execute_host(self.handle, h_in, h_out, stream)
+
+    def dedisperse_spectra(self, d_X, x_pitch, n_series, dm_first, n_dm, d_Y, y_pitch,
+                           out_kind=FDD_OUT_SPECTRA, stream=None):
+        fdd_dedisperse_spectra(self.handle, d_X, x_pitch, n_series, dm_first, n_dm, d_Y,
+                               y_pitch, out_kind, stream)
+
+    def query(self) -> dict:
+        return fdd_query(self.handle)
+
+    def profile_enable(self, on: bool = True):
+        fdd_profile_enable(self.handle, on)
+
+    def profile_read(self) -> dict:
+        return fdd_profile_read(self.handle)
+
+    def close(self):
+        if self.handle:
+            fdd_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

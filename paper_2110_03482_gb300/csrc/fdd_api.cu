@@ -1,0 +1,668 @@
+// fdd_api.cu -- the C ABI of include/fdd.h: parameter checks and plan
+// geometry, the FP64 plan constants (Eq. 1 delay rates and exact fixed-point
+// phase rates), device workspace, cuFFT plans for the channel transforms
+// (Eq. 3) and the inverse transforms (Eq. 6), and the execute orchestration
+// of Algorithm 1 (Sect. 3) on device-resident data.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fdd.h"
+#include "fdd_internal.h"
+
+struct fdd_plan_s {
+  fdd_params p{};
+  std::vector<double> dms;
+  fdd_info info{};
+  int device = -1;
+  double nu_ref = 0.0;
+  std::vector<double> rate;  // c_nu, samples per unit DM (Eq. 1 / t_samp)
+  std::vector<fdd::PhaseConst> pc_host;
+  fdd::PhaseConst* d_pc = nullptr;
+  float* d_xw = nullptr;      // [n_chan][L] channel series of one chunk
+  float2* d_X = nullptr;      // [n_chan][bin_pitch] their spectra
+  float2* d_Y = nullptr;      // [dm_batch][bin_pitch] dedispersed spectra (time output)
+  float* d_yt = nullptr;      // [dm_batch][L] inverse transforms (time output)
+  void* d_fftwork = nullptr;
+  int* d_status = nullptr;
+  cufftHandle r2c = 0, c2r = 0, c2r_tail = 0;
+  bool has_r2c = false, has_c2r = false, has_c2r_tail = false;
+  int c2r_tail_batch = 0;
+  void* d_in_stage = nullptr;
+  void* d_out_stage = nullptr;
+  size_t bytes_held = 0;
+  // profiling: event pairs around stage launches (fdd_profile_enable)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // 2 per slot
+  std::vector<int> prof_stage;
+  int prof_n = 0;
+  int64_t prof_dropped = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+fdd_status fail(fdd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define FDD_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(FDD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define FDD_CUFFT(call)                                                   \
+  do {                                                                    \
+    cufftResult r_ = (call);                                              \
+    if (r_ != CUFFT_SUCCESS) return fail(FDD_ERR_CUFFT, "%s: cufftResult %d", #call, (int)r_); \
+  } while (0)
+
+constexpr double kKdmPaper = 1.0 / 2.41e-4;  // Sect. 2.1
+constexpr size_t kDefaultWorkspace = size_t(16) << 30;
+constexpr size_t kMaxSmem = 227 * 1024;
+constexpr int kProfSlots = 4096;
+
+// Records an event pair around one stage launch when profiling is on.
+class StageTimer {
+ public:
+  StageTimer(fdd_plan_s* P, int stage, cudaStream_t s) : P_(P), s_(s) {
+    if (!P->prof_on) return;
+    if (P->prof_n >= kProfSlots) {
+      ++P->prof_dropped;
+      return;
+    }
+    idx_ = P->prof_n++;
+    P->prof_stage[idx_] = stage;
+    cudaEventRecord(P->prof_ev[2 * idx_], s_);
+  }
+  ~StageTimer() {
+    if (idx_ >= 0) cudaEventRecord(P_->prof_ev[2 * idx_ + 1], s_);
+  }
+  StageTimer(const StageTimer&) = delete;
+  StageTimer& operator=(const StageTimer&) = delete;
+
+ private:
+  fdd_plan_s* P_;
+  cudaStream_t s_;
+  int idx_ = -1;
+};
+
+int64_t next_pow2(int64_t n) {
+  int64_t p = 2;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
+
+// (x_hi + x_lo) mod 1 as a 64-bit fixed-point fraction of a cycle.
+uint64_t frac_to_fixed64(double x_hi, double x_lo) {
+  const double f = x_hi - std::floor(x_hi);     // exact
+  const double a = std::ldexp(f, 64);           // exact scaling, in [0, 2^64)
+  const double a_int = std::floor(a);
+  uint64_t ua;
+  if (a_int >= 18446744073709551616.0)
+    ua = 0;  // cannot happen for f < 1, kept for safety
+  else
+    ua = static_cast<uint64_t>(a_int);
+  const double rest = (a - a_int) + std::ldexp(x_lo, 64);  // small
+  const long long adj = std::llround(rest);
+  return ua + static_cast<uint64_t>(adj);  // wraps modulo 2^64
+}
+
+// (m * c / L) as an unevaluated double-double sum.
+void scaled_product(double m, double c, double L, double* hi, double* lo) {
+  const double p = m * c;
+  const double pe = std::fma(m, c, -p);  // exact error of the product
+  const double q = p / L;
+  const double r = std::fma(-q, L, p);   // exact remainder of the division
+  *hi = q;
+  *lo = (r + pe) / L;
+}
+
+fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* rate_out,
+                        double* nu_ref_out) {
+  if (!p) return fail(FDD_ERR_INVALID_ARG, "params is NULL");
+  if (!g) return fail(FDD_ERR_INVALID_ARG, "info is NULL");
+  if (p->n_chan < 1) return fail(FDD_ERR_INVALID_ARG, "n_chan must be >= 1 (got %d)", p->n_chan);
+  if (p->n_beams < 1) return fail(FDD_ERR_INVALID_ARG, "n_beams must be >= 1");
+  if (!(p->t_samp_s > 0.0) || !std::isfinite(p->t_samp_s))
+    return fail(FDD_ERR_INVALID_ARG, "t_samp_s must be > 0");
+  if (p->n_t < 2) return fail(FDD_ERR_INVALID_ARG, "n_t must be >= 2");
+  if (!p->dm_list) return fail(FDD_ERR_INVALID_ARG, "dm_list is NULL");
+  if (p->n_dm < 1) return fail(FDD_ERR_INVALID_ARG, "n_dm must be >= 1");
+  if (p->in_dtype != FDD_IN_U8 && p->in_dtype != FDD_IN_F32)
+    return fail(FDD_ERR_INVALID_ARG, "in_dtype %d unknown", p->in_dtype);
+  if (p->in_layout != FDD_LAYOUT_TIME_MAJOR && p->in_layout != FDD_LAYOUT_CHAN_MAJOR)
+    return fail(FDD_ERR_INVALID_ARG, "in_layout %d unknown", p->in_layout);
+  if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
+    return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
+  if (p->precision == FDD_PREC_BF16_HILO)
+    return fail(FDD_ERR_UNSUPPORTED, "precision FDD_PREC_BF16_HILO is not available in this build");
+  if (p->precision != FDD_PREC_FP32)
+    return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
+  if (p->reserved0 != 0) return fail(FDD_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (p->chunk_len < 0 || (p->chunk_len % 2) != 0)
+    return fail(FDD_ERR_INVALID_ARG, "chunk_len must be 0 or a positive even length");
+  if (!(p->dnu_mhz != 0.0) || !std::isfinite(p->dnu_mhz))
+    return fail(FDD_ERR_INVALID_ARG, "dnu_mhz must be nonzero");
+  if (!(p->k_dm >= 0.0) || !std::isfinite(p->k_dm))
+    return fail(FDD_ERR_INVALID_ARG, "k_dm must be >= 0 (0 selects the default)");
+
+  const int nc = p->n_chan;
+  double nu_max = -1.0, nu_min = std::numeric_limits<double>::infinity();
+  for (int c = 0; c < nc; ++c) {
+    const double nu = p->nu_lo_mhz + p->dnu_mhz * c;
+    if (!(nu > 0.0) || !std::isfinite(nu))
+      return fail(FDD_ERR_INVALID_ARG, "channel %d centre %.6g MHz is not positive", c, nu);
+    nu_max = nu > nu_max ? nu : nu_max;
+    nu_min = nu < nu_min ? nu : nu_min;
+  }
+  const double nu_ref = p->nu_ref_mhz == 0.0 ? nu_max : p->nu_ref_mhz;
+  if (!(nu_ref >= nu_max) || !std::isfinite(nu_ref))
+    return fail(FDD_ERR_INVALID_ARG, "nu_ref_mhz (%.9g) must be >= the highest channel centre (%.9g)",
+                nu_ref, nu_max);
+  const double kdm = p->k_dm == 0.0 ? kKdmPaper : p->k_dm;
+
+  std::vector<double> rate(nc);
+  double rate_max = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double nu = p->nu_lo_mhz + p->dnu_mhz * c;
+    rate[c] = kdm * (1.0 / (nu * nu) - 1.0 / (nu_ref * nu_ref)) / p->t_samp_s;
+    rate_max = rate[c] > rate_max ? rate[c] : rate_max;
+  }
+
+  double dm_max = 0.0;
+  for (int j = 0; j < p->n_dm; ++j) {
+    const double dm = p->dm_list[j];
+    if (!(dm >= 0.0) || !std::isfinite(dm))
+      return fail(FDD_ERR_INVALID_ARG, "dm_list[%d] = %g must be finite and >= 0", j, dm);
+    dm_max = dm > dm_max ? dm : dm_max;
+  }
+  // Uniform grid check: every entry within 4 ulp of dm0 + j ddm.
+  const double dm0 = p->dm_list[0];
+  const double ddm = p->n_dm > 1 ? (p->dm_list[p->n_dm - 1] - dm0) / (p->n_dm - 1) : 0.0;
+  const double tol = 4.0 * std::ldexp(std::numeric_limits<double>::epsilon(),
+                                      std::ilogb(dm_max > 1.0 ? dm_max : 1.0));
+  int uniform = 1;
+  for (int j = 0; j < p->n_dm && uniform; ++j)
+    if (std::fabs(p->dm_list[j] - (dm0 + j * ddm)) > tol) uniform = 0;
+  if (!uniform)
+    return fail(FDD_ERR_UNSUPPORTED, "non-uniform DM lists are not supported by this build");
+
+  const double max_delay = dm_max * rate_max;  // both factors are >= 0
+  if (max_delay > 4.0e18) return fail(FDD_ERR_INVALID_ARG, "delays overflow");
+  const int64_t d_max = static_cast<int64_t>(std::ceil(max_delay));
+
+  std::memset(g, 0, sizeof *g);
+  int64_t L, hop, n_chunks, out_len, valid_len;
+  if (p->chunk_len == 0) {
+    L = next_pow2(p->n_t);
+    hop = p->n_t;
+    n_chunks = 1;
+    out_len = p->n_t;
+    valid_len = p->n_t > d_max ? p->n_t - d_max : 0;
+  } else {
+    L = p->chunk_len;
+    hop = L - d_max;
+    if (hop <= 0)
+      return fail(FDD_ERR_INVALID_ARG,
+                  "chunk_len %lld does not exceed the largest delay (%lld samples)",
+                  (long long)L, (long long)d_max);
+    out_len = p->n_t - d_max;
+    if (out_len <= 0)
+      return fail(FDD_ERR_INVALID_ARG, "n_t %lld does not exceed the largest delay %lld",
+                  (long long)p->n_t, (long long)d_max);
+    n_chunks = (out_len + hop - 1) / hop;
+    valid_len = out_len;
+  }
+  const int64_t n_bins = L / 2 + 1;
+  if (L > (int64_t(1) << 30)) return fail(FDD_ERR_UNSUPPORTED, "transform length above 2^30");
+  // The kernels form k * j in 32-bit integers.
+  if (static_cast<double>(n_bins - 1) * static_cast<double>(p->n_dm - 1) >= 4294967296.0)
+    return fail(FDD_ERR_UNSUPPORTED, "(n_bins-1)*(n_dm-1) must be below 2^32");
+
+  g->fft_len = L;
+  g->n_bins = n_bins;
+  g->bin_pitch = round_up(n_bins, 64);
+  g->n_chunks = n_chunks;
+  g->hop = hop;
+  g->d_max = d_max;
+  g->out_len = out_len;
+  g->valid_len = valid_len;
+  g->in_elems = static_cast<int64_t>(p->n_beams) * p->n_t * nc;
+  if (p->output == FDD_OUT_TIME) {
+    g->out_elems = static_cast<int64_t>(p->n_beams) * p->n_dm * out_len;
+    g->out_bytes = g->out_elems * 4;
+  } else {
+    g->out_elems = static_cast<int64_t>(p->n_beams) * n_chunks * p->n_dm * n_bins;
+    g->out_bytes = g->out_elems * (p->output == FDD_OUT_SPECTRA ? 8 : 4);
+  }
+  g->dm0 = dm0;
+  g->ddm = ddm;
+  g->dm_uniform = uniform;
+  g->mac_variant = fdd::mac_variant_for(p->n_dm);
+  if (fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
+    return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
+
+  const size_t fixed = sizeof(fdd::PhaseConst) * nc + sizeof(float) * size_t(nc) * L +
+                       sizeof(float2) * size_t(nc) * g->bin_pitch + 256;
+  const size_t limit = p->workspace_limit ? p->workspace_limit : kDefaultWorkspace;
+  int64_t batch = p->n_dm;
+  size_t per_dm = 0;
+  if (p->output == FDD_OUT_TIME) {
+    per_dm = sizeof(float2) * g->bin_pitch + sizeof(float) * L;
+    if (fixed + per_dm > limit)
+      return fail(FDD_ERR_INVALID_ARG, "workspace_limit %zu is below the minimum %zu", limit,
+                  fixed + per_dm);
+    const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
+    if (fit < batch) {
+      const int64_t blk = fdd::mac_variant_trials_per_block(g->mac_variant);
+      batch = fit >= blk ? fit / blk * blk : fit;
+    }
+    if (batch > 65535) batch = 65535 / 64 * 64;
+  }
+  g->dm_batch = static_cast<int32_t>(batch);
+  g->workspace_bytes = static_cast<int64_t>(fixed + per_dm * batch);
+  if (rate_out) *rate_out = std::move(rate);
+  if (nu_ref_out) *nu_ref_out = nu_ref;
+  return FDD_OK;
+}
+
+void release(fdd_plan_s* P) {
+  if (!P) return;
+  if (P->has_r2c) cufftDestroy(P->r2c);
+  if (P->has_c2r) cufftDestroy(P->c2r);
+  if (P->has_c2r_tail) cufftDestroy(P->c2r_tail);
+  void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_fftwork, P->d_status,
+                  P->d_in_stage, P->d_out_stage};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (cudaEvent_t e : P->prof_ev)
+    if (e) cudaEventDestroy(e);
+  delete P;
+}
+
+fdd_status dev_alloc(fdd_plan_s* P, void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(FDD_ERR_ALLOC, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  P->bytes_held += bytes;
+  return FDD_OK;
+}
+
+fdd_status check_device(const fdd_plan_s* P) {
+  int dev = -1;
+  FDD_CUDA(cudaGetDevice(&dev));
+  if (dev != P->device)
+    return fail(FDD_ERR_INVALID_ARG, "plan was made on device %d, current device is %d", P->device,
+                dev);
+  return FDD_OK;
+}
+
+fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
+               cudaStream_t s) {
+  const fdd_params& p = P->p;
+  const fdd_info& g = P->info;
+  const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
+  const int64_t beam_elems = p.n_t * static_cast<int64_t>(p.n_chan);
+  FDD_CUFFT(cufftSetStream(P->r2c, s));
+  if (P->has_c2r) FDD_CUFFT(cufftSetStream(P->c2r, s));
+  if (P->has_c2r_tail) FDD_CUFFT(cufftSetStream(P->c2r_tail, s));
+
+  for (int b = 0; b < p.n_beams; ++b) {
+    const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
+    for (int64_t c = 0; c < g.n_chunks; ++c) {
+      fdd::UnpackArgs ua{in_b, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop, g.fft_len,
+                         P->d_xw, g.fft_len};
+      {
+        StageTimer t(P, FDD_STAGE_UNPACK, s);
+        FDD_CUDA(fdd::launch_unpack(ua, s));
+      }
+      {
+        StageTimer t(P, FDD_STAGE_R2C, s);
+        FDD_CUFFT(cufftExecR2C(P->r2c, P->d_xw, reinterpret_cast<cufftComplex*>(P->d_X)));
+      }
+
+      fdd::MacArgs m{};
+      m.X = P->d_X;
+      m.x_series_stride = 0;
+      m.x_chan_stride = g.bin_pitch;
+      m.pc = P->d_pc;
+      m.n_chan = p.n_chan;
+      m.n_bins = static_cast<int>(g.n_bins);
+      m.n_series = 1;
+      m.scale = 1.0f;
+      m.status = P->d_status;
+      if (p.output == FDD_OUT_TIME) {
+        for (int j0 = dm_first; j0 < dm_first + n_dm; j0 += g.dm_batch) {
+          const int nb = (dm_first + n_dm - j0) < g.dm_batch ? (dm_first + n_dm - j0) : g.dm_batch;
+          m.j_begin = j0;
+          m.n_dm = nb;
+          m.Y = P->d_Y;
+          m.y_series_stride = 0;
+          m.y_dm_stride = g.bin_pitch;
+          m.out_kind = 1;
+          m.real_bin_a = 0;                           // DC and Nyquist of a real
+          m.real_bin_b = static_cast<int>(g.fft_len / 2);  // series: real parts only
+          {
+            StageTimer t(P, FDD_STAGE_MAC, s);
+            FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
+          }
+          cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
+          {
+            StageTimer t(P, FDD_STAGE_C2R, s);
+            FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(P->d_Y), P->d_yt));
+          }
+          const int64_t keep = (g.out_len - c * g.hop) < g.hop ? (g.out_len - c * g.hop) : g.hop;
+          fdd::ScatterArgs sa{};
+          sa.src = P->d_yt;
+          sa.src_stride = g.fft_len;
+          sa.dst = static_cast<float*>(d_out) +
+                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * g.hop;
+          sa.dst_stride = g.out_len;
+          sa.n_dm = nb;
+          sa.n_keep = keep;
+          sa.scale = static_cast<float>(1.0 / static_cast<double>(g.fft_len));
+          StageTimer t(P, FDD_STAGE_SCATTER, s);
+          FDD_CUDA(fdd::launch_scatter(sa, s));
+        }
+      } else {
+        const int64_t row0 = (static_cast<int64_t>(b) * g.n_chunks + c) * n_dm;
+        m.j_begin = dm_first;
+        m.n_dm = n_dm;
+        m.y_series_stride = 0;
+        m.y_dm_stride = g.n_bins;
+        m.real_bin_a = -1;
+        m.real_bin_b = -1;
+        if (p.output == FDD_OUT_SPECTRA) {
+          m.out_kind = 1;
+          m.Y = static_cast<float2*>(d_out) + row0 * g.n_bins;
+        } else {
+          m.out_kind = 2;
+          m.Y = static_cast<float*>(d_out) + row0 * g.n_bins;
+        }
+        StageTimer t(P, FDD_STAGE_MAC, s);
+        FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
+      }
+    }
+  }
+  return FDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t fdd_abi_version(void) { return FDD_ABI_VERSION; }
+
+const char* fdd_status_string(fdd_status s) {
+  switch (s) {
+    case FDD_OK: return "FDD_OK";
+    case FDD_ERR_INVALID_ARG: return "FDD_ERR_INVALID_ARG";
+    case FDD_ERR_UNSUPPORTED: return "FDD_ERR_UNSUPPORTED";
+    case FDD_ERR_ALLOC: return "FDD_ERR_ALLOC";
+    case FDD_ERR_CUDA: return "FDD_ERR_CUDA";
+    case FDD_ERR_CUFFT: return "FDD_ERR_CUFFT";
+    case FDD_ERR_TIMEOUT: return "FDD_ERR_TIMEOUT";
+    case FDD_ERR_DEVICE: return "FDD_ERR_DEVICE";
+  }
+  return "FDD_ERR_UNKNOWN";
+}
+
+const char* fdd_last_error(void) { return g_err.c_str(); }
+
+void fdd_params_init(fdd_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->n_beams = 1;
+  p->in_dtype = FDD_IN_U8;
+  p->in_layout = FDD_LAYOUT_TIME_MAJOR;
+  p->output = FDD_OUT_TIME;
+  p->precision = FDD_PREC_FP32;
+}
+
+fdd_status fdd_plan_geometry(const fdd_params* p, fdd_info* out) {
+  return compute_plan(p, out, nullptr, nullptr);
+}
+
+fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
+  if (!out) return fail(FDD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  fdd_plan_s* P = new (std::nothrow) fdd_plan_s();
+  if (!P) return fail(FDD_ERR_ALLOC, "host allocation failed");
+  std::unique_ptr<fdd_plan_s, void (*)(fdd_plan_s*)> guard(P, release);
+
+  fdd_status st = compute_plan(p, &P->info, &P->rate, &P->nu_ref);
+  if (st != FDD_OK) return st;
+  P->p = *p;
+  P->dms.assign(p->dm_list, p->dm_list + p->n_dm);
+  P->p.dm_list = nullptr;
+
+  FDD_CUDA(cudaGetDevice(&P->device));
+  int major = 0, minor = 0;
+  FDD_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, P->device));
+  FDD_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, P->device));
+  if (major != 10 || minor != 3)
+    return fail(FDD_ERR_UNSUPPORTED, "kernels are built for sm_103a; device is sm_%d%d", major,
+                minor);
+  fdd_info& g = P->info;
+  FDD_CUDA(fdd::mac_prepare(g.mac_variant, p->n_chan));
+
+  // Exact fixed-point phase rates (see fdd_internal.h).
+  const double L = static_cast<double>(g.fft_len);
+  P->pc_host.resize(p->n_chan);
+  for (int c = 0; c < p->n_chan; ++c) {
+    double hi, lo;
+    scaled_product(g.dm0, P->rate[c], L, &hi, &lo);
+    const uint64_t u = frac_to_fixed64(hi, lo);
+    scaled_product(g.ddm, P->rate[c], L, &hi, &lo);
+    const uint64_t v = frac_to_fixed64(hi, lo);
+    P->pc_host[c] = fdd::PhaseConst{static_cast<uint32_t>(u), static_cast<uint32_t>(u >> 32),
+                                    static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32)};
+  }
+
+  const int nc = p->n_chan;
+  if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_pc), sizeof(fdd::PhaseConst) * nc)))
+    return st;
+  if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_status), 256))) return st;
+  if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_xw), sizeof(float) * size_t(nc) * g.fft_len)))
+    return st;
+  if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_X),
+                      sizeof(float2) * size_t(nc) * g.bin_pitch)))
+    return st;
+  if (p->output == FDD_OUT_TIME) {
+    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_Y),
+                        sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch)))
+      return st;
+    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_yt),
+                        sizeof(float) * size_t(g.dm_batch) * g.fft_len)))
+      return st;
+  }
+  FDD_CUDA(cudaMemcpy(P->d_pc, P->pc_host.data(), sizeof(fdd::PhaseConst) * nc,
+                      cudaMemcpyHostToDevice));
+  FDD_CUDA(cudaMemset(P->d_status, 0, 256));
+
+  // cuFFT plans with caller-owned work area (execute never allocates).
+  long long n[1] = {g.fft_len};
+  long long emb_real[1] = {g.fft_len};
+  long long emb_cplx[1] = {g.bin_pitch};
+  size_t w_r2c = 0, w_c2r = 0, w_tail = 0;
+  FDD_CUFFT(cufftCreate(&P->r2c));
+  P->has_r2c = true;
+  FDD_CUFFT(cufftSetAutoAllocation(P->r2c, 0));
+  FDD_CUFFT(cufftMakePlanMany64(P->r2c, 1, n, emb_real, 1, g.fft_len, emb_cplx, 1, g.bin_pitch,
+                                CUFFT_R2C, nc, &w_r2c));
+  if (p->output == FDD_OUT_TIME) {
+    FDD_CUFFT(cufftCreate(&P->c2r));
+    P->has_c2r = true;
+    FDD_CUFFT(cufftSetAutoAllocation(P->c2r, 0));
+    FDD_CUFFT(cufftMakePlanMany64(P->c2r, 1, n, emb_cplx, 1, g.bin_pitch, emb_real, 1, g.fft_len,
+                                  CUFFT_C2R, g.dm_batch, &w_c2r));
+    const int tail = p->n_dm % g.dm_batch;
+    if (tail != 0) {
+      FDD_CUFFT(cufftCreate(&P->c2r_tail));
+      P->has_c2r_tail = true;
+      P->c2r_tail_batch = tail;
+      FDD_CUFFT(cufftSetAutoAllocation(P->c2r_tail, 0));
+      FDD_CUFFT(cufftMakePlanMany64(P->c2r_tail, 1, n, emb_cplx, 1, g.bin_pitch, emb_real, 1,
+                                    g.fft_len, CUFFT_C2R, tail, &w_tail));
+    }
+  }
+  size_t w = w_r2c > w_c2r ? w_r2c : w_c2r;
+  w = w > w_tail ? w : w_tail;
+  if (w > 0) {
+    if ((st = dev_alloc(P, &P->d_fftwork, w))) return st;
+    FDD_CUFFT(cufftSetWorkArea(P->r2c, P->d_fftwork));
+    if (P->has_c2r) FDD_CUFFT(cufftSetWorkArea(P->c2r, P->d_fftwork));
+    if (P->has_c2r_tail) FDD_CUFFT(cufftSetWorkArea(P->c2r_tail, P->d_fftwork));
+  }
+  g.workspace_bytes = static_cast<int64_t>(P->bytes_held);
+  *out = guard.release();
+  return FDD_OK;
+}
+
+fdd_status fdd_query(fdd_plan_t plan, fdd_info* out) {
+  if (!plan || !out) return fail(FDD_ERR_INVALID_ARG, "NULL plan or info");
+  *out = plan->info;
+  int word = 0;
+  FDD_CUDA(cudaMemcpy(&word, plan->d_status, sizeof word, cudaMemcpyDeviceToHost));
+  if (word == FDD_ERR_TIMEOUT) return fail(FDD_ERR_TIMEOUT, "a device-side wait timed out");
+  if (word != 0) return fail(FDD_ERR_DEVICE, "device status word %d", word);
+  return FDD_OK;
+}
+
+fdd_status fdd_execute_dm_range(fdd_plan_t plan, const void* d_in, int32_t dm_first,
+                                int32_t n_dm, void* d_out, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  if (!d_in || !d_out) return fail(FDD_ERR_INVALID_ARG, "NULL input or output");
+  if (dm_first < 0 || n_dm < 1 || dm_first + static_cast<int64_t>(n_dm) > plan->p.n_dm)
+    return fail(FDD_ERR_INVALID_ARG, "trial range [%d, %d) outside [0, %d)", dm_first,
+                dm_first + n_dm, plan->p.n_dm);
+  fdd_status st = check_device(plan);
+  if (st != FDD_OK) return st;
+  return run(plan, d_in, dm_first, n_dm, d_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+fdd_status fdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  return fdd_execute_dm_range(plan, d_in, 0, plan->p.n_dm, d_out, stream);
+}
+
+fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  if (!h_in || !h_out) return fail(FDD_ERR_INVALID_ARG, "NULL input or output");
+  fdd_status st = check_device(plan);
+  if (st != FDD_OK) return st;
+  const size_t in_bytes =
+      static_cast<size_t>(plan->info.in_elems) * (plan->p.in_dtype == FDD_IN_U8 ? 1 : 4);
+  const size_t out_bytes = static_cast<size_t>(plan->info.out_bytes);
+  if (!plan->d_in_stage && (st = dev_alloc(plan, &plan->d_in_stage, in_bytes))) return st;
+  if (!plan->d_out_stage && (st = dev_alloc(plan, &plan->d_out_stage, out_bytes))) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FDD_CUDA(cudaMemcpyAsync(plan->d_in_stage, h_in, in_bytes, cudaMemcpyHostToDevice, s));
+  st = run(plan, plan->d_in_stage, 0, plan->p.n_dm, plan->d_out_stage, s);
+  if (st != FDD_OK) return st;
+  FDD_CUDA(cudaMemcpyAsync(h_out, plan->d_out_stage, out_bytes, cudaMemcpyDeviceToHost, s));
+  return FDD_OK;
+}
+
+fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pitch,
+                                  int32_t n_series, int32_t dm_first, int32_t n_dm, void* d_Y,
+                                  int64_t y_pitch, int32_t out_kind, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  if (!d_X || !d_Y) return fail(FDD_ERR_INVALID_ARG, "NULL spectra pointer");
+  const fdd_info& g = plan->info;
+  if (x_pitch < g.n_bins || y_pitch < g.n_bins)
+    return fail(FDD_ERR_INVALID_ARG, "pitches must be >= n_bins (%lld)", (long long)g.n_bins);
+  if (n_series < 1 || n_series > 65535)
+    return fail(FDD_ERR_INVALID_ARG, "n_series must be in [1, 65535]");
+  if (dm_first < 0 || n_dm < 1 || dm_first + static_cast<int64_t>(n_dm) > plan->p.n_dm)
+    return fail(FDD_ERR_INVALID_ARG, "trial range outside the plan's list");
+  if (out_kind != FDD_OUT_SPECTRA && out_kind != FDD_OUT_POWER)
+    return fail(FDD_ERR_INVALID_ARG, "out_kind must be FDD_OUT_SPECTRA or FDD_OUT_POWER");
+  fdd_status st = check_device(plan);
+  if (st != FDD_OK) return st;
+  fdd::MacArgs m{};
+  m.X = static_cast<const float2*>(d_X);
+  m.x_chan_stride = x_pitch;
+  m.x_series_stride = x_pitch * plan->p.n_chan;
+  m.pc = plan->d_pc;
+  m.n_chan = plan->p.n_chan;
+  m.n_bins = static_cast<int>(g.n_bins);
+  m.n_series = n_series;
+  m.j_begin = dm_first;
+  m.n_dm = n_dm;
+  m.Y = d_Y;
+  m.y_dm_stride = y_pitch;
+  m.y_series_stride = y_pitch * n_dm;
+  m.out_kind = out_kind == FDD_OUT_SPECTRA ? 1 : 2;
+  m.scale = 1.0f;
+  m.real_bin_a = -1;
+  m.real_bin_b = -1;
+  m.status = plan->d_status;
+  StageTimer t(plan, FDD_STAGE_MAC, reinterpret_cast<cudaStream_t>(stream));
+  FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));
+  return FDD_OK;
+}
+
+fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  if (on) {
+    if (plan->prof_ev.empty()) {
+      plan->prof_ev.assign(2 * kProfSlots, nullptr);
+      plan->prof_stage.assign(kProfSlots, 0);
+      for (auto& e : plan->prof_ev) FDD_CUDA(cudaEventCreate(&e));
+    }
+    plan->prof_n = 0;
+    plan->prof_dropped = 0;
+  }
+  plan->prof_on = on != 0;
+  return FDD_OK;
+}
+
+fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out) {
+  if (!plan || !out) return fail(FDD_ERR_INVALID_ARG, "NULL plan or profile");
+  std::memset(out, 0, sizeof *out);
+  out->dropped = plan->prof_dropped;
+  if (plan->prof_n == 0) return FDD_OK;
+  FDD_CUDA(cudaEventSynchronize(plan->prof_ev[2 * (plan->prof_n - 1) + 1]));
+  for (int i = 0; i < plan->prof_n; ++i) {
+    float ms = 0.f;
+    FDD_CUDA(cudaEventElapsedTime(&ms, plan->prof_ev[2 * i], plan->prof_ev[2 * i + 1]));
+    const int st = plan->prof_stage[i];
+    out->launches[st] += 1;
+    out->ms[st] += ms;
+  }
+  return FDD_OK;
+}
+
+fdd_status fdd_destroy(fdd_plan_t plan) {
+  if (!plan) return FDD_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  release(plan);
+  if (e != cudaSuccess)
+    return fail(FDD_ERR_CUDA, "cudaDeviceSynchronize: %s", cudaGetErrorString(e));
+  return FDD_OK;
+}
+
+}  // extern "C"

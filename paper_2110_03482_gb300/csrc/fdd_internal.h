@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdd {
+
+// Per-channel 64-bit fixed-point phase constants (fractions of a cycle):
+//   u = frac(DM_0 * c_nu / L) * 2^64,  v = frac(dDM * c_nu / L) * 2^64,
+// with c_nu the delay rate of Eq. 1 in samples per unit DM.  The phase of the
+// Eq. 4 phasor for bin k and trial j is then exactly (k u + k j v) mod 2^64.
+struct PhaseConst {
+  uint32_t u_lo, u_hi, v_lo, v_hi;
+};
+
+// Phase-rotate-and-sum launch arguments (Eq. 7 over one set of spectra).
+struct MacArgs {
+  const float2* X;          // [n_series][n_chan][x_chan_stride]
+  int64_t x_series_stride;  // complex elements
+  int64_t x_chan_stride;    // complex elements
+  const PhaseConst* pc;     // [n_chan]
+  int n_chan;
+  int n_bins;
+  int n_series;
+  int j_begin;              // first global trial index handled by this call
+  int n_dm;                 // trials handled by this call
+  void* Y;                  // [n_series][n_dm][y_dm_stride] complex or float
+  int64_t y_series_stride;  // elements of the output type
+  int64_t y_dm_stride;      // elements of the output type
+  int out_kind;             // 1 = complex spectra, 2 = |Y|^2
+  float scale;              // multiplies Y before the store (power: |scale Y|^2)
+  int real_bin_a;           // bins whose imaginary part is set to zero, or -1
+  int real_bin_b;
+  int* status;              // device status word (may be NULL)
+};
+
+// Kernel tile variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu).
+enum MacVariant { MAC_V8x8 = 0, MAC_V4x8 = 1, MAC_V4x4 = 2, MAC_NUM_VARIANTS = 3 };
+int mac_variant_for(int n_dm);
+int mac_variant_trials_per_block(int variant);
+cudaError_t mac_prepare(int variant, int n_chan);  // kernel attributes (host, once)
+cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s);
+size_t mac_smem_bytes(int variant, int n_chan);
+
+// Unpack / transpose / chunk / zero-pad (Sect. 3: transpose_and_unpack and
+// zero_pad of Algorithm 1) of one beam into channel-major float series.
+struct UnpackArgs {
+  const void* in;        // one beam of input
+  int in_dtype;          // FDD_IN_U8 | FDD_IN_F32
+  int in_layout;         // FDD_LAYOUT_*
+  int n_chan;
+  int64_t n_t;
+  int64_t t_begin;       // first input sample of the chunk
+  int64_t L;             // samples per output series
+  float* out;            // [n_chan][out_stride]
+  int64_t out_stride;
+};
+cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t s);
+
+// Scale by 1/L and place the first n_keep samples of each DM series of one
+// chunk into the time-domain output (the discard rule of Sect. 2.2).
+struct ScatterArgs {
+  const float* src;      // [n_dm][src_stride]
+  int64_t src_stride;
+  float* dst;            // row r of the output at dst + r * dst_stride
+  int64_t dst_stride;
+  int n_dm;
+  int64_t n_keep;
+  float scale;
+};
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
+
+}  // namespace fdd

@@ -1,0 +1,108 @@
+// fdd_prep.cu -- the HBM-bound steps around the phasor-MAC:
+//  * unpack: transpose_and_unpack + zero_pad of Algorithm 1 (Sect. 3), here
+//    also cutting one overlap-save chunk: a time-major [n_t][n_chan] u8/f32
+//    beam becomes channel-major float series of L samples, zero beyond n_t;
+//  * scatter: apply_scaling of Algorithm 1 (1/L) and keep the first n_keep
+//    samples of each inverse-transformed DM series (discard rule, Sect. 2.2).
+#include "fdd_internal.h"
+#include "fdd.h"
+
+namespace fdd {
+namespace {
+
+constexpr int kTile = 32;
+
+// 32 x 32 tile through shared memory: coalesced reads along channels,
+// coalesced writes along time.
+template <typename Tin>
+__global__ void __launch_bounds__(256) unpack_time_major_kernel(const Tin* __restrict__ in,
+                                                                int n_chan, int64_t n_t,
+                                                                int64_t t_begin, int64_t L,
+                                                                float* __restrict__ out,
+                                                                int64_t out_stride) {
+  __shared__ float tile[kTile][kTile + 1];
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * kTile;
+  const int c0 = blockIdx.y * kTile;
+#pragma unroll
+  for (int r = threadIdx.y; r < kTile; r += 8) {
+    const int64_t n = n0 + r;
+    const int64_t t = t_begin + n;
+    const int c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (n < L && t < n_t && c < n_chan) v = static_cast<float>(in[t * n_chan + c]);
+    tile[r][threadIdx.x] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = threadIdx.y; r < kTile; r += 8) {
+    const int c = c0 + r;
+    const int64_t n = n0 + threadIdx.x;
+    if (c < n_chan && n < L) out[static_cast<int64_t>(c) * out_stride + n] = tile[threadIdx.x][r];
+  }
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(256) unpack_chan_major_kernel(const Tin* __restrict__ in,
+                                                                int n_chan, int64_t n_t,
+                                                                int64_t t_begin, int64_t L,
+                                                                float* __restrict__ out,
+                                                                int64_t out_stride) {
+  const int c = blockIdx.y;
+  for (int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; n < L;
+       n += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t t = t_begin + n;
+    out[static_cast<int64_t>(c) * out_stride + n] =
+        (t < n_t) ? static_cast<float>(in[static_cast<int64_t>(c) * n_t + t]) : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(const float* __restrict__ src,
+                                                      int64_t src_stride, float* __restrict__ dst,
+                                                      int64_t dst_stride, int64_t n_keep,
+                                                      float scale) {
+  const int r = blockIdx.y;
+  const float* s = src + static_cast<int64_t>(r) * src_stride;
+  float* d = dst + static_cast<int64_t>(r) * dst_stride;
+  for (int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; n < n_keep;
+       n += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    d[n] = s[n] * scale;
+}
+
+}  // namespace
+
+cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t s) {
+  if (a.in_layout == FDD_LAYOUT_TIME_MAJOR) {
+    dim3 grid(static_cast<unsigned>((a.L + kTile - 1) / kTile), (a.n_chan + kTile - 1) / kTile);
+    dim3 block(kTile, 8);
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    if (a.in_dtype == FDD_IN_U8)
+      unpack_time_major_kernel<uint8_t><<<grid, block, 0, s>>>(
+          static_cast<const uint8_t*>(a.in), a.n_chan, a.n_t, a.t_begin, a.L, a.out, a.out_stride);
+    else
+      unpack_time_major_kernel<float><<<grid, block, 0, s>>>(
+          static_cast<const float*>(a.in), a.n_chan, a.n_t, a.t_begin, a.L, a.out, a.out_stride);
+  } else {
+    const int64_t blocks = (a.L + 255) / 256;
+    dim3 grid(static_cast<unsigned>(blocks < 4096 ? blocks : 4096), a.n_chan);
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    if (a.in_dtype == FDD_IN_U8)
+      unpack_chan_major_kernel<uint8_t><<<grid, 256, 0, s>>>(
+          static_cast<const uint8_t*>(a.in), a.n_chan, a.n_t, a.t_begin, a.L, a.out, a.out_stride);
+    else
+      unpack_chan_major_kernel<float><<<grid, 256, 0, s>>>(
+          static_cast<const float*>(a.in), a.n_chan, a.n_t, a.t_begin, a.L, a.out, a.out_stride);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
+  if (a.n_dm <= 0 || a.n_keep <= 0) return cudaSuccess;
+  if (a.n_dm > 65535) return cudaErrorInvalidConfiguration;
+  const int64_t blocks = (a.n_keep + 255) / 256;
+  dim3 grid(static_cast<unsigned>(blocks < 1024 ? blocks : 1024), a.n_dm);
+  scatter_kernel<<<grid, 256, 0, s>>>(a.src, a.src_stride, a.dst, a.dst_stride, a.n_keep,
+                                      a.scale);
+  return cudaGetLastError();
+}
+
+}  // namespace fdd

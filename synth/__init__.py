@@ -19,7 +19,9 @@ shapes follow the paper's parameter space.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -137,30 +139,45 @@ def _noise_block(rng: np.random.Generator, w: Workload, rows: int) -> np.ndarray
     return z
 
 
-def filterbank(w: Workload, seed: int, beam: int = 0, block_rows: int = 1 << 16):
+def filterbank(w: Workload, seed: int, beam: int = 0, rows: int | None = None,
+               block_rows: int = 1 << 14, threads: int | None = None):
     """One beam's [n_t, n_chan] time-major filterbank and its pulses.
 
-    Noise is drawn block by block (bounded host memory) from PCG64 seeded by
-    (seed, beam); u8 workloads are rounded and clipped to 0..255 after the
-    pulses are added.
+    Pulses come from PCG64 seeded by (seed, beam); the noise of row block b
+    (block_rows rows) from PCG64 seeded by (seed, beam, b), so blocks are
+    drawn in parallel threads and ``rows`` < n_t returns exactly the leading
+    rows of the full array.  u8 workloads are rounded and clipped to 0..255
+    after the pulses are added.
     """
-    rng = np.random.default_rng([seed, beam])
-    pulses = draw_pulses(w, rng)
-    out = np.empty((w.n_t, w.n_chan), dtype=np.uint8 if w.dtype == "u8" else np.float32)
+    pulses = draw_pulses(w, np.random.default_rng([seed, beam]))
+    n_rows = w.n_t if rows is None else min(int(rows), w.n_t)
+    out = np.empty((n_rows, w.n_chan), dtype=np.uint8 if w.dtype == "u8" else np.float32)
     sweeps = [(p, sky_delay_samples(w, p.dm)) for p in pulses]
-    for r0 in range(0, w.n_t, block_rows):
-        r1 = min(w.n_t, r0 + block_rows)
-        blk = _noise_block(rng, w, r1 - r0)
+
+    def fill(b: int) -> None:
+        r0 = b * block_rows
+        r1 = min(n_rows, r0 + block_rows)
+        blk = _noise_block(np.random.default_rng([seed, beam, b]), w, r1 - r0)
         for p, off in sweeps:
-            for c in range(w.n_chan):
-                s = p.t0 + int(off[c])
-                a, b = max(s, r0), min(s + p.width, r1)
-                if a < b:
-                    blk[a - r0: b - r0, c] += np.float32(p.amp)
+            start = p.t0 + off
+            for c in np.nonzero((start < r1) & (start + p.width > r0))[0]:
+                a, e = max(int(start[c]), r0), min(int(start[c]) + p.width, r1)
+                blk[a - r0: e - r0, c] += np.float32(p.amp)
         if w.dtype == "u8":
-            out[r0:r1] = np.clip(np.rint(blk), 0, 255).astype(np.uint8)
+            np.rint(blk, out=blk)
+            np.clip(blk, 0, 255, out=blk)
+            out[r0:r1] = blk.astype(np.uint8)
         else:
             out[r0:r1] = blk
+
+    n_blocks = (n_rows + block_rows - 1) // block_rows
+    workers = threads or min(16, os.cpu_count() or 1)
+    if workers > 1 and n_blocks > 1:
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(fill, range(n_blocks)))
+    else:
+        for b in range(n_blocks):
+            fill(b)
     return out, pulses
 
 

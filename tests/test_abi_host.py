@@ -1,0 +1,138 @@
+"""The C ABI on the CPU: the library loads, exports what include/fdd.h
+declares, and its host-only plan geometry agrees with the oracle's reading of
+the chunking (no GPU needed; no compute calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2110_03482_gb300 as fdd
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    fdd.build()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "fdd.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\**\s+\**(fdd_[a-z_0-9]+)\s*\(",
+                                 src, flags=re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == sorted(fdd.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(fdd.library_path())
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert fdd.fdd_abi_version() == 1
+
+
+def test_status_strings():
+    assert fdd.fdd_status_string(0) == "FDD_OK"
+    assert fdd.fdd_status_string(6) == "FDD_ERR_TIMEOUT"
+    assert fdd.fdd_status_string(99) == "FDD_ERR_UNKNOWN"
+
+
+def _params(w: synth.Workload, **kw):
+    d = dict(n_chan=w.n_chan, nu_lo_mhz=w.nu_lo_mhz, dnu_mhz=w.dnu_mhz, t_samp_s=w.t_samp_s,
+             n_t=w.n_t, dm_list=w.dms(), chunk_len=w.chunk_len, n_beams=w.n_beams,
+             in_dtype=fdd.FDD_IN_U8 if w.dtype == "u8" else fdd.FDD_IN_F32,
+             output={"time": 0, "spectra": 1, "power": 2}[w.output])
+    d.update(kw)
+    return fdd.Params(**d)
+
+
+@pytest.mark.parametrize("name", list(synth.WORKLOADS))
+def test_geometry_matches_oracle(name):
+    w = synth.WORKLOADS[name]
+    g = fdd.fdd_plan_geometry(_params(w))
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    og = oracle.geometry(w.n_t, w.chunk_len, d)
+    assert g["fft_len"] == og.L
+    assert g["n_bins"] == og.K
+    assert g["d_max"] == og.d_max
+    assert g["n_chunks"] == og.n_chunks
+    assert g["out_len"] == og.n_out
+    if w.chunk_len:
+        assert g["hop"] == og.hop
+    assert g["dm_uniform"] == 1
+    assert g["bin_pitch"] >= g["n_bins"] and g["bin_pitch"] % 64 == 0
+    assert g["in_elems"] == w.n_beams * w.n_t * w.n_chan
+
+
+def test_geometry_survey_values():
+    """Survey-shaped workload: 1024 channels over 1210-1520 MHz at 64 us, trials
+    0..1023.5: the sweep is ~16.2 samples per unit DM (16585 samples at the top
+    trial), so 2^18-sample chunks keep 245559 samples each and 5 chunks cover
+    the 2^20-sample series."""
+    w = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
+    g = fdd.fdd_plan_geometry(_params(w))
+    assert g["fft_len"] == 1 << 18 and g["n_bins"] == (1 << 17) + 1
+    assert 16580 <= g["d_max"] <= 16590
+    assert g["hop"] == (1 << 18) - g["d_max"]
+    assert g["n_chunks"] == 5
+    assert g["out_len"] == (1 << 20) - g["d_max"]
+    assert g["dm_batch"] == 2048
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n_chan=0), fdd.FDD_ERR_INVALID_ARG),
+    (dict(t_samp_s=0.0), fdd.FDD_ERR_INVALID_ARG),
+    (dict(n_t=1), fdd.FDD_ERR_INVALID_ARG),
+    (dict(dnu_mhz=0.0), fdd.FDD_ERR_INVALID_ARG),
+    (dict(chunk_len=101), fdd.FDD_ERR_INVALID_ARG),
+    (dict(chunk_len=64), fdd.FDD_ERR_INVALID_ARG),        # shorter than the delay
+    (dict(nu_ref_mhz=1000.0), fdd.FDD_ERR_INVALID_ARG),   # below the top channel
+    (dict(in_dtype=7), fdd.FDD_ERR_INVALID_ARG),
+    (dict(output=9), fdd.FDD_ERR_INVALID_ARG),
+    (dict(precision=fdd.FDD_PREC_BF16_HILO), fdd.FDD_ERR_UNSUPPORTED),
+    (dict(dm_list=np.array([0.0, 1.0, 3.0])), fdd.FDD_ERR_UNSUPPORTED),
+    (dict(dm_list=np.array([-1.0, 0.0])), fdd.FDD_ERR_INVALID_ARG),
+    (dict(dm_list=np.array([0.0, np.nan])), fdd.FDD_ERR_INVALID_ARG),
+    (dict(reserved0=1), fdd.FDD_ERR_INVALID_ARG),
+    (dict(workspace_limit=1024), fdd.FDD_ERR_INVALID_ARG),
+])
+def test_invalid_parameters(kw, status):
+    w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    with pytest.raises(fdd.FddError) as e:
+        fdd.fdd_plan_geometry(_params(w, **kw))
+    assert e.value.status == status
+    assert fdd.fdd_last_error()
+
+
+def test_geometry_edge_cases():
+    w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    # single trial, single channel, n_t not a power of two
+    g = fdd.fdd_plan_geometry(_params(w, n_chan=1, dm_list=np.array([5.0]), n_t=1000))
+    assert g["fft_len"] == 1024 and g["d_max"] == 0 and g["out_len"] == 1000
+    assert g["dm_uniform"] == 1 and g["ddm"] == 0.0
+    # descending band: channel 0 is the highest, still no negative delays
+    g = fdd.fdd_plan_geometry(_params(w, nu_lo_mhz=1550.0 - 4.6875 / 2, dnu_mhz=-4.6875))
+    g2 = fdd.fdd_plan_geometry(_params(w))
+    assert g["d_max"] == g2["d_max"]
+    # a workspace limit forces DM batches of whole kernel blocks
+    w2 = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
+    g = fdd.fdd_plan_geometry(_params(w2, workspace_limit=4 << 30))
+    assert 0 < g["dm_batch"] < 2048 and g["workspace_bytes"] <= 4 << 30
+
+
+def test_plan_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    with pytest.raises(fdd.FddError) as e:
+        fdd.fdd_plan(_params(w))
+    assert e.value.status in (fdd.FDD_ERR_CUDA, fdd.FDD_ERR_UNSUPPORTED)
