@@ -59,7 +59,29 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU-baseline sample")
+    ap.add_argument("--n-t", type=int, default=0,
+                    help="override samples per beam (smaller cases for profiler captures)")
+    ap.add_argument("--chunk-len", type=int, default=-1,
+                    help="override the overlap-save chunk length")
+    ap.add_argument("--mac-variant", type=int, default=0,
+                    help="0 = automatic, else 1 + FDD_MAC_* kernel variant")
+    ap.add_argument("--mac-sweep", default="",
+                    help="comma-separated FDD_MAC_* variants (or 'all'): time the "
+                         "phase-rotate-and-sum kernel alone for each on one chunk of the "
+                         "workload and print one JSON line per variant")
     return ap.parse_args()
+
+
+def workload_from_args(args) -> synth.Workload:
+    w = synth.WORKLOADS[args.workload]
+    kw = {}
+    if args.n_t:
+        kw["n_t"] = args.n_t
+    if args.chunk_len >= 0:
+        kw["chunk_len"] = args.chunk_len
+    if kw:
+        w = w.scaled(name=w.name + "_scaled", **kw)
+    return w
 
 
 # ------------------------------------------------------------------ helpers
@@ -203,7 +225,7 @@ def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
     import oracle
-    w = synth.WORKLOADS[args.workload]
+    w = workload_from_args(args)
     d, geo, X = oracle_sample_setup(w, args.seed)
     rng = np.random.default_rng(args.seed)
     nb = 64
@@ -239,7 +261,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     fdd.build()
-    w = synth.WORKLOADS[args.workload]
+    w = workload_from_args(args)
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
     gpu_id = str(getattr(props, "uuid", "")) or str(local)
@@ -247,7 +269,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
         gpu_id = "GPU-" + gpu_id
 
     fb, _ = synth.filterbank(w, seed=args.seed, beam=rank)
-    plan = fdd.Plan(**plan_params(w, fdd))
+    plan = fdd.Plan(**plan_params(w, fdd), mac_variant=args.mac_variant)
     info = plan.info
     stream = torch.cuda.current_stream()
     d_in = torch.from_numpy(fb.reshape(-1)).cuda()
@@ -300,7 +322,8 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
     traffic = read_traffic_summary()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "mac_fp32_kernel (phase-rotate-and-sum, Eqs. 4 and 7)",
+                "kernel": "phase-rotate-and-sum (Eqs. 4 and 7), variant "
+                          + fdd.MAC_VARIANT_NAMES[info["mac_variant"]],
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x "
                                f"{max_mhz:.0f} MHz max SM clock (FP32 FFMA; "
                                "MEASURED_PEAKS.json has no FP32 figure)",
@@ -357,8 +380,54 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
         print(json.dumps(line), flush=True)
 
 
+def run_mac_sweep(args) -> None:
+    """Kernel-only timing of phase-rotate-and-sum variants on one chunk's spectra."""
+    import torch
+
+    import paper_2110_03482_gb300 as fdd
+
+    fdd.build()
+    w = workload_from_args(args)
+    vs = range(fdd.FDD_MAC_VARIANTS) if args.mac_sweep == "all" else \
+        [int(v) for v in args.mac_sweep.split(",")]
+    props = torch.cuda.get_device_properties(0)
+    peaks = load_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    g = None
+    X = Y = None
+    for v in vs:
+        with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA),
+                      mac_variant=v + 1) as plan:
+            g = plan.info
+            if X is None:
+                gen = torch.Generator(device="cuda").manual_seed(args.seed)
+                X = torch.randn((w.n_chan, g["bin_pitch"], 2), device="cuda", generator=gen)
+                Y = torch.empty((w.n_dm, g["n_bins"], 2), device="cuda")
+            for _ in range(max(args.warmup, 1)):
+                plan.dedisperse_spectra(X, g["bin_pitch"], 1, 0, w.n_dm, Y, g["n_bins"])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                plan.dedisperse_spectra(X, g["bin_pitch"], 1, 0, w.n_dm, Y, g["n_bins"])
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+        flops = FLOPS_PER_MAC * w.n_dm * w.n_chan * g["n_bins"]
+        tf = flops / (ms / 1e3) / 1e12
+        print(json.dumps({"sweep": fdd.MAC_VARIANT_NAMES[v], "variant": v, "ms_per_launch": ms,
+                          "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,
+                          "n_bins": g["n_bins"], "n_dm": w.n_dm, "n_chan": w.n_chan}),
+              flush=True)
+
+
 def main():
     args = parse_args()
+    if args.mac_sweep:
+        run_mac_sweep(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -69,6 +69,21 @@ typedef enum fdd_status {
 #define FDD_OUT_POWER 2   /* float  [beam][chunk][n_dm][n_bins]: |Y|^2 for
                              periodicity searches (Sect. 5)                     */
 
+/* Kernel variants of the FP32 phase-rotate-and-sum (fdd_params.mac_variant - 1,
+ * fdd_info.mac_variant): F1 issues single FFMAs, F2 and F3 paired f32x2 FMAs
+ * (inline PTX and compiler builtin); AxB is the per-lane register tile (A*B
+ * trials per lane; a warp covers 2048, 1024 or 4 x 128 trials). */
+#define FDD_MAC_F1_8X8 0
+#define FDD_MAC_F1_4X8 1
+#define FDD_MAC_F1_4X4 2
+#define FDD_MAC_F2_8X8 3
+#define FDD_MAC_F2_4X8 4
+#define FDD_MAC_F2_4X4 5
+#define FDD_MAC_F3_8X8 6
+#define FDD_MAC_F3_4X8 7
+#define FDD_MAC_F3_4X4 8
+#define FDD_MAC_VARIANTS 9
+
 /* fdd_params.precision */
 #define FDD_PREC_FP32 0      /* FP32 phasors and accumulation (CUDA cores)       */
 #define FDD_PREC_BF16_HILO 1 /* tensor cores, BF16 hi+lo phasors (Sect. 5 future
@@ -93,7 +108,8 @@ typedef struct fdd_params {
   int32_t in_layout;      /* FDD_LAYOUT_*                                            */
   int32_t output;         /* FDD_OUT_*                                               */
   int32_t precision;      /* FDD_PREC_*                                              */
-  int32_t reserved0;      /* must be 0                                               */
+  int32_t mac_variant;    /* phase-rotate-and-sum kernel: 0 chooses automatically;
+                             1 + FDD_MAC_* forces that variant                      */
   size_t workspace_limit; /* device bytes the plan may hold; 0 = library default    */
 } fdd_params;
 

@@ -39,6 +39,18 @@ FDD_OUT_SPECTRA = 1
 FDD_OUT_POWER = 2
 FDD_PREC_FP32 = 0
 FDD_PREC_BF16_HILO = 1
+FDD_MAC_F1_8X8 = 0
+FDD_MAC_F1_4X8 = 1
+FDD_MAC_F1_4X4 = 2
+FDD_MAC_F2_8X8 = 3
+FDD_MAC_F2_4X8 = 4
+FDD_MAC_F2_4X4 = 5
+FDD_MAC_F3_8X8 = 6
+FDD_MAC_F3_4X8 = 7
+FDD_MAC_F3_4X4 = 8
+FDD_MAC_VARIANTS = 9
+MAC_VARIANT_NAMES = ["F1_8x8", "F1_4x8", "F1_4x4", "F2_8x8", "F2_4x8", "F2_4x4",
+                     "F3_8x8", "F3_4x8", "F3_4x4"]
 
 # Every symbol include/fdd.h declares.
 EXPORTS = [
@@ -74,7 +86,7 @@ class fdd_params(ctypes.Structure):
         ("in_layout", ctypes.c_int32),
         ("output", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("mac_variant", ctypes.c_int32),
         ("workspace_limit", ctypes.c_size_t),
     ]
 

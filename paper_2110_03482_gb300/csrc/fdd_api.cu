@@ -157,7 +157,9 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
     return fail(FDD_ERR_UNSUPPORTED, "precision FDD_PREC_BF16_HILO is not available in this build");
   if (p->precision != FDD_PREC_FP32)
     return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
-  if (p->reserved0 != 0) return fail(FDD_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
+    return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
+                FDD_MAC_VARIANTS);
   if (p->chunk_len < 0 || (p->chunk_len % 2) != 0)
     return fail(FDD_ERR_INVALID_ARG, "chunk_len must be 0 or a positive even length");
   if (!(p->dnu_mhz != 0.0) || !std::isfinite(p->dnu_mhz))
@@ -257,7 +259,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   g->dm0 = dm0;
   g->ddm = ddm;
   g->dm_uniform = uniform;
-  g->mac_variant = fdd::mac_variant_for(p->n_dm);
+  g->mac_variant = p->mac_variant ? p->mac_variant - 1 : fdd::mac_variant_for(p->n_dm);
   if (fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
     return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fdd.h"
+
 namespace fdd {
 
 // Per-channel 64-bit fixed-point phase constants (fractions of a cycle):
@@ -35,8 +37,21 @@ struct MacArgs {
   int* status;              // device status word (may be NULL)
 };
 
-// Kernel tile variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu).
-enum MacVariant { MAC_V8x8 = 0, MAC_V4x8 = 1, MAC_V4x4 = 2, MAC_NUM_VARIANTS = 3 };
+// Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu): F1 issues
+// single FFMAs, F2 / F3 paired f32x2 FMAs (inline PTX / compiler builtin);
+// AxB is the per-lane register tile.
+enum MacVariant {
+  MAC_F1_8x8 = FDD_MAC_F1_8X8,
+  MAC_F1_4x8 = FDD_MAC_F1_4X8,
+  MAC_F1_4x4 = FDD_MAC_F1_4X4,
+  MAC_F2_8x8 = FDD_MAC_F2_8X8,
+  MAC_F2_4x8 = FDD_MAC_F2_4X8,
+  MAC_F2_4x4 = FDD_MAC_F2_4X4,
+  MAC_F3_8x8 = FDD_MAC_F3_8X8,
+  MAC_F3_4x8 = FDD_MAC_F3_4X8,
+  MAC_F3_4x4 = FDD_MAC_F3_4X4,
+  MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
+};
 int mac_variant_for(int n_dm);
 int mac_variant_trials_per_block(int variant);
 cudaError_t mac_prepare(int variant, int n_chan);  // kernel attributes (host, once)

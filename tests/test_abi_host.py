@@ -101,7 +101,8 @@ def test_geometry_survey_values():
     (dict(dm_list=np.array([0.0, 1.0, 3.0])), fdd.FDD_ERR_UNSUPPORTED),
     (dict(dm_list=np.array([-1.0, 0.0])), fdd.FDD_ERR_INVALID_ARG),
     (dict(dm_list=np.array([0.0, np.nan])), fdd.FDD_ERR_INVALID_ARG),
-    (dict(reserved0=1), fdd.FDD_ERR_INVALID_ARG),
+    (dict(mac_variant=-1), fdd.FDD_ERR_INVALID_ARG),
+    (dict(mac_variant=fdd.FDD_MAC_VARIANTS + 1), fdd.FDD_ERR_INVALID_ARG),
     (dict(workspace_limit=1024), fdd.FDD_ERR_INVALID_ARG),
 ])
 def test_invalid_parameters(kw, status):
@@ -110,6 +111,15 @@ def test_invalid_parameters(kw, status):
         fdd.fdd_plan_geometry(_params(w, **kw))
     assert e.value.status == status
     assert fdd.fdd_last_error()
+
+
+def test_variant_choice():
+    w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    assert fdd.fdd_plan_geometry(_params(w))["mac_variant"] == fdd.FDD_MAC_F1_4X4
+    for v in range(fdd.FDD_MAC_VARIANTS):
+        assert fdd.fdd_plan_geometry(_params(w, mac_variant=v + 1))["mac_variant"] == v
+    w2 = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
+    assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_F1_8X8
 
 
 def test_geometry_edge_cases():
