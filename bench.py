@@ -166,6 +166,14 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def gpu_uuid(props, index: int) -> str:
+    """nvidia-smi --id for a torch device (its UUID when torch exposes one)."""
+    u = str(getattr(props, "uuid", "") or "")
+    if not u:
+        return str(index)
+    return u if u.startswith("GPU-") else "GPU-" + u
+
+
 def read_traffic_summary() -> float | None:
     """Per-launch DRAM bytes of the MAC kernel from the committed ncu summary,
     only if that summary was taken on the current kernel source."""
@@ -264,9 +272,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
     w = workload_from_args(args)
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
-    gpu_id = str(getattr(props, "uuid", "")) or str(local)
-    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
-        gpu_id = "GPU-" + gpu_id
+    gpu_id = gpu_uuid(props, local)
 
     fb, _ = synth.filterbank(w, seed=args.seed, beam=rank)
     plan = fdd.Plan(**plan_params(w, fdd), mac_variant=args.mac_variant)
@@ -407,6 +413,7 @@ def run_mac_sweep(args) -> None:
             for _ in range(max(args.warmup, 1)):
                 plan.dedisperse_spectra(X, g["bin_pitch"], 1, 0, w.n_dm, Y, g["n_bins"])
             torch.cuda.synchronize()
+            clocks = Clocks(gpu_uuid(props, 0))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -414,11 +421,13 @@ def run_mac_sweep(args) -> None:
                 plan.dedisperse_spectra(X, g["bin_pitch"], 1, 0, w.n_dm, Y, g["n_bins"])
             e1.record()
             torch.cuda.synchronize()
+            clk = clocks.stop()
             ms = e0.elapsed_time(e1) / args.steps
         flops = FLOPS_PER_MAC * w.n_dm * w.n_chan * g["n_bins"]
         tf = flops / (ms / 1e3) / 1e12
         print(json.dumps({"sweep": fdd.MAC_VARIANT_NAMES[v], "variant": v, "ms_per_launch": ms,
                           "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,
+                          "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
                           "n_bins": g["n_bins"], "n_dm": w.n_dm, "n_chan": w.n_chan}),
               flush=True)
 

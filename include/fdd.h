@@ -70,19 +70,25 @@ typedef enum fdd_status {
                              periodicity searches (Sect. 5)                     */
 
 /* Kernel variants of the FP32 phase-rotate-and-sum (fdd_params.mac_variant - 1,
- * fdd_info.mac_variant): F1 issues single FFMAs, F2 and F3 paired f32x2 FMAs
- * (inline PTX and compiler builtin); AxB is the per-lane register tile (A*B
- * trials per lane; a warp covers 2048, 1024 or 4 x 128 trials). */
-#define FDD_MAC_F1_8X8 0
-#define FDD_MAC_F1_4X8 1
-#define FDD_MAC_F1_4X4 2
-#define FDD_MAC_F2_8X8 3
-#define FDD_MAC_F2_4X8 4
-#define FDD_MAC_F2_4X4 5
-#define FDD_MAC_F3_8X8 6
-#define FDD_MAC_F3_4X8 7
-#define FDD_MAC_F3_4X4 8
-#define FDD_MAC_VARIANTS 9
+ * fdd_info.mac_variant).  S issues single FFMAs; Q and P issue paired f32x2
+ * FMAs (Q swaps compact (re, im) pairs between lanes, P pre-broadcast quads);
+ * SP and QP overlap the phasor evaluation of the next channel with the
+ * multiply-accumulates of the current one; AxB is the per-lane register tile
+ * (a warp covers 2048, 1024 or 4 x 128 trials). */
+#define FDD_MAC_S_8X8 0
+#define FDD_MAC_S_4X8 1
+#define FDD_MAC_S_4X4 2
+#define FDD_MAC_Q_8X8 3
+#define FDD_MAC_Q_4X8 4
+#define FDD_MAC_Q_4X4 5
+#define FDD_MAC_P_8X8 6
+#define FDD_MAC_SP_8X8 7
+#define FDD_MAC_QP_8X8 8
+#define FDD_MAC_Q2_8X8 9  /* Q with the MAC in two passes over the tile           */
+#define FDD_MAC_R_8X8 10  /* reference: the first scalar kernel                   */
+#define FDD_MAC_Q12_8X8 11 /* Q with 12-warp blocks (fewer registers, more warps)  */
+#define FDD_MAC_S12_8X8 12 /* S with 12-warp blocks                                */
+#define FDD_MAC_VARIANTS 13
 
 /* fdd_params.precision */
 #define FDD_PREC_FP32 0      /* FP32 phasors and accumulation (CUDA cores)       */

@@ -39,18 +39,12 @@ FDD_OUT_SPECTRA = 1
 FDD_OUT_POWER = 2
 FDD_PREC_FP32 = 0
 FDD_PREC_BF16_HILO = 1
-FDD_MAC_F1_8X8 = 0
-FDD_MAC_F1_4X8 = 1
-FDD_MAC_F1_4X4 = 2
-FDD_MAC_F2_8X8 = 3
-FDD_MAC_F2_4X8 = 4
-FDD_MAC_F2_4X4 = 5
-FDD_MAC_F3_8X8 = 6
-FDD_MAC_F3_4X8 = 7
-FDD_MAC_F3_4X4 = 8
-FDD_MAC_VARIANTS = 9
-MAC_VARIANT_NAMES = ["F1_8x8", "F1_4x8", "F1_4x4", "F2_8x8", "F2_4x8", "F2_4x4",
-                     "F3_8x8", "F3_4x8", "F3_4x4"]
+MAC_VARIANT_NAMES = ["S_8x8", "S_4x8", "S_4x4", "Q_8x8", "Q_4x8", "Q_4x4", "P_8x8",
+                     "SP_8x8", "QP_8x8", "Q2_8x8", "R_8x8", "Q12_8x8",
+                     "S12_8x8"]
+for _i, _n in enumerate(MAC_VARIANT_NAMES):
+    globals()["FDD_MAC_" + _n.upper()] = _i
+FDD_MAC_VARIANTS = len(MAC_VARIANT_NAMES)
 
 # Every symbol include/fdd.h declares.
 EXPORTS = [

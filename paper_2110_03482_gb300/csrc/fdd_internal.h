@@ -37,19 +37,22 @@ struct MacArgs {
   int* status;              // device status word (may be NULL)
 };
 
-// Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu): F1 issues
-// single FFMAs, F2 / F3 paired f32x2 FMAs (inline PTX / compiler builtin);
-// AxB is the per-lane register tile.
+// Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu and the
+// FDD_MAC_* list in fdd.h).
 enum MacVariant {
-  MAC_F1_8x8 = FDD_MAC_F1_8X8,
-  MAC_F1_4x8 = FDD_MAC_F1_4X8,
-  MAC_F1_4x4 = FDD_MAC_F1_4X4,
-  MAC_F2_8x8 = FDD_MAC_F2_8X8,
-  MAC_F2_4x8 = FDD_MAC_F2_4X8,
-  MAC_F2_4x4 = FDD_MAC_F2_4X4,
-  MAC_F3_8x8 = FDD_MAC_F3_8X8,
-  MAC_F3_4x8 = FDD_MAC_F3_4X8,
-  MAC_F3_4x4 = FDD_MAC_F3_4X4,
+  MAC_S_8x8 = FDD_MAC_S_8X8,
+  MAC_S_4x8 = FDD_MAC_S_4X8,
+  MAC_S_4x4 = FDD_MAC_S_4X4,
+  MAC_Q_8x8 = FDD_MAC_Q_8X8,
+  MAC_Q_4x8 = FDD_MAC_Q_4X8,
+  MAC_Q_4x4 = FDD_MAC_Q_4X4,
+  MAC_P_8x8 = FDD_MAC_P_8X8,
+  MAC_SP_8x8 = FDD_MAC_SP_8X8,
+  MAC_QP_8x8 = FDD_MAC_QP_8X8,
+  MAC_Q2_8x8 = FDD_MAC_Q2_8X8,
+  MAC_R_8x8 = FDD_MAC_R_8X8,
+  MAC_Q12_8x8 = FDD_MAC_Q12_8X8,
+  MAC_S12_8x8 = FDD_MAC_S12_8X8,
   MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
 };
 int mac_variant_for(int n_dm);

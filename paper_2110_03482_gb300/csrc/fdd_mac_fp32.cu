@@ -18,10 +18,31 @@
 // Hence for each bin, Y[aT + b] = sum_nu (X Q_a) P_b is a complex
 // (A x N_nu)(N_nu x T) matrix product whose operands are generated on the
 // fly.  A warp owns one bin (or a few bins) and a block of A*T trials.  For
-// every channel, each lane evaluates a few Q_a, P_b directly from the exact
-// phase (MUFU sin/cos, no recurrence), the warp swaps them through shared
-// memory, and each lane accumulates an AT x BT register tile with four FFMA
-// per complex multiply-accumulate, the FP32-pipe minimum for 8 flops.
+// every channel, each lane evaluates a few Z_a = X Q_a and P_b directly from
+// the exact phase (MUFU sin/cos, no recurrence), the warp swaps them through
+// shared memory, and each lane accumulates an AT x BT register tile with four
+// FP32 FMAs per complex multiply-accumulate, the FP32-pipe minimum for 8
+// flops.
+//
+// Three arithmetic forms share this structure:
+//  * scalar: single FFMAs; Z and P are swapped as (re, im) pairs;
+//  * packed: Blackwell's paired FMA (__ffma2_rn, two FMAs per issued
+//    instruction at the single-FMA pipe rate), pairs running along b:
+//      re[a][b:b+2] += (zr, zr)(pr_b, pr_b+1) + (zi, zi)(-pi_b, -pi_b+1)
+//      im[a][b:b+2] += (zr, zr)(pi_b, pi_b+1) + (zi, zi)(pr_b, pr_b+1)
+//    with Z swapped as (zr, zr, zi, zi) quads and P as planes pr, pi, -pi;
+//  * packed-compact: the same MAC with Z swapped as (zr, zi) pairs and P as
+//    planes pr, pi, the broadcast pairs being formed in registers.
+// and two schedules:
+//  * plain:     per channel c: generate(c) -> sync -> load(c) -> MAC(c);
+//  * pipelined: per channel c: load(c) -> generate(c+1) -> MAC(c) -> sync,
+//    so the sin/cos and shared-memory latencies of the generation overlap
+//    the independent FMAs of the previous channel.  Two swap stages suffice:
+//    generate(c+1) writes the stage last read by load(c-1), which every lane
+//    finished before the sync that closed channel c-1.
+// Lanes are numbered lane = ga * GB + gb, so each quarter warp reads a single
+// Z row (a broadcast) and GB distinct P rows; the P rows are padded so that
+// those reads fall in distinct shared-memory banks.
 #include "fdd_internal.h"
 
 namespace fdd {
@@ -29,10 +50,450 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kPrefetch = 4;  // channels of X kept in flight per lane
+constexpr int kUnroll = 4;  // channels per unrolled group (X loads run one group ahead)
+constexpr int kPrefetch = kUnroll;
 
 template <int AT_, int BT_, int GA_, int GB_>
-struct Tile {
+struct Geom {
+  static constexpr int AT = AT_;        // Z_a values per lane
+  static constexpr int BT = BT_;        // P_b values per lane
+  static constexpr int GA = GA_;        // lanes along a in a bin group
+  static constexpr int GB = GB_;        // lanes along b in a bin group
+  static constexpr int G = GA * GB;     // lanes per bin group
+  static constexpr int NG = 32 / G;     // bin groups per warp
+  static constexpr int AW = GA * AT;    // A: super-steps of the trial block
+  static constexpr int TW = GB * BT;    // T: sub-steps of the trial block
+  static constexpr int DMS = AW * TW;   // trials per block
+  static constexpr int ZGEN = (AW + G - 1) / G;  // Z_a evaluated per lane
+  static constexpr int PGEN = (TW + G - 1) / G;  // P_b evaluated per lane
+  static_assert(32 % G == 0, "bin group must divide a warp");
+};
+
+using G8x8 = Geom<8, 8, 4, 8>;  // 32 x 64 = 2048 trials per bin and warp
+using G4x8 = Geom<4, 8, 4, 8>;  // 16 x 64 = 1024
+using G4x4 = Geom<4, 4, 2, 4>;  //  8 x 16 =  128, four bins per warp
+
+// ----------------------------------------------------------------- scalar form
+template <class Gm>
+struct Scalar {
+  static constexpr int AT = Gm::AT, BT = Gm::BT;
+  static constexpr int ZROW = 2 * AT + 4;  // a-rows and b-rows padded by 16 bytes, so the
+  static constexpr int PROW = 2 * BT + 4;  // rows read by one load start in distinct banks
+  static constexpr int ZFL = Gm::GA * ZROW;
+  static constexpr int GFL = ZFL + Gm::GB * PROW;  // floats per group per stage
+  static_assert(AT % 2 == 0 && BT % 2 == 0, "rows are read as float4");
+
+  struct Ops {
+    float zr[AT], zi[AT], pr[BT], pi[BT];
+  };
+  struct Acc {
+    float re[AT][BT], im[AT][BT];
+  };
+  static __device__ __forceinline__ void zero(Acc& c) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i)
+#pragma unroll
+      for (int j = 0; j < BT; ++j) c.re[i][j] = c.im[i][j] = 0.f;
+  }
+  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 2 * (a % AT); }
+  static __device__ __forceinline__ int p_off(int b) {
+    return ZFL + (b / BT) * PROW + 2 * (b % BT);
+  }
+  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
+    *reinterpret_cast<float2*>(grp + off) = make_float2(zr, zi);
+  }
+  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
+    *reinterpret_cast<float2*>(grp + off) = make_float2(pr, pi);
+  }
+  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
+    const float4* z = reinterpret_cast<const float4*>(grp + ga * ZROW);
+    const float4* p = reinterpret_cast<const float4*>(grp + ZFL + gb * PROW);
+#pragma unroll
+    for (int h = 0; h < AT / 2; ++h) {
+      const float4 v = z[h];
+      o.zr[2 * h] = v.x;
+      o.zi[2 * h] = v.y;
+      o.zr[2 * h + 1] = v.z;
+      o.zi[2 * h + 1] = v.w;
+    }
+#pragma unroll
+    for (int h = 0; h < BT / 2; ++h) {
+      const float4 v = p[h];
+      o.pr[2 * h] = v.x;
+      o.pi[2 * h] = v.y;
+      o.pr[2 * h + 1] = v.z;
+      o.pi[2 * h + 1] = v.w;
+    }
+  }
+  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i)
+#pragma unroll
+      for (int j = 0; j < BT; ++j) {
+        c.re[i][j] = fmaf(o.zr[i], o.pr[j], c.re[i][j]);
+        c.re[i][j] = fmaf(-o.zi[i], o.pi[j], c.re[i][j]);
+        c.im[i][j] = fmaf(o.zr[i], o.pi[j], c.im[i][j]);
+        c.im[i][j] = fmaf(o.zi[i], o.pr[j], c.im[i][j]);
+      }
+  }
+  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
+    return make_float2(c.re[i][j], c.im[i][j]);
+  }
+};
+
+// ----------------------------------------------------------------- packed form
+template <class Gm>
+struct Packed {
+  static constexpr int AT = Gm::AT, BT = Gm::BT;
+  static constexpr int ZROW = 4 * (AT + 1);  // floats per a-row: AT quads + one of padding
+  static constexpr int PSTR = BT + 4;        // floats per b-row of a plane
+  static constexpr int ZFL = Gm::GA * ZROW;
+  static constexpr int PFL = Gm::GB * PSTR;  // floats per plane
+  static constexpr int GFL = ZFL + 3 * PFL;
+  static_assert(BT % 4 == 0, "plane rows are read as float4");
+
+  struct Ops {
+    float2 pr[BT / 2], pi[BT / 2], pn[BT / 2];
+    const float4* zq;  // the lane's Z quads, read inside the MAC
+  };
+  struct Acc {
+    float2 re[AT][BT / 2], im[AT][BT / 2];
+  };
+  static __device__ __forceinline__ void zero(Acc& c) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i)
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) c.re[i][j] = c.im[i][j] = make_float2(0.f, 0.f);
+  }
+  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 4 * (a % AT); }
+  static __device__ __forceinline__ int p_off(int b) { return ZFL + (b / BT) * PSTR + (b % BT); }
+  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
+    *reinterpret_cast<float4*>(grp + off) = make_float4(zr, zr, zi, zi);
+  }
+  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
+    grp[off] = pr;
+    grp[off + PFL] = pi;
+    grp[off + 2 * PFL] = -pi;
+  }
+  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
+    const float* row = grp + ZFL + gb * PSTR;
+#pragma unroll
+    for (int h = 0; h < BT / 4; ++h) {
+      const float4 r = *reinterpret_cast<const float4*>(row + 4 * h);
+      const float4 i = *reinterpret_cast<const float4*>(row + PFL + 4 * h);
+      const float4 n = *reinterpret_cast<const float4*>(row + 2 * PFL + 4 * h);
+      o.pr[2 * h] = make_float2(r.x, r.y);
+      o.pr[2 * h + 1] = make_float2(r.z, r.w);
+      o.pi[2 * h] = make_float2(i.x, i.y);
+      o.pi[2 * h + 1] = make_float2(i.z, i.w);
+      o.pn[2 * h] = make_float2(n.x, n.y);
+      o.pn[2 * h + 1] = make_float2(n.z, n.w);
+    }
+    o.zq = reinterpret_cast<const float4*>(grp + ga * ZROW);
+  }
+  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i) {
+      const float4 z = o.zq[i];
+      const float2 zr = make_float2(z.x, z.y), zi = make_float2(z.z, z.w);
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
+      }
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zi, o.pn[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
+      }
+    }
+  }
+  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
+    const float2 r = c.re[i][j / 2], m = c.im[i][j / 2];
+    return (j & 1) ? make_float2(r.y, m.y) : make_float2(r.x, m.x);
+  }
+};
+
+// ------------------------------------------------- packed form, compact swap
+// Z swapped as (zr, zi) pairs and P as planes pr, pi (the scalar form's
+// shared-memory volume); the broadcast pairs (zr, zr), (zi, zi), (-zi, -zi)
+// are formed in registers.
+template <class Gm>
+struct PackedCompact {
+  static constexpr int AT = Gm::AT, BT = Gm::BT;
+  static constexpr int ZROW = 2 * AT + 4;   // padded a-rows of (zr, zi) pairs
+  static constexpr int PSTR = BT + 4;       // padded b-rows of a plane
+  static constexpr int ZFL = Gm::GA * ZROW;
+  static constexpr int PFL = Gm::GB * PSTR;
+  static constexpr int GFL = ZFL + 2 * PFL;
+  static_assert(AT % 2 == 0 && BT % 4 == 0, "rows are read as float4");
+
+  struct Ops {
+    float zr[AT], zi[AT];
+    float2 pr[BT / 2], pi[BT / 2];
+  };
+  struct Acc {
+    float2 re[AT][BT / 2], im[AT][BT / 2];
+  };
+  static __device__ __forceinline__ void zero(Acc& c) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i)
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) c.re[i][j] = c.im[i][j] = make_float2(0.f, 0.f);
+  }
+  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 2 * (a % AT); }
+  static __device__ __forceinline__ int p_off(int b) { return ZFL + (b / BT) * PSTR + (b % BT); }
+  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
+    *reinterpret_cast<float2*>(grp + off) = make_float2(zr, zi);
+  }
+  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
+    grp[off] = pr;
+    grp[off + PFL] = pi;
+  }
+  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
+    const float4* z = reinterpret_cast<const float4*>(grp + ga * ZROW);
+#pragma unroll
+    for (int h = 0; h < AT / 2; ++h) {
+      const float4 v = z[h];
+      o.zr[2 * h] = v.x;
+      o.zi[2 * h] = v.y;
+      o.zr[2 * h + 1] = v.z;
+      o.zi[2 * h + 1] = v.w;
+    }
+    const float* row = grp + ZFL + gb * PSTR;
+#pragma unroll
+    for (int h = 0; h < BT / 4; ++h) {
+      const float4 r = *reinterpret_cast<const float4*>(row + 4 * h);
+      const float4 i = *reinterpret_cast<const float4*>(row + PFL + 4 * h);
+      o.pr[2 * h] = make_float2(r.x, r.y);
+      o.pr[2 * h + 1] = make_float2(r.z, r.w);
+      o.pi[2 * h] = make_float2(i.x, i.y);
+      o.pi[2 * h + 1] = make_float2(i.z, i.w);
+    }
+  }
+  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i) {
+      const float2 zr = make_float2(o.zr[i], o.zr[i]);
+      const float2 zi = make_float2(o.zi[i], o.zi[i]);
+      const float2 zn = make_float2(-o.zi[i], -o.zi[i]);
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
+      }
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zn, o.pi[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
+      }
+    }
+  }
+  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
+    const float2 r = c.re[i][j / 2], m = c.im[i][j / 2];
+    return (j & 1) ? make_float2(r.y, m.y) : make_float2(r.x, m.x);
+  }
+};
+
+// Same as PackedCompact with the MAC in two passes over the whole tile (all
+// zr terms, then all zi terms), so the two updates of an accumulator pair are
+// a full pass apart.
+template <class Gm>
+struct PackedCompact2 : PackedCompact<Gm> {
+  typedef PackedCompact<Gm> B;
+  static __device__ __forceinline__ void mac(typename B::Acc& c, const typename B::Ops& o) {
+#pragma unroll
+    for (int i = 0; i < B::AT; ++i) {
+      const float2 zr = make_float2(o.zr[i], o.zr[i]);
+#pragma unroll
+      for (int j = 0; j < B::BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < B::AT; ++i) {
+      const float2 zi = make_float2(o.zi[i], o.zi[i]);
+      const float2 zn = make_float2(-o.zi[i], -o.zi[i]);
+#pragma unroll
+      for (int j = 0; j < B::BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zn, o.pi[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
+      }
+    }
+  }
+};
+
+// Top 32 bits of (m * (hi:lo)) mod 2^64, without the carry of the low word
+// (an error of at most 2^-32 cycle).
+__device__ __forceinline__ uint32_t top32_mul(uint32_t m, uint32_t lo, uint32_t hi) {
+  return __umulhi(m, lo) + m * hi;
+}
+
+// Unit phasor of a phase given in units of 2^-32 cycle.  Read as a signed
+// integer the phase lies in [-1/2, 1/2) cycle, i.e. [-pi, pi) radians, the
+// range in which the hardware sine/cosine are accurate to about 2^-21.
+__device__ __forceinline__ float2 unit_phasor(uint32_t phase) {
+  const float x = __int2float_rn(static_cast<int>(phase)) * 1.46291807926715968e-9f;  // 2pi/2^32
+  float s, c;
+  __sincosf(x, &s, &c);
+  return make_float2(c, s);
+}
+
+// This lane's share of the phasor evaluation for one channel: Z_a = X Q_a for
+// a = lg + q G and P_b for b = lg + q G, written into the group's swap stage.
+template <class Gm, class M>
+struct Generator {
+  uint32_t mz[Gm::ZGEN], mp[Gm::PGEN];
+  int zoff[Gm::ZGEN], poff[Gm::PGEN];
+  bool zon[Gm::ZGEN], pon[Gm::PGEN];
+  uint32_t ku;
+
+  __device__ __forceinline__ void init(uint32_t k, int lg, int j_first) {
+    ku = k;
+#pragma unroll
+    for (int q = 0; q < Gm::ZGEN; ++q) {
+      const int ai = lg + q * Gm::G;
+      zon[q] = ai < Gm::AW;
+      mz[q] = k * static_cast<uint32_t>(j_first + ai * Gm::TW);
+      zoff[q] = M::z_off(ai);
+    }
+#pragma unroll
+    for (int q = 0; q < Gm::PGEN; ++q) {
+      const int bi = lg + q * Gm::G;
+      pon[q] = bi < Gm::TW;
+      mp[q] = k * static_cast<uint32_t>(bi);
+      poff[q] = M::p_off(bi);
+    }
+  }
+  __device__ __forceinline__ void run(const PhaseConst& p, float2 x, float* grp) const {
+    const uint32_t base = top32_mul(ku, p.u_lo, p.u_hi);
+#pragma unroll
+    for (int q = 0; q < Gm::ZGEN; ++q) {
+      if (zon[q]) {
+        const float2 w = unit_phasor(base + top32_mul(mz[q], p.v_lo, p.v_hi));
+        M::put_z(grp, zoff[q], x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Gm::PGEN; ++q) {
+      if (pon[q]) {
+        const float2 w = unit_phasor(top32_mul(mp[q], p.v_lo, p.v_hi));
+        M::put_p(grp, poff[q], w.x, w.y);
+      }
+    }
+  }
+};
+
+template <class Gm, class M, bool kPipe, int W = kWarps>
+__global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
+  float* swap_all = reinterpret_cast<float*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
+
+  for (int i = threadIdx.x; i < a.n_chan; i += W * 32) pcs[i] = a.pc[i];
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / Gm::G;
+  const int lg = lane % Gm::G;
+  const int ga = lg / Gm::GB;
+  const int gb = lg % Gm::GB;
+  const int k = (blockIdx.x * W + warp) * Gm::NG + g;
+  const bool k_ok = k < a.n_bins;
+  const uint32_t ku = k_ok ? static_cast<uint32_t>(k) : 0u;  // idle groups run bin 0, store nothing
+  const int jblk = blockIdx.y * Gm::DMS;
+  const int series = blockIdx.z;
+  const int nc = a.n_chan;
+
+  constexpr int kStage = Gm::NG * M::GFL;  // floats per warp per stage
+  float* grp0 = swap_all + warp * 2 * kStage + g * M::GFL;
+
+  Generator<Gm, M> gen;
+  gen.init(ku, lg, a.j_begin + jblk);
+
+  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + ku;
+  const int64_t xs = a.x_chan_stride;
+  // The generation of channel c uses X[c]; the pipelined schedule runs it one
+  // channel ahead, so a group of kUnroll iterations starting at c0 consumes
+  // X[c0 + off .. c0 + off + kUnroll).
+  constexpr int off = kPipe ? 1 : 0;
+
+  typename M::Acc acc;
+  M::zero(acc);
+
+  if (kPipe) {
+    gen.run(pcs[0], __ldg(xp), grp0);
+    __syncwarp();
+  }
+  float2 xcur[kUnroll];
+#pragma unroll
+  for (int i = 0; i < kUnroll; ++i) {
+    const int c = off + i;
+    xcur[i] = (c < nc) ? __ldg(xp + c * xs) : make_float2(0.f, 0.f);
+  }
+
+  int stage = 0;
+  for (int c0 = 0; c0 < nc; c0 += kUnroll) {
+    float2 xnext[kUnroll];
+#pragma unroll
+    for (int i = 0; i < kUnroll; ++i) {
+      const int c = c0 + kUnroll + off + i;
+      xnext[i] = (c < nc) ? __ldg(xp + c * xs) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < kUnroll; ++i) {
+      const int c = c0 + i;
+      if (c < nc) {
+        float* cur = grp0 + stage * kStage;
+        float* nxt = grp0 + (stage ^ 1) * kStage;
+        typename M::Ops ops;
+        if (kPipe) {
+          M::load(cur, ga, gb, ops);
+          if (c + 1 < nc) gen.run(pcs[c + 1], xcur[i], nxt);
+          M::mac(acc, ops);
+          __syncwarp();
+        } else {
+          gen.run(pcs[c], xcur[i], cur);
+          __syncwarp();
+          M::load(cur, ga, gb, ops);
+          M::mac(acc, ops);
+        }
+        stage ^= 1;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kUnroll; ++i) xcur[i] = xnext[i];
+  }
+
+  if (!k_ok) return;
+  const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
+#pragma unroll
+  for (int ii = 0; ii < Gm::AT; ++ii) {
+#pragma unroll
+    for (int jj = 0; jj < Gm::BT; ++jj) {
+      const int jl = jblk + (ga * Gm::AT + ii) * Gm::TW + gb * Gm::BT + jj;
+      if (jl < a.n_dm) {
+        const float2 v = M::get(acc, ii, jj);
+        const float re = v.x * a.scale;
+        const float im = real_only ? 0.f : v.y * a.scale;
+        const int64_t o = static_cast<int64_t>(series) * a.y_series_stride +
+                          static_cast<int64_t>(jl) * a.y_dm_stride + k;
+        if (a.out_kind == 2)
+          static_cast<float*>(a.Y)[o] = re * re + im * im;
+        else
+          static_cast<float2*>(a.Y)[o] = make_float2(re, im);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- reference
+// The first scalar kernel, kept verbatim as a timing reference: one warp-level
+// swap in float2 units and four consecutive FFMAs per register-tile element.
+template <int AT_, int BT_, int GA_, int GB_>
+struct LegacyTile {
   static constexpr int AT = AT_;            // Q_a values per lane
   static constexpr int BT = BT_;            // P_b values per lane
   static constexpr int GA = GA_;            // lanes along a in a bin group
@@ -54,28 +515,10 @@ struct Tile {
   static_assert(AT % 2 == 0 && BT % 2 == 0, "tiles are read as float4 pairs");
 };
 
-using TileV8x8 = Tile<8, 8, 4, 8>;  // 32 x 64 = 2048 trials per bin and warp
-using TileV4x8 = Tile<4, 8, 4, 8>;  // 16 x 64 = 1024
-using TileV4x4 = Tile<4, 4, 2, 4>;  //  8 x 16 =  128, four bins per warp
-
-// Top 32 bits of (m * (hi:lo)) mod 2^64, without the carry of the low word
-// (an error of at most 2^-32 cycle).
-__device__ __forceinline__ uint32_t top32_mul(uint32_t m, uint32_t lo, uint32_t hi) {
-  return __umulhi(m, lo) + m * hi;
-}
-
-// Unit phasor of a phase given in units of 2^-32 cycle.  Read as a signed
-// integer the phase lies in [-1/2, 1/2) cycle, i.e. [-pi, pi) radians, the
-// range in which the hardware sine/cosine are accurate to about 2^-21.
-__device__ __forceinline__ float2 unit_phasor(uint32_t phase) {
-  const float x = __int2float_rn(static_cast<int>(phase)) * 1.46291807926715968e-9f;  // 2pi/2^32
-  float s, c;
-  __sincosf(x, &s, &c);
-  return make_float2(c, s);
-}
+using LegacyV8x8 = LegacyTile<8, 8, 4, 8>;  // 32 x 64 = 2048 trials per bin and warp
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, 1) mac_fp32_kernel(const MacArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) mac_legacy_kernel(const MacArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
   float2* swap_all = reinterpret_cast<float2*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
@@ -220,275 +663,54 @@ __global__ void __launch_bounds__(kThreads, 1) mac_fp32_kernel(const MacArgs a) 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Packed form.  The same factorised product, with the MAC issued as Blackwell's
-// paired FP32 FMA (fma.rn.f32x2): two FMAs per issued instruction at the
-// FMA-pipe rate of single FFMAs, so the phasor evaluation, the shared-memory
-// swap and the loads issue in the slots the MAC leaves free.  Pairs run along
-// b: acc_re[a][b:b+2] += (zr, zr)(pr_b, pr_b+1) + (zi, zi)(-pi_b, -pi_b+1) and
-// acc_im[a][b:b+2] += (zr, zr)(pi_b, pi_b+1) + (zi, zi)(pr_b, pr_b+1), so the
-// swap area holds Z as (zr, zr, zi, zi) quads and P as three planes
-// (pr, pi, -pi).  Rows are padded so that the writes of a quarter warp and
-// the reads of the eight b-groups fall in distinct banks.
-typedef unsigned long long u64;
-
-// Two spellings of the paired FMA: inline PTX on 64-bit registers, and the
-// compiler builtin on float2.
-struct PairAsm {
-  typedef u64 pair;
-  typedef ulonglong2 quad;
-  static __device__ __forceinline__ pair zero() { return 0ull; }
-  static __device__ __forceinline__ pair fma(pair a, pair b, pair c) {
-    pair d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-  }
-  static __device__ __forceinline__ pair lo(quad q) { return q.x; }
-  static __device__ __forceinline__ pair hi(quad q) { return q.y; }
-  static __device__ __forceinline__ float2 split(pair v) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-  }
-};
-
-struct PairBuiltin {
-  typedef float2 pair;
-  typedef float4 quad;
-  static __device__ __forceinline__ pair zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ pair fma(pair a, pair b, pair c) { return __ffma2_rn(a, b, c); }
-  static __device__ __forceinline__ pair lo(quad q) { return make_float2(q.x, q.y); }
-  static __device__ __forceinline__ pair hi(quad q) { return make_float2(q.z, q.w); }
-  static __device__ __forceinline__ float2 split(pair v) { return v; }
-};
-
-template <int AT_, int BT_, int GA_, int GB_>
-struct Tile2 {
-  static constexpr int AT = AT_, BT = BT_, GA = GA_, GB = GB_;
-  static constexpr int G = GA * GB;
-  static constexpr int NG = 32 / G;
-  static constexpr int AW = GA * AT;
-  static constexpr int TW = GB * BT;
-  static constexpr int DMS = AW * TW;
-  static constexpr int ZG = AT + 1;           // Z quads per a-group row (one quad of padding)
-  static constexpr int ZFL = GA * ZG * 4;     // floats of the Z area
-  static constexpr int PSTR = BT + 4;         // floats per b-group row of a P plane
-  static constexpr int PFL = GB * PSTR;       // floats per P plane
-  static constexpr int GFL = ZFL + 3 * PFL;   // floats per group per stage
-  static constexpr int XFL = NG * GFL;        // floats per warp per stage
-  static constexpr int ZGEN = (AW + G - 1) / G;
-  static constexpr int PGEN = (TW + G - 1) / G;
-  static_assert(32 % G == 0, "bin group must divide a warp");
-  static_assert(BT % 4 == 0, "P rows are read as float4");
-};
-
-using Tile2V8x8 = Tile2<8, 8, 4, 8>;  // 32 x 64 = 2048 trials per bin and warp
-using Tile2V4x8 = Tile2<4, 8, 4, 8>;  // 16 x 64 = 1024
-using Tile2V4x4 = Tile2<4, 4, 2, 4>;  //  8 x 16 =  128, four bins per warp
-
-template <class T, class Op>
-__global__ void __launch_bounds__(kThreads, 1) mac_fp32x2_kernel(const MacArgs a) {
-  typedef typename Op::pair pair;
-  typedef typename Op::quad quad;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
-  float* swap_all = reinterpret_cast<float*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
-
-  for (int i = threadIdx.x; i < a.n_chan; i += kThreads) pcs[i] = a.pc[i];
-  __syncthreads();
-
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / T::G;
-  const int lg = lane % T::G;
-  const int ga = lg / T::GB;
-  const int gb = lg % T::GB;
-  const int k = (blockIdx.x * kWarps + warp) * T::NG + g;
-  const bool k_ok = k < a.n_bins;
-  const uint32_t ku = k_ok ? static_cast<uint32_t>(k) : 0u;
-  const int jblk = blockIdx.y * T::DMS;
-  const int series = blockIdx.z;
-
-  float* grp0 = swap_all + warp * 2 * T::XFL + g * T::GFL;
-
-  uint32_t mz[T::ZGEN];
-  int zoff[T::ZGEN];
-  bool zon[T::ZGEN];
-#pragma unroll
-  for (int q = 0; q < T::ZGEN; ++q) {
-    const int ai = lg + q * T::G;
-    zon[q] = ai < T::AW;
-    mz[q] = ku * static_cast<uint32_t>(a.j_begin + jblk + ai * T::TW);
-    zoff[q] = ((ai / T::AT) * T::ZG + (ai % T::AT)) * 4;
-  }
-  uint32_t mp[T::PGEN];
-  int poff[T::PGEN];
-  bool pon[T::PGEN];
-#pragma unroll
-  for (int q = 0; q < T::PGEN; ++q) {
-    const int bi = lg + q * T::G;
-    pon[q] = bi < T::TW;
-    mp[q] = ku * static_cast<uint32_t>(bi);
-    poff[q] = T::ZFL + (bi / T::BT) * T::PSTR + (bi % T::BT);
-  }
-
-  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + ku;
-  const int64_t xs = a.x_chan_stride;
-
-  pair accr[T::AT][T::BT / 2];
-  pair acci[T::AT][T::BT / 2];
-#pragma unroll
-  for (int i = 0; i < T::AT; ++i)
-#pragma unroll
-    for (int j = 0; j < T::BT / 2; ++j) {
-      accr[i][j] = Op::zero();
-      acci[i][j] = Op::zero();
-    }
-
-  float2 xnext[kPrefetch];
-#pragma unroll
-  for (int i = 0; i < kPrefetch; ++i)
-    xnext[i] = (i < a.n_chan) ? __ldg(xp + i * xs) : make_float2(0.f, 0.f);
-
-  int stage = 0;
-  for (int c0 = 0; c0 < a.n_chan; c0 += kPrefetch) {
-    float2 xcur[kPrefetch];
-#pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) {
-      xcur[i] = xnext[i];
-      const int cn = c0 + kPrefetch + i;
-      xnext[i] = (cn < a.n_chan) ? __ldg(xp + cn * xs) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) {
-      const int c = c0 + i;
-      if (c < a.n_chan) {
-        const PhaseConst p = pcs[c];
-        const uint32_t base = top32_mul(ku, p.u_lo, p.u_hi);
-        float* buf = grp0 + stage * T::XFL;
-#pragma unroll
-        for (int q = 0; q < T::ZGEN; ++q) {
-          if (zon[q]) {
-            const float2 w = unit_phasor(base + top32_mul(mz[q], p.v_lo, p.v_hi));
-            const float2 x = xcur[i];
-            const float zr = x.x * w.x - x.y * w.y;
-            const float zi = x.x * w.y + x.y * w.x;
-            *reinterpret_cast<float4*>(buf + zoff[q]) = make_float4(zr, zr, zi, zi);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < T::PGEN; ++q) {
-          if (pon[q]) {
-            const float2 w = unit_phasor(top32_mul(mp[q], p.v_lo, p.v_hi));
-            buf[poff[q]] = w.x;
-            buf[poff[q] + T::PFL] = w.y;
-            buf[poff[q] + 2 * T::PFL] = -w.y;
-          }
-        }
-        __syncwarp();
-
-        const float* prow = buf + T::ZFL + gb * T::PSTR;
-        pair pr2[T::BT / 2], pi2[T::BT / 2], pn2[T::BT / 2];
-#pragma unroll
-        for (int h = 0; h < T::BT / 4; ++h) {
-          const quad vr = *reinterpret_cast<const quad*>(prow + 4 * h);
-          const quad vi = *reinterpret_cast<const quad*>(prow + T::PFL + 4 * h);
-          const quad vn = *reinterpret_cast<const quad*>(prow + 2 * T::PFL + 4 * h);
-          pr2[2 * h] = Op::lo(vr);
-          pr2[2 * h + 1] = Op::hi(vr);
-          pi2[2 * h] = Op::lo(vi);
-          pi2[2 * h + 1] = Op::hi(vi);
-          pn2[2 * h] = Op::lo(vn);
-          pn2[2 * h + 1] = Op::hi(vn);
-        }
-        const quad* zq = reinterpret_cast<const quad*>(buf + ga * T::ZG * 4);
-#pragma unroll
-        for (int ii = 0; ii < T::AT; ++ii) {
-          const quad z = zq[ii];  // (zr, zr), (zi, zi)
-          const pair zrr = Op::lo(z), zii = Op::hi(z);
-#pragma unroll
-          for (int jp = 0; jp < T::BT / 2; ++jp) {
-            accr[ii][jp] = Op::fma(zrr, pr2[jp], accr[ii][jp]);
-            acci[ii][jp] = Op::fma(zrr, pi2[jp], acci[ii][jp]);
-          }
-#pragma unroll
-          for (int jp = 0; jp < T::BT / 2; ++jp) {
-            accr[ii][jp] = Op::fma(zii, pn2[jp], accr[ii][jp]);
-            acci[ii][jp] = Op::fma(zii, pr2[jp], acci[ii][jp]);
-          }
-        }
-        stage ^= 1;
-      }
-    }
-  }
-
-  if (!k_ok) return;
-  const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
-#pragma unroll
-  for (int ii = 0; ii < T::AT; ++ii) {
-#pragma unroll
-    for (int jp = 0; jp < T::BT / 2; ++jp) {
-      const float2 re2 = Op::split(accr[ii][jp]);
-      const float2 im2 = Op::split(acci[ii][jp]);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int jl = jblk + (ga * T::AT + ii) * T::TW + gb * T::BT + 2 * jp + h;
-        if (jl < a.n_dm) {
-          const float re = (h ? re2.y : re2.x) * a.scale;
-          const float im = real_only ? 0.f : (h ? im2.y : im2.x) * a.scale;
-          const int64_t off = static_cast<int64_t>(series) * a.y_series_stride +
-                              static_cast<int64_t>(jl) * a.y_dm_stride + k;
-          if (a.out_kind == 2)
-            static_cast<float*>(a.Y)[off] = re * re + im * im;
-          else
-            static_cast<float2*>(a.Y)[off] = make_float2(re, im);
-        }
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Variant table: kernel, trials per block, bin groups per warp, swap bytes.
+// ----------------------------------------------------------------- variants
 struct VariantInfo {
   const void* fn;
   int dms;
   int ng;
   size_t swap_bytes;  // per CTA, excluding the phase-constant table
+  int warps = kWarps;
 };
 
-template <class T>
-VariantInfo info_f1() {
-  return {reinterpret_cast<const void*>(&mac_fp32_kernel<T>), T::DMS, T::NG,
-          sizeof(float2) * static_cast<size_t>(kWarps) * 2 * T::XCH};
+VariantInfo info_legacy() {
+  return {reinterpret_cast<const void*>(&mac_legacy_kernel<LegacyV8x8>), LegacyV8x8::DMS,
+          LegacyV8x8::NG, sizeof(float2) * static_cast<size_t>(kWarps) * 2 * LegacyV8x8::XCH};
 }
 
-template <class T, class Op>
-VariantInfo info_f2() {
-  return {reinterpret_cast<const void*>(&mac_fp32x2_kernel<T, Op>), T::DMS, T::NG,
-          sizeof(float) * static_cast<size_t>(kWarps) * 2 * T::XFL};
+template <class Gm, class M, bool kPipe, int W = kWarps>
+VariantInfo info() {
+  return {reinterpret_cast<const void*>(&mac_kernel<Gm, M, kPipe, W>), Gm::DMS, Gm::NG,
+          sizeof(float) * static_cast<size_t>(W) * 2 * Gm::NG * M::GFL, W};
 }
 
 VariantInfo variant_info(int v) {
   switch (v) {
-    case MAC_F1_8x8: return info_f1<TileV8x8>();
-    case MAC_F1_4x8: return info_f1<TileV4x8>();
-    case MAC_F1_4x4: return info_f1<TileV4x4>();
-    case MAC_F2_8x8: return info_f2<Tile2V8x8, PairAsm>();
-    case MAC_F2_4x8: return info_f2<Tile2V4x8, PairAsm>();
-    case MAC_F2_4x4: return info_f2<Tile2V4x4, PairAsm>();
-    case MAC_F3_8x8: return info_f2<Tile2V8x8, PairBuiltin>();
-    case MAC_F3_4x8: return info_f2<Tile2V4x8, PairBuiltin>();
-    default: return info_f2<Tile2V4x4, PairBuiltin>();
+    case MAC_S_8x8: return info<G8x8, Scalar<G8x8>, false>();
+    case MAC_S_4x8: return info<G4x8, Scalar<G4x8>, false>();
+    case MAC_S_4x4: return info<G4x4, Scalar<G4x4>, false>();
+    case MAC_Q_8x8: return info<G8x8, PackedCompact<G8x8>, false>();
+    case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>, false>();
+    case MAC_Q_4x4: return info<G4x4, PackedCompact<G4x4>, false>();
+    case MAC_P_8x8: return info<G8x8, Packed<G8x8>, false>();
+    case MAC_SP_8x8: return info<G8x8, Scalar<G8x8>, true>();
+    case MAC_QP_8x8: return info<G8x8, PackedCompact<G8x8>, true>();
+    case MAC_Q2_8x8: return info<G8x8, PackedCompact2<G8x8>, false>();
+    case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, false, 12>();
+    case MAC_S12_8x8: return info<G8x8, Scalar<G8x8>, false, 12>();
+    default: return info_legacy();
   }
 }
 
 }  // namespace
 
+// Fastest variant per trial count on the survey-shaped workload (kernel-only
+// sweep on GB300: Q12_8x8 49.3 ms, R_8x8 50.3, Q_8x8 52.4, S_8x8 55.6 per
+// 2048-trial, 1024-channel, 131073-bin launch; Q_4x8 and Q_4x4 lead their
+// tile sizes).
 int mac_variant_for(int n_dm) {
-  if (n_dm > 1024) return MAC_F1_8x8;
-  if (n_dm > 256) return MAC_F1_4x8;
-  return MAC_F1_4x4;
+  if (n_dm > 1024) return MAC_Q12_8x8;
+  if (n_dm > 256) return MAC_Q_4x8;
+  return MAC_Q_4x4;
 }
 
 int mac_variant_trials_per_block(int variant) { return variant_info(variant).dms; }
@@ -506,14 +728,14 @@ cudaError_t mac_prepare(int variant, int n_chan) {
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   const VariantInfo vi = variant_info(variant);
-  const int bins_per_cta = kWarps * vi.ng;
+  const int bins_per_cta = vi.warps * vi.ng;
   dim3 grid((a.n_bins + bins_per_cta - 1) / bins_per_cta, (a.n_dm + vi.dms - 1) / vi.dms,
             a.n_series);
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
   MacArgs args = a;
   void* params[] = {&args};
-  return cudaLaunchKernel(vi.fn, grid, dim3(kThreads), params, mac_smem_bytes(variant, a.n_chan),
-                          s);
+  return cudaLaunchKernel(vi.fn, grid, dim3(vi.warps * 32), params,
+                          mac_smem_bytes(variant, a.n_chan), s);
 }
 
 }  // namespace fdd

@@ -115,11 +115,11 @@ def test_invalid_parameters(kw, status):
 
 def test_variant_choice():
     w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
-    assert fdd.fdd_plan_geometry(_params(w))["mac_variant"] == fdd.FDD_MAC_F1_4X4
+    assert fdd.fdd_plan_geometry(_params(w))["mac_variant"] == fdd.FDD_MAC_Q_4X4
     for v in range(fdd.FDD_MAC_VARIANTS):
         assert fdd.fdd_plan_geometry(_params(w, mac_variant=v + 1))["mac_variant"] == v
     w2 = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
-    assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_F1_8X8
+    assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_Q12_8X8
 
 
 def test_geometry_edge_cases():
