@@ -266,6 +266,38 @@ fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on);
  * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA. */
 fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out);
 
+/* Largest channel count accepted by fdd_dedisperse_spectra_static. */
+#define FDD_STATIC_MAX_CHAN 8192
+
+/*
+ * Phase-rotate-and-sum for callers that cannot allocate device memory (the
+ * paper has no counterpart: this entry point exists for such callers).
+ * Applications that hand all of a GPU's memory to their own pool, or
+ * real-time pipelines that forbid allocation once running, cannot create a
+ * plan, because fdd_plan allocates workspace.  This call takes the plan
+ * parameters *p directly (only the fields that the phase-rotate-and-sum
+ * uses are read and checked as fdd_plan would: channels, frequencies, t_samp,
+ * n_t and chunk_len for the transform length, the DM list, k_dm, nu_ref,
+ * mac_variant) and computes exactly what fdd_dedisperse_spectra computes for
+ * a plan made from *p, with the same arguments and layouts.  It allocates
+ * nothing, on the device or the host, and calls no allocating library routine.
+ * The per-channel phase table the kernel reads lives in a file-scope device
+ * array of FDD_STATIC_MAX_CHAN entries (128 KiB), which every GPU that loads
+ * the library holds until the process exits; it is rewritten, in stream
+ * order, by every call.  Calls share that one array, so calls that overlap
+ * on the GPU (on different streams, or from different threads) race and must
+ * be serialised by the caller.  The first call on each device looks up the
+ * array's device address (a one-time set-up); make that first call before
+ * any stream capture.
+ * Errors: FDD_ERR_INVALID_ARG (NULL pointers, n_chan above
+ * FDD_STATIC_MAX_CHAN, bad ranges or pitches), FDD_ERR_UNSUPPORTED
+ * (non-uniform DM list), FDD_ERR_CUDA.
+ */
+fdd_status fdd_dedisperse_spectra_static(const fdd_params* p, const void* d_X, int64_t x_pitch,
+                                         int32_t n_series, int32_t dm_first, int32_t n_dm,
+                                         void* d_Y, int64_t y_pitch, int32_t out_kind,
+                                         fdd_stream_t stream);
+
 /* Release the plan and everything it owns (synchronises the device first).
  * NULL is accepted and ignored. */
 fdd_status fdd_destroy(fdd_plan_t plan);

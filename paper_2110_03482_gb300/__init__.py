@@ -51,8 +51,9 @@ EXPORTS = [
     "fdd_abi_version", "fdd_status_string", "fdd_last_error", "fdd_params_init",
     "fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute", "fdd_execute_dm_range",
     "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
-    "fdd_destroy",
+    "fdd_destroy", "fdd_dedisperse_spectra_static",
 ]
+FDD_STATIC_MAX_CHAN = 8192
 
 FDD_STAGE_UNPACK = 0
 FDD_STAGE_R2C = 1
@@ -165,11 +166,14 @@ def lib() -> ctypes.CDLL:
         L.fdd_execute_host.argtypes = [vp, vp, vp, vp]
         L.fdd_dedisperse_spectra.argtypes = [vp, vp, i64, i32, i32, i32, vp, i64, i32, vp]
         L.fdd_destroy.argtypes = [vp]
+        L.fdd_dedisperse_spectra_static.argtypes = [ctypes.POINTER(fdd_params), vp, i64, i32,
+                                                     i32, i32, vp, i64, i32, vp]
         L.fdd_profile_enable.argtypes = [vp, i32]
         L.fdd_profile_read.argtypes = [vp, ctypes.POINTER(fdd_profile)]
         for name in ["fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute",
                      "fdd_execute_dm_range", "fdd_execute_host", "fdd_dedisperse_spectra",
-                     "fdd_profile_enable", "fdd_profile_read", "fdd_destroy"]:
+                     "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
+                     "fdd_dedisperse_spectra_static"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -271,6 +275,16 @@ def fdd_dedisperse_spectra(plan: int, d_X, x_pitch: int, n_series: int, dm_first
                            stream=None) -> None:
     _check(lib().fdd_dedisperse_spectra(plan, _ptr(d_X), x_pitch, n_series, dm_first, n_dm,
                                         _ptr(d_Y), y_pitch, out_kind, _stream(stream)))
+
+
+def fdd_dedisperse_spectra_static(params: Params, d_X, x_pitch: int, n_series: int,
+                                  dm_first: int, n_dm: int, d_Y, y_pitch: int,
+                                  out_kind: int = FDD_OUT_SPECTRA, stream=None) -> None:
+    """Phase-rotate-and-sum without a plan and without any allocation (for
+    callers whose device memory is owned elsewhere); see include/fdd.h."""
+    _check(lib().fdd_dedisperse_spectra_static(ctypes.byref(params.c), _ptr(d_X), x_pitch,
+                                               n_series, dm_first, n_dm, _ptr(d_Y), y_pitch,
+                                               out_kind, _stream(stream)))
 
 
 def fdd_profile_enable(plan: int, on: bool = True) -> None:

@@ -413,6 +413,18 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
 
 }  // namespace
 
+namespace fdd {
+
+fdd_status report_error(fdd_status s, const char* message) { return fail(s, "%s", message); }
+
+uint64_t fixed64_phase_rate(double m, double rate, double L) {
+  double hi, lo;
+  scaled_product(m, rate, L, &hi, &lo);
+  return frac_to_fixed64(hi, lo);
+}
+
+}  // namespace fdd
+
 extern "C" {
 
 int32_t fdd_abi_version(void) { return FDD_ABI_VERSION; }

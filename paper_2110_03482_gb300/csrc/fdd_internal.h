@@ -61,6 +61,11 @@ cudaError_t mac_prepare(int variant, int n_chan);  // kernel attributes (host, o
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s);
 size_t mac_smem_bytes(int variant, int n_chan);
 
+// Shared with the allocation-free entry point (fdd_noalloc.cu): the last-error
+// setter and the exact 64-bit fixed-point phase rate frac(m * rate / L) * 2^64.
+fdd_status report_error(fdd_status s, const char* message);
+uint64_t fixed64_phase_rate(double m, double rate, double L);
+
 // Unpack / transpose / chunk / zero-pad (Sect. 3: transpose_and_unpack and
 // zero_pad of Algorithm 1) of one beam into channel-major float series.
 struct UnpackArgs {
