@@ -394,39 +394,52 @@ def run_mac_sweep(args) -> None:
 
     fdd.build()
     w = workload_from_args(args)
-    vs = range(fdd.FDD_MAC_VARIANTS) if args.mac_sweep == "all" else \
-        [int(v) for v in args.mac_sweep.split(",")]
+    vs = list(range(fdd.FDD_MAC_VARIANTS)) if args.mac_sweep == "all" else \
+        [v if v == "tc" else int(v) for v in args.mac_sweep.split(",")]
     props = torch.cuda.get_device_properties(0)
     peaks = load_peaks()
     max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
     peak = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12
     g = None
     X = Y = None
+    bf16_peak = float(peaks.get("bf16_tflops") or 1895.5)
     for v in vs:
-        with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA),
-                      mac_variant=v + 1) as plan:
+        tc = v == "tc"
+        ns = w.n_beams if tc else 1
+        kw = dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA)
+        if tc:
+            kw.update(precision=fdd.FDD_PREC_BF16_HILO, n_beams=ns)
+        else:
+            kw.update(mac_variant=v + 1)
+        with fdd.Plan(**kw) as plan:
             g = plan.info
-            if X is None:
+            if X is None or X.shape[0] != ns:
+                X = Y = None
                 gen = torch.Generator(device="cuda").manual_seed(args.seed)
-                X = torch.randn((w.n_chan, g["bin_pitch"], 2), device="cuda", generator=gen)
-                Y = torch.empty((w.n_dm, g["n_bins"], 2), device="cuda")
+                X = torch.randn((ns, w.n_chan, g["bin_pitch"], 2), device="cuda", generator=gen)
+                Y = torch.empty((ns, w.n_dm, g["n_bins"], 2), device="cuda")
             for _ in range(max(args.warmup, 1)):
-                plan.dedisperse_spectra(X, g["bin_pitch"], 1, 0, w.n_dm, Y, g["n_bins"])
+                plan.dedisperse_spectra(X, g["bin_pitch"], ns, 0, w.n_dm, Y, g["n_bins"])
             torch.cuda.synchronize()
             clocks = Clocks(gpu_uuid(props, 0))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(args.steps):
-                plan.dedisperse_spectra(X, g["bin_pitch"], 1, 0, w.n_dm, Y, g["n_bins"])
+                plan.dedisperse_spectra(X, g["bin_pitch"], ns, 0, w.n_dm, Y, g["n_bins"])
             e1.record()
             torch.cuda.synchronize()
             clk = clocks.stop()
             ms = e0.elapsed_time(e1) / args.steps
-        flops = FLOPS_PER_MAC * w.n_dm * w.n_chan * g["n_bins"]
+            plan.query()  # raises if a kernel reported a device-side timeout
+        flops = FLOPS_PER_MAC * ns * w.n_dm * w.n_chan * g["n_bins"]
         tf = flops / (ms / 1e3) / 1e12
-        print(json.dumps({"sweep": fdd.MAC_VARIANT_NAMES[v], "variant": v, "ms_per_launch": ms,
+        extra = {"frac_bf16_peak_algorithmic": tf / bf16_peak,
+                 "tensor_tflops_hi_lo": 2 * tf} if tc else {}
+        print(json.dumps({"sweep": "TC" if tc else fdd.MAC_VARIANT_NAMES[v], "variant": v,
+                          "ms_per_launch": ms, "beams": ns, "macs_per_s": tf * 1e12 / 8,
                           "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,
+                          **extra,
                           "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
                           "n_bins": g["n_bins"], "n_dm": w.n_dm, "n_chan": w.n_chan}),
               flush=True)

@@ -89,11 +89,13 @@ typedef enum fdd_status {
 #define FDD_MAC_Q12_8X8 11 /* Q with 12-warp blocks (fewer registers, more warps)  */
 #define FDD_MAC_S12_8X8 12 /* S with 12-warp blocks                                */
 #define FDD_MAC_VARIANTS 13
+#define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
 
 /* fdd_params.precision */
 #define FDD_PREC_FP32 0      /* FP32 phasors and accumulation (CUDA cores)       */
-#define FDD_PREC_BF16_HILO 1 /* tensor cores, BF16 hi+lo phasors (Sect. 5 future
-                                work); reserved, returns FDD_ERR_UNSUPPORTED     */
+#define FDD_PREC_BF16_HILO 1 /* tensor cores (tcgen05), the direction of Sect. 5:
+                                BF16 hi+lo phasors, BF16 data, FP32 accumulation;
+                                all beams of a chunk share each bin's phasors    */
 
 typedef struct fdd_params {
   int32_t n_chan;         /* observing channels N_nu, >= 1                          */
@@ -278,8 +280,9 @@ fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out);
  * parameters *p directly (only the fields that the phase-rotate-and-sum
  * uses are read and checked as fdd_plan would: channels, frequencies, t_samp,
  * n_t and chunk_len for the transform length, the DM list, k_dm, nu_ref,
- * mac_variant) and computes exactly what fdd_dedisperse_spectra computes for
- * a plan made from *p, with the same arguments and layouts.  It allocates
+ * mac_variant; precision must be FDD_PREC_FP32) and computes exactly what
+ * fdd_dedisperse_spectra computes for a plan made from *p, with the same
+ * arguments and layouts.  It allocates
  * nothing, on the device or the host, and calls no allocating library routine.
  * The per-channel phase table the kernel reads lives in a file-scope device
  * array of FDD_STATIC_MAX_CHAN entries (128 KiB), which every GPU that loads
@@ -291,7 +294,7 @@ fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out);
  * any stream capture.
  * Errors: FDD_ERR_INVALID_ARG (NULL pointers, n_chan above
  * FDD_STATIC_MAX_CHAN, bad ranges or pitches), FDD_ERR_UNSUPPORTED
- * (non-uniform DM list), FDD_ERR_CUDA.
+ * (non-uniform DM list, precision other than FP32), FDD_ERR_CUDA.
  */
 fdd_status fdd_dedisperse_spectra_static(const fdd_params* p, const void* d_X, int64_t x_pitch,
                                          int32_t n_series, int32_t dm_first, int32_t n_dm,

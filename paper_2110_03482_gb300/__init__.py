@@ -45,6 +45,7 @@ MAC_VARIANT_NAMES = ["S_8x8", "S_4x8", "S_4x4", "Q_8x8", "Q_4x8", "Q_4x4", "P_8x
 for _i, _n in enumerate(MAC_VARIANT_NAMES):
     globals()["FDD_MAC_" + _n.upper()] = _i
 FDD_MAC_VARIANTS = len(MAC_VARIANT_NAMES)
+FDD_MAC_TC = 100
 
 # Every symbol include/fdd.h declares.
 EXPORTS = [

@@ -29,7 +29,11 @@ struct fdd_plan_s {
   fdd::PhaseConst* d_pc = nullptr;
   float* d_xw = nullptr;      // [n_chan][L] channel series of one chunk
   float2* d_X = nullptr;      // [n_chan][bin_pitch] their spectra
-  float2* d_Y = nullptr;      // [dm_batch][bin_pitch] dedispersed spectra (time output)
+                              // (tensor-core form: [beam][n_chan][bin_pitch], every beam)
+  bool tc = false;            // tensor-core form (FDD_PREC_BF16_HILO)
+  int n_sms = 0;
+  float2* d_Y = nullptr;      // [dm_batch][bin_pitch] dedispersed spectra (time output;
+                              // tensor-core form: [beam][dm_batch][bin_pitch])
   float* d_yt = nullptr;      // [dm_batch][L] inverse transforms (time output)
   void* d_fftwork = nullptr;
   int* d_status = nullptr;
@@ -153,9 +157,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
     return fail(FDD_ERR_INVALID_ARG, "in_layout %d unknown", p->in_layout);
   if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
-  if (p->precision == FDD_PREC_BF16_HILO)
-    return fail(FDD_ERR_UNSUPPORTED, "precision FDD_PREC_BF16_HILO is not available in this build");
-  if (p->precision != FDD_PREC_FP32)
+  if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO)
     return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
@@ -259,23 +261,27 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   g->dm0 = dm0;
   g->ddm = ddm;
   g->dm_uniform = uniform;
-  g->mac_variant = p->mac_variant ? p->mac_variant - 1 : fdd::mac_variant_for(p->n_dm);
-  if (fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
+  const bool tc = p->precision == FDD_PREC_BF16_HILO;
+  g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
+                                                     : fdd::mac_variant_for(p->n_dm));
+  if (!tc && fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
     return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
 
+  const size_t spectra_sets = tc ? static_cast<size_t>(p->n_beams) : 1;
   const size_t fixed = sizeof(fdd::PhaseConst) * nc + sizeof(float) * size_t(nc) * L +
-                       sizeof(float2) * size_t(nc) * g->bin_pitch + 256;
+                       sizeof(float2) * size_t(nc) * g->bin_pitch * spectra_sets + 256;
   const size_t limit = p->workspace_limit ? p->workspace_limit : kDefaultWorkspace;
   int64_t batch = p->n_dm;
   size_t per_dm = 0;
   if (p->output == FDD_OUT_TIME) {
-    per_dm = sizeof(float2) * g->bin_pitch + sizeof(float) * L;
+    per_dm = sizeof(float2) * g->bin_pitch * spectra_sets + sizeof(float) * L;
     if (fixed + per_dm > limit)
       return fail(FDD_ERR_INVALID_ARG, "workspace_limit %zu is below the minimum %zu", limit,
                   fixed + per_dm);
     const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
     if (fit < batch) {
-      const int64_t blk = fdd::mac_variant_trials_per_block(g->mac_variant);
+      const int64_t blk = tc ? fdd::mac_tc_trials_per_pass()
+                             : fdd::mac_variant_trials_per_block(g->mac_variant);
       batch = fit >= blk ? fit / blk * blk : fit;
     }
     if (batch > 65535) batch = 65535 / 64 * 64;
@@ -321,6 +327,9 @@ fdd_status check_device(const fdd_plan_s* P) {
   return FDD_OK;
 }
 
+fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
+                  cudaStream_t s);
+
 fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
                cudaStream_t s) {
   const fdd_params& p = P->p;
@@ -330,6 +339,7 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
   FDD_CUFFT(cufftSetStream(P->r2c, s));
   if (P->has_c2r) FDD_CUFFT(cufftSetStream(P->c2r, s));
   if (P->has_c2r_tail) FDD_CUFFT(cufftSetStream(P->c2r_tail, s));
+  if (P->tc) return run_tc(P, d_in, dm_first, n_dm, d_out, s);
 
   for (int b = 0; b < p.n_beams; ++b) {
     const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
@@ -411,6 +421,99 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
   return FDD_OK;
 }
 
+// Tensor-core form: every beam of a chunk is transformed first, then one
+// launch dedisperses all of them at once (the beams share each bin's phasors).
+fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
+                  cudaStream_t s) {
+  const fdd_params& p = P->p;
+  const fdd_info& g = P->info;
+  const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
+  const int64_t beam_elems = p.n_t * static_cast<int64_t>(p.n_chan);
+  const int64_t set_elems = static_cast<int64_t>(p.n_chan) * g.bin_pitch;
+  for (int64_t c = 0; c < g.n_chunks; ++c) {
+    for (int b = 0; b < p.n_beams; ++b) {
+      const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
+      fdd::UnpackArgs ua{in_b, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop, g.fft_len,
+                         P->d_xw, g.fft_len};
+      {
+        StageTimer t(P, FDD_STAGE_UNPACK, s);
+        FDD_CUDA(fdd::launch_unpack(ua, s));
+      }
+      {
+        StageTimer t(P, FDD_STAGE_R2C, s);
+        FDD_CUFFT(cufftExecR2C(P->r2c, P->d_xw,
+                               reinterpret_cast<cufftComplex*>(P->d_X + set_elems * b)));
+      }
+    }
+    fdd::MacArgs m{};
+    m.X = P->d_X;
+    m.x_series_stride = set_elems;
+    m.x_chan_stride = g.bin_pitch;
+    m.pc = P->d_pc;
+    m.n_chan = p.n_chan;
+    m.n_bins = static_cast<int>(g.n_bins);
+    m.n_series = p.n_beams;
+    m.scale = 1.0f;
+    m.status = P->d_status;
+    if (p.output == FDD_OUT_TIME) {
+      for (int j0 = dm_first; j0 < dm_first + n_dm; j0 += g.dm_batch) {
+        const int nb = (dm_first + n_dm - j0) < g.dm_batch ? (dm_first + n_dm - j0) : g.dm_batch;
+        m.j_begin = j0;
+        m.n_dm = nb;
+        m.Y = P->d_Y;
+        m.y_series_stride = static_cast<int64_t>(g.dm_batch) * g.bin_pitch;
+        m.y_dm_stride = g.bin_pitch;
+        m.out_kind = 1;
+        m.real_bin_a = 0;
+        m.real_bin_b = static_cast<int>(g.fft_len / 2);
+        {
+          StageTimer t(P, FDD_STAGE_MAC, s);
+          FDD_CUDA(fdd::launch_mac_tc(m, P->n_sms, s));
+        }
+        cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
+        const int64_t keep = (g.out_len - c * g.hop) < g.hop ? (g.out_len - c * g.hop) : g.hop;
+        for (int b = 0; b < p.n_beams; ++b) {
+          {
+            StageTimer t(P, FDD_STAGE_C2R, s);
+            FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(
+                                          P->d_Y + static_cast<int64_t>(b) * g.dm_batch * g.bin_pitch),
+                                   P->d_yt));
+          }
+          fdd::ScatterArgs sa{};
+          sa.src = P->d_yt;
+          sa.src_stride = g.fft_len;
+          sa.dst = static_cast<float*>(d_out) +
+                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * g.hop;
+          sa.dst_stride = g.out_len;
+          sa.n_dm = nb;
+          sa.n_keep = keep;
+          sa.scale = static_cast<float>(1.0 / static_cast<double>(g.fft_len));
+          StageTimer t(P, FDD_STAGE_SCATTER, s);
+          FDD_CUDA(fdd::launch_scatter(sa, s));
+        }
+      }
+    } else {
+      m.j_begin = dm_first;
+      m.n_dm = n_dm;
+      m.y_series_stride = g.n_chunks * static_cast<int64_t>(n_dm) * g.n_bins;
+      m.y_dm_stride = g.n_bins;
+      m.real_bin_a = -1;
+      m.real_bin_b = -1;
+      const int64_t off = c * static_cast<int64_t>(n_dm) * g.n_bins;
+      if (p.output == FDD_OUT_SPECTRA) {
+        m.out_kind = 1;
+        m.Y = static_cast<float2*>(d_out) + off;
+      } else {
+        m.out_kind = 2;
+        m.Y = static_cast<float*>(d_out) + off;
+      }
+      StageTimer t(P, FDD_STAGE_MAC, s);
+      FDD_CUDA(fdd::launch_mac_tc(m, P->n_sms, s));
+    }
+  }
+  return FDD_OK;
+}
+
 }  // namespace
 
 namespace fdd {
@@ -480,7 +583,12 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
     return fail(FDD_ERR_UNSUPPORTED, "kernels are built for sm_103a; device is sm_%d%d", major,
                 minor);
   fdd_info& g = P->info;
-  FDD_CUDA(fdd::mac_prepare(g.mac_variant, p->n_chan));
+  P->tc = p->precision == FDD_PREC_BF16_HILO;
+  FDD_CUDA(cudaDeviceGetAttribute(&P->n_sms, cudaDevAttrMultiProcessorCount, P->device));
+  if (P->tc)
+    FDD_CUDA(fdd::mac_tc_prepare());
+  else
+    FDD_CUDA(fdd::mac_prepare(g.mac_variant, p->n_chan));
 
   // Exact fixed-point phase rates (see fdd_internal.h).
   const double L = static_cast<double>(g.fft_len);
@@ -501,12 +609,13 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_status), 256))) return st;
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_xw), sizeof(float) * size_t(nc) * g.fft_len)))
     return st;
+  const size_t sets = P->tc ? static_cast<size_t>(p->n_beams) : 1;
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_X),
-                      sizeof(float2) * size_t(nc) * g.bin_pitch)))
+                      sizeof(float2) * size_t(nc) * g.bin_pitch * sets)))
     return st;
   if (p->output == FDD_OUT_TIME) {
     if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_Y),
-                        sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch)))
+                        sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch * sets)))
       return st;
     if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_yt),
                         sizeof(float) * size_t(g.dm_batch) * g.fft_len)))
@@ -635,7 +744,10 @@ fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pi
   m.real_bin_b = -1;
   m.status = plan->d_status;
   StageTimer t(plan, FDD_STAGE_MAC, reinterpret_cast<cudaStream_t>(stream));
-  FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));
+  if (plan->tc)
+    FDD_CUDA(fdd::launch_mac_tc(m, plan->n_sms, reinterpret_cast<cudaStream_t>(stream)));
+  else
+    FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));
   return FDD_OK;
 }
 

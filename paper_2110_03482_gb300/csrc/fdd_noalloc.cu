@@ -74,6 +74,9 @@ extern "C" fdd_status fdd_dedisperse_spectra_static(const fdd_params* p, const v
     return report_error(FDD_ERR_INVALID_ARG, "chunk_len must be 0 or a positive even length");
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return report_error(FDD_ERR_INVALID_ARG, "mac_variant out of range");
+  if (p->precision != FDD_PREC_FP32)
+    return report_error(FDD_ERR_UNSUPPORTED,
+                        "the allocation-free entry point runs the FP32 form only");
   if (n_series < 1 || n_series > 65535)
     return report_error(FDD_ERR_INVALID_ARG, "n_series must be in [1, 65535]");
   if (dm_first < 0 || n_dm < 1 || dm_first + static_cast<int64_t>(n_dm) > p->n_dm)

@@ -97,7 +97,7 @@ def test_geometry_survey_values():
     (dict(nu_ref_mhz=1000.0), fdd.FDD_ERR_INVALID_ARG),   # below the top channel
     (dict(in_dtype=7), fdd.FDD_ERR_INVALID_ARG),
     (dict(output=9), fdd.FDD_ERR_INVALID_ARG),
-    (dict(precision=fdd.FDD_PREC_BF16_HILO), fdd.FDD_ERR_UNSUPPORTED),
+    (dict(precision=5), fdd.FDD_ERR_INVALID_ARG),
     (dict(dm_list=np.array([0.0, 1.0, 3.0])), fdd.FDD_ERR_UNSUPPORTED),
     (dict(dm_list=np.array([-1.0, 0.0])), fdd.FDD_ERR_INVALID_ARG),
     (dict(dm_list=np.array([0.0, np.nan])), fdd.FDD_ERR_INVALID_ARG),
@@ -120,6 +120,22 @@ def test_variant_choice():
         assert fdd.fdd_plan_geometry(_params(w, mac_variant=v + 1))["mac_variant"] == v
     w2 = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
     assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_Q12_8X8
+
+
+def test_tensor_core_form_geometry():
+    """The tensor-core form holds the spectra of every beam at once and batches
+    DMs in whole 1024-trial passes when the workspace is bounded."""
+    w = synth.WORKLOADS["fdd_32beam_1024ch_2p19t_4096dm"]
+    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
+                                      workspace_limit=200 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC
+    assert g["dm_batch"] % 1024 == 0 and 0 < g["dm_batch"] <= 4096
+    spectra = 32 * 1024 * g["bin_pitch"] * 8
+    assert spectra < g["workspace_bytes"] <= 200 << 30
+    # below one 1024-trial pass per batch the batch is whatever fits
+    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
+                                      workspace_limit=120 << 30))
+    assert 0 < g["dm_batch"] < 1024 and g["workspace_bytes"] <= 120 << 30
 
 
 def test_geometry_edge_cases():

@@ -1,0 +1,125 @@
+"""Tensor-core form (tcgen05, BF16 hi+lo phasors, BF16 data, FP32 accumulation)
+against the FP64 oracle (GB300 only).
+
+The gate is the low-precision form's relative L2 error <= 3e-3 against FP64:
+BF16 rounding of the data side alone is ~2^-9 / sqrt(3) ~ 1.1e-3 per element.
+Shapes span partial and several beam groups (32 beams each), a ragged last
+channel tile (32 channels each) and partial 1024-trial passes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2110_03482_gb300 as fdd
+import synth
+from gpu_util import complex_to_device, device_to_complex, params_for, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TC_REL_L2 = 3e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fdd.build()
+
+
+def _workload(n_chan, n_t, dms, n_beams, band=(1200.0, 1500.0), t_samp=2e-3, chunk_len=0,
+              output="spectra", dtype="f32"):
+    dms = np.asarray(dms, dtype=np.float64)
+    ddm = float(dms[1] - dms[0]) if dms.size > 1 else 0.0
+    return synth.Workload(name="tc", n_chan=n_chan, band_lo_mhz=band[0], band_hi_mhz=band[1],
+                          t_samp_s=t_samp, n_t=n_t, dtype=dtype, dm0=float(dms[0]), ddm=ddm,
+                          n_dm=dms.size, chunk_len=chunk_len, n_beams=n_beams, output=output,
+                          pulses_per_beam=1)
+
+
+@pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
+    (5, 40, 256, 0.0, 0.5, 1100),    # partial beam group, ragged channel tile, 2 passes
+    (32, 64, 128, 3.0, 1.0, 1024),   # one full group, exactly one pass
+    (37, 33, 512, 0.0, 0.25, 300),   # two groups, one partial pass
+])
+def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm):
+    dms = dm0 + ddm * np.arange(n_dm)
+    w = _workload(n_chan, L, dms, n_series)
+    K = L // 2 + 1
+    rng = np.random.default_rng(n_series * 1000 + n_chan)
+    X = (rng.standard_normal((n_series, n_chan, K)) +
+         1j * rng.standard_normal((n_series, n_chan, K))).astype(np.complex64).astype(np.complex128)
+    xp, yp = K + 5, K + 2
+    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA,
+                               precision=fdd.FDD_PREC_BF16_HILO)) as plan:
+        assert plan.info["mac_variant"] == fdd.FDD_MAC_TC
+        dX = complex_to_device(X, xp)
+        dY = torch.zeros((n_series, n_dm, yp, 2), dtype=torch.float32, device="cuda")
+        plan.dedisperse_spectra(dX, xp, n_series, 0, n_dm, dY, yp)
+        dP = torch.zeros((n_series, n_dm, yp), dtype=torch.float32, device="cuda")
+        plan.dedisperse_spectra(dX, xp, n_series, 0, n_dm, dP, yp, out_kind=fdd.FDD_OUT_POWER)
+        torch.cuda.synchronize()
+        assert plan.query()["n_bins"] == K  # also reports a device-side timeout, if any
+        Y = device_to_complex(dY, K)
+        P = dP.cpu().numpy()[..., :K].astype(np.float64)
+        assert np.all(dY.cpu().numpy()[..., K:, :] == 0)
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    errs = []
+    for s in range(n_series):
+        ref = oracle.fdd_bins(X[s], np.arange(K), L, d)
+        errs.append(rel_l2(Y[s], ref))
+        assert rel_l2(P[s], np.abs(ref) ** 2) <= 2 * TC_REL_L2
+    print(f"tensor-core rel-L2 vs FP64: max over series {max(errs):.2e}")
+    assert max(errs) <= TC_REL_L2
+
+
+def test_tc_dm_subrange_matches_full():
+    n_series, n_chan, L = 8, 48, 256
+    dms = 0.5 * np.arange(2100)
+    w = _workload(n_chan, L, dms, n_series)
+    K = L // 2 + 1
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((n_series, n_chan, K)) + 1j * rng.standard_normal((n_series, n_chan, K))
+    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA,
+                               precision=fdd.FDD_PREC_BF16_HILO)) as plan:
+        dX = complex_to_device(X, K)
+        full = torch.zeros((n_series, 2100, K, 2), device="cuda")
+        plan.dedisperse_spectra(dX, K, n_series, 0, 2100, full, K)
+        part = torch.zeros((n_series, 700, K, 2), device="cuda")
+        plan.dedisperse_spectra(dX, K, n_series, 1111, 700, part, K)
+        torch.cuda.synchronize()
+        f = device_to_complex(full, K)[:, 1111:1811]
+        g = device_to_complex(part, K)
+    # same phasors, different split of the trial index: equal to BF16 accuracy
+    assert rel_l2(g, f) <= TC_REL_L2
+
+
+@pytest.mark.parametrize("output", ["time", "power"])
+def test_tc_end_to_end(output):
+    """Eight beams through the whole path on the tensor-core form."""
+    w = _workload(48, 3000, 2.0 * np.arange(150), 8, t_samp=5e-4, chunk_len=1024,
+                  output=output)
+    fbs = np.stack([synth.filterbank(w, seed=17, beam=b)[0] for b in range(8)])
+    with fdd.Plan(**params_for(w, precision=fdd.FDD_PREC_BF16_HILO)) as plan:
+        info = plan.info
+        dx = torch.from_numpy(fbs).cuda()
+        out = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
+        plan.execute(dx, out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.float64)
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    geo = oracle.geometry(w.n_t, w.chunk_len, d)
+    if output == "time":
+        o = o.reshape(8, w.n_dm, info["out_len"])
+        for b in range(8):
+            ref = oracle.fdd_time(fbs[b].T.astype(np.float64), d, w.chunk_len)
+            assert rel_l2(o[b], ref) <= TC_REL_L2
+    else:
+        o = o.reshape(8, geo.n_chunks, w.n_dm, geo.K)
+        for b in range(0, 8, 3):
+            x = fbs[b].T.astype(np.float64)
+            for c in range(geo.n_chunks):
+                ref = np.abs(oracle.fdd_bins(oracle.spectra(x, geo, c), np.arange(geo.K),
+                                             geo.L, d)) ** 2
+                assert rel_l2(o[b, c], ref) <= 2 * TC_REL_L2
