@@ -395,7 +395,7 @@ def run_mac_sweep(args) -> None:
     fdd.build()
     w = workload_from_args(args)
     vs = list(range(fdd.FDD_MAC_VARIANTS)) if args.mac_sweep == "all" else \
-        [v if v == "tc" else int(v) for v in args.mac_sweep.split(",")]
+        [v if v in ("tc", "tc1") else int(v) for v in args.mac_sweep.split(",")]
     props = torch.cuda.get_device_properties(0)
     peaks = load_peaks()
     max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
@@ -404,11 +404,12 @@ def run_mac_sweep(args) -> None:
     X = Y = None
     bf16_peak = float(peaks.get("bf16_tflops") or 1895.5)
     for v in vs:
-        tc = v == "tc"
+        tc = v in ("tc", "tc1")
         ns = w.n_beams if tc else 1
         kw = dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA)
         if tc:
-            kw.update(precision=fdd.FDD_PREC_BF16_HILO, n_beams=ns)
+            kw.update(precision=fdd.FDD_PREC_BF16_HILO if v == "tc" else fdd.FDD_PREC_BF16,
+                      n_beams=ns)
         else:
             kw.update(mac_variant=v + 1)
         with fdd.Plan(**kw) as plan:
@@ -435,8 +436,9 @@ def run_mac_sweep(args) -> None:
         flops = FLOPS_PER_MAC * ns * w.n_dm * w.n_chan * g["n_bins"]
         tf = flops / (ms / 1e3) / 1e12
         extra = {"frac_bf16_peak_algorithmic": tf / bf16_peak,
-                 "tensor_tflops_hi_lo": 2 * tf} if tc else {}
-        print(json.dumps({"sweep": "TC" if tc else fdd.MAC_VARIANT_NAMES[v], "variant": v,
+                 "tensor_tflops_physical": (2 if v == "tc" else 1) * tf} if tc else {}
+        print(json.dumps({"sweep": {"tc": "TC_hilo", "tc1": "TC_bf16"}.get(v, None) or
+                          fdd.MAC_VARIANT_NAMES[v], "variant": v,
                           "ms_per_launch": ms, "beams": ns, "macs_per_s": tf * 1e12 / 8,
                           "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,
                           **extra,

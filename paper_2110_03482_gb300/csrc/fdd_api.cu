@@ -157,7 +157,8 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
     return fail(FDD_ERR_INVALID_ARG, "in_layout %d unknown", p->in_layout);
   if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
-  if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO)
+  if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO &&
+      p->precision != FDD_PREC_BF16)
     return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
@@ -261,7 +262,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   g->dm0 = dm0;
   g->ddm = ddm;
   g->dm_uniform = uniform;
-  const bool tc = p->precision == FDD_PREC_BF16_HILO;
+  const bool tc = p->precision != FDD_PREC_FP32;
   g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
                                                      : fdd::mac_variant_for(p->n_dm));
   if (!tc && fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
@@ -468,7 +469,7 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.real_bin_b = static_cast<int>(g.fft_len / 2);
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
-          FDD_CUDA(fdd::launch_mac_tc(m, P->n_sms, s));
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, s));
         }
         cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
         const int64_t keep = (g.out_len - c * g.hop) < g.hop ? (g.out_len - c * g.hop) : g.hop;
@@ -508,7 +509,7 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.Y = static_cast<float*>(d_out) + off;
       }
       StageTimer t(P, FDD_STAGE_MAC, s);
-      FDD_CUDA(fdd::launch_mac_tc(m, P->n_sms, s));
+      FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, s));
     }
   }
   return FDD_OK;
@@ -583,7 +584,7 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
     return fail(FDD_ERR_UNSUPPORTED, "kernels are built for sm_103a; device is sm_%d%d", major,
                 minor);
   fdd_info& g = P->info;
-  P->tc = p->precision == FDD_PREC_BF16_HILO;
+  P->tc = p->precision != FDD_PREC_FP32;
   FDD_CUDA(cudaDeviceGetAttribute(&P->n_sms, cudaDevAttrMultiProcessorCount, P->device));
   if (P->tc)
     FDD_CUDA(fdd::mac_tc_prepare());
@@ -745,7 +746,8 @@ fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pi
   m.status = plan->d_status;
   StageTimer t(plan, FDD_STAGE_MAC, reinterpret_cast<cudaStream_t>(stream));
   if (plan->tc)
-    FDD_CUDA(fdd::launch_mac_tc(m, plan->n_sms, reinterpret_cast<cudaStream_t>(stream)));
+    FDD_CUDA(fdd::launch_mac_tc(m, plan->p.precision == FDD_PREC_BF16_HILO, plan->n_sms,
+                                reinterpret_cast<cudaStream_t>(stream)));
   else
     FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));
   return FDD_OK;

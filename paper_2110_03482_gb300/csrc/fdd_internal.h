@@ -61,12 +61,13 @@ cudaError_t mac_prepare(int variant, int n_chan);  // kernel attributes (host, o
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s);
 size_t mac_smem_bytes(int variant, int n_chan);
 
-// Tensor-core phase-rotate-and-sum (fdd_mac_tc.cu): BF16 hi+lo phasors, BF16
-// data, FP32 accumulation in tensor memory; one persistent CTA per SM.
+// Tensor-core phase-rotate-and-sum (fdd_mac_tc.cu): BF16 hi+lo (or BF16)
+// phasors, BF16 data, FP32 accumulation in tensor memory; one persistent CTA
+// per SM.
 size_t mac_tc_smem_bytes();
 int mac_tc_trials_per_pass();
 cudaError_t mac_tc_prepare();
-cudaError_t launch_mac_tc(const MacArgs& a, int n_sms, cudaStream_t s);
+cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s);
 
 // Shared with the allocation-free entry point (fdd_noalloc.cu): the last-error
 // setter and the exact 64-bit fixed-point phase rate frac(m * rate / L) * 2^64.

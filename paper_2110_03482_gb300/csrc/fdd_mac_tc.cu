@@ -11,17 +11,19 @@
 // i.e. for every group of a's one complex GEMM of (T x N_nu) phasors P by
 // (N_nu x beams) data.  It runs on tcgen05 as a real GEMM
 //   D[b][(a, beta, re|im)] = sum_{nu, re|im} A[b][(nu, re|im)] B[(a, beta, re|im)][(nu, re|im)]
-// with A = [Pr | Pi] (BF16 hi + lo: two MMAs) and B the real embedding
+// with A = [Pr | Pi] (BF16 hi + lo: two MMAs; or BF16 alone) and B the real embedding
 // [[Zr, -Zi], [Zi, Zr]] of Z (BF16), FP32 accumulation in tensor memory.
 // M = 128 trials b, N = 256 = 4 a's x 32 beams x (re, im), K = 64 per stage
-// (32 channels x (re, im)); two accumulators cover 8 a's = 1024 trials per
-// pass over the channels.
+// (32 channels x (re, im)); one pass over the channels covers 4 a's = 512
+// trials, and passes alternate between two accumulators in tensor memory.
 //
-// Warp 0 allocates tensor memory and one of its threads issues the MMAs; 8
-// producer warps evaluate P (exact fixed-point phase, MUFU sin/cos, hi/lo
-// split) and Z = Q X for each stage straight into the 128-byte-swizzled
-// K-major shared layout the MMA descriptors address, through a 2-stage
-// mbarrier ring, and read the accumulators back (tcgen05.ld) for the store.
+// Warp specialisation: warp 0 allocates tensor memory and one of its threads
+// issues the MMAs; 16 producer warps evaluate P (exact fixed-point phase,
+// MUFU sin/cos and short recurrences, hi/lo split) and Z = Q X for each stage
+// straight into the 128-byte-swizzled K-major shared layout the MMA
+// descriptors address, through a 3-stage mbarrier ring; 4 epilogue warps read
+// one accumulator back (tcgen05.ld) and store it while the MMAs of the next
+// pass fill the other.
 // Every wait is bounded: on timeout the kernel records FDD_ERR_TIMEOUT in the
 // status word, stops, drains its own MMAs (bounded), frees its tensor memory
 // and returns.
@@ -35,19 +37,20 @@ namespace {
 constexpr int kM = 128;                  // trials b per a (T)
 constexpr int kN = 256;                  // accumulator columns
 constexpr int kBeams = 32;               // beams per group
-constexpr int kNA = kN / (2 * kBeams);   // a's per accumulator (4)
-constexpr int kAcc = 2;                  // accumulators in tensor memory
-constexpr int kAPass = kNA * kAcc;       // a's per pass (8)
-constexpr int kDmsPass = kAPass * kM;    // trials per pass (1024)
+constexpr int kNA = kN / (2 * kBeams);   // a's per pass (4)
+constexpr int kDmsPass = kNA * kM;       // trials per pass (512)
 constexpr int kKC = 32;                  // channels per stage
-constexpr int kProdWarps = 8;
+constexpr int kProdWarps = 16;
 constexpr int kProd = 32 * kProdWarps;
-constexpr int kThreads = 32 + kProd;
+constexpr int kEpiWarps = 4;             // one per tensor-memory lane quarter
+constexpr int kEpi = 32 * kEpiWarps;
+constexpr int kThreads = 32 + kEpi + kProd;
 constexpr uint32_t kTileA = kM * 64 * 2;  // 16 KB
 constexpr uint32_t kTileB = kN * 64 * 2;  // 32 KB
-constexpr uint32_t kStageBytes = 2 * kTileA + kAcc * kTileB;  // 96 KB
-constexpr int kStages = 2;
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kStageBytes = 2 * kTileA + kTileB;  // 64 KB
+constexpr int kStages = 3;
+constexpr int kAccBufs = 2;              // accumulators alternate between passes
+constexpr uint32_t kTmemCols = kAccBufs * kN;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -128,28 +131,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// kHiLo: phasors as BF16 hi + lo (two MMAs per K step); otherwise BF16 only.
+template <bool kHiLo>
 __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
-  uint64_t* full = bars;              // [kStages], producers -> MMA
-  uint64_t* empty = bars + kStages;   // [kStages], MMA commit -> producers
-  uint64_t* acc_full = bars + 2 * kStages;
-  uint64_t* acc_empty = bars + 2 * kStages + 1;
-  uint64_t* drain = bars + 2 * kStages + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
+  uint64_t* full = bars;                        // [kStages]  producers -> MMA
+  uint64_t* empty = bars + kStages;             // [kStages]  MMA commit -> producers
+  uint64_t* acc_full = bars + 2 * kStages;      // [kAccBufs] MMA commit -> epilogue
+  uint64_t* acc_empty = acc_full + kAccBufs;    // [kAccBufs] epilogue -> MMA
+  uint64_t* drain = acc_empty + kAccBufs;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], kProd);
-      mbar_init(&empty[s], 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], kProd);
+      mbar_init(&empty[i], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kProd);
+    for (int i = 0; i < kAccBufs; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], kEpi);
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -175,43 +182,39 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t s = 0, p = 0;
-      bool issued = false;
-      for (int k = blockIdx.x; k < a.n_bins && !*abort_flag; k += gridDim.x) {
-        for (int it = 0; it < items_per_bin && !*abort_flag; ++it) {
-          if (!mbar_wait(acc_empty, (p & 1) ^ 1, abort_flag)) {
-            *abort_flag = 1;
+      bool issued = false, ok = true;
+      for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
+        for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
+          const uint32_t buf = p % kAccBufs;
+          if (!mbar_wait(&acc_empty[buf], ((p / kAccBufs) & 1) ^ 1, abort_flag)) {
+            ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          bool ok = true;
+          const uint32_t d = tmem + buf * kN;
           for (int t = 0; t < n_tiles; ++t, ++s) {
             const uint32_t st = s % kStages;
             if (!mbar_wait(&full[st], (s / kStages) & 1, abort_flag)) {
-              *abort_flag = 1;
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t stage = smem_u32(base + st * kStageBytes);
 #pragma unroll
-            for (int acc = 0; acc < kAcc; ++acc) {
-              const uint32_t d = tmem + acc * kN;
-              const uint32_t b_addr = stage + 2 * kTileA + acc * kTileB;
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t bd = smem_desc(b_addr + kk * 32);
-                const uint64_t ahi = smem_desc(stage + kk * 32);
-                const uint64_t alo = smem_desc(stage + kTileA + kk * 32);
-                const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-                    "l"(ahi), "l"(bd), "r"(kIdesc), "r"(accum));
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t bd = smem_desc(stage + 2 * kTileA + kk * 32);
+              const uint64_t ahi = smem_desc(stage + kk * 32);
+              const uint64_t alo = smem_desc(stage + kTileA + kk * 32);
+              const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                  "l"(ahi), "l"(bd), "r"(kIdesc), "r"(accum));
+              if (kHiLo)
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
                     "l"(alo), "l"(bd), "r"(kIdesc), "r"(1u));
-              }
             }
             issued = true;
             asm volatile(
@@ -222,12 +225,14 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           if (!ok) break;
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(acc_full))
+                  smem_u32(&acc_full[buf]))
               : "memory");
-          ++p;
         }
       }
-      if (*abort_flag && a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+      if (!ok) {
+        *abort_flag = 1;
+        if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+      }
       if (issued) {  // drain this thread's MMAs before tensor memory is freed
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -237,102 +242,36 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
         mbar_wait(drain, 0, &never);
       }
     }
-  } else {
-    // ------------------------------------------------------------ producers
-    const int pw = warp - 1;              // 0..7
-    const int quarter = warp & 3;         // tensor-memory lanes this warp may read
-    const int my_acc = pw / 4;            // accumulator this warp stores
-    uint32_t s = 0, p = 0;
+  } else if (warp <= kEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    // Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (trials b), all 256
+    // columns (a, beta, re|im) of the pass's accumulator, and stores Y.
+    const int quarter = warp & 3;
+    const int b = quarter * 32 + lane;
+    uint32_t p = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
-      const uint32_t ku = static_cast<uint32_t>(k);
-      for (int it = 0; it < items_per_bin && ok; ++it) {
+      const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
+      for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
         const int group = it / n_pass;
-        const int pass = it % n_pass;
-        const int j_pass = pass * kDmsPass;  // local trial offset of this pass
-        for (int t = 0; t < n_tiles; ++t, ++s) {
-          const uint32_t st = s % kStages;
-          // warp-uniform outcome, so the warp stays converged
-          if (!__all_sync(0xffffffffu, mbar_wait(&empty[st], ((s / kStages) & 1) ^ 1, abort_flag))) {
-            ok = false;
-            break;
-          }
-          unsigned char* stage = base + st * kStageBytes;
-          const int nu = t * kKC + lane;
-          const bool nu_ok = nu < a.n_chan;
-          PhaseConst pc = {0u, 0u, 0u, 0u};
-          if (nu_ok) pc = a.pc[nu];
-          // P_b = exp(2 pi i k b v): rows b = pw*16 .. pw*16+15, column pair 2*lane
-#pragma unroll 4
-          for (int i = 0; i < kM / kProdWarps; ++i) {
-            const int b = pw * (kM / kProdWarps) + i;
-            uint32_t hi_bits = 0u, lo_bits = 0u;
-            if (nu_ok) {
-              const float2 w = unit_phasor(top32_mul(ku * static_cast<uint32_t>(b), pc.v_lo, pc.v_hi));
-              const __nv_bfloat162 hi = __floats2bfloat162_rn(w.x, w.y);
-              const __nv_bfloat162 lo = __floats2bfloat162_rn(w.x - __low2float(hi),
-                                                              w.y - __high2float(hi));
-              hi_bits = bf16x2_bits(hi);
-              lo_bits = bf16x2_bits(lo);
-            }
-            const uint32_t off = sw128(b, 2 * lane);
-            *reinterpret_cast<uint32_t*>(stage + off) = hi_bits;
-            *reinterpret_cast<uint32_t*>(stage + kTileA + off) = lo_bits;
-          }
-          // Q_a for this channel and the pass's 8 a's
-          float2 q[kAPass];
-          const uint32_t base_ph = top32_mul(ku, pc.u_lo, pc.u_hi);
-#pragma unroll
-          for (int al = 0; al < kAPass; ++al) {
-            const uint32_t ja = static_cast<uint32_t>(a.j_begin + j_pass + al * kM);
-            q[al] = nu_ok ? unit_phasor(base_ph + top32_mul(ku * ja, pc.v_lo, pc.v_hi))
-                          : make_float2(0.f, 0.f);
-          }
-          // Z_a = Q_a X for beams beta = pw + 8m, real embedding into B
-#pragma unroll
-          for (int m = 0; m < kBeams / kProdWarps; ++m) {
-            const int beta = pw + kProdWarps * m;
-            const int bg = group * kBeams + beta;
-            float2 x = make_float2(0.f, 0.f);
-            if (nu_ok && bg < a.n_series)
-              x = __ldg(a.X + static_cast<int64_t>(bg) * a.x_series_stride +
-                        static_cast<int64_t>(nu) * a.x_chan_stride + k);
-#pragma unroll
-            for (int al = 0; al < kAPass; ++al) {
-              const float zr = x.x * q[al].x - x.y * q[al].y;
-              const float zi = x.x * q[al].y + x.y * q[al].x;
-              const int acc = al / kNA;
-              const int row = ((al % kNA) * kBeams + beta) * 2;
-              unsigned char* tb = stage + 2 * kTileA + acc * kTileB;
-              *reinterpret_cast<uint32_t*>(tb + sw128(row, 2 * lane)) =
-                  bf16x2_bits(__floats2bfloat162_rn(zr, -zi));
-              *reinterpret_cast<uint32_t*>(tb + sw128(row + 1, 2 * lane)) =
-                  bf16x2_bits(__floats2bfloat162_rn(zi, zr));
-            }
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(&full[st]);
-        }
-        if (!ok) break;
-        // epilogue: accumulator my_acc, tensor-memory lanes of this quarter
-        if (!__all_sync(0xffffffffu, mbar_wait(acc_full, p & 1, abort_flag))) {
+        const int j_pass = (it % n_pass) * kDmsPass;
+        const uint32_t buf = p % kAccBufs;
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (p / kAccBufs) & 1, abort_flag))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int b = quarter * 32 + lane;
-        const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
 #pragma unroll 1
         for (int c0 = 0; c0 < kN; c0 += 32) {
           uint32_t r[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + my_acc * kN + c0, r);
+          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * kN + c0, r);
 #pragma unroll
           for (int h = 0; h < 16; ++h) {
-            const int n = c0 + 2 * h;            // (a_in, beta, re) column
+            const int n = c0 + 2 * h;  // (a_in, beta, re) column
             const int a_in = n / (2 * kBeams);
             const int beta = (n % (2 * kBeams)) / 2;
             const int bg = group * kBeams + beta;
-            const int jl = j_pass + (my_acc * kNA + a_in) * kM + b;
+            const int jl = j_pass + a_in * kM + b;
             if (bg < a.n_series && jl < a.n_dm) {
               const float re = __uint_as_float(r[2 * h]) * a.scale;
               const float im = real_only ? 0.f : __uint_as_float(r[2 * h + 1]) * a.scale;
@@ -346,8 +285,130 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(acc_empty);
-        ++p;
+        mbar_arrive(&acc_empty[buf]);
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+    }
+  } else {
+    // ------------------------------------------------------------ producers
+    // Producer warp pw (0..15) evaluates, for channel nu = tile*32 + lane:
+    //   P_b for the 8 rows b = 8 pw .. 8 pw + 7 (one direct phasor, then the
+    //   recurrence P_{b+1} = P_b R with R = exp(2 pi i k v), at most 7 steps),
+    //   Q_a for the pass's 4 a's (Q_0 direct, Q_{a+1} = Q_a R^128),
+    //   Z_a = Q_a X for the beams beta = pw and pw + 16.
+    // X and the phase constants of the next tile are loaded one stage ahead.
+    const int pw = warp - 1 - kEpiWarps;           // 0..15
+    constexpr int kRows = kM / kProdWarps;         // P rows per warp (8)
+    constexpr int kBeamsPerWarp = kBeams / kProdWarps;  // 2
+    // Store offsets that do not change between stages (see sw128): the P
+    // rows of this warp, and the Z rows (al*32 + pw + 16m)*2 + e, whose
+    // position within an 8-row group depends only on pw and e.
+    const uint32_t lane_chunk = static_cast<uint32_t>((lane >> 2) << 4);
+    const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
+    uint32_t z_base[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int r = 2 * pw + e;  // row within the first 32-row block, < 32
+      z_base[e] = static_cast<uint32_t>((r >> 3) * 1024 + (r & 7) * 128 +
+                                        ((((lane >> 2) ^ (r & 7))) << 4) + (lane & 3) * 4);
+    }
+    uint32_t s = 0;
+    bool ok = true;
+    for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
+      const uint32_t ku = static_cast<uint32_t>(k);
+      for (int it = 0; it < items_per_bin && ok; ++it) {
+        const int group = it / n_pass;
+        const int j_pass = (it % n_pass) * kDmsPass;
+        PhaseConst pc_next = {0u, 0u, 0u, 0u};
+        float2 x_next[kBeamsPerWarp];
+        {
+          const int nu = lane;
+          if (nu < a.n_chan) pc_next = a.pc[nu];
+#pragma unroll
+          for (int m = 0; m < kBeamsPerWarp; ++m) {
+            const int bg = group * kBeams + pw + kProdWarps * m;
+            x_next[m] = (nu < a.n_chan && bg < a.n_series)
+                            ? __ldg(a.X + static_cast<int64_t>(bg) * a.x_series_stride +
+                                    static_cast<int64_t>(nu) * a.x_chan_stride + k)
+                            : make_float2(0.f, 0.f);
+          }
+        }
+        for (int t = 0; t < n_tiles; ++t, ++s) {
+          const int nu = t * kKC + lane;
+          const bool nu_ok = nu < a.n_chan;
+          const PhaseConst pc = pc_next;
+          float2 x[kBeamsPerWarp];
+#pragma unroll
+          for (int m = 0; m < kBeamsPerWarp; ++m) x[m] = x_next[m];
+          if (t + 1 < n_tiles) {  // prefetch the next tile
+            const int nn = nu + kKC;
+            pc_next = nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int m = 0; m < kBeamsPerWarp; ++m) {
+              const int bg = group * kBeams + pw + kProdWarps * m;
+              x_next[m] = (nn < a.n_chan && bg < a.n_series)
+                              ? __ldg(a.X + static_cast<int64_t>(bg) * a.x_series_stride +
+                                      static_cast<int64_t>(nn) * a.x_chan_stride + k)
+                              : make_float2(0.f, 0.f);
+            }
+          }
+          // phasors in registers before touching the stage
+          float2 r1 = make_float2(0.f, 0.f), pb = r1, qa = r1, r128 = r1;
+          if (nu_ok) {
+            r1 = unit_phasor(top32_mul(ku, pc.v_lo, pc.v_hi));
+            pb = unit_phasor(top32_mul(ku * static_cast<uint32_t>(pw * kRows), pc.v_lo, pc.v_hi));
+            r128 = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kM), pc.v_lo, pc.v_hi));
+            const uint32_t ja = static_cast<uint32_t>(a.j_begin + j_pass);
+            qa = unit_phasor(top32_mul(ku, pc.u_lo, pc.u_hi) + top32_mul(ku * ja, pc.v_lo, pc.v_hi));
+          }
+          const uint32_t st = s % kStages;
+          if (!__all_sync(0xffffffffu, mbar_wait(&empty[st], ((s / kStages) & 1) ^ 1, abort_flag))) {
+            ok = false;
+            break;
+          }
+          unsigned char* stage = base + st * kStageBytes;
+          // P rows b = 8 pw + i fill one 8-row swizzle group: the 16-byte chunk
+          // of column pair 2*lane is (lane/4) ^ i, the rest is a constant.
+#pragma unroll
+          for (int i = 0; i < kRows; ++i) {
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(pb.x, pb.y);
+            const uint32_t hb = bf16x2_bits(hi);
+            // residual P - hi (the hi halves widened back to FP32)
+            const float2 res = __ffma2_rn(make_float2(__uint_as_float(hb << 16),
+                                                      __uint_as_float(hb & 0xFFFF0000u)),
+                                          make_float2(-1.f, -1.f), pb);
+            const uint32_t off = p_base + i * 128 + ((lane_chunk ^ (i << 4)));
+            *reinterpret_cast<uint32_t*>(stage + off) = hb;
+            if (kHiLo)
+              *reinterpret_cast<uint32_t*>(stage + kTileA + off) =
+                  bf16x2_bits(__floats2bfloat162_rn(res.x, res.y));
+            // P <- P R as a paired multiply-add: (pr, pi) r1r + (-pi, pr) r1i
+            pb = __ffma2_rn(make_float2(-pb.y, pb.x), make_float2(r1.y, r1.y),
+                            __fmul2_rn(pb, make_float2(r1.x, r1.x)));
+          }
+          unsigned char* tb = stage + 2 * kTileA;
+#pragma unroll
+          for (int al = 0; al < kNA; ++al) {
+#pragma unroll
+            for (int m = 0; m < kBeamsPerWarp; ++m) {
+              // Z = X Q as (xr, xr)(qr, qi) + (-xi, xi)(qi, qr)
+              const float2 z = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qa.y, qa.x),
+                                          __fmul2_rn(make_float2(x[m].x, x[m].x), qa));
+              const uint32_t zb = bf16x2_bits(__floats2bfloat162_rn(z.x, z.y));
+              // rows (al*32 + beta)*2 + {0, 1}: per-thread base + a constant
+              const uint32_t row_off = static_cast<uint32_t>((8 * al + 4 * m) * 1024);
+              *reinterpret_cast<uint32_t*>(tb + z_base[0] + row_off) = zb ^ 0x80000000u;  // (zr, -zi)
+              *reinterpret_cast<uint32_t*>(tb + z_base[1] + row_off) = __byte_perm(zb, 0, 0x1032);  // (zi, zr)
+            }
+            qa = __ffma2_rn(make_float2(-qa.y, qa.x), make_float2(r128.y, r128.y),
+                            __fmul2_rn(qa, make_float2(r128.x, r128.x)));
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(&full[st]);
+        }
       }
     }
     if (!ok) {
@@ -372,16 +433,22 @@ size_t mac_tc_smem_bytes() { return kStages * kStageBytes + 1024 + 128; }
 int mac_tc_trials_per_pass() { return kDmsPass; }
 
 cudaError_t mac_tc_prepare() {
-  return cudaFuncSetAttribute(mac_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(mac_tc_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(mac_tc_smem_bytes()));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mac_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(mac_tc_smem_bytes()));
 }
 
-cudaError_t launch_mac_tc(const MacArgs& a, int n_sms, cudaStream_t s) {
+cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   const int grid = a.n_bins < n_sms ? a.n_bins : n_sms;
   MacArgs args = a;
   void* params[] = {&args};
-  return cudaLaunchKernel(reinterpret_cast<const void*>(&mac_tc_kernel), dim3(grid),
+  const void* fn = hi_lo ? reinterpret_cast<const void*>(&mac_tc_kernel<true>)
+                        : reinterpret_cast<const void*>(&mac_tc_kernel<false>);
+  return cudaLaunchKernel(fn, dim3(grid),
                           dim3(kThreads), params, mac_tc_smem_bytes(), s);
 }
 

@@ -98,6 +98,7 @@ def test_geometry_survey_values():
     (dict(in_dtype=7), fdd.FDD_ERR_INVALID_ARG),
     (dict(output=9), fdd.FDD_ERR_INVALID_ARG),
     (dict(precision=5), fdd.FDD_ERR_INVALID_ARG),
+    (dict(precision=-1), fdd.FDD_ERR_INVALID_ARG),
     (dict(dm_list=np.array([0.0, 1.0, 3.0])), fdd.FDD_ERR_UNSUPPORTED),
     (dict(dm_list=np.array([-1.0, 0.0])), fdd.FDD_ERR_INVALID_ARG),
     (dict(dm_list=np.array([0.0, np.nan])), fdd.FDD_ERR_INVALID_ARG),

@@ -38,12 +38,14 @@ def _workload(n_chan, n_t, dms, n_beams, band=(1200.0, 1500.0), t_samp=2e-3, chu
                           pulses_per_beam=1)
 
 
+@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16],
+                         ids=["bf16_hilo", "bf16"])
 @pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
     (5, 40, 256, 0.0, 0.5, 1100),    # partial beam group, ragged channel tile, 2 passes
     (32, 64, 128, 3.0, 1.0, 1024),   # one full group, exactly one pass
     (37, 33, 512, 0.0, 0.25, 300),   # two groups, one partial pass
 ])
-def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm):
+def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm, precision):
     dms = dm0 + ddm * np.arange(n_dm)
     w = _workload(n_chan, L, dms, n_series)
     K = L // 2 + 1
@@ -51,8 +53,7 @@ def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm):
     X = (rng.standard_normal((n_series, n_chan, K)) +
          1j * rng.standard_normal((n_series, n_chan, K))).astype(np.complex64).astype(np.complex128)
     xp, yp = K + 5, K + 2
-    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA,
-                               precision=fdd.FDD_PREC_BF16_HILO)) as plan:
+    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA, precision=precision)) as plan:
         assert plan.info["mac_variant"] == fdd.FDD_MAC_TC
         dX = complex_to_device(X, xp)
         dY = torch.zeros((n_series, n_dm, yp, 2), dtype=torch.float32, device="cuda")
@@ -70,7 +71,8 @@ def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm):
         ref = oracle.fdd_bins(X[s], np.arange(K), L, d)
         errs.append(rel_l2(Y[s], ref))
         assert rel_l2(P[s], np.abs(ref) ** 2) <= 2 * TC_REL_L2
-    print(f"tensor-core rel-L2 vs FP64: max over series {max(errs):.2e}")
+    print(f"tensor-core ({'hi+lo' if precision == fdd.FDD_PREC_BF16_HILO else 'bf16'}) "
+          f"rel-L2 vs FP64: max over series {max(errs):.2e}")
     assert max(errs) <= TC_REL_L2
 
 
