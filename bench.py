@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tc", action="store_true",
+                    help="skip the tensor-core form's timing on the 32-beam workload")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU-baseline sample")
     ap.add_argument("--n-t", type=int, default=0,
@@ -210,23 +212,80 @@ def oracle_rate(d, geo, X, n_bins: int, rng: np.random.Generator):
     extra = rng.choice(np.arange(2, geo.K - 1), size=max(0, n_bins - 3), replace=False)
     bins = np.unique(np.concatenate([fixed, extra]).astype(np.int64))
     t0 = time.perf_counter()
-    oracle.fdd_bins(X[:, bins], bins, geo.L, d)
+    Y = oracle.fdd_bins(X[:, bins], bins, geo.L, d)
     dt = time.perf_counter() - t0
+    oracle_rate.last = (bins, Y)
     return d.shape[0] * d.shape[1] * bins.size, dt
 
 
-def cpu_baseline(w: synth.Workload, seed: int, target_s: float) -> dict:
+def _gpu_sampled(plan, X, bins, n_dm, pitch):
+    """The CUDA path's spectra of the given bins, from complex spectra X [series][chan][K]."""
+    import torch
+    ns, nc, K = X.shape
+    host = np.zeros((ns, nc, pitch, 2), dtype=np.float32)
+    host[..., :K, 0] = X.real
+    host[..., :K, 1] = X.imag
+    dX = torch.from_numpy(host).cuda()
+    dY = torch.empty((ns, n_dm, K, 2), device="cuda")
+    plan.dedisperse_spectra(dX, pitch, ns, 0, n_dm, dY, K)
+    out = dY.index_select(2, torch.from_numpy(bins).cuda()).cpu().numpy().astype(np.float64)
+    del dX, dY
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def _rel(a, b) -> float:
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def cpu_baseline(w: synth.Workload, seed: int, target_s: float, plan=None) -> dict:
+    """Time the oracle on sampled bins; when a plan is given, also report the CUDA
+    path's relative L2 error on those bins (same FP64-derived spectra in)."""
     import oracle
     d, geo, X = oracle_sample_setup(w, seed)
     rng = np.random.default_rng(seed)
     macs, dt = oracle_rate(d, geo, X, 16, rng)
     nb = int(min(geo.K, max(16, 16 * target_s / max(dt, 1e-3))))
     macs, dt = oracle_rate(d, geo, X, nb, rng)
-    return {"value": macs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle phase-rotate-and-sum of {nb} sampled bins (incl. DC, 1, "
-                      f"Nyquist) x {w.n_dm} DMs x {w.n_chan} channels of chunk 0 "
-                      f"({macs:.3g} MACs in {dt:.1f} s; oracle FFT of the chunk untimed)",
-            "seconds": dt}
+    out = {"value": macs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle phase-rotate-and-sum of {nb} sampled bins (incl. DC, 1, "
+                     f"Nyquist) x {w.n_dm} DMs x {w.n_chan} channels of chunk 0 "
+                     f"({macs:.3g} MACs in {dt:.1f} s; oracle FFT of the chunk untimed)",
+           "seconds": dt}
+    if plan is not None:
+        bins, Y = oracle_rate.last
+        G = _gpu_sampled(plan, X[None].astype(np.complex64), bins, w.n_dm,
+                         plan.info["bin_pitch"])[0]
+        out["gpu_rel_l2_vs_oracle"] = _rel(G, Y)
+        out["gpu_rel_l2_vs_oracle_no_dc"] = _rel(G[:, bins > 0], Y[:, bins > 0])
+    return out
+
+
+TC_WORKLOAD = "fdd_32beam_1024ch_2p19t_4096dm"
+TC_N_T = 4096  # 2049 bins: a bounded slice of the 32-beam workload
+
+
+def tc_accuracy(seed: int) -> dict:
+    """Relative L2 error of both tensor-core precisions vs the FP64 oracle on 8
+    sampled bins of 2 beams (all 4096 trials, 1024 channels)."""
+    import oracle
+    import paper_2110_03482_gb300 as fdd
+    w = synth.WORKLOADS[TC_WORKLOAD].scaled(n_t=TC_N_T)
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    geo = oracle.geometry(w.n_t, w.chunk_len, d)
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((2, w.n_chan, geo.K)) +
+         1j * rng.standard_normal((2, w.n_chan, geo.K))).astype(np.complex64)
+    bins = np.unique(np.concatenate([[0, 1, geo.K - 1], rng.integers(2, geo.K - 1, 5)]))
+    refs = np.stack([oracle.fdd_bins(X[b][:, bins].astype(np.complex128), bins, geo.L, d)
+                     for b in range(2)])
+    res = {}
+    for name, prec in (("bf16_hilo", fdd.FDD_PREC_BF16_HILO), ("bf16", fdd.FDD_PREC_BF16)):
+        with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA, n_beams=2,
+                             precision=prec)) as plan:
+            G = _gpu_sampled(plan, X, bins, w.n_dm, plan.info["bin_pitch"])
+        res[name] = _rel(G, refs)
+    return {"rel_l2_vs_oracle": res,
+            "sample": f"8 bins x {w.n_dm} DMs x {w.n_chan} channels x 2 beams"}
 
 
 def run_reference(args, rank: int, world: int) -> None:
@@ -261,6 +320,50 @@ def run_reference(args, rank: int, world: int) -> None:
 
 
 # ------------------------------------------------------------------ GPU leg
+def measure_tc(args, fdd, torch, value_per_mac_kernel: float) -> dict:
+    """Kernel-only timing of the tensor-core form (both precisions) on a bounded
+    slice of the 32-beam workload: 32 beams x 1024 channels x 2049 bins x 4096
+    trials per launch (random spectra; every output written)."""
+    w = synth.WORKLOADS[TC_WORKLOAD].scaled(n_t=TC_N_T)
+    peaks = load_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops") or 1895.5)
+    res = {"workload": f"{TC_WORKLOAD} slice: {w.n_beams} beams x {w.n_chan} channels x "
+                       f"{TC_N_T // 2 + 1} bins x {w.n_dm} trials",
+           "unit": UNIT}
+    X = Y = None
+    for name, prec, passes in (("bf16_hilo", fdd.FDD_PREC_BF16_HILO, 2),
+                               ("bf16", fdd.FDD_PREC_BF16, 1)):
+        with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA,
+                             n_beams=w.n_beams, precision=prec)) as plan:
+            g = plan.info
+            if X is None:
+                gen = torch.Generator(device="cuda").manual_seed(args.seed)
+                X = torch.randn((w.n_beams, w.n_chan, g["bin_pitch"], 2), device="cuda",
+                                generator=gen)
+                Y = torch.empty((w.n_beams, w.n_dm, g["n_bins"], 2), device="cuda")
+            call = lambda: plan.dedisperse_spectra(X, g["bin_pitch"], w.n_beams, 0, w.n_dm, Y,
+                                                   g["n_bins"])
+            call()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            plan.query()
+            ms = e0.elapsed_time(e1) / 3
+        macs = w.n_beams * w.n_dm * w.n_chan * g["n_bins"]
+        tf = FLOPS_PER_MAC * macs / (ms / 1e3) / 1e12
+        res[name] = {"value": macs / (ms / 1e3), "ms_per_launch": ms, "tflops_algorithmic": tf,
+                     "tflops_tensor_physical": passes * tf,
+                     "frac_bf16_peak_physical": passes * tf / bf16_peak,
+                     "speedup_vs_fp32_kernel": tf / value_per_mac_kernel}
+    del X, Y
+    return res
+
+
 def run_fdd(args, rank: int, world: int, dist) -> None:
     import torch
 
@@ -367,9 +470,12 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
                "ms_per_step": e_ms / args.e2e_steps}
         del h_in, h_out
 
+    tc = None if args.no_tc else measure_tc(args, fdd, torch, value_per_mac_kernel=achieved)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.seed, args.cpu_seconds)
+        cpu = cpu_baseline(w, args.seed, args.cpu_seconds, plan)
+        if tc is not None:
+            tc.update(tc_accuracy(args.seed))
     plan.close()
 
     if rank == 0:
@@ -380,6 +486,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
                 "config": dict(workload_config(w, info), parallelism=f"beam-replicas x{world}"),
                 "gpu_launches": own_launches,
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "tc": tc,
                 "stage_ms_share": stage_share,
                 "fp32_frac_whole_step": value * FLOPS_PER_MAC / 1e12 / (peak * world),
                 "macs_per_step": macs_step * world}
