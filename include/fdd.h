@@ -270,6 +270,83 @@ fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on);
  * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA. */
 fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out);
 
+/* ------------------------------------------------------------------------
+ * Batching form: many beams of uneven length and uneven trial grids (the
+ * batch dimensions of Sect. 3 / Algorithm 1, and the autotuning suggested in
+ * Sect. 5).  Every beam shares the channel set, sampling time, k_DM, nu_ref,
+ * input type and layout of the common parameters; each has its own series
+ * length and uniform trial grid.  Each beam's series is transformed whole
+ * (L = next power of two >= n_t, as chunk_len 0), and the batch emits
+ * spectra or |Y|^2 (output FDD_OUT_SPECTRA or FDD_OUT_POWER, FP32 form).
+ * ---------------------------------------------------------------------- */
+typedef struct fdd_beam_desc {
+  int64_t n_t;      /* samples of this beam, >= 2                          */
+  double dm0;       /* first trial DM (pc cm^-3), >= 0                     */
+  double ddm;       /* trial step, >= 0                                    */
+  int32_t n_dm;     /* trials, >= 1                                        */
+  int32_t reserved; /* must be 0                                           */
+} fdd_beam_desc;
+
+typedef struct fdd_batch_s* fdd_batch_t;
+
+typedef struct fdd_batch_info {
+  int64_t in_elems;        /* elements of the concatenated input                 */
+  int64_t out_elems;       /* elements of the concatenated output                */
+  int64_t out_bytes;
+  int64_t workspace_bytes; /* device bytes held by the batch plan                */
+  int64_t work_items;      /* (beam, bin tile, trial block) items per execute    */
+  int32_t n_waves;         /* persistent launches per execute                    */
+  int32_t mac_variant;     /* kernel tile in use (FDD_MAC_*)                     */
+  int32_t ctas;            /* CTAs of each persistent launch                     */
+  int32_t reserved;
+  double autotune_ms[FDD_MAC_VARIANTS]; /* timed candidates (ms), -1 if untimed */
+} fdd_batch_info;
+
+/*
+ * Plan a batch.  *p supplies the common fields (n_chan, nu_lo_mhz, dnu_mhz,
+ * t_samp_s, k_dm, nu_ref_mhz, in_dtype, in_layout, output, precision,
+ * workspace_limit, mac_variant); its n_t, dm_list, n_dm, n_beams are not
+ * read and chunk_len must be 0.  beams[0 .. n_beams-1] describe the beams.
+ * Beams are grouped in order into waves whose spectra (n_chan x (L/2+1 rounded
+ * up to 64) complex each) fit in workspace_limit (default 16 GiB) minus the
+ * fixed part (n_chan x max L floats of staging, the phase tables and a
+ * 64 MiB reserve for the FFT work area);
+ * each wave is one persistent launch of the phase-rotate-and-sum whose CTAs
+ * take (beam, bin tile, trial block) work items from a counter.  With
+ * mac_variant 0 and autotune != 0 the candidate kernel tiles are timed on the
+ * batch's own shapes and the fastest is kept (remembered per shape in the
+ * process, and in the text file named by the FDD_AUTOTUNE_CACHE environment
+ * variable when set); mac_variant 0 without autotune selects Q12_8X8.
+ * Allocates all device memory (and, while autotuning, a temporary output).
+ * Layouts: the input is the beams' inputs concatenated in order (each
+ * [n_t][n_chan] or [n_chan][n_t]); the output is, per beam in order,
+ * [n_dm][L/2+1] complex (spectra) or float (power); fdd_batch_query gives the
+ * offsets.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_UNSUPPORTED (time output,
+ * chunking, non-FP32 precision, a tile without batched form), FDD_ERR_ALLOC,
+ * FDD_ERR_CUDA, FDD_ERR_CUFFT.
+ */
+fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32_t n_beams,
+                          int32_t autotune, fdd_batch_t* out);
+
+/* Sizes, waves, chosen tile and autotune timings; in_offsets / out_offsets
+ * (arrays of n_beams, or NULL) receive each beam's element offset in the
+ * concatenated input / output. */
+fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offsets,
+                           int64_t* out_offsets);
+
+/*
+ * Execute the batch: unpack and transform every beam (Eq. 3), then the
+ * phase-rotate-and-sum (Eqs. 4, 7) of each wave in one persistent launch.
+ * The sequence is captured once as a CUDA graph for a given (d_in, d_out)
+ * pair and replayed on the stream by later calls with the same buffers; a
+ * call with other buffers re-captures (synchronising the stream first).
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA, FDD_ERR_CUFFT.
+ */
+fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_stream_t stream);
+
+/* Release the batch plan (synchronises the device first).  NULL is ignored. */
+fdd_status fdd_batch_destroy(fdd_batch_t b);
+
 /* Largest channel count accepted by fdd_dedisperse_spectra_static. */
 #define FDD_STATIC_MAX_CHAN 8192
 

@@ -53,7 +53,8 @@ EXPORTS = [
     "fdd_abi_version", "fdd_status_string", "fdd_last_error", "fdd_params_init",
     "fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute", "fdd_execute_dm_range",
     "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
-    "fdd_destroy", "fdd_dedisperse_spectra_static",
+    "fdd_destroy", "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
+    "fdd_batch_execute", "fdd_batch_destroy",
 ]
 FDD_STATIC_MAX_CHAN = 8192
 
@@ -127,6 +128,37 @@ class fdd_profile(ctypes.Structure):
                 "dropped": int(self.dropped)}
 
 
+class fdd_beam_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_t", ctypes.c_int64),
+        ("dm0", ctypes.c_double),
+        ("ddm", ctypes.c_double),
+        ("n_dm", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class fdd_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("in_elems", ctypes.c_int64),
+        ("out_elems", ctypes.c_int64),
+        ("out_bytes", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64),
+        ("work_items", ctypes.c_int64),
+        ("n_waves", ctypes.c_int32),
+        ("mac_variant", ctypes.c_int32),
+        ("ctas", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("autotune_ms", ctypes.c_double * 13),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "autotune_ms"}
+        d["autotune_ms"] = {MAC_VARIANT_NAMES[i]: self.autotune_ms[i]
+                            for i in range(len(MAC_VARIANT_NAMES)) if self.autotune_ms[i] >= 0}
+        return d
+
+
 class FddError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -170,12 +202,19 @@ def lib() -> ctypes.CDLL:
         L.fdd_destroy.argtypes = [vp]
         L.fdd_dedisperse_spectra_static.argtypes = [ctypes.POINTER(fdd_params), vp, i64, i32,
                                                      i32, i32, vp, i64, i32, vp]
+        L.fdd_batch_plan.argtypes = [ctypes.POINTER(fdd_params), ctypes.POINTER(fdd_beam_desc),
+                                     i32, i32, ctypes.POINTER(vp)]
+        L.fdd_batch_query.argtypes = [vp, ctypes.POINTER(fdd_batch_info),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.fdd_batch_execute.argtypes = [vp, vp, vp, vp]
+        L.fdd_batch_destroy.argtypes = [vp]
         L.fdd_profile_enable.argtypes = [vp, i32]
         L.fdd_profile_read.argtypes = [vp, ctypes.POINTER(fdd_profile)]
         for name in ["fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute",
                      "fdd_execute_dm_range", "fdd_execute_host", "fdd_dedisperse_spectra",
                      "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
-                     "fdd_dedisperse_spectra_static"]:
+                     "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
+                     "fdd_batch_execute", "fdd_batch_destroy"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -287,6 +326,64 @@ def fdd_dedisperse_spectra_static(params: Params, d_X, x_pitch: int, n_series: i
     _check(lib().fdd_dedisperse_spectra_static(ctypes.byref(params.c), _ptr(d_X), x_pitch,
                                                n_series, dm_first, n_dm, _ptr(d_Y), y_pitch,
                                                out_kind, _stream(stream)))
+
+
+def fdd_batch_plan(params: Params, beams, autotune: bool = True) -> int:
+    """beams: sequence of (n_t, dm0, ddm, n_dm)."""
+    arr = (fdd_beam_desc * len(beams))()
+    for i, (n_t, dm0, ddm, n_dm) in enumerate(beams):
+        arr[i] = fdd_beam_desc(int(n_t), float(dm0), float(ddm), int(n_dm), 0)
+    h = ctypes.c_void_p()
+    _check(lib().fdd_batch_plan(ctypes.byref(params.c), arr, len(beams), 1 if autotune else 0,
+                                ctypes.byref(h)))
+    return h.value
+
+
+def fdd_batch_query(batch: int, n_beams: int):
+    info = fdd_batch_info()
+    ino = (ctypes.c_int64 * n_beams)()
+    outo = (ctypes.c_int64 * n_beams)()
+    _check(lib().fdd_batch_query(batch, ctypes.byref(info), ino, outo))
+    return info.as_dict(), list(ino), list(outo)
+
+
+def fdd_batch_execute(batch: int, d_in, d_out, stream=None) -> None:
+    _check(lib().fdd_batch_execute(batch, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+
+def fdd_batch_destroy(batch: int) -> None:
+    _check(lib().fdd_batch_destroy(batch))
+
+
+class Batch:
+    """RAII wrapper of a batch plan: Batch(beams, **common params)."""
+
+    def __init__(self, beams, autotune: bool = True, **kw):
+        kw.setdefault("dm_list", [0.0])
+        self.params = Params(**kw)
+        self.n_beams = len(beams)
+        self.handle = fdd_batch_plan(self.params, beams, autotune)
+        self.info, self.in_offsets, self.out_offsets = fdd_batch_query(self.handle, self.n_beams)
+
+    def execute(self, d_in, d_out, stream=None):
+        fdd_batch_execute(self.handle, d_in, d_out, stream)
+
+    def close(self):
+        if self.handle:
+            fdd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fdd_profile_enable(plan: int, on: bool = True) -> None:

@@ -55,7 +55,23 @@ enum MacVariant {
   MAC_S12_8x8 = FDD_MAC_S12_8X8,
   MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
 };
+// One set of spectra in a batch (the batching form): its launch arguments
+// (n_series 1) and its place in the batch's work-item numbering.
+struct BatchSet {
+  MacArgs args;
+  long long item_begin;  // first work item of this set
+  int n_dm_blocks;       // trial blocks (items per bin tile)
+  int n_bin_tiles;
+};
+
 int mac_variant_for(int n_dm);
+int mac_variant_bins_per_cta(int variant);
+bool mac_variant_batchable(int variant);
+// CTAs of the persistent batch kernel per SM (occupancy), 0 if unsupported.
+int mac_batch_ctas_per_sm(int variant, int n_chan);
+cudaError_t launch_mac_batch(const BatchSet* d_sets, int n_sets, long long n_items,
+                             unsigned long long* d_counter, int variant, int n_ctas,
+                             int n_chan, cudaStream_t s);
 int mac_variant_trials_per_block(int variant);
 cudaError_t mac_prepare(int variant, int n_chan);  // kernel attributes (host, once)
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s);

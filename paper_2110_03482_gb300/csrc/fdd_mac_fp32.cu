@@ -385,26 +385,23 @@ struct Generator {
   }
 };
 
-template <class Gm, class M, bool kPipe, int W = kWarps>
-__global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
-  float* swap_all = reinterpret_cast<float*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
-
-  for (int i = threadIdx.x; i < a.n_chan; i += W * 32) pcs[i] = a.pc[i];
-  __syncthreads();
-
+// One CTA's block of work: bins (bin_tile * W + warp) * NG + g and trials
+// dm_block * DMS + .. of one set of spectra, with the phase table already in
+// shared memory (pcs) and the swap area behind it.
+template <class Gm, class M, bool kPipe, int W>
+__device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pcs,
+                                          float* swap_all, int bin_tile, int dm_block,
+                                          int series) {
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int g = lane / Gm::G;
   const int lg = lane % Gm::G;
   const int ga = lg / Gm::GB;
   const int gb = lg % Gm::GB;
-  const int k = (blockIdx.x * W + warp) * Gm::NG + g;
+  const int k = (bin_tile * W + warp) * Gm::NG + g;
   const bool k_ok = k < a.n_bins;
   const uint32_t ku = k_ok ? static_cast<uint32_t>(k) : 0u;  // idle groups run bin 0, store nothing
-  const int jblk = blockIdx.y * Gm::DMS;
-  const int series = blockIdx.z;
+  const int jblk = dm_block * Gm::DMS;
   const int nc = a.n_chan;
 
   constexpr int kStage = Gm::NG * M::GFL;  // floats per warp per stage
@@ -486,6 +483,54 @@ __global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
           static_cast<float2*>(a.Y)[o] = make_float2(re, im);
       }
     }
+  }
+}
+
+template <class Gm, class M, bool kPipe, int W = kWarps>
+__global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
+  float* swap_all = reinterpret_cast<float*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
+  for (int i = threadIdx.x; i < a.n_chan; i += W * 32) pcs[i] = a.pc[i];
+  __syncthreads();
+  mac_block<Gm, M, kPipe, W>(a, pcs, swap_all, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Persistent form over a batch of spectra sets of uneven sizes (the batching
+// form): CTAs pull work items (set, bin tile, trial block) from a global
+// counter; a set's phase table is loaded into shared memory when the set
+// changes.  Items of a set are numbered bin-tile-major from item_begin.
+template <class Gm, class M, bool kPipe, int W = kWarps>
+__global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* sets, int n_sets,
+                                                              int64_t n_items,
+                                                              unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long item_s;
+  const int n_chan = sets[0].args.n_chan;  // common to the batch
+  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
+  float* swap_all = reinterpret_cast<float*>(smem_raw + sizeof(PhaseConst) * n_chan);
+  int cur = -1;
+  while (true) {
+    if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(counter, 1ull));
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= n_items) break;
+    int lo = 0, hi = n_sets - 1;  // last set with item_begin <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sets[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    const BatchSet& bs = sets[lo];
+    if (lo != cur) {
+      for (int i = threadIdx.x; i < n_chan; i += W * 32) pcs[i] = bs.args.pc[i];
+      __syncthreads();
+      cur = lo;
+    }
+    const long long local = item - bs.item_begin;
+    mac_block<Gm, M, kPipe, W>(bs.args, pcs, swap_all, static_cast<int>(local / bs.n_dm_blocks),
+                               static_cast<int>(local % bs.n_dm_blocks), 0);
+    __syncthreads();
   }
 }
 
@@ -670,6 +715,7 @@ struct VariantInfo {
   int ng;
   size_t swap_bytes;  // per CTA, excluding the phase-constant table
   int warps = kWarps;
+  const void* batch_fn = nullptr;  // persistent batch kernel of the same tile
 };
 
 VariantInfo info_legacy() {
@@ -680,7 +726,8 @@ VariantInfo info_legacy() {
 template <class Gm, class M, bool kPipe, int W = kWarps>
 VariantInfo info() {
   return {reinterpret_cast<const void*>(&mac_kernel<Gm, M, kPipe, W>), Gm::DMS, Gm::NG,
-          sizeof(float) * static_cast<size_t>(W) * 2 * Gm::NG * M::GFL, W};
+          sizeof(float) * static_cast<size_t>(W) * 2 * Gm::NG * M::GFL, W,
+          reinterpret_cast<const void*>(&mac_batch_kernel<Gm, M, kPipe, W>)};
 }
 
 VariantInfo variant_info(int v) {
@@ -721,8 +768,41 @@ size_t mac_smem_bytes(int variant, int n_chan) {
 
 cudaError_t mac_prepare(int variant, int n_chan) {
   const VariantInfo vi = variant_info(variant);
-  return cudaFuncSetAttribute(vi.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(mac_smem_bytes(variant, n_chan)));
+  const int bytes = static_cast<int>(mac_smem_bytes(variant, n_chan));
+  cudaError_t e = cudaFuncSetAttribute(vi.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess || !vi.batch_fn) return e;
+  return cudaFuncSetAttribute(vi.batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int mac_variant_bins_per_cta(int variant) {
+  const VariantInfo vi = variant_info(variant);
+  return vi.warps * vi.ng;
+}
+
+bool mac_variant_batchable(int variant) { return variant_info(variant).batch_fn != nullptr; }
+
+int mac_batch_ctas_per_sm(int variant, int n_chan) {
+  const VariantInfo vi = variant_info(variant);
+  if (!vi.batch_fn) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vi.batch_fn, vi.warps * 32,
+                                                    mac_smem_bytes(variant, n_chan)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_mac_batch(const BatchSet* d_sets, int n_sets, long long n_items,
+                             unsigned long long* d_counter, int variant, int n_ctas, int n_chan,
+                             cudaStream_t s) {
+  const VariantInfo vi = variant_info(variant);
+  if (!vi.batch_fn) return cudaErrorInvalidValue;
+  if (n_items <= 0) return cudaSuccess;
+  void* params[] = {&d_sets, &n_sets, &n_items, &d_counter};
+  return cudaLaunchKernel(vi.batch_fn, dim3(n_ctas), dim3(vi.warps * 32), params,
+                          mac_smem_bytes(variant, n_chan), s);
 }
 
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s) {

@@ -310,11 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
     uint32_t z_base[2];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int r = 2 * pw + e;  // row within the first 32-row block, < 32
-      z_base[e] = static_cast<uint32_t>((r >> 3) * 1024 + (r & 7) * 128 +
-                                        ((((lane >> 2) ^ (r & 7))) << 4) + (lane & 3) * 4);
-    }
+    for (int e = 0; e < 2; ++e) z_base[e] = sw128(2 * pw + e, 2 * lane);  // rows < 32
     uint32_t s = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {

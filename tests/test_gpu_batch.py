@@ -1,0 +1,137 @@
+"""The batching form (uneven beams and trial grids, persistent launch per wave,
+CUDA graph, autotuner) against the FP64 oracle (GB300 only)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2110_03482_gb300 as fdd
+import synth
+from gpu_util import FP32_REL_L2, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N_CHAN = 48
+BAND = (1200.0, 1500.0)
+T_SAMP = 1e-3
+# (n_t, dm0, ddm, n_dm): uneven lengths (several transform lengths), trial
+# counts spanning several kernel blocks, a single trial and a tiny beam
+BEAMS = [(3000, 0.0, 1.0, 130), (1000, 2.0, 0.5, 64), (5000, 0.0, 0.25, 2100),
+         (2048, 5.0, 0.0, 1), (700, 0.0, 2.0, 300)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fdd.build()
+
+
+def _common(output, **kw):
+    dnu = (BAND[1] - BAND[0]) / N_CHAN
+    d = dict(n_chan=N_CHAN, nu_lo_mhz=BAND[0] + 0.5 * dnu, dnu_mhz=dnu, t_samp_s=T_SAMP,
+             in_dtype=fdd.FDD_IN_F32, output=output, chunk_len=0)
+    d.update(kw)
+    return d
+
+
+def _inputs(seed=21):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((n_t, N_CHAN)).astype(np.float32) for n_t, *_ in BEAMS]
+
+
+def _oracle(x, beam):
+    n_t, dm0, ddm, n_dm = beam
+    dnu = (BAND[1] - BAND[0]) / N_CHAN
+    nu = BAND[0] + 0.5 * dnu + dnu * np.arange(N_CHAN)
+    d = oracle.delays(nu, dm0 + ddm * np.arange(n_dm), T_SAMP)
+    geo = oracle.geometry(n_t, 0, d)
+    X = oracle.spectra(x.T.astype(np.float64), geo, 0)
+    return oracle.fdd_bins(X, np.arange(geo.K), geo.L, d)
+
+
+_REFS = {}
+
+
+def _refs(xs):
+    if "r" not in _REFS:
+        _REFS["r"] = [_oracle(x, b) for x, b in zip(xs, BEAMS)]
+    return _REFS["r"]
+
+
+def _run(batch, xs, output):
+    d_in = torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
+    n = batch.info["out_elems"]
+    out = torch.zeros((n, 2) if output == fdd.FDD_OUT_SPECTRA else (n,), device="cuda")
+    batch.execute(d_in, out)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    if output == fdd.FDD_OUT_SPECTRA:
+        o = o[:, 0] + 1j * o[:, 1]
+    return o, d_in, out
+
+
+def _check(batch, o, refs, output):
+    for i, (b, ref) in enumerate(zip(BEAMS, refs)):
+        K = ref.shape[1]
+        got = o[batch.out_offsets[i]: batch.out_offsets[i] + b[3] * K].reshape(b[3], K)
+        want = ref if output == fdd.FDD_OUT_SPECTRA else np.abs(ref) ** 2
+        tol = FP32_REL_L2 if output == fdd.FDD_OUT_SPECTRA else 2 * FP32_REL_L2
+        assert rel_l2(got, want) <= tol, (i, rel_l2(got, want))
+
+
+@pytest.mark.parametrize("output", [fdd.FDD_OUT_SPECTRA, fdd.FDD_OUT_POWER])
+def test_batch_matches_oracle(output):
+    xs = _inputs()
+    with fdd.Batch(BEAMS, autotune=False, **_common(output)) as batch:
+        assert batch.info["n_waves"] == 1
+        assert batch.info["mac_variant"] == fdd.FDD_MAC_Q12_8X8
+        assert batch.in_offsets == list(np.cumsum([0] + [b[0] * N_CHAN for b in BEAMS])[:-1])
+        o, _, _ = _run(batch, xs, output)
+    _check(batch, o, _refs(xs), output)
+
+
+def test_batch_waves_graph_replay_and_rebind():
+    """A small workspace splits the batch into waves; replaying the captured graph
+    gives identical results; new buffers are re-captured correctly."""
+    xs = _inputs()
+    # fixed part (header): staging n_chan x max L floats, tables, 64 MiB reserve;
+    # a pool of 1.7 MB then holds beams {0,1}, {2}, {3,4}
+    fixed = 4 * N_CHAN * 8192 + 16 * N_CHAN * len(BEAMS) + (64 << 20)
+    with fdd.Batch(BEAMS, autotune=False, mac_variant=fdd.FDD_MAC_Q_4X8 + 1,
+                   workspace_limit=fixed + 1_700_000,
+                   **_common(fdd.FDD_OUT_SPECTRA)) as batch:
+        assert batch.info["n_waves"] == 3
+        o1, d_in, out = _run(batch, xs, fdd.FDD_OUT_SPECTRA)
+        out.zero_()
+        batch.execute(d_in, out)                 # graph replay
+        torch.cuda.synchronize()
+        o2 = out.cpu().numpy().astype(np.float64)
+        assert np.array_equal(o1, o2[:, 0] + 1j * o2[:, 1])
+        o3, _, _ = _run(batch, xs, fdd.FDD_OUT_SPECTRA)  # new buffers: re-capture
+        assert np.array_equal(o1, o3)
+    _check(batch, o1, _refs(xs), fdd.FDD_OUT_SPECTRA)
+
+
+def test_batch_autotune_picks_a_timed_candidate():
+    xs = _inputs()
+    with fdd.Batch(BEAMS, autotune=True, **_common(fdd.FDD_OUT_POWER)) as batch:
+        timed = batch.info["autotune_ms"]
+        assert len(timed) >= 2 and all(t > 0 for t in timed.values())
+        chosen = fdd.MAC_VARIANT_NAMES[batch.info["mac_variant"]]
+        assert chosen in timed and timed[chosen] == min(timed.values())
+        o, _, _ = _run(batch, xs, fdd.FDD_OUT_POWER)
+    _check(batch, o, _refs(xs), fdd.FDD_OUT_POWER)
+
+
+def test_batch_rejects_what_it_does_not_do():
+    with pytest.raises(fdd.FddError) as e:
+        fdd.Batch(BEAMS, **_common(fdd.FDD_OUT_TIME))
+    assert e.value.status == fdd.FDD_ERR_UNSUPPORTED
+    with pytest.raises(fdd.FddError) as e:
+        fdd.Batch(BEAMS, **_common(fdd.FDD_OUT_POWER, chunk_len=1024))
+    assert e.value.status == fdd.FDD_ERR_UNSUPPORTED
+    with pytest.raises(fdd.FddError) as e:
+        fdd.Batch([(100, -1.0, 1.0, 4)], **_common(fdd.FDD_OUT_POWER))
+    assert e.value.status == fdd.FDD_ERR_INVALID_ARG
