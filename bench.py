@@ -67,6 +67,11 @@ def parse_args():
                     help="override the overlap-save chunk length")
     ap.add_argument("--mac-variant", type=int, default=0,
                     help="0 = automatic, else 1 + FDD_MAC_* kernel variant")
+    ap.add_argument("--batch", default="",
+                    help="time the batching form on a BATCH_WORKLOADS entry instead "
+                         "(one JSON line)")
+    ap.add_argument("--batch-n-t-div", type=int, default=16,
+                    help="divide the batch workload's beam lengths (device memory bound)")
     ap.add_argument("--mac-sweep", default="",
                     help="comma-separated FDD_MAC_* variants (or 'all'): time the "
                          "phase-rotate-and-sum kernel alone for each on one chunk of the "
@@ -554,8 +559,74 @@ def run_mac_sweep(args) -> None:
               flush=True)
 
 
+def run_batch(args) -> None:
+    """Whole-batch throughput of the batching form (unpack, transforms and one
+    persistent phase-rotate-and-sum launch per wave, replayed as a CUDA graph)."""
+    import torch
+
+    import paper_2110_03482_gb300 as fdd
+
+    fdd.build()
+    bw = synth.BATCH_WORKLOADS[args.batch]
+    beams = bw.beams(args.seed, n_t_div=args.batch_n_t_div)
+    common = dict(n_chan=bw.n_chan, nu_lo_mhz=bw.nu_lo_mhz, dnu_mhz=bw.dnu_mhz,
+                  t_samp_s=bw.t_samp_s, in_dtype=fdd.FDD_IN_F32, chunk_len=0,
+                  output={"spectra": fdd.FDD_OUT_SPECTRA, "power": fdd.FDD_OUT_POWER}[bw.output],
+                  workspace_limit=64 << 30)
+    t0 = time.perf_counter()
+    with fdd.Batch(beams, autotune=True, **common) as batch:
+        plan_s = time.perf_counter() - t0
+        info = batch.info
+        gen = torch.Generator(device="cuda").manual_seed(args.seed)
+        d_in = torch.randn(info["in_elems"], device="cuda", generator=gen)
+        out = torch.empty(info["out_elems"] * (2 if bw.output == "spectra" else 1), device="cuda")
+        stream = torch.cuda.current_stream()
+        for _ in range(max(args.warmup, 1)):
+            batch.execute(d_in, out, stream)
+        torch.cuda.synchronize()
+        clocks = Clocks(gpu_uuid(torch.cuda.get_device_properties(0), 0))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.execute(d_in, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+    macs = sum(n_dm * bw.n_chan * (oracle_free_pow2(n_t) // 2 + 1) for n_t, _, _, n_dm in beams)
+    props = torch.cuda.get_device_properties(0)
+    peak = props.multi_processor_count * 128 * 2 * float(load_peaks().get("sm_max_mhz") or 2070) * 1e6
+    n_ts = [b[0] for b in beams]
+    line = {"metric": METRIC, "value": macs / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian noise generated on the device)",
+            "form": "batching (persistent launch per wave, CUDA graph, autotuned tile)",
+            "config": {"workload": bw.name, "beams": bw.n_beams, "n_chan": bw.n_chan,
+                       "n_t_range": [min(n_ts), max(n_ts)], "n_t_divisor": args.batch_n_t_div,
+                       "trials_range": [min(b[3] for b in beams), max(b[3] for b in beams)],
+                       "output": bw.output, "waves": info["n_waves"],
+                       "work_items": info["work_items"], "ctas": info["ctas"],
+                       "tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]],
+                       "autotune_ms": info["autotune_ms"], "plan_seconds": plan_s},
+            "fp32_frac_whole_step": FLOPS_PER_MAC * macs / (ms / 1e3) / peak,
+            "macs_per_step": macs, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def oracle_free_pow2(n: int) -> int:
+    p = 2
+    while p < n:
+        p <<= 1
+    return p
+
+
 def main():
     args = parse_args()
+    if args.batch:
+        run_batch(args)
+        return
     if args.mac_sweep:
         run_mac_sweep(args)
         return

@@ -181,6 +181,50 @@ def filterbank(w: Workload, seed: int, beam: int = 0, rows: int | None = None,
     return out, pulses
 
 
+@dataclass
+class BatchWorkload:
+    """Many beams of uneven length and uneven trial grids (the batching form)."""
+    name: str
+    n_beams: int
+    n_chan: int
+    band_lo_mhz: float
+    band_hi_mhz: float
+    t_samp_s: float
+    n_t_lo: int          # beam lengths drawn log-uniformly in [n_t_lo, n_t_hi]
+    n_t_hi: int
+    trials_lo: int       # trial counts drawn uniformly from multiples of trials_step
+    trials_hi: int
+    trials_step: int
+    ddm: float           # trials dm = 0, ddm, 2 ddm, ...
+    output: str = "power"
+
+    @property
+    def dnu_mhz(self) -> float:
+        return (self.band_hi_mhz - self.band_lo_mhz) / self.n_chan
+
+    @property
+    def nu_lo_mhz(self) -> float:
+        return self.band_lo_mhz + 0.5 * self.dnu_mhz
+
+    def beams(self, seed: int, n_t_div: int = 1):
+        """[(n_t, dm0, ddm, n_dm)] per beam; lengths divided by n_t_div."""
+        n_t = log_uniform_lengths(self.n_beams, self.n_t_lo, self.n_t_hi, seed) // n_t_div
+        rng = np.random.default_rng([seed, 1])
+        steps = np.arange(self.trials_lo, self.trials_hi + 1, self.trials_step)
+        n_dm = rng.choice(steps, size=self.n_beams)
+        return [(int(max(n, 2)), 0.0, self.ddm, int(m)) for n, m in zip(n_t, n_dm)]
+
+
+BATCH_WORKLOADS = {
+    # 96 beams, lengths log-uniform in 2^16..2^20 samples, 1536 channels over
+    # 1100-1700 MHz, 81.92 us, 512..4096 trials (multiples of 64) of step 0.5.
+    "fdd_96beam_1536ch_uneven": BatchWorkload(
+        name="fdd_96beam_1536ch_uneven", n_beams=96, n_chan=1536, band_lo_mhz=1100.0,
+        band_hi_mhz=1700.0, t_samp_s=81.92e-6, n_t_lo=1 << 16, n_t_hi=1 << 20, trials_lo=512,
+        trials_hi=4096, trials_step=64, ddm=0.5),
+}
+
+
 def log_uniform_lengths(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """n integers drawn log-uniformly in [lo, hi] (uneven beam lengths)."""
     rng = np.random.default_rng(seed)
