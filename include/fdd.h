@@ -240,6 +240,27 @@ fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pi
                                   void* d_Y, int64_t y_pitch, int32_t out_kind,
                                   fdd_stream_t stream);
 
+/*
+ * The hot path on a window of bins: bins bin_first .. bin_first + n_bins - 1
+ * of the plan's transform (Eqs. 4, 7 with k the absolute bin index).  Bins
+ * are independent through the phase-rotate-and-sum, so a window is the unit
+ * for splitting bins across calls, streams or devices, and for checking
+ * chosen bins of a full-size transform.
+ *   d_X      : complex float [n_series][n_chan][x_pitch]; element i of a row
+ *              is bin bin_first + i (x_pitch >= n_bins).
+ *   bin_first, n_bins : the window, inside [0, plan n_bins).
+ *   d_Y      : as fdd_dedisperse_spectra, element i of a row = bin bin_first + i
+ *              (y_pitch >= n_bins).
+ * The other arguments, ownership and errors are those of
+ * fdd_dedisperse_spectra; FDD_ERR_INVALID_ARG also for a window outside the
+ * plan's bins.  fdd_dedisperse_spectra is this call with the whole range.
+ */
+fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t x_pitch,
+                                       int32_t n_series, int32_t bin_first, int32_t n_bins,
+                                       int32_t dm_first, int32_t n_dm, void* d_Y,
+                                       int64_t y_pitch, int32_t out_kind,
+                                       fdd_stream_t stream);
+
 /* Stages of the path timed by the profiling calls below. */
 #define FDD_STAGE_UNPACK 0  /* transpose_and_unpack + zero_pad (Algorithm 1)   */
 #define FDD_STAGE_R2C 1     /* channel transforms, Eq. 3 (cuFFT)                */

@@ -54,7 +54,7 @@ EXPORTS = [
     "fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute", "fdd_execute_dm_range",
     "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
     "fdd_destroy", "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
-    "fdd_batch_execute", "fdd_batch_destroy",
+    "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins",
 ]
 FDD_STATIC_MAX_CHAN = 8192
 
@@ -199,6 +199,8 @@ def lib() -> ctypes.CDLL:
         L.fdd_execute_dm_range.argtypes = [vp, vp, i32, i32, vp, vp]
         L.fdd_execute_host.argtypes = [vp, vp, vp, vp]
         L.fdd_dedisperse_spectra.argtypes = [vp, vp, i64, i32, i32, i32, vp, i64, i32, vp]
+        L.fdd_dedisperse_spectra_bins.argtypes = [vp, vp, i64, i32, i32, i32, i32, i32, vp,
+                                                  i64, i32, vp]
         L.fdd_destroy.argtypes = [vp]
         L.fdd_dedisperse_spectra_static.argtypes = [ctypes.POINTER(fdd_params), vp, i64, i32,
                                                      i32, i32, vp, i64, i32, vp]
@@ -214,7 +216,7 @@ def lib() -> ctypes.CDLL:
                      "fdd_execute_dm_range", "fdd_execute_host", "fdd_dedisperse_spectra",
                      "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
                      "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
-                     "fdd_batch_execute", "fdd_batch_destroy"]:
+                     "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -316,6 +318,14 @@ def fdd_dedisperse_spectra(plan: int, d_X, x_pitch: int, n_series: int, dm_first
                            stream=None) -> None:
     _check(lib().fdd_dedisperse_spectra(plan, _ptr(d_X), x_pitch, n_series, dm_first, n_dm,
                                         _ptr(d_Y), y_pitch, out_kind, _stream(stream)))
+
+
+def fdd_dedisperse_spectra_bins(plan: int, d_X, x_pitch: int, n_series: int, bin_first: int,
+                                n_bins: int, dm_first: int, n_dm: int, d_Y, y_pitch: int,
+                                out_kind: int = FDD_OUT_SPECTRA, stream=None) -> None:
+    _check(lib().fdd_dedisperse_spectra_bins(plan, _ptr(d_X), x_pitch, n_series, bin_first,
+                                             n_bins, dm_first, n_dm, _ptr(d_Y), y_pitch,
+                                             out_kind, _stream(stream)))
 
 
 def fdd_dedisperse_spectra_static(params: Params, d_X, x_pitch: int, n_series: int,
@@ -422,6 +432,11 @@ class Plan:
                            out_kind=FDD_OUT_SPECTRA, stream=None):
         fdd_dedisperse_spectra(self.handle, d_X, x_pitch, n_series, dm_first, n_dm, d_Y,
                                y_pitch, out_kind, stream)
+
+    def dedisperse_spectra_bins(self, d_X, x_pitch, n_series, bin_first, n_bins, dm_first, n_dm,
+                                d_Y, y_pitch, out_kind=FDD_OUT_SPECTRA, stream=None):
+        fdd_dedisperse_spectra_bins(self.handle, d_X, x_pitch, n_series, bin_first, n_bins,
+                                    dm_first, n_dm, d_Y, y_pitch, out_kind, stream)
 
     def query(self) -> dict:
         return fdd_query(self.handle)

@@ -281,7 +281,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
                   fixed + per_dm);
     const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
     if (fit < batch) {
-      const int64_t blk = tc ? fdd::mac_tc_trials_per_pass()
+      const int64_t blk = tc ? fdd::mac_tc_trials_per_pass(p->n_beams)
                              : fdd::mac_variant_trials_per_block(g->mac_variant);
       batch = fit >= blk ? fit / blk * blk : fit;
     }
@@ -710,14 +710,18 @@ fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_
   return FDD_OK;
 }
 
-fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pitch,
-                                  int32_t n_series, int32_t dm_first, int32_t n_dm, void* d_Y,
-                                  int64_t y_pitch, int32_t out_kind, fdd_stream_t stream) {
+fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t x_pitch,
+                                       int32_t n_series, int32_t bin_first, int32_t n_bins,
+                                       int32_t dm_first, int32_t n_dm, void* d_Y,
+                                       int64_t y_pitch, int32_t out_kind, fdd_stream_t stream) {
   if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
   if (!d_X || !d_Y) return fail(FDD_ERR_INVALID_ARG, "NULL spectra pointer");
   const fdd_info& g = plan->info;
-  if (x_pitch < g.n_bins || y_pitch < g.n_bins)
-    return fail(FDD_ERR_INVALID_ARG, "pitches must be >= n_bins (%lld)", (long long)g.n_bins);
+  if (bin_first < 0 || n_bins < 1 || bin_first + static_cast<int64_t>(n_bins) > g.n_bins)
+    return fail(FDD_ERR_INVALID_ARG, "bin range [%d, %lld) outside [0, %lld)", bin_first,
+                static_cast<long long>(bin_first) + n_bins, (long long)g.n_bins);
+  if (x_pitch < n_bins || y_pitch < n_bins)
+    return fail(FDD_ERR_INVALID_ARG, "pitches must be >= n_bins (%d)", n_bins);
   if (n_series < 1 || n_series > 65535)
     return fail(FDD_ERR_INVALID_ARG, "n_series must be in [1, 65535]");
   if (dm_first < 0 || n_dm < 1 || dm_first + static_cast<int64_t>(n_dm) > plan->p.n_dm)
@@ -732,7 +736,8 @@ fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pi
   m.x_series_stride = x_pitch * plan->p.n_chan;
   m.pc = plan->d_pc;
   m.n_chan = plan->p.n_chan;
-  m.n_bins = static_cast<int>(g.n_bins);
+  m.n_bins = n_bins;
+  m.k_begin = bin_first;
   m.n_series = n_series;
   m.j_begin = dm_first;
   m.n_dm = n_dm;
@@ -751,6 +756,15 @@ fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pi
   else
     FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));
   return FDD_OK;
+}
+
+fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pitch,
+                                  int32_t n_series, int32_t dm_first, int32_t n_dm, void* d_Y,
+                                  int64_t y_pitch, int32_t out_kind, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  return fdd_dedisperse_spectra_bins(plan, d_X, x_pitch, n_series, 0,
+                                     static_cast<int32_t>(plan->info.n_bins), dm_first, n_dm,
+                                     d_Y, y_pitch, out_kind, stream);
 }
 
 fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on) {

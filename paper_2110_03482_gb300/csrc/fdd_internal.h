@@ -23,7 +23,8 @@ struct MacArgs {
   int64_t x_chan_stride;    // complex elements
   const PhaseConst* pc;     // [n_chan]
   int n_chan;
-  int n_bins;
+  int n_bins;               // bins handled by this call (local indices 0 .. n_bins-1)
+  int k_begin;              // absolute bin index of local bin 0 (phases use k_begin + k)
   int n_series;
   int j_begin;              // first global trial index handled by this call
   int n_dm;                 // trials handled by this call
@@ -32,7 +33,7 @@ struct MacArgs {
   int64_t y_dm_stride;      // elements of the output type
   int out_kind;             // 1 = complex spectra, 2 = |Y|^2
   float scale;              // multiplies Y before the store (power: |scale Y|^2)
-  int real_bin_a;           // bins whose imaginary part is set to zero, or -1
+  int real_bin_a;           // absolute bins whose imaginary part is set to zero, or -1
   int real_bin_b;
   int* status;              // device status word (may be NULL)
 };
@@ -81,8 +82,11 @@ size_t mac_smem_bytes(int variant, int n_chan);
 // phasors, BF16 data, FP32 accumulation in tensor memory; one persistent CTA
 // per SM.
 size_t mac_tc_smem_bytes();
-int mac_tc_trials_per_pass();
+int mac_tc_trials_per_pass(int n_series);
 cudaError_t mac_tc_prepare();
+// Beams per tensor-core group: 16 when a call has at most 16 series (then a
+// pass covers 1024 trials), else 32 (512 trials per pass).
+int mac_tc_beams_per_group(int n_series);
 cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s);
 
 // Shared with the allocation-free entry point (fdd_noalloc.cu): the last-error

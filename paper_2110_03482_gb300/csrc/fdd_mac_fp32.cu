@@ -398,9 +398,10 @@ __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pc
   const int lg = lane % Gm::G;
   const int ga = lg / Gm::GB;
   const int gb = lg % Gm::GB;
-  const int k = (bin_tile * W + warp) * Gm::NG + g;
+  const int k = (bin_tile * W + warp) * Gm::NG + g;  // local bin
   const bool k_ok = k < a.n_bins;
-  const uint32_t ku = k_ok ? static_cast<uint32_t>(k) : 0u;  // idle groups run bin 0, store nothing
+  const int kl = k_ok ? k : 0;  // idle groups run local bin 0, store nothing
+  const uint32_t ku = static_cast<uint32_t>(a.k_begin + kl);
   const int jblk = dm_block * Gm::DMS;
   const int nc = a.n_chan;
 
@@ -410,7 +411,7 @@ __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pc
   Generator<Gm, M> gen;
   gen.init(ku, lg, a.j_begin + jblk);
 
-  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + ku;
+  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
   const int64_t xs = a.x_chan_stride;
   // The generation of channel c uses X[c]; the pipelined schedule runs it one
   // channel ahead, so a group of kUnroll iterations starting at c0 consumes
@@ -465,7 +466,7 @@ __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pc
   }
 
   if (!k_ok) return;
-  const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
+  const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
 #pragma unroll
   for (int ii = 0; ii < Gm::AT; ++ii) {
 #pragma unroll
@@ -577,9 +578,10 @@ __global__ void __launch_bounds__(kThreads, 1) mac_legacy_kernel(const MacArgs a
   const int lg = lane % T::G;
   const int ga = lg / T::GB;
   const int gb = lg % T::GB;
-  const int k = (blockIdx.x * kWarps + warp) * T::NG + g;
+  const int k = (blockIdx.x * kWarps + warp) * T::NG + g;  // local bin
   const bool k_ok = k < a.n_bins;
-  const uint32_t ku = k_ok ? static_cast<uint32_t>(k) : 0u;  // idle groups compute bin 0, store nothing
+  const int kl = k_ok ? k : 0;  // idle groups compute local bin 0, store nothing
+  const uint32_t ku = static_cast<uint32_t>(a.k_begin + kl);
   const int jblk = blockIdx.y * T::DMS;
   const int series = blockIdx.z;
 
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_legacy_kernel(const MacArgs a
     poff[q] = T::ZSZ + (bi / T::BT) * T::PROW + (bi % T::BT);
   }
 
-  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + ku;
+  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
   const int64_t xs = a.x_chan_stride;
 
   float acc_re[T::AT][T::BT];
@@ -688,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_legacy_kernel(const MacArgs a
   }
 
   if (!k_ok) return;
-  const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
+  const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
 #pragma unroll
   for (int ii = 0; ii < T::AT; ++ii) {
 #pragma unroll

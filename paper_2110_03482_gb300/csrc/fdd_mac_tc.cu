@@ -16,6 +16,8 @@
 // M = 128 trials b, N = 256 = 4 a's x 32 beams x (re, im), K = 64 per stage
 // (32 channels x (re, im)); one pass over the channels covers 4 a's = 512
 // trials, and passes alternate between two accumulators in tensor memory.
+// Calls with at most 16 series use groups of 16 beams instead: N = 256 = 8 a's
+// x 16 beams x (re, im), 1024 trials per pass, no idle columns.
 //
 // Warp specialisation: warp 0 allocates tensor memory and one of its threads
 // issues the MMAs; 16 producer warps evaluate P (exact fixed-point phase,
@@ -36,9 +38,10 @@ namespace {
 
 constexpr int kM = 128;                  // trials b per a (T)
 constexpr int kN = 256;                  // accumulator columns
-constexpr int kBeams = 32;               // beams per group
-constexpr int kNA = kN / (2 * kBeams);   // a's per pass (4)
-constexpr int kDmsPass = kNA * kM;       // trials per pass (512)
+// Beams per group (kBeams, 16 or 32) is a template parameter: a pass covers
+// kNA = kN / (2 kBeams) a's, i.e. kNA * kM trials.
+template <int kBeams>
+__host__ __device__ constexpr int dms_per_pass() { return kN / (2 * kBeams) * kM; }
 constexpr int kKC = 32;                  // channels per stage
 constexpr int kProdWarps = 16;
 constexpr int kProd = 32 * kProdWarps;
@@ -132,8 +135,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // kHiLo: phasors as BF16 hi + lo (two MMAs per K step); otherwise BF16 only.
-template <bool kHiLo>
+template <bool kHiLo, int kBeams>
 __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
+  static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
+  constexpr int kNA = kN / (2 * kBeams);      // a's per pass
+  constexpr int kDmsPass = dms_per_pass<kBeams>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     uint32_t p = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
-      const bool real_only = (k == a.real_bin_a) || (k == a.real_bin_b);
+      const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
       for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
@@ -297,14 +303,14 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     // Producer warp pw (0..15) evaluates, for channel nu = tile*32 + lane:
     //   P_b for the 8 rows b = 8 pw .. 8 pw + 7 (one direct phasor, then the
     //   recurrence P_{b+1} = P_b R with R = exp(2 pi i k v), at most 7 steps),
-    //   Q_a for the pass's 4 a's (Q_0 direct, Q_{a+1} = Q_a R^128),
-    //   Z_a = Q_a X for the beams beta = pw and pw + 16.
+    //   Q_a for the pass's kNA a's (Q_0 direct, Q_{a+1} = Q_a R^128),
+    //   Z_a = Q_a X for the beams beta = pw (and pw + 16 in 32-beam groups).
     // X and the phase constants of the next tile are loaded one stage ahead.
     const int pw = warp - 1 - kEpiWarps;           // 0..15
     constexpr int kRows = kM / kProdWarps;         // P rows per warp (8)
-    constexpr int kBeamsPerWarp = kBeams / kProdWarps;  // 2
+    constexpr int kBeamsPerWarp = kBeams / kProdWarps;  // 1 or 2
     // Store offsets that do not change between stages (see sw128): the P
-    // rows of this warp, and the Z rows (al*32 + pw + 16m)*2 + e, whose
+    // rows of this warp, and the Z rows (al*kBeams + pw + 16m)*2 + e, whose
     // position within an 8-row group depends only on pw and e.
     const uint32_t lane_chunk = static_cast<uint32_t>((lane >> 2) << 4);
     const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     uint32_t s = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
-      const uint32_t ku = static_cast<uint32_t>(k);
+      const uint32_t ku = static_cast<uint32_t>(a.k_begin + k);  // absolute bin
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
@@ -394,8 +400,8 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
               const float2 z = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qa.y, qa.x),
                                           __fmul2_rn(make_float2(x[m].x, x[m].x), qa));
               const uint32_t zb = bf16x2_bits(__floats2bfloat162_rn(z.x, z.y));
-              // rows (al*32 + beta)*2 + {0, 1}: per-thread base + a constant
-              const uint32_t row_off = static_cast<uint32_t>((8 * al + 4 * m) * 1024);
+              // rows (al*kBeams + beta)*2 + {0, 1}: per-thread base + a constant
+              const uint32_t row_off = static_cast<uint32_t>((kBeams / 4 * al + 4 * m) * 1024);
               *reinterpret_cast<uint32_t*>(tb + z_base[0] + row_off) = zb ^ 0x80000000u;  // (zr, -zi)
               *reinterpret_cast<uint32_t*>(tb + z_base[1] + row_off) = __byte_perm(zb, 0, 0x1032);  // (zi, zr)
             }
@@ -426,15 +432,23 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
 
 size_t mac_tc_smem_bytes() { return kStages * kStageBytes + 1024 + 128; }
 
-int mac_tc_trials_per_pass() { return kDmsPass; }
+int mac_tc_beams_per_group(int n_series) { return n_series <= 16 ? 16 : 32; }
+
+int mac_tc_trials_per_pass(int n_series) {
+  return mac_tc_beams_per_group(n_series) == 16 ? dms_per_pass<16>() : dms_per_pass<32>();
+}
 
 cudaError_t mac_tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(mac_tc_kernel<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(mac_tc_smem_bytes()));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(mac_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(mac_tc_smem_bytes()));
+  const void* fns[] = {reinterpret_cast<const void*>(&mac_tc_kernel<true, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<false, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<true, 16>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<false, 16>)};
+  for (const void* fn : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(mac_tc_smem_bytes()));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s) {
@@ -442,8 +456,12 @@ cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t 
   const int grid = a.n_bins < n_sms ? a.n_bins : n_sms;
   MacArgs args = a;
   void* params[] = {&args};
-  const void* fn = hi_lo ? reinterpret_cast<const void*>(&mac_tc_kernel<true>)
-                        : reinterpret_cast<const void*>(&mac_tc_kernel<false>);
+  const bool g16 = mac_tc_beams_per_group(a.n_series) == 16;
+  const void* fn =
+      hi_lo ? (g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<true, 16>)
+                   : reinterpret_cast<const void*>(&mac_tc_kernel<true, 32>))
+            : (g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<false, 16>)
+                   : reinterpret_cast<const void*>(&mac_tc_kernel<false, 32>));
   return cudaLaunchKernel(fn, dim3(grid),
                           dim3(kThreads), params, mac_tc_smem_bytes(), s);
 }

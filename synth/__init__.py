@@ -225,6 +225,64 @@ BATCH_WORKLOADS = {
 }
 
 
+# ------------------------------------------------- counter-based (Philox) inputs
+def sweep_starts(nu_mhz: np.ndarray, t_samp_s: float, t0: int, dm: float) -> np.ndarray:
+    """First sample of a pulse emitted at t0 (top channel) in every channel,
+    along the sky-model sweep (module docstring)."""
+    nu = np.asarray(nu_mhz, dtype=np.float64)
+    return t0 + np.rint(dm * K_DM_SKY * (nu ** -2 - nu.max() ** -2) / t_samp_s).astype(np.int64)
+
+
+def philox_pulses(nu_mhz: np.ndarray, t_samp_s: float, n_t: int, dm_lo: float, dm_hi: float,
+                  seed: int, beam: int, n_pulses: int, amp: float = 2.0, width: int = 4):
+    """Pulses of one beam for the counter-based generator: DMs uniform in
+    [dm_lo, dm_hi], emission times uniform in [0, n_t - sweep - 4), drawn from
+    PCG64 seeded by (seed, beam, 7).  Returns ([Pulse], [(starts, width, amp)])."""
+    rng = np.random.default_rng([seed, beam, 7])
+    pulses, specs = [], []
+    for _ in range(n_pulses):
+        dm = float(rng.uniform(dm_lo, dm_hi))
+        starts0 = sweep_starts(nu_mhz, t_samp_s, 0, dm)
+        t_hi = max(1, n_t - int(starts0.max()) - 4)
+        t0 = int(rng.integers(0, t_hi))
+        pulses.append(Pulse(t0=t0, dm=dm, amp=amp, width=width))
+        specs.append((starts0 + t0, width, amp))
+    return pulses, specs
+
+
+def philox_beam_args(w: Workload, seed: int, beam: int) -> dict:
+    """Keyword arguments of ``synth.philox.filterbank`` / ``synth.gpu.filterbank``
+    for one beam of a workload (noise, 8-bit or float, the beam's pulses)."""
+    dms = w.dms()
+    pulses, specs = philox_pulses(w.channel_centres(), w.t_samp_s, w.n_t, float(dms.min()),
+                                  float(dms.max()), seed, beam, w.pulses_per_beam,
+                                  amp=2.0 * w.noise_sigma)
+    return dict(n_chan=w.n_chan, seed=seed, beam=beam, mean=w.noise_mean, sigma=w.noise_sigma,
+                u8=w.dtype == "u8", pulses=specs), pulses
+
+
+def batch_beam_args(bw: "BatchWorkload", desc, seed: int, beam: int,
+                    pulses_per_beam: int = 1) -> tuple[dict, list]:
+    """Counter-based generator arguments for beam ``beam`` of a batch, whose
+    (n_t, dm0, ddm, n_dm) is ``desc``: float32 N(0,1) noise and pulses with DMs
+    in the beam's own trial range."""
+    n_t, dm0, ddm, n_dm = desc
+    nu = bw.nu_lo_mhz + bw.dnu_mhz * np.arange(bw.n_chan, dtype=np.float64)
+    pulses, specs = philox_pulses(nu, bw.t_samp_s, int(n_t), float(dm0),
+                                  float(dm0 + ddm * (n_dm - 1)), seed, beam, pulses_per_beam)
+    return dict(n_chan=bw.n_chan, seed=seed, beam=beam, pulses=specs), pulses
+
+
+def philox_filterbank(w: Workload, seed: int, beam: int = 0, t0: int = 0,
+                      rows: int | None = None):
+    """Host copy of rows [t0, t0 + rows) of one beam (counter-based generator);
+    ``synth.gpu.filterbank`` makes the same bytes on the device."""
+    from . import philox
+    kw, pulses = philox_beam_args(w, seed, beam)
+    n = w.n_t - t0 if rows is None else rows
+    return philox.filterbank(n_rows=n, t0=t0, **kw), pulses
+
+
 def log_uniform_lengths(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """n integers drawn log-uniformly in [lo, hi] (uneven beam lengths)."""
     rng = np.random.default_rng(seed)

@@ -121,6 +121,30 @@ def test_kernel_dm_subrange_and_large_phases():
         assert rel_l2(Y[:, q], ref[:, q]) <= 4 * FP32_REL_L2, bins[q]
 
 
+@pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_Q_4X4 + 1, fdd.FDD_MAC_R_8X8 + 1])
+def test_kernel_bin_windows_equal_the_whole_range(variant):
+    """A window of bins (absolute phases k_begin + k) gives bit for bit the
+    columns of the whole-range call, for the default and two other tiles."""
+    n_chan, L, n_dm = 48, 4096, 1100
+    w = _small_workload(n_chan, L, 0.5 * np.arange(n_dm))
+    K = L // 2 + 1
+    rng = np.random.default_rng(17)
+    X = rng.standard_normal((2, n_chan, K)) + 1j * rng.standard_normal((2, n_chan, K))
+    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA, mac_variant=variant)) as plan:
+        dX = complex_to_device(X, K)
+        full = torch.zeros((2, n_dm, K, 2), device="cuda")
+        plan.dedisperse_spectra(dX, K, 2, 0, n_dm, full, K)
+        for b0, nb in [(0, 1), (1, 100), (777, 333), (K - 13, 13)]:
+            win = torch.zeros((2, n_dm, nb, 2), device="cuda")
+            xw = dX[:, :, b0: b0 + nb].contiguous()
+            plan.dedisperse_spectra_bins(xw, nb, 2, b0, nb, 0, n_dm, win, nb)
+            torch.cuda.synchronize()
+            assert torch.equal(win, full[:, :, b0: b0 + nb]), (b0, nb)
+        with pytest.raises(fdd.FddError) as e:
+            plan.dedisperse_spectra_bins(dX, K, 2, -1, 4, 0, n_dm, full, K)
+        assert e.value.status == fdd.FDD_ERR_INVALID_ARG
+
+
 # ----------------------------------------------------------------- end to end
 def _run_execute(w, x_host, output, **kw):
     with fdd.Plan(**params_for(w, output=output, **kw)) as plan:

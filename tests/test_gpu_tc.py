@@ -3,8 +3,9 @@ against the FP64 oracle (GB300 only).
 
 The gate is the low-precision form's relative L2 error <= 3e-3 against FP64:
 BF16 rounding of the data side alone is ~2^-9 / sqrt(3) ~ 1.1e-3 per element.
-Shapes span partial and several beam groups (32 beams each), a ragged last
-channel tile (32 channels each) and partial 1024-trial passes.
+Shapes span partial and several beam groups (16 beams each for calls of at
+most 16 series, else 32), a ragged last channel tile (32 channels each) and
+partial trial passes (1024 trials in 16-beam groups, 512 in 32-beam groups).
 """
 import numpy as np
 import pytest
@@ -44,6 +45,7 @@ def _workload(n_chan, n_t, dms, n_beams, band=(1200.0, 1500.0), t_samp=2e-3, chu
     (5, 40, 256, 0.0, 0.5, 1100),    # partial beam group, ragged channel tile, 2 passes
     (32, 64, 128, 3.0, 1.0, 1024),   # one full group, exactly one pass
     (37, 33, 512, 0.0, 0.25, 300),   # two groups, one partial pass
+    (16, 64, 512, 1.0, 0.25, 2100),  # one full 16-beam group, 1024-trial passes, ragged
 ])
 def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm, precision):
     dms = dm0 + ddm * np.arange(n_dm)
@@ -125,3 +127,28 @@ def test_tc_end_to_end(output):
                 ref = np.abs(oracle.fdd_bins(oracle.spectra(x, geo, c), np.arange(geo.K),
                                              geo.L, d)) ** 2
                 assert rel_l2(o[b, c], ref) <= 2 * TC_REL_L2
+
+
+@pytest.mark.parametrize("n_series", [7, 20])
+def test_tc_bin_windows_equal_the_whole_range(n_series):
+    """A window of bins (absolute phases k_begin + k) gives bit for bit the
+    columns of the whole-range call: every bin's products and sums are the same."""
+    n_chan, L, n_dm = 40, 1024, 700
+    w = _workload(n_chan, L, 0.5 * np.arange(n_dm), n_series)
+    K = L // 2 + 1
+    rng = np.random.default_rng(n_series)
+    X = rng.standard_normal((n_series, n_chan, K)) + 1j * rng.standard_normal((n_series, n_chan, K))
+    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA,
+                               precision=fdd.FDD_PREC_BF16_HILO)) as plan:
+        dX = complex_to_device(X, K)
+        full = torch.zeros((n_series, n_dm, K, 2), device="cuda")
+        plan.dedisperse_spectra(dX, K, n_series, 0, n_dm, full, K)
+        for b0, nb in [(0, 3), (200, 57), (K - 5, 5)]:
+            win = torch.zeros((n_series, n_dm, nb, 2), device="cuda")
+            plan.dedisperse_spectra_bins(dX[:, :, b0:].contiguous(), K - b0, n_series, b0, nb,
+                                         0, n_dm, win, nb)
+            torch.cuda.synchronize()
+            assert torch.equal(win, full[:, :, b0: b0 + nb]), (b0, nb)
+        with pytest.raises(fdd.FddError) as e:
+            plan.dedisperse_spectra_bins(dX, K, n_series, K - 2, 3, 0, n_dm, full, K)
+        assert e.value.status == fdd.FDD_ERR_INVALID_ARG
