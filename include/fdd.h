@@ -88,7 +88,10 @@ typedef enum fdd_status {
 #define FDD_MAC_R_8X8 10  /* reference: the first scalar kernel                   */
 #define FDD_MAC_Q12_8X8 11 /* Q with 12-warp blocks (fewer registers, more warps)  */
 #define FDD_MAC_S12_8X8 12 /* S with 12-warp blocks                                */
-#define FDD_MAC_VARIANTS 13
+#define FDD_MAC_Z12_8X8 13 /* Z swapped as pre-broadcast quads, 12-warp blocks    */
+#define FDD_MAC_P12_8X8 14 /* P with 12-warp blocks                                */
+#define FDD_MAC_W12_8X8 15 /* warp-specialised: 4 phasor warps feed 8 MAC warps   */
+#define FDD_MAC_VARIANTS 16
 #define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
 
 /* fdd_params.precision */

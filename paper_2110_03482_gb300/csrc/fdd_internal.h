@@ -54,6 +54,9 @@ enum MacVariant {
   MAC_R_8x8 = FDD_MAC_R_8X8,
   MAC_Q12_8x8 = FDD_MAC_Q12_8X8,
   MAC_S12_8x8 = FDD_MAC_S12_8X8,
+  MAC_Z12_8x8 = FDD_MAC_Z12_8X8,
+  MAC_P12_8x8 = FDD_MAC_P12_8X8,
+  MAC_W12_8x8 = FDD_MAC_W12_8X8,
   MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
 };
 // One set of spectra in a batch (the batching form): its launch arguments

@@ -43,10 +43,14 @@
 // Lanes are numbered lane = ga * GB + gb, so each quarter warp reads a single
 // Z row (a broadcast) and GB distinct P rows; the P rows are padded so that
 // those reads fall in distinct shared-memory banks.
+#include "fdd_device.cuh"
 #include "fdd_internal.h"
 
 namespace fdd {
 namespace {
+
+using dev::top32_mul;
+using dev::unit_phasor;
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
@@ -295,6 +299,80 @@ struct PackedCompact {
   }
 };
 
+// ------------------------------------------- packed form, Z quads, P planes
+// Z swapped as pre-broadcast quads (zr, zr, zi, zi), so the paired FMAs take
+// their Z operands straight from the loaded registers; P as planes pr, pi;
+// the -zi pair is the negated (zi, zi) operand.  One quad is read per a row
+// inside the MAC, which keeps the register count of the compact form.
+template <class Gm>
+struct PackedZQuad {
+  static constexpr int AT = Gm::AT, BT = Gm::BT;
+  static constexpr int ZROW = 4 * AT + 4;   // padded a-rows of quads
+  static constexpr int PSTR = BT + 4;       // padded b-rows of a plane
+  static constexpr int ZFL = Gm::GA * ZROW;
+  static constexpr int PFL = Gm::GB * PSTR;
+  static constexpr int GFL = ZFL + 2 * PFL;
+  static_assert(BT % 4 == 0, "plane rows are read as float4");
+
+  struct Ops {
+    float2 pr[BT / 2], pi[BT / 2];
+    const float4* zq;
+  };
+  struct Acc {
+    float2 re[AT][BT / 2], im[AT][BT / 2];
+  };
+  static __device__ __forceinline__ void zero(Acc& c) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i)
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) c.re[i][j] = c.im[i][j] = make_float2(0.f, 0.f);
+  }
+  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 4 * (a % AT); }
+  static __device__ __forceinline__ int p_off(int b) { return ZFL + (b / BT) * PSTR + (b % BT); }
+  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
+    *reinterpret_cast<float4*>(grp + off) = make_float4(zr, zr, zi, zi);
+  }
+  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
+    grp[off] = pr;
+    grp[off + PFL] = pi;
+  }
+  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
+    const float* row = grp + ZFL + gb * PSTR;
+#pragma unroll
+    for (int h = 0; h < BT / 4; ++h) {
+      const float4 r = *reinterpret_cast<const float4*>(row + 4 * h);
+      const float4 i = *reinterpret_cast<const float4*>(row + PFL + 4 * h);
+      o.pr[2 * h] = make_float2(r.x, r.y);
+      o.pr[2 * h + 1] = make_float2(r.z, r.w);
+      o.pi[2 * h] = make_float2(i.x, i.y);
+      o.pi[2 * h + 1] = make_float2(i.z, i.w);
+    }
+    o.zq = reinterpret_cast<const float4*>(grp + ga * ZROW);
+  }
+  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
+#pragma unroll
+    for (int i = 0; i < AT; ++i) {
+      const float4 z = o.zq[i];
+      const float2 zr = make_float2(z.x, z.y), zi = make_float2(z.z, z.w);
+      const float2 zn = make_float2(-z.z, -z.w);
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
+      }
+#pragma unroll
+      for (int j = 0; j < BT / 2; ++j) {
+        c.re[i][j] = __ffma2_rn(zn, o.pi[j], c.re[i][j]);
+        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
+      }
+    }
+  }
+  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
+    const float2 r = c.re[i][j / 2], m = c.im[i][j / 2];
+    return (j & 1) ? make_float2(r.y, m.y) : make_float2(r.x, m.x);
+  }
+};
+
 // Same as PackedCompact with the MAC in two passes over the whole tile (all
 // zr terms, then all zi terms), so the two updates of an accumulator pair are
 // a full pass apart.
@@ -323,22 +401,6 @@ struct PackedCompact2 : PackedCompact<Gm> {
     }
   }
 };
-
-// Top 32 bits of (m * (hi:lo)) mod 2^64, without the carry of the low word
-// (an error of at most 2^-32 cycle).
-__device__ __forceinline__ uint32_t top32_mul(uint32_t m, uint32_t lo, uint32_t hi) {
-  return __umulhi(m, lo) + m * hi;
-}
-
-// Unit phasor of a phase given in units of 2^-32 cycle.  Read as a signed
-// integer the phase lies in [-1/2, 1/2) cycle, i.e. [-pi, pi) radians, the
-// range in which the hardware sine/cosine are accurate to about 2^-21.
-__device__ __forceinline__ float2 unit_phasor(uint32_t phase) {
-  const float x = __int2float_rn(static_cast<int>(phase)) * 1.46291807926715968e-9f;  // 2pi/2^32
-  float s, c;
-  __sincosf(x, &s, &c);
-  return make_float2(c, s);
-}
 
 // This lane's share of the phasor evaluation for one channel: Z_a = X Q_a for
 // a = lg + q G and P_b for b = lg + q G, written into the group's swap stage.
@@ -495,6 +557,198 @@ __global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
   for (int i = threadIdx.x; i < a.n_chan; i += W * 32) pcs[i] = a.pc[i];
   __syncthreads();
   mac_block<Gm, M, kPipe, W>(a, pcs, swap_all, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// --------------------------------------------- warp-specialised schedule
+// The plain and pipelined schedules make every warp alternate between the
+// latency-bound phasor evaluation (integer phase, MUFU sin/cos, the swap) and
+// its block of paired FMAs; with three warps per scheduler the FMA pipe idles
+// whenever all of them are evaluating.  Here the two jobs go to different
+// warps: kCons consumer warps each own one bin of the CTA's tile and only read
+// Z and P from shared memory and accumulate, while kProd producer warps
+// evaluate Z_a = X Q_a and P_b for every consumer's bin, kWsCh channels at a
+// time, into a ring of kWsStages stages.  A pair of mbarriers per stage orders
+// the two sides (full: every producer thread has written the stage; empty:
+// every consumer thread has read it).  Every wait is bounded; a timeout stops
+// both sides and is reported in the status word.
+template <class Gm, class M, int kCons, int kProd, int kWsCh = 4, int kWsStages = 3>
+struct WsLayout {
+  static_assert(Gm::NG == 1, "one bin per consumer warp");
+  static_assert(kCons % kProd == 0, "producers share the consumers' bins evenly");
+  static constexpr int kBinsPerProd = kCons / kProd;
+  static constexpr int kStageFloats = kWsCh * kCons * M::GFL;  // [channel][consumer][GFL]
+  // 2 kWsStages mbarriers and the abort flag, rounded up to 16 bytes
+  static constexpr size_t kBarBytes = (2 * kWsStages * 8 + 4 + 15) / 16 * 16;
+  static constexpr size_t kSwapBytes =
+      kBarBytes + sizeof(float) * static_cast<size_t>(kWsStages) * kStageFloats;
+  static_assert(2 * kWsStages * 8 + 4 <= kBarBytes, "barrier area");
+};
+
+// kRegCons / kRegProd: registers per thread of the consumer / producer
+// warpgroups after a setmaxnreg split (0: no split); kPre: consumers load the
+// next channel's operands before the current channel's MAC (double buffer).
+template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages, int kRegCons,
+          int kRegProd, bool kPre>
+__global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const MacArgs a) {
+  using Ly = WsLayout<Gm, M, kCons, kProd, kWsCh, kWsStages>;
+  static_assert(kRegCons == 0 ||
+                    (kCons % 4 == 0 && kProd % 4 == 0 &&
+                     kRegCons * kCons + kRegProd * kProd <= (65536 / ((kCons + kProd) * 32) / 8 * 8) * (kCons + kProd)),
+                "register split above the launch's registers");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
+  unsigned char* tail = smem_raw + sizeof(PhaseConst) * a.n_chan;  // 16-byte aligned
+  uint64_t* full = reinterpret_cast<uint64_t*>(tail);
+  uint64_t* empty = full + kWsStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kWsStages);
+  float* stages = reinterpret_cast<float*>(tail + Ly::kBarBytes);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWsStages; ++i) {
+      dev::mbar_init(&full[i], kProd * 32);
+      dev::mbar_init(&empty[i], kCons * 32);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < a.n_chan; i += blockDim.x) pcs[i] = a.pc[i];
+  __syncthreads();
+
+  const int n_iter = (a.n_chan + kWsCh - 1) / kWsCh;
+  const int jblk = blockIdx.y * Gm::DMS;
+  const int series = blockIdx.z;
+  const int k_tile = blockIdx.x * kCons;  // first local bin of the CTA
+  bool ok = true;
+
+  if (warp >= kCons) {
+    // ------------------------------------------------------------ producers
+    if (kRegCons) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegProd));
+    const int pw = warp - kCons;
+    constexpr int NB = Ly::kBinsPerProd;
+    Generator<Gm, M> gen[NB];
+    const float2* xp[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int k = k_tile + pw * NB + q;
+      const int kl = k < a.n_bins ? k : 0;  // idle bins evaluate local bin 0, stored by nobody
+      gen[q].init(static_cast<uint32_t>(a.k_begin + kl), lane, a.j_begin + jblk);
+      xp[q] = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
+    }
+    const int64_t xs = a.x_chan_stride;
+    float2 xn[NB][kWsCh];
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int ch = 0; ch < kWsCh; ++ch)
+        xn[q][ch] = ch < a.n_chan ? __ldg(xp[q] + ch * xs) : make_float2(0.f, 0.f);
+    for (int it = 0; it < n_iter; ++it) {
+      const int s = it % kWsStages;
+      float2 x[NB][kWsCh];
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int ch = 0; ch < kWsCh; ++ch) {
+          x[q][ch] = xn[q][ch];
+          const int c = (it + 1) * kWsCh + ch;  // prefetch the next stage's X
+          xn[q][ch] = c < a.n_chan ? __ldg(xp[q] + c * xs) : make_float2(0.f, 0.f);
+        }
+      ok = __all_sync(0xffffffffu,
+                      dev::mbar_wait(&empty[s], ((it / kWsStages) & 1) ^ 1, abort_flag));
+      if (!ok) break;
+      float* st = stages + s * Ly::kStageFloats + (pw * NB) * M::GFL;
+#pragma unroll
+      for (int ch = 0; ch < kWsCh; ++ch) {
+        const int c = it * kWsCh + ch;
+        if (c < a.n_chan) {
+          const PhaseConst p = pcs[c];
+#pragma unroll
+          for (int q = 0; q < NB; ++q) gen[q].run(p, x[q][ch], st + (ch * kCons + q) * M::GFL);
+        }
+      }
+      dev::mbar_arrive(&full[s]);
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    if (kRegCons) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCons));
+    const int k = k_tile + warp;  // local bin
+    const int ga = lane / Gm::GB;
+    const int gb = lane % Gm::GB;
+    typename M::Acc acc;
+    M::zero(acc);
+    if (!kPre) {
+      for (int it = 0; it < n_iter; ++it) {
+        const int s = it % kWsStages;
+        ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (it / kWsStages) & 1, abort_flag));
+        if (!ok) break;
+        const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
+        const int nc = a.n_chan - it * kWsCh;
+#pragma unroll
+        for (int ch = 0; ch < kWsCh; ++ch) {
+          if (ch < nc) {
+            typename M::Ops ops;
+            M::load(st + ch * kCons * M::GFL, ga, gb, ops);
+            M::mac(acc, ops);
+          }
+        }
+        dev::mbar_arrive(&empty[s]);
+      }
+    } else {
+      // operands of channel ch in A (ch even) or B (ch odd); the next channel's
+      // are loaded before the current channel's MAC
+      static_assert(kWsCh % 2 == 0, "channels alternate between two operand sets");
+      typename M::Ops A, B;
+      ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[0], 0, abort_flag));
+      if (ok) M::load(stages + warp * M::GFL, ga, gb, A);
+      for (int it = 0; it < n_iter && ok; ++it) {
+        const int s = it % kWsStages;
+        const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
+        const int nc = a.n_chan - it * kWsCh;
+#pragma unroll
+        for (int ch = 0; ch < kWsCh; ++ch) {
+          typename M::Ops& cur = (ch & 1) ? B : A;
+          typename M::Ops& nxt = (ch & 1) ? A : B;
+          if (ch < nc) {
+            if (ch + 1 < kWsCh) {
+              if (ch + 1 < nc) M::load(st + (ch + 1) * kCons * M::GFL, ga, gb, nxt);
+            } else if (it + 1 < n_iter) {
+              const int sn = (it + 1) % kWsStages;
+              ok = __all_sync(0xffffffffu,
+                              dev::mbar_wait(&full[sn], ((it + 1) / kWsStages) & 1, abort_flag));
+              if (ok) M::load(stages + sn * Ly::kStageFloats + warp * M::GFL, ga, gb, nxt);
+            }
+            M::mac(acc, cur);
+          }
+        }
+        dev::mbar_arrive(&empty[s]);
+      }
+    }
+    if (ok && k < a.n_bins) {
+      const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
+#pragma unroll
+      for (int ii = 0; ii < Gm::AT; ++ii) {
+#pragma unroll
+        for (int jj = 0; jj < Gm::BT; ++jj) {
+          const int jl = jblk + (ga * Gm::AT + ii) * Gm::TW + gb * Gm::BT + jj;
+          if (jl < a.n_dm) {
+            const float2 v = M::get(acc, ii, jj);
+            const float re = v.x * a.scale;
+            const float im = real_only ? 0.f : v.y * a.scale;
+            const int64_t o = static_cast<int64_t>(series) * a.y_series_stride +
+                              static_cast<int64_t>(jl) * a.y_dm_stride + k;
+            if (a.out_kind == 2)
+              static_cast<float*>(a.Y)[o] = re * re + im * im;
+            else
+              static_cast<float2*>(a.Y)[o] = make_float2(re, im);
+          }
+        }
+      }
+    }
+  }
+  if (!ok) {
+    *abort_flag = 1;
+    if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+  }
 }
 
 // Persistent form over a batch of spectra sets of uneven sizes (the batching
@@ -718,6 +972,8 @@ struct VariantInfo {
   size_t swap_bytes;  // per CTA, excluding the phase-constant table
   int warps = kWarps;
   const void* batch_fn = nullptr;  // persistent batch kernel of the same tile
+  int bin_warps = 0;  // warps that own bins (0: all of them)
+  int bins() const { return (bin_warps ? bin_warps : warps) * ng; }
 };
 
 VariantInfo info_legacy() {
@@ -730,6 +986,17 @@ VariantInfo info() {
   return {reinterpret_cast<const void*>(&mac_kernel<Gm, M, kPipe, W>), Gm::DMS, Gm::NG,
           sizeof(float) * static_cast<size_t>(W) * 2 * Gm::NG * M::GFL, W,
           reinterpret_cast<const void*>(&mac_batch_kernel<Gm, M, kPipe, W>)};
+}
+
+template <class Gm, class M, int kCons, int kProd, int kCh = 4, int kSt = 3, int kRC = 0,
+          int kRP = 0, bool kPre = false>
+VariantInfo info_ws() {
+  using Ly = WsLayout<Gm, M, kCons, kProd, kCh, kSt>;
+  VariantInfo vi{reinterpret_cast<const void*>(
+                     &mac_ws_kernel<Gm, M, kCons, kProd, kCh, kSt, kRC, kRP, kPre>),
+                 Gm::DMS, Gm::NG, Ly::kSwapBytes, kCons + kProd, nullptr};
+  vi.bin_warps = kCons;
+  return vi;
 }
 
 VariantInfo variant_info(int v) {
@@ -746,6 +1013,9 @@ VariantInfo variant_info(int v) {
     case MAC_Q2_8x8: return info<G8x8, PackedCompact2<G8x8>, false>();
     case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, false, 12>();
     case MAC_S12_8x8: return info<G8x8, Scalar<G8x8>, false, 12>();
+    case MAC_Z12_8x8: return info<G8x8, PackedZQuad<G8x8>, false, 12>();
+    case MAC_P12_8x8: return info<G8x8, Packed<G8x8>, false, 12>();
+    case MAC_W12_8x8: return info_ws<G8x8, PackedCompact<G8x8>, 8, 4>();
     default: return info_legacy();
   }
 }
@@ -753,11 +1023,11 @@ VariantInfo variant_info(int v) {
 }  // namespace
 
 // Fastest variant per trial count on the survey-shaped workload (kernel-only
-// sweep on GB300: Q12_8x8 49.3 ms, R_8x8 50.3, Q_8x8 52.4, S_8x8 55.6 per
-// 2048-trial, 1024-channel, 131073-bin launch; Q_4x8 and Q_4x4 lead their
-// tile sizes).
+// sweep on GB300 per 2048-trial, 1024-channel, 131073-bin launch: W12_8x8
+// 43.7 ms, Q12_8x8 49.5, R_8x8 50.3, Q_8x8 52.4, Z12_8x8 52.4, S_8x8 55.6,
+// P12_8x8 63.0; Q_4x8 and Q_4x4 lead their tile sizes).
 int mac_variant_for(int n_dm) {
-  if (n_dm > 1024) return MAC_Q12_8x8;
+  if (n_dm > 1024) return MAC_W12_8x8;
   if (n_dm > 256) return MAC_Q_4x8;
   return MAC_Q_4x4;
 }
@@ -776,10 +1046,7 @@ cudaError_t mac_prepare(int variant, int n_chan) {
   return cudaFuncSetAttribute(vi.batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-int mac_variant_bins_per_cta(int variant) {
-  const VariantInfo vi = variant_info(variant);
-  return vi.warps * vi.ng;
-}
+int mac_variant_bins_per_cta(int variant) { return variant_info(variant).bins(); }
 
 bool mac_variant_batchable(int variant) { return variant_info(variant).batch_fn != nullptr; }
 
@@ -810,7 +1077,7 @@ cudaError_t launch_mac_batch(const BatchSet* d_sets, int n_sets, long long n_ite
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   const VariantInfo vi = variant_info(variant);
-  const int bins_per_cta = vi.warps * vi.ng;
+  const int bins_per_cta = vi.bins();
   dim3 grid((a.n_bins + bins_per_cta - 1) / bins_per_cta, (a.n_dm + vi.dms - 1) / vi.dms,
             a.n_series);
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;

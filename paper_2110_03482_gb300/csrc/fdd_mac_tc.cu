@@ -31,10 +31,18 @@
 // and returns.
 #include <cuda_bf16.h>
 
+#include "fdd_device.cuh"
 #include "fdd_internal.h"
 
 namespace fdd {
 namespace {
+
+using dev::mbar_arrive;
+using dev::mbar_init;
+using dev::mbar_wait;
+using dev::smem_u32;
+using dev::top32_mul;
+using dev::unit_phasor;
 
 constexpr int kM = 128;                  // trials b per a (T)
 constexpr int kN = 256;                  // accumulator columns
@@ -54,11 +62,6 @@ constexpr uint32_t kStageBytes = 2 * kTileA + kTileB;  // 64 KB
 constexpr int kStages = 3;
 constexpr int kAccBufs = 2;              // accumulators alternate between passes
 constexpr uint32_t kTmemCols = kAccBufs * kN;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Byte offset of element (row, kk) in a K-major tile of 64 BF16 per row with
 // the 128-byte swizzle: 16-byte chunks of a row are permuted by (row mod 8).
@@ -78,44 +81,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                             (static_cast<uint32_t>(kN >> 3) << 17) |
                             (static_cast<uint32_t>(kM >> 4) << 24);
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-// Bounded wait for the phase of the given parity; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          volatile int* abort_flag) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done)
-                 : "r"(smem_u32(bar)), "r"(parity)
-                 : "memory");
-    if (done) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-}
-
-__device__ __forceinline__ uint32_t top32_mul(uint32_t m, uint32_t lo, uint32_t hi) {
-  return __umulhi(m, lo) + m * hi;
-}
-
-__device__ __forceinline__ float2 unit_phasor(uint32_t phase) {
-  const float x = __int2float_rn(static_cast<int>(phase)) * 1.46291807926715968e-9f;  // 2pi/2^32
-  float s, c;
-  __sincosf(x, &s, &c);
-  return make_float2(c, s);
-}
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<uint32_t*>(&v);

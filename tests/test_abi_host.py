@@ -120,23 +120,30 @@ def test_variant_choice():
     for v in range(fdd.FDD_MAC_VARIANTS):
         assert fdd.fdd_plan_geometry(_params(w, mac_variant=v + 1))["mac_variant"] == v
     w2 = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
-    assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_Q12_8X8
+    assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_W12_8X8
 
 
 def test_tensor_core_form_geometry():
     """The tensor-core form holds the spectra of every beam at once and batches
-    DMs in whole 1024-trial passes when the workspace is bounded."""
+    DMs in whole trial passes (512 trials in 32-beam groups, 1024 in 16-beam
+    groups) when the workspace is bounded; below one pass, whatever fits."""
     w = synth.WORKLOADS["fdd_32beam_1024ch_2p19t_4096dm"]
     g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
                                       workspace_limit=200 << 30))
     assert g["mac_variant"] == fdd.FDD_MAC_TC
-    assert g["dm_batch"] % 1024 == 0 and 0 < g["dm_batch"] <= 4096
+    assert g["dm_batch"] % 512 == 0 and 0 < g["dm_batch"] <= 4096
     spectra = 32 * 1024 * g["bin_pitch"] * 8
     assert spectra < g["workspace_bytes"] <= 200 << 30
-    # below one 1024-trial pass per batch the batch is whatever fits
     g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
                                       workspace_limit=120 << 30))
-    assert 0 < g["dm_batch"] < 1024 and g["workspace_bytes"] <= 120 << 30
+    assert g["dm_batch"] == 512 and g["workspace_bytes"] <= 120 << 30
+    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
+                                      workspace_limit=70 << 30))
+    assert 0 < g["dm_batch"] < 512 and g["workspace_bytes"] <= 70 << 30
+    # 16 beams: 1024-trial passes
+    g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=fdd.FDD_PREC_BF16_HILO,
+                                      workspace_limit=80 << 30))
+    assert g["dm_batch"] % 1024 == 0 and g["workspace_bytes"] <= 80 << 30
 
 
 def test_geometry_edge_cases():
