@@ -340,7 +340,7 @@ typedef struct fdd_batch_info {
  * mac_variant 0 and autotune != 0 the candidate kernel tiles are timed on the
  * batch's own shapes and the fastest is kept (remembered per shape in the
  * process, and in the text file named by the FDD_AUTOTUNE_CACHE environment
- * variable when set); mac_variant 0 without autotune selects Q12_8X8.
+ * variable when set); mac_variant 0 without autotune selects W12_8X8.
  * Allocates all device memory (and, while autotuning, a temporary output).
  * Layouts: the input is the beams' inputs concatenated in order (each
  * [n_t][n_chan] or [n_chan][n_t]); the output is, per beam in order,

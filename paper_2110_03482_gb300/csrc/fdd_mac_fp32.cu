@@ -584,46 +584,30 @@ struct WsLayout {
   static_assert(2 * kWsStages * 8 + 4 <= kBarBytes, "barrier area");
 };
 
-// kRegCons / kRegProd: registers per thread of the consumer / producer
-// warpgroups after a setmaxnreg split (0: no split); kPre: consumers load the
-// next channel's operands before the current channel's MAC (double buffer).
+// One work item of the warp-specialised schedule: the CTA's kCons bins
+// starting at local bin bin_tile * kCons and the trials dm_block * DMS + ..
+// of one set of spectra, with the phase table already in shared memory.
+// Stages and barrier phases continue from iteration it0 of the ring (items
+// of a persistent CTA follow one another).  kRegCons / kRegProd: registers
+// per thread of the consumer / producer warpgroups after a setmaxnreg split
+// (0: no split); kPre: consumers load the next channel's operands before the
+// current channel's MAC.  Returns false after a timeout.
 template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages, int kRegCons,
           int kRegProd, bool kPre>
-__global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const MacArgs a) {
+__device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs, float* stages,
+                                        uint64_t* full, uint64_t* empty,
+                                        volatile int* abort_flag, int bin_tile, int dm_block,
+                                        int series, uint32_t it0) {
   using Ly = WsLayout<Gm, M, kCons, kProd, kWsCh, kWsStages>;
-  static_assert(kRegCons == 0 ||
-                    (kCons % 4 == 0 && kProd % 4 == 0 &&
-                     kRegCons * kCons + kRegProd * kProd <= (65536 / ((kCons + kProd) * 32) / 8 * 8) * (kCons + kProd)),
-                "register split above the launch's registers");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
-  unsigned char* tail = smem_raw + sizeof(PhaseConst) * a.n_chan;  // 16-byte aligned
-  uint64_t* full = reinterpret_cast<uint64_t*>(tail);
-  uint64_t* empty = full + kWsStages;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kWsStages);
-  float* stages = reinterpret_cast<float*>(tail + Ly::kBarBytes);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kWsStages; ++i) {
-      dev::mbar_init(&full[i], kProd * 32);
-      dev::mbar_init(&empty[i], kCons * 32);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int i = threadIdx.x; i < a.n_chan; i += blockDim.x) pcs[i] = a.pc[i];
-  __syncthreads();
-
   const int n_iter = (a.n_chan + kWsCh - 1) / kWsCh;
-  const int jblk = blockIdx.y * Gm::DMS;
-  const int series = blockIdx.z;
-  const int k_tile = blockIdx.x * kCons;  // first local bin of the CTA
+  const int jblk = dm_block * Gm::DMS;
+  const int k_tile = bin_tile * kCons;  // first local bin of the item
   bool ok = true;
 
   if (warp >= kCons) {
     // ------------------------------------------------------------ producers
-    if (kRegCons) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegProd));
     const int pw = warp - kCons;
     constexpr int NB = Ly::kBinsPerProd;
     Generator<Gm, M> gen[NB];
@@ -643,7 +627,8 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
       for (int ch = 0; ch < kWsCh; ++ch)
         xn[q][ch] = ch < a.n_chan ? __ldg(xp[q] + ch * xs) : make_float2(0.f, 0.f);
     for (int it = 0; it < n_iter; ++it) {
-      const int s = it % kWsStages;
+      const uint32_t g = it0 + it;
+      const int s = g % kWsStages;
       float2 x[NB][kWsCh];
 #pragma unroll
       for (int q = 0; q < NB; ++q)
@@ -654,7 +639,7 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
           xn[q][ch] = c < a.n_chan ? __ldg(xp[q] + c * xs) : make_float2(0.f, 0.f);
         }
       ok = __all_sync(0xffffffffu,
-                      dev::mbar_wait(&empty[s], ((it / kWsStages) & 1) ^ 1, abort_flag));
+                      dev::mbar_wait(&empty[s], ((g / kWsStages) & 1) ^ 1, abort_flag));
       if (!ok) break;
       float* st = stages + s * Ly::kStageFloats + (pw * NB) * M::GFL;
 #pragma unroll
@@ -670,7 +655,6 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
     }
   } else {
     // ------------------------------------------------------------ consumers
-    if (kRegCons) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCons));
     const int k = k_tile + warp;  // local bin
     const int ga = lane / Gm::GB;
     const int gb = lane % Gm::GB;
@@ -678,8 +662,9 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
     M::zero(acc);
     if (!kPre) {
       for (int it = 0; it < n_iter; ++it) {
-        const int s = it % kWsStages;
-        ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (it / kWsStages) & 1, abort_flag));
+        const uint32_t g = it0 + it;
+        const int s = g % kWsStages;
+        ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kWsStages) & 1, abort_flag));
         if (!ok) break;
         const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
         const int nc = a.n_chan - it * kWsCh;
@@ -698,10 +683,15 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
       // are loaded before the current channel's MAC
       static_assert(kWsCh % 2 == 0, "channels alternate between two operand sets");
       typename M::Ops A, B;
-      ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[0], 0, abort_flag));
-      if (ok) M::load(stages + warp * M::GFL, ga, gb, A);
+      {
+        const int s0 = it0 % kWsStages;
+        ok = __all_sync(0xffffffffu,
+                        dev::mbar_wait(&full[s0], (it0 / kWsStages) & 1, abort_flag));
+        if (ok) M::load(stages + s0 * Ly::kStageFloats + warp * M::GFL, ga, gb, A);
+      }
       for (int it = 0; it < n_iter && ok; ++it) {
-        const int s = it % kWsStages;
+        const uint32_t g = it0 + it;
+        const int s = g % kWsStages;
         const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
         const int nc = a.n_chan - it * kWsCh;
 #pragma unroll
@@ -712,9 +702,10 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
             if (ch + 1 < kWsCh) {
               if (ch + 1 < nc) M::load(st + (ch + 1) * kCons * M::GFL, ga, gb, nxt);
             } else if (it + 1 < n_iter) {
-              const int sn = (it + 1) % kWsStages;
+              const uint32_t gn = g + 1;
+              const int sn = gn % kWsStages;
               ok = __all_sync(0xffffffffu,
-                              dev::mbar_wait(&full[sn], ((it + 1) / kWsStages) & 1, abort_flag));
+                              dev::mbar_wait(&full[sn], (gn / kWsStages) & 1, abort_flag));
               if (ok) M::load(stages + sn * Ly::kStageFloats + warp * M::GFL, ga, gb, nxt);
             }
             M::mac(acc, cur);
@@ -748,6 +739,104 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
   if (!ok) {
     *abort_flag = 1;
     if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+  }
+  return ok;
+}
+
+// Shared-memory carve-up of the warp-specialised kernels: phase table, then
+// the barriers and abort flag, then the stages.
+template <class Ly>
+struct WsSmem {
+  PhaseConst* pcs;
+  uint64_t* full;
+  uint64_t* empty;
+  volatile int* abort_flag;
+  float* stages;
+  template <int kWsStages>
+  __device__ __forceinline__ void init(unsigned char* raw, int n_chan, int n_cons_threads,
+                                       int n_prod_threads) {
+    pcs = reinterpret_cast<PhaseConst*>(raw);
+    unsigned char* tail = raw + sizeof(PhaseConst) * n_chan;  // 16-byte aligned
+    full = reinterpret_cast<uint64_t*>(tail);
+    empty = full + kWsStages;
+    abort_flag = reinterpret_cast<volatile int*>(empty + kWsStages);
+    stages = reinterpret_cast<float*>(tail + Ly::kBarBytes);
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < kWsStages; ++i) {
+        dev::mbar_init(&full[i], n_prod_threads);
+        dev::mbar_init(&empty[i], n_cons_threads);
+      }
+      *abort_flag = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+};
+
+template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages, int kRegCons,
+          int kRegProd, bool kPre>
+__global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const MacArgs a) {
+  using Ly = WsLayout<Gm, M, kCons, kProd, kWsCh, kWsStages>;
+  static_assert(kRegCons == 0 ||
+                    (kCons % 4 == 0 && kProd % 4 == 0 &&
+                     kRegCons * kCons + kRegProd * kProd <=
+                         (65536 / ((kCons + kProd) * 32) / 8 * 8) * (kCons + kProd)),
+                "register split above the launch's registers");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WsSmem<Ly> sm;
+  sm.template init<kWsStages>(smem_raw, a.n_chan, kCons * 32, kProd * 32);
+  for (int i = threadIdx.x; i < a.n_chan; i += blockDim.x) sm.pcs[i] = a.pc[i];
+  __syncthreads();
+  if (kRegCons) {
+    if ((threadIdx.x >> 5) >= kCons)
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegProd));
+    else
+      asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCons));
+  }
+  ws_item<Gm, M, kCons, kProd, kWsCh, kWsStages, kRegCons, kRegProd, kPre>(
+      a, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag, blockIdx.x, blockIdx.y, blockIdx.z,
+      0u);
+}
+
+// Persistent form of the warp-specialised schedule over a batch of spectra
+// sets (the batching form): CTAs pull (set, bin tile, trial block) items from
+// a global counter, numbered bin-tile-major from each set's item_begin; the
+// stage ring runs on across items; the phase table is reloaded when the set
+// changes.
+template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages>
+__global__ void __launch_bounds__((kCons + kProd) * 32, 1)
+    mac_ws_batch_kernel(const BatchSet* sets, int n_sets, int64_t n_items,
+                        unsigned long long* counter) {
+  using Ly = WsLayout<Gm, M, kCons, kProd, kWsCh, kWsStages>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long item_s;
+  const int n_chan = sets[0].args.n_chan;  // common to the batch
+  WsSmem<Ly> sm;
+  sm.template init<kWsStages>(smem_raw, n_chan, kCons * 32, kProd * 32);
+  int cur = -1;
+  uint32_t it0 = 0;
+  const uint32_t n_iter = static_cast<uint32_t>((n_chan + kWsCh - 1) / kWsCh);
+  while (true) {
+    if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(counter, 1ull));
+    __syncthreads();  // also: every stage of the previous item has been read
+    const long long item = item_s;
+    if (item >= n_items || *sm.abort_flag) break;
+    int lo = 0, hi = n_sets - 1;  // last set with item_begin <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sets[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    const BatchSet& bs = sets[lo];
+    if (lo != cur) {
+      for (int i = threadIdx.x; i < n_chan; i += blockDim.x) sm.pcs[i] = bs.args.pc[i];
+      cur = lo;
+    }
+    __syncthreads();  // phase table ready; item_s read by every thread
+    const long long local = item - bs.item_begin;
+    ws_item<Gm, M, kCons, kProd, kWsCh, kWsStages, 0, 0, false>(
+        bs.args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
+        static_cast<int>(local / bs.n_dm_blocks), static_cast<int>(local % bs.n_dm_blocks), 0,
+        it0);
+    it0 += n_iter;
   }
 }
 
@@ -994,7 +1083,8 @@ VariantInfo info_ws() {
   using Ly = WsLayout<Gm, M, kCons, kProd, kCh, kSt>;
   VariantInfo vi{reinterpret_cast<const void*>(
                      &mac_ws_kernel<Gm, M, kCons, kProd, kCh, kSt, kRC, kRP, kPre>),
-                 Gm::DMS, Gm::NG, Ly::kSwapBytes, kCons + kProd, nullptr};
+                 Gm::DMS, Gm::NG, Ly::kSwapBytes, kCons + kProd,
+                 reinterpret_cast<const void*>(&mac_ws_batch_kernel<Gm, M, kCons, kProd, kCh, kSt>)};
   vi.bin_warps = kCons;
   return vi;
 }
