@@ -31,6 +31,8 @@ struct fdd_plan_s {
   float2* d_X = nullptr;      // [n_chan][bin_pitch] their spectra
                               // (tensor-core form: [beam][n_chan][bin_pitch], every beam)
   bool tc = false;            // tensor-core form (FDD_PREC_BF16_HILO)
+  float2* d_tcx = nullptr;    // tensor-core form: bin-major spectra of a block of bins
+  size_t tcx_bytes = 0;
   int n_sms = 0;
   float2* d_Y = nullptr;      // [dm_batch][bin_pitch] dedispersed spectra (time output;
                               // tensor-core form: [beam][dm_batch][bin_pitch])
@@ -270,7 +272,8 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
 
   const size_t spectra_sets = tc ? static_cast<size_t>(p->n_beams) : 1;
   const size_t fixed = sizeof(fdd::PhaseConst) * nc + sizeof(float) * size_t(nc) * L +
-                       sizeof(float2) * size_t(nc) * g->bin_pitch * spectra_sets + 256;
+                       sizeof(float2) * size_t(nc) * g->bin_pitch * spectra_sets + 256 +
+                       (tc ? fdd::mac_tc_scratch_bytes(p->n_beams, nc, n_bins) : 0);
   const size_t limit = p->workspace_limit ? p->workspace_limit : kDefaultWorkspace;
   int64_t batch = p->n_dm;
   size_t per_dm = 0;
@@ -300,7 +303,7 @@ void release(fdd_plan_s* P) {
   if (P->has_c2r) cufftDestroy(P->c2r);
   if (P->has_c2r_tail) cufftDestroy(P->c2r_tail);
   void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_fftwork, P->d_status,
-                  P->d_in_stage, P->d_out_stage};
+                  P->d_in_stage, P->d_out_stage, P->d_tcx};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->prof_ev)
@@ -469,7 +472,8 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.real_bin_b = static_cast<int>(g.fft_len / 2);
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
-          FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, s));
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, P->d_tcx,
+                                      P->tcx_bytes, s));
         }
         cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
         const int64_t keep = (g.out_len - c * g.hop) < g.hop ? (g.out_len - c * g.hop) : g.hop;
@@ -509,7 +513,8 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.Y = static_cast<float*>(d_out) + off;
       }
       StageTimer t(P, FDD_STAGE_MAC, s);
-      FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, s));
+      FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, P->d_tcx,
+                                      P->tcx_bytes, s));
     }
   }
   return FDD_OK;
@@ -611,6 +616,10 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_xw), sizeof(float) * size_t(nc) * g.fft_len)))
     return st;
   const size_t sets = P->tc ? static_cast<size_t>(p->n_beams) : 1;
+  if (P->tc) {
+    P->tcx_bytes = fdd::mac_tc_scratch_bytes(p->n_beams, nc, g.n_bins);
+    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_tcx), P->tcx_bytes))) return st;
+  }
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_X),
                       sizeof(float2) * size_t(nc) * g.bin_pitch * sets)))
     return st;
@@ -728,6 +737,9 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
     return fail(FDD_ERR_INVALID_ARG, "trial range outside the plan's list");
   if (out_kind != FDD_OUT_SPECTRA && out_kind != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "out_kind must be FDD_OUT_SPECTRA or FDD_OUT_POWER");
+  if (plan->tc && sizeof(float2) * static_cast<size_t>(n_series) * plan->p.n_chan > plan->tcx_bytes)
+    return fail(FDD_ERR_UNSUPPORTED,
+                "n_series x n_chan spectra of one bin exceed the tensor-core form's scratch");
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
   fdd::MacArgs m{};
@@ -752,6 +764,7 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
   StageTimer t(plan, FDD_STAGE_MAC, reinterpret_cast<cudaStream_t>(stream));
   if (plan->tc)
     FDD_CUDA(fdd::launch_mac_tc(m, plan->p.precision == FDD_PREC_BF16_HILO, plan->n_sms,
+                                plan->d_tcx, plan->tcx_bytes,
                                 reinterpret_cast<cudaStream_t>(stream)));
   else
     FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));

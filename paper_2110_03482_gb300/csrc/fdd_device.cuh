@@ -43,6 +43,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
                : "memory");
 }
 
+// One arrive for the whole (converged) warp: __syncwarp orders every lane's
+// earlier shared-memory accesses before lane 0's release arrive, so a barrier
+// counts warps instead of threads (fewer same-address atomics per phase).
+__device__ __forceinline__ void mbar_arrive_warp(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
 // Bounded wait for the phase of the given parity; false on timeout or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
                                           volatile int* abort_flag) {

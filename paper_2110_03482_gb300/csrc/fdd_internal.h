@@ -21,6 +21,8 @@ struct MacArgs {
   const float2* X;          // [n_series][n_chan][x_chan_stride]
   int64_t x_series_stride;  // complex elements
   int64_t x_chan_stride;    // complex elements
+  int64_t x_bin_stride;     // complex elements between bins; read by the tensor-core
+                            // kernel only (the FP32 kernels take bins contiguous)
   const PhaseConst* pc;     // [n_chan]
   int n_chan;
   int n_bins;               // bins handled by this call (local indices 0 .. n_bins-1)
@@ -90,7 +92,27 @@ cudaError_t mac_tc_prepare();
 // Beams per tensor-core group: 16 when a call has at most 16 series (then a
 // pass covers 1024 trials), else 32 (512 trials per pass).
 int mac_tc_beams_per_group(int n_series);
-cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s);
+// The tensor-core kernel reads the spectra bin-major, X_T[k][series][chan]
+// (a 256-byte row per 32 channels of one beam); launch_mac_tc takes them in
+// the [series][chan][pitch] layout (x_series_stride = n_chan x_chan_stride)
+// and transposes them, a block of bins at a time, into `scratch` before each
+// block's launch.  mac_tc_scratch_bytes: the scratch a plan allocates for
+// n_series x n_chan spectra of n_bins bins (at most 2 GiB, at least one bin).
+size_t mac_tc_scratch_bytes(int n_series, int n_chan, int64_t n_bins);
+cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scratch,
+                          size_t scratch_bytes, cudaStream_t s);
+
+// Bins k0 .. k0 + n_bins - 1 of `rows` complex rows of stride in_stride into
+// out[k][row] (bin-major), for the tensor-core kernel.
+struct BinTransposeArgs {
+  const float2* in;      // row r, bin k at in + r * in_stride + k
+  int64_t in_stride;
+  int64_t rows;
+  int64_t k0;
+  int n_bins;
+  float2* out;           // [n_bins][rows]
+};
+cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s);
 
 // Shared with the allocation-free entry point (fdd_noalloc.cu): the last-error
 // setter and the exact 64-bit fixed-point phase rate frac(m * rate / L) * 2^64.

@@ -568,9 +568,9 @@ __global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
 // Z and P from shared memory and accumulate, while kProd producer warps
 // evaluate Z_a = X Q_a and P_b for every consumer's bin, kWsCh channels at a
 // time, into a ring of kWsStages stages.  A pair of mbarriers per stage orders
-// the two sides (full: every producer thread has written the stage; empty:
-// every consumer thread has read it).  Every wait is bounded; a timeout stops
-// both sides and is reported in the status word.
+// the two sides (full: every producer warp has written the stage; empty:
+// every consumer warp has read it; one arrive per warp).  Every wait is
+// bounded; a timeout stops both sides and is reported in the status word.
 template <class Gm, class M, int kCons, int kProd, int kWsCh = 4, int kWsStages = 3>
 struct WsLayout {
   static_assert(Gm::NG == 1, "one bin per consumer warp");
@@ -651,7 +651,7 @@ __device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs,
           for (int q = 0; q < NB; ++q) gen[q].run(p, x[q][ch], st + (ch * kCons + q) * M::GFL);
         }
       }
-      dev::mbar_arrive(&full[s]);
+      dev::mbar_arrive_warp(&full[s]);
     }
   } else {
     // ------------------------------------------------------------ consumers
@@ -676,7 +676,7 @@ __device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs,
             M::mac(acc, ops);
           }
         }
-        dev::mbar_arrive(&empty[s]);
+        dev::mbar_arrive_warp(&empty[s]);
       }
     } else {
       // operands of channel ch in A (ch even) or B (ch odd); the next channel's
@@ -711,7 +711,7 @@ __device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs,
             M::mac(acc, cur);
           }
         }
-        dev::mbar_arrive(&empty[s]);
+        dev::mbar_arrive_warp(&empty[s]);
       }
     }
     if (ok && k < a.n_bins) {
@@ -753,8 +753,8 @@ struct WsSmem {
   volatile int* abort_flag;
   float* stages;
   template <int kWsStages>
-  __device__ __forceinline__ void init(unsigned char* raw, int n_chan, int n_cons_threads,
-                                       int n_prod_threads) {
+  __device__ __forceinline__ void init(unsigned char* raw, int n_chan, int n_cons_warps,
+                                       int n_prod_warps) {
     pcs = reinterpret_cast<PhaseConst*>(raw);
     unsigned char* tail = raw + sizeof(PhaseConst) * n_chan;  // 16-byte aligned
     full = reinterpret_cast<uint64_t*>(tail);
@@ -763,8 +763,8 @@ struct WsSmem {
     stages = reinterpret_cast<float*>(tail + Ly::kBarBytes);
     if (threadIdx.x == 0) {
       for (int i = 0; i < kWsStages; ++i) {
-        dev::mbar_init(&full[i], n_prod_threads);
-        dev::mbar_init(&empty[i], n_cons_threads);
+        dev::mbar_init(&full[i], n_prod_warps);  // one arrive per warp
+        dev::mbar_init(&empty[i], n_cons_warps);
       }
       *abort_flag = 0;
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const M
                 "register split above the launch's registers");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WsSmem<Ly> sm;
-  sm.template init<kWsStages>(smem_raw, a.n_chan, kCons * 32, kProd * 32);
+  sm.template init<kWsStages>(smem_raw, a.n_chan, kCons, kProd);
   for (int i = threadIdx.x; i < a.n_chan; i += blockDim.x) sm.pcs[i] = a.pc[i];
   __syncthreads();
   if (kRegCons) {
@@ -811,7 +811,7 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1)
   __shared__ long long item_s;
   const int n_chan = sets[0].args.n_chan;  // common to the batch
   WsSmem<Ly> sm;
-  sm.template init<kWsStages>(smem_raw, n_chan, kCons * 32, kProd * 32);
+  sm.template init<kWsStages>(smem_raw, n_chan, kCons, kProd);
   int cur = -1;
   uint32_t it0 = 0;
   const uint32_t n_iter = static_cast<uint32_t>((n_chan + kWsCh - 1) / kWsCh);

@@ -25,7 +25,7 @@
 // straight into the 128-byte-swizzled K-major shared layout the MMA
 // descriptors address, through a 3-stage mbarrier ring; 4 epilogue warps read
 // one accumulator back (tcgen05.ld) and store it while the MMAs of the next
-// pass fill the other.
+// pass fill the other.  Barriers count warps (one arrive per warp).
 // Every wait is bounded: on timeout the kernel records FDD_ERR_TIMEOUT in the
 // status word, stops, drains its own MMAs (bounded), frees its tensor memory
 // and returns.
@@ -38,6 +38,7 @@ namespace fdd {
 namespace {
 
 using dev::mbar_arrive;
+using dev::mbar_arrive_warp;
 using dev::mbar_init;
 using dev::mbar_wait;
 using dev::smem_u32;
@@ -121,12 +122,12 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&full[i], kProd);
+      mbar_init(&full[i], kProdWarps);  // one arrive per producer warp
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], kEpi);
+      mbar_init(&acc_empty[i], kEpiWarps);  // one arrive per epilogue warp
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     // ------------------------------------------------------------ epilogue
     // Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (trials b), all 256
     // columns (a, beta, re|im) of the pass's accumulator, and stores Y.
-    const int quarter = warp & 3;
+    const int quarter = warp & 3;  // the lanes this warp may read
     const int b = quarter * 32 + lane;
     uint32_t p = 0;
     bool ok = true;
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&acc_empty[buf]);
+        mbar_arrive_warp(&acc_empty[buf]);
       }
     }
     if (!ok) {
@@ -298,8 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           for (int m = 0; m < kBeamsPerWarp; ++m) {
             const int bg = group * kBeams + pw + kProdWarps * m;
             x_next[m] = (nu < a.n_chan && bg < a.n_series)
-                            ? __ldg(a.X + static_cast<int64_t>(bg) * a.x_series_stride +
-                                    static_cast<int64_t>(nu) * a.x_chan_stride + k)
+                            ? __ldg(a.X + static_cast<int64_t>(k) * a.x_bin_stride +
+                                    static_cast<int64_t>(bg) * a.x_series_stride +
+                                    static_cast<int64_t>(nu) * a.x_chan_stride)
                             : make_float2(0.f, 0.f);
           }
         }
@@ -317,8 +319,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             for (int m = 0; m < kBeamsPerWarp; ++m) {
               const int bg = group * kBeams + pw + kProdWarps * m;
               x_next[m] = (nn < a.n_chan && bg < a.n_series)
-                              ? __ldg(a.X + static_cast<int64_t>(bg) * a.x_series_stride +
-                                      static_cast<int64_t>(nn) * a.x_chan_stride + k)
+                              ? __ldg(a.X + static_cast<int64_t>(k) * a.x_bin_stride +
+                                      static_cast<int64_t>(bg) * a.x_series_stride +
+                                      static_cast<int64_t>(nn) * a.x_chan_stride)
                               : make_float2(0.f, 0.f);
             }
           }
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                             __fmul2_rn(qa, make_float2(r128.x, r128.x)));
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(&full[st]);
+          mbar_arrive_warp(&full[st]);
         }
       }
     }
@@ -416,8 +419,45 @@ cudaError_t mac_tc_prepare() {
   return cudaSuccess;
 }
 
-cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s) {
+static cudaError_t launch_mac_tc_block(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s);
+
+size_t mac_tc_scratch_bytes(int n_series, int n_chan, int64_t n_bins) {
+  const size_t per_bin = sizeof(float2) * static_cast<size_t>(n_series) * n_chan;
+  const size_t cap = size_t(2) << 30;
+  int64_t kb = static_cast<int64_t>(cap / per_bin);
+  if (kb < 1) kb = 1;
+  if (kb > n_bins) kb = n_bins;
+  return per_bin * static_cast<size_t>(kb);
+}
+
+cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scratch,
+                          size_t scratch_bytes, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
+  if (a.x_series_stride != a.x_chan_stride * a.n_chan) return cudaErrorInvalidValue;
+  const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
+  const int64_t kb = static_cast<int64_t>(scratch_bytes / (sizeof(float2) * rows));
+  if (!scratch || kb < 1) return cudaErrorInvalidValue;
+  const size_t y_elem = a.out_kind == 2 ? sizeof(float) : sizeof(float2);
+  for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb) {
+    const int nb = static_cast<int>((a.n_bins - k0) < kb ? (a.n_bins - k0) : kb);
+    BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, scratch};
+    cudaError_t e = launch_bin_transpose(t, s);
+    if (e != cudaSuccess) return e;
+    MacArgs b = a;
+    b.X = scratch;
+    b.x_bin_stride = rows;
+    b.x_series_stride = a.n_chan;
+    b.x_chan_stride = 1;
+    b.n_bins = nb;
+    b.k_begin = a.k_begin + static_cast<int>(k0);
+    b.Y = static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0);
+    e = launch_mac_tc_block(b, hi_lo, n_sms, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t launch_mac_tc_block(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s) {
   const int grid = a.n_bins < n_sms ? a.n_bins : n_sms;
   MacArgs args = a;
   void* params[] = {&args};

@@ -3,7 +3,8 @@
 //    also cutting one overlap-save chunk: a time-major [n_t][n_chan] u8/f32
 //    beam becomes channel-major float series of L samples, zero beyond n_t;
 //  * scatter: apply_scaling of Algorithm 1 (1/L) and keep the first n_keep
-//    samples of each inverse-transformed DM series (discard rule, Sect. 2.2).
+//    samples of each inverse-transformed DM series (discard rule, Sect. 2.2);
+//  * bin transpose: spectra [row][bin] -> [bin][row] for the tensor-core form.
 #include "fdd_internal.h"
 #include "fdd.h"
 
@@ -68,7 +69,45 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float* __restrict__ 
     d[n] = s[n] * scale;
 }
 
+// 32 bins x 32 rows through shared memory: coalesced reads along bins,
+// coalesced writes along rows.  Rows beyond gridDim.y tiles are covered by a
+// grid-stride loop.
+__global__ void __launch_bounds__(256) bin_transpose_kernel(const float2* __restrict__ in,
+                                                            int64_t in_stride, int64_t rows,
+                                                            int64_t k0, int n_bins,
+                                                            float2* __restrict__ out) {
+  __shared__ float2 tile[kTile][kTile + 1];
+  const int kb0 = blockIdx.x * kTile;
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTile; r0 < rows;
+       r0 += static_cast<int64_t>(gridDim.y) * kTile) {
+#pragma unroll
+    for (int i = threadIdx.y; i < kTile; i += 8) {
+      const int64_t r = r0 + i;
+      const int kb = kb0 + threadIdx.x;
+      if (r < rows && kb < n_bins) tile[i][threadIdx.x] = in[r * in_stride + k0 + kb];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = threadIdx.y; i < kTile; i += 8) {
+      const int kb = kb0 + i;
+      const int64_t r = r0 + threadIdx.x;
+      if (r < rows && kb < n_bins) out[static_cast<int64_t>(kb) * rows + r] = tile[threadIdx.x][i];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s) {
+  if (a.n_bins <= 0 || a.rows <= 0) return cudaSuccess;
+  const int64_t row_tiles = (a.rows + kTile - 1) / kTile;
+  dim3 grid((a.n_bins + kTile - 1) / kTile,
+            static_cast<unsigned>(row_tiles < 65535 ? row_tiles : 65535));
+  bin_transpose_kernel<<<grid, dim3(kTile, 8), 0, s>>>(a.in, a.in_stride, a.rows, a.k0,
+                                                      a.n_bins, a.out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t s) {
   if (a.in_layout == FDD_LAYOUT_TIME_MAJOR) {
