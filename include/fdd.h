@@ -218,11 +218,17 @@ fdd_status fdd_execute_dm_range(fdd_plan_t plan, const void* d_in, int32_t dm_fi
                                 int32_t n_dm, void* d_out, fdd_stream_t stream);
 
 /*
- * End-to-end call with HOST buffers: copies h_in to the device, runs
- * fdd_execute and copies the result back into h_out, all on the stream
- * (page-locked host buffers make the copies asynchronous; the call returns
- * after enqueueing them).  The device staging buffers are allocated on the
- * first call of this function for the plan and reused afterwards.
+ * End-to-end call with HOST buffers: h_in (layout of fdd_execute's d_in) to
+ * the device, fdd_execute, and the result back into h_out (layout of d_out).
+ * The copies run on two plan-owned streams as a pipeline over (beam, chunk)
+ * units: each unit's new input samples go up before it is computed and its
+ * output comes back right after, so copies overlap the computation of the
+ * neighbouring units.  Events order the copy streams with `stream`: they
+ * start after the work already queued on it, and `stream` waits for the last
+ * copy, so synchronising `stream` covers the whole call.  Page-locked host
+ * buffers make the copies asynchronous (the call returns after enqueueing);
+ * both buffers must stay valid until then.  The device staging buffers,
+ * streams and events are created on the first call for the plan and reused.
  * Errors: as fdd_execute, plus FDD_ERR_ALLOC on the first call.
  */
 fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_stream_t stream);

@@ -44,6 +44,10 @@ struct fdd_plan_s {
   int c2r_tail_batch = 0;
   void* d_in_stage = nullptr;
   void* d_out_stage = nullptr;
+  // fdd_execute_host: copy streams and the events that order them with the
+  // compute stream (created on its first call)
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  std::vector<cudaEvent_t> pipe_ev;
   size_t bytes_held = 0;
   // profiling: event pairs around stage launches (fdd_profile_enable)
   bool prof_on = false;
@@ -308,6 +312,10 @@ void release(fdd_plan_s* P) {
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->prof_ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->pipe_ev)
+    if (e) cudaEventDestroy(e);
+  if (P->h2d) cudaStreamDestroy(P->h2d);
+  if (P->d2h) cudaStreamDestroy(P->d2h);
   delete P;
 }
 
@@ -331,11 +339,81 @@ fdd_status check_device(const fdd_plan_s* P) {
   return FDD_OK;
 }
 
+// Host-buffer execution (fdd_execute_host) as a pipeline: before a (beam,
+// chunk) unit is computed, the input samples it reads that are not on the
+// device yet go up on the h2d stream and the compute stream waits for them;
+// after the unit, the d2h stream waits for it and brings its output back.
+// Copies of one unit thus overlap the computation of its neighbours.
+struct HostPipe {
+  fdd_plan_s* P;
+  const char* h_in;
+  char* h_out;
+  std::vector<int64_t> copied;  // per beam: first input sample not yet sent
+  size_t next_ev = 0;
+
+  cudaEvent_t event() { return P->pipe_ev[next_ev++]; }
+
+  fdd_status before(int b, int64_t c, cudaStream_t s) {
+    const fdd_params& p = P->p;
+    const fdd_info& g = P->info;
+    const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
+    int64_t end = c * g.hop + g.fft_len;
+    if (end > p.n_t) end = p.n_t;
+    if (copied[b] >= end) return FDD_OK;
+    const int64_t t0 = copied[b];
+    const size_t beam_off = esz * static_cast<size_t>(p.n_t) * p.n_chan * b;
+    const char* src = h_in + beam_off;
+    char* dst = static_cast<char*>(P->d_in_stage) + beam_off;
+    if (p.in_layout == FDD_LAYOUT_TIME_MAJOR) {
+      const size_t off = esz * static_cast<size_t>(t0) * p.n_chan;
+      FDD_CUDA(cudaMemcpyAsync(dst + off, src + off, esz * static_cast<size_t>(end - t0) * p.n_chan,
+                               cudaMemcpyHostToDevice, P->h2d));
+    } else {
+      const size_t pitch = esz * static_cast<size_t>(p.n_t);
+      FDD_CUDA(cudaMemcpy2DAsync(dst + esz * t0, pitch, src + esz * t0, pitch,
+                                 esz * static_cast<size_t>(end - t0), p.n_chan,
+                                 cudaMemcpyHostToDevice, P->h2d));
+    }
+    copied[b] = end;
+    cudaEvent_t e = event();
+    FDD_CUDA(cudaEventRecord(e, P->h2d));
+    FDD_CUDA(cudaStreamWaitEvent(s, e, 0));
+    return FDD_OK;
+  }
+
+  // Output of beams b0 .. b0 + nb - 1 for chunk c (the whole DM list).
+  fdd_status after(int b0, int nb, int64_t c, cudaStream_t s) {
+    const fdd_params& p = P->p;
+    const fdd_info& g = P->info;
+    cudaEvent_t e = event();
+    FDD_CUDA(cudaEventRecord(e, s));
+    FDD_CUDA(cudaStreamWaitEvent(P->d2h, e, 0));
+    const char* d_out = static_cast<const char*>(P->d_out_stage);
+    if (p.output == FDD_OUT_TIME) {
+      int64_t keep = g.out_len - c * g.hop;
+      if (keep > g.hop) keep = g.hop;
+      const size_t pitch = sizeof(float) * static_cast<size_t>(g.out_len);
+      const size_t off = sizeof(float) * (static_cast<size_t>(b0) * p.n_dm * g.out_len + c * g.hop);
+      FDD_CUDA(cudaMemcpy2DAsync(h_out + off, pitch, d_out + off, pitch, sizeof(float) * keep,
+                                 static_cast<size_t>(nb) * p.n_dm, cudaMemcpyDeviceToHost,
+                                 P->d2h));
+    } else {
+      const size_t esz = p.output == FDD_OUT_SPECTRA ? 8 : 4;
+      const size_t block = esz * static_cast<size_t>(p.n_dm) * g.n_bins;  // one beam, one chunk
+      const size_t pitch = block * g.n_chunks;                          // between beams
+      const size_t off = pitch * b0 + block * c;
+      FDD_CUDA(cudaMemcpy2DAsync(h_out + off, pitch, d_out + off, pitch, block, nb,
+                                 cudaMemcpyDeviceToHost, P->d2h));
+    }
+    return FDD_OK;
+  }
+};
+
 fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
-                  cudaStream_t s);
+                  cudaStream_t s, HostPipe* hp);
 
 fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
-               cudaStream_t s) {
+               cudaStream_t s, HostPipe* hp = nullptr) {
   const fdd_params& p = P->p;
   const fdd_info& g = P->info;
   const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
@@ -343,11 +421,13 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
   FDD_CUFFT(cufftSetStream(P->r2c, s));
   if (P->has_c2r) FDD_CUFFT(cufftSetStream(P->c2r, s));
   if (P->has_c2r_tail) FDD_CUFFT(cufftSetStream(P->c2r_tail, s));
-  if (P->tc) return run_tc(P, d_in, dm_first, n_dm, d_out, s);
+  if (P->tc) return run_tc(P, d_in, dm_first, n_dm, d_out, s, hp);
+  fdd_status pst;
 
   for (int b = 0; b < p.n_beams; ++b) {
     const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
     for (int64_t c = 0; c < g.n_chunks; ++c) {
+      if (hp && (pst = hp->before(b, c, s)) != FDD_OK) return pst;
       fdd::UnpackArgs ua{in_b, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop, g.fft_len,
                          P->d_xw, g.fft_len};
       {
@@ -420,6 +500,7 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
         StageTimer t(P, FDD_STAGE_MAC, s);
         FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
       }
+      if (hp && (pst = hp->after(b, 1, c, s)) != FDD_OK) return pst;
     }
   }
   return FDD_OK;
@@ -428,7 +509,8 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
 // Tensor-core form: every beam of a chunk is transformed first, then one
 // launch dedisperses all of them at once (the beams share each bin's phasors).
 fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
-                  cudaStream_t s) {
+                  cudaStream_t s, HostPipe* hp) {
+  fdd_status pst;
   const fdd_params& p = P->p;
   const fdd_info& g = P->info;
   const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
@@ -436,6 +518,7 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
   const int64_t set_elems = static_cast<int64_t>(p.n_chan) * g.bin_pitch;
   for (int64_t c = 0; c < g.n_chunks; ++c) {
     for (int b = 0; b < p.n_beams; ++b) {
+      if (hp && (pst = hp->before(b, c, s)) != FDD_OK) return pst;
       const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
       fdd::UnpackArgs ua{in_b, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop, g.fft_len,
                          P->d_xw, g.fft_len};
@@ -516,6 +599,7 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
       FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, P->d_tcx,
                                       P->tcx_bytes, s));
     }
+    if (hp && (pst = hp->after(0, p.n_beams, c, s)) != FDD_OK) return pst;
   }
   return FDD_OK;
 }
@@ -711,11 +795,29 @@ fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_
   const size_t out_bytes = static_cast<size_t>(plan->info.out_bytes);
   if (!plan->d_in_stage && (st = dev_alloc(plan, &plan->d_in_stage, in_bytes))) return st;
   if (!plan->d_out_stage && (st = dev_alloc(plan, &plan->d_out_stage, out_bytes))) return st;
+  const fdd_info& g = plan->info;
+  const size_t n_ev = 2 * static_cast<size_t>(plan->p.n_beams) * g.n_chunks + 2;
+  if (!plan->h2d) FDD_CUDA(cudaStreamCreateWithFlags(&plan->h2d, cudaStreamNonBlocking));
+  if (!plan->d2h) FDD_CUDA(cudaStreamCreateWithFlags(&plan->d2h, cudaStreamNonBlocking));
+  while (plan->pipe_ev.size() < n_ev) {
+    cudaEvent_t e = nullptr;
+    FDD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    plan->pipe_ev.push_back(e);
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  FDD_CUDA(cudaMemcpyAsync(plan->d_in_stage, h_in, in_bytes, cudaMemcpyHostToDevice, s));
-  st = run(plan, plan->d_in_stage, 0, plan->p.n_dm, plan->d_out_stage, s);
+  HostPipe hp{plan, static_cast<const char*>(h_in), static_cast<char*>(h_out),
+              std::vector<int64_t>(plan->p.n_beams, 0), 0};
+  // the copy streams start after the work already queued on the caller's stream
+  cudaEvent_t e0 = hp.event();
+  FDD_CUDA(cudaEventRecord(e0, s));
+  FDD_CUDA(cudaStreamWaitEvent(plan->h2d, e0, 0));
+  FDD_CUDA(cudaStreamWaitEvent(plan->d2h, e0, 0));
+  st = run(plan, plan->d_in_stage, 0, plan->p.n_dm, plan->d_out_stage, s, &hp);
   if (st != FDD_OK) return st;
-  FDD_CUDA(cudaMemcpyAsync(h_out, plan->d_out_stage, out_bytes, cudaMemcpyDeviceToHost, s));
+  // and the caller's stream ends after the last copy back
+  cudaEvent_t e1 = hp.event();
+  FDD_CUDA(cudaEventRecord(e1, plan->d2h));
+  FDD_CUDA(cudaStreamWaitEvent(s, e1, 0));
   return FDD_OK;
 }
 

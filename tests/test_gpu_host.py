@@ -1,0 +1,89 @@
+"""fdd_execute_host (host buffers, copies pipelined with the computation over
+(beam, chunk) units on two plan-owned streams) gives bit for bit what
+fdd_execute gives on device buffers (GB300 only): both layouts, every output
+kind, several beams and chunks, the tensor-core form, back-to-back calls
+with different inputs, and pageable host memory."""
+import numpy as np
+import pytest
+
+import paper_2110_03482_gb300 as fdd
+import synth
+from gpu_util import params_for
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fdd.build()
+
+
+def _workload(n_beams, output, dtype="u8", chunk_len=2048, n_t=7000):
+    return synth.Workload(name="host", n_chan=40, band_lo_mhz=400.0, band_hi_mhz=500.0,
+                          t_samp_s=1e-3, n_t=n_t, dtype=dtype, dm0=0.0, ddm=1.0, n_dm=90,
+                          chunk_len=chunk_len, n_beams=n_beams, output=output,
+                          pulses_per_beam=1,
+                          noise_mean=128.0 if dtype == "u8" else 0.0,
+                          noise_sigma=16.0 if dtype == "u8" else 1.0)
+
+
+def _inputs(w, layout, seed):
+    fbs = [synth.filterbank(w, seed=seed, beam=b)[0] for b in range(w.n_beams)]
+    if layout == fdd.FDD_LAYOUT_CHAN_MAJOR:
+        fbs = [np.ascontiguousarray(f.T) for f in fbs]
+    return np.ascontiguousarray(np.stack(fbs))
+
+
+def _out_like(info, output, device):
+    shape = (info["out_elems"], 2) if output == fdd.FDD_OUT_SPECTRA else (info["out_elems"],)
+    if device:
+        return torch.empty(shape, dtype=torch.float32, device="cuda")
+    return torch.empty(shape, dtype=torch.float32).pin_memory()
+
+
+@pytest.mark.parametrize("output,layout,n_beams,precision", [
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 1, fdd.FDD_PREC_FP32),
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_CHAN_MAJOR, 2, fdd.FDD_PREC_FP32),
+    (fdd.FDD_OUT_SPECTRA, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_FP32),
+    (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_CHAN_MAJOR, 2, fdd.FDD_PREC_FP32),
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 5, fdd.FDD_PREC_BF16_HILO),
+    (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_BF16_HILO),
+])
+def test_host_pipeline_equals_device_execute(output, layout, n_beams, precision):
+    out_name = {fdd.FDD_OUT_TIME: "time", fdd.FDD_OUT_SPECTRA: "spectra",
+                fdd.FDD_OUT_POWER: "power"}[output]
+    w = _workload(n_beams, out_name)
+    with fdd.Plan(**params_for(w, in_layout=layout, precision=precision)) as plan:
+        info = plan.info
+        assert info["n_chunks"] >= 3
+        stream = torch.cuda.current_stream()
+        results = []
+        for seed in (1, 2):  # back-to-back calls reuse the pipeline
+            x = _inputs(w, layout, seed)
+            d_out = _out_like(info, output, True)
+            plan.execute(torch.from_numpy(x).cuda(), d_out)
+            h_in = torch.from_numpy(x.reshape(-1)).pin_memory()
+            h_out = _out_like(info, output, False)
+            h_out.fill_(float("nan"))
+            plan.execute_host(h_in, h_out, stream)
+            results.append((d_out, h_out, h_in))  # h_in stays alive until the sync
+        stream.synchronize()
+        for d_out, h_out, _ in results:
+            assert torch.equal(d_out.cpu(), h_out)
+
+
+def test_host_pipeline_pageable_memory_and_single_chunk():
+    w = _workload(2, "time", dtype="f32", chunk_len=0, n_t=3000)
+    x = _inputs(w, fdd.FDD_LAYOUT_TIME_MAJOR, 7)
+    with fdd.Plan(**params_for(w)) as plan:
+        info = plan.info
+        d_out = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
+        plan.execute(torch.from_numpy(x).cuda(), d_out)
+        h_out = torch.empty(info["out_elems"], dtype=torch.float32)  # pageable
+        plan.execute_host(torch.from_numpy(x.reshape(-1)), h_out)
+        torch.cuda.synchronize()
+        assert torch.equal(d_out.cpu(), h_out)
