@@ -618,6 +618,8 @@ def run_batch(args) -> None:
                        "output": bw.output, "waves": info["n_waves"],
                        "work_items": info["work_items"], "ctas": info["ctas"],
                        "tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]],
+                       "tail_tile": (fdd.MAC_VARIANT_NAMES[info["tail_variant"]]
+                                     if info["tail_variant"] >= 0 else None),
                        "autotune_ms": info["autotune_ms"], "plan_seconds": plan_s},
             "fp32_frac_whole_step": FLOPS_PER_MAC * macs / (ms / 1e3) / peak,
             "macs_per_step": macs, "clocks": clk}

@@ -324,11 +324,15 @@ typedef struct fdd_batch_info {
   int64_t out_elems;       /* elements of the concatenated output                */
   int64_t out_bytes;
   int64_t workspace_bytes; /* device bytes held by the batch plan                */
-  int64_t work_items;      /* (beam, bin tile, trial block) items per execute    */
-  int32_t n_waves;         /* persistent launches per execute                    */
+  int64_t work_items;      /* (beam, bin tile, trial block) items per execute,
+                              tail items included                                */
+  int32_t n_waves;         /* waves (one or two persistent launches each)        */
   int32_t mac_variant;     /* kernel tile in use (FDD_MAC_*)                     */
-  int32_t ctas;            /* CTAs of each persistent launch                     */
-  int32_t reserved;
+  int32_t ctas;            /* CTAs of each persistent launch of that tile        */
+  int32_t tail_variant;    /* tile of the ragged last trial blocks (FDD_MAC_*), or
+                              -1: with a 2048-trial tile, a beam's last block of
+                              1024 or fewer trials runs in a second persistent
+                              launch on this tile's 128-trial blocks            */
   double autotune_ms[FDD_MAC_VARIANTS]; /* timed candidates (ms), -1 if untimed */
 } fdd_batch_info;
 

@@ -148,7 +148,7 @@ class fdd_batch_info(ctypes.Structure):
         ("n_waves", ctypes.c_int32),
         ("mac_variant", ctypes.c_int32),
         ("ctas", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tail_variant", ctypes.c_int32),
         ("autotune_ms", ctypes.c_double * FDD_MAC_VARIANTS),
     ]
 

@@ -34,6 +34,8 @@ struct fdd_batch_s {
   int n_sms = 0;
   int variant = 0;
   int ctas = 0;
+  int tail_variant = -1;  // tile of the ragged last trial blocks, -1: none
+  int tail_ctas = 0;
   double tune_ms[FDD_MAC_VARIANTS];
   // per beam
   std::vector<int64_t> L, n_bins, pitch, in_off, out_off, spec_off;
@@ -44,6 +46,11 @@ struct fdd_batch_s {
     long long n_items = 0;
     fdd::BatchSet* d_sets = nullptr;
     std::vector<fdd::BatchSet> h_sets;
+    // ragged last trial blocks of 1024 or fewer trials, on the tail tile
+    long long n_tail_items = 0;
+    fdd::BatchSet* d_tail = nullptr;
+    std::vector<fdd::BatchSet> h_tail;
+    std::vector<int> tail_beam;  // beam of each tail set
   };
   std::vector<Wave> waves;
   int64_t in_elems = 0, out_elems = 0;
@@ -85,8 +92,10 @@ void release(fdd_batch_s* B) {
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   for (auto& kv : B->r2c) cufftDestroy(kv.second);
-  for (auto& w : B->waves)
+  for (auto& w : B->waves) {
     if (w.d_sets) cudaFree(w.d_sets);
+    if (w.d_tail) cudaFree(w.d_tail);
+  }
   void* ptrs[] = {B->d_pc, B->d_xw, B->d_pool, B->d_counter, B->d_fftwork};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -104,17 +113,24 @@ fdd_status alloc(fdd_batch_s* B, void** p, size_t bytes) {
   return FDD_OK;
 }
 
-// Sets the output pointers of every work set for the given output buffer.
+// Sets the output pointers of every work set for the given output buffer: a
+// set's row 0 is trial j_begin of its beam.
+// (`origin`: output element at d_out, nonzero for a buffer that holds only
+// the beams from some beam on)
+void bind_set(const fdd_batch_s* B, fdd::BatchSet& bs, int b, void* d_out, int64_t origin = 0) {
+  fdd::MacArgs& m = bs.args;
+  const int64_t off = B->out_off[b] - origin + static_cast<int64_t>(m.j_begin) * B->n_bins[b];
+  if (B->p.output == FDD_OUT_SPECTRA)
+    m.Y = static_cast<float2*>(d_out) + off;
+  else
+    m.Y = static_cast<float*>(d_out) + off;
+}
+
 void bind_output(fdd_batch_s* B, void* d_out) {
-  for (auto& w : B->waves)
-    for (int i = 0; i < w.count; ++i) {
-      const int b = w.first + i;
-      fdd::MacArgs& m = w.h_sets[i].args;
-      if (B->p.output == FDD_OUT_SPECTRA)
-        m.Y = static_cast<float2*>(d_out) + B->out_off[b];
-      else
-        m.Y = static_cast<float*>(d_out) + B->out_off[b];
-    }
+  for (auto& w : B->waves) {
+    for (int i = 0; i < w.count; ++i) bind_set(B, w.h_sets[i], w.first + i, d_out);
+    for (size_t i = 0; i < w.h_tail.size(); ++i) bind_set(B, w.h_tail[i], w.tail_beam[i], d_out);
+  }
 }
 
 // All work of one execute, issued on stream s (also used under capture).
@@ -132,17 +148,31 @@ fdd_status issue(fdd_batch_s* B, const void* d_in, cudaStream_t s) {
       B_CUFFT(cufftExecR2C(B->r2c.at(B->L[b]), B->d_xw,
                            reinterpret_cast<cufftComplex*>(B->d_pool + B->spec_off[b])));
     }
-    B_CUDA(cudaMemsetAsync(B->d_counter + wi, 0, sizeof(unsigned long long), s));
-    B_CUDA(fdd::launch_mac_batch(w.d_sets, w.count, w.n_items, B->d_counter + wi, B->variant,
-                                 B->ctas, B->p.n_chan, s));
+    B_CUDA(cudaMemsetAsync(B->d_counter + 2 * wi, 0, 2 * sizeof(unsigned long long), s));
+    B_CUDA(fdd::launch_mac_batch(w.d_sets, w.count, w.n_items, B->d_counter + 2 * wi,
+                                 B->variant, B->ctas, B->p.n_chan, s));
+    if (w.n_tail_items)
+      B_CUDA(fdd::launch_mac_batch(w.d_tail, static_cast<int>(w.h_tail.size()), w.n_tail_items,
+                                   B->d_counter + 2 * wi + 1, B->tail_variant, B->tail_ctas,
+                                   B->p.n_chan, s));
   }
   return FDD_OK;
 }
 
-fdd_status upload_sets(fdd_batch_s* B, cudaStream_t s) {
-  for (auto& w : B->waves)
-    B_CUDA(cudaMemcpyAsync(w.d_sets, w.h_sets.data(), sizeof(fdd::BatchSet) * w.count,
+fdd_status upload_wave(const fdd_batch_s::Wave& w, cudaStream_t s) {
+  B_CUDA(cudaMemcpyAsync(w.d_sets, w.h_sets.data(), sizeof(fdd::BatchSet) * w.count,
+                         cudaMemcpyHostToDevice, s));
+  if (!w.h_tail.empty())
+    B_CUDA(cudaMemcpyAsync(w.d_tail, w.h_tail.data(), sizeof(fdd::BatchSet) * w.h_tail.size(),
                            cudaMemcpyHostToDevice, s));
+  return FDD_OK;
+}
+
+fdd_status upload_sets(fdd_batch_s* B, cudaStream_t s) {
+  for (auto& w : B->waves) {
+    fdd_status st = upload_wave(w, s);
+    if (st != FDD_OK) return st;
+  }
   return FDD_OK;
 }
 
@@ -300,7 +330,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     return st;
   if ((st = alloc(B, reinterpret_cast<void**>(&B->d_pool), pool_need))) return st;
   if ((st = alloc(B, reinterpret_cast<void**>(&B->d_counter),
-                  sizeof(unsigned long long) * B->waves.size())))
+                  2 * sizeof(unsigned long long) * B->waves.size())))
     return st;
   B_CUDA(cudaMemcpy(B->d_pc, pc.data(), sizeof(fdd::PhaseConst) * pc.size(),
                     cudaMemcpyHostToDevice));
@@ -324,44 +354,86 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     for (auto& kv : B->r2c) B_CUFFT(cufftSetWorkArea(kv.second, B->d_fftwork));
   }
 
-  // Work sets per wave (output pointers bound at execute).
+  // Work sets per wave (output pointers bound at execute).  With a tile of
+  // 2048-trial blocks, a beam's last block of 1024 or fewer trials goes to the
+  // tail tile's 128-trial blocks instead (less padding beyond the trial grid).
+  auto base_args = [&](int b) {
+    fdd::MacArgs m{};
+    m.X = B->d_pool + B->spec_off[b];
+    m.x_series_stride = 0;
+    m.x_chan_stride = B->pitch[b];
+    m.pc = B->d_pc + static_cast<size_t>(b) * p->n_chan;
+    m.n_chan = p->n_chan;
+    m.n_bins = static_cast<int>(B->n_bins[b]);
+    m.n_series = 1;
+    m.y_series_stride = 0;
+    m.y_dm_stride = B->n_bins[b];
+    m.out_kind = p->output == FDD_OUT_SPECTRA ? 1 : 2;
+    m.scale = 1.0f;
+    m.real_bin_a = -1;
+    m.real_bin_b = -1;
+    return m;
+  };
   auto build_sets = [&](int variant) -> fdd_status {
     const int bins_per_cta = fdd::mac_variant_bins_per_cta(variant);
     const int dms = fdd::mac_variant_trials_per_block(variant);
+    const int tv = B->tail_variant;
+    const int tail_dms = tv >= 0 ? fdd::mac_variant_trials_per_block(tv) : 0;
+    const bool tails = tv >= 0 && dms >= 2048 && tail_dms < dms;
     for (auto& wv : B->waves) {
       wv.h_sets.assign(wv.count, fdd::BatchSet{});
-      long long items = 0;
+      wv.h_tail.clear();
+      wv.tail_beam.clear();
+      long long items = 0, t_items = 0;
       for (int i = 0; i < wv.count; ++i) {
         const int b = wv.first + i;
+        const int n_dm = B->beams[b].n_dm;
+        const int full = n_dm / dms, rem = n_dm % dms;
+        const bool tail = tails && rem > 0 && rem <= dms / 2;
+        const int blocks = full + (rem > 0 && !tail ? 1 : 0);
         fdd::BatchSet& bs = wv.h_sets[i];
-        fdd::MacArgs& m = bs.args;
-        m.X = B->d_pool + B->spec_off[b];
-        m.x_series_stride = 0;
-        m.x_chan_stride = B->pitch[b];
-        m.pc = B->d_pc + static_cast<size_t>(b) * p->n_chan;
-        m.n_chan = p->n_chan;
-        m.n_bins = static_cast<int>(B->n_bins[b]);
-        m.n_series = 1;
-        m.j_begin = 0;
-        m.n_dm = B->beams[b].n_dm;
-        m.y_series_stride = 0;
-        m.y_dm_stride = B->n_bins[b];
-        m.out_kind = p->output == FDD_OUT_SPECTRA ? 1 : 2;
-        m.scale = 1.0f;
-        m.real_bin_a = -1;
-        m.real_bin_b = -1;
+        bs.args = base_args(b);
+        bs.args.j_begin = 0;
+        bs.args.n_dm = tail ? full * dms : n_dm;
         bs.n_bin_tiles = static_cast<int>((B->n_bins[b] + bins_per_cta - 1) / bins_per_cta);
-        bs.n_dm_blocks = (B->beams[b].n_dm + dms - 1) / dms;
+        bs.n_dm_blocks = blocks;
         bs.item_begin = items;
-        items += static_cast<long long>(bs.n_bin_tiles) * bs.n_dm_blocks;
+        items += static_cast<long long>(bs.n_bin_tiles) * blocks;
+        if (tail) {
+          fdd::BatchSet ts{};
+          ts.args = base_args(b);
+          ts.args.j_begin = full * dms;
+          ts.args.n_dm = rem;
+          const int tb = fdd::mac_variant_bins_per_cta(tv);
+          ts.n_bin_tiles = static_cast<int>((B->n_bins[b] + tb - 1) / tb);
+          ts.n_dm_blocks = (rem + tail_dms - 1) / tail_dms;
+          ts.item_begin = t_items;
+          t_items += static_cast<long long>(ts.n_bin_tiles) * ts.n_dm_blocks;
+          wv.h_tail.push_back(ts);
+          wv.tail_beam.push_back(b);
+        }
       }
       wv.n_items = items;
+      wv.n_tail_items = t_items;
     }
     return FDD_OK;
   };
-  for (auto& wv : B->waves)
+  for (auto& wv : B->waves) {
     if ((st = alloc(B, reinterpret_cast<void**>(&wv.d_sets), sizeof(fdd::BatchSet) * wv.count)))
       return st;
+    if ((st = alloc(B, reinterpret_cast<void**>(&wv.d_tail), sizeof(fdd::BatchSet) * wv.count)))
+      return st;
+  }
+  // the tail tile (128-trial blocks, four bins per warp)
+  {
+    const int tv = FDD_MAC_Q_4X4;
+    B_CUDA(fdd::mac_prepare(tv, p->n_chan));
+    const int per_sm = fdd::mac_batch_ctas_per_sm(tv, p->n_chan);
+    if (per_sm >= 1) {
+      B->tail_variant = tv;
+      B->tail_ctas = per_sm * B->n_sms;
+    }
+  }
 
   auto use_variant = [&](int v) -> fdd_status {
     B->variant = v;
@@ -396,20 +468,22 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     for (int v : cands) {
       if ((tst = use_variant(v))) break;
       // output of wave 0 into the scratch, laid out like the real output
-      for (int i = 0; i < w0.count; ++i) {
-        const int b = w0.first + i;
-        const int64_t off = B->out_off[b] - B->out_off[w0.first];
-        fdd::MacArgs& m = B->waves[0].h_sets[i].args;
-        m.Y = static_cast<char*>(scratch) + (p->output == FDD_OUT_SPECTRA ? 8 : 4) * off;
-      }
-      cudaMemcpy(w0.d_sets, w0.h_sets.data(), sizeof(fdd::BatchSet) * w0.count,
-                 cudaMemcpyHostToDevice);
+      auto& w0m = B->waves[0];
+      const int64_t origin = B->out_off[w0.first];
+      for (int i = 0; i < w0.count; ++i) bind_set(B, w0m.h_sets[i], w0.first + i, scratch, origin);
+      for (size_t i = 0; i < w0.h_tail.size(); ++i)
+        bind_set(B, w0m.h_tail[i], w0.tail_beam[i], scratch, origin);
+      if ((tst = upload_wave(w0, nullptr))) break;
       float ms = 0.f, tot = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
-        cudaMemset(B->d_counter, 0, sizeof(unsigned long long));
+        cudaMemset(B->d_counter, 0, 2 * sizeof(unsigned long long));
         cudaEventRecord(e0);
         fdd::launch_mac_batch(w0.d_sets, w0.count, w0.n_items, B->d_counter, v, B->ctas,
                               p->n_chan, nullptr);
+        if (w0.n_tail_items)
+          fdd::launch_mac_batch(w0.d_tail, static_cast<int>(w0.h_tail.size()), w0.n_tail_items,
+                                B->d_counter + 1, B->tail_variant, B->tail_ctas, p->n_chan,
+                                nullptr);
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
@@ -449,9 +523,14 @@ fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offs
   info->n_waves = static_cast<int32_t>(b->waves.size());
   info->mac_variant = b->variant;
   long long items = 0;
-  for (auto& w : b->waves) items += w.n_items;
+  bool any_tail = false;
+  for (auto& w : b->waves) {
+    items += w.n_items + w.n_tail_items;
+    any_tail = any_tail || w.n_tail_items > 0;
+  }
   info->work_items = items;
   info->ctas = b->ctas;
+  info->tail_variant = any_tail ? b->tail_variant : -1;
   for (int v = 0; v < FDD_MAC_VARIANTS; ++v) info->autotune_ms[v] = b->tune_ms[v];
   for (size_t i = 0; i < b->beams.size(); ++i) {
     if (in_offsets) in_offsets[i] = b->in_off[i];

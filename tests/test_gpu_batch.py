@@ -87,6 +87,8 @@ def test_batch_matches_oracle(output):
     with fdd.Batch(BEAMS, autotune=False, **_common(output)) as batch:
         assert batch.info["n_waves"] == 1
         assert batch.info["mac_variant"] == fdd.FDD_MAC_W12_8X8
+        # every beam's last block of <= 1024 trials runs on 128-trial blocks
+        assert batch.info["tail_variant"] == fdd.FDD_MAC_Q_4X4
         assert batch.in_offsets == list(np.cumsum([0] + [b[0] * N_CHAN for b in BEAMS])[:-1])
         o, _, _ = _run(batch, xs, output)
     _check(batch, o, _refs(xs), output)
@@ -113,6 +115,7 @@ def test_batch_waves_graph_replay_and_rebind():
                    workspace_limit=fixed + 1_700_000,
                    **_common(fdd.FDD_OUT_SPECTRA)) as batch:
         assert batch.info["n_waves"] == 3
+        assert batch.info["tail_variant"] == -1  # 1024-trial blocks leave no tail
         o1, d_in, out = _run(batch, xs, fdd.FDD_OUT_SPECTRA)
         out.zero_()
         batch.execute(d_in, out)                 # graph replay
