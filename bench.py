@@ -59,6 +59,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tc", action="store_true",
                     help="skip the tensor-core form's timing on the 32-beam workload")
+    ap.add_argument("--no-tdd", action="store_true",
+                    help="skip the brute-force time-domain dedispersion on the same workload")
+    ap.add_argument("--crossover", action="store_true",
+                    help="time Fourier- and time-domain dedispersion of the workload at "
+                         "128..n_dm trials (one JSON line per trial count)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU-baseline sample")
     ap.add_argument("--n-t", type=int, default=0,
@@ -369,6 +374,83 @@ def measure_tc(args, fdd, torch, value_per_mac_kernel: float) -> dict:
     return res
 
 
+TDD_SMEM_ADDS_PER_CLK = 32  # one 4-byte shared load per add, 128 B per clock per SM
+
+
+def measure_tdd(plan, w, info, d_in, stream, torch, sm_count, fdd_ms_per_step, reps=3) -> dict:
+    """Brute-force time-domain dedispersion (Eq. 2) of the same beam with the
+    same plan: whole call (unpack + shift-and-sum), CUDA events."""
+    out_len = w.n_t - info["d_max"]
+    y = torch.empty((w.n_dm, out_len), dtype=torch.float32, device="cuda")
+    plan.tdd_execute(d_in, y, stream)
+    torch.cuda.synchronize()
+    plan.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.tdd_execute(d_in, y, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile_enable(False)
+    ms = e0.elapsed_time(e1) / reps
+    kernel_ms = prof["ms"]["tdd"] / max(prof["launches"]["tdd"], 1)
+    adds = w.n_dm * w.n_chan * out_len
+    peak = TDD_SMEM_ADDS_PER_CLK * sm_count * float(load_peaks().get("sm_max_mhz") or 2070) * 1e6
+    del y
+    return {"method": "brute-force time-domain shift-and-sum (Eq. 2), same workload",
+            "ms_per_step": ms, "kernel_ms": kernel_ms,
+            "adds_per_s_kernel": adds / (kernel_ms / 1e3),
+            "frac_smem_bound": adds / (kernel_ms / 1e3) / peak,
+            "bound": f"shared memory: {TDD_SMEM_ADDS_PER_CLK} adds (4-byte loads) per clock per SM",
+            "output_samples_per_trial": out_len,
+            "fdd_over_tdd_time": fdd_ms_per_step / ms}
+
+
+def run_crossover(args) -> None:
+    """Fourier-domain (this library's default path) against brute-force
+    time-domain dedispersion on the workload's shape at 128, 256, .. n_dm
+    trials of the same grid (the comparison of Sect. 4)."""
+    import torch
+
+    import paper_2110_03482_gb300 as fdd
+
+    fdd.build()
+    w0 = workload_from_args(args)
+    fb, _ = synth.filterbank(w0, seed=args.seed)
+    d_in = torch.from_numpy(fb.reshape(-1)).cuda()
+    stream = torch.cuda.current_stream()
+    n = 128
+    while n <= w0.n_dm:
+        w = w0.scaled(n_dm=n)
+        with fdd.Plan(**plan_params(w, fdd)) as plan:
+            info = plan.info
+            out = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
+            y = torch.empty((n, w.n_t - info["d_max"]), dtype=torch.float32, device="cuda")
+            res = {}
+            for name, call in (("fdd", lambda: plan.execute(d_in, out, stream)),
+                               ("tdd", lambda: plan.tdd_execute(d_in, y, stream))):
+                for _ in range(max(args.warmup, 1)):
+                    call()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[name] = e0.elapsed_time(e1) / args.steps
+            print(json.dumps({"crossover": w0.name, "n_dm": n, "fdd_ms": res["fdd"],
+                              "tdd_ms": res["tdd"], "tdd_over_fdd_time": res["tdd"] / res["fdd"],
+                              "fdd_tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]],
+                              "fft_len": info["fft_len"], "n_chunks": info["n_chunks"]}),
+                  flush=True)
+            del out, y
+        n *= 2
+
+
 def run_fdd(args, rank: int, world: int, dist) -> None:
     import torch
 
@@ -475,6 +557,10 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
                "ms_per_step": e_ms / args.e2e_steps}
         del h_in, h_out
 
+    tdd = None
+    if not args.no_tdd and world == 1:
+        tdd = measure_tdd(plan, w, info, d_in, stream, torch, sm_count,
+                          fdd_ms_per_step=ms_max / args.steps)
     tc = None if args.no_tc else measure_tc(args, fdd, torch, value_per_mac_kernel=achieved)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -492,6 +578,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
                 "gpu_launches": own_launches,
                 "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "tc": tc,
+                "tdd": tdd,
                 "stage_ms_share": stage_share,
                 "fp32_frac_whole_step": value * FLOPS_PER_MAC / 1e12 / (peak * world),
                 "macs_per_step": macs_step * world}
@@ -640,6 +727,9 @@ def main():
         return
     if args.mac_sweep:
         run_mac_sweep(args)
+        return
+    if args.crossover:
+        run_crossover(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -270,13 +270,34 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
                                        int64_t y_pitch, int32_t out_kind,
                                        fdd_stream_t stream);
 
+/*
+ * Brute-force time-domain dedispersion (Eq. 2), the method the paper
+ * measures Fourier-domain dedispersion against (Sect. 4), with the plan's
+ * channels, sampling time, k_DM, reference frequency and DM list (any list:
+ * uniform or not):
+ *   y[beam][j][n] = sum_nu x[beam][nu][n + s[j][nu]],  n < n_t - d_max,
+ * where s[j][nu] is the delay of Eq. 1 in samples, computed in FP64 and
+ * rounded to the nearest sample (halves away from zero), and d_max is
+ * fdd_info.d_max (ceil of the largest delay), so every sample read exists.
+ *   d_in  : as fdd_execute (u8 or f32, either layout, n_beams beams).
+ *   d_out : float [n_beams][n_dm][n_t - d_max].
+ * The first call builds the shift tables and a channel-major copy of one
+ * beam (n_chan x n_t floats) in plan memory; later calls reuse them.
+ * Asynchronous on the stream.  Errors: FDD_ERR_INVALID_ARG (NULL pointers,
+ * n_t <= d_max), FDD_ERR_UNSUPPORTED (a block of 32 trials spans more than
+ * ~6000 samples of delay in one channel, or more than 2^24 output samples),
+ * FDD_ERR_ALLOC, FDD_ERR_CUDA.
+ */
+fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream);
+
 /* Stages of the path timed by the profiling calls below. */
 #define FDD_STAGE_UNPACK 0  /* transpose_and_unpack + zero_pad (Algorithm 1)   */
 #define FDD_STAGE_R2C 1     /* channel transforms, Eq. 3 (cuFFT)                */
 #define FDD_STAGE_MAC 2     /* phase-rotate-and-sum, Eqs. 4 and 7               */
 #define FDD_STAGE_C2R 3     /* inverse transforms, Eq. 6 (cuFFT)                */
 #define FDD_STAGE_SCATTER 4 /* 1/L scaling and valid-sample placement           */
-#define FDD_STAGE_COUNT 5
+#define FDD_STAGE_TDD 5     /* brute-force time-domain shift-and-sum (Eq. 2)    */
+#define FDD_STAGE_COUNT 6
 
 typedef struct fdd_profile {
   int64_t launches[FDD_STAGE_COUNT]; /* timed launches per stage               */

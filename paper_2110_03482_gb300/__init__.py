@@ -54,7 +54,7 @@ EXPORTS = [
     "fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute", "fdd_execute_dm_range",
     "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
     "fdd_destroy", "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
-    "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins",
+    "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins", "fdd_tdd_execute",
 ]
 FDD_STATIC_MAX_CHAN = 8192
 
@@ -63,8 +63,9 @@ FDD_STAGE_R2C = 1
 FDD_STAGE_MAC = 2
 FDD_STAGE_C2R = 3
 FDD_STAGE_SCATTER = 4
-FDD_STAGE_COUNT = 5
-STAGE_NAMES = ["unpack", "r2c", "mac", "c2r", "scatter"]
+FDD_STAGE_TDD = 5
+FDD_STAGE_COUNT = 6
+STAGE_NAMES = ["unpack", "r2c", "mac", "c2r", "scatter", "tdd"]
 
 
 class fdd_params(ctypes.Structure):
@@ -198,6 +199,7 @@ def lib() -> ctypes.CDLL:
         L.fdd_execute.argtypes = [vp, vp, vp, vp]
         L.fdd_execute_dm_range.argtypes = [vp, vp, i32, i32, vp, vp]
         L.fdd_execute_host.argtypes = [vp, vp, vp, vp]
+        L.fdd_tdd_execute.argtypes = [vp, vp, vp, vp]
         L.fdd_dedisperse_spectra.argtypes = [vp, vp, i64, i32, i32, i32, vp, i64, i32, vp]
         L.fdd_dedisperse_spectra_bins.argtypes = [vp, vp, i64, i32, i32, i32, i32, i32, vp,
                                                   i64, i32, vp]
@@ -216,7 +218,8 @@ def lib() -> ctypes.CDLL:
                      "fdd_execute_dm_range", "fdd_execute_host", "fdd_dedisperse_spectra",
                      "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
                      "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
-                     "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins"]:
+                     "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins",
+                     "fdd_tdd_execute"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -307,6 +310,10 @@ def fdd_execute(plan: int, d_in, d_out, stream=None) -> None:
 def fdd_execute_dm_range(plan: int, d_in, dm_first: int, n_dm: int, d_out, stream=None) -> None:
     _check(lib().fdd_execute_dm_range(plan, _ptr(d_in), dm_first, n_dm, _ptr(d_out),
                                       _stream(stream)))
+
+
+def fdd_tdd_execute(plan: int, d_in, d_out, stream=None) -> None:
+    _check(lib().fdd_tdd_execute(plan, _ptr(d_in), _ptr(d_out), _stream(stream)))
 
 
 def fdd_execute_host(plan: int, h_in, h_out, stream=None) -> None:
@@ -427,6 +434,11 @@ class Plan:
 
     def execute_host(self, h_in, h_out, stream=None):
         fdd_execute_host(self.handle, h_in, h_out, stream)
+
+    def tdd_execute(self, d_in, d_out, stream=None):
+        """Brute-force time-domain dedispersion (Eq. 2) with this plan's
+        parameters: d_out is float [n_beams][n_dm][n_t - d_max]."""
+        fdd_tdd_execute(self.handle, d_in, d_out, stream)
 
     def dedisperse_spectra(self, d_X, x_pitch, n_series, dm_first, n_dm, d_Y, y_pitch,
                            out_kind=FDD_OUT_SPECTRA, stream=None):

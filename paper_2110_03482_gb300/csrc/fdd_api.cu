@@ -5,6 +5,8 @@
 // of Algorithm 1 (Sect. 3) on device-resident data.
 #include <cufft.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,6 +50,11 @@ struct fdd_plan_s {
   // compute stream (created on its first call)
   cudaStream_t h2d = nullptr, d2h = nullptr;
   std::vector<cudaEvent_t> pipe_ev;
+  // fdd_tdd_execute: rounded shift tables and one beam's channel-major series
+  int* d_shift = nullptr;
+  int* d_shift_base = nullptr;
+  float* d_tdd_x = nullptr;
+  int tdd_win = 0;
   size_t bytes_held = 0;
   // profiling: event pairs around stage launches (fdd_profile_enable)
   bool prof_on = false;
@@ -211,11 +218,11 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   const double ddm = p->n_dm > 1 ? (p->dm_list[p->n_dm - 1] - dm0) / (p->n_dm - 1) : 0.0;
   const double tol = 4.0 * std::ldexp(std::numeric_limits<double>::epsilon(),
                                       std::ilogb(dm_max > 1.0 ? dm_max : 1.0));
+  // (A non-uniform list makes a valid plan: the time-domain path takes any
+  // list; the Fourier-domain calls refuse it, see need_uniform_grid.)
   int uniform = 1;
   for (int j = 0; j < p->n_dm && uniform; ++j)
     if (std::fabs(p->dm_list[j] - (dm0 + j * ddm)) > tol) uniform = 0;
-  if (!uniform)
-    return fail(FDD_ERR_UNSUPPORTED, "non-uniform DM lists are not supported by this build");
 
   const double max_delay = dm_max * rate_max;  // both factors are >= 0
   if (max_delay > 4.0e18) return fail(FDD_ERR_INVALID_ARG, "delays overflow");
@@ -307,7 +314,8 @@ void release(fdd_plan_s* P) {
   if (P->has_c2r) cufftDestroy(P->c2r);
   if (P->has_c2r_tail) cufftDestroy(P->c2r_tail);
   void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_fftwork, P->d_status,
-                  P->d_in_stage, P->d_out_stage, P->d_tcx};
+                  P->d_in_stage, P->d_out_stage, P->d_tcx, P->d_shift, P->d_shift_base,
+                  P->d_tdd_x};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->prof_ev)
@@ -317,6 +325,13 @@ void release(fdd_plan_s* P) {
   if (P->h2d) cudaStreamDestroy(P->h2d);
   if (P->d2h) cudaStreamDestroy(P->d2h);
   delete P;
+}
+
+// The Fourier-domain kernels form the phase as k u + k j v (a uniform grid).
+fdd_status need_uniform_grid(const fdd_plan_s* P) {
+  if (P->info.dm_uniform) return FDD_OK;
+  return fail(FDD_ERR_UNSUPPORTED,
+              "the Fourier-domain kernels need a uniform DM grid (fdd_tdd_execute takes any list)");
 }
 
 fdd_status dev_alloc(fdd_plan_s* P, void** ptr, size_t bytes) {
@@ -777,6 +792,7 @@ fdd_status fdd_execute_dm_range(fdd_plan_t plan, const void* d_in, int32_t dm_fi
                 dm_first + n_dm, plan->p.n_dm);
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
+  if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
   return run(plan, d_in, dm_first, n_dm, d_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -790,6 +806,7 @@ fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_
   if (!h_in || !h_out) return fail(FDD_ERR_INVALID_ARG, "NULL input or output");
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
+  if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
   const size_t in_bytes =
       static_cast<size_t>(plan->info.in_elems) * (plan->p.in_dtype == FDD_IN_U8 ? 1 : 4);
   const size_t out_bytes = static_cast<size_t>(plan->info.out_bytes);
@@ -844,6 +861,7 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
                 "n_series x n_chan spectra of one bin exceed the tensor-core form's scratch");
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
+  if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
   fdd::MacArgs m{};
   m.X = static_cast<const float2*>(d_X);
   m.x_chan_stride = x_pitch;
@@ -880,6 +898,83 @@ fdd_status fdd_dedisperse_spectra(fdd_plan_t plan, const void* d_X, int64_t x_pi
   return fdd_dedisperse_spectra_bins(plan, d_X, x_pitch, n_series, 0,
                                      static_cast<int32_t>(plan->info.n_bins), dm_first, n_dm,
                                      d_Y, y_pitch, out_kind, stream);
+}
+
+fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  if (!d_in || !d_out) return fail(FDD_ERR_INVALID_ARG, "NULL input or output");
+  const fdd_params& p = plan->p;
+  const fdd_info& g = plan->info;
+  const int64_t out_len = p.n_t - g.d_max;
+  if (out_len <= 0)
+    return fail(FDD_ERR_INVALID_ARG, "n_t %lld does not exceed the largest delay %lld",
+                (long long)p.n_t, (long long)g.d_max);
+  if (out_len > int64_t(65535) * fdd::kTdSamp)
+    return fail(FDD_ERR_UNSUPPORTED, "more than %lld output samples per trial",
+                (long long)int64_t(65535) * fdd::kTdSamp);
+  fdd_status st = check_device(plan);
+  if (st != FDD_OK) return st;
+  const int nc = p.n_chan, nd = p.n_dm;
+  if (!plan->d_shift) {
+    // Eq. 1 delays in samples (FP64), rounded to the nearest sample (halves
+    // away from zero; delays are >= 0), and per block of kTdDms trials the
+    // smallest shift of each channel and the widest span.
+    std::vector<int> sh(static_cast<size_t>(nd) * nc);
+    for (int j = 0; j < nd; ++j)
+      for (int c = 0; c < nc; ++c) {
+        const double d = plan->dms[j] * plan->rate[c];
+        if (!(d >= 0.0) || d > 2.0e9) return fail(FDD_ERR_UNSUPPORTED, "delay out of range");
+        sh[static_cast<size_t>(j) * nc + c] = static_cast<int>(std::floor(d + 0.5));
+      }
+    const int n_blk = (nd + fdd::kTdDms - 1) / fdd::kTdDms;
+    std::vector<int> base(static_cast<size_t>(n_blk) * nc);
+    int span = 0;
+    for (int b = 0; b < n_blk; ++b)
+      for (int c = 0; c < nc; ++c) {
+        int lo = INT_MAX, hi = INT_MIN;
+        for (int j = b * fdd::kTdDms; j < nd && j < (b + 1) * fdd::kTdDms; ++j) {
+          lo = std::min(lo, sh[static_cast<size_t>(j) * nc + c]);
+          hi = std::max(hi, sh[static_cast<size_t>(j) * nc + c]);
+        }
+        base[static_cast<size_t>(b) * nc + c] = lo;
+        span = std::max(span, hi - lo);
+      }
+    const int win = (fdd::kTdSamp + span + 3) / 4 * 4;
+    if (fdd::tdd_smem_bytes(win) > kMaxSmem)
+      return fail(FDD_ERR_UNSUPPORTED,
+                  "a block of %d trials spans %d samples of delay in one channel", fdd::kTdDms,
+                  span);
+    if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_shift), sizeof(int) * sh.size())))
+      return st;
+    if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_shift_base),
+                        sizeof(int) * base.size())))
+      return st;
+    if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_tdd_x),
+                        sizeof(float) * static_cast<size_t>(nc) * p.n_t)))
+      return st;
+    FDD_CUDA(cudaMemcpy(plan->d_shift, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice));
+    FDD_CUDA(cudaMemcpy(plan->d_shift_base, base.data(), sizeof(int) * base.size(),
+                        cudaMemcpyHostToDevice));
+    FDD_CUDA(fdd::tdd_prepare(win));
+    plan->tdd_win = win;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
+  const int64_t beam_elems = p.n_t * static_cast<int64_t>(nc);
+  for (int b = 0; b < p.n_beams; ++b) {
+    fdd::UnpackArgs ua{static_cast<const char*>(d_in) + esz * beam_elems * b, p.in_dtype,
+                       p.in_layout, nc, p.n_t, 0, p.n_t, plan->d_tdd_x, p.n_t};
+    {
+      StageTimer t(plan, FDD_STAGE_UNPACK, s);
+      FDD_CUDA(fdd::launch_unpack(ua, s));
+    }
+    fdd::TddArgs ta{plan->d_tdd_x, p.n_t, nc, plan->d_shift, plan->d_shift_base, nd,
+                    plan->tdd_win,
+                    static_cast<float*>(d_out) + static_cast<int64_t>(b) * nd * out_len, out_len};
+    StageTimer t(plan, FDD_STAGE_TDD, s);
+    FDD_CUDA(fdd::launch_tdd(ta, s));
+  }
+  return FDD_OK;
 }
 
 fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on) {

@@ -147,4 +147,24 @@ struct ScatterArgs {
 };
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 
+// Brute-force time-domain dedispersion (fdd_tdd.cu), Eq. 2.
+constexpr int kTdDms = 32;   // trials per CTA
+constexpr int kTdSamp = 256;  // output samples per CTA
+constexpr int kTdCh = 8;     // channels per shared-memory stage
+struct TddArgs {
+  const float* x;     // one beam, channel-major [n_chan][n_t]
+  int64_t n_t;
+  int n_chan;
+  const int* shift;   // [n_dm][n_chan] delays of Eq. 1 rounded to the nearest sample
+  const int* base;    // [blocks of kTdDms trials][n_chan] smallest shift of the block
+  int n_dm;
+  int win;            // window floats per channel: kTdSamp + the largest shift span
+                      // of a block, rounded up to a multiple of 4
+  float* y;           // [n_dm][out_len]
+  int64_t out_len;    // valid samples, n_t - D_max
+};
+size_t tdd_smem_bytes(int win);
+cudaError_t tdd_prepare(int win);
+cudaError_t launch_tdd(const TddArgs& a, cudaStream_t s);
+
 }  // namespace fdd

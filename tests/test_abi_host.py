@@ -99,7 +99,6 @@ def test_geometry_survey_values():
     (dict(output=9), fdd.FDD_ERR_INVALID_ARG),
     (dict(precision=5), fdd.FDD_ERR_INVALID_ARG),
     (dict(precision=-1), fdd.FDD_ERR_INVALID_ARG),
-    (dict(dm_list=np.array([0.0, 1.0, 3.0])), fdd.FDD_ERR_UNSUPPORTED),
     (dict(dm_list=np.array([-1.0, 0.0])), fdd.FDD_ERR_INVALID_ARG),
     (dict(dm_list=np.array([0.0, np.nan])), fdd.FDD_ERR_INVALID_ARG),
     (dict(mac_variant=-1), fdd.FDD_ERR_INVALID_ARG),
@@ -112,6 +111,14 @@ def test_invalid_parameters(kw, status):
         fdd.fdd_plan_geometry(_params(w, **kw))
     assert e.value.status == status
     assert fdd.fdd_last_error()
+
+
+def test_non_uniform_dm_list_makes_a_plan_for_the_time_domain_path():
+    """Any DM list makes a valid plan (the brute-force time-domain path takes
+    it); the geometry reports it, and the Fourier-domain calls refuse it."""
+    w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    g = fdd.fdd_plan_geometry(_params(w, dm_list=np.array([0.0, 1.0, 3.0])))
+    assert g["dm_uniform"] == 0 and g["d_max"] > 0
 
 
 def test_variant_choice():
