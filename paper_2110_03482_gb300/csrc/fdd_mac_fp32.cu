@@ -1112,14 +1112,31 @@ VariantInfo variant_info(int v) {
 
 }  // namespace
 
-// Fastest variant per trial count on the survey-shaped workload (kernel-only
-// sweep on GB300 per 2048-trial, 1024-channel, 131073-bin launch: W12_8x8
-// 43.7 ms, Q12_8x8 49.5, R_8x8 50.3, Q_8x8 52.4, Z12_8x8 52.4, S_8x8 55.6,
-// P12_8x8 63.0; Q_4x8 and Q_4x4 lead their tile sizes).
+// Default tile for a trial count: the one with the least time for the padded
+// trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
+// measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
+// 131073 bins, full blocks): W12_8x8 0.623 (2048-trial blocks), Q_4x8 0.493
+// (1024), Q_4x4 0.347 (128).  Other tiles measured on the same launch (ms):
+// W12_8x8 43.7, Q12_8x8 49.5, R_8x8 50.3, Q_8x8 52.4, Z12_8x8 52.4,
+// S_8x8 55.6, P_8x8 56.3, SP_8x8 57.8, P12_8x8 63.0.
 int mac_variant_for(int n_dm) {
-  if (n_dm > 1024) return MAC_W12_8x8;
-  if (n_dm > 256) return MAC_Q_4x8;
-  return MAC_Q_4x4;
+  struct Tile {
+    int variant, block;
+    double rate;
+  };
+  static const Tile tiles[] = {
+      {MAC_W12_8x8, 2048, 0.623}, {MAC_Q_4x8, 1024, 0.493}, {MAC_Q_4x4, 128, 0.347}};
+  int best = MAC_W12_8x8;
+  double best_cost = 0.0;
+  for (const Tile& t : tiles) {
+    const double padded = static_cast<double>((n_dm + t.block - 1) / t.block) * t.block;
+    const double cost = padded / t.rate;
+    if (best_cost == 0.0 || cost < best_cost) {
+      best = t.variant;
+      best_cost = cost;
+    }
+  }
+  return best;
 }
 
 int mac_variant_trials_per_block(int variant) { return variant_info(variant).dms; }
