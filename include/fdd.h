@@ -285,7 +285,7 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
  * beam (n_chan x n_t floats) in plan memory; later calls reuse them.
  * Asynchronous on the stream.  Errors: FDD_ERR_INVALID_ARG (NULL pointers,
  * n_t <= d_max), FDD_ERR_UNSUPPORTED (a block of 32 trials spans more than
- * ~6000 samples of delay in one channel, or more than 2^24 output samples),
+ * ~3300 samples of delay in one channel, or more than 2^24 output samples),
  * FDD_ERR_ALLOC, FDD_ERR_CUDA.
  */
 fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream);

@@ -50,7 +50,8 @@ struct fdd_plan_s {
   // compute stream (created on its first call)
   cudaStream_t h2d = nullptr, d2h = nullptr;
   std::vector<cudaEvent_t> pipe_ev;
-  // fdd_tdd_execute: rounded shift tables and one beam's channel-major series
+  // fdd_tdd_execute: rounded shift tables (relative to each block of trials'
+  // smallest, and those smallest) and one beam's channel-major series
   int* d_shift = nullptr;
   int* d_shift_base = nullptr;
   float* d_tdd_x = nullptr;
@@ -928,6 +929,7 @@ fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_s
       }
     const int n_blk = (nd + fdd::kTdDms - 1) / fdd::kTdDms;
     std::vector<int> base(static_cast<size_t>(n_blk) * nc);
+    std::vector<int> rel(static_cast<size_t>(n_blk) * nc * fdd::kTdDms, 0);
     int span = 0;
     for (int b = 0; b < n_blk; ++b)
       for (int c = 0; c < nc; ++c) {
@@ -938,13 +940,16 @@ fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_s
         }
         base[static_cast<size_t>(b) * nc + c] = lo;
         span = std::max(span, hi - lo);
+        for (int j = b * fdd::kTdDms; j < nd && j < (b + 1) * fdd::kTdDms; ++j)
+          rel[(static_cast<size_t>(b) * nc + c) * fdd::kTdDms + (j - b * fdd::kTdDms)] =
+              sh[static_cast<size_t>(j) * nc + c] - lo;
       }
     const int win = (fdd::kTdSamp + span + 3) / 4 * 4;
     if (fdd::tdd_smem_bytes(win) > kMaxSmem)
       return fail(FDD_ERR_UNSUPPORTED,
                   "a block of %d trials spans %d samples of delay in one channel", fdd::kTdDms,
                   span);
-    if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_shift), sizeof(int) * sh.size())))
+    if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_shift), sizeof(int) * rel.size())))
       return st;
     if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_shift_base),
                         sizeof(int) * base.size())))
@@ -952,7 +957,8 @@ fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_s
     if ((st = dev_alloc(plan, reinterpret_cast<void**>(&plan->d_tdd_x),
                         sizeof(float) * static_cast<size_t>(nc) * p.n_t)))
       return st;
-    FDD_CUDA(cudaMemcpy(plan->d_shift, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice));
+    FDD_CUDA(cudaMemcpy(plan->d_shift, rel.data(), sizeof(int) * rel.size(),
+                        cudaMemcpyHostToDevice));
     FDD_CUDA(cudaMemcpy(plan->d_shift_base, base.data(), sizeof(int) * base.size(),
                         cudaMemcpyHostToDevice));
     FDD_CUDA(fdd::tdd_prepare(win));

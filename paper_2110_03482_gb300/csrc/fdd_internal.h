@@ -155,7 +155,9 @@ struct TddArgs {
   const float* x;     // one beam, channel-major [n_chan][n_t]
   int64_t n_t;
   int n_chan;
-  const int* shift;   // [n_dm][n_chan] delays of Eq. 1 rounded to the nearest sample
+  const int* rel;     // [blocks of kTdDms trials][n_chan][kTdDms]: the delays of Eq. 1
+                      // rounded to the nearest sample, minus the block's smallest
+                      // (0 for trials beyond n_dm)
   const int* base;    // [blocks of kTdDms trials][n_chan] smallest shift of the block
   int n_dm;
   int win;            // window floats per channel: kTdSamp + the largest shift span
