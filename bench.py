@@ -374,6 +374,22 @@ def measure_tc(args, fdd, torch, value_per_mac_kernel: float) -> dict:
     return res
 
 
+def max_over_ranks(dist, ms: float, device: str) -> float:
+    """The job's time: the largest of every rank's (the slowest rank ends it)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job's time
+    (weak scaling: each rank dedisperses its own beam of the same shape)."""
+    return units_per_rank_step * steps * world / (ms_max / 1e3)
+
+
 TDD_SMEM_ADDS_PER_CLK = 32  # one 4-byte shared load per add, 128 B per clock per SM
 
 
@@ -499,13 +515,8 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
     prof = plan.profile_read()
     plan.profile_enable(False)
 
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    total_macs = macs_step * args.steps * world
-    value = total_macs / (ms_max / 1e3)
+    ms_max = max_over_ranks(dist, ms, "cuda")
+    value = job_rate(macs_step, args.steps, world, ms_max)
 
     # dominant kernel: the phasor-MAC
     mac_n = prof["launches"]["mac"]
@@ -546,12 +557,8 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
             plan.execute_host(h_in, h_out, stream)
         f1.record(stream)
         torch.cuda.synchronize()
-        e_ms = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": macs_step * args.e2e_steps * world / (e_ms / 1e3), "unit": UNIT,
+        e_ms = max_over_ranks(dist, f0.elapsed_time(f1), "cuda")
+        e2e = {"value": job_rate(macs_step, args.e2e_steps, world, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
                "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
                "ms_per_step": e_ms / args.e2e_steps}
