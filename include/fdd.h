@@ -124,6 +124,13 @@ typedef struct fdd_params {
   int32_t mac_variant;    /* phase-rotate-and-sum kernel: 0 chooses automatically;
                              1 + FDD_MAC_* forces that variant                      */
   size_t workspace_limit; /* device bytes the plan may hold; 0 = library default    */
+  int32_t downsample;     /* FDD_OUT_TIME: shorten the inverse transform by this
+                             power-of-two factor f (0 or 1: none; Sect. 2.2, last
+                             paragraph): only the bins k <= L/(2f) are dedispersed
+                             and inverted with length L/f, scaled by 1/L, giving
+                             the series low-passed to those bins and sampled every
+                             f native samples; with chunking the hop is rounded
+                             down to a multiple of f.  L must be divisible by 2f. */
 } fdd_params;
 
 typedef struct fdd_info {
@@ -133,7 +140,8 @@ typedef struct fdd_info {
   int64_t n_chunks;        /* chunks per beam                                      */
   int64_t hop;             /* output samples kept per chunk                        */
   int64_t d_max;           /* ceil(largest delay) in samples (Sect. 2.2)           */
-  int64_t out_len;         /* time samples per DM in FDD_OUT_TIME output           */
+  int64_t out_len;         /* time samples per DM in FDD_OUT_TIME output (down-
+                              sampled: ceil of the native count / downsample)        */
   int64_t valid_len;       /* leading output samples free of wrap-around           */
   int64_t in_elems;        /* elements of the input buffer                         */
   int64_t out_elems;       /* elements (float or complex) of a full output buffer  */
@@ -144,7 +152,7 @@ typedef struct fdd_info {
   int32_t dm_uniform;      /* 1 when the list is an arithmetic progression         */
   int32_t dm_batch;        /* trials per internal batch (bounded by workspace)     */
   int32_t mac_variant;     /* phasor-MAC kernel tile chosen for this plan          */
-  int32_t reserved1;
+  int32_t downsample;      /* factor of the shortened inverse transform (1: none)    */
 } fdd_info;
 
 /* ABI version of the loaded library (FDD_ABI_VERSION at build time). */

@@ -31,6 +31,15 @@ notes as well):
   hop = L - D_max, the valid output is n_out = n_t - D_max samples, and chunk
   c reads x[c*hop, c*hop + L) (zero beyond n_t) and keeps its first hop
   output samples (the discard rule of Sect. 2.2 applied per chunk).
+* Down-sampling by a shorter inverse transform (Sect. 2.2, last paragraph:
+  the paper names the technique, not its details).  A factor f (a power of
+  two dividing L/2) keeps the bins k <= L/(2f) of the dedispersed spectrum
+  and inverts them with length L/f, scaled by 1/L (not 1/(L/f)): that is the
+  series low-passed to those bins and sampled every f native samples, at the
+  native amplitude (a constant input keeps its level).  The kept Nyquist bin
+  of the short transform contributes its real part only.  With chunking, the
+  hop is rounded down to a multiple of f, so the chunks tile the down-sampled
+  grid; the output keeps ceil(n_out / f) samples.
 """
 from __future__ import annotations
 
@@ -296,6 +305,45 @@ def spectra(x, geo: Geometry, c: int) -> np.ndarray:
     if geo.L & (geo.L - 1) == 0:
         return fft_r2c(xc)
     return np.stack([dft_r2c(row) for row in xc])
+
+
+def geometry_downsampled(n_t: int, chunk_len: int, d, f: int) -> Geometry:
+    """geometry() with the hop rounded down to a multiple of the factor f and
+    n_out counted in down-sampled samples (reading in the module header)."""
+    g = geometry(n_t, chunk_len, d)
+    if f == 1:
+        return g
+    if f < 1 or f & (f - 1) or g.L % (2 * f):
+        raise ValueError("f must be a power of two dividing L/2")
+    if chunk_len == 0:  # one chunk: keep ceil(n_t / f) samples
+        n_out = -(-g.n_out // f)
+        return Geometry(g.L, g.K, g.d_max, n_out * f, 1, n_out)
+    hop = g.hop // f * f
+    if hop <= 0:
+        raise ValueError("chunk too short for the largest delay at this factor")
+    n_out_native = g.n_out
+    return Geometry(g.L, g.K, g.d_max, hop, -(-n_out_native // hop), -(-n_out_native // f))
+
+
+def fdd_time_downsampled(x, d, chunk_len: int, f: int) -> np.ndarray:
+    """FDD with the inverse transform shortened by f (Sect. 2.2, last
+    paragraph): per chunk, Eq. 7 on the bins k <= L/(2f) only, then their
+    inverse of length L/f scaled by 1/L; y [n_dm, ceil(n_out / f)]."""
+    x = _f64(x)
+    n_t = x.shape[1]
+    geo = geometry_downsampled(n_t, chunk_len, d, f)
+    Ls = geo.L // f
+    bins = np.arange(Ls // 2 + 1, dtype=np.int64)
+    y = np.empty((d.shape[0], geo.n_out), dtype=np.float64)
+    for c in range(geo.n_chunks):
+        X = spectra(x, geometry(n_t, chunk_len, d) if chunk_len == 0 else
+                    Geometry(geo.L, geo.K, geo.d_max, geo.hop, geo.n_chunks, n_t - geo.d_max), c)
+        Y = fdd_bins(X[:, : bins.size], bins, geo.L, d)
+        yc = irfft(Y, Ls) / f  # irfft scales by f / L: back to 1 / L
+        s = c * geo.hop // f
+        n = min(geo.hop // f, geo.n_out - s)
+        y[:, s: s + n] = yc[:, :n]
+    return y
 
 
 def fdd_time(x, d, chunk_len: int) -> np.ndarray:

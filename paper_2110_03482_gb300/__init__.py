@@ -87,6 +87,7 @@ class fdd_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("mac_variant", ctypes.c_int32),
         ("workspace_limit", ctypes.c_size_t),
+        ("downsample", ctypes.c_int32),
     ]
 
 
@@ -109,7 +110,7 @@ class fdd_info(ctypes.Structure):
         ("dm_uniform", ctypes.c_int32),
         ("dm_batch", ctypes.c_int32),
         ("mac_variant", ctypes.c_int32),
-        ("reserved1", ctypes.c_int32),
+        ("downsample", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

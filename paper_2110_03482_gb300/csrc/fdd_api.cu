@@ -251,6 +251,31 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
     n_chunks = (out_len + hop - 1) / hop;
     valid_len = out_len;
   }
+  // Down-sampling by a shorter inverse transform (Sect. 2.2, last paragraph):
+  // the hop becomes a multiple of f and the output counts samples of f.
+  const int f = p->downsample > 1 ? p->downsample : 1;
+  if (p->downsample < 0 || (f & (f - 1)) != 0)
+    return fail(FDD_ERR_INVALID_ARG, "downsample must be 0, 1 or a power of two");
+  if (f > 1) {
+    if (p->output != FDD_OUT_TIME)
+      return fail(FDD_ERR_INVALID_ARG, "downsample applies to FDD_OUT_TIME output");
+    if (L % (2 * static_cast<int64_t>(f)) != 0)
+      return fail(FDD_ERR_INVALID_ARG, "transform length %lld is not divisible by 2 x %d",
+                  (long long)L, f);
+    if (p->chunk_len == 0) {
+      out_len = (out_len + f - 1) / f;
+      valid_len = (valid_len + f - 1) / f;
+      hop = out_len * f;
+    } else {
+      hop = hop / f * f;
+      if (hop <= 0)
+        return fail(FDD_ERR_INVALID_ARG, "chunk_len %lld leaves no hop at downsample %d",
+                    (long long)L, f);
+      n_chunks = (out_len + hop - 1) / hop;
+      out_len = (out_len + f - 1) / f;
+      valid_len = out_len;
+    }
+  }
   const int64_t n_bins = L / 2 + 1;
   if (L > (int64_t(1) << 30)) return fail(FDD_ERR_UNSUPPORTED, "transform length above 2^30");
   // The kernels form k * j in 32-bit integers.
@@ -265,6 +290,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   g->d_max = d_max;
   g->out_len = out_len;
   g->valid_len = valid_len;
+  g->downsample = f;
   g->in_elems = static_cast<int64_t>(p->n_beams) * p->n_t * nc;
   if (p->output == FDD_OUT_TIME) {
     g->out_elems = static_cast<int64_t>(p->n_beams) * p->n_dm * out_len;
@@ -290,7 +316,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   int64_t batch = p->n_dm;
   size_t per_dm = 0;
   if (p->output == FDD_OUT_TIME) {
-    per_dm = sizeof(float2) * g->bin_pitch * spectra_sets + sizeof(float) * L;
+    per_dm = sizeof(float2) * g->bin_pitch * spectra_sets + sizeof(float) * (L / f);
     if (fixed + per_dm > limit)
       return fail(FDD_ERR_INVALID_ARG, "workspace_limit %zu is below the minimum %zu", limit,
                   fixed + per_dm);
@@ -406,10 +432,11 @@ struct HostPipe {
     FDD_CUDA(cudaStreamWaitEvent(P->d2h, e, 0));
     const char* d_out = static_cast<const char*>(P->d_out_stage);
     if (p.output == FDD_OUT_TIME) {
-      int64_t keep = g.out_len - c * g.hop;
-      if (keep > g.hop) keep = g.hop;
+      const int64_t hop_o = g.hop / g.downsample;  // output samples per chunk
+      int64_t keep = g.out_len - c * hop_o;
+      if (keep > hop_o) keep = hop_o;
       const size_t pitch = sizeof(float) * static_cast<size_t>(g.out_len);
-      const size_t off = sizeof(float) * (static_cast<size_t>(b0) * p.n_dm * g.out_len + c * g.hop);
+      const size_t off = sizeof(float) * (static_cast<size_t>(b0) * p.n_dm * g.out_len + c * hop_o);
       FDD_CUDA(cudaMemcpy2DAsync(h_out + off, pitch, d_out + off, pitch, sizeof(float) * keep,
                                  static_cast<size_t>(nb) * p.n_dm, cudaMemcpyDeviceToHost,
                                  P->d2h));
@@ -466,6 +493,9 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
       m.scale = 1.0f;
       m.status = P->d_status;
       if (p.output == FDD_OUT_TIME) {
+        // (shortened inverse: only the bins up to Nyquist of length L / f)
+        const int64_t Ls = g.fft_len / g.downsample, hop_o = g.hop / g.downsample;
+        m.n_bins = static_cast<int>(Ls / 2 + 1);
         for (int j0 = dm_first; j0 < dm_first + n_dm; j0 += g.dm_batch) {
           const int nb = (dm_first + n_dm - j0) < g.dm_batch ? (dm_first + n_dm - j0) : g.dm_batch;
           m.j_begin = j0;
@@ -475,7 +505,7 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
           m.y_dm_stride = g.bin_pitch;
           m.out_kind = 1;
           m.real_bin_a = 0;                           // DC and Nyquist of a real
-          m.real_bin_b = static_cast<int>(g.fft_len / 2);  // series: real parts only
+          m.real_bin_b = static_cast<int>(Ls / 2);    // series: real parts only
           {
             StageTimer t(P, FDD_STAGE_MAC, s);
             FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
@@ -485,12 +515,12 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
             StageTimer t(P, FDD_STAGE_C2R, s);
             FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(P->d_Y), P->d_yt));
           }
-          const int64_t keep = (g.out_len - c * g.hop) < g.hop ? (g.out_len - c * g.hop) : g.hop;
+          const int64_t keep = (g.out_len - c * hop_o) < hop_o ? (g.out_len - c * hop_o) : hop_o;
           fdd::ScatterArgs sa{};
           sa.src = P->d_yt;
-          sa.src_stride = g.fft_len;
+          sa.src_stride = Ls;
           sa.dst = static_cast<float*>(d_out) +
-                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * g.hop;
+                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * hop_o;
           sa.dst_stride = g.out_len;
           sa.n_dm = nb;
           sa.n_keep = keep;
@@ -559,6 +589,9 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
     m.scale = 1.0f;
     m.status = P->d_status;
     if (p.output == FDD_OUT_TIME) {
+      // (shortened inverse: only the bins up to Nyquist of length L / f)
+      const int64_t Ls = g.fft_len / g.downsample, hop_o = g.hop / g.downsample;
+      m.n_bins = static_cast<int>(Ls / 2 + 1);
       for (int j0 = dm_first; j0 < dm_first + n_dm; j0 += g.dm_batch) {
         const int nb = (dm_first + n_dm - j0) < g.dm_batch ? (dm_first + n_dm - j0) : g.dm_batch;
         m.j_begin = j0;
@@ -568,14 +601,14 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.y_dm_stride = g.bin_pitch;
         m.out_kind = 1;
         m.real_bin_a = 0;
-        m.real_bin_b = static_cast<int>(g.fft_len / 2);
+        m.real_bin_b = static_cast<int>(Ls / 2);
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
           FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, P->d_tcx,
                                       P->tcx_bytes, s));
         }
         cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
-        const int64_t keep = (g.out_len - c * g.hop) < g.hop ? (g.out_len - c * g.hop) : g.hop;
+        const int64_t keep = (g.out_len - c * hop_o) < hop_o ? (g.out_len - c * hop_o) : hop_o;
         for (int b = 0; b < p.n_beams; ++b) {
           {
             StageTimer t(P, FDD_STAGE_C2R, s);
@@ -585,9 +618,9 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
           }
           fdd::ScatterArgs sa{};
           sa.src = P->d_yt;
-          sa.src_stride = g.fft_len;
+          sa.src_stride = Ls;
           sa.dst = static_cast<float*>(d_out) +
-                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * g.hop;
+                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * hop_o;
           sa.dst_stride = g.out_len;
           sa.n_dm = nb;
           sa.n_keep = keep;
@@ -728,7 +761,7 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
                         sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch * sets)))
       return st;
     if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_yt),
-                        sizeof(float) * size_t(g.dm_batch) * g.fft_len)))
+                        sizeof(float) * size_t(g.dm_batch) * (g.fft_len / g.downsample))))
       return st;
   }
   FDD_CUDA(cudaMemcpy(P->d_pc, P->pc_host.data(), sizeof(fdd::PhaseConst) * nc,
@@ -746,10 +779,12 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   FDD_CUFFT(cufftMakePlanMany64(P->r2c, 1, n, emb_real, 1, g.fft_len, emb_cplx, 1, g.bin_pitch,
                                 CUFFT_R2C, nc, &w_r2c));
   if (p->output == FDD_OUT_TIME) {
+    // inverse transforms of length L / downsample over the first bins of each row
+    long long ns[1] = {g.fft_len / g.downsample};
     FDD_CUFFT(cufftCreate(&P->c2r));
     P->has_c2r = true;
     FDD_CUFFT(cufftSetAutoAllocation(P->c2r, 0));
-    FDD_CUFFT(cufftMakePlanMany64(P->c2r, 1, n, emb_cplx, 1, g.bin_pitch, emb_real, 1, g.fft_len,
+    FDD_CUFFT(cufftMakePlanMany64(P->c2r, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
                                   CUFFT_C2R, g.dm_batch, &w_c2r));
     const int tail = p->n_dm % g.dm_batch;
     if (tail != 0) {
@@ -757,8 +792,8 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
       P->has_c2r_tail = true;
       P->c2r_tail_batch = tail;
       FDD_CUFFT(cufftSetAutoAllocation(P->c2r_tail, 0));
-      FDD_CUFFT(cufftMakePlanMany64(P->c2r_tail, 1, n, emb_cplx, 1, g.bin_pitch, emb_real, 1,
-                                    g.fft_len, CUFFT_C2R, tail, &w_tail));
+      FDD_CUFFT(cufftMakePlanMany64(P->c2r_tail, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
+                                    CUFFT_C2R, tail, &w_tail));
     }
   }
   size_t w = w_r2c > w_c2r ? w_r2c : w_c2r;

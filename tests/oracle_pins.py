@@ -257,7 +257,57 @@ def pin_overlap_save_equals_linear_tdd():
     assert np.max(np.abs(y - ref)) < 1e-12
 
 
+def pin_downsampled_inverse_f1_is_fdd_time():
+    """A shortening factor of 1 is the plain inverse (whole series and chunked)."""
+    rng = _rng(41)
+    nu = 1200.0 + 10.0 * np.arange(8)
+    d = oracle.delays(nu, 1.5 * np.arange(6), 1e-3)
+    x = rng.standard_normal((8, 1000))
+    for chunk in (0, 256):
+        assert np.array_equal(oracle.fdd_time_downsampled(x, d, chunk, 1),
+                              oracle.fdd_time(x, d, chunk))
+
+
+def pin_downsampled_inverse_decimates_band_limited_series():
+    """Sect. 2.2, last paragraph: with every input bin below L/(2f), shortening
+    the inverse transform by f returns every f-th sample of the full output
+    (nothing above the kept bins to lose), at the native amplitude."""
+    L, f = 1024, 4
+    n = np.arange(L)
+    nu = 1200.0 + 10.0 * np.arange(8)
+    d = oracle.delays(nu, 2.0 * np.arange(5), 1e-3)
+    x = np.stack([np.cos(2 * np.pi * (3 + c) * n / L + c) + 0.5 * np.sin(2 * np.pi * (40 + c) * n / L)
+                  for c in range(8)])
+    full = oracle.fdd_time(x, d, 0)
+    short = oracle.fdd_time_downsampled(x, d, 0, f)
+    assert short.shape == (5, L // f)
+    assert np.max(np.abs(short - full[:, ::f])) < 1e-12
+    # a constant filling the whole transform keeps its level (DC scaled by 1/L)
+    const = oracle.fdd_time_downsampled(np.full((8, L), 3.0), d, 0, f)
+    assert np.allclose(const, 24.0, atol=1e-12)
+
+
+def pin_downsampled_chunks_tile_the_grid():
+    """Chunked, the hop is a multiple of f, the output has ceil(n_out / f)
+    samples, and a constant input (a pure DC bin in every full chunk, whatever
+    the circular shifts) comes out at the native level n_chan * value in every
+    chunk that lies inside the series."""
+    f = 2
+    nu = 1200.0 + 10.0 * np.arange(4)
+    d = oracle.delays(nu, np.arange(3.0), 1e-3)
+    geo = oracle.geometry_downsampled(4000, 512, d, f)
+    assert geo.hop % f == 0 and geo.n_out == -(-(4000 - geo.d_max) // f)
+    y = oracle.fdd_time_downsampled(np.full((4, 4000), 3.0), d, 512, f)
+    assert y.shape == (3, geo.n_out)
+    full_chunks = (4000 - geo.L) // geo.hop + 1  # chunks read entirely inside the series
+    m = full_chunks * geo.hop // f
+    assert m > 0 and np.allclose(y[:, :m], 12.0, atol=1e-11)
+
+
 ALL_PINS = [
+    pin_downsampled_inverse_f1_is_fdd_time,
+    pin_downsampled_inverse_decimates_band_limited_series,
+    pin_downsampled_chunks_tile_the_grid,
     pin_delay_law_golden,
     pin_delay_law_scaling,
     pin_dft_closed_forms,

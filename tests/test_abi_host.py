@@ -121,6 +121,27 @@ def test_non_uniform_dm_list_makes_a_plan_for_the_time_domain_path():
     assert g["dm_uniform"] == 0 and g["d_max"] > 0
 
 
+def test_downsample_geometry_matches_oracle():
+    """Shortened inverse transform (Sect. 2.2, last paragraph): the hop is a
+    multiple of f and the output counts ceil(native / f) samples."""
+    w = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    for f in (1, 2, 4, 8):
+        g = fdd.fdd_plan_geometry(_params(w, downsample=f))
+        geo = oracle.geometry_downsampled(w.n_t, w.chunk_len, d, f)
+        assert g["downsample"] == f and g["hop"] == geo.hop and g["hop"] % f == 0
+        assert g["out_len"] == geo.n_out and g["n_chunks"] == geo.n_chunks
+        assert g["out_elems"] == w.n_dm * geo.n_out
+    w1 = synth.WORKLOADS["fdd_64ch_4096t_128dm"].scaled(n_t=4001)
+    g = fdd.fdd_plan_geometry(_params(w1, downsample=4))
+    assert g["out_len"] == 1001 and g["n_chunks"] == 1
+    for kw in (dict(downsample=3), dict(downsample=-2), dict(downsample=2, output=1),
+               dict(downsample=4096)):
+        with pytest.raises(fdd.FddError) as e:
+            fdd.fdd_plan_geometry(_params(w1, **kw))
+        assert e.value.status == fdd.FDD_ERR_INVALID_ARG
+
+
 def test_variant_choice():
     w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
     assert fdd.fdd_plan_geometry(_params(w))["mac_variant"] == fdd.FDD_MAC_Q_4X4

@@ -45,19 +45,21 @@ def _out_like(info, output, device):
     return torch.empty(shape, dtype=torch.float32).pin_memory()
 
 
-@pytest.mark.parametrize("output,layout,n_beams,precision", [
-    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 1, fdd.FDD_PREC_FP32),
-    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_CHAN_MAJOR, 2, fdd.FDD_PREC_FP32),
-    (fdd.FDD_OUT_SPECTRA, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_FP32),
-    (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_CHAN_MAJOR, 2, fdd.FDD_PREC_FP32),
-    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 5, fdd.FDD_PREC_BF16_HILO),
-    (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_BF16_HILO),
+@pytest.mark.parametrize("output,layout,n_beams,precision,ds", [
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 1, fdd.FDD_PREC_FP32, 1),
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_CHAN_MAJOR, 2, fdd.FDD_PREC_FP32, 1),
+    (fdd.FDD_OUT_SPECTRA, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_FP32, 1),
+    (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_CHAN_MAJOR, 2, fdd.FDD_PREC_FP32, 1),
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 5, fdd.FDD_PREC_BF16_HILO, 1),
+    (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_BF16_HILO, 1),
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 2, fdd.FDD_PREC_FP32, 4),   # down-sampled
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_BF16_HILO, 2),
 ])
-def test_host_pipeline_equals_device_execute(output, layout, n_beams, precision):
+def test_host_pipeline_equals_device_execute(output, layout, n_beams, precision, ds):
     out_name = {fdd.FDD_OUT_TIME: "time", fdd.FDD_OUT_SPECTRA: "spectra",
                 fdd.FDD_OUT_POWER: "power"}[output]
     w = _workload(n_beams, out_name)
-    with fdd.Plan(**params_for(w, in_layout=layout, precision=precision)) as plan:
+    with fdd.Plan(**params_for(w, in_layout=layout, precision=precision, downsample=ds)) as plan:
         info = plan.info
         assert info["n_chunks"] >= 3
         stream = torch.cuda.current_stream()

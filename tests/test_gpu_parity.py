@@ -207,6 +207,28 @@ def test_end_to_end_chunked_u8(layout):
                   ref - ref.mean(axis=1, keepdims=True)) <= 4 * FP32_REL_L2
 
 
+@pytest.mark.parametrize("f,chunk_len,n_t,dtype,precision", [
+    (2, 2048, 5000, "u8", fdd.FDD_PREC_FP32),
+    (4, 2048, 5000, "u8", fdd.FDD_PREC_FP32),
+    (4, 0, 4001, "f32", fdd.FDD_PREC_FP32),    # whole series, n_t not a multiple of f
+    (2, 2048, 5000, "f32", fdd.FDD_PREC_BF16_HILO),
+])
+def test_downsampled_inverse_matches_oracle(f, chunk_len, n_t, dtype, precision):
+    """Down-sampling by a shorter inverse transform (Sect. 2.2, last paragraph):
+    only bins k <= L/(2f) are dedispersed and inverted with length L/f."""
+    w = _small_workload(48, n_t, 1.5 * np.arange(70), band=(400.0, 500.0), t_samp=1e-3,
+                        dtype=dtype, chunk_len=chunk_len)
+    fb, _ = synth.filterbank(w, seed=13)
+    y, info = _run_execute(w, fb, fdd.FDD_OUT_TIME, downsample=f, precision=precision)
+    d = _oracle_delays(w)
+    ref = oracle.fdd_time_downsampled(fb.T.astype(np.float64), d, chunk_len, f)
+    assert info["downsample"] == f and info["out_len"] == ref.shape[1]
+    y = y.reshape(w.n_dm, -1)
+    tol = FP32_REL_L2 if precision == fdd.FDD_PREC_FP32 else 3e-3
+    assert rel_l2(y, ref) <= tol
+    assert rel_l2(y - y.mean(axis=1, keepdims=True), ref - ref.mean(axis=1, keepdims=True)) <= 4 * tol
+
+
 def test_end_to_end_beams_and_dm_range():
     w = _small_workload(32, 3000, 2.0 * np.arange(40), t_samp=5e-4, n_beams=3, chunk_len=1024)
     fbs = np.stack([synth.filterbank(w, seed=3, beam=b)[0] for b in range(3)])
