@@ -187,16 +187,18 @@ fdd_status fdd_plan_geometry(const fdd_params* p, fdd_info* out);
  * delay table, spin-frequency grid, FFT plans, device buffers).  Computes in
  * FP64 the per-channel delay rate of Eq. 1 and, for a uniform DM list, the
  * exact 64-bit fixed-point phase rates used by the kernels.  Allocates all
- * device workspace here; execute calls never allocate.
- * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_UNSUPPORTED (non-uniform DM list,
- * unsupported precision), FDD_ERR_ALLOC, FDD_ERR_CUDA, FDD_ERR_CUFFT.
+ * device workspace here; execute calls never allocate.  Any DM list makes a
+ * plan; the Fourier-domain calls need a uniform one (fdd_info.dm_uniform),
+ * the time-domain call takes any.
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_UNSUPPORTED (unsupported precision or
+ * sizes), FDD_ERR_ALLOC, FDD_ERR_CUDA, FDD_ERR_CUFFT.
  * On error *out is set to NULL and nothing is leaked.
  */
 fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out);
 
 /* Copy the plan's geometry into *out.  Also reports (FDD_ERR_DEVICE or
- * FDD_ERR_TIMEOUT) a status word left by an earlier kernel; this call
- * synchronises the plan's status read with the device. */
+ * FDD_ERR_TIMEOUT) a status word left by an earlier kernel, once: reading it
+ * clears it.  This call synchronises the plan's status read with the device. */
 fdd_status fdd_query(fdd_plan_t plan, fdd_info* out);
 
 /*
@@ -297,6 +299,28 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
  * FDD_ERR_ALLOC, FDD_ERR_CUDA.
  */
 fdd_status fdd_tdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream);
+
+/*
+ * Failure-detection self-tests (no counterpart in the paper).  Nothing here
+ * faults or hangs a GPU: every wait in the kernels is bounded (about 2 s of
+ * SM clock), after which the kernel records FDD_ERR_TIMEOUT in the plan's
+ * status word, releases what it holds and returns.
+ *
+ * fdd_debug_stall_test runs the plan's waiting phase-rotate-and-sum kernel
+ * (the warp-specialised FP32 tile, or the tensor-core kernel) on one bin,
+ * one trial and one series, with its producers withholding every "stage
+ * filled" arrival, so the consumers' waits run out.  It blocks until the
+ * kernel has returned (about 2 s); the next fdd_query then reports
+ * FDD_ERR_TIMEOUT once (reading a device status clears it), and the plan
+ * stays usable.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA.
+ *
+ * fdd_debug_fail_alloc makes the library's device allocations after the
+ * next `after` ones fail once with FDD_ERR_ALLOC (plans and batch plans
+ * release what they hold and report it); after < 0 turns it off.  Process
+ * wide.  Always FDD_OK.
+ */
+fdd_status fdd_debug_stall_test(fdd_plan_t plan, fdd_stream_t stream);
+fdd_status fdd_debug_fail_alloc(int32_t after);
 
 /* Stages of the path timed by the profiling calls below. */
 #define FDD_STAGE_UNPACK 0  /* transpose_and_unpack + zero_pad (Algorithm 1)   */

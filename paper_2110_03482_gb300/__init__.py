@@ -55,6 +55,7 @@ EXPORTS = [
     "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
     "fdd_destroy", "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
     "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins", "fdd_tdd_execute",
+    "fdd_debug_stall_test", "fdd_debug_fail_alloc",
 ]
 FDD_STATIC_MAX_CHAN = 8192
 
@@ -201,6 +202,8 @@ def lib() -> ctypes.CDLL:
         L.fdd_execute_dm_range.argtypes = [vp, vp, i32, i32, vp, vp]
         L.fdd_execute_host.argtypes = [vp, vp, vp, vp]
         L.fdd_tdd_execute.argtypes = [vp, vp, vp, vp]
+        L.fdd_debug_stall_test.argtypes = [vp, vp]
+        L.fdd_debug_fail_alloc.argtypes = [i32]
         L.fdd_dedisperse_spectra.argtypes = [vp, vp, i64, i32, i32, i32, vp, i64, i32, vp]
         L.fdd_dedisperse_spectra_bins.argtypes = [vp, vp, i64, i32, i32, i32, i32, i32, vp,
                                                   i64, i32, vp]
@@ -220,7 +223,7 @@ def lib() -> ctypes.CDLL:
                      "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
                      "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
                      "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins",
-                     "fdd_tdd_execute"]:
+                     "fdd_tdd_execute", "fdd_debug_stall_test", "fdd_debug_fail_alloc"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -311,6 +314,17 @@ def fdd_execute(plan: int, d_in, d_out, stream=None) -> None:
 def fdd_execute_dm_range(plan: int, d_in, dm_first: int, n_dm: int, d_out, stream=None) -> None:
     _check(lib().fdd_execute_dm_range(plan, _ptr(d_in), dm_first, n_dm, _ptr(d_out),
                                       _stream(stream)))
+
+
+def fdd_debug_stall_test(plan: int, stream=None) -> None:
+    """Run the plan's waiting kernel with producers that never arrive: its
+    bounded waits run out (~2 s) and the next query reports FDD_ERR_TIMEOUT."""
+    _check(lib().fdd_debug_stall_test(plan, _stream(stream)))
+
+
+def fdd_debug_fail_alloc(after: int) -> None:
+    """Make the device allocation after the next `after` ones fail once (-1: off)."""
+    _check(lib().fdd_debug_fail_alloc(after))
 
 
 def fdd_tdd_execute(plan: int, d_in, d_out, stream=None) -> None:
@@ -435,6 +449,9 @@ class Plan:
 
     def execute_host(self, h_in, h_out, stream=None):
         fdd_execute_host(self.handle, h_in, h_out, stream)
+
+    def debug_stall_test(self, stream=None):
+        fdd_debug_stall_test(self.handle, stream)
 
     def tdd_execute(self, d_in, d_out, stream=None):
         """Brute-force time-domain dedispersion (Eq. 2) with this plan's

@@ -5,7 +5,10 @@
 // of Algorithm 1 (Sect. 3) on device-resident data.
 #include <cufft.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -97,9 +100,15 @@ constexpr size_t kMaxSmem = 227 * 1024;
 constexpr int kProfSlots = 4096;
 
 // Records an event pair around one stage launch when profiling is on.
+const char* const kStageNames[FDD_STAGE_COUNT] = {"fdd unpack", "fdd r2c", "fdd mac",
+                                                   "fdd c2r", "fdd scatter", "fdd tdd"};
+
+// CUDA events around a stage launch when profiling is on, and an NVTX range
+// (named after the stage) always; both cost next to nothing without a tool.
 class StageTimer {
  public:
   StageTimer(fdd_plan_s* P, int stage, cudaStream_t s) : P_(P), s_(s) {
+    nvtxRangePushA(kStageNames[stage]);
     if (!P->prof_on) return;
     if (P->prof_n >= kProfSlots) {
       ++P->prof_dropped;
@@ -111,6 +120,7 @@ class StageTimer {
   }
   ~StageTimer() {
     if (idx_ >= 0) cudaEventRecord(P_->prof_ev[2 * idx_ + 1], s_);
+    nvtxRangePop();
   }
   StageTimer(const StageTimer&) = delete;
   StageTimer& operator=(const StageTimer&) = delete;
@@ -362,6 +372,10 @@ fdd_status need_uniform_grid(const fdd_plan_s* P) {
 }
 
 fdd_status dev_alloc(fdd_plan_s* P, void** ptr, size_t bytes) {
+  if (fdd::injected_alloc_failure()) {
+    *ptr = nullptr;
+    return fail(FDD_ERR_ALLOC, "injected allocation failure");
+  }
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -659,6 +673,16 @@ namespace fdd {
 
 fdd_status report_error(fdd_status s, const char* message) { return fail(s, "%s", message); }
 
+// fdd_debug_fail_alloc: allocations to let through before one fails (-1: none).
+std::atomic<int> g_fail_alloc{-1};
+
+bool injected_alloc_failure() {
+  int k = g_fail_alloc.load();
+  while (k >= 0)
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return k == 0;  // fails once, then off
+  return false;
+}
+
 uint64_t fixed64_phase_rate(double m, double rate, double L) {
   double hi, lo;
   scaled_product(m, rate, L, &hi, &lo);
@@ -814,8 +838,57 @@ fdd_status fdd_query(fdd_plan_t plan, fdd_info* out) {
   *out = plan->info;
   int word = 0;
   FDD_CUDA(cudaMemcpy(&word, plan->d_status, sizeof word, cudaMemcpyDeviceToHost));
+  if (word == 0) return FDD_OK;
+  FDD_CUDA(cudaMemset(plan->d_status, 0, sizeof word));  // reported once
   if (word == FDD_ERR_TIMEOUT) return fail(FDD_ERR_TIMEOUT, "a device-side wait timed out");
-  if (word != 0) return fail(FDD_ERR_DEVICE, "device status word %d", word);
+  return fail(FDD_ERR_DEVICE, "device status word %d", word);
+}
+
+fdd_status fdd_debug_fail_alloc(int32_t after) {
+  fdd::g_fail_alloc.store(after < 0 ? -1 : after);
+  return FDD_OK;
+}
+
+fdd_status fdd_debug_stall_test(fdd_plan_t plan, fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  fdd_status st = check_device(plan);
+  if (st != FDD_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // One bin, one trial, one series: a single CTA whose producers withhold
+  // every arrival; the plan's spectra buffer serves as (unread-for-value) X.
+  void* y = nullptr;
+  FDD_CUDA(cudaMalloc(&y, 64));
+  fdd::MacArgs m{};
+  m.X = plan->d_X;
+  m.x_chan_stride = plan->info.bin_pitch;
+  m.x_series_stride = plan->info.bin_pitch * plan->p.n_chan;
+  m.pc = plan->d_pc;
+  m.n_chan = plan->p.n_chan;
+  m.n_bins = 1;
+  m.n_series = 1;
+  m.j_begin = 0;
+  m.n_dm = 1;
+  m.Y = y;
+  m.y_dm_stride = 1;
+  m.y_series_stride = 1;
+  m.out_kind = 1;
+  m.scale = 1.0f;
+  m.real_bin_a = -1;
+  m.real_bin_b = -1;
+  m.status = plan->d_status;
+  m.test_withhold = 1;
+  cudaError_t e;
+  if (plan->tc) {
+    e = fdd::launch_mac_tc(m, plan->p.precision == FDD_PREC_BF16_HILO, plan->n_sms, plan->d_tcx,
+                           plan->tcx_bytes, s);
+  } else {
+    e = fdd::mac_prepare(fdd::MAC_W12_8x8, plan->p.n_chan);
+    if (e == cudaSuccess) e = fdd::launch_mac_fp32(m, fdd::MAC_W12_8x8, s);
+  }
+  const cudaError_t es = cudaStreamSynchronize(s);
+  cudaFree(y);
+  if (e != cudaSuccess) return fail(FDD_ERR_CUDA, "%s", cudaGetErrorString(e));
+  if (es != cudaSuccess) return fail(FDD_ERR_CUDA, "%s", cudaGetErrorString(es));
   return FDD_OK;
 }
 

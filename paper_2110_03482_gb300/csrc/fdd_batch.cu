@@ -103,6 +103,10 @@ void release(fdd_batch_s* B) {
 }
 
 fdd_status alloc(fdd_batch_s* B, void** p, size_t bytes) {
+  if (fdd::injected_alloc_failure()) {
+    *p = nullptr;
+    return fdd::report_error(FDD_ERR_ALLOC, "injected allocation failure");
+  }
   const cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;

@@ -38,6 +38,8 @@ struct MacArgs {
   int real_bin_a;           // absolute bins whose imaginary part is set to zero, or -1
   int real_bin_b;
   int* status;              // device status word (may be NULL)
+  int test_withhold;        // self-test only: producers never announce a filled stage,
+                            // so the consumers' bounded waits run out (FDD_ERR_TIMEOUT)
 };
 
 // Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu and the
@@ -113,6 +115,10 @@ struct BinTransposeArgs {
   float2* out;           // [n_bins][rows]
 };
 cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s);
+
+// Allocation-failure injection (fdd_debug_fail_alloc): true when this device
+// allocation is to fail; every library allocator asks before cudaMalloc.
+bool injected_alloc_failure();
 
 // Shared with the allocation-free entry point (fdd_noalloc.cu): the last-error
 // setter and the exact 64-bit fixed-point phase rate frac(m * rate / L) * 2^64.

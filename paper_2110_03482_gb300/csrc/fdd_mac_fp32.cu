@@ -651,7 +651,7 @@ __device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs,
           for (int q = 0; q < NB; ++q) gen[q].run(p, x[q][ch], st + (ch * kCons + q) * M::GFL);
         }
       }
-      dev::mbar_arrive_warp(&full[s]);
+      if (!a.test_withhold) dev::mbar_arrive_warp(&full[s]);
     }
   } else {
     // ------------------------------------------------------------ consumers

@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                             __fmul2_rn(qa, make_float2(r128.x, r128.x)));
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive_warp(&full[st]);
+          if (!a.test_withhold) mbar_arrive_warp(&full[st]);
         }
       }
     }
