@@ -588,12 +588,8 @@ struct WsLayout {
 // starting at local bin bin_tile * kCons and the trials dm_block * DMS + ..
 // of one set of spectra, with the phase table already in shared memory.
 // Stages and barrier phases continue from iteration it0 of the ring (items
-// of a persistent CTA follow one another).  kRegCons / kRegProd: registers
-// per thread of the consumer / producer warpgroups after a setmaxnreg split
-// (0: no split); kPre: consumers load the next channel's operands before the
-// current channel's MAC.  Returns false after a timeout.
-template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages, int kRegCons,
-          int kRegProd, bool kPre>
+// of a persistent CTA follow one another).  Returns false after a timeout.
+template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages>
 __device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs, float* stages,
                                         uint64_t* full, uint64_t* empty,
                                         volatile int* abort_flag, int bin_tile, int dm_block,
@@ -660,59 +656,22 @@ __device__ __forceinline__ bool ws_item(const MacArgs& a, const PhaseConst* pcs,
     const int gb = lane % Gm::GB;
     typename M::Acc acc;
     M::zero(acc);
-    if (!kPre) {
-      for (int it = 0; it < n_iter; ++it) {
-        const uint32_t g = it0 + it;
-        const int s = g % kWsStages;
-        ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kWsStages) & 1, abort_flag));
-        if (!ok) break;
-        const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
-        const int nc = a.n_chan - it * kWsCh;
+    for (int it = 0; it < n_iter; ++it) {
+      const uint32_t g = it0 + it;
+      const int s = g % kWsStages;
+      ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kWsStages) & 1, abort_flag));
+      if (!ok) break;
+      const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
+      const int nc = a.n_chan - it * kWsCh;
 #pragma unroll
-        for (int ch = 0; ch < kWsCh; ++ch) {
-          if (ch < nc) {
-            typename M::Ops ops;
-            M::load(st + ch * kCons * M::GFL, ga, gb, ops);
-            M::mac(acc, ops);
-          }
+      for (int ch = 0; ch < kWsCh; ++ch) {
+        if (ch < nc) {
+          typename M::Ops ops;
+          M::load(st + ch * kCons * M::GFL, ga, gb, ops);
+          M::mac(acc, ops);
         }
-        dev::mbar_arrive_warp(&empty[s]);
       }
-    } else {
-      // operands of channel ch in A (ch even) or B (ch odd); the next channel's
-      // are loaded before the current channel's MAC
-      static_assert(kWsCh % 2 == 0, "channels alternate between two operand sets");
-      typename M::Ops A, B;
-      {
-        const int s0 = it0 % kWsStages;
-        ok = __all_sync(0xffffffffu,
-                        dev::mbar_wait(&full[s0], (it0 / kWsStages) & 1, abort_flag));
-        if (ok) M::load(stages + s0 * Ly::kStageFloats + warp * M::GFL, ga, gb, A);
-      }
-      for (int it = 0; it < n_iter && ok; ++it) {
-        const uint32_t g = it0 + it;
-        const int s = g % kWsStages;
-        const float* st = stages + s * Ly::kStageFloats + warp * M::GFL;
-        const int nc = a.n_chan - it * kWsCh;
-#pragma unroll
-        for (int ch = 0; ch < kWsCh; ++ch) {
-          typename M::Ops& cur = (ch & 1) ? B : A;
-          typename M::Ops& nxt = (ch & 1) ? A : B;
-          if (ch < nc) {
-            if (ch + 1 < kWsCh) {
-              if (ch + 1 < nc) M::load(st + (ch + 1) * kCons * M::GFL, ga, gb, nxt);
-            } else if (it + 1 < n_iter) {
-              const uint32_t gn = g + 1;
-              const int sn = gn % kWsStages;
-              ok = __all_sync(0xffffffffu,
-                              dev::mbar_wait(&full[sn], (gn / kWsStages) & 1, abort_flag));
-              if (ok) M::load(stages + sn * Ly::kStageFloats + warp * M::GFL, ga, gb, nxt);
-            }
-            M::mac(acc, cur);
-          }
-        }
-        dev::mbar_arrive_warp(&empty[s]);
-      }
+      dev::mbar_arrive_warp(&empty[s]);
     }
     if (ok && k < a.n_bins) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
@@ -772,27 +731,15 @@ struct WsSmem {
   }
 };
 
-template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages, int kRegCons,
-          int kRegProd, bool kPre>
+template <class Gm, class M, int kCons, int kProd, int kWsCh, int kWsStages>
 __global__ void __launch_bounds__((kCons + kProd) * 32, 1) mac_ws_kernel(const MacArgs a) {
   using Ly = WsLayout<Gm, M, kCons, kProd, kWsCh, kWsStages>;
-  static_assert(kRegCons == 0 ||
-                    (kCons % 4 == 0 && kProd % 4 == 0 &&
-                     kRegCons * kCons + kRegProd * kProd <=
-                         (65536 / ((kCons + kProd) * 32) / 8 * 8) * (kCons + kProd)),
-                "register split above the launch's registers");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WsSmem<Ly> sm;
   sm.template init<kWsStages>(smem_raw, a.n_chan, kCons, kProd);
   for (int i = threadIdx.x; i < a.n_chan; i += blockDim.x) sm.pcs[i] = a.pc[i];
   __syncthreads();
-  if (kRegCons) {
-    if ((threadIdx.x >> 5) >= kCons)
-      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegProd));
-    else
-      asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCons));
-  }
-  ws_item<Gm, M, kCons, kProd, kWsCh, kWsStages, kRegCons, kRegProd, kPre>(
+  ws_item<Gm, M, kCons, kProd, kWsCh, kWsStages>(
       a, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag, blockIdx.x, blockIdx.y, blockIdx.z,
       0u);
 }
@@ -832,7 +779,7 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1)
     }
     __syncthreads();  // phase table ready; item_s read by every thread
     const long long local = item - bs.item_begin;
-    ws_item<Gm, M, kCons, kProd, kWsCh, kWsStages, 0, 0, false>(
+    ws_item<Gm, M, kCons, kProd, kWsCh, kWsStages>(
         bs.args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
         static_cast<int>(local / bs.n_dm_blocks), static_cast<int>(local % bs.n_dm_blocks), 0,
         it0);
@@ -1077,12 +1024,10 @@ VariantInfo info() {
           reinterpret_cast<const void*>(&mac_batch_kernel<Gm, M, kPipe, W>)};
 }
 
-template <class Gm, class M, int kCons, int kProd, int kCh = 4, int kSt = 3, int kRC = 0,
-          int kRP = 0, bool kPre = false>
+template <class Gm, class M, int kCons, int kProd, int kCh = 4, int kSt = 3>
 VariantInfo info_ws() {
   using Ly = WsLayout<Gm, M, kCons, kProd, kCh, kSt>;
-  VariantInfo vi{reinterpret_cast<const void*>(
-                     &mac_ws_kernel<Gm, M, kCons, kProd, kCh, kSt, kRC, kRP, kPre>),
+  VariantInfo vi{reinterpret_cast<const void*>(&mac_ws_kernel<Gm, M, kCons, kProd, kCh, kSt>),
                  Gm::DMS, Gm::NG, Ly::kSwapBytes, kCons + kProd,
                  reinterpret_cast<const void*>(&mac_ws_batch_kernel<Gm, M, kCons, kProd, kCh, kSt>)};
   vi.bin_warps = kCons;
