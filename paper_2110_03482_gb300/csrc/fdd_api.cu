@@ -321,7 +321,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   const size_t spectra_sets = tc ? static_cast<size_t>(p->n_beams) : 1;
   const size_t fixed = sizeof(fdd::PhaseConst) * nc + sizeof(float) * size_t(nc) * L +
                        sizeof(float2) * size_t(nc) * g->bin_pitch * spectra_sets + 256 +
-                       (tc ? fdd::mac_tc_scratch_bytes(p->n_beams, nc, n_bins) : 0);
+                       (tc ? fdd::mac_tc_scratch_bytes(p->n_beams, nc, p->n_dm, n_bins) : 0);
   const size_t limit = p->workspace_limit ? p->workspace_limit : kDefaultWorkspace;
   int64_t batch = p->n_dm;
   size_t per_dm = 0;
@@ -774,7 +774,7 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
     return st;
   const size_t sets = P->tc ? static_cast<size_t>(p->n_beams) : 1;
   if (P->tc) {
-    P->tcx_bytes = fdd::mac_tc_scratch_bytes(p->n_beams, nc, g.n_bins);
+    P->tcx_bytes = fdd::mac_tc_scratch_bytes(p->n_beams, nc, p->n_dm, g.n_bins);
     if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_tcx), P->tcx_bytes))) return st;
   }
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_X),

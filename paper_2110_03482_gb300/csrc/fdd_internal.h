@@ -33,6 +33,8 @@ struct MacArgs {
   void* Y;                  // [n_series][n_dm][y_dm_stride] complex or float
   int64_t y_series_stride;  // elements of the output type
   int64_t y_dm_stride;      // elements of the output type
+  int64_t y_bin_stride;     // elements between bins; used by the tensor-core kernel only
+                            // (the FP32 kernels write bins contiguous)
   int out_kind;             // 1 = complex spectra, 2 = |Y|^2
   float scale;              // multiplies Y before the store (power: |scale Y|^2)
   int real_bin_a;           // absolute bins whose imaginary part is set to zero, or -1
@@ -92,15 +94,18 @@ size_t mac_tc_smem_bytes();
 int mac_tc_trials_per_pass(int n_series);
 cudaError_t mac_tc_prepare();
 // Beams per tensor-core group: 16 when a call has at most 16 series (then a
-// pass covers 1024 trials), else 32 (512 trials per pass).
+// pass covers 2048 trials), else 32 (1024 trials per pass).
 int mac_tc_beams_per_group(int n_series);
 // The tensor-core kernel reads the spectra bin-major, X_T[k][series][chan]
-// (a 256-byte row per 32 channels of one beam); launch_mac_tc takes them in
-// the [series][chan][pitch] layout (x_series_stride = n_chan x_chan_stride)
-// and transposes them, a block of bins at a time, into `scratch` before each
-// block's launch.  mac_tc_scratch_bytes: the scratch a plan allocates for
-// n_series x n_chan spectra of n_bins bins (at most 2 GiB, at least one bin).
-size_t mac_tc_scratch_bytes(int n_series, int n_chan, int64_t n_bins);
+// (a 256-byte row per 32 channels of one beam), and writes Y bin-major,
+// Y_T[k][series][trial].  launch_mac_tc takes the caller's layouts (X as
+// [series][chan][pitch] with x_series_stride = n_chan x_chan_stride, Y with
+// bins innermost) and, a block of bins at a time, transposes X into
+// `scratch`, runs the kernel into the rest of `scratch`, and transposes Y
+// out.  mac_tc_scratch_bytes: the scratch a plan allocates for calls of up
+// to n_dm trials on n_series x n_chan spectra of n_bins bins (blocks of at
+// most 3 GiB, at least one bin).
+size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins);
 cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s);
 
@@ -115,6 +120,20 @@ struct BinTransposeArgs {
   float2* out;           // [n_bins][rows]
 };
 cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s);
+
+// The way back for the output: in[k][series][trial] (bin-major, n_bins bins)
+// into out + series * out_series_stride + trial * out_dm_stride + k.
+struct BinUntransposeArgs {
+  const void* in;
+  int elem_bytes;        // 8 (complex) or 4 (power)
+  int n_series;
+  int n_dm;
+  int n_bins;
+  void* out;
+  int64_t out_series_stride;  // elements
+  int64_t out_dm_stride;      // elements
+};
+cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s);
 
 // Allocation-failure injection (fdd_debug_fail_alloc): true when this device
 // allocation is to fail; every library allocator asks before cudaMalloc.

@@ -9,26 +9,36 @@
 //   Y[aT + b][beta] = sum_nu P_b[nu] Z_a[nu][beta],   Z_a = Q_a X[nu][beta],
 //
 // i.e. for every group of a's one complex GEMM of (T x N_nu) phasors P by
-// (N_nu x beams) data.  It runs on tcgen05 as a real GEMM
-//   D[b][(a, beta, re|im)] = sum_{nu, re|im} A[b][(nu, re|im)] B[(a, beta, re|im)][(nu, re|im)]
-// with A = [Pr | Pi] (BF16 hi + lo: two MMAs; or BF16 alone) and B the real embedding
-// [[Zr, -Zi], [Zi, Zr]] of Z (BF16), FP32 accumulation in tensor memory.
-// M = 128 trials b, N = 256 = 4 a's x 32 beams x (re, im), K = 64 per stage
-// (32 channels x (re, im)); one pass over the channels covers 4 a's = 512
-// trials, and passes alternate between two accumulators in tensor memory.
-// Calls with at most 16 series use groups of 16 beams instead: N = 256 = 8 a's
-// x 16 beams x (re, im), 1024 trials per pass, no idle columns.
+// (N_nu x beams) data.  It runs on tcgen05 as two real GEMMs that share one B
+// operand.  With K = (nu, re|im) and B[(a, beta)][(nu, c)] = (Zr, Zi)[nu]:
+//
+//   D_re[b][(a, beta)] = sum_K A_re[b][K] B[(a, beta)][K],   A_re = (Pr, -Pi),
+//   D_im[b][(a, beta)] = sum_K A_im[b][K] B[(a, beta)][K],   A_im = (Pi,  Pr),
+//
+// i.e. Re and Im of P Z.  Phasors are BF16 hi + lo (four MMAs per K step) or
+// BF16 alone (two), data BF16, accumulation FP32 in tensor memory.  M = 128
+// trials b, N = 256 (a, beta) pairs (8 a's x 32 beams, or 16 a's x 16 beams
+// for calls with at most 16 series), K = 64 per stage (32 channels x
+// (re, im)).  D_re and D_im fill all 512 tensor-memory columns, so one pass
+// over the channels covers 1024 trials (2048 in 16-beam groups): every P tile
+// the producers build serves 256 output columns, and every Z value is
+// written to shared memory once.
 //
 // Warp specialisation: warp 0 allocates tensor memory and one of its threads
 // issues the MMAs; 16 producer warps evaluate P (exact fixed-point phase,
 // MUFU sin/cos and short recurrences, hi/lo split) and Z = Q X for each stage
 // straight into the 128-byte-swizzled K-major shared layout the MMA
-// descriptors address, through a 3-stage mbarrier ring; 4 epilogue warps read
-// one accumulator back (tcgen05.ld) and store it while the MMAs of the next
-// pass fill the other.  Barriers count warps (one arrive per warp).
-// Every wait is bounded: on timeout the kernel records FDD_ERR_TIMEOUT in the
-// status word, stops, drains its own MMAs (bounded), frees its tensor memory
-// and returns.
+// descriptors address, through an mbarrier ring (2 stages of 96 KB with hi +
+// lo phasors, 3 of 64 KB without); 4 epilogue warps read the accumulators
+// back (tcgen05.ld) and store them, while the producers already fill the ring
+// for the next pass.  The kernel writes Y bin-major, [bin][series][trial], so
+// each warp store covers 256 contiguous bytes; launch_mac_tc then moves it
+// into the caller's layout (bins innermost) with an HBM-bound transpose.
+// (Stored straight into that layout, each 8-byte value of one bin is its own
+// partial sector, and those scattered stores cost more than the transpose.)
+// Barriers count warps (one arrive per warp).  Every wait is bounded: on
+// timeout the kernel records FDD_ERR_TIMEOUT in the status word, stops,
+// drains its own MMAs (bounded), frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include "fdd_device.cuh"
@@ -46,23 +56,27 @@ using dev::top32_mul;
 using dev::unit_phasor;
 
 constexpr int kM = 128;                  // trials b per a (T)
-constexpr int kN = 256;                  // accumulator columns
+constexpr int kN = 256;                  // (a, beta) columns of each accumulator
 // Beams per group (kBeams, 16 or 32) is a template parameter: a pass covers
-// kNA = kN / (2 kBeams) a's, i.e. kNA * kM trials.
+// kN / kBeams a's, i.e. kN / kBeams * kM trials.
 template <int kBeams>
-__host__ __device__ constexpr int dms_per_pass() { return kN / (2 * kBeams) * kM; }
+__host__ __device__ constexpr int dms_per_pass() { return kN / kBeams * kM; }
 constexpr int kKC = 32;                  // channels per stage
 constexpr int kProdWarps = 16;
-constexpr int kProd = 32 * kProdWarps;
 constexpr int kEpiWarps = 4;             // one per tensor-memory lane quarter
-constexpr int kEpi = 32 * kEpiWarps;
-constexpr int kThreads = 32 + kEpi + kProd;
+constexpr int kThreads = 32 + 32 * kEpiWarps + 32 * kProdWarps;
 constexpr uint32_t kTileA = kM * 64 * 2;  // 16 KB
 constexpr uint32_t kTileB = kN * 64 * 2;  // 32 KB
-constexpr uint32_t kStageBytes = 2 * kTileA + kTileB;  // 64 KB
-constexpr int kStages = 3;
-constexpr int kAccBufs = 2;              // accumulators alternate between passes
-constexpr uint32_t kTmemCols = kAccBufs * kN;
+constexpr uint32_t kRingBytes = 192 * 1024;
+// Stage layout: A_re hi, A_im hi (, A_re lo, A_im lo), then B.
+template <bool kHiLo>
+struct Ring {
+  static constexpr int kATiles = kHiLo ? 4 : 2;
+  static constexpr uint32_t kBOff = kATiles * kTileA;
+  static constexpr uint32_t kStageBytes = kBOff + kTileB;       // 96 or 64 KB
+  static constexpr int kStages = kRingBytes / kStageBytes;      // 2 or 3
+};
+constexpr uint32_t kTmemCols = 2 * kN;   // D_re | D_im
 
 // Byte offset of element (row, kk) in a K-major tile of 64 BF16 per row with
 // the 128-byte swizzle: 16-byte chunks of a row are permuted by (row mod 8).
@@ -87,34 +101,54 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes, from two
+// places at once (one wait for both loads).
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (&r)[16],
+                                            uint32_t (&q)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+        "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
+        "=r"(q[14]), "=r"(q[15])
+      : "r"(tb));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// kHiLo: phasors as BF16 hi + lo (two MMAs per K step); otherwise BF16 only.
+// D (+)= A B^T for one K step of 16: M = 128, N = 256, BF16 in, FP32 out.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum));
+}
+
+// kHiLo: phasors as BF16 hi + lo (four MMAs per K step); otherwise BF16 only.
 template <bool kHiLo, int kBeams>
 __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
-  constexpr int kNA = kN / (2 * kBeams);      // a's per pass
+  constexpr int kNA = kN / kBeams;            // a's per pass (8 or 16)
   constexpr int kDmsPass = dms_per_pass<kBeams>();
+  constexpr int kStages = Ring<kHiLo>::kStages;
+  constexpr uint32_t kStageBytes = Ring<kHiLo>::kStageBytes;
+  constexpr uint32_t kBOff = Ring<kHiLo>::kBOff;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kRingBytes);
   uint64_t* full = bars;                        // [kStages]  producers -> MMA
   uint64_t* empty = bars + kStages;             // [kStages]  MMA commit -> producers
-  uint64_t* acc_full = bars + 2 * kStages;      // [kAccBufs] MMA commit -> epilogue
-  uint64_t* acc_empty = acc_full + kAccBufs;    // [kAccBufs] epilogue -> MMA
-  uint64_t* drain = acc_empty + kAccBufs;
+  uint64_t* acc_full = bars + 2 * kStages;      // MMA commit -> epilogue
+  uint64_t* acc_empty = acc_full + 1;           // epilogue -> MMA
+  uint64_t* drain = acc_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -125,10 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       mbar_init(&full[i], kProdWarps);  // one arrive per producer warp
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < kAccBufs; ++i) {
-      mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], kEpiWarps);  // one arrive per epilogue warp
-    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);    // one arrive per epilogue warp
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -157,13 +189,12 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       bool issued = false, ok = true;
       for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
         for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
-          const uint32_t buf = p % kAccBufs;
-          if (!mbar_wait(&acc_empty[buf], ((p / kAccBufs) & 1) ^ 1, abort_flag)) {
+          // the epilogue has read the previous pass out of tensor memory
+          if (!mbar_wait(acc_empty, (p & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t d = tmem + buf * kN;
           for (int t = 0; t < n_tiles; ++t, ++s) {
             const uint32_t st = s % kStages;
             if (!mbar_wait(&full[st], (s / kStages) & 1, abort_flag)) {
@@ -174,19 +205,14 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             const uint32_t stage = smem_u32(base + st * kStageBytes);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t bd = smem_desc(stage + 2 * kTileA + kk * 32);
-              const uint64_t ahi = smem_desc(stage + kk * 32);
-              const uint64_t alo = smem_desc(stage + kTileA + kk * 32);
+              const uint64_t bd = smem_desc(stage + kBOff + kk * 32);
               const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-                  "l"(ahi), "l"(bd), "r"(kIdesc), "r"(accum));
-              if (kHiLo)
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-                    "l"(alo), "l"(bd), "r"(kIdesc), "r"(1u));
+              mma_bf16(tmem, smem_desc(stage + kk * 32), bd, accum);               // re, hi
+              mma_bf16(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum);  // im, hi
+              if (kHiLo) {
+                mma_bf16(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u);       // re, lo
+                mma_bf16(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u);  // im, lo
+              }
             }
             issued = true;
             asm volatile(
@@ -197,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           if (!ok) break;
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(&acc_full[buf]))
+                  smem_u32(acc_full))
               : "memory");
         }
       }
@@ -216,48 +242,58 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     }
   } else if (warp <= kEpiWarps) {
     // ------------------------------------------------------------ epilogue
-    // Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (trials b), all 256
-    // columns (a, beta, re|im) of the pass's accumulator, and stores Y.
+    // Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (trials b) of D_re
+    // and D_im, all 256 (a, beta) columns, and stores Y[k][beta][aT + b]:
+    // the warp's 32 lanes write 32 consecutive trials.
     const int quarter = warp & 3;  // the lanes this warp may read
     const int b = quarter * 32 + lane;
+    const uint32_t t_lanes = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     uint32_t p = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
+      const float2 sc = make_float2(a.scale, real_only ? 0.f : a.scale);
+      const int64_t o_bin = static_cast<int64_t>(k) * a.y_bin_stride;
       for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
-        const uint32_t buf = p % kAccBufs;
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (p / kAccBufs) & 1, abort_flag))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(acc_full, p & 1, abort_flag))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-        for (int c0 = 0; c0 < kN; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * kN + c0, r);
+        for (int c0 = 0; c0 < kN; c0 += 16) {
+          uint32_t re[16], im[16];
+          tmem_ld16x2(t_lanes + c0, t_lanes + kN + c0, re, im);
+          // the 16 columns share a_in = c0 / kBeams; beams beta0 .. beta0 + 15
+          const int bg0 = group * kBeams + c0 % kBeams;
+          const int jl = j_pass + (c0 / kBeams) * kM + b;
+          const int n_valid = a.n_series - bg0;  // beams of this chunk in range (may be <= 0)
+          if (jl < a.n_dm && n_valid > 0) {
+            const int64_t o0 = o_bin + static_cast<int64_t>(bg0) * a.y_series_stride +
+                               static_cast<int64_t>(jl) * a.y_dm_stride;
+            if (a.out_kind == 2) {
+              float* q = static_cast<float*>(a.Y) + o0;
 #pragma unroll
-          for (int h = 0; h < 16; ++h) {
-            const int n = c0 + 2 * h;  // (a_in, beta, re) column
-            const int a_in = n / (2 * kBeams);
-            const int beta = (n % (2 * kBeams)) / 2;
-            const int bg = group * kBeams + beta;
-            const int jl = j_pass + a_in * kM + b;
-            if (bg < a.n_series && jl < a.n_dm) {
-              const float re = __uint_as_float(r[2 * h]) * a.scale;
-              const float im = real_only ? 0.f : __uint_as_float(r[2 * h + 1]) * a.scale;
-              const int64_t o = static_cast<int64_t>(bg) * a.y_series_stride +
-                                static_cast<int64_t>(jl) * a.y_dm_stride + k;
-              if (a.out_kind == 2)
-                static_cast<float*>(a.Y)[o] = re * re + im * im;
-              else
-                static_cast<float2*>(a.Y)[o] = make_float2(re, im);
+              for (int h = 0; h < 16; ++h) {
+                const float2 y =
+                    __fmul2_rn(make_float2(__uint_as_float(re[h]), __uint_as_float(im[h])), sc);
+                if (h < n_valid) q[h * a.y_series_stride] = y.x * y.x + y.y * y.y;
+              }
+            } else {
+              float2* q = static_cast<float2*>(a.Y) + o0;
+#pragma unroll
+              for (int h = 0; h < 16; ++h) {
+                const float2 y =
+                    __fmul2_rn(make_float2(__uint_as_float(re[h]), __uint_as_float(im[h])), sc);
+                if (h < n_valid) q[h * a.y_series_stride] = y;
+              }
             }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive_warp(&acc_empty[buf]);
+        mbar_arrive_warp(acc_empty);
       }
     }
     if (!ok) {
@@ -269,20 +305,21 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     // Producer warp pw (0..15) evaluates, for channel nu = tile*32 + lane:
     //   P_b for the 8 rows b = 8 pw .. 8 pw + 7 (one direct phasor, then the
     //   recurrence P_{b+1} = P_b R with R = exp(2 pi i k v), at most 7 steps),
-    //   Q_a for the pass's kNA a's (Q_0 direct, Q_{a+1} = Q_a R^128),
+    //   stored as the A_re and A_im rows (hi, and lo = P - hi);
+    //   Q_a for the pass's kNA a's as two chains of kNA / 2 (Q of each
+    //   chain's first a direct, then Q_{a+1} = Q_a R^128),
     //   Z_a = Q_a X for the beams beta = pw (and pw + 16 in 32-beam groups).
     // X and the phase constants of the next tile are loaded one stage ahead.
     const int pw = warp - 1 - kEpiWarps;           // 0..15
     constexpr int kRows = kM / kProdWarps;         // P rows per warp (8)
     constexpr int kBeamsPerWarp = kBeams / kProdWarps;  // 1 or 2
+    constexpr int kHalfA = kNA / 2;                // a's per Q chain
     // Store offsets that do not change between stages (see sw128): the P
-    // rows of this warp, and the Z rows (al*kBeams + pw + 16m)*2 + e, whose
-    // position within an 8-row group depends only on pw and e.
+    // rows of this warp, and the B rows a_in * kBeams + pw + 16 m, whose
+    // position within an 8-row group is pw mod 8.
     const uint32_t lane_chunk = static_cast<uint32_t>((lane >> 2) << 4);
     const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
-    uint32_t z_base[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) z_base[e] = sw128(2 * pw + e, 2 * lane);  // rows < 32
+    const uint32_t z_base = sw128(pw, 2 * lane);  // row pw < 16
     uint32_t s = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
@@ -325,14 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                               : make_float2(0.f, 0.f);
             }
           }
-          // phasors in registers before touching the stage
-          float2 r1 = make_float2(0.f, 0.f), pb = r1, qa = r1, r128 = r1;
+          // phasors in registers before touching the stage (zero beyond n_chan)
+          float2 r1 = make_float2(0.f, 0.f), pb = r1, r128 = r1, qa = r1, qb = r1;
           if (nu_ok) {
             r1 = unit_phasor(top32_mul(ku, pc.v_lo, pc.v_hi));
             pb = unit_phasor(top32_mul(ku * static_cast<uint32_t>(pw * kRows), pc.v_lo, pc.v_hi));
             r128 = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kM), pc.v_lo, pc.v_hi));
             const uint32_t ja = static_cast<uint32_t>(a.j_begin + j_pass);
-            qa = unit_phasor(top32_mul(ku, pc.u_lo, pc.u_hi) + top32_mul(ku * ja, pc.v_lo, pc.v_hi));
+            const uint32_t ph_u = top32_mul(ku, pc.u_lo, pc.u_hi);
+            qa = unit_phasor(ph_u + top32_mul(ku * ja, pc.v_lo, pc.v_hi));
+            qb = unit_phasor(ph_u + top32_mul(ku * (ja + static_cast<uint32_t>(kHalfA * kM)),
+                                              pc.v_lo, pc.v_hi));
           }
           const uint32_t st = s % kStages;
           if (!__all_sync(0xffffffffu, mbar_wait(&empty[st], ((s / kStages) & 1) ^ 1, abort_flag))) {
@@ -340,41 +380,49 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             break;
           }
           unsigned char* stage = base + st * kStageBytes;
-          // P rows b = 8 pw + i fill one 8-row swizzle group: the 16-byte chunk
+          // A rows b = 8 pw + i fill one 8-row swizzle group: the 16-byte chunk
           // of column pair 2*lane is (lane/4) ^ i, the rest is a constant.
 #pragma unroll
           for (int i = 0; i < kRows; ++i) {
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(pb.x, pb.y);
-            const uint32_t hb = bf16x2_bits(hi);
-            // residual P - hi (the hi halves widened back to FP32)
-            const float2 res = __ffma2_rn(make_float2(__uint_as_float(hb << 16),
-                                                      __uint_as_float(hb & 0xFFFF0000u)),
-                                          make_float2(-1.f, -1.f), pb);
+            const uint32_t hb = bf16x2_bits(__floats2bfloat162_rn(pb.x, pb.y));  // (pr, pi)
             const uint32_t off = p_base + i * 128 + ((lane_chunk ^ (i << 4)));
-            *reinterpret_cast<uint32_t*>(stage + off) = hb;
-            if (kHiLo)
-              *reinterpret_cast<uint32_t*>(stage + kTileA + off) =
-                  bf16x2_bits(__floats2bfloat162_rn(res.x, res.y));
+            *reinterpret_cast<uint32_t*>(stage + off) = hb ^ 0x80000000u;                  // (pr, -pi)
+            *reinterpret_cast<uint32_t*>(stage + kTileA + off) = __byte_perm(hb, 0, 0x1032);  // (pi, pr)
+            if (kHiLo) {
+              // residual P - hi (the hi halves widened back to FP32)
+              const float2 res = __ffma2_rn(make_float2(__uint_as_float(hb << 16),
+                                                        __uint_as_float(hb & 0xFFFF0000u)),
+                                            make_float2(-1.f, -1.f), pb);
+              const uint32_t lb = bf16x2_bits(__floats2bfloat162_rn(res.x, res.y));
+              *reinterpret_cast<uint32_t*>(stage + 2 * kTileA + off) = lb ^ 0x80000000u;
+              *reinterpret_cast<uint32_t*>(stage + 3 * kTileA + off) = __byte_perm(lb, 0, 0x1032);
+            }
             // P <- P R as a paired multiply-add: (pr, pi) r1r + (-pi, pr) r1i
             pb = __ffma2_rn(make_float2(-pb.y, pb.x), make_float2(r1.y, r1.y),
                             __fmul2_rn(pb, make_float2(r1.x, r1.x)));
           }
-          unsigned char* tb = stage + 2 * kTileA;
+          unsigned char* tb = stage + kBOff;
 #pragma unroll
-          for (int al = 0; al < kNA; ++al) {
+          for (int al = 0; al < kHalfA; ++al) {
 #pragma unroll
             for (int m = 0; m < kBeamsPerWarp; ++m) {
-              // Z = X Q as (xr, xr)(qr, qi) + (-xi, xi)(qi, qr)
-              const float2 z = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qa.y, qa.x),
-                                          __fmul2_rn(make_float2(x[m].x, x[m].x), qa));
-              const uint32_t zb = bf16x2_bits(__floats2bfloat162_rn(z.x, z.y));
-              // rows (al*kBeams + beta)*2 + {0, 1}: per-thread base + a constant
-              const uint32_t row_off = static_cast<uint32_t>((kBeams / 4 * al + 4 * m) * 1024);
-              *reinterpret_cast<uint32_t*>(tb + z_base[0] + row_off) = zb ^ 0x80000000u;  // (zr, -zi)
-              *reinterpret_cast<uint32_t*>(tb + z_base[1] + row_off) = __byte_perm(zb, 0, 0x1032);  // (zi, zr)
+              // Z = X Q as (xr, xr)(qr, qi) + (-xi, xi)(qi, qr), for a = al and al + kHalfA
+              const float2 za = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qa.y, qa.x),
+                                           __fmul2_rn(make_float2(x[m].x, x[m].x), qa));
+              const float2 zb = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qb.y, qb.x),
+                                           __fmul2_rn(make_float2(x[m].x, x[m].x), qb));
+              // row a_in * kBeams + pw + 16 m: z_base + (kBeams / 8 * a_in + 2 m) groups
+              const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
+              const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
+              *reinterpret_cast<uint32_t*>(tb + z_base + ra) =
+                  bf16x2_bits(__floats2bfloat162_rn(za.x, za.y));
+              *reinterpret_cast<uint32_t*>(tb + z_base + rb) =
+                  bf16x2_bits(__floats2bfloat162_rn(zb.x, zb.y));
             }
             qa = __ffma2_rn(make_float2(-qa.y, qa.x), make_float2(r128.y, r128.y),
                             __fmul2_rn(qa, make_float2(r128.x, r128.x)));
+            qb = __ffma2_rn(make_float2(-qb.y, qb.x), make_float2(r128.y, r128.y),
+                            __fmul2_rn(qb, make_float2(r128.x, r128.x)));
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           if (!a.test_withhold) mbar_arrive_warp(&full[st]);
@@ -398,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
 
 }  // namespace
 
-size_t mac_tc_smem_bytes() { return kStages * kStageBytes + 1024 + 128; }
+size_t mac_tc_smem_bytes() { return kRingBytes + 1024 + 128; }
 
 int mac_tc_beams_per_group(int n_series) { return n_series <= 16 ? 16 : 32; }
 
@@ -421,13 +469,22 @@ cudaError_t mac_tc_prepare() {
 
 static cudaError_t launch_mac_tc_block(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s);
 
-size_t mac_tc_scratch_bytes(int n_series, int n_chan, int64_t n_bins) {
-  const size_t per_bin = sizeof(float2) * static_cast<size_t>(n_series) * n_chan;
-  const size_t cap = size_t(2) << 30;
-  int64_t kb = static_cast<int64_t>(cap / per_bin);
+namespace {
+constexpr size_t kScratchAlign = 256;
+constexpr size_t kScratchCap = size_t(3) << 30;
+// Scratch bytes per bin: the bin-major spectra and the bin-major output
+// (complex, the larger of the two output kinds).
+size_t scratch_per_bin(int n_series, int n_chan, int n_dm) {
+  return sizeof(float2) * static_cast<size_t>(n_series) * (static_cast<size_t>(n_chan) + n_dm);
+}
+}  // namespace
+
+size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins) {
+  const size_t per_bin = scratch_per_bin(n_series, n_chan, n_dm);
+  int64_t kb = static_cast<int64_t>(kScratchCap / per_bin);
   if (kb < 1) kb = 1;
   if (kb > n_bins) kb = n_bins;
-  return per_bin * static_cast<size_t>(kb);
+  return per_bin * static_cast<size_t>(kb) + kScratchAlign;
 }
 
 cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scratch,
@@ -435,9 +492,17 @@ cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scrat
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   if (a.x_series_stride != a.x_chan_stride * a.n_chan) return cudaErrorInvalidValue;
   const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
-  const int64_t kb = static_cast<int64_t>(scratch_bytes / (sizeof(float2) * rows));
-  if (!scratch || kb < 1) return cudaErrorInvalidValue;
+  const int64_t y_rows = static_cast<int64_t>(a.n_series) * a.n_dm;
   const size_t y_elem = a.out_kind == 2 ? sizeof(float) : sizeof(float2);
+  const size_t per_bin = sizeof(float2) * rows + y_elem * y_rows;
+  const int64_t kb = scratch_bytes > kScratchAlign
+                         ? static_cast<int64_t>((scratch_bytes - kScratchAlign) / per_bin)
+                         : 0;
+  if (!scratch || kb < 1) return cudaErrorInvalidValue;
+  // [kb][rows] spectra, then (256-byte aligned) [kb][series][trial] output
+  const uintptr_t y_addr =
+      (reinterpret_cast<uintptr_t>(scratch + kb * rows) + kScratchAlign - 1) & ~(kScratchAlign - 1);
+  void* y_scratch = reinterpret_cast<void*>(y_addr);
   for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb) {
     const int nb = static_cast<int>((a.n_bins - k0) < kb ? (a.n_bins - k0) : kb);
     BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, scratch};
@@ -450,8 +515,16 @@ cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scrat
     b.x_chan_stride = 1;
     b.n_bins = nb;
     b.k_begin = a.k_begin + static_cast<int>(k0);
-    b.Y = static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0);
+    b.Y = y_scratch;
+    b.y_bin_stride = y_rows;
+    b.y_series_stride = a.n_dm;
+    b.y_dm_stride = 1;
     e = launch_mac_tc_block(b, hi_lo, n_sms, s);
+    if (e != cudaSuccess) return e;
+    BinUntransposeArgs u{y_scratch, static_cast<int>(y_elem), a.n_series, a.n_dm, nb,
+                         static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0),
+                         a.y_series_stride, a.y_dm_stride};
+    e = launch_bin_untranspose(u, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

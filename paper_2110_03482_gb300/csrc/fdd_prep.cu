@@ -4,7 +4,8 @@
 //    beam becomes channel-major float series of L samples, zero beyond n_t;
 //  * scatter: apply_scaling of Algorithm 1 (1/L) and keep the first n_keep
 //    samples of each inverse-transformed DM series (discard rule, Sect. 2.2);
-//  * bin transpose: spectra [row][bin] -> [bin][row] for the tensor-core form.
+//  * bin transpose: spectra [row][bin] -> [bin][row] for the tensor-core
+//    form, and its output back, [bin][series][trial] -> [series][trial][bin].
 #include "fdd_internal.h"
 #include "fdd.h"
 
@@ -97,7 +98,60 @@ __global__ void __launch_bounds__(256) bin_transpose_kernel(const float2* __rest
   }
 }
 
+// 32 trials x 32 bins of one series through shared memory: coalesced reads
+// along trials (bin-major input), coalesced writes along bins.  Tiles of
+// (series, trial) beyond gridDim.y are covered by a grid-stride loop.
+template <typename T>
+__global__ void __launch_bounds__(256) bin_untranspose_kernel(const T* __restrict__ in,
+                                                              int n_series, int n_dm, int n_bins,
+                                                              T* __restrict__ out,
+                                                              int64_t out_series_stride,
+                                                              int64_t out_dm_stride) {
+  __shared__ T tile[kTile][kTile + 1];
+  const int kb0 = blockIdx.x * kTile;
+  const int d_tiles = (n_dm + kTile - 1) / kTile;
+  const int64_t rows = static_cast<int64_t>(n_series) * n_dm;  // per bin
+  const int64_t n_tiles = static_cast<int64_t>(n_series) * d_tiles;
+  for (int64_t q = blockIdx.y; q < n_tiles; q += gridDim.y) {
+    const int sr = static_cast<int>(q / d_tiles);
+    const int d0 = static_cast<int>(q - static_cast<int64_t>(sr) * d_tiles) * kTile;
+    const T* src = in + static_cast<int64_t>(sr) * n_dm;
+#pragma unroll
+    for (int i = threadIdx.y; i < kTile; i += 8) {
+      const int kb = kb0 + i;
+      const int d = d0 + threadIdx.x;
+      if (kb < n_bins && d < n_dm) tile[i][threadIdx.x] = src[static_cast<int64_t>(kb) * rows + d];
+    }
+    __syncthreads();
+    T* dst = out + static_cast<int64_t>(sr) * out_series_stride;
+#pragma unroll
+    for (int i = threadIdx.y; i < kTile; i += 8) {
+      const int d = d0 + i;
+      const int kb = kb0 + threadIdx.x;
+      if (kb < n_bins && d < n_dm) dst[static_cast<int64_t>(d) * out_dm_stride + kb] = tile[threadIdx.x][i];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s) {
+  if (a.n_bins <= 0 || a.n_dm <= 0 || a.n_series <= 0) return cudaSuccess;
+  const int64_t tiles = static_cast<int64_t>(a.n_series) * ((a.n_dm + kTile - 1) / kTile);
+  dim3 grid((a.n_bins + kTile - 1) / kTile, static_cast<unsigned>(tiles < 65535 ? tiles : 65535));
+  if (a.elem_bytes == 8)
+    bin_untranspose_kernel<float2><<<grid, dim3(kTile, 8), 0, s>>>(
+        static_cast<const float2*>(a.in), a.n_series, a.n_dm, a.n_bins,
+        static_cast<float2*>(a.out), a.out_series_stride, a.out_dm_stride);
+  else if (a.elem_bytes == 4)
+    bin_untranspose_kernel<float><<<grid, dim3(kTile, 8), 0, s>>>(
+        static_cast<const float*>(a.in), a.n_series, a.n_dm, a.n_bins,
+        static_cast<float*>(a.out), a.out_series_stride, a.out_dm_stride);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s) {
   if (a.n_bins <= 0 || a.rows <= 0) return cudaSuccess;

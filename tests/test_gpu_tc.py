@@ -5,7 +5,7 @@ The gate is the low-precision form's relative L2 error <= 3e-3 against FP64:
 BF16 rounding of the data side alone is ~2^-9 / sqrt(3) ~ 1.1e-3 per element.
 Shapes span partial and several beam groups (16 beams each for calls of at
 most 16 series, else 32), a ragged last channel tile (32 channels each) and
-partial trial passes (1024 trials in 16-beam groups, 512 in 32-beam groups).
+partial trial passes (2048 trials in 16-beam groups, 1024 in 32-beam groups).
 """
 import numpy as np
 import pytest
@@ -42,10 +42,11 @@ def _workload(n_chan, n_t, dms, n_beams, band=(1200.0, 1500.0), t_samp=2e-3, chu
 @pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16],
                          ids=["bf16_hilo", "bf16"])
 @pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
-    (5, 40, 256, 0.0, 0.5, 1100),    # partial beam group, ragged channel tile, 2 passes
+    (5, 40, 256, 0.0, 0.5, 2100),    # partial 16-beam group, ragged channel tile, 2 passes
     (32, 64, 128, 3.0, 1.0, 1024),   # one full group, exactly one pass
     (37, 33, 512, 0.0, 0.25, 300),   # two groups, one partial pass
-    (16, 64, 512, 1.0, 0.25, 2100),  # one full 16-beam group, 1024-trial passes, ragged
+    (16, 64, 512, 1.0, 0.25, 2100),  # one full 16-beam group, 2048-trial passes, ragged
+    (33, 40, 256, 0.5, 0.5, 2200),   # 32-beam groups (one of 1 beam), 3 passes, ragged
 ])
 def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm, precision):
     dms = dm0 + ddm * np.arange(n_dm)
