@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(256) unpack_chan_major_kernel(const Tin* __res
   }
 }
 
+// One row per blockIdx.y.  The destination rows start at arbitrary offsets,
+// so each thread writes 16-byte aligned float4 groups of the row (a scalar
+// head and tail around them) and reads its four source values with plain
+// loads; a warp's loads cover 512 contiguous bytes of the row.
 __global__ void __launch_bounds__(256) scatter_kernel(const float* __restrict__ src,
                                                       int64_t src_stride, float* __restrict__ dst,
                                                       int64_t dst_stride, int64_t n_keep,
@@ -65,9 +69,21 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float* __restrict__ 
   const int r = blockIdx.y;
   const float* s = src + static_cast<int64_t>(r) * src_stride;
   float* d = dst + static_cast<int64_t>(r) * dst_stride;
-  for (int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; n < n_keep;
-       n += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    d[n] = s[n] * scale;
+  // elements before the first 16-byte boundary of the destination row
+  int64_t head = static_cast<int64_t>((16 - (reinterpret_cast<uintptr_t>(d) & 15)) & 15) / 4;
+  if (head > n_keep) head = n_keep;
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  if (tid < head) d[tid] = s[tid] * scale;
+  const int64_t n_vec = (n_keep - head) / 4;
+  float4* dv = reinterpret_cast<float4*>(d + head);
+  const float* sv = s + head;
+  for (int64_t q = tid; q < n_vec; q += nth) {
+    const float* p = sv + 4 * q;
+    dv[q] = make_float4(p[0] * scale, p[1] * scale, p[2] * scale, p[3] * scale);
+  }
+  const int64_t t0 = head + 4 * n_vec;
+  if (t0 + tid < n_keep) d[t0 + tid] = s[t0 + tid] * scale;
 }
 
 // 32 bins x 32 rows through shared memory: coalesced reads along bins,
@@ -191,7 +207,8 @@ cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t s) {
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_keep <= 0) return cudaSuccess;
   if (a.n_dm > 65535) return cudaErrorInvalidConfiguration;
-  const int64_t blocks = (a.n_keep + 255) / 256;
+  // about 8 float4 groups per thread
+  const int64_t blocks = (a.n_keep + 256 * 32 - 1) / (256 * 32);
   dim3 grid(static_cast<unsigned>(blocks < 1024 ? blocks : 1024), a.n_dm);
   scatter_kernel<<<grid, 256, 0, s>>>(a.src, a.src_stride, a.dst, a.dst_stride, a.n_keep,
                                       a.scale);
