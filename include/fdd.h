@@ -99,8 +99,8 @@ typedef enum fdd_status {
 #define FDD_PREC_BF16_HILO 1 /* tensor cores (tcgen05), the direction of Sect. 5:
                                 BF16 hi+lo phasors, BF16 data, FP32 accumulation;
                                 all beams of a chunk share each bin's phasors    */
-#define FDD_PREC_BF16 2      /* the same with BF16 phasors only (one MMA per step,
-                                about half the tensor work, larger error)        */
+#define FDD_PREC_BF16 2      /* the same with BF16 phasors only (half the tensor
+                                work of hi+lo, larger error)                     */
 
 typedef struct fdd_params {
   int32_t n_chan;         /* observing channels N_nu, >= 1                          */

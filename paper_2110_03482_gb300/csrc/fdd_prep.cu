@@ -117,8 +117,12 @@ __global__ void __launch_bounds__(256) bin_transpose_kernel(const float2* __rest
 // 32 trials x 32 bins of one series through shared memory: coalesced reads
 // along trials (bin-major input), coalesced writes along bins.  Tiles of
 // (series, trial) beyond gridDim.y are covered by a grid-stride loop.
+// Thread rows of the untranspose's 32 x 32 tiles (4: measured 5.7 TB/s on the
+// 32-beam slice, against 5.5 TB/s with 8 rows and less with wider tiles).
+constexpr int kUntrRows = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(256) bin_untranspose_kernel(const T* __restrict__ in,
+__global__ void __launch_bounds__(32 * kUntrRows) bin_untranspose_kernel(const T* __restrict__ in,
                                                               int n_series, int n_dm, int n_bins,
                                                               T* __restrict__ out,
                                                               int64_t out_series_stride,
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(256) bin_untranspose_kernel(const T* __restric
     const int d0 = static_cast<int>(q - static_cast<int64_t>(sr) * d_tiles) * kTile;
     const T* src = in + static_cast<int64_t>(sr) * n_dm;
 #pragma unroll
-    for (int i = threadIdx.y; i < kTile; i += 8) {
+    for (int i = threadIdx.y; i < kTile; i += kUntrRows) {
       const int kb = kb0 + i;
       const int d = d0 + threadIdx.x;
       if (kb < n_bins && d < n_dm) tile[i][threadIdx.x] = src[static_cast<int64_t>(kb) * rows + d];
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(256) bin_untranspose_kernel(const T* __restric
     __syncthreads();
     T* dst = out + static_cast<int64_t>(sr) * out_series_stride;
 #pragma unroll
-    for (int i = threadIdx.y; i < kTile; i += 8) {
+    for (int i = threadIdx.y; i < kTile; i += kUntrRows) {
       const int d = d0 + i;
       const int kb = kb0 + threadIdx.x;
       if (kb < n_bins && d < n_dm) dst[static_cast<int64_t>(d) * out_dm_stride + kb] = tile[threadIdx.x][i];
@@ -157,11 +161,11 @@ cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s) 
   const int64_t tiles = static_cast<int64_t>(a.n_series) * ((a.n_dm + kTile - 1) / kTile);
   dim3 grid((a.n_bins + kTile - 1) / kTile, static_cast<unsigned>(tiles < 65535 ? tiles : 65535));
   if (a.elem_bytes == 8)
-    bin_untranspose_kernel<float2><<<grid, dim3(kTile, 8), 0, s>>>(
+    bin_untranspose_kernel<float2><<<grid, dim3(kTile, kUntrRows), 0, s>>>(
         static_cast<const float2*>(a.in), a.n_series, a.n_dm, a.n_bins,
         static_cast<float2*>(a.out), a.out_series_stride, a.out_dm_stride);
   else if (a.elem_bytes == 4)
-    bin_untranspose_kernel<float><<<grid, dim3(kTile, 8), 0, s>>>(
+    bin_untranspose_kernel<float><<<grid, dim3(kTile, kUntrRows), 0, s>>>(
         static_cast<const float*>(a.in), a.n_series, a.n_dm, a.n_bins,
         static_cast<float*>(a.out), a.out_series_stride, a.out_dm_stride);
   else

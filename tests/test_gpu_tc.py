@@ -47,6 +47,8 @@ def _workload(n_chan, n_t, dms, n_beams, band=(1200.0, 1500.0), t_samp=2e-3, chu
     (37, 33, 512, 0.0, 0.25, 300),   # two groups, one partial pass
     (16, 64, 512, 1.0, 0.25, 2100),  # one full 16-beam group, 2048-trial passes, ragged
     (33, 40, 256, 0.5, 0.5, 2200),   # 32-beam groups (one of 1 beam), 3 passes, ragged
+    (1, 1, 64, 0.0, 1.0, 1),         # one series, one channel, one trial
+    (2, 7, 32, 5.0, 0.1, 3),         # a few of everything, non-zero first trial
 ])
 def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm, precision):
     dms = dm0 + ddm * np.arange(n_dm)
