@@ -14,32 +14,69 @@ namespace {
 
 constexpr int kTile = 32;
 
-// 32 x 32 tile through shared memory: coalesced reads along channels,
-// coalesced writes along time.
+// 32 samples x 128 channels through shared memory: coalesced reads along
+// channels (each thread four consecutive channels, one 4-byte (u8) or
+// 16-byte (f32) load when kVec), coalesced 128-byte writes along time.  The
+// tile is [channel][sample] with the sample column rotated by channel / 4,
+// so both the scattered writes of the read phase (four channels per thread)
+// and the row reads of the write phase hit 32 different banks.
+constexpr int kUnpC = 128;  // channels per tile
 template <typename Tin>
+struct Vec4;
+template <>
+struct Vec4<uint8_t> {
+  __device__ static void load(const uint8_t* p, float (&v)[4]) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = static_cast<float>((w >> (8 * e)) & 0xFFu);
+  }
+};
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float* p, float (&v)[4]) {
+    const float4 w = *reinterpret_cast<const float4*>(p);
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+  }
+};
+
+template <typename Tin, bool kVec>
 __global__ void __launch_bounds__(256) unpack_time_major_kernel(const Tin* __restrict__ in,
                                                                 int n_chan, int64_t n_t,
                                                                 int64_t t_begin, int64_t L,
                                                                 float* __restrict__ out,
                                                                 int64_t out_stride) {
-  __shared__ float tile[kTile][kTile + 1];
+  __shared__ float tile[kUnpC][kTile + 1];
   const int64_t n0 = static_cast<int64_t>(blockIdx.x) * kTile;
-  const int c0 = blockIdx.y * kTile;
+  const int c0 = blockIdx.y * kUnpC;
+  const int cq = c0 + 4 * threadIdx.x;  // this thread's four channels
 #pragma unroll
   for (int r = threadIdx.y; r < kTile; r += 8) {
     const int64_t n = n0 + r;
     const int64_t t = t_begin + n;
-    const int c = c0 + threadIdx.x;
-    float v = 0.f;
-    if (n < L && t < n_t && c < n_chan) v = static_cast<float>(in[t * n_chan + c]);
-    tile[r][threadIdx.x] = v;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (n < L && t < n_t) {
+      const Tin* row = in + t * n_chan;
+      if (kVec && cq + 3 < n_chan) {
+        Vec4<Tin>::load(row + cq, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (cq + e < n_chan) v[e] = static_cast<float>(row[cq + e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tile[4 * threadIdx.x + e][(r + threadIdx.x) & (kTile - 1)] = v[e];
   }
   __syncthreads();
 #pragma unroll
-  for (int r = threadIdx.y; r < kTile; r += 8) {
-    const int c = c0 + r;
+  for (int cl = threadIdx.y; cl < kUnpC; cl += 8) {
+    const int c = c0 + cl;
     const int64_t n = n0 + threadIdx.x;
-    if (c < n_chan && n < L) out[static_cast<int64_t>(c) * out_stride + n] = tile[threadIdx.x][r];
+    if (c < n_chan && n < L)
+      out[static_cast<int64_t>(c) * out_stride + n] = tile[cl][(threadIdx.x + (cl >> 2)) & (kTile - 1)];
   }
 }
 
@@ -185,15 +222,33 @@ cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s) {
 
 cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t s) {
   if (a.in_layout == FDD_LAYOUT_TIME_MAJOR) {
-    dim3 grid(static_cast<unsigned>((a.L + kTile - 1) / kTile), (a.n_chan + kTile - 1) / kTile);
+    dim3 grid(static_cast<unsigned>((a.L + kTile - 1) / kTile), (a.n_chan + kUnpC - 1) / kUnpC);
     dim3 block(kTile, 8);
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    if (a.in_dtype == FDD_IN_U8)
-      unpack_time_major_kernel<uint8_t><<<grid, block, 0, s>>>(
-          static_cast<const uint8_t*>(a.in), a.n_chan, a.n_t, a.t_begin, a.L, a.out, a.out_stride);
-    else
-      unpack_time_major_kernel<float><<<grid, block, 0, s>>>(
-          static_cast<const float*>(a.in), a.n_chan, a.n_t, a.t_begin, a.L, a.out, a.out_stride);
+    // vector loads when every row of four channels is aligned for them
+    const size_t esz = a.in_dtype == FDD_IN_U8 ? 1 : 4;
+    const bool vec = a.n_chan % 4 == 0 && reinterpret_cast<uintptr_t>(a.in) % (4 * esz) == 0;
+    if (a.in_dtype == FDD_IN_U8) {
+      const uint8_t* in = static_cast<const uint8_t*>(a.in);
+      if (vec)
+        unpack_time_major_kernel<uint8_t, true><<<grid, block, 0, s>>>(in, a.n_chan, a.n_t,
+                                                                       a.t_begin, a.L, a.out,
+                                                                       a.out_stride);
+      else
+        unpack_time_major_kernel<uint8_t, false><<<grid, block, 0, s>>>(in, a.n_chan, a.n_t,
+                                                                        a.t_begin, a.L, a.out,
+                                                                        a.out_stride);
+    } else {
+      const float* in = static_cast<const float*>(a.in);
+      if (vec)
+        unpack_time_major_kernel<float, true><<<grid, block, 0, s>>>(in, a.n_chan, a.n_t,
+                                                                     a.t_begin, a.L, a.out,
+                                                                     a.out_stride);
+      else
+        unpack_time_major_kernel<float, false><<<grid, block, 0, s>>>(in, a.n_chan, a.n_t,
+                                                                      a.t_begin, a.L, a.out,
+                                                                      a.out_stride);
+    }
   } else {
     const int64_t blocks = (a.L + 255) / 256;
     dim3 grid(static_cast<unsigned>(blocks < 4096 ? blocks : 4096), a.n_chan);
