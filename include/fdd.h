@@ -213,6 +213,9 @@ fdd_status fdd_query(fdd_plan_t plan, fdd_info* out);
  *          TIME    float [beam][n_dm][out_len]
  *          SPECTRA complex float [beam][chunk][n_dm][n_bins]
  *          POWER   float [beam][chunk][n_dm][n_bins]
+ * Asynchronous on `stream`; never synchronises or allocates, so with
+ * profiling off a caller may capture the call into a CUDA graph and replay it
+ * (the graph keeps d_in and d_out).
  * Errors: FDD_ERR_INVALID_ARG (NULL plan or pointer), FDD_ERR_CUDA,
  * FDD_ERR_CUFFT.
  */

@@ -2,7 +2,8 @@
 (beam, chunk) units on two plan-owned streams) gives bit for bit what
 fdd_execute gives on device buffers (GB300 only): both layouts, every output
 kind, several beams and chunks, the tensor-core form, back-to-back calls
-with different inputs, and pageable host memory."""
+with different inputs, and pageable host memory.  fdd_execute captured into a
+CUDA graph replays bit for bit."""
 import numpy as np
 import pytest
 
@@ -89,3 +90,40 @@ def test_host_pipeline_pageable_memory_and_single_chunk():
         plan.execute_host(torch.from_numpy(x.reshape(-1)), h_out)
         torch.cuda.synchronize()
         assert torch.equal(d_out.cpu(), h_out)
+
+
+@pytest.mark.parametrize("precision", [fdd.FDD_PREC_FP32, fdd.FDD_PREC_BF16_HILO],
+                         ids=["fp32", "bf16_hilo"])
+def test_execute_replays_from_a_cuda_graph(precision):
+    """fdd_execute neither synchronises nor allocates, so a caller can capture
+    it into a CUDA graph (with profiling off): every replay equals the direct
+    call bit for bit, including after the input buffer is refilled in place."""
+    w = _workload(2, "time", chunk_len=2048)
+    x1 = torch.from_numpy(_inputs(w, fdd.FDD_LAYOUT_TIME_MAJOR, 3)).cuda()
+    x2 = torch.from_numpy(_inputs(w, fdd.FDD_LAYOUT_TIME_MAJOR, 4)).cuda()
+    with fdd.Plan(**params_for(w, precision=precision)) as plan:
+        info = plan.info
+        ref1 = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
+        ref2 = torch.empty_like(ref1)
+        plan.execute(x1, ref1)
+        plan.execute(x2, ref2)
+        d_in = x1.clone()
+        out = torch.zeros_like(ref1)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.execute(d_in, out)  # warm-up on the capture stream
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.execute(d_in, out)
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref1)
+        d_in.copy_(x2)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref2)
+        assert plan.query()["n_dm"] == w.n_dm  # no device-side status raised
