@@ -126,4 +126,4 @@ def test_execute_replays_from_a_cuda_graph(precision):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(out, ref2)
-        assert plan.query()["n_dm"] == w.n_dm  # no device-side status raised
+        assert plan.query()["out_elems"] == info["out_elems"]  # no device-side status raised
