@@ -78,7 +78,7 @@ def parse_args():
     ap.add_argument("--batch-n-t-div", type=int, default=16,
                     help="divide the batch workload's beam lengths (device memory bound)")
     ap.add_argument("--mac-sweep", default="",
-                    help="comma-separated FDD_MAC_* variants (or 'all'): time the "
+                    help="comma-separated FDD_MAC_* variants, by number or name (or 'all'): time the "
                          "phase-rotate-and-sum kernel alone for each on one chunk of the "
                          "workload and print one JSON line per variant")
     return ap.parse_args()
@@ -600,8 +600,13 @@ def run_mac_sweep(args) -> None:
 
     fdd.build()
     w = workload_from_args(args)
+    def variant(v: str):
+        if v in ("tc", "tc1"):
+            return v
+        return fdd.MAC_VARIANT_NAMES.index(v) if v in fdd.MAC_VARIANT_NAMES else int(v)
+
     vs = list(range(fdd.FDD_MAC_VARIANTS)) if args.mac_sweep == "all" else \
-        [v if v in ("tc", "tc1") else int(v) for v in args.mac_sweep.split(",")]
+        [variant(v) for v in args.mac_sweep.split(",")]
     props = torch.cuda.get_device_properties(0)
     peaks = load_peaks()
     max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)

@@ -91,7 +91,10 @@ typedef enum fdd_status {
 #define FDD_MAC_Z12_8X8 13 /* Z swapped as pre-broadcast quads, 12-warp blocks    */
 #define FDD_MAC_P12_8X8 14 /* P with 12-warp blocks                                */
 #define FDD_MAC_W12_8X8 15 /* warp-specialised: 4 phasor warps feed 8 MAC warps   */
-#define FDD_MAC_VARIANTS 16
+#define FDD_MAC_Q_8X8_512 16 /* Q, 8x8 lane tile, 8 lanes per bin, four bins per
+                                warp: 512-trial blocks (between Q_4X4's 128 and
+                                Q_4X8's 1024)                                    */
+#define FDD_MAC_VARIANTS 17
 #define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
 
 /* fdd_params.precision */

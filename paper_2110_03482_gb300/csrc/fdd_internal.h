@@ -63,6 +63,7 @@ enum MacVariant {
   MAC_Z12_8x8 = FDD_MAC_Z12_8X8,
   MAC_P12_8x8 = FDD_MAC_P12_8X8,
   MAC_W12_8x8 = FDD_MAC_W12_8X8,
+  MAC_Q_8x8_512 = FDD_MAC_Q_8X8_512,
   MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
 };
 // One set of spectra in a batch (the batching form): its launch arguments

@@ -76,6 +76,7 @@ struct Geom {
 using G8x8 = Geom<8, 8, 4, 8>;  // 32 x 64 = 2048 trials per bin and warp
 using G4x8 = Geom<4, 8, 4, 8>;  // 16 x 64 = 1024
 using G4x4 = Geom<4, 4, 2, 4>;  //  8 x 16 =  128, four bins per warp
+using G8x8q = Geom<8, 8, 2, 4>; // 16 x 32 =  512, four bins per warp
 
 // ----------------------------------------------------------------- scalar form
 template <class Gm>
@@ -1051,6 +1052,7 @@ VariantInfo variant_info(int v) {
     case MAC_Z12_8x8: return info<G8x8, PackedZQuad<G8x8>, false, 12>();
     case MAC_P12_8x8: return info<G8x8, Packed<G8x8>, false, 12>();
     case MAC_W12_8x8: return info_ws<G8x8, PackedCompact<G8x8>, 8, 4>();
+    case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>, false>();
     default: return info_legacy();
   }
 }
@@ -1061,16 +1063,18 @@ VariantInfo variant_info(int v) {
 // trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
 // measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
 // 131073 bins, full blocks): W12_8x8 0.623 (2048-trial blocks), Q_4x8 0.493
-// (1024), Q_4x4 0.347 (128).  Other tiles measured on the same launch (ms):
-// W12_8x8 43.7, Q12_8x8 49.5, R_8x8 50.3, Q_8x8 52.4, Z12_8x8 52.4,
-// S_8x8 55.6, P_8x8 56.3, SP_8x8 57.8, P12_8x8 63.0.
+// (1024), Q_8x8_512 0.415 (512), Q_4x4 0.347 (128).  Other tiles measured on
+// the same launch (ms): W12_8x8 43.7, Q12_8x8 49.5, R_8x8 50.3, Q_8x8 52.4,
+// Z12_8x8 52.4, S_8x8 55.6, P_8x8 56.3, SP_8x8 57.8, P12_8x8 63.0; a
+// 512-trial tile of 4x4 lane tiles over 32 lanes of one bin 0.363.
 int mac_variant_for(int n_dm) {
   struct Tile {
     int variant, block;
     double rate;
   };
   static const Tile tiles[] = {
-      {MAC_W12_8x8, 2048, 0.623}, {MAC_Q_4x8, 1024, 0.493}, {MAC_Q_4x4, 128, 0.347}};
+      {MAC_W12_8x8, 2048, 0.623}, {MAC_Q_4x8, 1024, 0.493}, {MAC_Q_8x8_512, 512, 0.415},
+      {MAC_Q_4x4, 128, 0.347}};
   int best = MAC_W12_8x8;
   double best_cost = 0.0;
   for (const Tile& t : tiles) {
