@@ -121,10 +121,11 @@ def test_kernel_dm_subrange_and_large_phases():
         assert rel_l2(Y[:, q], ref[:, q]) <= 4 * FP32_REL_L2, bins[q]
 
 
-@pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_Q_4X4 + 1, fdd.FDD_MAC_R_8X8 + 1])
+@pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_Q_4X4 + 1, fdd.FDD_MAC_R_8X8 + 1,
+                                     fdd.FDD_MAC_Q_8X8_512 + 1])
 def test_kernel_bin_windows_equal_the_whole_range(variant):
     """A window of bins (absolute phases k_begin + k) gives bit for bit the
-    columns of the whole-range call, for the default and two other tiles."""
+    columns of the whole-range call, for the default and three other tiles."""
     n_chan, L, n_dm = 48, 4096, 1100
     w = _small_workload(n_chan, L, 0.5 * np.arange(n_dm))
     K = L // 2 + 1
