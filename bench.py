@@ -61,6 +61,9 @@ def parse_args():
                     help="skip the tensor-core form's timing on the 32-beam workload")
     ap.add_argument("--no-tdd", action="store_true",
                     help="skip the brute-force time-domain dedispersion on the same workload")
+    ap.add_argument("--downsample-sweep", action="store_true",
+                    help="time the workload's whole call at down-sampling factors 1, 2, 4, 8 "
+                         "and print one JSON line per factor")
     ap.add_argument("--crossover", action="store_true",
                     help="time Fourier- and time-domain dedispersion of the workload at "
                          "128..n_dm trials (one JSON line per trial count)")
@@ -467,6 +470,46 @@ def run_crossover(args) -> None:
         n *= 2
 
 
+def run_downsample_sweep(args) -> None:
+    """The workload's whole call (unpack, R2C, MAC, C2R, scatter) at
+    down-sampling factors 1, 2, 4, 8 (Sect. 2.2, last paragraph: the MAC on
+    the bins k <= L / 2f only and an inverse transform of length L / f), one
+    JSON line per factor with the MACs the call actually does."""
+    import torch
+
+    import paper_2110_03482_gb300 as fdd
+
+    fdd.build()
+    w = workload_from_args(args)
+    fb, _ = synth.filterbank(w, seed=args.seed)
+    d_in = torch.from_numpy(fb.reshape(-1)).cuda()
+    stream = torch.cuda.current_stream()
+    ms1 = None
+    for f in (1, 2, 4, 8):
+        with fdd.Plan(**dict(plan_params(w, fdd), downsample=f)) as plan:
+            info = plan.info
+            out = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
+            for _ in range(max(args.warmup, 1)):
+                plan.execute(d_in, out, stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                plan.execute(d_in, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            ms1 = ms if ms1 is None else ms1
+            bins = info["fft_len"] // f // 2 + 1
+            macs = int(info["n_chunks"]) * w.n_dm * w.n_chan * bins
+            print(json.dumps({"downsample": f, "workload": w.name, "ms_per_call": ms,
+                              "out_len": info["out_len"], "mac_bins_per_chunk": bins,
+                              "macs_per_s": macs / (ms / 1e3), "time_over_f1": ms / ms1,
+                              "tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]]}), flush=True)
+            del out
+
+
 def run_fdd(args, rank: int, world: int, dist) -> None:
     import torch
 
@@ -742,6 +785,9 @@ def main():
         return
     if args.crossover:
         run_crossover(args)
+        return
+    if args.downsample_sweep:
+        run_downsample_sweep(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
