@@ -250,7 +250,24 @@ def _rel(a, b) -> float:
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def cpu_baseline(w: synth.Workload, seed: int, target_s: float, plan=None) -> dict:
+def oracle_small_full() -> dict:
+    """The oracle's whole path (delays, FFT, Eq. 7 over every bin, inverse) on
+    the complete 64-channel workload, timed once."""
+    import oracle
+    w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    fb, _ = synth.filterbank(w, seed=20211008)
+    t0 = time.perf_counter()
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    oracle.fdd_time(fb.T.astype(np.float64), d, w.chunk_len)
+    dt = time.perf_counter() - t0
+    K = w.n_t // 2 + 1
+    return {"workload": w.name, "seconds": dt,
+            "macs_per_s": w.n_dm * w.n_chan * K / dt,
+            "note": "whole oracle path on the complete workload (not a sample)"}
+
+
+def cpu_baseline(w: synth.Workload, seed: int, target_s: float, plan=None,
+                 macs_step: int | None = None) -> dict:
     """Time the oracle on sampled bins; when a plan is given, also report the CUDA
     path's relative L2 error on those bins (same FP64-derived spectra in)."""
     import oracle
@@ -264,6 +281,10 @@ def cpu_baseline(w: synth.Workload, seed: int, target_s: float, plan=None) -> di
                      f"Nyquist) x {w.n_dm} DMs x {w.n_chan} channels of chunk 0 "
                      f"({macs:.3g} MACs in {dt:.1f} s; oracle FFT of the chunk untimed)",
            "seconds": dt}
+    if macs_step:
+        # labelled as an extrapolation: the sampled rate applied to a whole step
+        out["extrapolated_seconds_per_step"] = macs_step / (macs / dt)
+    out["small_full"] = oracle_small_full()
     if plan is not None:
         bins, Y = oracle_rate.last
         G = _gpu_sampled(plan, X[None].astype(np.complex64), bins, w.n_dm,
@@ -614,7 +635,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
     tc = None if args.no_tc else measure_tc(args, fdd, torch, value_per_mac_kernel=achieved)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.seed, args.cpu_seconds, plan)
+        cpu = cpu_baseline(w, args.seed, args.cpu_seconds, plan, macs_step=macs_step)
         if tc is not None:
             tc.update(tc_accuracy(args.seed))
     plan.close()
