@@ -61,6 +61,9 @@ def parse_args():
                     help="skip the tensor-core form's timing on the 32-beam workload")
     ap.add_argument("--no-tdd", action="store_true",
                     help="skip the brute-force time-domain dedispersion on the same workload")
+    ap.add_argument("--sweep-window", type=int, default=0,
+                    help="with --mac-sweep: time a window of this many bins in the middle of "
+                         "the whole transform (fdd_dedisperse_spectra_bins) instead of all bins")
     ap.add_argument("--downsample-sweep", action="store_true",
                     help="time the workload's whole call at down-sampling factors 1, 2, 4, 8 "
                          "and print one JSON line per factor")
@@ -689,26 +692,38 @@ def run_mac_sweep(args) -> None:
             kw.update(mac_variant=v + 1)
         with fdd.Plan(**kw) as plan:
             g = plan.info
+            # the whole transform's bins, or (--sweep-window N) a window of N bins
+            # in its middle through fdd_dedisperse_spectra_bins
+            nb = min(args.sweep_window, g["n_bins"]) if args.sweep_window > 0 else g["n_bins"]
+            b0 = (g["n_bins"] - nb) // 2 if args.sweep_window > 0 else 0
+            pitch = nb if args.sweep_window > 0 else g["bin_pitch"]
             if X is None or X.shape[0] != ns:
                 X = Y = None
                 gen = torch.Generator(device="cuda").manual_seed(args.seed)
-                X = torch.randn((ns, w.n_chan, g["bin_pitch"], 2), device="cuda", generator=gen)
-                Y = torch.empty((ns, w.n_dm, g["n_bins"], 2), device="cuda")
+                X = torch.randn((ns, w.n_chan, pitch, 2), device="cuda", generator=gen)
+                Y = torch.empty((ns, w.n_dm, nb, 2), device="cuda")
+
+            def call():
+                if args.sweep_window > 0:
+                    plan.dedisperse_spectra_bins(X, pitch, ns, b0, nb, 0, w.n_dm, Y, nb)
+                else:
+                    plan.dedisperse_spectra(X, pitch, ns, 0, w.n_dm, Y, nb)
+
             for _ in range(max(args.warmup, 1)):
-                plan.dedisperse_spectra(X, g["bin_pitch"], ns, 0, w.n_dm, Y, g["n_bins"])
+                call()
             torch.cuda.synchronize()
             clocks = Clocks(gpu_uuid(props, 0))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(args.steps):
-                plan.dedisperse_spectra(X, g["bin_pitch"], ns, 0, w.n_dm, Y, g["n_bins"])
+                call()
             e1.record()
             torch.cuda.synchronize()
             clk = clocks.stop()
             ms = e0.elapsed_time(e1) / args.steps
             plan.query()  # raises if a kernel reported a device-side timeout
-        flops = FLOPS_PER_MAC * ns * w.n_dm * w.n_chan * g["n_bins"]
+        flops = FLOPS_PER_MAC * ns * w.n_dm * w.n_chan * nb
         tf = flops / (ms / 1e3) / 1e12
         extra = {"frac_bf16_peak_algorithmic": tf / bf16_peak,
                  "tensor_tflops_physical": (2 if v == "tc" else 1) * tf} if tc else {}
@@ -718,7 +733,8 @@ def run_mac_sweep(args) -> None:
                           "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,
                           **extra,
                           "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
-                          "n_bins": g["n_bins"], "n_dm": w.n_dm, "n_chan": w.n_chan}),
+                          "n_bins": nb, "bin_window_start": b0, "n_dm": w.n_dm,
+                          "n_chan": w.n_chan}),
               flush=True)
 
 
