@@ -84,7 +84,8 @@ def parse_args():
     ap.add_argument("--batch-n-t-div", type=int, default=16,
                     help="divide the batch workload's beam lengths (device memory bound)")
     ap.add_argument("--mac-sweep", default="",
-                    help="comma-separated FDD_MAC_* variants, by number or name (or 'all'): time the "
+                    help="comma-separated FDD_MAC_* variants, by number or name, or tc / tc1 / tc16 for "
+                         "the tensor-core form in BF16 hi+lo / BF16 / FP16 (or 'all'): time the "
                          "phase-rotate-and-sum kernel alone for each on one chunk of the "
                          "workload and print one JSON line per variant")
     return ap.parse_args()
@@ -316,7 +317,8 @@ def tc_accuracy(seed: int) -> dict:
     refs = np.stack([oracle.fdd_bins(X[b][:, bins].astype(np.complex128), bins, geo.L, d)
                      for b in range(2)])
     res = {}
-    for name, prec in (("bf16_hilo", fdd.FDD_PREC_BF16_HILO), ("bf16", fdd.FDD_PREC_BF16)):
+    for name, prec in (("bf16_hilo", fdd.FDD_PREC_BF16_HILO), ("bf16", fdd.FDD_PREC_BF16),
+                       ("fp16", fdd.FDD_PREC_FP16)):
         with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA, n_beams=2,
                              precision=prec)) as plan:
             G = _gpu_sampled(plan, X, bins, w.n_dm, plan.info["bin_pitch"])
@@ -369,7 +371,8 @@ def measure_tc(args, fdd, torch, value_per_mac_kernel: float) -> dict:
            "unit": UNIT}
     X = Y = None
     for name, prec, passes in (("bf16_hilo", fdd.FDD_PREC_BF16_HILO, 2),
-                               ("bf16", fdd.FDD_PREC_BF16, 1)):
+                               ("bf16", fdd.FDD_PREC_BF16, 1),
+                               ("fp16", fdd.FDD_PREC_FP16, 1)):
         with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA,
                              n_beams=w.n_beams, precision=prec)) as plan:
             g = plan.info
@@ -667,8 +670,11 @@ def run_mac_sweep(args) -> None:
 
     fdd.build()
     w = workload_from_args(args)
+    tc_prec = {"tc": fdd.FDD_PREC_BF16_HILO, "tc1": fdd.FDD_PREC_BF16,
+               "tc16": fdd.FDD_PREC_FP16}
+
     def variant(v: str):
-        if v in ("tc", "tc1"):
+        if v in tc_prec:
             return v
         return fdd.MAC_VARIANT_NAMES.index(v) if v in fdd.MAC_VARIANT_NAMES else int(v)
 
@@ -682,12 +688,11 @@ def run_mac_sweep(args) -> None:
     X = Y = None
     bf16_peak = float(peaks.get("bf16_tflops") or 1895.5)
     for v in vs:
-        tc = v in ("tc", "tc1")
+        tc = v in tc_prec
         ns = w.n_beams if tc else 1
         kw = dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA)
         if tc:
-            kw.update(precision=fdd.FDD_PREC_BF16_HILO if v == "tc" else fdd.FDD_PREC_BF16,
-                      n_beams=ns)
+            kw.update(precision=tc_prec[v], n_beams=ns)
         else:
             kw.update(mac_variant=v + 1)
         with fdd.Plan(**kw) as plan:
@@ -727,7 +732,8 @@ def run_mac_sweep(args) -> None:
         tf = flops / (ms / 1e3) / 1e12
         extra = {"frac_bf16_peak_algorithmic": tf / bf16_peak,
                  "tensor_tflops_physical": (2 if v == "tc" else 1) * tf} if tc else {}
-        print(json.dumps({"sweep": {"tc": "TC_hilo", "tc1": "TC_bf16"}.get(v, None) or
+        print(json.dumps({"sweep": {"tc": "TC_hilo", "tc1": "TC_bf16",
+                                    "tc16": "TC_fp16"}.get(v, None) or
                           fdd.MAC_VARIANT_NAMES[v], "variant": v,
                           "ms_per_launch": ms, "beams": ns, "macs_per_s": tf * 1e12 / 8,
                           "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,

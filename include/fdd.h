@@ -104,6 +104,9 @@ typedef enum fdd_status {
                                 all beams of a chunk share each bin's phasors    */
 #define FDD_PREC_BF16 2      /* the same with BF16 phasors only (half the tensor
                                 work of hi+lo, larger error)                     */
+#define FDD_PREC_FP16 3      /* tensor cores with FP16 phasors and FP16 data, each
+                                bin's data scaled by a power of two into FP16's
+                                range (the tensor work of BF16, smaller error)   */
 
 typedef struct fdd_params {
   int32_t n_chan;         /* observing channels N_nu, >= 1                          */

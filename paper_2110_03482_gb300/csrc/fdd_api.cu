@@ -35,7 +35,7 @@ struct fdd_plan_s {
   float* d_xw = nullptr;      // [n_chan][L] channel series of one chunk
   float2* d_X = nullptr;      // [n_chan][bin_pitch] their spectra
                               // (tensor-core form: [beam][n_chan][bin_pitch], every beam)
-  bool tc = false;            // tensor-core form (FDD_PREC_BF16_HILO)
+  bool tc = false;            // tensor-core form (any precision but FDD_PREC_FP32)
   float2* d_tcx = nullptr;    // tensor-core form: bin-major spectra of a block of bins
   size_t tcx_bytes = 0;
   int n_sms = 0;
@@ -182,7 +182,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
   if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO &&
-      p->precision != FDD_PREC_BF16)
+      p->precision != FDD_PREC_BF16 && p->precision != FDD_PREC_FP16)
     return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
@@ -618,7 +618,7 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.real_bin_b = static_cast<int>(Ls / 2);
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
-          FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, P->d_tcx,
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx,
                                       P->tcx_bytes, s));
         }
         cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
@@ -659,7 +659,7 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
         m.Y = static_cast<float*>(d_out) + off;
       }
       StageTimer t(P, FDD_STAGE_MAC, s);
-      FDD_CUDA(fdd::launch_mac_tc(m, p.precision == FDD_PREC_BF16_HILO, P->n_sms, P->d_tcx,
+      FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx,
                                       P->tcx_bytes, s));
     }
     if (hp && (pst = hp->after(0, p.n_beams, c, s)) != FDD_OK) return pst;
@@ -879,7 +879,7 @@ fdd_status fdd_debug_stall_test(fdd_plan_t plan, fdd_stream_t stream) {
   m.test_withhold = 1;
   cudaError_t e;
   if (plan->tc) {
-    e = fdd::launch_mac_tc(m, plan->p.precision == FDD_PREC_BF16_HILO, plan->n_sms, plan->d_tcx,
+    e = fdd::launch_mac_tc(m, plan->p.precision, plan->n_sms, plan->d_tcx,
                            plan->tcx_bytes, s);
   } else {
     e = fdd::mac_prepare(fdd::MAC_W12_8x8, plan->p.n_chan);
@@ -992,7 +992,7 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
   m.status = plan->d_status;
   StageTimer t(plan, FDD_STAGE_MAC, reinterpret_cast<cudaStream_t>(stream));
   if (plan->tc)
-    FDD_CUDA(fdd::launch_mac_tc(m, plan->p.precision == FDD_PREC_BF16_HILO, plan->n_sms,
+    FDD_CUDA(fdd::launch_mac_tc(m, plan->p.precision, plan->n_sms,
                                 plan->d_tcx, plan->tcx_bytes,
                                 reinterpret_cast<cudaStream_t>(stream)));
   else

@@ -42,6 +42,8 @@ struct MacArgs {
   int* status;              // device status word (may be NULL)
   int test_withhold;        // self-test only: producers never announce a filled stage,
                             // so the consumers' bounded waits run out (FDD_ERR_TIMEOUT)
+  const float* bin_absmax;  // tensor cores in FP16 only: per local bin, the largest
+                            // |re| or |im| of the spectra (sets that bin's data scale)
 };
 
 // Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu and the
@@ -107,7 +109,8 @@ int mac_tc_beams_per_group(int n_series);
 // to n_dm trials on n_series x n_chan spectra of n_bins bins (blocks of at
 // most 3 GiB, at least one bin).
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins);
-cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scratch,
+// precision: FDD_PREC_BF16_HILO, FDD_PREC_BF16 or FDD_PREC_FP16.
+cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s);
 
 // Bins k0 .. k0 + n_bins - 1 of `rows` complex rows of stride in_stride into
@@ -119,6 +122,9 @@ struct BinTransposeArgs {
   int64_t k0;
   int n_bins;
   float2* out;           // [n_bins][rows]
+  unsigned int* absmax;  // optional: per bin, atomic max of the bits of max(|re|, |im|)
+                         // over the rows (non-negative floats order as their bits);
+                         // the caller zeroes it first
 };
 cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s);
 

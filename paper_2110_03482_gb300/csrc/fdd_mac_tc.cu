@@ -15,8 +15,10 @@
 //   D_re[b][(a, beta)] = sum_K A_re[b][K] B[(a, beta)][K],   A_re = (Pr, -Pi),
 //   D_im[b][(a, beta)] = sum_K A_im[b][K] B[(a, beta)][K],   A_im = (Pi,  Pr),
 //
-// i.e. Re and Im of P Z.  Phasors are BF16 hi + lo (four MMAs per K step) or
-// BF16 alone (two), data BF16, accumulation FP32 in tensor memory.  M = 128
+// i.e. Re and Im of P Z.  Operands are BF16 (phasors hi + lo: four MMAs per K
+// step; or hi alone: two) or FP16 (two MMAs; each bin's data scaled by a power
+// of two so its largest component lands near 2^14, undone in the epilogue),
+// accumulation FP32 in tensor memory.  M = 128
 // trials b, N = 256 (a, beta) pairs (8 a's x 32 beams, or 16 a's x 16 beams
 // for calls with at most 16 series), K = 64 per stage (32 channels x
 // (re, im)).  D_re and D_im fill all 512 tensor-memory columns, so one pass
@@ -40,6 +42,7 @@
 // timeout the kernel records FDD_ERR_TIMEOUT in the status word, stops,
 // drains its own MMAs (bounded), frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "fdd_device.cuh"
 #include "fdd_internal.h"
@@ -92,13 +95,42 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
          (static_cast<uint64_t>(2) << 61);
 }
 
-// Instruction descriptor: D FP32, A and B BF16, both K-major, N and M.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            (static_cast<uint32_t>(kN >> 3) << 17) |
-                            (static_cast<uint32_t>(kM >> 4) << 24);
+// Operand precisions of the kernel (from fdd_params.precision).
+enum TcPrec { kBf16HiLo = 0, kBf16 = 1, kF16 = 2 };
+
+// Instruction descriptor: D FP32, A and B both BF16 (format 1) or both FP16
+// (format 0), both K-major, N and M.
+template <int kPrec>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (kPrec == kF16 ? 0u : ((1u << 7) | (1u << 10))) |
+         (static_cast<uint32_t>(kN >> 3) << 17) | (static_cast<uint32_t>(kM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// (x, y) rounded to the kernel's 16-bit operand type, x in the low half.
+template <int kPrec>
+__device__ __forceinline__ uint32_t pack2(float x, float y) {
+  if constexpr (kPrec == kF16) {
+    __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    return bf16x2_bits(__floats2bfloat162_rn(x, y));
+  }
+}
+
+// FP16 data scale of a bin whose largest |re| or |im| is m: with E the biased
+// exponent of m (m < 2^(E - 126)), the power of two 2^(140 - E), so that m
+// times it is below 2^14 and every component of Z = Q X (|Z| <= sqrt(2) m)
+// stays below 2^14.5, well inside FP16's range (65504).  Powers of two keep
+// the scaling and its undoing exact.
+__device__ __forceinline__ float f16_bin_scale(float m) {
+  const int e = static_cast<int>((__float_as_uint(m) >> 23) & 0xFFu);
+  int f = 267 - e;  // biased exponent of 2^(140 - E)
+  f = f < 1 ? 1 : (f > 253 ? 253 : f);
+  return __uint_as_float(static_cast<uint32_t>(f) << 23);
 }
 
 // 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes, from two
@@ -122,19 +154,22 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// D (+)= A B^T for one K step of 16: M = 128, N = 256, BF16 in, FP32 out.
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accum) {
+// D (+)= A B^T for one K step of 16: M = 128, N = 256, 16-bit in, FP32 out.
+template <int kPrec>
+__device__ __forceinline__ void mma16(uint32_t d, uint64_t adesc, uint64_t bdesc,
+                                      uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum));
+      "l"(adesc), "l"(bdesc), "r"(idesc<kPrec>()), "r"(accum));
 }
 
-// kHiLo: phasors as BF16 hi + lo (four MMAs per K step); otherwise BF16 only.
-template <bool kHiLo, int kBeams>
+// kPrec: kBf16HiLo (phasors as BF16 hi + lo, four MMAs per K step), kBf16
+// (BF16 only) or kF16 (FP16 phasors and scaled FP16 data).
+template <int kPrec, int kBeams>
 __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
+  constexpr bool kHiLo = kPrec == kBf16HiLo;
   constexpr int kNA = kN / kBeams;            // a's per pass (8 or 16)
   constexpr int kDmsPass = dms_per_pass<kBeams>();
   constexpr int kStages = Ring<kHiLo>::kStages;
@@ -207,11 +242,11 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t bd = smem_desc(stage + kBOff + kk * 32);
               const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
-              mma_bf16(tmem, smem_desc(stage + kk * 32), bd, accum);               // re, hi
-              mma_bf16(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum);  // im, hi
+              mma16<kPrec>(tmem, smem_desc(stage + kk * 32), bd, accum);               // re, hi
+              mma16<kPrec>(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum);  // im, hi
               if (kHiLo) {
-                mma_bf16(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u);       // re, lo
-                mma_bf16(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u);  // im, lo
+                mma16<kPrec>(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u);       // re, lo
+                mma16<kPrec>(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u);  // im, lo
               }
             }
             issued = true;
@@ -252,7 +287,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
-      const float2 sc = make_float2(a.scale, real_only ? 0.f : a.scale);
+      // FP16: undo the bin's data scale (a power of two, so exactly)
+      const float sy = kPrec == kF16 ? a.scale / f16_bin_scale(a.bin_absmax[k]) : a.scale;
+      const float2 sc = make_float2(sy, real_only ? 0.f : sy);
       const int64_t o_bin = static_cast<int64_t>(k) * a.y_bin_stride;
       for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
         const int group = it / n_pass;
@@ -324,6 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
       const uint32_t ku = static_cast<uint32_t>(a.k_begin + k);  // absolute bin
+      const float sx = kPrec == kF16 ? f16_bin_scale(a.bin_absmax[k]) : 1.f;  // data scale
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
@@ -348,7 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           const PhaseConst pc = pc_next;
           float2 x[kBeamsPerWarp];
 #pragma unroll
-          for (int m = 0; m < kBeamsPerWarp; ++m) x[m] = x_next[m];
+          for (int m = 0; m < kBeamsPerWarp; ++m)
+            x[m] = kPrec == kF16 ? make_float2(x_next[m].x * sx, x_next[m].y * sx) : x_next[m];
           if (t + 1 < n_tiles) {  // prefetch the next tile
             const int nn = nu + kKC;
             pc_next = nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
@@ -384,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           // of column pair 2*lane is (lane/4) ^ i, the rest is a constant.
 #pragma unroll
           for (int i = 0; i < kRows; ++i) {
-            const uint32_t hb = bf16x2_bits(__floats2bfloat162_rn(pb.x, pb.y));  // (pr, pi)
+            const uint32_t hb = pack2<kPrec>(pb.x, pb.y);  // (pr, pi)
             const uint32_t off = p_base + i * 128 + ((lane_chunk ^ (i << 4)));
             *reinterpret_cast<uint32_t*>(stage + off) = hb ^ 0x80000000u;                  // (pr, -pi)
             *reinterpret_cast<uint32_t*>(stage + kTileA + off) = __byte_perm(hb, 0, 0x1032);  // (pi, pr)
@@ -414,10 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
               // row a_in * kBeams + pw + 16 m: z_base + (kBeams / 8 * a_in + 2 m) groups
               const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
               const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
-              *reinterpret_cast<uint32_t*>(tb + z_base + ra) =
-                  bf16x2_bits(__floats2bfloat162_rn(za.x, za.y));
-              *reinterpret_cast<uint32_t*>(tb + z_base + rb) =
-                  bf16x2_bits(__floats2bfloat162_rn(zb.x, zb.y));
+              *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack2<kPrec>(za.x, za.y);
+              *reinterpret_cast<uint32_t*>(tb + z_base + rb) = pack2<kPrec>(zb.x, zb.y);
             }
             qa = __ffma2_rn(make_float2(-qa.y, qa.x), make_float2(r128.y, r128.y),
                             __fmul2_rn(qa, make_float2(r128.x, r128.x)));
@@ -455,10 +492,12 @@ int mac_tc_trials_per_pass(int n_series) {
 }
 
 cudaError_t mac_tc_prepare() {
-  const void* fns[] = {reinterpret_cast<const void*>(&mac_tc_kernel<true, 32>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<false, 32>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<true, 16>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<false, 16>)};
+  const void* fns[] = {reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 16>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 16>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)};
   for (const void* fn : fns) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(mac_tc_smem_bytes()));
@@ -467,16 +506,18 @@ cudaError_t mac_tc_prepare() {
   return cudaSuccess;
 }
 
-static cudaError_t launch_mac_tc_block(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s);
+static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cudaStream_t s);
 
 namespace {
 constexpr size_t kScratchAlign = 256;
 constexpr size_t kScratchCap = size_t(3) << 30;
-// Scratch bytes per bin: the bin-major spectra and the bin-major output
-// (complex, the larger of the two output kinds).
+// Scratch bytes per bin: the bin-major spectra, the bin-major output
+// (complex, the larger of the two output kinds) and the bin's FP16 scale key.
 size_t scratch_per_bin(int n_series, int n_chan, int n_dm) {
-  return sizeof(float2) * static_cast<size_t>(n_series) * (static_cast<size_t>(n_chan) + n_dm);
+  return sizeof(float2) * static_cast<size_t>(n_series) * (static_cast<size_t>(n_chan) + n_dm) +
+         sizeof(float);
 }
+uintptr_t align_up(uintptr_t p) { return (p + kScratchAlign - 1) & ~(kScratchAlign - 1); }
 }  // namespace
 
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins) {
@@ -484,29 +525,42 @@ size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins) 
   int64_t kb = static_cast<int64_t>(kScratchCap / per_bin);
   if (kb < 1) kb = 1;
   if (kb > n_bins) kb = n_bins;
-  return per_bin * static_cast<size_t>(kb) + kScratchAlign;
+  return per_bin * static_cast<size_t>(kb) + 2 * kScratchAlign;
 }
 
-cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scratch,
+cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   if (a.x_series_stride != a.x_chan_stride * a.n_chan) return cudaErrorInvalidValue;
+  const int prec = precision == FDD_PREC_BF16_HILO ? kBf16HiLo
+                   : precision == FDD_PREC_BF16    ? kBf16
+                   : precision == FDD_PREC_FP16    ? kF16
+                                                   : -1;
+  if (prec < 0) return cudaErrorInvalidValue;
   const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
   const int64_t y_rows = static_cast<int64_t>(a.n_series) * a.n_dm;
   const size_t y_elem = a.out_kind == 2 ? sizeof(float) : sizeof(float2);
-  const size_t per_bin = sizeof(float2) * rows + y_elem * y_rows;
-  const int64_t kb = scratch_bytes > kScratchAlign
-                         ? static_cast<int64_t>((scratch_bytes - kScratchAlign) / per_bin)
+  const size_t per_bin = sizeof(float2) * rows + y_elem * y_rows + sizeof(float);
+  const int64_t kb = scratch_bytes > 2 * kScratchAlign
+                         ? static_cast<int64_t>((scratch_bytes - 2 * kScratchAlign) / per_bin)
                          : 0;
   if (!scratch || kb < 1) return cudaErrorInvalidValue;
-  // [kb][rows] spectra, then (256-byte aligned) [kb][series][trial] output
-  const uintptr_t y_addr =
-      (reinterpret_cast<uintptr_t>(scratch + kb * rows) + kScratchAlign - 1) & ~(kScratchAlign - 1);
+  // [kb][rows] spectra, then (256-byte aligned) [kb][series][trial] output,
+  // then (aligned) the kb per-bin maxima of the FP16 form
+  const uintptr_t y_addr = align_up(reinterpret_cast<uintptr_t>(scratch + kb * rows));
   void* y_scratch = reinterpret_cast<void*>(y_addr);
+  unsigned int* absmax =
+      reinterpret_cast<unsigned int*>(align_up(y_addr + y_elem * static_cast<size_t>(kb * y_rows)));
   for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb) {
     const int nb = static_cast<int>((a.n_bins - k0) < kb ? (a.n_bins - k0) : kb);
-    BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, scratch};
-    cudaError_t e = launch_bin_transpose(t, s);
+    cudaError_t e;
+    if (prec == kF16) {
+      e = cudaMemsetAsync(absmax, 0, sizeof(unsigned int) * static_cast<size_t>(nb), s);
+      if (e != cudaSuccess) return e;
+    }
+    BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, scratch,
+                       prec == kF16 ? absmax : nullptr};
+    e = launch_bin_transpose(t, s);
     if (e != cudaSuccess) return e;
     MacArgs b = a;
     b.X = scratch;
@@ -519,7 +573,8 @@ cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scrat
     b.y_bin_stride = y_rows;
     b.y_series_stride = a.n_dm;
     b.y_dm_stride = 1;
-    e = launch_mac_tc_block(b, hi_lo, n_sms, s);
+    b.bin_absmax = reinterpret_cast<const float*>(absmax);
+    e = launch_mac_tc_block(b, prec, n_sms, s);
     if (e != cudaSuccess) return e;
     BinUntransposeArgs u{y_scratch, static_cast<int>(y_elem), a.n_series, a.n_dm, nb,
                          static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0),
@@ -530,16 +585,21 @@ cudaError_t launch_mac_tc(const MacArgs& a, bool hi_lo, int n_sms, float2* scrat
   return cudaSuccess;
 }
 
-static cudaError_t launch_mac_tc_block(const MacArgs& a, bool hi_lo, int n_sms, cudaStream_t s) {
+static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cudaStream_t s) {
   const int grid = a.n_bins < n_sms ? a.n_bins : n_sms;
   MacArgs args = a;
   void* params[] = {&args};
   const bool g16 = mac_tc_beams_per_group(a.n_series) == 16;
-  const void* fn =
-      hi_lo ? (g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<true, 16>)
-                   : reinterpret_cast<const void*>(&mac_tc_kernel<true, 32>))
-            : (g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<false, 16>)
-                   : reinterpret_cast<const void*>(&mac_tc_kernel<false, 32>));
+  const void* fn;
+  if (prec == kBf16HiLo)
+    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 16>)
+             : reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 32>);
+  else if (prec == kBf16)
+    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 16>)
+             : reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 32>);
+  else
+    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)
+             : reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>);
   return cudaLaunchKernel(fn, dim3(grid),
                           dim3(kThreads), params, mac_tc_smem_bytes(), s);
 }

@@ -125,20 +125,28 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float* __restrict__ 
 
 // 32 bins x 32 rows through shared memory: coalesced reads along bins,
 // coalesced writes along rows.  Rows beyond gridDim.y tiles are covered by a
-// grid-stride loop.
+// grid-stride loop.  With absmax, each bin's largest |re| or |im| over the
+// rows this block read goes to absmax[bin] by one atomic max per bin.
 __global__ void __launch_bounds__(256) bin_transpose_kernel(const float2* __restrict__ in,
                                                             int64_t in_stride, int64_t rows,
                                                             int64_t k0, int n_bins,
-                                                            float2* __restrict__ out) {
+                                                            float2* __restrict__ out,
+                                                            unsigned int* __restrict__ absmax) {
   __shared__ float2 tile[kTile][kTile + 1];
+  __shared__ float red[8][kTile];
   const int kb0 = blockIdx.x * kTile;
+  float m = 0.f;  // bin kb0 + threadIdx.x, the rows this thread read
   for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTile; r0 < rows;
        r0 += static_cast<int64_t>(gridDim.y) * kTile) {
 #pragma unroll
     for (int i = threadIdx.y; i < kTile; i += 8) {
       const int64_t r = r0 + i;
       const int kb = kb0 + threadIdx.x;
-      if (r < rows && kb < n_bins) tile[i][threadIdx.x] = in[r * in_stride + k0 + kb];
+      if (r < rows && kb < n_bins) {
+        const float2 v = in[r * in_stride + k0 + kb];
+        tile[i][threadIdx.x] = v;
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -149,11 +157,18 @@ __global__ void __launch_bounds__(256) bin_transpose_kernel(const float2* __rest
     }
     __syncthreads();
   }
+  if (absmax) {
+    red[threadIdx.y][threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+#pragma unroll
+      for (int j = 1; j < 8; ++j) m = fmaxf(m, red[j][threadIdx.x]);
+      const int kb = kb0 + threadIdx.x;
+      if (kb < n_bins && m > 0.f) atomicMax(absmax + kb, __float_as_uint(m));
+    }
+  }
 }
 
-// 32 trials x 32 bins of one series through shared memory: coalesced reads
-// along trials (bin-major input), coalesced writes along bins.  Tiles of
-// (series, trial) beyond gridDim.y are covered by a grid-stride loop.
 // Thread rows of the untranspose's 32 x 32 tiles (4: measured 5.7 TB/s on the
 // 32-beam slice, against 5.5 TB/s with 8 rows and less with wider tiles).
 constexpr int kUntrRows = 4;
@@ -216,7 +231,7 @@ cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s) {
   dim3 grid((a.n_bins + kTile - 1) / kTile,
             static_cast<unsigned>(row_tiles < 65535 ? row_tiles : 65535));
   bin_transpose_kernel<<<grid, dim3(kTile, 8), 0, s>>>(a.in, a.in_stride, a.rows, a.k0,
-                                                      a.n_bins, a.out);
+                                                      a.n_bins, a.out, a.absmax);
   return cudaGetLastError();
 }
 

@@ -124,8 +124,8 @@ def _random_spectra(rng, shape):
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16],
-                         ids=["bf16_hilo", "bf16"])
+@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16,
+                                       fdd.FDD_PREC_FP16], ids=["bf16_hilo", "bf16", "fp16"])
 def test_32beam_tensor_core_bench_slice(precision):
     w = synth.WORKLOADS["fdd_32beam_1024ch_2p19t_4096dm"].scaled(n_t=4096)
     rng = np.random.default_rng(SEED + 3)
@@ -144,7 +144,9 @@ def test_32beam_tensor_core_bench_slice(precision):
     d = _delays(w)
     errs = [rel_l2(got[i], oracle.fdd_bins(X[b][:, bins].astype(np.complex128), bins, w.n_t, d))
             for i, b in enumerate(beams)]
-    print(f"32 beams, tensor cores ({'hi+lo' if precision == fdd.FDD_PREC_BF16_HILO else 'bf16'}),"
+    name = {fdd.FDD_PREC_BF16_HILO: "hi+lo", fdd.FDD_PREC_BF16: "bf16",
+            fdd.FDD_PREC_FP16: "fp16"}[precision]
+    print(f"32 beams, tensor cores ({name}),"
           f" bench slice: rel-L2 vs FP64 {max(errs):.2e}")
     assert max(errs) <= TC_REL_L2
 

@@ -55,6 +55,7 @@ def _out_like(info, output, device):
     (fdd.FDD_OUT_POWER, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_BF16_HILO, 1),
     (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 2, fdd.FDD_PREC_FP32, 4),   # down-sampled
     (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_BF16_HILO, 2),
+    (fdd.FDD_OUT_TIME, fdd.FDD_LAYOUT_TIME_MAJOR, 3, fdd.FDD_PREC_FP16, 1),
 ])
 def test_host_pipeline_equals_device_execute(output, layout, n_beams, precision, ds):
     out_name = {fdd.FDD_OUT_TIME: "time", fdd.FDD_OUT_SPECTRA: "spectra",

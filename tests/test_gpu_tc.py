@@ -1,5 +1,5 @@
-"""Tensor-core form (tcgen05, BF16 hi+lo phasors, BF16 data, FP32 accumulation)
-against the FP64 oracle (GB300 only).
+"""Tensor-core form (tcgen05; BF16 hi+lo, BF16, or FP16 operands with per-bin
+data scaling; FP32 accumulation) against the FP64 oracle (GB300 only).
 
 The gate is the low-precision form's relative L2 error <= 3e-3 against FP64:
 BF16 rounding of the data side alone is ~2^-9 / sqrt(3) ~ 1.1e-3 per element.
@@ -36,11 +36,17 @@ def _workload(n_chan, n_t, dms, n_beams, band=(1200.0, 1500.0), t_samp=2e-3, chu
     return synth.Workload(name="tc", n_chan=n_chan, band_lo_mhz=band[0], band_hi_mhz=band[1],
                           t_samp_s=t_samp, n_t=n_t, dtype=dtype, dm0=float(dms[0]), ddm=ddm,
                           n_dm=dms.size, chunk_len=chunk_len, n_beams=n_beams, output=output,
-                          pulses_per_beam=1)
+                          pulses_per_beam=1,
+                          noise_mean=128.0 if dtype == "u8" else 0.0,
+                          noise_sigma=16.0 if dtype == "u8" else 1.0)
 
 
-@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16],
-                         ids=["bf16_hilo", "bf16"])
+PREC_NAMES = {fdd.FDD_PREC_BF16_HILO: "hi+lo", fdd.FDD_PREC_BF16: "bf16",
+              fdd.FDD_PREC_FP16: "fp16"}
+
+
+@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16,
+                                       fdd.FDD_PREC_FP16], ids=["bf16_hilo", "bf16", "fp16"])
 @pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
     (5, 40, 256, 0.0, 0.5, 2100),    # partial 16-beam group, ragged channel tile, 2 passes
     (32, 64, 128, 3.0, 1.0, 1024),   # one full group, exactly one pass
@@ -76,7 +82,7 @@ def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm, precision
         ref = oracle.fdd_bins(X[s], np.arange(K), L, d)
         errs.append(rel_l2(Y[s], ref))
         assert rel_l2(P[s], np.abs(ref) ** 2) <= 2 * TC_REL_L2
-    print(f"tensor-core ({'hi+lo' if precision == fdd.FDD_PREC_BF16_HILO else 'bf16'}) "
+    print(f"tensor-core ({PREC_NAMES[precision]}) "
           f"rel-L2 vs FP64: max over series {max(errs):.2e}")
     assert max(errs) <= TC_REL_L2
 
@@ -102,13 +108,19 @@ def test_tc_dm_subrange_matches_full():
     assert rel_l2(g, f) <= TC_REL_L2
 
 
+@pytest.mark.parametrize("precision,dtype", [(fdd.FDD_PREC_BF16_HILO, "f32"),
+                                             (fdd.FDD_PREC_FP16, "f32"),
+                                             (fdd.FDD_PREC_FP16, "u8")],
+                         ids=["bf16_hilo", "fp16", "fp16_u8"])
 @pytest.mark.parametrize("output", ["time", "power"])
-def test_tc_end_to_end(output):
-    """Eight beams through the whole path on the tensor-core form."""
+def test_tc_end_to_end(output, precision, dtype):
+    """Eight beams through the whole path on the tensor-core form; with 8-bit
+    input (mean 128) the FP16 form's per-bin scale must hold spectra whose DC
+    bins reach ~1e5 while the rest are ~1e2-1e3."""
     w = _workload(48, 3000, 2.0 * np.arange(150), 8, t_samp=5e-4, chunk_len=1024,
-                  output=output)
+                  output=output, dtype=dtype)
     fbs = np.stack([synth.filterbank(w, seed=17, beam=b)[0] for b in range(8)])
-    with fdd.Plan(**params_for(w, precision=fdd.FDD_PREC_BF16_HILO)) as plan:
+    with fdd.Plan(**params_for(w, precision=precision)) as plan:
         info = plan.info
         dx = torch.from_numpy(fbs).cuda()
         out = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
@@ -122,6 +134,9 @@ def test_tc_end_to_end(output):
         for b in range(8):
             ref = oracle.fdd_time(fbs[b].T.astype(np.float64), d, w.chunk_len)
             assert rel_l2(o[b], ref) <= TC_REL_L2
+            # the zero-mean part too (with 8-bit data the constant dominates the above)
+            zm = lambda y: y - y.mean(axis=1, keepdims=True)  # noqa: E731
+            assert rel_l2(zm(o[b]), zm(ref)) <= TC_REL_L2
     else:
         o = o.reshape(8, geo.n_chunks, w.n_dm, geo.K)
         for b in range(0, 8, 3):
@@ -130,6 +145,7 @@ def test_tc_end_to_end(output):
                 ref = np.abs(oracle.fdd_bins(oracle.spectra(x, geo, c), np.arange(geo.K),
                                              geo.L, d)) ** 2
                 assert rel_l2(o[b, c], ref) <= 2 * TC_REL_L2
+                assert rel_l2(o[b, c][:, 1:], ref[:, 1:]) <= 2 * TC_REL_L2  # without DC
 
 
 @pytest.mark.parametrize("n_series", [7, 20])
