@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FDD_ABI_VERSION 1
+#define FDD_ABI_VERSION 2
 
 struct CUstream_st;
 typedef struct CUstream_st* fdd_stream_t; /* same type as cudaStream_t */
@@ -69,32 +69,20 @@ typedef enum fdd_status {
 #define FDD_OUT_POWER 2   /* float  [beam][chunk][n_dm][n_bins]: |Y|^2 for
                              periodicity searches (Sect. 5)                     */
 
-/* Kernel variants of the FP32 phase-rotate-and-sum (fdd_params.mac_variant - 1,
- * fdd_info.mac_variant).  S issues single FFMAs; Q and P issue paired f32x2
- * FMAs (Q swaps compact (re, im) pairs between lanes, P pre-broadcast quads);
- * SP and QP overlap the phasor evaluation of the next channel with the
- * multiply-accumulates of the current one; AxB is the per-lane register tile
- * (a warp covers 2048, 1024 or 4 x 128 trials). */
-#define FDD_MAC_S_8X8 0
-#define FDD_MAC_S_4X8 1
-#define FDD_MAC_S_4X4 2
-#define FDD_MAC_Q_8X8 3
-#define FDD_MAC_Q_4X8 4
-#define FDD_MAC_Q_4X4 5
-#define FDD_MAC_P_8X8 6
-#define FDD_MAC_SP_8X8 7
-#define FDD_MAC_QP_8X8 8
-#define FDD_MAC_Q2_8X8 9  /* Q with the MAC in two passes over the tile           */
-#define FDD_MAC_R_8X8 10  /* reference: the first scalar kernel                   */
-#define FDD_MAC_Q12_8X8 11 /* Q with 12-warp blocks (fewer registers, more warps)  */
-#define FDD_MAC_S12_8X8 12 /* S with 12-warp blocks                                */
-#define FDD_MAC_Z12_8X8 13 /* Z swapped as pre-broadcast quads, 12-warp blocks    */
-#define FDD_MAC_P12_8X8 14 /* P with 12-warp blocks                                */
-#define FDD_MAC_W12_8X8 15 /* warp-specialised: 4 phasor warps feed 8 MAC warps   */
-#define FDD_MAC_Q_8X8_512 16 /* Q, 8x8 lane tile, 8 lanes per bin, four bins per
-                                warp: 512-trial blocks (between Q_4X4's 128 and
-                                Q_4X8's 1024)                                    */
-#define FDD_MAC_VARIANTS 17
+/* Kernel tiles of the FP32 phase-rotate-and-sum (fdd_params.mac_variant - 1,
+ * fdd_info.mac_variant).  All issue paired f32x2 FMAs on an A x B register
+ * tile per lane (a warp covers 2048, 1024, 4 x 512 or 4 x 128 trials of its
+ * bins); W12 splits phasor evaluation (4 warps) from the multiply-accumulates
+ * (8 warps), the others let every warp do both. */
+#define FDD_MAC_W12_8X8 0   /* warp-specialised, 2048-trial blocks (default for
+                               large trial counts)                              */
+#define FDD_MAC_Q12_8X8 1   /* 2048-trial blocks, 12 warps, plain schedule       */
+#define FDD_MAC_Q_4X8 2     /* 1024-trial blocks                                 */
+#define FDD_MAC_Q_8X8_512 3 /* 8x8 lane tile, 8 lanes per bin, four bins per
+                               warp: 512-trial blocks                           */
+#define FDD_MAC_Q_4X4 4     /* 4x4 lane tile, four bins per warp: 128-trial
+                               blocks (small trial counts, ragged tails)        */
+#define FDD_MAC_VARIANTS 5
 #define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
 
 /* fdd_params.precision */
@@ -452,24 +440,29 @@ fdd_status fdd_batch_destroy(fdd_batch_t b);
  * Applications that hand all of a GPU's memory to their own pool, or
  * real-time pipelines that forbid allocation once running, cannot create a
  * plan, because fdd_plan allocates workspace.  This call takes the plan
- * parameters *p directly (only the fields that the phase-rotate-and-sum
- * uses are read and checked as fdd_plan would: channels, frequencies, t_samp,
- * n_t and chunk_len for the transform length, the DM list, k_dm, nu_ref,
- * mac_variant; precision must be FDD_PREC_FP32) and computes exactly what
+ * parameters *p directly (the fields that the phase-rotate-and-sum uses --
+ * channels, frequencies, t_samp, n_t and chunk_len for the transform length,
+ * the DM list, k_dm, nu_ref -- are checked exactly as fdd_plan checks them;
+ * precision must be FDD_PREC_FP32) and computes bit for bit what
  * fdd_dedisperse_spectra computes for a plan made from *p, with the same
- * arguments and layouts.  It allocates
- * nothing, on the device or the host, and calls no allocating library routine.
- * The per-channel phase table the kernel reads lives in a file-scope device
- * array of FDD_STATIC_MAX_CHAN entries (128 KiB), which every GPU that loads
- * the library holds until the process exits; it is rewritten, in stream
- * order, by every call.  Calls share that one array, so calls that overlap
- * on the GPU (on different streams, or from different threads) race and must
- * be serialised by the caller.  The first call on each device looks up the
- * array's device address (a one-time set-up); make that first call before
- * any stream capture.
+ * arguments and layouts.  It allocates nothing, on the device or the host,
+ * and calls no allocating library routine.  The per-channel phase table the
+ * kernel reads lives in a file-scope device array of FDD_STATIC_MAX_CHAN
+ * entries (128 KiB), which every GPU that loads the library holds until the
+ * process exits; every call rewrites it, in stream order, with small kernel
+ * launches that carry the constants in their parameters.  Calls share that
+ * one array, so calls that overlap on the GPU (on different streams, or from
+ * different threads) race and must be serialised by the caller; calls queued
+ * on one stream are ordered and need nothing more.  The first call on each
+ * device looks up the array's device address (a one-time set-up); make that
+ * first call before any stream capture.  Without a plan there is no status
+ * word: a bounded device-side wait that runs out (reported as FDD_ERR_TIMEOUT
+ * by the planned calls) is not reported here, and the output is then
+ * incomplete.
  * Errors: FDD_ERR_INVALID_ARG (NULL pointers, n_chan above
- * FDD_STATIC_MAX_CHAN, bad ranges or pitches), FDD_ERR_UNSUPPORTED
- * (non-uniform DM list, precision other than FP32), FDD_ERR_CUDA.
+ * FDD_STATIC_MAX_CHAN, bad ranges or pitches, the parameter errors of
+ * fdd_plan), FDD_ERR_UNSUPPORTED (non-uniform DM list, precision other than
+ * FP32, transform length above 2^30), FDD_ERR_CUDA.
  */
 fdd_status fdd_dedisperse_spectra_static(const fdd_params* p, const void* d_X, int64_t x_pitch,
                                          int32_t n_series, int32_t dm_first, int32_t n_dm,

@@ -28,7 +28,7 @@ struct fdd_plan_s {
   std::vector<double> dms;
   fdd_info info{};
   int device = -1;
-  double nu_ref = 0.0;
+  fdd::CoreGeometry core{};   // Eq. 1 constants and the chunking
   std::vector<double> rate;  // c_nu, samples per unit DM (Eq. 1 / t_samp)
   std::vector<fdd::PhaseConst> pc_host;
   fdd::PhaseConst* d_pc = nullptr;
@@ -70,15 +70,15 @@ struct fdd_plan_s {
 
 namespace {
 
-thread_local std::string g_err;
+// Last error message of this thread (a fixed buffer: reporting an error
+// never allocates).
+thread_local char g_err[512];
 
 fdd_status fail(fdd_status s, const char* fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
   va_end(ap);
-  g_err = buf;
   return s;
 }
 
@@ -164,29 +164,33 @@ void scaled_product(double m, double c, double L, double* hi, double* lo) {
   *lo = (r + pe) / L;
 }
 
-fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* rate_out,
-                        double* nu_ref_out) {
+}  // namespace
+
+namespace fdd {
+
+double delay_rate(const fdd_params& p, const CoreGeometry& g, int c) {
+  const double nu = p.nu_lo_mhz + p.dnu_mhz * c;
+  return g.k_dm * (1.0 / (nu * nu) - 1.0 / (g.nu_ref * g.nu_ref)) / p.t_samp_s;
+}
+
+PhaseConst phase_const(double rate, double L, double dm0, double ddm) {
+  double hi, lo;
+  scaled_product(dm0, rate, L, &hi, &lo);
+  const uint64_t u = frac_to_fixed64(hi, lo);
+  scaled_product(ddm, rate, L, &hi, &lo);
+  const uint64_t v = frac_to_fixed64(hi, lo);
+  return PhaseConst{static_cast<uint32_t>(u), static_cast<uint32_t>(u >> 32),
+                    static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32)};
+}
+
+fdd_status core_geometry(const fdd_params* p, CoreGeometry* out) {
   if (!p) return fail(FDD_ERR_INVALID_ARG, "params is NULL");
-  if (!g) return fail(FDD_ERR_INVALID_ARG, "info is NULL");
   if (p->n_chan < 1) return fail(FDD_ERR_INVALID_ARG, "n_chan must be >= 1 (got %d)", p->n_chan);
-  if (p->n_beams < 1) return fail(FDD_ERR_INVALID_ARG, "n_beams must be >= 1");
   if (!(p->t_samp_s > 0.0) || !std::isfinite(p->t_samp_s))
     return fail(FDD_ERR_INVALID_ARG, "t_samp_s must be > 0");
   if (p->n_t < 2) return fail(FDD_ERR_INVALID_ARG, "n_t must be >= 2");
   if (!p->dm_list) return fail(FDD_ERR_INVALID_ARG, "dm_list is NULL");
   if (p->n_dm < 1) return fail(FDD_ERR_INVALID_ARG, "n_dm must be >= 1");
-  if (p->in_dtype != FDD_IN_U8 && p->in_dtype != FDD_IN_F32)
-    return fail(FDD_ERR_INVALID_ARG, "in_dtype %d unknown", p->in_dtype);
-  if (p->in_layout != FDD_LAYOUT_TIME_MAJOR && p->in_layout != FDD_LAYOUT_CHAN_MAJOR)
-    return fail(FDD_ERR_INVALID_ARG, "in_layout %d unknown", p->in_layout);
-  if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
-    return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
-  if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO &&
-      p->precision != FDD_PREC_BF16 && p->precision != FDD_PREC_FP16)
-    return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
-  if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
-    return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
-                FDD_MAC_VARIANTS);
   if (p->chunk_len < 0 || (p->chunk_len % 2) != 0)
     return fail(FDD_ERR_INVALID_ARG, "chunk_len must be 0 or a positive even length");
   if (!(p->dnu_mhz != 0.0) || !std::isfinite(p->dnu_mhz))
@@ -194,27 +198,24 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   if (!(p->k_dm >= 0.0) || !std::isfinite(p->k_dm))
     return fail(FDD_ERR_INVALID_ARG, "k_dm must be >= 0 (0 selects the default)");
 
+  CoreGeometry g{};
   const int nc = p->n_chan;
-  double nu_max = -1.0, nu_min = std::numeric_limits<double>::infinity();
+  double nu_max = -1.0;
   for (int c = 0; c < nc; ++c) {
     const double nu = p->nu_lo_mhz + p->dnu_mhz * c;
     if (!(nu > 0.0) || !std::isfinite(nu))
       return fail(FDD_ERR_INVALID_ARG, "channel %d centre %.6g MHz is not positive", c, nu);
     nu_max = nu > nu_max ? nu : nu_max;
-    nu_min = nu < nu_min ? nu : nu_min;
   }
-  const double nu_ref = p->nu_ref_mhz == 0.0 ? nu_max : p->nu_ref_mhz;
-  if (!(nu_ref >= nu_max) || !std::isfinite(nu_ref))
+  g.nu_ref = p->nu_ref_mhz == 0.0 ? nu_max : p->nu_ref_mhz;
+  if (!(g.nu_ref >= nu_max) || !std::isfinite(g.nu_ref))
     return fail(FDD_ERR_INVALID_ARG, "nu_ref_mhz (%.9g) must be >= the highest channel centre (%.9g)",
-                nu_ref, nu_max);
-  const double kdm = p->k_dm == 0.0 ? kKdmPaper : p->k_dm;
-
-  std::vector<double> rate(nc);
-  double rate_max = 0.0;
+                g.nu_ref, nu_max);
+  g.k_dm = p->k_dm == 0.0 ? kKdmPaper : p->k_dm;
+  g.rate_max = 0.0;
   for (int c = 0; c < nc; ++c) {
-    const double nu = p->nu_lo_mhz + p->dnu_mhz * c;
-    rate[c] = kdm * (1.0 / (nu * nu) - 1.0 / (nu_ref * nu_ref)) / p->t_samp_s;
-    rate_max = rate[c] > rate_max ? rate[c] : rate_max;
+    const double r = delay_rate(*p, g, c);
+    g.rate_max = r > g.rate_max ? r : g.rate_max;
   }
 
   double dm_max = 0.0;
@@ -225,39 +226,38 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
     dm_max = dm > dm_max ? dm : dm_max;
   }
   // Uniform grid check: every entry within 4 ulp of dm0 + j ddm.
-  const double dm0 = p->dm_list[0];
-  const double ddm = p->n_dm > 1 ? (p->dm_list[p->n_dm - 1] - dm0) / (p->n_dm - 1) : 0.0;
+  g.dm0 = p->dm_list[0];
+  g.ddm = p->n_dm > 1 ? (p->dm_list[p->n_dm - 1] - g.dm0) / (p->n_dm - 1) : 0.0;
   const double tol = 4.0 * std::ldexp(std::numeric_limits<double>::epsilon(),
                                       std::ilogb(dm_max > 1.0 ? dm_max : 1.0));
   // (A non-uniform list makes a valid plan: the time-domain path takes any
   // list; the Fourier-domain calls refuse it, see need_uniform_grid.)
-  int uniform = 1;
-  for (int j = 0; j < p->n_dm && uniform; ++j)
-    if (std::fabs(p->dm_list[j] - (dm0 + j * ddm)) > tol) uniform = 0;
+  g.uniform = 1;
+  for (int j = 0; j < p->n_dm && g.uniform; ++j)
+    if (std::fabs(p->dm_list[j] - (g.dm0 + j * g.ddm)) > tol) g.uniform = 0;
 
-  const double max_delay = dm_max * rate_max;  // both factors are >= 0
+  const double max_delay = dm_max * g.rate_max;  // both factors are >= 0
   if (max_delay > 4.0e18) return fail(FDD_ERR_INVALID_ARG, "delays overflow");
-  const int64_t d_max = static_cast<int64_t>(std::ceil(max_delay));
+  g.d_max = static_cast<int64_t>(std::ceil(max_delay));
 
-  std::memset(g, 0, sizeof *g);
   int64_t L, hop, n_chunks, out_len, valid_len;
   if (p->chunk_len == 0) {
     L = next_pow2(p->n_t);
     hop = p->n_t;
     n_chunks = 1;
     out_len = p->n_t;
-    valid_len = p->n_t > d_max ? p->n_t - d_max : 0;
+    valid_len = p->n_t > g.d_max ? p->n_t - g.d_max : 0;
   } else {
     L = p->chunk_len;
-    hop = L - d_max;
+    hop = L - g.d_max;
     if (hop <= 0)
       return fail(FDD_ERR_INVALID_ARG,
                   "chunk_len %lld does not exceed the largest delay (%lld samples)",
-                  (long long)L, (long long)d_max);
-    out_len = p->n_t - d_max;
+                  (long long)L, (long long)g.d_max);
+    out_len = p->n_t - g.d_max;
     if (out_len <= 0)
       return fail(FDD_ERR_INVALID_ARG, "n_t %lld does not exceed the largest delay %lld",
-                  (long long)p->n_t, (long long)d_max);
+                  (long long)p->n_t, (long long)g.d_max);
     n_chunks = (out_len + hop - 1) / hop;
     valid_len = out_len;
   }
@@ -291,15 +291,53 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   // The kernels form k * j in 32-bit integers.
   if (static_cast<double>(n_bins - 1) * static_cast<double>(p->n_dm - 1) >= 4294967296.0)
     return fail(FDD_ERR_UNSUPPORTED, "(n_bins-1)*(n_dm-1) must be below 2^32");
+  g.L = L;
+  g.n_bins = n_bins;
+  g.hop = hop;
+  g.n_chunks = n_chunks;
+  g.out_len = out_len;
+  g.valid_len = valid_len;
+  g.downsample = f;
+  *out = g;
+  return FDD_OK;
+}
 
+}  // namespace fdd
+
+namespace {
+
+fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* core_out) {
+  if (!p) return fail(FDD_ERR_INVALID_ARG, "params is NULL");
+  if (!g) return fail(FDD_ERR_INVALID_ARG, "info is NULL");
+  if (p->n_beams < 1) return fail(FDD_ERR_INVALID_ARG, "n_beams must be >= 1");
+  if (p->in_dtype != FDD_IN_U8 && p->in_dtype != FDD_IN_F32)
+    return fail(FDD_ERR_INVALID_ARG, "in_dtype %d unknown", p->in_dtype);
+  if (p->in_layout != FDD_LAYOUT_TIME_MAJOR && p->in_layout != FDD_LAYOUT_CHAN_MAJOR)
+    return fail(FDD_ERR_INVALID_ARG, "in_layout %d unknown", p->in_layout);
+  if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
+    return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
+  if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO &&
+      p->precision != FDD_PREC_BF16 && p->precision != FDD_PREC_FP16)
+    return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
+  if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
+    return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
+                FDD_MAC_VARIANTS);
+  fdd::CoreGeometry cg;
+  fdd_status st = fdd::core_geometry(p, &cg);
+  if (st != FDD_OK) return st;
+  const int nc = p->n_chan;
+  const int64_t L = cg.L, n_bins = cg.n_bins, n_chunks = cg.n_chunks, out_len = cg.out_len;
+  const int f = cg.downsample;
+
+  std::memset(g, 0, sizeof *g);
   g->fft_len = L;
   g->n_bins = n_bins;
   g->bin_pitch = round_up(n_bins, 64);
   g->n_chunks = n_chunks;
-  g->hop = hop;
-  g->d_max = d_max;
+  g->hop = cg.hop;
+  g->d_max = cg.d_max;
   g->out_len = out_len;
-  g->valid_len = valid_len;
+  g->valid_len = cg.valid_len;
   g->downsample = f;
   g->in_elems = static_cast<int64_t>(p->n_beams) * p->n_t * nc;
   if (p->output == FDD_OUT_TIME) {
@@ -309,9 +347,9 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
     g->out_elems = static_cast<int64_t>(p->n_beams) * n_chunks * p->n_dm * n_bins;
     g->out_bytes = g->out_elems * (p->output == FDD_OUT_SPECTRA ? 8 : 4);
   }
-  g->dm0 = dm0;
-  g->ddm = ddm;
-  g->dm_uniform = uniform;
+  g->dm0 = cg.dm0;
+  g->ddm = cg.ddm;
+  g->dm_uniform = cg.uniform;
   const bool tc = p->precision != FDD_PREC_FP32;
   g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
                                                      : fdd::mac_variant_for(p->n_dm));
@@ -340,8 +378,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, std::vector<double>* r
   }
   g->dm_batch = static_cast<int32_t>(batch);
   g->workspace_bytes = static_cast<int64_t>(fixed + per_dm * batch);
-  if (rate_out) *rate_out = std::move(rate);
-  if (nu_ref_out) *nu_ref_out = nu_ref;
+  if (core_out) *core_out = cg;
   return FDD_OK;
 }
 
@@ -683,11 +720,6 @@ bool injected_alloc_failure() {
   return false;
 }
 
-uint64_t fixed64_phase_rate(double m, double rate, double L) {
-  double hi, lo;
-  scaled_product(m, rate, L, &hi, &lo);
-  return frac_to_fixed64(hi, lo);
-}
 
 }  // namespace fdd
 
@@ -709,7 +741,7 @@ const char* fdd_status_string(fdd_status s) {
   return "FDD_ERR_UNKNOWN";
 }
 
-const char* fdd_last_error(void) { return g_err.c_str(); }
+const char* fdd_last_error(void) { return g_err; }
 
 void fdd_params_init(fdd_params* p) {
   if (!p) return;
@@ -722,7 +754,7 @@ void fdd_params_init(fdd_params* p) {
 }
 
 fdd_status fdd_plan_geometry(const fdd_params* p, fdd_info* out) {
-  return compute_plan(p, out, nullptr, nullptr);
+  return compute_plan(p, out, nullptr);
 }
 
 fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
@@ -732,8 +764,10 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   if (!P) return fail(FDD_ERR_ALLOC, "host allocation failed");
   std::unique_ptr<fdd_plan_s, void (*)(fdd_plan_s*)> guard(P, release);
 
-  fdd_status st = compute_plan(p, &P->info, &P->rate, &P->nu_ref);
+  fdd_status st = compute_plan(p, &P->info, &P->core);
   if (st != FDD_OK) return st;
+  P->rate.resize(p->n_chan);
+  for (int c = 0; c < p->n_chan; ++c) P->rate[c] = fdd::delay_rate(*p, P->core, c);
   P->p = *p;
   P->dms.assign(p->dm_list, p->dm_list + p->n_dm);
   P->p.dm_list = nullptr;
@@ -754,17 +788,9 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
     FDD_CUDA(fdd::mac_prepare(g.mac_variant, p->n_chan));
 
   // Exact fixed-point phase rates (see fdd_internal.h).
-  const double L = static_cast<double>(g.fft_len);
   P->pc_host.resize(p->n_chan);
-  for (int c = 0; c < p->n_chan; ++c) {
-    double hi, lo;
-    scaled_product(g.dm0, P->rate[c], L, &hi, &lo);
-    const uint64_t u = frac_to_fixed64(hi, lo);
-    scaled_product(g.ddm, P->rate[c], L, &hi, &lo);
-    const uint64_t v = frac_to_fixed64(hi, lo);
-    P->pc_host[c] = fdd::PhaseConst{static_cast<uint32_t>(u), static_cast<uint32_t>(u >> 32),
-                                    static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32)};
-  }
+  for (int c = 0; c < p->n_chan; ++c)
+    P->pc_host[c] = fdd::phase_const(P->rate[c], static_cast<double>(g.fft_len), g.dm0, g.ddm);
 
   const int nc = p->n_chan;
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_pc), sizeof(fdd::PhaseConst) * nc)))

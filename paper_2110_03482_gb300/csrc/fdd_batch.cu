@@ -280,19 +280,11 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     in_acc += d.n_t * static_cast<int64_t>(p->n_chan);
     out_acc += g.n_bins * static_cast<int64_t>(d.n_dm);
     L_max = std::max(L_max, g.fft_len);
-    const double kdm = p->k_dm == 0.0 ? 1.0 / 2.41e-4 : p->k_dm;
-    double nu_max = -1.0;
-    for (int c = 0; c < p->n_chan; ++c) nu_max = std::max(nu_max, p->nu_lo_mhz + p->dnu_mhz * c);
-    const double nu_ref = p->nu_ref_mhz == 0.0 ? nu_max : p->nu_ref_mhz;
-    for (int c = 0; c < p->n_chan; ++c) {
-      const double nu = p->nu_lo_mhz + p->dnu_mhz * c;
-      const double rate = kdm * (1.0 / (nu * nu) - 1.0 / (nu_ref * nu_ref)) / p->t_samp_s;
-      const uint64_t u = fdd::fixed64_phase_rate(g.dm0, rate, static_cast<double>(g.fft_len));
-      const uint64_t v = fdd::fixed64_phase_rate(g.ddm, rate, static_cast<double>(g.fft_len));
-      pc[static_cast<size_t>(b) * p->n_chan + c] =
-          fdd::PhaseConst{static_cast<uint32_t>(u), static_cast<uint32_t>(u >> 32),
-                          static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32)};
-    }
+    fdd::CoreGeometry cg;
+    if ((st = fdd::core_geometry(&q, &cg)) != FDD_OK) return st;
+    for (int c = 0; c < p->n_chan; ++c)
+      pc[static_cast<size_t>(b) * p->n_chan + c] = fdd::phase_const(
+          fdd::delay_rate(q, cg, c), static_cast<double>(g.fft_len), g.dm0, g.ddm);
   }
   B->in_elems = in_acc;
   B->out_elems = out_acc;

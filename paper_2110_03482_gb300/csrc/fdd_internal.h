@@ -49,23 +49,11 @@ struct MacArgs {
 // Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu and the
 // FDD_MAC_* list in fdd.h).
 enum MacVariant {
-  MAC_S_8x8 = FDD_MAC_S_8X8,
-  MAC_S_4x8 = FDD_MAC_S_4X8,
-  MAC_S_4x4 = FDD_MAC_S_4X4,
-  MAC_Q_8x8 = FDD_MAC_Q_8X8,
-  MAC_Q_4x8 = FDD_MAC_Q_4X8,
-  MAC_Q_4x4 = FDD_MAC_Q_4X4,
-  MAC_P_8x8 = FDD_MAC_P_8X8,
-  MAC_SP_8x8 = FDD_MAC_SP_8X8,
-  MAC_QP_8x8 = FDD_MAC_QP_8X8,
-  MAC_Q2_8x8 = FDD_MAC_Q2_8X8,
-  MAC_R_8x8 = FDD_MAC_R_8X8,
-  MAC_Q12_8x8 = FDD_MAC_Q12_8X8,
-  MAC_S12_8x8 = FDD_MAC_S12_8X8,
-  MAC_Z12_8x8 = FDD_MAC_Z12_8X8,
-  MAC_P12_8x8 = FDD_MAC_P12_8X8,
   MAC_W12_8x8 = FDD_MAC_W12_8X8,
+  MAC_Q12_8x8 = FDD_MAC_Q12_8X8,
+  MAC_Q_4x8 = FDD_MAC_Q_4X8,
   MAC_Q_8x8_512 = FDD_MAC_Q_8X8_512,
+  MAC_Q_4x4 = FDD_MAC_Q_4X4,
   MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
 };
 // One set of spectra in a batch (the batching form): its launch arguments
@@ -146,10 +134,31 @@ cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s);
 // allocation is to fail; every library allocator asks before cudaMalloc.
 bool injected_alloc_failure();
 
-// Shared with the allocation-free entry point (fdd_noalloc.cu): the last-error
-// setter and the exact 64-bit fixed-point phase rate frac(m * rate / L) * 2^64.
+// The last-error setter shared by every translation unit (never allocates).
 fdd_status report_error(fdd_status s, const char* message);
-uint64_t fixed64_phase_rate(double m, double rate, double L);
+
+// The plan constants every entry point derives from fdd_params, validated and
+// computed without allocating (fdd_plan, fdd_plan_geometry, fdd_batch_plan
+// per beam, and the allocation-free entry point all use these):
+//   Eq. 1 reference frequency and dispersion constant, the largest delay,
+//   the DM grid, the transform length and the overlap-save chunking
+//   (Sect. 2.2 discard rule, Sect. 3 zero padding), down-sampling.
+struct CoreGeometry {
+  double nu_ref;     // Eq. 1 reference frequency nu_0, MHz
+  double k_dm;       // dispersion constant in use, MHz^2 pc^-1 cm^3 s
+  double rate_max;   // largest delay per unit DM over the channels, samples
+  double dm0, ddm;   // first trial and step of the list
+  int uniform;       // 1 when the list is an arithmetic progression
+  int downsample;    // factor of the shortened inverse transform (1: none)
+  int64_t d_max;     // ceil of the largest delay, samples
+  int64_t L, n_bins, hop, n_chunks, out_len, valid_len;
+};
+fdd_status core_geometry(const fdd_params* p, CoreGeometry* out);
+// Eq. 1: the delay of channel c per unit DM, in samples.
+double delay_rate(const fdd_params& p, const CoreGeometry& g, int c);
+// The exact fixed-point phase constants of a channel with delay rate `rate`
+// (samples per unit DM) for transform length L and the trial grid dm0 + j ddm.
+PhaseConst phase_const(double rate, double L, double dm0, double ddm);
 
 // Unpack / transpose / chunk / zero-pad (Sect. 3: transpose_and_unpack and
 // zero_pad of Algorithm 1) of one beam into channel-major float series.

@@ -24,22 +24,15 @@
 // FP32 FMAs per complex multiply-accumulate, the FP32-pipe minimum for 8
 // flops.
 //
-// Three arithmetic forms share this structure:
-//  * scalar: single FFMAs; Z and P are swapped as (re, im) pairs;
-//  * packed: Blackwell's paired FMA (__ffma2_rn, two FMAs per issued
-//    instruction at the single-FMA pipe rate), pairs running along b:
-//      re[a][b:b+2] += (zr, zr)(pr_b, pr_b+1) + (zi, zi)(-pi_b, -pi_b+1)
-//      im[a][b:b+2] += (zr, zr)(pi_b, pi_b+1) + (zi, zi)(pr_b, pr_b+1)
-//    with Z swapped as (zr, zr, zi, zi) quads and P as planes pr, pi, -pi;
-//  * packed-compact: the same MAC with Z swapped as (zr, zi) pairs and P as
-//    planes pr, pi, the broadcast pairs being formed in registers.
-// and two schedules:
-//  * plain:     per channel c: generate(c) -> sync -> load(c) -> MAC(c);
-//  * pipelined: per channel c: load(c) -> generate(c+1) -> MAC(c) -> sync,
-//    so the sin/cos and shared-memory latencies of the generation overlap
-//    the independent FMAs of the previous channel.  Two swap stages suffice:
-//    generate(c+1) writes the stage last read by load(c-1), which every lane
-//    finished before the sync that closed channel c-1.
+// The arithmetic uses Blackwell's paired FMA (__ffma2_rn: two FMAs per issued
+// instruction at the single-FMA pipe rate), pairs running along b:
+//   re[a][b:b+2] += (zr, zr)(pr_b, pr_b+1) + (-zi, -zi)(pi_b, pi_b+1)
+//   im[a][b:b+2] += (zr, zr)(pi_b, pi_b+1) + (zi, zi)(pr_b, pr_b+1)
+// with Z swapped as (zr, zi) pairs and P as planes pr, pi; the broadcast
+// pairs are formed in registers.  Two schedules share it: the plain one
+// (every warp evaluates its phasors, synchronises, loads and accumulates,
+// per channel), used by the smaller tiles, and the warp-specialised one
+// below, used by the 2048-trial tile.
 // Lanes are numbered lane = ga * GB + gb, so each quarter warp reads a single
 // Z row (a broadcast) and GB distinct P rows; the P rows are padded so that
 // those reads fall in distinct shared-memory banks.
@@ -53,9 +46,7 @@ using dev::top32_mul;
 using dev::unit_phasor;
 
 constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
 constexpr int kUnroll = 4;  // channels per unrolled group (X loads run one group ahead)
-constexpr int kPrefetch = kUnroll;
 
 template <int AT_, int BT_, int GA_, int GB_>
 struct Geom {
@@ -78,151 +69,9 @@ using G4x8 = Geom<4, 8, 4, 8>;  // 16 x 64 = 1024
 using G4x4 = Geom<4, 4, 2, 4>;  //  8 x 16 =  128, four bins per warp
 using G8x8q = Geom<8, 8, 2, 4>; // 16 x 32 =  512, four bins per warp
 
-// ----------------------------------------------------------------- scalar form
-template <class Gm>
-struct Scalar {
-  static constexpr int AT = Gm::AT, BT = Gm::BT;
-  static constexpr int ZROW = 2 * AT + 4;  // a-rows and b-rows padded by 16 bytes, so the
-  static constexpr int PROW = 2 * BT + 4;  // rows read by one load start in distinct banks
-  static constexpr int ZFL = Gm::GA * ZROW;
-  static constexpr int GFL = ZFL + Gm::GB * PROW;  // floats per group per stage
-  static_assert(AT % 2 == 0 && BT % 2 == 0, "rows are read as float4");
-
-  struct Ops {
-    float zr[AT], zi[AT], pr[BT], pi[BT];
-  };
-  struct Acc {
-    float re[AT][BT], im[AT][BT];
-  };
-  static __device__ __forceinline__ void zero(Acc& c) {
-#pragma unroll
-    for (int i = 0; i < AT; ++i)
-#pragma unroll
-      for (int j = 0; j < BT; ++j) c.re[i][j] = c.im[i][j] = 0.f;
-  }
-  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 2 * (a % AT); }
-  static __device__ __forceinline__ int p_off(int b) {
-    return ZFL + (b / BT) * PROW + 2 * (b % BT);
-  }
-  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
-    *reinterpret_cast<float2*>(grp + off) = make_float2(zr, zi);
-  }
-  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
-    *reinterpret_cast<float2*>(grp + off) = make_float2(pr, pi);
-  }
-  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
-    const float4* z = reinterpret_cast<const float4*>(grp + ga * ZROW);
-    const float4* p = reinterpret_cast<const float4*>(grp + ZFL + gb * PROW);
-#pragma unroll
-    for (int h = 0; h < AT / 2; ++h) {
-      const float4 v = z[h];
-      o.zr[2 * h] = v.x;
-      o.zi[2 * h] = v.y;
-      o.zr[2 * h + 1] = v.z;
-      o.zi[2 * h + 1] = v.w;
-    }
-#pragma unroll
-    for (int h = 0; h < BT / 2; ++h) {
-      const float4 v = p[h];
-      o.pr[2 * h] = v.x;
-      o.pi[2 * h] = v.y;
-      o.pr[2 * h + 1] = v.z;
-      o.pi[2 * h + 1] = v.w;
-    }
-  }
-  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
-#pragma unroll
-    for (int i = 0; i < AT; ++i)
-#pragma unroll
-      for (int j = 0; j < BT; ++j) {
-        c.re[i][j] = fmaf(o.zr[i], o.pr[j], c.re[i][j]);
-        c.re[i][j] = fmaf(-o.zi[i], o.pi[j], c.re[i][j]);
-        c.im[i][j] = fmaf(o.zr[i], o.pi[j], c.im[i][j]);
-        c.im[i][j] = fmaf(o.zi[i], o.pr[j], c.im[i][j]);
-      }
-  }
-  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
-    return make_float2(c.re[i][j], c.im[i][j]);
-  }
-};
-
-// ----------------------------------------------------------------- packed form
-template <class Gm>
-struct Packed {
-  static constexpr int AT = Gm::AT, BT = Gm::BT;
-  static constexpr int ZROW = 4 * (AT + 1);  // floats per a-row: AT quads + one of padding
-  static constexpr int PSTR = BT + 4;        // floats per b-row of a plane
-  static constexpr int ZFL = Gm::GA * ZROW;
-  static constexpr int PFL = Gm::GB * PSTR;  // floats per plane
-  static constexpr int GFL = ZFL + 3 * PFL;
-  static_assert(BT % 4 == 0, "plane rows are read as float4");
-
-  struct Ops {
-    float2 pr[BT / 2], pi[BT / 2], pn[BT / 2];
-    const float4* zq;  // the lane's Z quads, read inside the MAC
-  };
-  struct Acc {
-    float2 re[AT][BT / 2], im[AT][BT / 2];
-  };
-  static __device__ __forceinline__ void zero(Acc& c) {
-#pragma unroll
-    for (int i = 0; i < AT; ++i)
-#pragma unroll
-      for (int j = 0; j < BT / 2; ++j) c.re[i][j] = c.im[i][j] = make_float2(0.f, 0.f);
-  }
-  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 4 * (a % AT); }
-  static __device__ __forceinline__ int p_off(int b) { return ZFL + (b / BT) * PSTR + (b % BT); }
-  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
-    *reinterpret_cast<float4*>(grp + off) = make_float4(zr, zr, zi, zi);
-  }
-  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
-    grp[off] = pr;
-    grp[off + PFL] = pi;
-    grp[off + 2 * PFL] = -pi;
-  }
-  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
-    const float* row = grp + ZFL + gb * PSTR;
-#pragma unroll
-    for (int h = 0; h < BT / 4; ++h) {
-      const float4 r = *reinterpret_cast<const float4*>(row + 4 * h);
-      const float4 i = *reinterpret_cast<const float4*>(row + PFL + 4 * h);
-      const float4 n = *reinterpret_cast<const float4*>(row + 2 * PFL + 4 * h);
-      o.pr[2 * h] = make_float2(r.x, r.y);
-      o.pr[2 * h + 1] = make_float2(r.z, r.w);
-      o.pi[2 * h] = make_float2(i.x, i.y);
-      o.pi[2 * h + 1] = make_float2(i.z, i.w);
-      o.pn[2 * h] = make_float2(n.x, n.y);
-      o.pn[2 * h + 1] = make_float2(n.z, n.w);
-    }
-    o.zq = reinterpret_cast<const float4*>(grp + ga * ZROW);
-  }
-  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
-#pragma unroll
-    for (int i = 0; i < AT; ++i) {
-      const float4 z = o.zq[i];
-      const float2 zr = make_float2(z.x, z.y), zi = make_float2(z.z, z.w);
-#pragma unroll
-      for (int j = 0; j < BT / 2; ++j) {
-        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
-        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
-      }
-#pragma unroll
-      for (int j = 0; j < BT / 2; ++j) {
-        c.re[i][j] = __ffma2_rn(zi, o.pn[j], c.re[i][j]);
-        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
-      }
-    }
-  }
-  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
-    const float2 r = c.re[i][j / 2], m = c.im[i][j / 2];
-    return (j & 1) ? make_float2(r.y, m.y) : make_float2(r.x, m.x);
-  }
-};
-
-// ------------------------------------------------- packed form, compact swap
-// Z swapped as (zr, zi) pairs and P as planes pr, pi (the scalar form's
-// shared-memory volume); the broadcast pairs (zr, zr), (zi, zi), (-zi, -zi)
-// are formed in registers.
+// ------------------------------------------------- paired-FMA tile, compact swap
+// Z swapped as (zr, zi) pairs and P as planes pr, pi; the broadcast pairs
+// (zr, zr), (zi, zi), (-zi, -zi) are formed in registers.
 template <class Gm>
 struct PackedCompact {
   static constexpr int AT = Gm::AT, BT = Gm::BT;
@@ -300,111 +149,6 @@ struct PackedCompact {
   }
 };
 
-// ------------------------------------------- packed form, Z quads, P planes
-// Z swapped as pre-broadcast quads (zr, zr, zi, zi), so the paired FMAs take
-// their Z operands straight from the loaded registers; P as planes pr, pi;
-// the -zi pair is the negated (zi, zi) operand.  One quad is read per a row
-// inside the MAC, which keeps the register count of the compact form.
-template <class Gm>
-struct PackedZQuad {
-  static constexpr int AT = Gm::AT, BT = Gm::BT;
-  static constexpr int ZROW = 4 * AT + 4;   // padded a-rows of quads
-  static constexpr int PSTR = BT + 4;       // padded b-rows of a plane
-  static constexpr int ZFL = Gm::GA * ZROW;
-  static constexpr int PFL = Gm::GB * PSTR;
-  static constexpr int GFL = ZFL + 2 * PFL;
-  static_assert(BT % 4 == 0, "plane rows are read as float4");
-
-  struct Ops {
-    float2 pr[BT / 2], pi[BT / 2];
-    const float4* zq;
-  };
-  struct Acc {
-    float2 re[AT][BT / 2], im[AT][BT / 2];
-  };
-  static __device__ __forceinline__ void zero(Acc& c) {
-#pragma unroll
-    for (int i = 0; i < AT; ++i)
-#pragma unroll
-      for (int j = 0; j < BT / 2; ++j) c.re[i][j] = c.im[i][j] = make_float2(0.f, 0.f);
-  }
-  static __device__ __forceinline__ int z_off(int a) { return (a / AT) * ZROW + 4 * (a % AT); }
-  static __device__ __forceinline__ int p_off(int b) { return ZFL + (b / BT) * PSTR + (b % BT); }
-  static __device__ __forceinline__ void put_z(float* grp, int off, float zr, float zi) {
-    *reinterpret_cast<float4*>(grp + off) = make_float4(zr, zr, zi, zi);
-  }
-  static __device__ __forceinline__ void put_p(float* grp, int off, float pr, float pi) {
-    grp[off] = pr;
-    grp[off + PFL] = pi;
-  }
-  static __device__ __forceinline__ void load(const float* grp, int ga, int gb, Ops& o) {
-    const float* row = grp + ZFL + gb * PSTR;
-#pragma unroll
-    for (int h = 0; h < BT / 4; ++h) {
-      const float4 r = *reinterpret_cast<const float4*>(row + 4 * h);
-      const float4 i = *reinterpret_cast<const float4*>(row + PFL + 4 * h);
-      o.pr[2 * h] = make_float2(r.x, r.y);
-      o.pr[2 * h + 1] = make_float2(r.z, r.w);
-      o.pi[2 * h] = make_float2(i.x, i.y);
-      o.pi[2 * h + 1] = make_float2(i.z, i.w);
-    }
-    o.zq = reinterpret_cast<const float4*>(grp + ga * ZROW);
-  }
-  static __device__ __forceinline__ void mac(Acc& c, const Ops& o) {
-#pragma unroll
-    for (int i = 0; i < AT; ++i) {
-      const float4 z = o.zq[i];
-      const float2 zr = make_float2(z.x, z.y), zi = make_float2(z.z, z.w);
-      const float2 zn = make_float2(-z.z, -z.w);
-#pragma unroll
-      for (int j = 0; j < BT / 2; ++j) {
-        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
-        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
-      }
-#pragma unroll
-      for (int j = 0; j < BT / 2; ++j) {
-        c.re[i][j] = __ffma2_rn(zn, o.pi[j], c.re[i][j]);
-        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
-      }
-    }
-  }
-  static __device__ __forceinline__ float2 get(const Acc& c, int i, int j) {
-    const float2 r = c.re[i][j / 2], m = c.im[i][j / 2];
-    return (j & 1) ? make_float2(r.y, m.y) : make_float2(r.x, m.x);
-  }
-};
-
-// Same as PackedCompact with the MAC in two passes over the whole tile (all
-// zr terms, then all zi terms), so the two updates of an accumulator pair are
-// a full pass apart.
-template <class Gm>
-struct PackedCompact2 : PackedCompact<Gm> {
-  typedef PackedCompact<Gm> B;
-  static __device__ __forceinline__ void mac(typename B::Acc& c, const typename B::Ops& o) {
-#pragma unroll
-    for (int i = 0; i < B::AT; ++i) {
-      const float2 zr = make_float2(o.zr[i], o.zr[i]);
-#pragma unroll
-      for (int j = 0; j < B::BT / 2; ++j) {
-        c.re[i][j] = __ffma2_rn(zr, o.pr[j], c.re[i][j]);
-        c.im[i][j] = __ffma2_rn(zr, o.pi[j], c.im[i][j]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < B::AT; ++i) {
-      const float2 zi = make_float2(o.zi[i], o.zi[i]);
-      const float2 zn = make_float2(-o.zi[i], -o.zi[i]);
-#pragma unroll
-      for (int j = 0; j < B::BT / 2; ++j) {
-        c.re[i][j] = __ffma2_rn(zn, o.pi[j], c.re[i][j]);
-        c.im[i][j] = __ffma2_rn(zi, o.pr[j], c.im[i][j]);
-      }
-    }
-  }
-};
-
-// This lane's share of the phasor evaluation for one channel: Z_a = X Q_a for
-// a = lg + q G and P_b for b = lg + q G, written into the group's swap stage.
 template <class Gm, class M>
 struct Generator {
   uint32_t mz[Gm::ZGEN], mp[Gm::PGEN];
@@ -451,7 +195,7 @@ struct Generator {
 // One CTA's block of work: bins (bin_tile * W + warp) * NG + g and trials
 // dm_block * DMS + .. of one set of spectra, with the phase table already in
 // shared memory (pcs) and the swap area behind it.
-template <class Gm, class M, bool kPipe, int W>
+template <class Gm, class M, int W>
 __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pcs,
                                           float* swap_all, int bin_tile, int dm_block,
                                           int series) {
@@ -476,31 +220,22 @@ __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pc
 
   const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
   const int64_t xs = a.x_chan_stride;
-  // The generation of channel c uses X[c]; the pipelined schedule runs it one
-  // channel ahead, so a group of kUnroll iterations starting at c0 consumes
-  // X[c0 + off .. c0 + off + kUnroll).
-  constexpr int off = kPipe ? 1 : 0;
-
   typename M::Acc acc;
   M::zero(acc);
 
-  if (kPipe) {
-    gen.run(pcs[0], __ldg(xp), grp0);
-    __syncwarp();
-  }
   float2 xcur[kUnroll];
 #pragma unroll
-  for (int i = 0; i < kUnroll; ++i) {
-    const int c = off + i;
-    xcur[i] = (c < nc) ? __ldg(xp + c * xs) : make_float2(0.f, 0.f);
-  }
+  for (int i = 0; i < kUnroll; ++i) xcur[i] = (i < nc) ? __ldg(xp + i * xs) : make_float2(0.f, 0.f);
 
+  // per channel c: generate(c) -> sync -> load(c) -> MAC(c); two swap stages,
+  // so generate(c + 1) writes the stage that load(c - 1) read before the sync
+  // that closed channel c.
   int stage = 0;
   for (int c0 = 0; c0 < nc; c0 += kUnroll) {
     float2 xnext[kUnroll];
 #pragma unroll
     for (int i = 0; i < kUnroll; ++i) {
-      const int c = c0 + kUnroll + off + i;
+      const int c = c0 + kUnroll + i;
       xnext[i] = (c < nc) ? __ldg(xp + c * xs) : make_float2(0.f, 0.f);
     }
 #pragma unroll
@@ -508,19 +243,11 @@ __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pc
       const int c = c0 + i;
       if (c < nc) {
         float* cur = grp0 + stage * kStage;
-        float* nxt = grp0 + (stage ^ 1) * kStage;
         typename M::Ops ops;
-        if (kPipe) {
-          M::load(cur, ga, gb, ops);
-          if (c + 1 < nc) gen.run(pcs[c + 1], xcur[i], nxt);
-          M::mac(acc, ops);
-          __syncwarp();
-        } else {
-          gen.run(pcs[c], xcur[i], cur);
-          __syncwarp();
-          M::load(cur, ga, gb, ops);
-          M::mac(acc, ops);
-        }
+        gen.run(pcs[c], xcur[i], cur);
+        __syncwarp();
+        M::load(cur, ga, gb, ops);
+        M::mac(acc, ops);
         stage ^= 1;
       }
     }
@@ -550,18 +277,18 @@ __device__ __forceinline__ void mac_block(const MacArgs& a, const PhaseConst* pc
   }
 }
 
-template <class Gm, class M, bool kPipe, int W = kWarps>
+template <class Gm, class M, int W = kWarps>
 __global__ void __launch_bounds__(W * 32, 1) mac_kernel(const MacArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
   float* swap_all = reinterpret_cast<float*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
   for (int i = threadIdx.x; i < a.n_chan; i += W * 32) pcs[i] = a.pc[i];
   __syncthreads();
-  mac_block<Gm, M, kPipe, W>(a, pcs, swap_all, blockIdx.x, blockIdx.y, blockIdx.z);
+  mac_block<Gm, M, W>(a, pcs, swap_all, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // --------------------------------------------- warp-specialised schedule
-// The plain and pipelined schedules make every warp alternate between the
+// The plain schedule makes every warp alternate between the
 // latency-bound phasor evaluation (integer phase, MUFU sin/cos, the swap) and
 // its block of paired FMAs; with three warps per scheduler the FMA pipe idles
 // whenever all of them are evaluating.  Here the two jobs go to different
@@ -792,7 +519,7 @@ __global__ void __launch_bounds__((kCons + kProd) * 32, 1)
 // form): CTAs pull work items (set, bin tile, trial block) from a global
 // counter; a set's phase table is loaded into shared memory when the set
 // changes.  Items of a set are numbered bin-tile-major from item_begin.
-template <class Gm, class M, bool kPipe, int W = kWarps>
+template <class Gm, class M, int W = kWarps>
 __global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* sets, int n_sets,
                                                               int64_t n_items,
                                                               unsigned long long* counter) {
@@ -820,184 +547,9 @@ __global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* se
       cur = lo;
     }
     const long long local = item - bs.item_begin;
-    mac_block<Gm, M, kPipe, W>(bs.args, pcs, swap_all, static_cast<int>(local / bs.n_dm_blocks),
+    mac_block<Gm, M, W>(bs.args, pcs, swap_all, static_cast<int>(local / bs.n_dm_blocks),
                                static_cast<int>(local % bs.n_dm_blocks), 0);
     __syncthreads();
-  }
-}
-
-// ----------------------------------------------------------------- reference
-// The first scalar kernel, kept verbatim as a timing reference: one warp-level
-// swap in float2 units and four consecutive FFMAs per register-tile element.
-template <int AT_, int BT_, int GA_, int GB_>
-struct LegacyTile {
-  static constexpr int AT = AT_;            // Q_a values per lane
-  static constexpr int BT = BT_;            // P_b values per lane
-  static constexpr int GA = GA_;            // lanes along a in a bin group
-  static constexpr int GB = GB_;            // lanes along b in a bin group
-  static constexpr int G = GA * GB;         // lanes per bin group
-  static constexpr int NG = 32 / G;         // bin groups per warp
-  static constexpr int AW = GA * AT;        // A: super-steps of the trial block
-  static constexpr int TW = GB * BT;        // T: sub-steps of the trial block
-  static constexpr int DMS = AW * TW;       // trials per block
-  static constexpr int ZROW = AT + 2;       // padded rows (float2) of the swap area
-  static constexpr int PROW = BT + 2;
-  static constexpr int ZSZ = GA * ZROW;     // float2 per group per stage
-  static constexpr int PSZ = GB * PROW;
-  static constexpr int GSZ = ZSZ + PSZ;
-  static constexpr int XCH = NG * GSZ;      // float2 per warp per stage
-  static constexpr int ZGEN = (AW + G - 1) / G;  // Q_a evaluated per lane
-  static constexpr int PGEN = (TW + G - 1) / G;  // P_b evaluated per lane
-  static_assert(32 % G == 0, "bin group must divide a warp");
-  static_assert(AT % 2 == 0 && BT % 2 == 0, "tiles are read as float4 pairs");
-};
-
-using LegacyV8x8 = LegacyTile<8, 8, 4, 8>;  // 32 x 64 = 2048 trials per bin and warp
-
-template <class T>
-__global__ void __launch_bounds__(kThreads, 1) mac_legacy_kernel(const MacArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PhaseConst* pcs = reinterpret_cast<PhaseConst*>(smem_raw);
-  float2* swap_all = reinterpret_cast<float2*>(smem_raw + sizeof(PhaseConst) * a.n_chan);
-
-  for (int i = threadIdx.x; i < a.n_chan; i += kThreads) pcs[i] = a.pc[i];
-  __syncthreads();
-
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / T::G;
-  const int lg = lane % T::G;
-  const int ga = lg / T::GB;
-  const int gb = lg % T::GB;
-  const int k = (blockIdx.x * kWarps + warp) * T::NG + g;  // local bin
-  const bool k_ok = k < a.n_bins;
-  const int kl = k_ok ? k : 0;  // idle groups compute local bin 0, store nothing
-  const uint32_t ku = static_cast<uint32_t>(a.k_begin + kl);
-  const int jblk = blockIdx.y * T::DMS;
-  const int series = blockIdx.z;
-
-  float2* swap0 = swap_all + warp * 2 * T::XCH + g * T::GSZ;
-
-  // Generation duties of this lane: Q_a for a = lg + q G, P_b for b = lg + q G.
-  uint32_t mz[T::ZGEN];
-  int zoff[T::ZGEN];
-  bool zon[T::ZGEN];
-#pragma unroll
-  for (int q = 0; q < T::ZGEN; ++q) {
-    const int ai = lg + q * T::G;
-    zon[q] = ai < T::AW;
-    mz[q] = ku * static_cast<uint32_t>(a.j_begin + jblk + ai * T::TW);
-    zoff[q] = (ai / T::AT) * T::ZROW + (ai % T::AT);
-  }
-  uint32_t mp[T::PGEN];
-  int poff[T::PGEN];
-  bool pon[T::PGEN];
-#pragma unroll
-  for (int q = 0; q < T::PGEN; ++q) {
-    const int bi = lg + q * T::G;
-    pon[q] = bi < T::TW;
-    mp[q] = ku * static_cast<uint32_t>(bi);
-    poff[q] = T::ZSZ + (bi / T::BT) * T::PROW + (bi % T::BT);
-  }
-
-  const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
-  const int64_t xs = a.x_chan_stride;
-
-  float acc_re[T::AT][T::BT];
-  float acc_im[T::AT][T::BT];
-#pragma unroll
-  for (int i = 0; i < T::AT; ++i)
-#pragma unroll
-    for (int j = 0; j < T::BT; ++j) {
-      acc_re[i][j] = 0.f;
-      acc_im[i][j] = 0.f;
-    }
-
-  float2 xnext[kPrefetch];
-#pragma unroll
-  for (int i = 0; i < kPrefetch; ++i)
-    xnext[i] = (i < a.n_chan) ? __ldg(xp + i * xs) : make_float2(0.f, 0.f);
-
-  int stage = 0;
-  for (int c0 = 0; c0 < a.n_chan; c0 += kPrefetch) {
-    float2 xcur[kPrefetch];
-#pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) {
-      xcur[i] = xnext[i];
-      const int cn = c0 + kPrefetch + i;
-      xnext[i] = (cn < a.n_chan) ? __ldg(xp + cn * xs) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) {
-      const int c = c0 + i;
-      if (c < a.n_chan) {
-        const PhaseConst p = pcs[c];
-        const uint32_t base = top32_mul(ku, p.u_lo, p.u_hi);
-        float2* buf = swap0 + stage * T::XCH;
-#pragma unroll
-        for (int q = 0; q < T::ZGEN; ++q) {
-          if (zon[q]) {
-            const float2 w = unit_phasor(base + top32_mul(mz[q], p.v_lo, p.v_hi));
-            const float2 x = xcur[i];
-            buf[zoff[q]] = make_float2(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < T::PGEN; ++q)
-          if (pon[q]) buf[poff[q]] = unit_phasor(top32_mul(mp[q], p.v_lo, p.v_hi));
-        __syncwarp();
-
-        float zr[T::AT], zi[T::AT], pr[T::BT], pi[T::BT];
-        const float4* zrow = reinterpret_cast<const float4*>(buf + ga * T::ZROW);
-        const float4* prow = reinterpret_cast<const float4*>(buf + T::ZSZ + gb * T::PROW);
-#pragma unroll
-        for (int h = 0; h < T::AT / 2; ++h) {
-          const float4 v = zrow[h];
-          zr[2 * h] = v.x;
-          zi[2 * h] = v.y;
-          zr[2 * h + 1] = v.z;
-          zi[2 * h + 1] = v.w;
-        }
-#pragma unroll
-        for (int h = 0; h < T::BT / 2; ++h) {
-          const float4 v = prow[h];
-          pr[2 * h] = v.x;
-          pi[2 * h] = v.y;
-          pr[2 * h + 1] = v.z;
-          pi[2 * h + 1] = v.w;
-        }
-#pragma unroll
-        for (int ii = 0; ii < T::AT; ++ii)
-#pragma unroll
-          for (int jj = 0; jj < T::BT; ++jj) {
-            acc_re[ii][jj] = fmaf(zr[ii], pr[jj], acc_re[ii][jj]);
-            acc_re[ii][jj] = fmaf(-zi[ii], pi[jj], acc_re[ii][jj]);
-            acc_im[ii][jj] = fmaf(zr[ii], pi[jj], acc_im[ii][jj]);
-            acc_im[ii][jj] = fmaf(zi[ii], pr[jj], acc_im[ii][jj]);
-          }
-        stage ^= 1;
-      }
-    }
-  }
-
-  if (!k_ok) return;
-  const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
-#pragma unroll
-  for (int ii = 0; ii < T::AT; ++ii) {
-#pragma unroll
-    for (int jj = 0; jj < T::BT; ++jj) {
-      const int jl = jblk + (ga * T::AT + ii) * T::TW + gb * T::BT + jj;
-      if (jl < a.n_dm) {
-        const float re = acc_re[ii][jj] * a.scale;
-        const float im = real_only ? 0.f : acc_im[ii][jj] * a.scale;
-        const int64_t off = static_cast<int64_t>(series) * a.y_series_stride +
-                            static_cast<int64_t>(jl) * a.y_dm_stride + k;
-        if (a.out_kind == 2)
-          static_cast<float*>(a.Y)[off] = re * re + im * im;
-        else
-          static_cast<float2*>(a.Y)[off] = make_float2(re, im);
-      }
-    }
   }
 }
 
@@ -1013,16 +565,11 @@ struct VariantInfo {
   int bins() const { return (bin_warps ? bin_warps : warps) * ng; }
 };
 
-VariantInfo info_legacy() {
-  return {reinterpret_cast<const void*>(&mac_legacy_kernel<LegacyV8x8>), LegacyV8x8::DMS,
-          LegacyV8x8::NG, sizeof(float2) * static_cast<size_t>(kWarps) * 2 * LegacyV8x8::XCH};
-}
-
-template <class Gm, class M, bool kPipe, int W = kWarps>
+template <class Gm, class M, int W = kWarps>
 VariantInfo info() {
-  return {reinterpret_cast<const void*>(&mac_kernel<Gm, M, kPipe, W>), Gm::DMS, Gm::NG,
+  return {reinterpret_cast<const void*>(&mac_kernel<Gm, M, W>), Gm::DMS, Gm::NG,
           sizeof(float) * static_cast<size_t>(W) * 2 * Gm::NG * M::GFL, W,
-          reinterpret_cast<const void*>(&mac_batch_kernel<Gm, M, kPipe, W>)};
+          reinterpret_cast<const void*>(&mac_batch_kernel<Gm, M, W>)};
 }
 
 template <class Gm, class M, int kCons, int kProd, int kCh = 4, int kSt = 3>
@@ -1037,23 +584,11 @@ VariantInfo info_ws() {
 
 VariantInfo variant_info(int v) {
   switch (v) {
-    case MAC_S_8x8: return info<G8x8, Scalar<G8x8>, false>();
-    case MAC_S_4x8: return info<G4x8, Scalar<G4x8>, false>();
-    case MAC_S_4x4: return info<G4x4, Scalar<G4x4>, false>();
-    case MAC_Q_8x8: return info<G8x8, PackedCompact<G8x8>, false>();
-    case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>, false>();
-    case MAC_Q_4x4: return info<G4x4, PackedCompact<G4x4>, false>();
-    case MAC_P_8x8: return info<G8x8, Packed<G8x8>, false>();
-    case MAC_SP_8x8: return info<G8x8, Scalar<G8x8>, true>();
-    case MAC_QP_8x8: return info<G8x8, PackedCompact<G8x8>, true>();
-    case MAC_Q2_8x8: return info<G8x8, PackedCompact2<G8x8>, false>();
-    case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, false, 12>();
-    case MAC_S12_8x8: return info<G8x8, Scalar<G8x8>, false, 12>();
-    case MAC_Z12_8x8: return info<G8x8, PackedZQuad<G8x8>, false, 12>();
-    case MAC_P12_8x8: return info<G8x8, Packed<G8x8>, false, 12>();
-    case MAC_W12_8x8: return info_ws<G8x8, PackedCompact<G8x8>, 8, 4>();
-    case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>, false>();
-    default: return info_legacy();
+    case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, 12>();
+    case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>>();
+    case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>>();
+    case MAC_Q_4x4: return info<G4x4, PackedCompact<G4x4>>();
+    default: return info_ws<G8x8, PackedCompact<G8x8>, 8, 4>();  // MAC_W12_8x8
   }
 }
 
@@ -1063,10 +598,9 @@ VariantInfo variant_info(int v) {
 // trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
 // measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
 // 131073 bins, full blocks): W12_8x8 0.623 (2048-trial blocks), Q_4x8 0.493
-// (1024), Q_8x8_512 0.415 (512), Q_4x4 0.347 (128).  Other tiles measured on
-// the same launch (ms): W12_8x8 43.7, Q12_8x8 49.5, R_8x8 50.3, Q_8x8 52.4,
-// Z12_8x8 52.4, S_8x8 55.6, P_8x8 56.3, SP_8x8 57.8, P12_8x8 63.0; a
-// 512-trial tile of 4x4 lane tiles over 32 lanes of one bin 0.363.
+// (1024), Q_8x8_512 0.415 (512), Q_4x4 0.347 (128).  (Q12_8x8, the 2048-trial
+// tile on the plain schedule, measured 49.5 ms against 43.7 for W12_8x8 on
+// the same launch.)
 int mac_variant_for(int n_dm) {
   struct Tile {
     int variant, block;

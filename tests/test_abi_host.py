@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
     L = ctypes.CDLL(fdd.library_path())
     for name in declared_functions():
         assert hasattr(L, name), name
-    assert fdd.fdd_abi_version() == 1
+    assert fdd.fdd_abi_version() == 2
 
 
 def test_status_strings():

@@ -121,7 +121,7 @@ def test_kernel_dm_subrange_and_large_phases():
         assert rel_l2(Y[:, q], ref[:, q]) <= 4 * FP32_REL_L2, bins[q]
 
 
-@pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_Q_4X4 + 1, fdd.FDD_MAC_R_8X8 + 1,
+@pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_Q_4X4 + 1, fdd.FDD_MAC_Q12_8X8 + 1,
                                      fdd.FDD_MAC_Q_8X8_512 + 1])
 def test_kernel_bin_windows_equal_the_whole_range(variant):
     """A window of bins (absolute phases k_begin + k) gives bit for bit the
