@@ -147,6 +147,9 @@ typedef struct fdd_info {
   int32_t dm_batch;        /* trials per internal batch (bounded by workspace)     */
   int32_t mac_variant;     /* phasor-MAC kernel tile chosen for this plan          */
   int32_t downsample;      /* factor of the shortened inverse transform (1: none)    */
+  int32_t block_dm;        /* trials per output block of the streamed calls        */
+  int64_t stream_bytes;    /* device bytes the first streamed call adds to the plan
+                              (two input windows and two output blocks)           */
 } fdd_info;
 
 /* ABI version of the loaded library (FDD_ABI_VERSION at build time). */
@@ -225,17 +228,88 @@ fdd_status fdd_execute_dm_range(fdd_plan_t plan, const void* d_in, int32_t dm_fi
                                 int32_t n_dm, void* d_out, fdd_stream_t stream);
 
 /*
+ * Streaming: inputs and outputs larger than device memory (Algorithm 1's
+ * per-chunk copies and DM-outer batches, Sect. 3).  The path runs chunk by
+ * chunk; each (beam, chunk) input window passes through a plan-owned ring of
+ * two windows, and the output leaves in blocks through a ring of two output
+ * blocks, so no device buffer is sized by the whole input or output.
+ *
+ * A source fills one input window: samples t_begin .. t_begin + n_samples - 1
+ * (n_samples <= fdd_info.fft_len) of beam `beam`, into d_window, in the
+ * plan's input type and layout restricted to those samples ([n_samples]
+ * [n_chan] time-major, or [n_chan][n_samples] channel-major).  The window's
+ * previous contents may still be read by work queued on `stream` before the
+ * call: work on another stream that writes the window must first wait for
+ * `ready_event` (a cudaEvent_t; NULL when the slot is new).  The source must
+ * order its writes before later work on `stream` (enqueue them there, or make
+ * the stream wait for them).  It returns FDD_OK, or a status that ends the
+ * call.
+ *
+ * A sink receives one output block (its d_data is device memory of the plan):
+ *   FDD_OUT_TIME:    [n_dm][row_pitch] float for one beam (n_beams 1); row r
+ *                    holds samples out_offset .. out_offset + row_len - 1 of
+ *                    trial dm_first + r (the kept samples of this chunk, 1/L
+ *                    scaled; down-sampled when the plan down-samples);
+ *   FDD_OUT_SPECTRA / FDD_OUT_POWER: [n_beams][n_dm][n_bins] complex / float
+ *                    of chunk `chunk` (row_len = row_pitch = n_bins,
+ *                    out_offset 0), for beams beam_first .. + n_beams - 1.
+ * The block is complete for work enqueued on `stream` after the sink is
+ * called.  Its slot is rewritten two blocks later: a sink that reads it on
+ * `stream` needs nothing more; one that reads it on another stream stores in
+ * release_event a cudaEvent_t recorded after those reads, and the library
+ * makes `stream` wait for it before rewriting the slot.  Blocks come
+ * chunk-outer for the tensor-core form, beam-outer for the FP32 form; within
+ * a (beam, chunk) in increasing trial order.
+ */
+typedef struct fdd_block {
+  int32_t beam_first;  /* first beam of the block                                   */
+  int32_t n_beams;     /* beams in the block                                        */
+  int64_t chunk;       /* chunk index                                               */
+  int32_t dm_first;    /* first trial of the block (index into the DM list)         */
+  int32_t n_dm;        /* trials in the block                                       */
+  const void* d_data;  /* the block (device memory owned by the plan)               */
+  int64_t row_len;     /* valid elements per (beam, trial) row                      */
+  int64_t row_pitch;   /* elements between consecutive rows                         */
+  int64_t out_offset;  /* FDD_OUT_TIME: sample index of row element 0 in the whole
+                          output row; 0 otherwise                                    */
+  void* release_event; /* set by the sink (optional): see above; NULL on entry      */
+} fdd_block;
+
+typedef fdd_status (*fdd_source_fn)(void* user, int32_t beam, int64_t t_begin,
+                                    int64_t n_samples, void* d_window, void* ready_event,
+                                    fdd_stream_t stream);
+typedef fdd_status (*fdd_sink_fn)(void* user, fdd_block* block, fdd_stream_t stream);
+
+/*
+ * The whole path for every trial DM with streamed output, and input either
+ * resident on the device (d_in, layout of fdd_execute; source NULL) or
+ * streamed from a source (d_in NULL): the source is called once per (beam,
+ * chunk) window, the sink once per output block; the computation is that of
+ * fdd_execute.  Both callbacks run on the calling thread, inside this call.
+ * The first call allocates the rings (fdd_info.stream_bytes); later calls
+ * reuse them.  Asynchronous on `stream` apart from what the callbacks do.
+ * Errors: as fdd_execute; FDD_ERR_INVALID_ARG (NULL sink, or not exactly one
+ * of d_in and source); FDD_ERR_ALLOC on the first call; a callback's own
+ * status.
+ */
+fdd_status fdd_execute_stream(fdd_plan_t plan, const void* d_in, fdd_source_fn source,
+                              void* source_user, fdd_sink_fn sink, void* sink_user,
+                              fdd_stream_t stream);
+
+/*
  * End-to-end call with HOST buffers: h_in (layout of fdd_execute's d_in) to
- * the device, fdd_execute, and the result back into h_out (layout of d_out).
- * The copies run on two plan-owned streams as a pipeline over (beam, chunk)
- * units: each unit's new input samples go up before it is computed and its
- * output comes back right after, so copies overlap the computation of the
- * neighbouring units.  Events order the copy streams with `stream`: they
- * start after the work already queued on it, and `stream` waits for the last
- * copy, so synchronising `stream` covers the whole call.  Page-locked host
- * buffers make the copies asynchronous (the call returns after enqueueing);
- * both buffers must stay valid until then.  The device staging buffers,
- * streams and events are created on the first call for the plan and reused.
+ * the device, the path, and the result back into h_out (layout of d_out),
+ * streamed as fdd_execute_stream streams: each (beam, chunk) input window
+ * goes up on a plan-owned copy stream into the window ring, and each output
+ * block comes back on a second copy stream, so copies overlap the
+ * computation of the neighbouring windows and blocks and the device holds
+ * only the two rings, whatever the sizes of h_in and h_out.  Events order the
+ * copy streams with `stream`: they start after the work already queued on
+ * it, and `stream` waits for the last copy, so synchronising `stream` covers
+ * the whole call.  Page-locked host buffers make the copies asynchronous
+ * (the call returns after enqueueing); both buffers must stay valid until
+ * then.  The rings, copy streams and events are created on the first
+ * streamed call for the plan and reused.
  * Errors: as fdd_execute, plus FDD_ERR_ALLOC on the first call.
  */
 fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_stream_t stream);

@@ -51,7 +51,8 @@ FDD_MAC_TC = 100
 EXPORTS = [
     "fdd_abi_version", "fdd_status_string", "fdd_last_error", "fdd_params_init",
     "fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute", "fdd_execute_dm_range",
-    "fdd_execute_host", "fdd_dedisperse_spectra", "fdd_profile_enable", "fdd_profile_read",
+    "fdd_execute_host", "fdd_execute_stream", "fdd_dedisperse_spectra", "fdd_profile_enable",
+    "fdd_profile_read",
     "fdd_destroy", "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
     "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins", "fdd_tdd_execute",
     "fdd_debug_stall_test", "fdd_debug_fail_alloc",
@@ -111,10 +112,37 @@ class fdd_info(ctypes.Structure):
         ("dm_batch", ctypes.c_int32),
         ("mac_variant", ctypes.c_int32),
         ("downsample", ctypes.c_int32),
+        ("block_dm", ctypes.c_int32),
+        ("stream_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class fdd_block(ctypes.Structure):
+    _fields_ = [
+        ("beam_first", ctypes.c_int32),
+        ("n_beams", ctypes.c_int32),
+        ("chunk", ctypes.c_int64),
+        ("dm_first", ctypes.c_int32),
+        ("n_dm", ctypes.c_int32),
+        ("d_data", ctypes.c_void_p),
+        ("row_len", ctypes.c_int64),
+        ("row_pitch", ctypes.c_int64),
+        ("out_offset", ctypes.c_int64),
+        ("release_event", ctypes.c_void_p),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+# fdd_source_fn / fdd_sink_fn
+SOURCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+SINK_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(fdd_block),
+                           ctypes.c_void_p)
 
 
 class fdd_profile(ctypes.Structure):
@@ -200,6 +228,7 @@ def lib() -> ctypes.CDLL:
         L.fdd_execute.argtypes = [vp, vp, vp, vp]
         L.fdd_execute_dm_range.argtypes = [vp, vp, i32, i32, vp, vp]
         L.fdd_execute_host.argtypes = [vp, vp, vp, vp]
+        L.fdd_execute_stream.argtypes = [vp, vp, SOURCE_FN, vp, SINK_FN, vp, vp]
         L.fdd_tdd_execute.argtypes = [vp, vp, vp, vp]
         L.fdd_debug_stall_test.argtypes = [vp, vp]
         L.fdd_debug_fail_alloc.argtypes = [i32]
@@ -218,7 +247,8 @@ def lib() -> ctypes.CDLL:
         L.fdd_profile_enable.argtypes = [vp, i32]
         L.fdd_profile_read.argtypes = [vp, ctypes.POINTER(fdd_profile)]
         for name in ["fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute",
-                     "fdd_execute_dm_range", "fdd_execute_host", "fdd_dedisperse_spectra",
+                     "fdd_execute_dm_range", "fdd_execute_host", "fdd_execute_stream",
+                     "fdd_dedisperse_spectra",
                      "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
                      "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
                      "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins",
@@ -226,6 +256,45 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+_cudart = None
+
+
+def cudart() -> ctypes.CDLL:
+    """The CUDA runtime (for raw-pointer copies inside streaming callbacks;
+    the library itself needs nothing from here)."""
+    global _cudart
+    if _cudart is None:
+        home = _build_mod._cuda_home()
+        for name in (os.path.join(home, "lib64", "libcudart.so"), "libcudart.so.13",
+                     "libcudart.so"):
+            try:
+                _cudart = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _cudart is None:
+            raise FddError(-1, "libcudart not found")
+        sz = ctypes.c_size_t
+        vp = ctypes.c_void_p
+        _cudart.cudaMemcpyAsync.argtypes = [vp, vp, sz, ctypes.c_int, vp]
+        _cudart.cudaMemcpy2DAsync.argtypes = [vp, sz, vp, sz, sz, sz, ctypes.c_int, vp]
+    return _cudart
+
+
+def memcpy_async(dst: int, src: int, nbytes: int, stream: int) -> None:
+    """cudaMemcpyAsync with cudaMemcpyDefault (direction from the addresses)."""
+    rc = cudart().cudaMemcpyAsync(dst, src, nbytes, 4, stream)
+    if rc != 0:
+        raise FddError(FDD_ERR_CUDA, f"cudaMemcpyAsync failed ({rc})")
+
+
+def memcpy2d_async(dst: int, dpitch: int, src: int, spitch: int, width: int, height: int,
+                   stream: int) -> None:
+    rc = cudart().cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, 4, stream)
+    if rc != 0:
+        raise FddError(FDD_ERR_CUDA, f"cudaMemcpy2DAsync failed ({rc})")
 
 
 def _check(status: int):
@@ -308,6 +377,42 @@ def fdd_query(plan: int) -> dict:
 
 def fdd_execute(plan: int, d_in, d_out, stream=None) -> None:
     _check(lib().fdd_execute(plan, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+
+def fdd_execute_stream(plan: int, source, sink, stream=None, d_in=None) -> None:
+    """Streamed execute.  Input: ``d_in`` resident on the device (source None),
+    or ``source(beam, t_begin, n_samples, d_window, ready_event, stream)``
+    filling each window (device address d_window; raw CUDA event and stream
+    handles).  Output: ``sink(block, stream)`` for each block, ``block`` a dict
+    of the fdd_block fields; a sink that reads the block on another stream
+    returns the handle of a CUDA event recorded after those reads (else None).
+    An exception in a callback ends the call and is raised here."""
+    err = []
+
+    def _src(_user, beam, t_begin, n, d_window, ready, s):
+        try:
+            source(int(beam), int(t_begin), int(n), int(d_window), ready, s)
+            return FDD_OK
+        except BaseException as e:  # noqa: BLE001 -- re-raised below
+            err.append(e)
+            return FDD_ERR_INVALID_ARG
+
+    def _snk(_user, blk, s):
+        try:
+            ev = sink(blk.contents.as_dict(), s)
+            blk.contents.release_event = ev
+            return FDD_OK
+        except BaseException as e:  # noqa: BLE001 -- re-raised below
+            err.append(e)
+            return FDD_ERR_INVALID_ARG
+
+    c_src = SOURCE_FN(_src) if source is not None else ctypes.cast(None, SOURCE_FN)
+    c_snk = SINK_FN(_snk)
+    status = lib().fdd_execute_stream(plan, _ptr(d_in), c_src, None, c_snk, None,
+                                      _stream(stream))
+    if err:
+        raise err[0]
+    _check(status)
 
 
 def fdd_execute_dm_range(plan: int, d_in, dm_first: int, n_dm: int, d_out, stream=None) -> None:
@@ -448,6 +553,9 @@ class Plan:
 
     def execute_host(self, h_in, h_out, stream=None):
         fdd_execute_host(self.handle, h_in, h_out, stream)
+
+    def execute_stream(self, source, sink, stream=None, d_in=None):
+        fdd_execute_stream(self.handle, source, sink, stream, d_in)
 
     def debug_stall_test(self, stream=None):
         fdd_debug_stall_test(self.handle, stream)

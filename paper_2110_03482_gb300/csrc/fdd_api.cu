@@ -47,12 +47,20 @@ struct fdd_plan_s {
   cufftHandle r2c = 0, c2r = 0, c2r_tail = 0;
   bool has_r2c = false, has_c2r = false, has_c2r_tail = false;
   int c2r_tail_batch = 0;
-  void* d_in_stage = nullptr;
-  void* d_out_stage = nullptr;
-  // fdd_execute_host: copy streams and the events that order them with the
-  // compute stream (created on its first call)
+  // streamed calls (fdd_execute_stream, fdd_execute_host): rings of two input
+  // windows [n_chan x L] and two output blocks (made on the first such call),
+  // the trials per spectra / power block, and for host buffers the copy
+  // streams and the events that order them with the compute stream
+  void* d_win[2] = {nullptr, nullptr};
+  void* d_blk[2] = {nullptr, nullptr};
+  size_t blk_bytes = 0;
+  int block_dm = 0;
+  unsigned win_next = 0, blk_next = 0;
+  bool win_used[2] = {false, false}, blk_used[2] = {false, false};
+  void* blk_release[2] = {nullptr, nullptr};  // a sink's event per block slot
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  std::vector<cudaEvent_t> pipe_ev;
+  cudaEvent_t win_free[2] = {}, win_full[2] = {}, blk_free[2] = {}, blk_done[2] = {};
+  cudaEvent_t pipe_start = nullptr, pipe_end = nullptr;
   // fdd_tdd_execute: rounded shift tables (relative to each block of trials'
   // smallest, and those smallest) and one beam's channel-major series
   int* d_shift = nullptr;
@@ -378,6 +386,28 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   }
   g->dm_batch = static_cast<int32_t>(batch);
   g->workspace_bytes = static_cast<int64_t>(fixed + per_dm * batch);
+  // Streamed calls: output blocks of one beam's DM batch (time), or of
+  // block_dm trials of every spectra set (spectra, power; whole passes of the
+  // kernel tile, up to 4 GiB or a quarter of workspace_limit, at least one
+  // pass); two input windows of one beam's chunk.
+  const size_t in_esz = p->in_dtype == FDD_IN_U8 ? 1 : 4;
+  size_t blk_bytes;
+  if (p->output == FDD_OUT_TIME) {
+    g->block_dm = g->dm_batch;
+    blk_bytes = sizeof(float) * static_cast<size_t>(batch) * (cg.hop / f);
+  } else {
+    const size_t per_trial = (p->output == FDD_OUT_SPECTRA ? 8 : 4) * spectra_sets *
+                             static_cast<size_t>(n_bins);
+    const int64_t pass = tc ? fdd::mac_tc_trials_per_pass(p->n_beams)
+                            : fdd::mac_variant_trials_per_block(g->mac_variant);
+    const size_t cap = std::min<size_t>(size_t(4) << 30, limit / 4);
+    int64_t bd = static_cast<int64_t>(cap / per_trial) / pass * pass;
+    if (bd < pass) bd = pass;
+    if (bd > p->n_dm) bd = p->n_dm;
+    g->block_dm = static_cast<int32_t>(bd);
+    blk_bytes = per_trial * static_cast<size_t>(bd);
+  }
+  g->stream_bytes = static_cast<int64_t>(2 * blk_bytes + 2 * in_esz * size_t(nc) * L);
   if (core_out) *core_out = cg;
   return FDD_OK;
 }
@@ -388,13 +418,16 @@ void release(fdd_plan_s* P) {
   if (P->has_c2r) cufftDestroy(P->c2r);
   if (P->has_c2r_tail) cufftDestroy(P->c2r_tail);
   void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_fftwork, P->d_status,
-                  P->d_in_stage, P->d_out_stage, P->d_tcx, P->d_shift, P->d_shift_base,
-                  P->d_tdd_x};
+                  P->d_win[0], P->d_win[1], P->d_blk[0], P->d_blk[1], P->d_tcx, P->d_shift,
+                  P->d_shift_base, P->d_tdd_x};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->prof_ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : P->pipe_ev)
+  cudaEvent_t pipe[] = {P->win_free[0], P->win_free[1], P->win_full[0], P->win_full[1],
+                        P->blk_free[0], P->blk_free[1], P->blk_done[0], P->blk_done[1],
+                        P->pipe_start, P->pipe_end};
+  for (cudaEvent_t e : pipe)
     if (e) cudaEventDestroy(e);
   if (P->h2d) cudaStreamDestroy(P->h2d);
   if (P->d2h) cudaStreamDestroy(P->d2h);
@@ -432,107 +465,202 @@ fdd_status check_device(const fdd_plan_s* P) {
   return FDD_OK;
 }
 
-// Host-buffer execution (fdd_execute_host) as a pipeline: before a (beam,
-// chunk) unit is computed, the input samples it reads that are not on the
-// device yet go up on the h2d stream and the compute stream waits for them;
-// after the unit, the d2h stream waits for it and brings its output back.
-// Copies of one unit thus overlap the computation of its neighbours.
-struct HostPipe {
-  fdd_plan_s* P;
-  const char* h_in;
-  char* h_out;
-  std::vector<int64_t> copied;  // per beam: first input sample not yet sent
-  size_t next_ev = 0;
-
-  cudaEvent_t event() { return P->pipe_ev[next_ev++]; }
-
-  fdd_status before(int b, int64_t c, cudaStream_t s) {
-    const fdd_params& p = P->p;
-    const fdd_info& g = P->info;
-    const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
-    int64_t end = c * g.hop + g.fft_len;
-    if (end > p.n_t) end = p.n_t;
-    if (copied[b] >= end) return FDD_OK;
-    const int64_t t0 = copied[b];
-    const size_t beam_off = esz * static_cast<size_t>(p.n_t) * p.n_chan * b;
-    const char* src = h_in + beam_off;
-    char* dst = static_cast<char*>(P->d_in_stage) + beam_off;
-    if (p.in_layout == FDD_LAYOUT_TIME_MAJOR) {
-      const size_t off = esz * static_cast<size_t>(t0) * p.n_chan;
-      FDD_CUDA(cudaMemcpyAsync(dst + off, src + off, esz * static_cast<size_t>(end - t0) * p.n_chan,
-                               cudaMemcpyHostToDevice, P->h2d));
-    } else {
-      const size_t pitch = esz * static_cast<size_t>(p.n_t);
-      FDD_CUDA(cudaMemcpy2DAsync(dst + esz * t0, pitch, src + esz * t0, pitch,
-                                 esz * static_cast<size_t>(end - t0), p.n_chan,
-                                 cudaMemcpyHostToDevice, P->h2d));
-    }
-    copied[b] = end;
-    cudaEvent_t e = event();
-    FDD_CUDA(cudaEventRecord(e, P->h2d));
-    FDD_CUDA(cudaStreamWaitEvent(s, e, 0));
-    return FDD_OK;
-  }
-
-  // Output of beams b0 .. b0 + nb - 1 for chunk c (the whole DM list).
-  fdd_status after(int b0, int nb, int64_t c, cudaStream_t s) {
-    const fdd_params& p = P->p;
-    const fdd_info& g = P->info;
-    cudaEvent_t e = event();
-    FDD_CUDA(cudaEventRecord(e, s));
-    FDD_CUDA(cudaStreamWaitEvent(P->d2h, e, 0));
-    const char* d_out = static_cast<const char*>(P->d_out_stage);
-    if (p.output == FDD_OUT_TIME) {
-      const int64_t hop_o = g.hop / g.downsample;  // output samples per chunk
-      int64_t keep = g.out_len - c * hop_o;
-      if (keep > hop_o) keep = hop_o;
-      const size_t pitch = sizeof(float) * static_cast<size_t>(g.out_len);
-      const size_t off = sizeof(float) * (static_cast<size_t>(b0) * p.n_dm * g.out_len + c * hop_o);
-      FDD_CUDA(cudaMemcpy2DAsync(h_out + off, pitch, d_out + off, pitch, sizeof(float) * keep,
-                                 static_cast<size_t>(nb) * p.n_dm, cudaMemcpyDeviceToHost,
-                                 P->d2h));
-    } else {
-      const size_t esz = p.output == FDD_OUT_SPECTRA ? 8 : 4;
-      const size_t block = esz * static_cast<size_t>(p.n_dm) * g.n_bins;  // one beam, one chunk
-      const size_t pitch = block * g.n_chunks;                          // between beams
-      const size_t off = pitch * b0 + block * c;
-      FDD_CUDA(cudaMemcpy2DAsync(h_out + off, pitch, d_out + off, pitch, block, nb,
-                                 cudaMemcpyDeviceToHost, P->d2h));
-    }
-    return FDD_OK;
-  }
+// Where a run's input comes from and where its output goes (the copies of
+// Algorithm 1).  fdd_execute: the whole input and output on the device.
+// Otherwise input windows and output blocks pass through plan-owned rings of
+// two slots each: filled by the caller's source and handed to its sink in
+// stream order (fdd_execute_stream), or copied from / to host buffers on the
+// plan's two copy streams (fdd_execute_host), so no device buffer is sized by
+// the whole input or output.
+struct Io {
+  const void* d_in = nullptr;
+  void* d_out = nullptr;
+  fdd_source_fn source = nullptr;
+  void* source_user = nullptr;
+  fdd_sink_fn sink = nullptr;
+  void* sink_user = nullptr;
+  const char* h_in = nullptr;
+  char* h_out = nullptr;
+  bool host() const { return h_in != nullptr; }
+  int dm_first = 0, n_dm = 0;  // the trials of this run
 };
 
-fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
-                  cudaStream_t s, HostPipe* hp);
-
-fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
-               cudaStream_t s, HostPipe* hp = nullptr) {
+// Where the unpack of (beam b, chunk c) reads: into *ua.  Streamed input
+// fills a window slot with samples [c hop, c hop + L) of beam b first.
+fdd_status input_for(fdd_plan_s* P, const Io& io, int b, int64_t c, cudaStream_t s,
+                     fdd::UnpackArgs* ua, int* slot_out) {
   const fdd_params& p = P->p;
   const fdd_info& g = P->info;
   const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
-  const int64_t beam_elems = p.n_t * static_cast<int64_t>(p.n_chan);
+  *slot_out = -1;
+  *ua = fdd::UnpackArgs{nullptr, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop,
+                        g.fft_len, P->d_xw, g.fft_len};
+  if (io.d_in) {
+    ua->in = static_cast<const char*>(io.d_in) + esz * static_cast<size_t>(p.n_t) * p.n_chan * b;
+    return FDD_OK;
+  }
+  const int w = static_cast<int>(P->win_next++ & 1);
+  const int64_t t0 = c * g.hop;
+  const int64_t n = std::min<int64_t>(g.fft_len, p.n_t - t0);
+  void* dst = P->d_win[w];
+  if (io.host()) {
+    if (P->win_used[w]) FDD_CUDA(cudaStreamWaitEvent(P->h2d, P->win_free[w], 0));
+    const char* src = io.h_in + esz * static_cast<size_t>(p.n_t) * p.n_chan * b;
+    if (p.in_layout == FDD_LAYOUT_TIME_MAJOR) {
+      FDD_CUDA(cudaMemcpyAsync(dst, src + esz * static_cast<size_t>(t0) * p.n_chan,
+                               esz * static_cast<size_t>(n) * p.n_chan, cudaMemcpyHostToDevice,
+                               P->h2d));
+    } else {
+      FDD_CUDA(cudaMemcpy2DAsync(dst, esz * static_cast<size_t>(n), src + esz * t0,
+                                 esz * static_cast<size_t>(p.n_t), esz * static_cast<size_t>(n),
+                                 p.n_chan, cudaMemcpyHostToDevice, P->h2d));
+    }
+    FDD_CUDA(cudaEventRecord(P->win_full[w], P->h2d));
+    FDD_CUDA(cudaStreamWaitEvent(s, P->win_full[w], 0));
+  } else {
+    void* ready = P->win_used[w] ? static_cast<void*>(P->win_free[w]) : nullptr;
+    const fdd_status st =
+        io.source(io.source_user, b, t0, n, dst, ready, reinterpret_cast<fdd_stream_t>(s));
+    if (st != FDD_OK) return fail(st, "the input source failed for beam %d, samples %lld..%lld", b,
+                                  (long long)t0, (long long)(t0 + n));
+  }
+  ua->in = dst;
+  ua->n_t = n;
+  ua->t_begin = 0;
+  *slot_out = w;
+  return FDD_OK;
+}
+
+// After the unpack that read window slot w (streamed input): the slot may be
+// refilled once the unpack is done.
+fdd_status input_done(fdd_plan_s* P, const Io& io, int w, cudaStream_t s) {
+  (void)io;
+  if (w < 0) return FDD_OK;
+  FDD_CUDA(cudaEventRecord(P->win_free[w], s));
+  P->win_used[w] = true;
+  return FDD_OK;
+}
+
+// An output block slot for the next block (streamed output); waits until the
+// host copy of its previous block is done.
+fdd_status block_slot(fdd_plan_s* P, const Io& io, cudaStream_t s, int* slot) {
+  const int k = static_cast<int>(P->blk_next++ & 1);
+  if (io.host() && P->blk_used[k]) FDD_CUDA(cudaStreamWaitEvent(s, P->blk_free[k], 0));
+  if (!io.host() && P->blk_release[k]) {  // the sink's reads of the slot's last block
+    FDD_CUDA(cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(P->blk_release[k]), 0));
+    P->blk_release[k] = nullptr;
+  }
+  *slot = k;
+  return FDD_OK;
+}
+
+// Hand a finished block to the sink, or copy it to the host output.
+fdd_status deliver(fdd_plan_s* P, const Io& io, int k, fdd_block& blk, cudaStream_t s) {
+  const fdd_params& p = P->p;
+  const fdd_info& g = P->info;
+  if (!io.host()) {
+    blk.release_event = nullptr;
+    const fdd_status st = io.sink(io.sink_user, &blk, reinterpret_cast<fdd_stream_t>(s));
+    if (st != FDD_OK) return fail(st, "the output sink failed (chunk %lld, trials %d..%d)",
+                                  (long long)blk.chunk, blk.dm_first, blk.dm_first + blk.n_dm);
+    P->blk_release[k] = blk.release_event;
+    return FDD_OK;
+  }
+  FDD_CUDA(cudaEventRecord(P->blk_done[k], s));
+  FDD_CUDA(cudaStreamWaitEvent(P->d2h, P->blk_done[k], 0));
+  const int rel = blk.dm_first - io.dm_first;  // row of the first trial in the output
+  if (p.output == FDD_OUT_TIME) {
+    // rows [beam][trial] of out_len samples; the block holds row_len of them
+    const size_t dst_pitch = sizeof(float) * static_cast<size_t>(g.out_len);
+    for (int q = 0; q < blk.n_beams; ++q) {
+      char* dst = io.h_out + sizeof(float) * ((static_cast<size_t>(blk.beam_first + q) * io.n_dm + rel) *
+                                                  g.out_len + blk.out_offset);
+      const char* src = static_cast<const char*>(blk.d_data) +
+                        sizeof(float) * static_cast<size_t>(q) * blk.n_dm * blk.row_pitch;
+      FDD_CUDA(cudaMemcpy2DAsync(dst, dst_pitch, src, sizeof(float) * blk.row_pitch,
+                                 sizeof(float) * blk.row_len, blk.n_dm, cudaMemcpyDeviceToHost,
+                                 P->d2h));
+    }
+  } else {
+    const size_t esz = p.output == FDD_OUT_SPECTRA ? 8 : 4;
+    const size_t rows_beam = static_cast<size_t>(g.n_chunks) * io.n_dm;  // rows per beam
+    char* dst = io.h_out + esz * ((static_cast<size_t>(blk.beam_first) * rows_beam +
+                                   static_cast<size_t>(blk.chunk) * io.n_dm + rel) *
+                                  g.n_bins);
+    FDD_CUDA(cudaMemcpy2DAsync(dst, esz * rows_beam * g.n_bins, blk.d_data,
+                               esz * static_cast<size_t>(blk.n_dm) * g.n_bins,
+                               esz * static_cast<size_t>(blk.n_dm) * g.n_bins, blk.n_beams,
+                               cudaMemcpyDeviceToHost, P->d2h));
+  }
+  FDD_CUDA(cudaEventRecord(P->blk_free[k], P->d2h));
+  P->blk_used[k] = true;
+  return FDD_OK;
+}
+
+// Unpack + forward transforms of (beam b, chunk c) into spectra X (Eq. 3).
+fdd_status transform(fdd_plan_s* P, const Io& io, int b, int64_t c, float2* X, cudaStream_t s) {
+  fdd::UnpackArgs ua;
+  int w;
+  fdd_status st = input_for(P, io, b, c, s, &ua, &w);
+  if (st != FDD_OK) return st;
+  {
+    StageTimer t(P, FDD_STAGE_UNPACK, s);
+    FDD_CUDA(fdd::launch_unpack(ua, s));
+  }
+  if ((st = input_done(P, io, w, s)) != FDD_OK) return st;
+  StageTimer t(P, FDD_STAGE_R2C, s);
+  FDD_CUFFT(cufftExecR2C(P->r2c, P->d_xw, reinterpret_cast<cufftComplex*>(X)));
+  return FDD_OK;
+}
+
+// The 1/L scaling and valid-sample placement of DM batch [j0, j0 + nb) of
+// beam b, chunk c, from the inverse transforms in d_yt: into the output rows,
+// or into a block handed on.
+fdd_status place_time(fdd_plan_s* P, const Io& io, int b, int64_t c, int j0, int nb,
+                      cudaStream_t s) {
+  const fdd_info& g = P->info;
+  const int64_t Ls = g.fft_len / g.downsample, hop_o = g.hop / g.downsample;
+  const int64_t keep = (g.out_len - c * hop_o) < hop_o ? (g.out_len - c * hop_o) : hop_o;
+  fdd::ScatterArgs sa{};
+  sa.src = P->d_yt;
+  sa.src_stride = Ls;
+  sa.n_dm = nb;
+  sa.n_keep = keep;
+  sa.scale = static_cast<float>(1.0 / static_cast<double>(g.fft_len));
+  int k = -1;
+  if (io.d_out) {
+    sa.dst = static_cast<float*>(io.d_out) +
+             (static_cast<int64_t>(b) * io.n_dm + (j0 - io.dm_first)) * g.out_len + c * hop_o;
+    sa.dst_stride = g.out_len;
+  } else {
+    fdd_status st = block_slot(P, io, s, &k);
+    if (st != FDD_OK) return st;
+    sa.dst = static_cast<float*>(P->d_blk[k]);
+    sa.dst_stride = hop_o;
+  }
+  {
+    StageTimer t(P, FDD_STAGE_SCATTER, s);
+    FDD_CUDA(fdd::launch_scatter(sa, s));
+  }
+  if (k < 0) return FDD_OK;
+  fdd_block blk{b, 1, c, j0, nb, P->d_blk[k], keep, hop_o, c * hop_o, nullptr};
+  return deliver(P, io, k, blk, s);
+}
+
+fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s);
+
+fdd_status run(fdd_plan_s* P, const Io& io, cudaStream_t s) {
+  const fdd_params& p = P->p;
+  const fdd_info& g = P->info;
   FDD_CUFFT(cufftSetStream(P->r2c, s));
   if (P->has_c2r) FDD_CUFFT(cufftSetStream(P->c2r, s));
   if (P->has_c2r_tail) FDD_CUFFT(cufftSetStream(P->c2r_tail, s));
-  if (P->tc) return run_tc(P, d_in, dm_first, n_dm, d_out, s, hp);
-  fdd_status pst;
-
+  if (P->tc) return run_tc(P, io, s);
+  fdd_status st;
+  const int dm_end = io.dm_first + io.n_dm;
   for (int b = 0; b < p.n_beams; ++b) {
-    const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
     for (int64_t c = 0; c < g.n_chunks; ++c) {
-      if (hp && (pst = hp->before(b, c, s)) != FDD_OK) return pst;
-      fdd::UnpackArgs ua{in_b, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop, g.fft_len,
-                         P->d_xw, g.fft_len};
-      {
-        StageTimer t(P, FDD_STAGE_UNPACK, s);
-        FDD_CUDA(fdd::launch_unpack(ua, s));
-      }
-      {
-        StageTimer t(P, FDD_STAGE_R2C, s);
-        FDD_CUFFT(cufftExecR2C(P->r2c, P->d_xw, reinterpret_cast<cufftComplex*>(P->d_X)));
-      }
-
+      if ((st = transform(P, io, b, c, P->d_X, s)) != FDD_OK) return st;
       fdd::MacArgs m{};
       m.X = P->d_X;
       m.x_series_stride = 0;
@@ -545,10 +673,10 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
       m.status = P->d_status;
       if (p.output == FDD_OUT_TIME) {
         // (shortened inverse: only the bins up to Nyquist of length L / f)
-        const int64_t Ls = g.fft_len / g.downsample, hop_o = g.hop / g.downsample;
+        const int64_t Ls = g.fft_len / g.downsample;
         m.n_bins = static_cast<int>(Ls / 2 + 1);
-        for (int j0 = dm_first; j0 < dm_first + n_dm; j0 += g.dm_batch) {
-          const int nb = (dm_first + n_dm - j0) < g.dm_batch ? (dm_first + n_dm - j0) : g.dm_batch;
+        for (int j0 = io.dm_first; j0 < dm_end; j0 += g.dm_batch) {
+          const int nb = (dm_end - j0) < g.dm_batch ? (dm_end - j0) : g.dm_batch;
           m.j_begin = j0;
           m.n_dm = nb;
           m.Y = P->d_Y;
@@ -566,69 +694,56 @@ fdd_status run(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_
             StageTimer t(P, FDD_STAGE_C2R, s);
             FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(P->d_Y), P->d_yt));
           }
-          const int64_t keep = (g.out_len - c * hop_o) < hop_o ? (g.out_len - c * hop_o) : hop_o;
-          fdd::ScatterArgs sa{};
-          sa.src = P->d_yt;
-          sa.src_stride = Ls;
-          sa.dst = static_cast<float*>(d_out) +
-                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * hop_o;
-          sa.dst_stride = g.out_len;
-          sa.n_dm = nb;
-          sa.n_keep = keep;
-          sa.scale = static_cast<float>(1.0 / static_cast<double>(g.fft_len));
-          StageTimer t(P, FDD_STAGE_SCATTER, s);
-          FDD_CUDA(fdd::launch_scatter(sa, s));
+          if ((st = place_time(P, io, b, c, j0, nb, s)) != FDD_OK) return st;
         }
       } else {
-        const int64_t row0 = (static_cast<int64_t>(b) * g.n_chunks + c) * n_dm;
-        m.j_begin = dm_first;
-        m.n_dm = n_dm;
         m.y_series_stride = 0;
         m.y_dm_stride = g.n_bins;
         m.real_bin_a = -1;
         m.real_bin_b = -1;
-        if (p.output == FDD_OUT_SPECTRA) {
-          m.out_kind = 1;
-          m.Y = static_cast<float2*>(d_out) + row0 * g.n_bins;
-        } else {
-          m.out_kind = 2;
-          m.Y = static_cast<float*>(d_out) + row0 * g.n_bins;
+        m.out_kind = p.output == FDD_OUT_SPECTRA ? 1 : 2;
+        const size_t esz = p.output == FDD_OUT_SPECTRA ? 8 : 4;
+        // the whole trial range into the output, or blocks of block_dm trials
+        const int step = io.d_out ? io.n_dm : P->block_dm;
+        for (int j0 = io.dm_first; j0 < dm_end; j0 += step) {
+          const int nb = (dm_end - j0) < step ? (dm_end - j0) : step;
+          m.j_begin = j0;
+          m.n_dm = nb;
+          int k = -1;
+          if (io.d_out) {
+            const int64_t row0 = (static_cast<int64_t>(b) * g.n_chunks + c) * io.n_dm;
+            m.Y = static_cast<char*>(io.d_out) + esz * row0 * g.n_bins;
+          } else {
+            if ((st = block_slot(P, io, s, &k)) != FDD_OK) return st;
+            m.Y = P->d_blk[k];
+          }
+          {
+            StageTimer t(P, FDD_STAGE_MAC, s);
+            FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
+          }
+          if (k >= 0) {
+            fdd_block blk{b, 1, c, j0, nb, P->d_blk[k], g.n_bins, g.n_bins, 0, nullptr};
+            if ((st = deliver(P, io, k, blk, s)) != FDD_OK) return st;
+          }
         }
-        StageTimer t(P, FDD_STAGE_MAC, s);
-        FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
       }
-      if (hp && (pst = hp->after(b, 1, c, s)) != FDD_OK) return pst;
     }
   }
   return FDD_OK;
 }
 
 // Tensor-core form: every beam of a chunk is transformed first, then one
-// launch dedisperses all of them at once (the beams share each bin's phasors).
-fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void* d_out,
-                  cudaStream_t s, HostPipe* hp) {
-  fdd_status pst;
+// launch per DM batch dedisperses all of them at once (the beams share each
+// bin's phasors).
+fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
+  fdd_status st;
   const fdd_params& p = P->p;
   const fdd_info& g = P->info;
-  const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
-  const int64_t beam_elems = p.n_t * static_cast<int64_t>(p.n_chan);
   const int64_t set_elems = static_cast<int64_t>(p.n_chan) * g.bin_pitch;
+  const int dm_end = io.dm_first + io.n_dm;
   for (int64_t c = 0; c < g.n_chunks; ++c) {
-    for (int b = 0; b < p.n_beams; ++b) {
-      if (hp && (pst = hp->before(b, c, s)) != FDD_OK) return pst;
-      const void* in_b = static_cast<const char*>(d_in) + esz * beam_elems * b;
-      fdd::UnpackArgs ua{in_b, p.in_dtype, p.in_layout, p.n_chan, p.n_t, c * g.hop, g.fft_len,
-                         P->d_xw, g.fft_len};
-      {
-        StageTimer t(P, FDD_STAGE_UNPACK, s);
-        FDD_CUDA(fdd::launch_unpack(ua, s));
-      }
-      {
-        StageTimer t(P, FDD_STAGE_R2C, s);
-        FDD_CUFFT(cufftExecR2C(P->r2c, P->d_xw,
-                               reinterpret_cast<cufftComplex*>(P->d_X + set_elems * b)));
-      }
-    }
+    for (int b = 0; b < p.n_beams; ++b)
+      if ((st = transform(P, io, b, c, P->d_X + set_elems * b, s)) != FDD_OK) return st;
     fdd::MacArgs m{};
     m.X = P->d_X;
     m.x_series_stride = set_elems;
@@ -641,66 +756,96 @@ fdd_status run_tc(fdd_plan_s* P, const void* d_in, int dm_first, int n_dm, void*
     m.status = P->d_status;
     if (p.output == FDD_OUT_TIME) {
       // (shortened inverse: only the bins up to Nyquist of length L / f)
-      const int64_t Ls = g.fft_len / g.downsample, hop_o = g.hop / g.downsample;
+      const int64_t Ls = g.fft_len / g.downsample;
       m.n_bins = static_cast<int>(Ls / 2 + 1);
-      for (int j0 = dm_first; j0 < dm_first + n_dm; j0 += g.dm_batch) {
-        const int nb = (dm_first + n_dm - j0) < g.dm_batch ? (dm_first + n_dm - j0) : g.dm_batch;
+      for (int j0 = io.dm_first; j0 < dm_end; j0 += g.dm_batch) {
+        const int nb = (dm_end - j0) < g.dm_batch ? (dm_end - j0) : g.dm_batch;
+        // bin-major [bin][beam][trial] with the trial stride of the matching
+        // inverse-transform plan (trials beyond nb are computed by nobody
+        // and their transforms discarded)
+        const bool tail = P->has_c2r_tail && nb == P->c2r_tail_batch;
+        const int sb = tail ? P->c2r_tail_batch : g.dm_batch;
         m.j_begin = j0;
         m.n_dm = nb;
         m.Y = P->d_Y;
-        m.y_series_stride = static_cast<int64_t>(g.dm_batch) * g.bin_pitch;
-        m.y_dm_stride = g.bin_pitch;
+        m.y_bin_stride = static_cast<int64_t>(p.n_beams) * sb;
+        m.y_series_stride = sb;
+        m.y_dm_stride = 1;
         m.out_kind = 1;
         m.real_bin_a = 0;
         m.real_bin_b = static_cast<int>(Ls / 2);
+        m.absmax_ready = j0 > io.dm_first;  // the spectra's per-bin maxima, found once
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
-          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx,
-                                      P->tcx_bytes, s));
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s));
         }
-        cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
-        const int64_t keep = (g.out_len - c * hop_o) < hop_o ? (g.out_len - c * hop_o) : hop_o;
+        cufftHandle h = tail ? P->c2r_tail : P->c2r;
         for (int b = 0; b < p.n_beams; ++b) {
           {
             StageTimer t(P, FDD_STAGE_C2R, s);
             FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(
-                                          P->d_Y + static_cast<int64_t>(b) * g.dm_batch * g.bin_pitch),
+                                          P->d_Y + static_cast<int64_t>(b) * sb),
                                    P->d_yt));
           }
-          fdd::ScatterArgs sa{};
-          sa.src = P->d_yt;
-          sa.src_stride = Ls;
-          sa.dst = static_cast<float*>(d_out) +
-                   (static_cast<int64_t>(b) * n_dm + (j0 - dm_first)) * g.out_len + c * hop_o;
-          sa.dst_stride = g.out_len;
-          sa.n_dm = nb;
-          sa.n_keep = keep;
-          sa.scale = static_cast<float>(1.0 / static_cast<double>(g.fft_len));
-          StageTimer t(P, FDD_STAGE_SCATTER, s);
-          FDD_CUDA(fdd::launch_scatter(sa, s));
+          if ((st = place_time(P, io, b, c, j0, nb, s)) != FDD_OK) return st;
         }
       }
     } else {
-      m.j_begin = dm_first;
-      m.n_dm = n_dm;
-      m.y_series_stride = g.n_chunks * static_cast<int64_t>(n_dm) * g.n_bins;
-      m.y_dm_stride = g.n_bins;
       m.real_bin_a = -1;
       m.real_bin_b = -1;
-      const int64_t off = c * static_cast<int64_t>(n_dm) * g.n_bins;
-      if (p.output == FDD_OUT_SPECTRA) {
-        m.out_kind = 1;
-        m.Y = static_cast<float2*>(d_out) + off;
-      } else {
-        m.out_kind = 2;
-        m.Y = static_cast<float*>(d_out) + off;
+      m.out_kind = p.output == FDD_OUT_SPECTRA ? 1 : 2;
+      const size_t esz = p.output == FDD_OUT_SPECTRA ? 8 : 4;
+      const int step = io.d_out ? io.n_dm : P->block_dm;
+      for (int j0 = io.dm_first; j0 < dm_end; j0 += step) {
+        const int nb = (dm_end - j0) < step ? (dm_end - j0) : step;
+        m.j_begin = j0;
+        m.n_dm = nb;
+        m.absmax_ready = j0 > io.dm_first;
+        int k = -1;
+        if (io.d_out) {
+          m.y_series_stride = g.n_chunks * static_cast<int64_t>(io.n_dm) * g.n_bins;
+          m.Y = static_cast<char*>(io.d_out) + esz * (c * static_cast<int64_t>(io.n_dm) * g.n_bins);
+        } else {
+          if ((st = block_slot(P, io, s, &k)) != FDD_OK) return st;
+          m.y_series_stride = static_cast<int64_t>(nb) * g.n_bins;
+          m.Y = P->d_blk[k];
+        }
+        m.y_dm_stride = g.n_bins;
+        {
+          StageTimer t(P, FDD_STAGE_MAC, s);
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s));
+        }
+        if (k >= 0) {
+          fdd_block blk{0, p.n_beams, c, j0, nb, P->d_blk[k], g.n_bins, g.n_bins, 0, nullptr};
+          if ((st = deliver(P, io, k, blk, s)) != FDD_OK) return st;
+        }
       }
-      StageTimer t(P, FDD_STAGE_MAC, s);
-      FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx,
-                                      P->tcx_bytes, s));
     }
-    if (hp && (pst = hp->after(0, p.n_beams, c, s)) != FDD_OK) return pst;
   }
+  return FDD_OK;
+}
+
+// The streaming rings (made on the first streamed call): two input windows
+// of n_chan x L samples and two output blocks.
+fdd_status make_rings(fdd_plan_s* P, bool host) {
+  const fdd_params& p = P->p;
+  const fdd_info& g = P->info;
+  fdd_status st;
+  const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
+  for (int w = 0; w < 2; ++w) {
+    if (!P->d_win[w] &&
+        (st = dev_alloc(P, &P->d_win[w], esz * static_cast<size_t>(p.n_chan) * g.fft_len)))
+      return st;
+    if (!P->d_blk[w] && (st = dev_alloc(P, &P->d_blk[w], P->blk_bytes))) return st;
+  }
+  cudaEvent_t* evs[] = {&P->win_free[0], &P->win_free[1], &P->win_full[0], &P->win_full[1],
+                        &P->blk_free[0], &P->blk_free[1], &P->blk_done[0], &P->blk_done[1],
+                        &P->pipe_start, &P->pipe_end};
+  for (cudaEvent_t* e : evs)
+    if (!*e) FDD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  if (!host) return FDD_OK;
+  if (!P->h2d) FDD_CUDA(cudaStreamCreateWithFlags(&P->h2d, cudaStreamNonBlocking));
+  if (!P->d2h) FDD_CUDA(cudaStreamCreateWithFlags(&P->d2h, cudaStreamNonBlocking));
   return FDD_OK;
 }
 
@@ -830,20 +975,31 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
                                 CUFFT_R2C, nc, &w_r2c));
   if (p->output == FDD_OUT_TIME) {
     // inverse transforms of length L / downsample over the first bins of each row
+    // (FP32 form: one beam's DM batch, rows of bin_pitch bins.  Tensor-core
+    // form: the kernel writes the DM batch of every beam bin-major,
+    // [bin][beam][trial], and each beam's inverse reads its trials as
+    // interleaved batches: bin stride n_beams x batch, batch stride 1.)
     long long ns[1] = {g.fft_len / g.downsample};
-    FDD_CUFFT(cufftCreate(&P->c2r));
+    auto make_c2r = [&](cufftHandle* h, int batch, size_t* work) -> fdd_status {
+      FDD_CUFFT(cufftCreate(h));
+      FDD_CUFFT(cufftSetAutoAllocation(*h, 0));
+      if (P->tc) {
+        long long emb_bm[1] = {ns[0] / 2 + 1};
+        FDD_CUFFT(cufftMakePlanMany64(*h, 1, ns, emb_bm, static_cast<long long>(p->n_beams) * batch,
+                                      1, ns, 1, ns[0], CUFFT_C2R, batch, work));
+      } else {
+        FDD_CUFFT(cufftMakePlanMany64(*h, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
+                                      CUFFT_C2R, batch, work));
+      }
+      return FDD_OK;
+    };
     P->has_c2r = true;
-    FDD_CUFFT(cufftSetAutoAllocation(P->c2r, 0));
-    FDD_CUFFT(cufftMakePlanMany64(P->c2r, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
-                                  CUFFT_C2R, g.dm_batch, &w_c2r));
+    if ((st = make_c2r(&P->c2r, g.dm_batch, &w_c2r)) != FDD_OK) return st;
     const int tail = p->n_dm % g.dm_batch;
     if (tail != 0) {
-      FDD_CUFFT(cufftCreate(&P->c2r_tail));
       P->has_c2r_tail = true;
       P->c2r_tail_batch = tail;
-      FDD_CUFFT(cufftSetAutoAllocation(P->c2r_tail, 0));
-      FDD_CUFFT(cufftMakePlanMany64(P->c2r_tail, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
-                                    CUFFT_C2R, tail, &w_tail));
+      if ((st = make_c2r(&P->c2r_tail, tail, &w_tail)) != FDD_OK) return st;
     }
   }
   size_t w = w_r2c > w_c2r ? w_r2c : w_c2r;
@@ -855,6 +1011,11 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
     if (P->has_c2r_tail) FDD_CUFFT(cufftSetWorkArea(P->c2r_tail, P->d_fftwork));
   }
   g.workspace_bytes = static_cast<int64_t>(P->bytes_held);
+  P->block_dm = g.block_dm;
+  P->blk_bytes = p->output == FDD_OUT_TIME
+                     ? sizeof(float) * static_cast<size_t>(g.dm_batch) * (g.hop / g.downsample)
+                     : (p->output == FDD_OUT_SPECTRA ? 8 : 4) * sets *
+                           static_cast<size_t>(g.n_bins) * g.block_dm;
   *out = guard.release();
   return FDD_OK;
 }
@@ -928,12 +1089,39 @@ fdd_status fdd_execute_dm_range(fdd_plan_t plan, const void* d_in, int32_t dm_fi
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
   if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
-  return run(plan, d_in, dm_first, n_dm, d_out, reinterpret_cast<cudaStream_t>(stream));
+  Io io;
+  io.d_in = d_in;
+  io.d_out = d_out;
+  io.dm_first = dm_first;
+  io.n_dm = n_dm;
+  return run(plan, io, reinterpret_cast<cudaStream_t>(stream));
 }
 
 fdd_status fdd_execute(fdd_plan_t plan, const void* d_in, void* d_out, fdd_stream_t stream) {
   if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
   return fdd_execute_dm_range(plan, d_in, 0, plan->p.n_dm, d_out, stream);
+}
+
+fdd_status fdd_execute_stream(fdd_plan_t plan, const void* d_in, fdd_source_fn source,
+                              void* source_user, fdd_sink_fn sink, void* sink_user,
+                              fdd_stream_t stream) {
+  if (!plan) return fail(FDD_ERR_INVALID_ARG, "plan is NULL");
+  if (!sink) return fail(FDD_ERR_INVALID_ARG, "NULL sink");
+  if ((d_in == nullptr) == (source == nullptr))
+    return fail(FDD_ERR_INVALID_ARG, "give exactly one of d_in and source");
+  fdd_status st = check_device(plan);
+  if (st != FDD_OK) return st;
+  if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
+  if ((st = make_rings(plan, false)) != FDD_OK) return st;
+  Io io;
+  io.d_in = d_in;
+  io.source = source;
+  io.source_user = source_user;
+  io.sink = sink;
+  io.sink_user = sink_user;
+  io.dm_first = 0;
+  io.n_dm = plan->p.n_dm;
+  return run(plan, io, reinterpret_cast<cudaStream_t>(stream));
 }
 
 fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_stream_t stream) {
@@ -942,34 +1130,22 @@ fdd_status fdd_execute_host(fdd_plan_t plan, const void* h_in, void* h_out, fdd_
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
   if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
-  const size_t in_bytes =
-      static_cast<size_t>(plan->info.in_elems) * (plan->p.in_dtype == FDD_IN_U8 ? 1 : 4);
-  const size_t out_bytes = static_cast<size_t>(plan->info.out_bytes);
-  if (!plan->d_in_stage && (st = dev_alloc(plan, &plan->d_in_stage, in_bytes))) return st;
-  if (!plan->d_out_stage && (st = dev_alloc(plan, &plan->d_out_stage, out_bytes))) return st;
-  const fdd_info& g = plan->info;
-  const size_t n_ev = 2 * static_cast<size_t>(plan->p.n_beams) * g.n_chunks + 2;
-  if (!plan->h2d) FDD_CUDA(cudaStreamCreateWithFlags(&plan->h2d, cudaStreamNonBlocking));
-  if (!plan->d2h) FDD_CUDA(cudaStreamCreateWithFlags(&plan->d2h, cudaStreamNonBlocking));
-  while (plan->pipe_ev.size() < n_ev) {
-    cudaEvent_t e = nullptr;
-    FDD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    plan->pipe_ev.push_back(e);
-  }
+  if ((st = make_rings(plan, true)) != FDD_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  HostPipe hp{plan, static_cast<const char*>(h_in), static_cast<char*>(h_out),
-              std::vector<int64_t>(plan->p.n_beams, 0), 0};
+  Io io;
+  io.h_in = static_cast<const char*>(h_in);
+  io.h_out = static_cast<char*>(h_out);
+  io.dm_first = 0;
+  io.n_dm = plan->p.n_dm;
   // the copy streams start after the work already queued on the caller's stream
-  cudaEvent_t e0 = hp.event();
-  FDD_CUDA(cudaEventRecord(e0, s));
-  FDD_CUDA(cudaStreamWaitEvent(plan->h2d, e0, 0));
-  FDD_CUDA(cudaStreamWaitEvent(plan->d2h, e0, 0));
-  st = run(plan, plan->d_in_stage, 0, plan->p.n_dm, plan->d_out_stage, s, &hp);
+  FDD_CUDA(cudaEventRecord(plan->pipe_start, s));
+  FDD_CUDA(cudaStreamWaitEvent(plan->h2d, plan->pipe_start, 0));
+  FDD_CUDA(cudaStreamWaitEvent(plan->d2h, plan->pipe_start, 0));
+  st = run(plan, io, s);
   if (st != FDD_OK) return st;
   // and the caller's stream ends after the last copy back
-  cudaEvent_t e1 = hp.event();
-  FDD_CUDA(cudaEventRecord(e1, plan->d2h));
-  FDD_CUDA(cudaStreamWaitEvent(s, e1, 0));
+  FDD_CUDA(cudaEventRecord(plan->pipe_end, plan->d2h));
+  FDD_CUDA(cudaStreamWaitEvent(s, plan->pipe_end, 0));
   return FDD_OK;
 }
 
@@ -991,9 +1167,9 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
     return fail(FDD_ERR_INVALID_ARG, "trial range outside the plan's list");
   if (out_kind != FDD_OUT_SPECTRA && out_kind != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "out_kind must be FDD_OUT_SPECTRA or FDD_OUT_POWER");
-  if (plan->tc && sizeof(float2) * static_cast<size_t>(n_series) * plan->p.n_chan > plan->tcx_bytes)
+  if (plan->tc && fdd::mac_tc_min_scratch(n_series, n_dm, n_bins) > plan->tcx_bytes)
     return fail(FDD_ERR_UNSUPPORTED,
-                "n_series x n_chan spectra of one bin exceed the tensor-core form's scratch");
+                "n_series x n_dm outputs of one bin exceed the tensor-core form's scratch");
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
   if ((st = need_uniform_grid(plan)) != FDD_OK) return st;

@@ -44,6 +44,8 @@ struct MacArgs {
                             // so the consumers' bounded waits run out (FDD_ERR_TIMEOUT)
   const float* bin_absmax;  // tensor cores in FP16 only: per local bin, the largest
                             // |re| or |im| of the spectra (sets that bin's data scale)
+  int absmax_ready;         // tensor cores in FP16: the scratch already holds the
+                            // per-bin maxima of these spectra (a later DM batch)
 };
 
 // Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu and the
@@ -87,34 +89,36 @@ cudaError_t mac_tc_prepare();
 // Beams per tensor-core group: 16 when a call has at most 16 series (then a
 // pass covers 2048 trials), else 32 (1024 trials per pass).
 int mac_tc_beams_per_group(int n_series);
-// The tensor-core kernel reads the spectra bin-major, X_T[k][series][chan]
-// (a 256-byte row per 32 channels of one beam), and writes Y bin-major,
-// Y_T[k][series][trial].  launch_mac_tc takes the caller's layouts (X as
-// [series][chan][pitch] with x_series_stride = n_chan x_chan_stride, Y with
-// bins innermost) and, a block of bins at a time, transposes X into
-// `scratch`, runs the kernel into the rest of `scratch`, and transposes Y
-// out.  mac_tc_scratch_bytes: the scratch a plan allocates for calls of up
-// to n_dm trials on n_series x n_chan spectra of n_bins bins (blocks of at
-// most 3 GiB, at least one bin).
+// The tensor-core kernel reads the spectra where the caller keeps them, X as
+// [series][chan][pitch] with bins innermost (x_series_stride = n_chan x
+// x_chan_stride; x_bin_stride is set to 1 by launch_mac_tc).  Its output is
+// bin-major: with a.y_bin_stride > 0 the kernel writes Y[k][series][trial]
+// straight to the caller at the given strides (y_dm_stride 1 keeps every
+// warp store contiguous); with a.y_bin_stride == 0 the caller's Y has bins
+// innermost, and launch_mac_tc writes blocks of bins bin-major into `scratch`
+// and moves each block into the caller's layout.  The FP16 form first finds
+// each bin's largest component (one read of X).  mac_tc_scratch_bytes: the
+// scratch a plan allocates for calls of up to n_dm trials on n_series x
+// n_chan spectra of n_bins bins (per-bin maxima, and blocks of bin-major
+// output of at most 3 GiB, at least one bin); mac_tc_min_scratch: the least
+// scratch a call of that shape needs.
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins);
+size_t mac_tc_min_scratch(int n_series, int n_dm, int64_t n_bins);
 // precision: FDD_PREC_BF16_HILO, FDD_PREC_BF16 or FDD_PREC_FP16.
 cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s);
 
-// Bins k0 .. k0 + n_bins - 1 of `rows` complex rows of stride in_stride into
-// out[k][row] (bin-major), for the tensor-core kernel.
-struct BinTransposeArgs {
-  const float2* in;      // row r, bin k at in + r * in_stride + k
+// Per bin k < n_bins, the largest |re| or |im| of `rows` complex rows
+// in[r * in_stride + k], as float bits, by atomic max into absmax[k] (zeroed
+// by the caller): the FP16 tensor-core form's per-bin data scale.
+struct BinAbsmaxArgs {
+  const float2* in;
   int64_t in_stride;
   int64_t rows;
-  int64_t k0;
   int n_bins;
-  float2* out;           // [n_bins][rows]
-  unsigned int* absmax;  // optional: per bin, atomic max of the bits of max(|re|, |im|)
-                         // over the rows (non-negative floats order as their bits);
-                         // the caller zeroes it first
+  unsigned int* absmax;
 };
-cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s);
+cudaError_t launch_bin_absmax(const BinAbsmaxArgs& a, cudaStream_t s);
 
 // The way back for the output: in[k][series][trial] (bin-major, n_bins bins)
 // into out + series * out_series_stride + trial * out_dm_stride + k.

@@ -511,70 +511,84 @@ static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cu
 namespace {
 constexpr size_t kScratchAlign = 256;
 constexpr size_t kScratchCap = size_t(3) << 30;
-// Scratch bytes per bin: the bin-major spectra, the bin-major output
-// (complex, the larger of the two output kinds) and the bin's FP16 scale key.
-size_t scratch_per_bin(int n_series, int n_chan, int n_dm) {
-  return sizeof(float2) * static_cast<size_t>(n_series) * (static_cast<size_t>(n_chan) + n_dm) +
-         sizeof(float);
+size_t align_up(size_t p) { return (p + kScratchAlign - 1) & ~(kScratchAlign - 1); }
+// Bin-major output of one bin for the bins-innermost path (complex, the
+// larger of the two output kinds).
+size_t ybin_bytes(int n_series, int n_dm) {
+  return sizeof(float2) * static_cast<size_t>(n_series) * static_cast<size_t>(n_dm);
 }
-uintptr_t align_up(uintptr_t p) { return (p + kScratchAlign - 1) & ~(kScratchAlign - 1); }
+// Bins per block of the bins-innermost path: as many as 3 GiB of bin-major
+// output hold, at least one.
+int64_t block_bins(size_t per_bin, int64_t n_bins) {
+  int64_t kb = static_cast<int64_t>(kScratchCap / per_bin);
+  if (kb < 1) kb = 1;
+  return kb < n_bins ? kb : n_bins;
+}
+int tc_prec(int precision) {
+  return precision == FDD_PREC_BF16_HILO ? kBf16HiLo
+         : precision == FDD_PREC_BF16    ? kBf16
+         : precision == FDD_PREC_FP16    ? kF16
+                                         : -1;
+}
 }  // namespace
 
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins) {
-  const size_t per_bin = scratch_per_bin(n_series, n_chan, n_dm);
-  int64_t kb = static_cast<int64_t>(kScratchCap / per_bin);
-  if (kb < 1) kb = 1;
-  if (kb > n_bins) kb = n_bins;
-  return per_bin * static_cast<size_t>(kb) + 2 * kScratchAlign;
+  (void)n_chan;
+  // the per-bin FP16 maxima of every bin, then the bin-major output of a block
+  const size_t per_bin = ybin_bytes(n_series, n_dm);
+  return align_up(sizeof(unsigned int) * static_cast<size_t>(n_bins)) +
+         per_bin * static_cast<size_t>(block_bins(per_bin, n_bins)) + kScratchAlign;
+}
+
+size_t mac_tc_min_scratch(int n_series, int n_dm, int64_t n_bins) {
+  return align_up(sizeof(unsigned int) * static_cast<size_t>(n_bins)) +
+         ybin_bytes(n_series, n_dm) + kScratchAlign;
 }
 
 cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   if (a.x_series_stride != a.x_chan_stride * a.n_chan) return cudaErrorInvalidValue;
-  const int prec = precision == FDD_PREC_BF16_HILO ? kBf16HiLo
-                   : precision == FDD_PREC_BF16    ? kBf16
-                   : precision == FDD_PREC_FP16    ? kF16
-                                                   : -1;
-  if (prec < 0) return cudaErrorInvalidValue;
-  const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
-  const int64_t y_rows = static_cast<int64_t>(a.n_series) * a.n_dm;
+  const int prec = tc_prec(precision);
+  if (prec < 0 || !scratch) return cudaErrorInvalidValue;
+  // scratch: [n_bins] per-bin maxima (FP16), then the bin-major output block
+  unsigned int* absmax = reinterpret_cast<unsigned int*>(scratch);
+  const size_t head = align_up(sizeof(unsigned int) * static_cast<size_t>(a.n_bins));
+  if (scratch_bytes < head + kScratchAlign) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (prec == kF16 && !a.absmax_ready) {
+    e = cudaMemsetAsync(absmax, 0, sizeof(unsigned int) * static_cast<size_t>(a.n_bins), s);
+    if (e != cudaSuccess) return e;
+    BinAbsmaxArgs t{a.X, a.x_chan_stride, static_cast<int64_t>(a.n_series) * a.n_chan, a.n_bins,
+                    absmax};
+    e = launch_bin_absmax(t, s);
+    if (e != cudaSuccess) return e;
+  }
+  // The kernel reads the spectra where they are (bins innermost).
+  MacArgs b = a;
+  b.x_bin_stride = 1;
+  b.bin_absmax = reinterpret_cast<const float*>(absmax);
+  if (a.y_bin_stride > 0) return launch_mac_tc_block(b, prec, n_sms, s);  // bin-major output
+
+  // Bins-innermost output: blocks of bins written bin-major into the scratch,
+  // then moved into the caller's layout.
   const size_t y_elem = a.out_kind == 2 ? sizeof(float) : sizeof(float2);
-  const size_t per_bin = sizeof(float2) * rows + y_elem * y_rows + sizeof(float);
-  const int64_t kb = scratch_bytes > 2 * kScratchAlign
-                         ? static_cast<int64_t>((scratch_bytes - 2 * kScratchAlign) / per_bin)
-                         : 0;
-  if (!scratch || kb < 1) return cudaErrorInvalidValue;
-  // [kb][rows] spectra, then (256-byte aligned) [kb][series][trial] output,
-  // then (aligned) the kb per-bin maxima of the FP16 form
-  const uintptr_t y_addr = align_up(reinterpret_cast<uintptr_t>(scratch + kb * rows));
-  void* y_scratch = reinterpret_cast<void*>(y_addr);
-  unsigned int* absmax =
-      reinterpret_cast<unsigned int*>(align_up(y_addr + y_elem * static_cast<size_t>(kb * y_rows)));
+  const size_t per_bin = y_elem * static_cast<size_t>(a.n_series) * a.n_dm;
+  const int64_t kb = static_cast<int64_t>((scratch_bytes - head - kScratchAlign) / per_bin);
+  if (kb < 1) return cudaErrorInvalidValue;
+  void* y_scratch = reinterpret_cast<char*>(scratch) + head;
   for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb) {
     const int nb = static_cast<int>((a.n_bins - k0) < kb ? (a.n_bins - k0) : kb);
-    cudaError_t e;
-    if (prec == kF16) {
-      e = cudaMemsetAsync(absmax, 0, sizeof(unsigned int) * static_cast<size_t>(nb), s);
-      if (e != cudaSuccess) return e;
-    }
-    BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, scratch,
-                       prec == kF16 ? absmax : nullptr};
-    e = launch_bin_transpose(t, s);
-    if (e != cudaSuccess) return e;
-    MacArgs b = a;
-    b.X = scratch;
-    b.x_bin_stride = rows;
-    b.x_series_stride = a.n_chan;
-    b.x_chan_stride = 1;
-    b.n_bins = nb;
-    b.k_begin = a.k_begin + static_cast<int>(k0);
-    b.Y = y_scratch;
-    b.y_bin_stride = y_rows;
-    b.y_series_stride = a.n_dm;
-    b.y_dm_stride = 1;
-    b.bin_absmax = reinterpret_cast<const float*>(absmax);
-    e = launch_mac_tc_block(b, prec, n_sms, s);
+    MacArgs c = b;
+    c.X = a.X + k0;
+    c.n_bins = nb;
+    c.k_begin = a.k_begin + static_cast<int>(k0);
+    c.bin_absmax = reinterpret_cast<const float*>(absmax + k0);
+    c.Y = y_scratch;
+    c.y_bin_stride = static_cast<int64_t>(a.n_series) * a.n_dm;
+    c.y_series_stride = a.n_dm;
+    c.y_dm_stride = 1;
+    e = launch_mac_tc_block(c, prec, n_sms, s);
     if (e != cudaSuccess) return e;
     BinUntransposeArgs u{y_scratch, static_cast<int>(y_elem), a.n_series, a.n_dm, nb,
                          static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0),
