@@ -83,6 +83,10 @@ def parse_args():
                          "(one JSON line)")
     ap.add_argument("--batch-n-t-div", type=int, default=16,
                     help="divide the batch workload's beam lengths (device memory bound)")
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "bf16_hilo"],
+                    help="tensor-core form of the multi-beam workloads")
+    ap.add_argument("--workspace-gib", type=float, default=200.0,
+                    help="device workspace limit of the multi-beam plans (GiB)")
     ap.add_argument("--mac-sweep", default="",
                     help="comma-separated FDD_MAC_* variants, by number or name, or tc / tc1 / tc16 for "
                          "the tensor-core form in BF16 hi+lo / BF16 / FP16 (or 'all'): time the "
@@ -609,8 +613,7 @@ def run_fdd(args, rank: int, world: int, dist) -> None:
     if clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak * clk["sm_mhz"] / max_mhz)
     stage_share = {k: v / max(sum(prof["ms"].values()), 1e-9) for k, v in prof["ms"].items()}
-    own_launches = prof["launches"]["unpack"] + prof["launches"]["mac"] + \
-        prof["launches"]["scatter"]
+    own_launches = prof["kernels"]
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -744,6 +747,269 @@ def run_mac_sweep(args) -> None:
               flush=True)
 
 
+TC_PREC = {"fp16": 3, "bf16": 2, "bf16_hilo": 1}  # FDD_PREC_* of the tensor-core forms
+RESIDENT_INPUT_BYTES = 100 << 30  # larger inputs stream from the generator
+
+
+def tc_workload_accuracy(fdd, w: synth.Workload, prec: int, seed: int, beams) -> dict:
+    """rel-L2 of the tensor-core form against the FP64 oracle on sampled bins of
+    the workload's own first chunk (beam 0: the counter-based input, made on
+    the device and copied back; oracle FFT of every channel), all trials."""
+    import torch
+
+    import oracle
+    d = oracle.delays(w.channel_centres(), w.dms(), w.t_samp_s)
+    geo = oracle.geometry(w.n_t, w.chunk_len, d)
+    rows = min(geo.L, w.n_t)
+    buf = torch.empty(rows * w.n_chan, dtype=torch.float32, device="cuda")
+    beams.fill(0, buf.data_ptr(), 0, rows, torch.cuda.current_stream().cuda_stream)
+    fb = buf.cpu().numpy().reshape(rows, w.n_chan)
+    del buf
+    X = oracle.spectra(fb.T.astype(np.float64), geo, 0)
+    rng = np.random.default_rng(seed)
+    bins = np.unique(np.concatenate([[0, 1, geo.K - 1], rng.integers(2, geo.K - 1, 5)]))
+    ref = oracle.fdd_bins(X[:, bins], bins, geo.L, d)
+    res = {}
+    with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA, n_beams=1,
+                         precision=prec, workspace_limit=8 << 30)) as plan:
+        nb = bins.size
+        host = np.zeros((1, w.n_chan, nb, 2), dtype=np.float32)
+        Xs = X[:, bins].astype(np.complex64)
+        host[0, :, :, 0] = Xs.real
+        host[0, :, :, 1] = Xs.imag
+        dX = torch.from_numpy(host).cuda()
+        got = np.zeros((w.n_dm, nb), dtype=np.complex128)
+        for q, k in enumerate(bins):  # bin windows of one bin (absolute phases)
+            dY = torch.empty((1, w.n_dm, 1, 2), device="cuda")
+            plan.dedisperse_spectra_bins(dX[:, :, q:q + 1].contiguous(), 1, 1, int(k), 1, 0,
+                                         w.n_dm, dY, 1)
+            y = dY.cpu().numpy().astype(np.float64)[0, :, 0]
+            got[:, q] = y[:, 0] + 1j * y[:, 1]
+    res["rel_l2_vs_oracle"] = _rel(got, ref)
+    res["rel_l2_vs_oracle_no_dc"] = _rel(got[:, bins > 0], ref[:, bins > 0])
+    res["sample"] = (f"beam 0, chunk 0: {bins.size} bins (DC, 1, Nyquist, 5 random) x "
+                     f"{w.n_dm} trials x {w.n_chan} channels, oracle FFT spectra in")
+    return res
+
+
+def run_tc_workload(args) -> None:
+    """A multi-beam workload on the tensor-core form (beams share every bin's
+    phasors), streamed: whole input resident on the device when it fits,
+    else each (beam, chunk) window generated on the device by the
+    counter-based generator; output blocks handed to a sink that reads them
+    (``value``: device line, sink discards), or copied to a pinned host ring
+    (``e2e``: host input windows in, every output block back to the host)."""
+    import ctypes
+
+    import torch
+
+    import paper_2110_03482_gb300 as fdd
+    import synth.gpu
+
+    fdd.build()
+    synth.gpu.build()
+    w = workload_from_args(args)
+    prec = TC_PREC[args.precision]
+    props = torch.cuda.get_device_properties(0)
+    gpu_id = gpu_uuid(props, 0)
+    stream = torch.cuda.current_stream()
+    s_handle = stream.cuda_stream
+    params = dict(plan_params(w, fdd), n_beams=w.n_beams, precision=prec,
+                  workspace_limit=int(args.workspace_gib * (1 << 30)))
+    esz = 1 if w.dtype == "u8" else 4
+    in_bytes = w.n_beams * w.n_t * w.n_chan * esz
+    beams = synth.gpu.BeamWindows([synth.philox_beam_args(w, args.seed, b)[0]
+                                   for b in range(w.n_beams)])
+    t_plan = time.perf_counter()
+    plan = fdd.Plan(**params)
+    plan_s = time.perf_counter() - t_plan
+    info = plan.info
+    resident = in_bytes <= RESIDENT_INPUT_BYTES
+    d_in = None
+    if resident:
+        d_in = torch.empty(in_bytes, dtype=torch.uint8, device="cuda")
+        for b in range(w.n_beams):
+            beams.fill(b, d_in.data_ptr() + b * w.n_t * w.n_chan * esz, 0, w.n_t, s_handle)
+        stream.synchronize()
+    out_esz = 4 if w.output in ("time", "power") else 8
+    out_bytes = int(info["out_bytes"])
+    blocks = [0, 0]
+
+    def source(beam, t0, n, d_window, ready, s):  # stream-ordered on s
+        beams.fill(beam, d_window, t0, n, s)
+
+    def sink(blk, s):  # the device line consumes nothing: count what arrived
+        blocks[0] += 1
+        blocks[1] += blk["n_beams"] * blk["n_dm"] * blk["row_len"] * out_esz
+        return None
+
+    def step():
+        if resident:
+            plan.execute_stream(None, sink, stream, d_in=d_in)
+        else:
+            plan.execute_stream(source, sink, stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    plan.profile_enable(True)
+    clocks = Clocks(gpu_id)
+    blocks[:] = [0, 0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile_read()
+    plan.profile_enable(False)
+    plan.query()  # raises if a kernel reported a device-side timeout
+    macs_step = w.n_beams * int(info["n_chunks"]) * w.n_dm * w.n_chan * int(info["n_bins"])
+    value = macs_step * args.steps / (ms / 1e3)
+    mac_n = prof["launches"]["mac"]
+    mac_ms = prof["ms"]["mac"] / max(mac_n, 1)
+    macs_launch = macs_step / max(mac_n / args.steps, 1)
+    achieved = FLOPS_PER_MAC * macs_launch / (mac_ms / 1e3) / 1e12
+    peaks = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained") or 1723.8)
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"tensor-core phase-rotate-and-sum ({args.precision}), per-bin "
+                          "maxima pass and bin-major output included",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured; FP16 "
+                               "and BF16 dense rates are equal, nominal ratio 1)",
+                "algorithmic_flops_per_launch": FLOPS_PER_MAC * macs_launch,
+                "mac_ms_per_launch": mac_ms, "mac_launches_timed": mac_n}
+    if args.precision == "bf16_hilo":
+        roofline["tensor_frac_physical"] = 2 * achieved / peak
+    stage_share = {k: v / max(sum(prof["ms"].values()), 1e-9) for k, v in prof["ms"].items()}
+
+    # end to end: pinned host input (or a pool of generated windows when the
+    # input exceeds host memory), every output block back to a pinned host ring
+    e2e = None
+    if not args.no_e2e:
+        rt = fdd.cudart()
+        vp = ctypes.c_void_p
+        rt.cudaEventCreateWithFlags.argtypes = [ctypes.POINTER(vp), ctypes.c_uint]
+        rt.cudaEventRecord.argtypes = [vp, vp]
+        rt.cudaStreamWaitEvent.argtypes = [vp, vp, ctypes.c_uint]
+        rt.cudaEventDestroy.argtypes = [vp]
+
+        def new_event():
+            e = vp()
+            rt.cudaEventCreateWithFlags(ctypes.byref(e), 2)
+            return e.value
+        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        win_bytes = w.n_chan * int(info["fft_len"]) * esz
+        if resident:
+            h_in = torch.empty(in_bytes, dtype=torch.uint8, pin_memory=True)
+            h_in.copy_(d_in)
+            pool = None
+        else:
+            pool_n = 4
+            h_in = torch.empty(pool_n * win_bytes, dtype=torch.uint8, pin_memory=True)
+            tmp = torch.empty(win_bytes, dtype=torch.uint8, device="cuda")
+            for i in range(pool_n):  # distinct generated windows, reused cyclically
+                beams.fill(i % w.n_beams, tmp.data_ptr(), 0,
+                           min(int(info["fft_len"]), w.n_t), s_handle)
+                stream.synchronize()
+                h_in[i * win_bytes:(i + 1) * win_bytes].copy_(tmp)
+            del tmp
+            pool = pool_n
+        blk_max = max(1, int(info["stream_bytes"]) // 2 - win_bytes)
+        ring = [torch.empty(blk_max, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        ev_pool = [new_event() for _ in range(8)]
+        state = {"win": 0, "blk": 0, "h2d": 0, "d2h": 0}
+
+        def host_source(beam, t0, n, d_window, ready, s):
+            e_full = ev_pool[state["win"] % 2]
+            if ready:
+                rt.cudaStreamWaitEvent(h2d.cuda_stream, ready, 0)
+            nbytes = n * w.n_chan * esz
+            if pool is None:
+                src = h_in.data_ptr() + (beam * w.n_t + t0) * w.n_chan * esz
+            else:
+                src = h_in.data_ptr() + (state["win"] % pool) * win_bytes
+            fdd.memcpy_async(d_window, src, nbytes, h2d.cuda_stream)
+            rt.cudaEventRecord(e_full, h2d.cuda_stream)
+            rt.cudaStreamWaitEvent(s, e_full, 0)
+            state["win"] += 1
+            state["h2d"] += nbytes
+
+        def host_sink(blk, s):
+            k = state["blk"] % 2
+            e_done, e_rel = ev_pool[2 + k], ev_pool[4 + k]
+            rt.cudaEventRecord(e_done, s)
+            rt.cudaStreamWaitEvent(d2h.cuda_stream, e_done, 0)
+            rows = blk["n_beams"] * blk["n_dm"]
+            width = blk["row_len"] * out_esz
+            fdd.memcpy2d_async(ring[k].data_ptr(), width, blk["d_data"],
+                               blk["row_pitch"] * out_esz, width, rows, d2h.cuda_stream)
+            rt.cudaEventRecord(e_rel, d2h.cuda_stream)
+            state["blk"] += 1
+            state["d2h"] += rows * width
+            return e_rel
+
+        def e2e_step():
+            plan.execute_stream(host_source, host_sink, stream)
+            end = ev_pool[6]
+            rt.cudaEventRecord(end, d2h.cuda_stream)
+            rt.cudaStreamWaitEvent(s_handle, end, 0)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        state.update(h2d=0, d2h=0)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = f0.elapsed_time(f1)
+        e2e = {"value": macs_step * args.e2e_steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": state["h2d"] // args.e2e_steps,
+               "d2h_bytes_per_step": state["d2h"] // args.e2e_steps,
+               "ms_per_step": e_ms / args.e2e_steps,
+               "input": ("whole input from pinned host memory" if pool is None else
+                         f"every window from a pinned host pool of {pool} generated windows "
+                         f"(the {in_bytes / 1e9:.0f} GB input exceeds host memory)"),
+               "output": "every output block to a pinned host ring of two blocks"}
+        for e in ev_pool:
+            rt.cudaEventDestroy(e)
+        del h_in, ring
+    acc = tc_workload_accuracy(fdd, w, prec, args.seed, beams) if not args.no_cpu_baseline \
+        else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(w.scaled(n_beams=1), args.seed, args.cpu_seconds,
+                           macs_step=macs_step)
+    plan.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic (seeded counter-based filterbank, generated on the device)",
+            "form": "tensor cores, beams share each bin's phasors; streamed output blocks",
+            "config": dict(workload_config(w, info), beams_per_gpu=w.n_beams,
+                           precision=args.precision, dm_batch=info["dm_batch"],
+                           block_dm=info["block_dm"],
+                           input=("resident in HBM" if resident else
+                                  "generated per (beam, chunk) window on the device "
+                                  f"({in_bytes / 1e9:.0f} GB exceeds HBM)"),
+                           output_bytes_per_step=out_bytes,
+                           output_bytes_delivered=blocks[1] // max(args.steps, 1),
+                           workspace_gib=info["workspace_bytes"] / 2 ** 30,
+                           plan_seconds=plan_s),
+            "gpu_launches": prof["kernels"],
+            "clocks": clk, "roofline": roofline, "e2e": e2e, "accuracy": acc,
+            "cpu_baseline": cpu, "stage_ms_share": stage_share,
+            "macs_per_step": macs_step}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args) -> None:
     """Whole-batch throughput of the batching form (unpack, transforms and one
     persistent phase-rotate-and-sum launch per wave, replayed as a CUDA graph)."""
@@ -831,6 +1097,9 @@ def main():
         return
     if args.downsample_sweep:
         run_downsample_sweep(args)
+        return
+    if args.impl == "fdd" and synth.WORKLOADS[args.workload].n_beams > 1:
+        run_tc_workload(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -400,12 +400,17 @@ fdd_status fdd_debug_fail_alloc(int32_t after);
 #define FDD_STAGE_C2R 3     /* inverse transforms, Eq. 6 (cuFFT)                */
 #define FDD_STAGE_SCATTER 4 /* 1/L scaling and valid-sample placement           */
 #define FDD_STAGE_TDD 5     /* brute-force time-domain shift-and-sum (Eq. 2)    */
-#define FDD_STAGE_COUNT 6
+#define FDD_STAGE_TRANSPOSE 6 /* tensor-core form: spectra to bin-major, and each
+                                 beam's output back to bins innermost            */
+#define FDD_STAGE_COUNT 7
 
 typedef struct fdd_profile {
   int64_t launches[FDD_STAGE_COUNT]; /* timed launches per stage               */
   double ms[FDD_STAGE_COUNT];        /* summed device time per stage, ms        */
   int64_t dropped;                   /* launches not timed (event ring full)    */
+  int64_t kernels;                   /* kernels of this library launched since
+                                        profiling was enabled on this plan (all
+                                        plans and threads of the process)        */
 } fdd_profile;
 
 /*

@@ -65,8 +65,9 @@ FDD_STAGE_MAC = 2
 FDD_STAGE_C2R = 3
 FDD_STAGE_SCATTER = 4
 FDD_STAGE_TDD = 5
-FDD_STAGE_COUNT = 6
-STAGE_NAMES = ["unpack", "r2c", "mac", "c2r", "scatter", "tdd"]
+FDD_STAGE_TRANSPOSE = 6
+FDD_STAGE_COUNT = 7
+STAGE_NAMES = ["unpack", "r2c", "mac", "c2r", "scatter", "tdd", "transpose"]
 
 
 class fdd_params(ctypes.Structure):
@@ -150,12 +151,13 @@ class fdd_profile(ctypes.Structure):
         ("launches", ctypes.c_int64 * FDD_STAGE_COUNT),
         ("ms", ctypes.c_double * FDD_STAGE_COUNT),
         ("dropped", ctypes.c_int64),
+        ("kernels", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
         return {"launches": {STAGE_NAMES[i]: int(self.launches[i]) for i in range(FDD_STAGE_COUNT)},
                 "ms": {STAGE_NAMES[i]: float(self.ms[i]) for i in range(FDD_STAGE_COUNT)},
-                "dropped": int(self.dropped)}
+                "dropped": int(self.dropped), "kernels": int(self.kernels)}
 
 
 class fdd_beam_desc(ctypes.Structure):

@@ -42,6 +42,9 @@ struct fdd_plan_s {
   float2* d_Y = nullptr;      // [dm_batch][bin_pitch] dedispersed spectra (time output;
                               // tensor-core form: [beam][dm_batch][bin_pitch])
   float* d_yt = nullptr;      // [dm_batch][L] inverse transforms (time output)
+  float2* d_xb = nullptr;     // tensor-core form: one beam's spectra [n_chan][bin_pitch]
+  float2* d_Yb = nullptr;     // tensor-core form, time output: one beam's DM batch
+                              // [dm_batch][bin_pitch] with bins innermost
   void* d_fftwork = nullptr;
   int* d_status = nullptr;
   cufftHandle r2c = 0, c2r = 0, c2r_tail = 0;
@@ -74,6 +77,7 @@ struct fdd_plan_s {
   std::vector<int> prof_stage;
   int prof_n = 0;
   int64_t prof_dropped = 0;
+  long long prof_launch0 = 0;  // the library's launch count when profiling started
 };
 
 namespace {
@@ -108,8 +112,9 @@ constexpr size_t kMaxSmem = 227 * 1024;
 constexpr int kProfSlots = 4096;
 
 // Records an event pair around one stage launch when profiling is on.
-const char* const kStageNames[FDD_STAGE_COUNT] = {"fdd unpack", "fdd r2c", "fdd mac",
-                                                   "fdd c2r", "fdd scatter", "fdd tdd"};
+const char* const kStageNames[FDD_STAGE_COUNT] = {"fdd unpack", "fdd r2c",     "fdd mac",
+                                                   "fdd c2r",    "fdd scatter", "fdd tdd",
+                                                   "fdd transpose"};
 
 // CUDA events around a stage launch when profiling is on, and an NVTX range
 // (named after the stage) always; both cost next to nothing without a tool.
@@ -366,13 +371,14 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
 
   const size_t spectra_sets = tc ? static_cast<size_t>(p->n_beams) : 1;
   const size_t fixed = sizeof(fdd::PhaseConst) * nc + sizeof(float) * size_t(nc) * L +
-                       sizeof(float2) * size_t(nc) * g->bin_pitch * spectra_sets + 256 +
+                       sizeof(float2) * size_t(nc) * g->bin_pitch * (spectra_sets + (tc ? 1 : 0)) +
+                       256 +
                        (tc ? fdd::mac_tc_scratch_bytes(p->n_beams, nc, p->n_dm, n_bins) : 0);
   const size_t limit = p->workspace_limit ? p->workspace_limit : kDefaultWorkspace;
   int64_t batch = p->n_dm;
   size_t per_dm = 0;
   if (p->output == FDD_OUT_TIME) {
-    per_dm = sizeof(float2) * g->bin_pitch * spectra_sets + sizeof(float) * (L / f);
+    per_dm = sizeof(float2) * g->bin_pitch * (spectra_sets + (tc ? 1 : 0)) + sizeof(float) * (L / f);
     if (fixed + per_dm > limit)
       return fail(FDD_ERR_INVALID_ARG, "workspace_limit %zu is below the minimum %zu", limit,
                   fixed + per_dm);
@@ -417,7 +423,8 @@ void release(fdd_plan_s* P) {
   if (P->has_r2c) cufftDestroy(P->r2c);
   if (P->has_c2r) cufftDestroy(P->c2r);
   if (P->has_c2r_tail) cufftDestroy(P->c2r_tail);
-  void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_fftwork, P->d_status,
+  void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_xb, P->d_Yb, P->d_fftwork,
+                  P->d_status,
                   P->d_win[0], P->d_win[1], P->d_blk[0], P->d_blk[1], P->d_tcx, P->d_shift,
                   P->d_shift_base, P->d_tdd_x};
   for (void* q : ptrs)
@@ -732,60 +739,74 @@ fdd_status run(fdd_plan_s* P, const Io& io, cudaStream_t s) {
   return FDD_OK;
 }
 
-// Tensor-core form: every beam of a chunk is transformed first, then one
-// launch per DM batch dedisperses all of them at once (the beams share each
-// bin's phasors).
+// Tensor-core form: every beam of a chunk is transformed first, each beam's
+// spectra moved into the bin-major X_T[k][beam][chan] the kernel reads (the
+// FP16 form's per-bin maxima found on the way), then one launch per DM batch
+// dedisperses all of them at once (the beams share each bin's phasors).
 fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
   fdd_status st;
   const fdd_params& p = P->p;
   const fdd_info& g = P->info;
-  const int64_t set_elems = static_cast<int64_t>(p.n_chan) * g.bin_pitch;
+  const int64_t rows = static_cast<int64_t>(p.n_beams) * p.n_chan;  // X_T row per bin
+  unsigned int* absmax = reinterpret_cast<unsigned int*>(P->d_tcx);  // scratch head
+  const bool f16 = p.precision == FDD_PREC_FP16;
   const int dm_end = io.dm_first + io.n_dm;
   for (int64_t c = 0; c < g.n_chunks; ++c) {
-    for (int b = 0; b < p.n_beams; ++b)
-      if ((st = transform(P, io, b, c, P->d_X + set_elems * b, s)) != FDD_OK) return st;
+    if (f16) FDD_CUDA(cudaMemsetAsync(absmax, 0, sizeof(unsigned int) * g.n_bins, s));
+    for (int b = 0; b < p.n_beams; ++b) {
+      if ((st = transform(P, io, b, c, P->d_xb, s)) != FDD_OK) return st;
+      fdd::BinTransposeArgs t{P->d_xb, g.bin_pitch, p.n_chan, 0, static_cast<int>(g.n_bins),
+                              P->d_X + static_cast<int64_t>(b) * p.n_chan, f16 ? absmax : nullptr,
+                              rows};
+      StageTimer tt(P, FDD_STAGE_TRANSPOSE, s);
+      FDD_CUDA(fdd::launch_bin_transpose(t, s));
+    }
     fdd::MacArgs m{};
     m.X = P->d_X;
-    m.x_series_stride = set_elems;
-    m.x_chan_stride = g.bin_pitch;
+    m.x_bin_stride = rows;
+    m.x_series_stride = p.n_chan;
+    m.x_chan_stride = 1;
     m.pc = P->d_pc;
     m.n_chan = p.n_chan;
     m.n_bins = static_cast<int>(g.n_bins);
     m.n_series = p.n_beams;
     m.scale = 1.0f;
     m.status = P->d_status;
+    m.absmax_ready = 1;  // found by the transposes
     if (p.output == FDD_OUT_TIME) {
       // (shortened inverse: only the bins up to Nyquist of length L / f)
       const int64_t Ls = g.fft_len / g.downsample;
-      m.n_bins = static_cast<int>(Ls / 2 + 1);
+      const int ks = static_cast<int>(Ls / 2 + 1);
+      m.n_bins = ks;
       for (int j0 = io.dm_first; j0 < dm_end; j0 += g.dm_batch) {
         const int nb = (dm_end - j0) < g.dm_batch ? (dm_end - j0) : g.dm_batch;
-        // bin-major [bin][beam][trial] with the trial stride of the matching
-        // inverse-transform plan (trials beyond nb are computed by nobody
-        // and their transforms discarded)
-        const bool tail = P->has_c2r_tail && nb == P->c2r_tail_batch;
-        const int sb = tail ? P->c2r_tail_batch : g.dm_batch;
+        // bin-major [bin][beam][trial] for every beam of the batch
         m.j_begin = j0;
         m.n_dm = nb;
         m.Y = P->d_Y;
-        m.y_bin_stride = static_cast<int64_t>(p.n_beams) * sb;
-        m.y_series_stride = sb;
+        m.y_bin_stride = static_cast<int64_t>(p.n_beams) * g.dm_batch;
+        m.y_series_stride = g.dm_batch;
         m.y_dm_stride = 1;
         m.out_kind = 1;
         m.real_bin_a = 0;
         m.real_bin_b = static_cast<int>(Ls / 2);
-        m.absmax_ready = j0 > io.dm_first;  // the spectra's per-bin maxima, found once
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
           FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s));
         }
-        cufftHandle h = tail ? P->c2r_tail : P->c2r;
+        cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
         for (int b = 0; b < p.n_beams; ++b) {
+          // this beam's trials with bins innermost, then its inverse transforms
+          fdd::BinUntransposeArgs u{P->d_Y + static_cast<int64_t>(b) * g.dm_batch, 8, 1, nb, ks,
+                                    P->d_Yb, 0, g.bin_pitch,
+                                    static_cast<int64_t>(p.n_beams) * g.dm_batch};
+          {
+            StageTimer t(P, FDD_STAGE_TRANSPOSE, s);
+            FDD_CUDA(fdd::launch_bin_untranspose(u, s));
+          }
           {
             StageTimer t(P, FDD_STAGE_C2R, s);
-            FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(
-                                          P->d_Y + static_cast<int64_t>(b) * sb),
-                                   P->d_yt));
+            FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(P->d_Yb), P->d_yt));
           }
           if ((st = place_time(P, io, b, c, j0, nb, s)) != FDD_OK) return st;
         }
@@ -800,7 +821,6 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
         const int nb = (dm_end - j0) < step ? (dm_end - j0) : step;
         m.j_begin = j0;
         m.n_dm = nb;
-        m.absmax_ready = j0 > io.dm_first;
         int k = -1;
         if (io.d_out) {
           m.y_series_stride = g.n_chunks * static_cast<int64_t>(io.n_dm) * g.n_bins;
@@ -854,6 +874,10 @@ fdd_status make_rings(fdd_plan_s* P, bool host) {
 namespace fdd {
 
 fdd_status report_error(fdd_status s, const char* message) { return fail(s, "%s", message); }
+
+std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 // fdd_debug_fail_alloc: allocations to let through before one fails (-1: none).
 std::atomic<int> g_fail_alloc{-1};
@@ -951,6 +975,13 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_X),
                       sizeof(float2) * size_t(nc) * g.bin_pitch * sets)))
     return st;
+  if (P->tc && (st = dev_alloc(P, reinterpret_cast<void**>(&P->d_xb),
+                               sizeof(float2) * size_t(nc) * g.bin_pitch)))
+    return st;
+  if (P->tc && p->output == FDD_OUT_TIME &&
+      (st = dev_alloc(P, reinterpret_cast<void**>(&P->d_Yb),
+                      sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch)))
+    return st;
   if (p->output == FDD_OUT_TIME) {
     if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_Y),
                         sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch * sets)))
@@ -975,22 +1006,13 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
                                 CUFFT_R2C, nc, &w_r2c));
   if (p->output == FDD_OUT_TIME) {
     // inverse transforms of length L / downsample over the first bins of each row
-    // (FP32 form: one beam's DM batch, rows of bin_pitch bins.  Tensor-core
-    // form: the kernel writes the DM batch of every beam bin-major,
-    // [bin][beam][trial], and each beam's inverse reads its trials as
-    // interleaved batches: bin stride n_beams x batch, batch stride 1.)
+    // (one beam's DM batch, rows of bin_pitch bins, for both forms)
     long long ns[1] = {g.fft_len / g.downsample};
     auto make_c2r = [&](cufftHandle* h, int batch, size_t* work) -> fdd_status {
       FDD_CUFFT(cufftCreate(h));
       FDD_CUFFT(cufftSetAutoAllocation(*h, 0));
-      if (P->tc) {
-        long long emb_bm[1] = {ns[0] / 2 + 1};
-        FDD_CUFFT(cufftMakePlanMany64(*h, 1, ns, emb_bm, static_cast<long long>(p->n_beams) * batch,
-                                      1, ns, 1, ns[0], CUFFT_C2R, batch, work));
-      } else {
-        FDD_CUFFT(cufftMakePlanMany64(*h, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
-                                      CUFFT_C2R, batch, work));
-      }
+      FDD_CUFFT(cufftMakePlanMany64(*h, 1, ns, emb_cplx, 1, g.bin_pitch, ns, 1, ns[0],
+                                    CUFFT_C2R, batch, work));
       return FDD_OK;
     };
     P->has_c2r = true;
@@ -1167,9 +1189,9 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
     return fail(FDD_ERR_INVALID_ARG, "trial range outside the plan's list");
   if (out_kind != FDD_OUT_SPECTRA && out_kind != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "out_kind must be FDD_OUT_SPECTRA or FDD_OUT_POWER");
-  if (plan->tc && fdd::mac_tc_min_scratch(n_series, n_dm, n_bins) > plan->tcx_bytes)
+  if (plan->tc && fdd::mac_tc_min_scratch(n_series, plan->p.n_chan, n_dm, n_bins) > plan->tcx_bytes)
     return fail(FDD_ERR_UNSUPPORTED,
-                "n_series x n_dm outputs of one bin exceed the tensor-core form's scratch");
+                "the spectra and outputs of one bin exceed the tensor-core form's scratch");
   fdd_status st = check_device(plan);
   if (st != FDD_OK) return st;
   if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
@@ -1303,6 +1325,7 @@ fdd_status fdd_profile_enable(fdd_plan_t plan, int32_t on) {
     }
     plan->prof_n = 0;
     plan->prof_dropped = 0;
+    plan->prof_launch0 = fdd::launches_so_far();
   }
   plan->prof_on = on != 0;
   return FDD_OK;
@@ -1312,6 +1335,7 @@ fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out) {
   if (!plan || !out) return fail(FDD_ERR_INVALID_ARG, "NULL plan or profile");
   std::memset(out, 0, sizeof *out);
   out->dropped = plan->prof_dropped;
+  out->kernels = fdd::launches_so_far() - plan->prof_launch0;
   if (plan->prof_n == 0) return FDD_OK;
   FDD_CUDA(cudaEventSynchronize(plan->prof_ev[2 * (plan->prof_n - 1) + 1]));
   for (int i = 0; i < plan->prof_n; ++i) {

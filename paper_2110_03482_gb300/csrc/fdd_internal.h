@@ -89,32 +89,49 @@ cudaError_t mac_tc_prepare();
 // Beams per tensor-core group: 16 when a call has at most 16 series (then a
 // pass covers 2048 trials), else 32 (1024 trials per pass).
 int mac_tc_beams_per_group(int n_series);
-// The tensor-core kernel reads the spectra where the caller keeps them, X as
+// The tensor-core kernel reads the spectra bin-major, X_T[k][series][chan]
+// (a 256-byte row per 32 channels of one beam), and writes Y bin-major,
+// Y_T[k][series][trial] (every warp store contiguous).  launch_mac_tc takes
+// either layout on each side: a.x_bin_stride > 0 means X is bin-major at the
+// given strides (x_chan_stride 1) and is read in place, 0 means X is
 // [series][chan][pitch] with bins innermost (x_series_stride = n_chan x
-// x_chan_stride; x_bin_stride is set to 1 by launch_mac_tc).  Its output is
-// bin-major: with a.y_bin_stride > 0 the kernel writes Y[k][series][trial]
-// straight to the caller at the given strides (y_dm_stride 1 keeps every
-// warp store contiguous); with a.y_bin_stride == 0 the caller's Y has bins
-// innermost, and launch_mac_tc writes blocks of bins bin-major into `scratch`
-// and moves each block into the caller's layout.  The FP16 form first finds
-// each bin's largest component (one read of X).  mac_tc_scratch_bytes: the
-// scratch a plan allocates for calls of up to n_dm trials on n_series x
-// n_chan spectra of n_bins bins (per-bin maxima, and blocks of bin-major
-// output of at most 3 GiB, at least one bin); mac_tc_min_scratch: the least
-// scratch a call of that shape needs.
+// x_chan_stride) and is moved bin-major into `scratch` a block of bins at a
+// time; likewise a.y_bin_stride > 0 writes Y in place bin-major, 0 writes a
+// block bin-major into the scratch and moves it into the caller's layout
+// (bins innermost).  The FP16 form first finds each bin's largest component.
+// mac_tc_scratch_bytes: the scratch a plan allocates for calls of up to n_dm
+// trials on n_series x n_chan spectra of n_bins bins in the caller's layouts
+// (per-bin maxima, blocks of at most 3 GiB, at least one bin);
+// mac_tc_min_scratch: the least scratch such a call needs.
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins);
-size_t mac_tc_min_scratch(int n_series, int n_dm, int64_t n_bins);
+size_t mac_tc_min_scratch(int n_series, int n_chan, int n_dm, int64_t n_bins);
 // precision: FDD_PREC_BF16_HILO, FDD_PREC_BF16 or FDD_PREC_FP16.
 cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s);
 
-// Per bin k < n_bins, the largest |re| or |im| of `rows` complex rows
-// in[r * in_stride + k], as float bits, by atomic max into absmax[k] (zeroed
-// by the caller): the FP16 tensor-core form's per-bin data scale.
-struct BinAbsmaxArgs {
-  const float2* in;
+// Bins k0 .. k0 + n_bins - 1 of `rows` complex rows of stride in_stride into
+// out[k][row] (bin-major), for the tensor-core kernel.
+struct BinTransposeArgs {
+  const float2* in;      // row r, bin k at in + r * in_stride + k
   int64_t in_stride;
   int64_t rows;
+  int64_t k0;
+  int n_bins;
+  float2* out;           // bin k, row r at out + k * out_bin_stride + r
+  unsigned int* absmax;  // optional: per bin, atomic max of the bits of max(|re|, |im|)
+                         // over the rows (non-negative floats order as their bits);
+                         // the caller zeroes it first
+  int64_t out_bin_stride = 0;  // 0: rows
+};
+cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s);
+
+// Per bin k < n_bins of bin-major spectra (rows contiguous: in[k * bin_stride
+// + r], r < rows), the bits of the largest |re| or |im| into absmax[k]: the
+// FP16 tensor-core form's per-bin data scale.
+struct BinAbsmaxArgs {
+  const float2* in;
+  int64_t bin_stride;
+  int rows;
   int n_bins;
   unsigned int* absmax;
 };
@@ -131,12 +148,18 @@ struct BinUntransposeArgs {
   void* out;
   int64_t out_series_stride;  // elements
   int64_t out_dm_stride;      // elements
+  int64_t in_bin_stride = 0;  // elements between bins of `in`; 0: n_series * n_dm
 };
 cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s);
 
 // Allocation-failure injection (fdd_debug_fail_alloc): true when this device
 // allocation is to fail; every library allocator asks before cudaMalloc.
 bool injected_alloc_failure();
+
+// Kernels this library has launched (process wide): every launch wrapper
+// adds to it; the profiling calls report the count over a profiled region.
+void note_launches(int n);
+long long launches_so_far();
 
 // The last-error setter shared by every translation unit (never allocates).
 fdd_status report_error(fdd_status s, const char* message);

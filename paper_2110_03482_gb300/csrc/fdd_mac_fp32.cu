@@ -660,6 +660,7 @@ cudaError_t launch_mac_batch(const BatchSet* d_sets, int n_sets, long long n_ite
   if (!vi.batch_fn) return cudaErrorInvalidValue;
   if (n_items <= 0) return cudaSuccess;
   void* params[] = {&d_sets, &n_sets, &n_items, &d_counter};
+  note_launches(1);
   return cudaLaunchKernel(vi.batch_fn, dim3(n_ctas), dim3(vi.warps * 32), params,
                           mac_smem_bytes(variant, n_chan), s);
 }
@@ -673,6 +674,7 @@ cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s) {
   if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
   MacArgs args = a;
   void* params[] = {&args};
+  note_launches(1);
   return cudaLaunchKernel(vi.fn, grid, dim3(vi.warps * 32), params,
                           mac_smem_bytes(variant, a.n_chan), s);
 }

@@ -512,17 +512,12 @@ namespace {
 constexpr size_t kScratchAlign = 256;
 constexpr size_t kScratchCap = size_t(3) << 30;
 size_t align_up(size_t p) { return (p + kScratchAlign - 1) & ~(kScratchAlign - 1); }
-// Bin-major output of one bin for the bins-innermost path (complex, the
-// larger of the two output kinds).
-size_t ybin_bytes(int n_series, int n_dm) {
-  return sizeof(float2) * static_cast<size_t>(n_series) * static_cast<size_t>(n_dm);
-}
-// Bins per block of the bins-innermost path: as many as 3 GiB of bin-major
-// output hold, at least one.
-int64_t block_bins(size_t per_bin, int64_t n_bins) {
-  int64_t kb = static_cast<int64_t>(kScratchCap / per_bin);
-  if (kb < 1) kb = 1;
-  return kb < n_bins ? kb : n_bins;
+// Scratch bytes per bin of a block: the bin-major spectra (when the caller's
+// are bins innermost) and the bin-major output (when the caller's is).
+size_t block_bytes_per_bin(bool x_in_place, bool y_in_place, int n_series, int n_chan, int n_dm,
+                           size_t y_elem) {
+  return (x_in_place ? 0 : sizeof(float2) * static_cast<size_t>(n_series) * n_chan) +
+         (y_in_place ? 0 : y_elem * static_cast<size_t>(n_series) * n_dm);
 }
 int tc_prec(int precision) {
   return precision == FDD_PREC_BF16_HILO ? kBf16HiLo
@@ -533,68 +528,96 @@ int tc_prec(int precision) {
 }  // namespace
 
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins) {
-  (void)n_chan;
-  // the per-bin FP16 maxima of every bin, then the bin-major output of a block
-  const size_t per_bin = ybin_bytes(n_series, n_dm);
+  // the per-bin FP16 maxima of every bin, then blocks of both bin-major sides
+  const size_t per_bin = block_bytes_per_bin(false, false, n_series, n_chan, n_dm, sizeof(float2));
+  int64_t kb = static_cast<int64_t>(kScratchCap / per_bin);
+  if (kb < 1) kb = 1;
+  if (kb > n_bins) kb = n_bins;
   return align_up(sizeof(unsigned int) * static_cast<size_t>(n_bins)) +
-         per_bin * static_cast<size_t>(block_bins(per_bin, n_bins)) + kScratchAlign;
+         per_bin * static_cast<size_t>(kb) + 2 * kScratchAlign;
 }
 
-size_t mac_tc_min_scratch(int n_series, int n_dm, int64_t n_bins) {
+size_t mac_tc_min_scratch(int n_series, int n_chan, int n_dm, int64_t n_bins) {
   return align_up(sizeof(unsigned int) * static_cast<size_t>(n_bins)) +
-         ybin_bytes(n_series, n_dm) + kScratchAlign;
+         block_bytes_per_bin(false, false, n_series, n_chan, n_dm, sizeof(float2)) +
+         2 * kScratchAlign;
 }
 
 cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
                           size_t scratch_bytes, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
-  if (a.x_series_stride != a.x_chan_stride * a.n_chan) return cudaErrorInvalidValue;
   const int prec = tc_prec(precision);
   if (prec < 0 || !scratch) return cudaErrorInvalidValue;
-  // scratch: [n_bins] per-bin maxima (FP16), then the bin-major output block
+  const bool x_in_place = a.x_bin_stride > 0;
+  const bool y_in_place = a.y_bin_stride > 0;
+  if (x_in_place && a.x_chan_stride != 1) return cudaErrorInvalidValue;
+  if (!x_in_place && a.x_series_stride != a.x_chan_stride * a.n_chan) return cudaErrorInvalidValue;
+  // scratch: [n_bins] per-bin maxima (FP16), then a block of bin-major
+  // spectra and a block of bin-major output, as the caller's layouts need
   unsigned int* absmax = reinterpret_cast<unsigned int*>(scratch);
   const size_t head = align_up(sizeof(unsigned int) * static_cast<size_t>(a.n_bins));
-  if (scratch_bytes < head + kScratchAlign) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (prec == kF16 && !a.absmax_ready) {
-    e = cudaMemsetAsync(absmax, 0, sizeof(unsigned int) * static_cast<size_t>(a.n_bins), s);
-    if (e != cudaSuccess) return e;
-    BinAbsmaxArgs t{a.X, a.x_chan_stride, static_cast<int64_t>(a.n_series) * a.n_chan, a.n_bins,
-                    absmax};
-    e = launch_bin_absmax(t, s);
-    if (e != cudaSuccess) return e;
-  }
-  // The kernel reads the spectra where they are (bins innermost).
-  MacArgs b = a;
-  b.x_bin_stride = 1;
-  b.bin_absmax = reinterpret_cast<const float*>(absmax);
-  if (a.y_bin_stride > 0) return launch_mac_tc_block(b, prec, n_sms, s);  // bin-major output
-
-  // Bins-innermost output: blocks of bins written bin-major into the scratch,
-  // then moved into the caller's layout.
   const size_t y_elem = a.out_kind == 2 ? sizeof(float) : sizeof(float2);
-  const size_t per_bin = y_elem * static_cast<size_t>(a.n_series) * a.n_dm;
-  const int64_t kb = static_cast<int64_t>((scratch_bytes - head - kScratchAlign) / per_bin);
+  cudaError_t e;
+  if (x_in_place && y_in_place) {
+    if (prec == kF16 && !a.absmax_ready) {
+      BinAbsmaxArgs t{a.X, a.x_bin_stride, a.n_series * a.n_chan, a.n_bins, absmax};
+      if ((e = launch_bin_absmax(t, s)) != cudaSuccess) return e;
+    }
+    MacArgs b = a;
+    b.bin_absmax = reinterpret_cast<const float*>(absmax);
+    return launch_mac_tc_block(b, prec, n_sms, s);
+  }
+  const size_t per_bin =
+      block_bytes_per_bin(x_in_place, y_in_place, a.n_series, a.n_chan, a.n_dm, y_elem);
+  if (scratch_bytes < head + 2 * kScratchAlign) return cudaErrorInvalidValue;
+  const int64_t kb = static_cast<int64_t>((scratch_bytes - head - 2 * kScratchAlign) / per_bin);
   if (kb < 1) return cudaErrorInvalidValue;
-  void* y_scratch = reinterpret_cast<char*>(scratch) + head;
+  char* blk = reinterpret_cast<char*>(scratch) + head;
+  float2* x_scratch = reinterpret_cast<float2*>(blk);
+  const size_t x_block = x_in_place ? 0 : sizeof(float2) * static_cast<size_t>(kb) * a.n_series *
+                                              a.n_chan;
+  void* y_scratch = blk + align_up(x_block);
+  const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
+  if (prec == kF16 && x_in_place && !a.absmax_ready) {
+    BinAbsmaxArgs t{a.X, a.x_bin_stride, a.n_series * a.n_chan, a.n_bins, absmax};
+    if ((e = launch_bin_absmax(t, s)) != cudaSuccess) return e;
+  }
   for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb) {
     const int nb = static_cast<int>((a.n_bins - k0) < kb ? (a.n_bins - k0) : kb);
-    MacArgs c = b;
-    c.X = a.X + k0;
+    MacArgs c = a;
     c.n_bins = nb;
     c.k_begin = a.k_begin + static_cast<int>(k0);
     c.bin_absmax = reinterpret_cast<const float*>(absmax + k0);
-    c.Y = y_scratch;
-    c.y_bin_stride = static_cast<int64_t>(a.n_series) * a.n_dm;
-    c.y_series_stride = a.n_dm;
-    c.y_dm_stride = 1;
-    e = launch_mac_tc_block(c, prec, n_sms, s);
-    if (e != cudaSuccess) return e;
-    BinUntransposeArgs u{y_scratch, static_cast<int>(y_elem), a.n_series, a.n_dm, nb,
-                         static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0),
-                         a.y_series_stride, a.y_dm_stride};
-    e = launch_bin_untranspose(u, s);
-    if (e != cudaSuccess) return e;
+    if (x_in_place) {
+      c.X = a.X + k0 * a.x_bin_stride;
+    } else {
+      if (prec == kF16) {
+        e = cudaMemsetAsync(absmax + k0, 0, sizeof(unsigned int) * static_cast<size_t>(nb), s);
+        if (e != cudaSuccess) return e;
+      }
+      BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, x_scratch,
+                         prec == kF16 ? absmax + k0 : nullptr};
+      if ((e = launch_bin_transpose(t, s)) != cudaSuccess) return e;
+      c.X = x_scratch;
+      c.x_bin_stride = rows;
+      c.x_series_stride = a.n_chan;
+      c.x_chan_stride = 1;
+    }
+    if (y_in_place) {
+      c.Y = static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0 * a.y_bin_stride);
+    } else {
+      c.Y = y_scratch;
+      c.y_bin_stride = static_cast<int64_t>(a.n_series) * a.n_dm;
+      c.y_series_stride = a.n_dm;
+      c.y_dm_stride = 1;
+    }
+    if ((e = launch_mac_tc_block(c, prec, n_sms, s)) != cudaSuccess) return e;
+    if (!y_in_place) {
+      BinUntransposeArgs u{y_scratch, static_cast<int>(y_elem), a.n_series, a.n_dm, nb,
+                           static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0),
+                           a.y_series_stride, a.y_dm_stride};
+      if ((e = launch_bin_untranspose(u, s)) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -614,6 +637,7 @@ static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cu
   else
     fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)
              : reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>);
+  note_launches(1);
   return cudaLaunchKernel(fn, dim3(grid),
                           dim3(kThreads), params, mac_tc_smem_bytes(), s);
 }

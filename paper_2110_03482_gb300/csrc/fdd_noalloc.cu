@@ -115,6 +115,7 @@ extern "C" fdd_status fdd_dedisperse_spectra_static(const fdd_params* p, const v
       blk.pc[i] = fdd::phase_const(fdd::delay_rate(*p, g, c0 + i), static_cast<double>(g.L),
                                    g.dm0, g.ddm);
     fill_table_kernel<<<1, 256, 0, s>>>(table, blk);
+    fdd::note_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(FDD_ERR_CUDA, cudaGetErrorString(e));
   }

@@ -123,38 +123,78 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float* __restrict__ 
   if (t0 + tid < n_keep) d[t0 + tid] = s[t0 + tid] * scale;
 }
 
-// Per bin, the largest |re| or |im| of complex rows in[r * in_stride + k]
-// (the FP16 tensor-core form scales each bin's data by a power of two chosen
-// from it).  Consecutive threads take consecutive bins, so every warp load is
-// one contiguous run of a row; blockIdx.y strides over the rows, and each
-// block ends with one atomic max per bin (non-negative floats order as their
-// bits; the caller zeroes absmax first).
+// 32 bins x 32 rows through shared memory: coalesced reads along bins,
+// coalesced writes along rows.  Rows beyond gridDim.y tiles are covered by a
+// grid-stride loop.  With absmax, each bin's largest |re| or |im| over the
+// rows this block read goes to absmax[bin] by one atomic max per bin.
+__global__ void __launch_bounds__(256) bin_transpose_kernel(const float2* __restrict__ in,
+                                                            int64_t in_stride, int64_t rows,
+                                                            int64_t k0, int n_bins,
+                                                            float2* __restrict__ out,
+                                                            int64_t out_bin_stride,
+                                                            unsigned int* __restrict__ absmax) {
+  __shared__ float2 tile[kTile][kTile + 1];
+  __shared__ float red[8][kTile];
+  const int kb0 = blockIdx.x * kTile;
+  float m = 0.f;  // bin kb0 + threadIdx.x, the rows this thread read
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTile; r0 < rows;
+       r0 += static_cast<int64_t>(gridDim.y) * kTile) {
+#pragma unroll
+    for (int i = threadIdx.y; i < kTile; i += 8) {
+      const int64_t r = r0 + i;
+      const int kb = kb0 + threadIdx.x;
+      if (r < rows && kb < n_bins) {
+        const float2 v = in[r * in_stride + k0 + kb];
+        tile[i][threadIdx.x] = v;
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = threadIdx.y; i < kTile; i += 8) {
+      const int kb = kb0 + i;
+      const int64_t r = r0 + threadIdx.x;
+      if (r < rows && kb < n_bins) out[static_cast<int64_t>(kb) * out_bin_stride + r] = tile[threadIdx.x][i];
+    }
+    __syncthreads();
+  }
+  if (absmax) {
+    red[threadIdx.y][threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+#pragma unroll
+      for (int j = 1; j < 8; ++j) m = fmaxf(m, red[j][threadIdx.x]);
+      const int kb = kb0 + threadIdx.x;
+      if (kb < n_bins && m > 0.f) atomicMax(absmax + kb, __float_as_uint(m));
+    }
+  }
+}
+
+
+// Per bin k, the largest |re| or |im| of its bin-major spectra
+// in[k * bin_stride + r], r < rows (the FP16 tensor-core form scales each
+// bin's data by a power of two chosen from it): one block per bin, a
+// coalesced sweep of the bin's rows and a block reduction; absmax[k] gets
+// the float's bits (non-negative floats order as their bits).
 __global__ void __launch_bounds__(256) bin_absmax_kernel(const float2* __restrict__ in,
-                                                         int64_t in_stride, int64_t rows,
-                                                         int n_bins,
+                                                         int64_t bin_stride, int rows,
                                                          unsigned int* __restrict__ absmax) {
-  const int kb = blockIdx.x * 256 + threadIdx.x;
-  if (kb >= n_bins) return;
-  const float2* p = in + kb;
-  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  int64_t r = blockIdx.y;
-  const int64_t step = gridDim.y;
-  for (; r + 3 * step < rows; r += 4 * step) {
-    const float2 v0 = __ldg(p + r * in_stride);
-    const float2 v1 = __ldg(p + (r + step) * in_stride);
-    const float2 v2 = __ldg(p + (r + 2 * step) * in_stride);
-    const float2 v3 = __ldg(p + (r + 3 * step) * in_stride);
-    m0 = fmaxf(m0, fmaxf(fabsf(v0.x), fabsf(v0.y)));
-    m1 = fmaxf(m1, fmaxf(fabsf(v1.x), fabsf(v1.y)));
-    m2 = fmaxf(m2, fmaxf(fabsf(v2.x), fabsf(v2.y)));
-    m3 = fmaxf(m3, fmaxf(fabsf(v3.x), fabsf(v3.y)));
+  __shared__ float red[8];
+  const float2* p = in + static_cast<int64_t>(blockIdx.x) * bin_stride;
+  float m = 0.f;
+  for (int r = threadIdx.x; r < rows; r += 256) {
+    const float2 v = __ldg(p + r);
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
-  for (; r < rows; r += step) {
-    const float2 v = __ldg(p + r * in_stride);
-    m0 = fmaxf(m0, fmaxf(fabsf(v.x), fabsf(v.y)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 1; i < 8; ++i) m = fmaxf(m, red[i]);
+    absmax[blockIdx.x] = __float_as_uint(m);
   }
-  const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-  if (m > 0.f) atomicMax(absmax + kb, __float_as_uint(m));
 }
 
 // Thread rows of the untranspose's 32 x 32 tiles (4: measured 5.7 TB/s on the
@@ -164,13 +204,13 @@ constexpr int kUntrRows = 4;
 template <typename T>
 __global__ void __launch_bounds__(32 * kUntrRows) bin_untranspose_kernel(const T* __restrict__ in,
                                                               int n_series, int n_dm, int n_bins,
-                                                              T* __restrict__ out,
+                                                              int64_t rows, T* __restrict__ out,
                                                               int64_t out_series_stride,
                                                               int64_t out_dm_stride) {
   __shared__ T tile[kTile][kTile + 1];
   const int kb0 = blockIdx.x * kTile;
   const int d_tiles = (n_dm + kTile - 1) / kTile;
-  const int64_t rows = static_cast<int64_t>(n_series) * n_dm;  // per bin
+  // (rows: elements between bins of the input)
   const int64_t n_tiles = static_cast<int64_t>(n_series) * d_tiles;
   for (int64_t q = blockIdx.y; q < n_tiles; q += gridDim.y) {
     const int sr = static_cast<int>(q / d_tiles);
@@ -200,32 +240,43 @@ cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s) 
   if (a.n_bins <= 0 || a.n_dm <= 0 || a.n_series <= 0) return cudaSuccess;
   const int64_t tiles = static_cast<int64_t>(a.n_series) * ((a.n_dm + kTile - 1) / kTile);
   dim3 grid((a.n_bins + kTile - 1) / kTile, static_cast<unsigned>(tiles < 65535 ? tiles : 65535));
+  note_launches(1);
+  const int64_t rows =
+      a.in_bin_stride > 0 ? a.in_bin_stride : static_cast<int64_t>(a.n_series) * a.n_dm;
   if (a.elem_bytes == 8)
     bin_untranspose_kernel<float2><<<grid, dim3(kTile, kUntrRows), 0, s>>>(
-        static_cast<const float2*>(a.in), a.n_series, a.n_dm, a.n_bins,
+        static_cast<const float2*>(a.in), a.n_series, a.n_dm, a.n_bins, rows,
         static_cast<float2*>(a.out), a.out_series_stride, a.out_dm_stride);
   else if (a.elem_bytes == 4)
     bin_untranspose_kernel<float><<<grid, dim3(kTile, kUntrRows), 0, s>>>(
-        static_cast<const float*>(a.in), a.n_series, a.n_dm, a.n_bins,
+        static_cast<const float*>(a.in), a.n_series, a.n_dm, a.n_bins, rows,
         static_cast<float*>(a.out), a.out_series_stride, a.out_dm_stride);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
+cudaError_t launch_bin_transpose(const BinTransposeArgs& a, cudaStream_t s) {
+  if (a.n_bins <= 0 || a.rows <= 0) return cudaSuccess;
+  const int64_t row_tiles = (a.rows + kTile - 1) / kTile;
+  dim3 grid((a.n_bins + kTile - 1) / kTile,
+            static_cast<unsigned>(row_tiles < 65535 ? row_tiles : 65535));
+  note_launches(1);
+  bin_transpose_kernel<<<grid, dim3(kTile, 8), 0, s>>>(
+      a.in, a.in_stride, a.rows, a.k0, a.n_bins, a.out,
+      a.out_bin_stride > 0 ? a.out_bin_stride : a.rows, a.absmax);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_absmax(const BinAbsmaxArgs& a, cudaStream_t s) {
   if (a.n_bins <= 0 || a.rows <= 0) return cudaSuccess;
-  const int bx = (a.n_bins + 255) / 256;
-  // enough blocks to keep every SM streaming, at most one row slice per row
-  int64_t by = (4 * 152 * 8 + bx - 1) / bx;
-  if (by > a.rows) by = a.rows;
-  if (by > 65535) by = 65535;
-  bin_absmax_kernel<<<dim3(bx, static_cast<unsigned>(by)), 256, 0, s>>>(a.in, a.in_stride, a.rows,
-                                                                        a.n_bins, a.absmax);
+  note_launches(1);
+  bin_absmax_kernel<<<a.n_bins, 256, 0, s>>>(a.in, a.bin_stride, a.rows, a.absmax);
   return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t s) {
+  note_launches(1);
   if (a.in_layout == FDD_LAYOUT_TIME_MAJOR) {
     dim3 grid(static_cast<unsigned>((a.L + kTile - 1) / kTile), (a.n_chan + kUnpC - 1) / kUnpC);
     dim3 block(kTile, 8);
@@ -274,6 +325,7 @@ cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
   // about 8 float4 groups per thread
   const int64_t blocks = (a.n_keep + 256 * 32 - 1) / (256 * 32);
   dim3 grid(static_cast<unsigned>(blocks < 1024 ? blocks : 1024), a.n_dm);
+  note_launches(1);
   scatter_kernel<<<grid, 256, 0, s>>>(a.src, a.src_stride, a.dst, a.dst_stride, a.n_keep,
                                       a.scale);
   return cudaGetLastError();

@@ -143,6 +143,7 @@ cudaError_t launch_tdd(const TddArgs& a, cudaStream_t s) {
   if (t_blocks > 65535) return cudaErrorInvalidConfiguration;
   dim3 grid((a.n_dm + kTdDms - 1) / kTdDms, static_cast<unsigned>(t_blocks));
   tdd_kernel<<<grid, kTdThreads, tdd_smem_bytes(a.win), s>>>(a);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -88,3 +88,35 @@ def filterbank(out, n_chan: int, n_rows: int, t0: int, seed: int, beam: int, *,
         raise RuntimeError(f"synth_philox_filterbank failed with code {rc}")
     if d_starts is not None:
         s.synchronize()  # d_starts is freed on return
+
+
+class BeamWindows:
+    """Fills raw device windows with rows of one workload's beams (the same
+    bytes as ``filterbank``), for streaming sources: the pulses' start tables
+    stay on the device for the object's lifetime."""
+
+    def __init__(self, beam_kwargs: list[dict]):
+        import torch
+        self.kw = []
+        for kw in beam_kwargs:
+            pulses = list(kw.get("pulses", ()))
+            d_starts = None
+            if pulses:
+                starts = np.stack([np.asarray(p[0], dtype=np.int64) for p in pulses])
+                d_starts = torch.from_numpy(starts).cuda()
+            widths = (ctypes.c_int * max(1, len(pulses)))(*[int(p[1]) for p in pulses])
+            amps = (ctypes.c_float * max(1, len(pulses)))(*[float(np.float32(p[2]))
+                                                           for p in pulses])
+            self.kw.append((kw, d_starts, widths, amps, len(pulses)))
+
+    def fill(self, beam: int, ptr: int, t0: int, n_rows: int, stream: int) -> None:
+        """Rows [t0, t0 + n_rows) of beam ``beam`` (time-major) at device address ptr."""
+        kw, d_starts, widths, amps, n_p = self.kw[beam]
+        rc = lib().synth_philox_filterbank(
+            ctypes.c_void_p(ptr), int(kw.get("u8", False)), n_rows, kw["n_chan"], t0,
+            kw["beam"], kw["seed"], float(np.float32(kw.get("mean", 0.0))),
+            float(np.float32(kw.get("sigma", 1.0))), float(philox.IH8_INV_SIGMA),
+            ctypes.c_void_p(d_starts.data_ptr() if d_starts is not None else 0), widths, amps,
+            n_p, ctypes.c_void_p(stream))
+        if rc != 0:
+            raise RuntimeError(f"synth_philox_filterbank failed with code {rc}")

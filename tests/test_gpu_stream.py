@@ -26,8 +26,10 @@ def built():
 
 
 def _workload(n_beams, output, n_dm, dtype="u8", chunk_len=2048, n_t=7000):
+    # (trials span DM 0 .. 90 whatever their count: delays stay below the chunk)
     return synth.Workload(name="stream", n_chan=40, band_lo_mhz=400.0, band_hi_mhz=500.0,
-                          t_samp_s=1e-3, n_t=n_t, dtype=dtype, dm0=0.0, ddm=1.0, n_dm=n_dm,
+                          t_samp_s=1e-3, n_t=n_t, dtype=dtype, dm0=0.0, ddm=90.0 / n_dm,
+                          n_dm=n_dm,
                           chunk_len=chunk_len, n_beams=n_beams, output=output,
                           pulses_per_beam=1,
                           noise_mean=128.0 if dtype == "u8" else 0.0,
