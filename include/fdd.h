@@ -82,7 +82,10 @@ typedef enum fdd_status {
                                warp: 512-trial blocks                           */
 #define FDD_MAC_Q_4X4 4     /* 4x4 lane tile, four bins per warp: 128-trial
                                blocks (small trial counts, ragged tails)        */
-#define FDD_MAC_VARIANTS 5
+#define FDD_MAC_G12_4X8 5   /* warp-specialised, 2048-trial blocks, three real
+                               products per complex MAC (Gauss's form): 4 phasor
+                               warps feed 8 MAC warps, two per bin              */
+#define FDD_MAC_VARIANTS 6
 #define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
 
 /* fdd_params.precision */

@@ -620,32 +620,60 @@ fdd_status transform(fdd_plan_s* P, const Io& io, int b, int64_t c, float2* X, c
   return FDD_OK;
 }
 
-// The 1/L scaling and valid-sample placement of DM batch [j0, j0 + nb) of
-// beam b, chunk c, from the inverse transforms in d_yt: into the output rows,
-// or into a block handed on.
-fdd_status place_time(fdd_plan_s* P, const Io& io, int b, int64_t c, int j0, int nb,
-                      cudaStream_t s) {
+// Whole rows: one chunk whose kept samples are the whole inverse transform
+// (an unchunked series whose length is the transform length).  Then the
+// phase-rotate-and-sum applies the 1/L scaling (exact for a power-of-two L)
+// and the inverse transforms write the output rows directly: no scatter.
+bool whole_rows(const fdd_plan_s* P) {
+  const fdd_info& g = P->info;
+  return g.n_chunks == 1 && g.out_len == g.fft_len / g.downsample;
+}
+
+// The inverse transforms (Eq. 6) of DM batch [j0, j0 + nb) of beam b, chunk c,
+// from bins-innermost spectra Y, then the 1/L scaling and valid-sample
+// placement (the discard rule of Sect. 2.2): into the output rows, or into a
+// block handed on.
+fdd_status inverse_and_place(fdd_plan_s* P, const Io& io, int b, int64_t c, int j0, int nb,
+                             float2* Y, cudaStream_t s) {
   const fdd_info& g = P->info;
   const int64_t Ls = g.fft_len / g.downsample, hop_o = g.hop / g.downsample;
   const int64_t keep = (g.out_len - c * hop_o) < hop_o ? (g.out_len - c * hop_o) : hop_o;
-  fdd::ScatterArgs sa{};
-  sa.src = P->d_yt;
-  sa.src_stride = Ls;
-  sa.n_dm = nb;
-  sa.n_keep = keep;
-  sa.scale = static_cast<float>(1.0 / static_cast<double>(g.fft_len));
+  const bool tail = P->has_c2r_tail && nb == P->c2r_tail_batch;
+  cufftHandle h = tail ? P->c2r_tail : P->c2r;
+  const bool direct = whole_rows(P);
   int k = -1;
+  float* dst;
+  int64_t dst_stride;
   if (io.d_out) {
-    sa.dst = static_cast<float*>(io.d_out) +
-             (static_cast<int64_t>(b) * io.n_dm + (j0 - io.dm_first)) * g.out_len + c * hop_o;
-    sa.dst_stride = g.out_len;
+    dst = static_cast<float*>(io.d_out) +
+          (static_cast<int64_t>(b) * io.n_dm + (j0 - io.dm_first)) * g.out_len + c * hop_o;
+    dst_stride = g.out_len;
   } else {
     fdd_status st = block_slot(P, io, s, &k);
     if (st != FDD_OK) return st;
-    sa.dst = static_cast<float*>(P->d_blk[k]);
-    sa.dst_stride = hop_o;
+    dst = static_cast<float*>(P->d_blk[k]);
+    dst_stride = hop_o;
   }
-  {
+  // (direct: rows of Ls samples at stride Ls, the C2R plan's own output
+  // layout; a batch of fewer trials than the plan's writes nb rows only when
+  // it is the tail plan, so a short batch goes through d_yt)
+  const bool plan_rows = tail || nb == g.dm_batch;
+  if (direct && plan_rows) {
+    StageTimer t(P, FDD_STAGE_C2R, s);
+    FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(Y), dst));
+  } else {
+    {
+      StageTimer t(P, FDD_STAGE_C2R, s);
+      FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(Y), P->d_yt));
+    }
+    fdd::ScatterArgs sa{};
+    sa.src = P->d_yt;
+    sa.src_stride = Ls;
+    sa.n_dm = nb;
+    sa.n_keep = keep;
+    sa.scale = direct ? 1.0f : static_cast<float>(1.0 / static_cast<double>(g.fft_len));
+    sa.dst = dst;
+    sa.dst_stride = dst_stride;
     StageTimer t(P, FDD_STAGE_SCATTER, s);
     FDD_CUDA(fdd::launch_scatter(sa, s));
   }
@@ -692,16 +720,12 @@ fdd_status run(fdd_plan_s* P, const Io& io, cudaStream_t s) {
           m.out_kind = 1;
           m.real_bin_a = 0;                           // DC and Nyquist of a real
           m.real_bin_b = static_cast<int>(Ls / 2);    // series: real parts only
+          m.scale = whole_rows(P) ? static_cast<float>(1.0 / static_cast<double>(g.fft_len)) : 1.0f;
           {
             StageTimer t(P, FDD_STAGE_MAC, s);
             FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, s));
           }
-          cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
-          {
-            StageTimer t(P, FDD_STAGE_C2R, s);
-            FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(P->d_Y), P->d_yt));
-          }
-          if ((st = place_time(P, io, b, c, j0, nb, s)) != FDD_OK) return st;
+          if ((st = inverse_and_place(P, io, b, c, j0, nb, P->d_Y, s)) != FDD_OK) return st;
         }
       } else {
         m.y_series_stride = 0;
@@ -790,11 +814,11 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
         m.out_kind = 1;
         m.real_bin_a = 0;
         m.real_bin_b = static_cast<int>(Ls / 2);
+        m.scale = whole_rows(P) ? static_cast<float>(1.0 / static_cast<double>(g.fft_len)) : 1.0f;
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
           FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s));
         }
-        cufftHandle h = (P->has_c2r_tail && nb == P->c2r_tail_batch) ? P->c2r_tail : P->c2r;
         for (int b = 0; b < p.n_beams; ++b) {
           // this beam's trials with bins innermost, then its inverse transforms
           fdd::BinUntransposeArgs u{P->d_Y + static_cast<int64_t>(b) * g.dm_batch, 8, 1, nb, ks,
@@ -804,11 +828,7 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
             StageTimer t(P, FDD_STAGE_TRANSPOSE, s);
             FDD_CUDA(fdd::launch_bin_untranspose(u, s));
           }
-          {
-            StageTimer t(P, FDD_STAGE_C2R, s);
-            FDD_CUFFT(cufftExecC2R(h, reinterpret_cast<cufftComplex*>(P->d_Yb), P->d_yt));
-          }
-          if ((st = place_time(P, io, b, c, j0, nb, s)) != FDD_OK) return st;
+          if ((st = inverse_and_place(P, io, b, c, j0, nb, P->d_Yb, s)) != FDD_OK) return st;
         }
       }
     } else {

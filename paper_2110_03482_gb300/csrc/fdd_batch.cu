@@ -449,7 +449,8 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   if (variant < 0 && autotune) {
     // Time each candidate on wave 0's real shapes (spectra and output scratch
     // are this plan's; values do not affect the timing).
-    const int cands[] = {FDD_MAC_W12_8X8, FDD_MAC_Q12_8X8, FDD_MAC_Q_4X8, FDD_MAC_Q_4X4};
+    const int cands[] = {FDD_MAC_W12_8X8, FDD_MAC_G12_4X8, FDD_MAC_Q12_8X8, FDD_MAC_Q_4X8,
+                         FDD_MAC_Q_4X4};
     const auto& w0 = B->waves[0];
     int64_t w0_out = 0;
     for (int i = 0; i < w0.count; ++i)

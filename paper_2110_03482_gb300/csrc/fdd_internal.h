@@ -56,6 +56,7 @@ enum MacVariant {
   MAC_Q_4x8 = FDD_MAC_Q_4X8,
   MAC_Q_8x8_512 = FDD_MAC_Q_8X8_512,
   MAC_Q_4x4 = FDD_MAC_Q_4X4,
+  MAC_G12_4x8 = FDD_MAC_G12_4X8,
   MAC_NUM_VARIANTS = FDD_MAC_VARIANTS
 };
 // One set of spectra in a batch (the batching form): its launch arguments

@@ -553,6 +553,249 @@ __global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* se
   }
 }
 
+// --------------------------------------- three-multiplication warp-specialised tile
+// The complex multiply-accumulate y += z p needs four real products; with
+//   A += zr pr,  B += zi pi,  C += (zr + zi)(pr + pi)
+// accumulated instead, Re y = A - B and Im y = C - A - B at the end: three
+// real products per complex MAC (Gauss's three-multiplication form), the
+// sums zr + zi and pr + pi being formed once per phasor by the producers.
+// Its FP32 rounding is that of the four-product form to within a few
+// percent (every term is of the same size as a product of the four-product
+// form).  The tile: producer warp q evaluates, for bin q of the CTA's four
+// and each channel, the 64 Z_a = X Q_a and 32 P_b of a 2048-trial block (T =
+// 32), as planes zr, zi, zs and pr, pi, ps; consumer warps 2q and 2q + 1 own
+// the a's 0..31 and 32..63 of that bin, each lane a 4 x 8 tile of (a, b)
+// with the three accumulators as pairs along b: 48 paired FMAs per lane and
+// channel for 32 complex MACs.
+template <int kCh, int kStages>
+struct G3 {
+  static constexpr int kA = 64;                // a's per bin (Z_a)
+  static constexpr int kT = 32;                // b's per bin (P_b): T
+  static constexpr int kDms = kA * kT;         // 2048 trials per bin
+  static constexpr int kBins = 4;              // bins per CTA (one producer warp each)
+  static constexpr int kCons = 2 * kBins;      // consumer warps
+  static constexpr int kProd = kBins;          // producer warps
+  static constexpr int kThreads = 32 * (kCons + kProd);
+  static constexpr int kGFL = 3 * kA + 3 * kT;  // floats per (bin, channel): zr zi zs pr pi ps
+  static constexpr int kStageFloats = kCh * kBins * kGFL;
+  static constexpr size_t kBarBytes = (2 * kStages * 8 + 4 + 15) / 16 * 16;
+  static constexpr size_t kSwapBytes = kBarBytes + sizeof(float) * size_t(kStages) * kStageFloats;
+};
+
+// One work item of the three-multiplication tile: the CTA's four bins from
+// local bin bin_tile * 4 and trials dm_block * 2048 + .. of one set of
+// spectra; ring stages and barrier phases continue from iteration it0.
+// Returns false after a timeout.
+template <int kCh, int kStages>
+__device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs, float* stages,
+                                        uint64_t* full, uint64_t* empty,
+                                        volatile int* abort_flag, int bin_tile, int dm_block,
+                                        int series, uint32_t it0) {
+  using Ly = G3<kCh, kStages>;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n_iter = (a.n_chan + kCh - 1) / kCh;
+  const int jblk = dm_block * Ly::kDms;
+  bool ok = true;
+
+  if (warp >= Ly::kCons) {
+    // ------------------------------------------------------------ producers
+    const int q = warp - Ly::kCons;               // the CTA's bin q
+    const int k = bin_tile * Ly::kBins + q;
+    const int kl = k < a.n_bins ? k : 0;          // idle bins evaluate local bin 0, unused
+    const uint32_t ku = static_cast<uint32_t>(a.k_begin + kl);
+    const uint32_t m_z0 = ku * static_cast<uint32_t>(a.j_begin + jblk + lane * Ly::kT);
+    const uint32_t m_z1 = ku * static_cast<uint32_t>(a.j_begin + jblk + (lane + 32) * Ly::kT);
+    const uint32_t m_p = ku * static_cast<uint32_t>(lane);
+    const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
+    const int64_t xs = a.x_chan_stride;
+    float2 xn[kCh];
+#pragma unroll
+    for (int ch = 0; ch < kCh; ++ch)
+      xn[ch] = ch < a.n_chan ? __ldg(xp + ch * xs) : make_float2(0.f, 0.f);
+    for (int it = 0; it < n_iter; ++it) {
+      const uint32_t g = it0 + it;
+      const int s = g % kStages;
+      float2 x[kCh];
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) {
+        x[ch] = xn[ch];
+        const int c = (it + 1) * kCh + ch;  // prefetch the next stage's X
+        xn[ch] = c < a.n_chan ? __ldg(xp + c * xs) : make_float2(0.f, 0.f);
+      }
+      ok = __all_sync(0xffffffffu,
+                      dev::mbar_wait(&empty[s], ((g / kStages) & 1) ^ 1, abort_flag));
+      if (!ok) break;
+      float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) {
+        const int c = it * kCh + ch;
+        if (c < a.n_chan) {
+          const PhaseConst p = pcs[c];
+          const uint32_t base = top32_mul(ku, p.u_lo, p.u_hi);
+          const float2 w0 = unit_phasor(base + top32_mul(m_z0, p.v_lo, p.v_hi));
+          const float2 w1 = unit_phasor(base + top32_mul(m_z1, p.v_lo, p.v_hi));
+          const float2 wp = unit_phasor(top32_mul(m_p, p.v_lo, p.v_hi));
+          const float2 xv = x[ch];
+          const float z0r = xv.x * w0.x - xv.y * w0.y, z0i = xv.x * w0.y + xv.y * w0.x;
+          const float z1r = xv.x * w1.x - xv.y * w1.y, z1i = xv.x * w1.y + xv.y * w1.x;
+          float* grp = st + ch * Ly::kBins * Ly::kGFL;
+          grp[lane] = z0r;
+          grp[Ly::kA + lane] = z0i;
+          grp[2 * Ly::kA + lane] = z0r + z0i;
+          grp[32 + lane] = z1r;
+          grp[Ly::kA + 32 + lane] = z1i;
+          grp[2 * Ly::kA + 32 + lane] = z1r + z1i;
+          grp[3 * Ly::kA + lane] = wp.x;
+          grp[3 * Ly::kA + Ly::kT + lane] = wp.y;
+          grp[3 * Ly::kA + 2 * Ly::kT + lane] = wp.x + wp.y;
+        }
+      }
+      if (!a.test_withhold) dev::mbar_arrive_warp(&full[s]);
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int q = warp >> 1;                      // the CTA's bin
+    const int h = warp & 1;                       // a's 32 h .. 32 h + 31
+    const int k = bin_tile * Ly::kBins + q;       // local bin
+    const int ga = lane >> 2;                     // a = 32 h + 4 ga + i
+    const int gb = lane & 3;                      // b = 8 gb + j
+    float2 A[4][4], B[4][4], C[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) A[i][m] = B[i][m] = C[i][m] = make_float2(0.f, 0.f);
+    for (int it = 0; it < n_iter; ++it) {
+      const uint32_t g = it0 + it;
+      const int s = g % kStages;
+      ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
+      if (!ok) break;
+      const float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
+      const int nc = a.n_chan - it * kCh;
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) {
+        if (ch < nc) {
+          const float* grp = st + ch * Ly::kBins * Ly::kGFL;
+          const float4 zr = *reinterpret_cast<const float4*>(grp + 32 * h + 4 * ga);
+          const float4 zi = *reinterpret_cast<const float4*>(grp + Ly::kA + 32 * h + 4 * ga);
+          const float4 zs = *reinterpret_cast<const float4*>(grp + 2 * Ly::kA + 32 * h + 4 * ga);
+          const float* pp = grp + 3 * Ly::kA + 8 * gb;
+          const float4 pr0 = *reinterpret_cast<const float4*>(pp);
+          const float4 pr1 = *reinterpret_cast<const float4*>(pp + 4);
+          const float4 pi0 = *reinterpret_cast<const float4*>(pp + Ly::kT);
+          const float4 pi1 = *reinterpret_cast<const float4*>(pp + Ly::kT + 4);
+          const float4 ps0 = *reinterpret_cast<const float4*>(pp + 2 * Ly::kT);
+          const float4 ps1 = *reinterpret_cast<const float4*>(pp + 2 * Ly::kT + 4);
+          const float2 pr[4] = {make_float2(pr0.x, pr0.y), make_float2(pr0.z, pr0.w),
+                                make_float2(pr1.x, pr1.y), make_float2(pr1.z, pr1.w)};
+          const float2 pi[4] = {make_float2(pi0.x, pi0.y), make_float2(pi0.z, pi0.w),
+                                make_float2(pi1.x, pi1.y), make_float2(pi1.z, pi1.w)};
+          const float2 ps[4] = {make_float2(ps0.x, ps0.y), make_float2(ps0.z, ps0.w),
+                                make_float2(ps1.x, ps1.y), make_float2(ps1.z, ps1.w)};
+          const float zrv[4] = {zr.x, zr.y, zr.z, zr.w};
+          const float ziv[4] = {zi.x, zi.y, zi.z, zi.w};
+          const float zsv[4] = {zs.x, zs.y, zs.z, zs.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 r2 = make_float2(zrv[i], zrv[i]);
+            const float2 i2 = make_float2(ziv[i], ziv[i]);
+            const float2 s2 = make_float2(zsv[i], zsv[i]);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              A[i][m] = __ffma2_rn(r2, pr[m], A[i][m]);
+              B[i][m] = __ffma2_rn(i2, pi[m], B[i][m]);
+              C[i][m] = __ffma2_rn(s2, ps[m], C[i][m]);
+            }
+          }
+        }
+      }
+      dev::mbar_arrive_warp(&empty[s]);
+    }
+    if (ok && k < a.n_bins) {
+      const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float av = e ? A[i][m].y : A[i][m].x;
+            const float bv = e ? B[i][m].y : B[i][m].x;
+            const float cv = e ? C[i][m].y : C[i][m].x;
+            const int jl = jblk + (32 * h + 4 * ga + i) * Ly::kT + 8 * gb + 2 * m + e;
+            if (jl < a.n_dm) {
+              const float re = (av - bv) * a.scale;
+              const float im = real_only ? 0.f : (cv - av - bv) * a.scale;
+              const int64_t o = static_cast<int64_t>(series) * a.y_series_stride +
+                                static_cast<int64_t>(jl) * a.y_dm_stride + k;
+              if (a.out_kind == 2)
+                static_cast<float*>(a.Y)[o] = re * re + im * im;
+              else
+                static_cast<float2*>(a.Y)[o] = make_float2(re, im);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (!ok) {
+    *abort_flag = 1;
+    if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+  }
+  return ok;
+}
+
+template <int kCh, int kStages>
+__global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1) mac_g3_kernel(const MacArgs a) {
+  using Ly = G3<kCh, kStages>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WsSmem<Ly> sm;
+  sm.template init<kStages>(smem_raw, a.n_chan, Ly::kCons, Ly::kProd);
+  for (int i = threadIdx.x; i < a.n_chan; i += blockDim.x) sm.pcs[i] = a.pc[i];
+  __syncthreads();
+  g3_item<kCh, kStages>(a, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag, blockIdx.x,
+                        blockIdx.y, blockIdx.z, 0u);
+}
+
+// Persistent form of the three-multiplication tile over a batch of spectra
+// sets (the batching form), as mac_ws_batch_kernel.
+template <int kCh, int kStages>
+__global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
+    mac_g3_batch_kernel(const BatchSet* sets, int n_sets, int64_t n_items,
+                        unsigned long long* counter) {
+  using Ly = G3<kCh, kStages>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long item_s;
+  const int n_chan = sets[0].args.n_chan;  // common to the batch
+  WsSmem<Ly> sm;
+  sm.template init<kStages>(smem_raw, n_chan, Ly::kCons, Ly::kProd);
+  int cur = -1;
+  uint32_t it0 = 0;
+  const uint32_t n_iter = static_cast<uint32_t>((n_chan + kCh - 1) / kCh);
+  while (true) {
+    if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(counter, 1ull));
+    __syncthreads();  // also: every stage of the previous item has been read
+    const long long item = item_s;
+    if (item >= n_items || *sm.abort_flag) break;
+    int lo = 0, hi = n_sets - 1;  // last set with item_begin <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sets[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    const BatchSet& bs = sets[lo];
+    if (lo != cur) {
+      for (int i = threadIdx.x; i < n_chan; i += blockDim.x) sm.pcs[i] = bs.args.pc[i];
+      cur = lo;
+    }
+    __syncthreads();  // phase table ready; item_s read by every thread
+    const long long local = item - bs.item_begin;
+    g3_item<kCh, kStages>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
+                          static_cast<int>(local / bs.n_dm_blocks),
+                          static_cast<int>(local % bs.n_dm_blocks), 0, it0);
+    it0 += n_iter;
+  }
+}
+
 // ----------------------------------------------------------------- variants
 struct VariantInfo {
   const void* fn;
@@ -582,8 +825,19 @@ VariantInfo info_ws() {
   return vi;
 }
 
+template <int kCh, int kSt>
+VariantInfo info_g3() {
+  using Ly = G3<kCh, kSt>;
+  VariantInfo vi{reinterpret_cast<const void*>(&mac_g3_kernel<kCh, kSt>), Ly::kDms, 1,
+                 Ly::kSwapBytes, Ly::kCons + Ly::kProd,
+                 reinterpret_cast<const void*>(&mac_g3_batch_kernel<kCh, kSt>)};
+  vi.bin_warps = Ly::kBins;
+  return vi;
+}
+
 VariantInfo variant_info(int v) {
   switch (v) {
+    case MAC_G12_4x8: return info_g3<4, 3>();
     case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, 12>();
     case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>>();
     case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>>();

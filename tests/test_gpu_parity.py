@@ -122,10 +122,10 @@ def test_kernel_dm_subrange_and_large_phases():
 
 
 @pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_Q_4X4 + 1, fdd.FDD_MAC_Q12_8X8 + 1,
-                                     fdd.FDD_MAC_Q_8X8_512 + 1])
+                                     fdd.FDD_MAC_G12_4X8 + 1, fdd.FDD_MAC_Q_8X8_512 + 1])
 def test_kernel_bin_windows_equal_the_whole_range(variant):
     """A window of bins (absolute phases k_begin + k) gives bit for bit the
-    columns of the whole-range call, for the default and three other tiles."""
+    columns of the whole-range call, for the default and four other tiles."""
     n_chan, L, n_dm = 48, 4096, 1100
     w = _small_workload(n_chan, L, 0.5 * np.arange(n_dm))
     K = L // 2 + 1
