@@ -31,6 +31,20 @@ notes as well):
   hop = L - D_max, the valid output is n_out = n_t - D_max samples, and chunk
   c reads x[c*hop, c*hop + L) (zero beyond n_t) and keeps its first hop
   output samples (the discard rule of Sect. 2.2 applied per chunk).
+* Spin-frequency-dependent DM grids (Sect. 2.3, Eqs. 8 and 9: the paper
+  gives the scaled grid and says the result is to be re-sampled to the wanted
+  trials, with no rule, and leaves the tolerable DM contraction open).  Bins
+  are taken in groups of G consecutive bins from a first grouped bin
+  K_min = max(1, ceil((G - 1) / eps)) on (bin 0, whose phasors are 1 at every
+  DM, has no scaled grid), so that within a group the DM contraction
+  1 - k / k_ref stays below eps; each group uses the phasors of its highest
+  bin k_ref (Eq. 9 with f_s0 at k_ref), which for bin k evaluate Eq. 7 at the
+  trial DMs DM'_j k_ref / k (Eq. 8), DM'_j = DM'_0 + j dDM over the scaled
+  grid j = 0 .. n_s - 1 (DM'_0 = DM_0 + j_lo dDM reaches below DM_0 far
+  enough, j_lo = 0 for DM_0 = 0 else floor(-eps DM_0 / dDM) - 1).  Bin k is
+  re-sampled to trial t of the plan's grid by linear interpolation along the
+  scaled trial axis at x = (DM_t k / k_ref - DM'_0) / dDM.  Bins below K_min
+  follow Eq. 7 exactly.
 * Down-sampling by a shorter inverse transform (Sect. 2.2, last paragraph:
   the paper names the technique, not its details).  A factor f (a power of
   two dividing L/2) keeps the bins k <= L/(2f) of the dedispersed spectrum
@@ -90,6 +104,11 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_fft_r2c_many.restype = ctypes.c_int
     lib.oracle_fdd_bins.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _i64p, _dp,
                                     ctypes.c_int, _dp, _dp]
+    lib.oracle_fdd_bins_spin.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _i64p,
+                                         _dp, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int64, ctypes.c_int64, _dp]
+    lib.oracle_fdd_bins_spin.restype = ctypes.c_int
     lib.oracle_irdft.argtypes = [ctypes.c_int64, _dp, _dp]
     lib.oracle_irfft_many.argtypes = [ctypes.c_int64, ctypes.c_int64, _dp, _dp]
     lib.oracle_irfft_many.restype = ctypes.c_int
@@ -200,6 +219,65 @@ def fdd_bins(X, bins, L: int, d) -> np.ndarray:
     xi[1::2] = X.imag.ravel()
     out = np.empty(2 * n_dm * nq, dtype=np.float64)
     lib().oracle_fdd_bins(n_chan, int(L), nq, _iptr(b), _ptr(xi), n_dm, _ptr(d), _ptr(out))
+    return (out[0::2] + 1j * out[1::2]).reshape(n_dm, nq)
+
+
+# --------------------------------------------------------------------------
+# Sect. 2.3, Eqs. 8 and 9 (reading in the module header)
+# --------------------------------------------------------------------------
+@dataclass
+class SpinGroups:
+    G: int          # bins per group
+    eps: float      # largest relative DM contraction within a group
+    k_min: int      # first grouped bin (bins below follow Eq. 7)
+    j_lo: int       # the scaled grid starts at trial j_lo of the plan's grid
+    n_s: int        # trials of the scaled grid
+
+
+def spin_groups(K: int, dm0: float, ddm: float, n_dm: int, G: int, eps: float) -> SpinGroups:
+    """Grouping of bins 0 .. K-1 for the spin-frequency-dependent DM grid."""
+    if G < 1 or not eps > 0:
+        raise ValueError("G >= 1 and eps > 0")
+    # (bin 0 never groups: its phasors are 1 for every DM, Eq. 8 has no grid)
+    k_min = min(K, max(1, int(math.ceil((G - 1) / eps))))
+    j_lo = 0 if dm0 == 0 else int(math.floor(-eps * dm0 / ddm)) - 1
+    return SpinGroups(G, eps, k_min, j_lo, n_dm - j_lo)
+
+
+def spin_reference_bin(k: int, K: int, sg: SpinGroups) -> int:
+    """k_ref of bin k: the highest bin of its group (k itself below k_min)."""
+    if k < sg.k_min:
+        return k
+    g = (k - sg.k_min) // sg.G
+    return min(sg.k_min + (g + 1) * sg.G, K) - 1
+
+
+def fdd_bins_spin(X, bins, L: int, nu_mhz, dm0: float, ddm: float, n_dm: int,
+                  t_samp_s: float, G: int, eps: float, k_dm: float = K_DM_PAPER,
+                  nu_ref_mhz: float | None = None) -> np.ndarray:
+    """Eq. 7 on the spin-frequency-dependent DM grids of Eqs. 8, 9, re-sampled
+    to the trials dm0 + t ddm (t < n_dm) by linear interpolation; Y[t, q] for
+    the spectra X[c, q] of the bins `bins` (module header)."""
+    X = np.ascontiguousarray(X, dtype=np.complex128)
+    n_chan, nq = X.shape
+    b = np.ascontiguousarray(bins, dtype=np.int64)
+    assert b.size == nq
+    K = L // 2 + 1
+    if n_dm < 2 or not ddm > 0:
+        raise ValueError("the scaled grid needs at least two trials of positive step")
+    sg = spin_groups(K, dm0, ddm, n_dm, G, eps)
+    dm0s = dm0 + sg.j_lo * ddm
+    d_s = delays(nu_mhz, dm0s + ddm * np.arange(sg.n_s), t_samp_s, k_dm, nu_ref_mhz)
+    d_t = delays(nu_mhz, dm0 + ddm * np.arange(n_dm), t_samp_s, k_dm, nu_ref_mhz)
+    xi = np.empty(2 * X.size, dtype=np.float64)
+    xi[0::2] = X.real.ravel()
+    xi[1::2] = X.imag.ravel()
+    out = np.empty(2 * n_dm * nq, dtype=np.float64)
+    rc = lib().oracle_fdd_bins_spin(n_chan, int(L), nq, _iptr(b), _ptr(xi), n_dm, _ptr(d_t),
+                                    sg.n_s, _ptr(d_s), float(dm0), float(ddm), float(dm0s),
+                                    int(sg.G), int(sg.k_min), _ptr(out))
+    if rc != 0:
+        raise ValueError("interpolation point outside the scaled grid")
     return (out[0::2] + 1j * out[1::2]).reshape(n_dm, nq)
 
 

@@ -14,6 +14,8 @@
  *   oracle_dft_r2c    Sect. 2.2, Eq. 3   forward Fourier transform, direct sum
  *   oracle_fft        Sect. 2.2, Eq. 3   the same transform by radix-2 FFT
  *   oracle_fdd_bins   Sect. 2.2, Eqs. 4 and 7   phasors and sum over channels
+ *   oracle_fdd_bins_spin  Sect. 2.3, Eqs. 8, 9   the same on spin-frequency-
+ *                     dependent DM grids, re-sampled to the plan's trials
  *   oracle_irdft      Sect. 2.2, Eq. 6   inverse transform back to time
  *   oracle_tdd        Sect. 2.1, Eq. 2   brute-force time-domain shift-and-sum
  *
@@ -175,6 +177,75 @@ void oracle_fdd_bins(int n_chan, int64_t L, int64_t nq, const int64_t* bins,
       Y[2 * ((int64_t)j * nq + q) + 1] = im;
     }
   }
+}
+
+/*
+ * Sect. 2.3, Eqs. 8 and 9: Eq. 7 on spin-frequency-dependent DM grids, the
+ * reading of the Python driver's header.  Bins below k_min follow Eq. 7 at
+ * the plan's delays d_t (n_dm x n_chan).  Bin k >= k_min belongs to the group
+ * (k - k_min) / G, whose highest bin k_ref supplies the phasors: over the
+ * scaled grid (delays d_s, n_s x n_chan, of the DMs dm0s + j ddm)
+ *   ys[j] = sum_c exp(+2 pi i k_ref d_s[j][c] / L) X[c][q],
+ * which is Eq. 7 of bin k at the DMs (dm0s + j ddm) k_ref / k (Eq. 8); then
+ * trial t of the plan's grid (DM_t = dm0 + t ddm) is the linear
+ * interpolation of ys at x = (DM_t k / k_ref - dm0s) / ddm.
+ * ys is scratch of 2 n_s doubles per thread (allocated here).
+ */
+/* One sum of Eq. 7 for phasor frequency kk (in bins) and one row of delays. */
+static void spin_sum(double kk, const double* d_row, int n_chan, int64_t L, const double* X,
+                     int64_t q, int64_t nq, double* out) {
+  double sr = 0.0, si = 0.0;
+  for (int c = 0; c < n_chan; ++c) {
+    double ph = kk * d_row[c] / (double)L;
+    ph -= floor(ph);
+    const double cr = cos(TWO_PI * ph), ci = sin(TWO_PI * ph);
+    const double a = X[2 * ((int64_t)c * nq + q)], b = X[2 * ((int64_t)c * nq + q) + 1];
+    sr += cr * a - ci * b;
+    si += cr * b + ci * a;
+  }
+  out[0] = sr;
+  out[1] = si;
+}
+
+int oracle_fdd_bins_spin(int n_chan, int64_t L, int64_t nq, const int64_t* bins,
+                         const double* X, int n_dm, const double* d_t, int n_s,
+                         const double* d_s, double dm0, double ddm, double dm0s, int64_t G,
+                         int64_t k_min, double* Y) {
+  const int64_t K = L / 2 + 1;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+  for (int64_t q = 0; q < nq; ++q) {
+    const int64_t k = bins[q];
+    if (k < k_min) {
+      for (int j = 0; j < n_dm; ++j)
+        spin_sum((double)k, d_t + (int64_t)j * n_chan, n_chan, L, X, q, nq,
+                 Y + 2 * ((int64_t)j * nq + q));
+      continue;
+    }
+    int64_t k_ref = k_min + ((k - k_min) / G + 1) * G - 1;
+    if (k_ref > K - 1) k_ref = K - 1;
+    double* ys = (double*)malloc(sizeof(double) * 2 * (size_t)n_s);
+    if (!ys) {
+      bad = 1;
+      continue;
+    }
+    for (int j = 0; j < n_s; ++j)
+      spin_sum((double)k_ref, d_s + (int64_t)j * n_chan, n_chan, L, X, q, nq, ys + 2 * j);
+    for (int t = 0; t < n_dm; ++t) {
+      const double x = ((dm0 + t * ddm) * ((double)k / (double)k_ref) - dm0s) / ddm;
+      int64_t m = (int64_t)floor(x);
+      double delta = x - (double)m;
+      if (m < 0 || m > n_s - 1) {
+        bad = 1;
+        m = m < 0 ? 0 : n_s - 1;
+      }
+      const int64_t m1 = m + 1 < n_s ? m + 1 : n_s - 1;
+      Y[2 * ((int64_t)t * nq + q)] = (1.0 - delta) * ys[2 * m] + delta * ys[2 * m1];
+      Y[2 * ((int64_t)t * nq + q) + 1] = (1.0 - delta) * ys[2 * m + 1] + delta * ys[2 * m1 + 1];
+    }
+    free(ys);
+  }
+  return bad ? -1 : 0;
 }
 
 /*

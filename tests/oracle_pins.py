@@ -257,6 +257,77 @@ def pin_overlap_save_equals_linear_tdd():
     assert np.max(np.abs(y - ref)) < 1e-12
 
 
+# ---------------------------------------------------------------- Sect. 2.3, Eqs. 8, 9
+def _spin_case(seed=5, n_chan=24, L=4096, dm0=3.0, ddm=0.25, n_dm=48):
+    rng = _rng(seed)
+    nu = oracle.channel_centres(n_chan, 1150.0, 12.5)
+    bins = np.array([0, 1, 37, 499, 500, 501, 1023, 1500, 2047, 2048])
+    X = rng.standard_normal((n_chan, bins.size)) + 1j * rng.standard_normal((n_chan, bins.size))
+    d = oracle.delays(nu, dm0 + ddm * np.arange(n_dm), 1e-3)
+    return nu, bins, X, d, L, dm0, ddm, n_dm
+
+
+def pin_spin_groups_of_one_are_eq7():
+    """Groups of one bin: every bin is its own reference (Eq. 8 scales by
+    k/k = 1), so the scaled grid is the plan's grid, shifted below DM_0 > 0,
+    and the result is Eq. 7 exactly (brute-force reference)."""
+    nu, bins, X, d, L, dm0, ddm, n_dm = _spin_case()
+    ref = oracle.fdd_bins(X, bins, L, d)
+    got = oracle.fdd_bins_spin(X, bins, L, nu, dm0, ddm, n_dm, 1e-3, G=1, eps=0.01)
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def pin_spin_group_top_bins_are_eq7():
+    """The highest bin of a group is its own reference: Eq. 7 exactly there;
+    bins below the first group are Eq. 7 too; other bins differ."""
+    nu, bins, X, d, L, dm0, ddm, n_dm = _spin_case()
+    K = L // 2 + 1
+    G, eps = 16, 0.05
+    sg = oracle.spin_groups(K, dm0, ddm, n_dm, G, eps)
+    assert sg.k_min == 300 and sg.j_lo < 0
+    ref = oracle.fdd_bins(X, bins, L, d)
+    got = oracle.fdd_bins_spin(X, bins, L, nu, dm0, ddm, n_dm, 1e-3, G=G, eps=eps)
+    for q, k in enumerate(bins):
+        top = k < sg.k_min or (k - sg.k_min) % G == G - 1 or k == K - 1
+        err = np.max(np.abs(got[:, q] - ref[:, q])) / np.max(np.abs(ref[:, q]))
+        if top:
+            assert err <= 1e-11, (k, err)
+        else:
+            assert err > 1e-9, (k, err)
+
+
+def pin_spin_single_tone_within_interpolation_bound():
+    """A unit tone in one channel: Eq. 7 of bin k at DM is exp(i a_k DM) and
+    the scaled grid samples exp(i a_ref DM') at DM' = DM'_0 + j dDM, the same
+    exponential of DM k_ref / k.  Linear interpolation between unit-spaced
+    samples of exp(i b x) errs by at most b^2 / 8 (the textbook bound
+    h^2 max|f''| / 8), b = a_ref dDM the phase step of the scaled grid; half
+    way between samples the error comes within a few percent of it."""
+    n_chan, L, dm0, ddm, n_dm = 8, 8192, 0.0, 0.05, 400
+    nu = oracle.channel_centres(n_chan, 1150.0, 25.0)
+    K = L // 2 + 1
+    G, eps = 32, 0.02
+    c1 = 0  # the lowest channel: the largest delay
+    bins = np.array([2500, 2517, 3100, 3131, 4000])
+    X = np.zeros((n_chan, bins.size), dtype=np.complex128)
+    X[c1, :] = 1.0
+    d = oracle.delays(nu, dm0 + ddm * np.arange(n_dm), 1e-3)
+    exact = oracle.fdd_bins(X, bins, L, d)
+    got = oracle.fdd_bins_spin(X, bins, L, nu, dm0, ddm, n_dm, 1e-3, G=G, eps=eps)
+    rate = oracle.delays(nu, [1.0], 1e-3)[0, c1]  # samples of delay per unit DM
+    sg = oracle.spin_groups(K, dm0, ddm, n_dm, G, eps)
+    worst = 0.0
+    for q, k in enumerate(bins):
+        k_ref = oracle.spin_reference_bin(int(k), K, sg)
+        b = 2 * np.pi * k_ref * rate * ddm / L
+        bound = b * b / 8
+        err = np.abs(got[:, q] - exact[:, q])
+        assert np.max(err) <= bound * (1 + 1e-6) + 1e-12, (k, np.max(err), bound)
+        if k != k_ref:
+            worst = max(worst, np.max(err) / bound)
+    assert worst > 0.9, worst
+
+
 def pin_downsampled_inverse_f1_is_fdd_time():
     """A shortening factor of 1 is the plain inverse (whole series and chunked)."""
     rng = _rng(41)
@@ -305,6 +376,9 @@ def pin_downsampled_chunks_tile_the_grid():
 
 
 ALL_PINS = [
+    pin_spin_groups_of_one_are_eq7,
+    pin_spin_group_top_bins_are_eq7,
+    pin_spin_single_tone_within_interpolation_bound,
     pin_downsampled_inverse_f1_is_fdd_time,
     pin_downsampled_inverse_decimates_band_limited_series,
     pin_downsampled_chunks_tile_the_grid,

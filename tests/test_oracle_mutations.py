@@ -40,6 +40,14 @@ MUTATIONS = [
     ("tdd_delays_instead", "int64_t t = n + shift[(int64_t)j * n_chan + c];",
      "int64_t t = n - shift[(int64_t)j * n_chan + c];"),
     ("tdd_wrong_modulus", "t %= n_t;", "t %= (n_t - 1);"),
+    ("spin_phasor_of_bin_not_reference",
+     "spin_sum((double)k_ref, d_s + (int64_t)j * n_chan",
+     "spin_sum((double)k, d_s + (int64_t)j * n_chan"),
+    ("spin_ratio_inverted", "((double)k / (double)k_ref)", "((double)k_ref / (double)k)"),
+    ("spin_nearest_not_interpolated", "double delta = x - (double)m;",
+     "double delta = 0.0;"),
+    ("spin_grid_origin_ignored", "- dm0s) / ddm;", "- dm0) / ddm;"),
+    ("spin_phase_drops_cross_term", "sr += cr * a - ci * b;", "sr += cr * a;"),
 ]
 
 
