@@ -128,6 +128,18 @@ typedef struct fdd_params {
                              the series low-passed to those bins and sampled every
                              f native samples; with chunking the hop is rounded
                              down to a multiple of f.  L must be divisible by 2f. */
+  int32_t spin_group;     /* tensor-core form, one beam: 0 (off), 16 or 32 -- the
+                             spin-frequency-dependent DM grids of Sect. 2.3
+                             (Eqs. 8, 9): bins from k_min on are taken in groups of
+                             this many consecutive bins that share the phasors of
+                             their highest bin k_ref, i.e. bin k is dedispersed at
+                             the DMs DM_j k_ref / k, and is then re-sampled to the
+                             plan's trials by linear interpolation along the
+                             trial axis.  An approximation: its error against
+                             Eq. 7 grows with the DM step and the bin.          */
+  double spin_tol;        /* largest relative DM contraction 1 - k / k_ref within a
+                             group (0: 0.01); bins below k_min = max(1,
+                             ceil((spin_group - 1) / spin_tol)) follow Eq. 7 exactly */
 } fdd_params;
 
 typedef struct fdd_info {
@@ -153,6 +165,10 @@ typedef struct fdd_info {
   int32_t block_dm;        /* trials per output block of the streamed calls        */
   int64_t stream_bytes;    /* device bytes the first streamed call adds to the plan
                               (two input windows and two output blocks)           */
+  int32_t spin_group;      /* bins per group of the spin-frequency grids (0: off)  */
+  int32_t spin_k_min;      /* first grouped bin                                    */
+  int32_t spin_j_lo;       /* the scaled grid's first trial, relative to the plan's */
+  int32_t spin_n_s;        /* trials of the scaled grid                            */
 } fdd_info;
 
 /* ABI version of the loaded library (FDD_ABI_VERSION at build time). */

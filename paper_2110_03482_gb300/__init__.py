@@ -90,6 +90,8 @@ class fdd_params(ctypes.Structure):
         ("mac_variant", ctypes.c_int32),
         ("workspace_limit", ctypes.c_size_t),
         ("downsample", ctypes.c_int32),
+        ("spin_group", ctypes.c_int32),
+        ("spin_tol", ctypes.c_double),
     ]
 
 
@@ -115,6 +117,10 @@ class fdd_info(ctypes.Structure):
         ("downsample", ctypes.c_int32),
         ("block_dm", ctypes.c_int32),
         ("stream_bytes", ctypes.c_int64),
+        ("spin_group", ctypes.c_int32),
+        ("spin_k_min", ctypes.c_int32),
+        ("spin_j_lo", ctypes.c_int32),
+        ("spin_n_s", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -16,7 +16,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libfdd.so")
 
 SOURCES = ["fdd_api.cu", "fdd_mac_fp32.cu", "fdd_mac_tc.cu", "fdd_prep.cu", "fdd_batch.cu",
-           "fdd_noalloc.cu", "fdd_tdd.cu"]
+           "fdd_noalloc.cu", "fdd_tdd.cu", "fdd_spin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -42,6 +42,15 @@ struct fdd_plan_s {
   float2* d_Y = nullptr;      // [dm_batch][bin_pitch] dedispersed spectra (time output;
                               // tensor-core form: [beam][dm_batch][bin_pitch])
   float* d_yt = nullptr;      // [dm_batch][L] inverse transforms (time output)
+  // spin-frequency-dependent grids (fdd_params.spin_group): the scaled grid's
+  // phase table, the scratch of the groups, and the FP32 tile of the bins
+  // below the first group
+  bool spin_on = false;
+  fdd::SpinGeometry spin{};
+  fdd::PhaseConst* d_pc_spin = nullptr;
+  void* d_spin_scratch = nullptr;
+  size_t spin_scratch_bytes = 0;
+  int spin_fp32_variant = 0;
   float2* d_xb = nullptr;     // tensor-core form: one beam's spectra [n_chan][bin_pitch]
   float2* d_Yb = nullptr;     // tensor-core form, time output: one beam's DM batch
                               // [dm_batch][bin_pitch] with bins innermost
@@ -319,6 +328,15 @@ fdd_status core_geometry(const fdd_params* p, CoreGeometry* out) {
 
 namespace {
 
+// Device bytes a spin-frequency plan adds: the scaled grid's phase table and
+// the scratch of its blocks of groups.
+size_t spin_plan_bytes(const fdd_params* p, const fdd::CoreGeometry& cg, int64_t n_bins) {
+  fdd::SpinGeometry sg;
+  fdd::spin_geometry(n_bins, p->n_dm, cg.dm0, cg.ddm, p->spin_group,
+                     p->spin_tol > 0.0 ? p->spin_tol : 0.01, &sg);
+  return sizeof(fdd::PhaseConst) * p->n_chan + fdd::spin_scratch_bytes(sg, p->n_chan, n_bins);
+}
+
 fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* core_out) {
   if (!p) return fail(FDD_ERR_INVALID_ARG, "params is NULL");
   if (!g) return fail(FDD_ERR_INVALID_ARG, "info is NULL");
@@ -335,6 +353,15 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
                 FDD_MAC_VARIANTS);
+  if (p->spin_group != 0) {
+    if (p->spin_group != 16 && p->spin_group != 32)
+      return fail(FDD_ERR_INVALID_ARG, "spin_group must be 0, 16 or 32");
+    if (p->precision == FDD_PREC_FP32 || p->n_beams != 1)
+      return fail(FDD_ERR_UNSUPPORTED,
+                  "spin-frequency grids run on the tensor-core form for one beam");
+    if (!(p->spin_tol >= 0.0) || !(p->spin_tol < 1.0))
+      return fail(FDD_ERR_INVALID_ARG, "spin_tol must be in [0, 1) (0 selects 0.01)");
+  }
   fdd::CoreGeometry cg;
   fdd_status st = fdd::core_geometry(p, &cg);
   if (st != FDD_OK) return st;
@@ -363,6 +390,19 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   g->dm0 = cg.dm0;
   g->ddm = cg.ddm;
   g->dm_uniform = cg.uniform;
+  if (p->spin_group != 0) {
+    if (p->n_dm < 2 || !(cg.ddm > 0.0))
+      return fail(FDD_ERR_UNSUPPORTED, "spin-frequency grids need two or more increasing trials");
+    fdd::SpinGeometry sg;
+    fdd::spin_geometry(n_bins, p->n_dm, cg.dm0, cg.ddm, p->spin_group,
+                       p->spin_tol > 0.0 ? p->spin_tol : 0.01, &sg);
+    if (static_cast<double>(n_bins - 1) * static_cast<double>(sg.n_s - 1) >= 4294967296.0)
+      return fail(FDD_ERR_UNSUPPORTED, "(n_bins-1)*(scaled trials-1) must be below 2^32");
+    g->spin_group = sg.G;
+    g->spin_k_min = sg.k_min;
+    g->spin_j_lo = sg.j_lo;
+    g->spin_n_s = sg.n_s;
+  }
   const bool tc = p->precision != FDD_PREC_FP32;
   g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
                                                      : fdd::mac_variant_for(p->n_dm));
@@ -373,7 +413,8 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   const size_t fixed = sizeof(fdd::PhaseConst) * nc + sizeof(float) * size_t(nc) * L +
                        sizeof(float2) * size_t(nc) * g->bin_pitch * (spectra_sets + (tc ? 1 : 0)) +
                        256 +
-                       (tc ? fdd::mac_tc_scratch_bytes(p->n_beams, nc, p->n_dm, n_bins) : 0);
+                       (tc ? fdd::mac_tc_scratch_bytes(p->n_beams, nc, p->n_dm, n_bins) : 0) +
+                       (p->spin_group ? spin_plan_bytes(p, cg, n_bins) : 0);
   const size_t limit = p->workspace_limit ? p->workspace_limit : kDefaultWorkspace;
   int64_t batch = p->n_dm;
   size_t per_dm = 0;
@@ -424,7 +465,7 @@ void release(fdd_plan_s* P) {
   if (P->has_c2r) cufftDestroy(P->c2r);
   if (P->has_c2r_tail) cufftDestroy(P->c2r_tail);
   void* ptrs[] = {P->d_pc, P->d_xw, P->d_X, P->d_Y, P->d_yt, P->d_xb, P->d_Yb, P->d_fftwork,
-                  P->d_status,
+                  P->d_pc_spin, P->d_spin_scratch, P->d_status,
                   P->d_win[0], P->d_win[1], P->d_blk[0], P->d_blk[1], P->d_tcx, P->d_shift,
                   P->d_shift_base, P->d_tdd_x};
   for (void* q : ptrs)
@@ -763,6 +804,83 @@ fdd_status run(fdd_plan_s* P, const Io& io, cudaStream_t s) {
   return FDD_OK;
 }
 
+// Spin-frequency-dependent grids (one beam, tensor cores): per chunk the
+// beam's spectra stay bins innermost (d_xb); launch_mac_spin writes the
+// dedispersed spectra bins innermost too, so the inverse transforms read
+// them directly (time output) or they go straight to the output.
+fdd_status run_spin(fdd_plan_s* P, const Io& io, cudaStream_t s) {
+  fdd_status st;
+  const fdd_params& p = P->p;
+  const fdd_info& g = P->info;
+  const int dm_end = io.dm_first + io.n_dm;
+  for (int64_t c = 0; c < g.n_chunks; ++c) {
+    if ((st = transform(P, io, 0, c, P->d_xb, s)) != FDD_OK) return st;
+    fdd::MacArgs m{};
+    m.X = P->d_xb;
+    m.x_chan_stride = g.bin_pitch;
+    m.x_series_stride = static_cast<int64_t>(p.n_chan) * g.bin_pitch;
+    m.pc = P->d_pc;
+    m.n_chan = p.n_chan;
+    m.n_series = 1;
+    m.status = P->d_status;
+    m.scale = 1.0f;
+    if (p.output == FDD_OUT_TIME) {
+      const int64_t Ls = g.fft_len / g.downsample;
+      m.n_bins = static_cast<int>(Ls / 2 + 1);
+      m.out_kind = 1;
+      m.real_bin_a = 0;
+      m.real_bin_b = static_cast<int>(Ls / 2);
+      m.scale = whole_rows(P) ? static_cast<float>(1.0 / static_cast<double>(g.fft_len)) : 1.0f;
+      for (int j0 = io.dm_first; j0 < dm_end; j0 += g.dm_batch) {
+        const int nb = (dm_end - j0) < g.dm_batch ? (dm_end - j0) : g.dm_batch;
+        m.j_begin = j0;
+        m.n_dm = nb;
+        m.Y = P->d_Yb;
+        m.y_dm_stride = g.bin_pitch;
+        {
+          StageTimer t(P, FDD_STAGE_MAC, s);
+          FDD_CUDA(fdd::launch_mac_spin(m, P->spin, P->d_pc_spin, P->spin_fp32_variant,
+                                        p.precision, P->n_sms, P->d_spin_scratch,
+                                        P->spin_scratch_bytes, s));
+        }
+        if ((st = inverse_and_place(P, io, 0, c, j0, nb, P->d_Yb, s)) != FDD_OK) return st;
+      }
+    } else {
+      m.n_bins = static_cast<int>(g.n_bins);
+      m.out_kind = p.output == FDD_OUT_SPECTRA ? 1 : 2;
+      m.real_bin_a = -1;
+      m.real_bin_b = -1;
+      const size_t esz = p.output == FDD_OUT_SPECTRA ? 8 : 4;
+      const int step = io.d_out ? io.n_dm : P->block_dm;
+      for (int j0 = io.dm_first; j0 < dm_end; j0 += step) {
+        const int nb = (dm_end - j0) < step ? (dm_end - j0) : step;
+        m.j_begin = j0;
+        m.n_dm = nb;
+        m.y_dm_stride = g.n_bins;
+        int k = -1;
+        if (io.d_out) {
+          m.Y = static_cast<char*>(io.d_out) +
+                esz * ((c * static_cast<int64_t>(io.n_dm) + (j0 - io.dm_first)) * g.n_bins);
+        } else {
+          if ((st = block_slot(P, io, s, &k)) != FDD_OK) return st;
+          m.Y = P->d_blk[k];
+        }
+        {
+          StageTimer t(P, FDD_STAGE_MAC, s);
+          FDD_CUDA(fdd::launch_mac_spin(m, P->spin, P->d_pc_spin, P->spin_fp32_variant,
+                                        p.precision, P->n_sms, P->d_spin_scratch,
+                                        P->spin_scratch_bytes, s));
+        }
+        if (k >= 0) {
+          fdd_block blk{0, 1, c, j0, nb, P->d_blk[k], g.n_bins, g.n_bins, 0, nullptr};
+          if ((st = deliver(P, io, k, blk, s)) != FDD_OK) return st;
+        }
+      }
+    }
+  }
+  return FDD_OK;
+}
+
 // Tensor-core form: every beam of a chunk is transformed first, each beam's
 // spectra moved into the bin-major X_T[k][beam][chan] the kernel reads (the
 // FP16 form's per-bin maxima found on the way), then one launch per DM batch
@@ -775,6 +893,7 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
   unsigned int* absmax = reinterpret_cast<unsigned int*>(P->d_tcx);  // scratch head
   const bool f16 = p.precision == FDD_PREC_FP16;
   const int dm_end = io.dm_first + io.n_dm;
+  if (P->spin_on) return run_spin(P, io, s);
   for (int64_t c = 0; c < g.n_chunks; ++c) {
     if (f16) FDD_CUDA(cudaMemsetAsync(absmax, 0, sizeof(unsigned int) * g.n_bins, s));
     for (int b = 0; b < p.n_beams; ++b) {
@@ -1012,6 +1131,26 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   }
   FDD_CUDA(cudaMemcpy(P->d_pc, P->pc_host.data(), sizeof(fdd::PhaseConst) * nc,
                       cudaMemcpyHostToDevice));
+  if (p->spin_group != 0) {
+    // the scaled grid's phase constants (first DM dm0s), its scratch, and the
+    // FP32 tile of the bins below the first group
+    P->spin_on = true;
+    fdd::spin_geometry(g.n_bins, p->n_dm, g.dm0, g.ddm, p->spin_group,
+                       p->spin_tol > 0.0 ? p->spin_tol : 0.01, &P->spin);
+    std::vector<fdd::PhaseConst> pcs(nc);
+    for (int c = 0; c < nc; ++c)
+      pcs[c] = fdd::phase_const(P->rate[c], static_cast<double>(g.fft_len), P->spin.dm0s, g.ddm);
+    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_pc_spin), sizeof(fdd::PhaseConst) * nc)))
+      return st;
+    FDD_CUDA(cudaMemcpy(P->d_pc_spin, pcs.data(), sizeof(fdd::PhaseConst) * nc,
+                        cudaMemcpyHostToDevice));
+    P->spin_scratch_bytes = fdd::spin_scratch_bytes(P->spin, nc, g.n_bins);
+    if ((st = dev_alloc(P, &P->d_spin_scratch, P->spin_scratch_bytes))) return st;
+    P->spin_fp32_variant = fdd::mac_variant_for(p->n_dm);
+    if (fdd::mac_smem_bytes(P->spin_fp32_variant, nc) > kMaxSmem)
+      return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
+    FDD_CUDA(fdd::mac_prepare(P->spin_fp32_variant, nc));
+  }
   FDD_CUDA(cudaMemset(P->d_status, 0, 256));
 
   // cuFFT plans with caller-owned work area (execute never allocates).
@@ -1235,7 +1374,14 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
   m.real_bin_b = -1;
   m.status = plan->d_status;
   StageTimer t(plan, FDD_STAGE_MAC, reinterpret_cast<cudaStream_t>(stream));
-  if (plan->tc)
+  if (plan->spin_on) {
+    if (bin_first != 0 || n_bins != g.n_bins || n_series != 1)
+      return fail(FDD_ERR_UNSUPPORTED,
+                  "spin-frequency grids take one series of every bin (no bin windows)");
+    FDD_CUDA(fdd::launch_mac_spin(m, plan->spin, plan->d_pc_spin, plan->spin_fp32_variant,
+                                  plan->p.precision, plan->n_sms, plan->d_spin_scratch,
+                                  plan->spin_scratch_bytes, reinterpret_cast<cudaStream_t>(stream)));
+  } else if (plan->tc)
     FDD_CUDA(fdd::launch_mac_tc(m, plan->p.precision, plan->n_sms,
                                 plan->d_tcx, plan->tcx_bytes,
                                 reinterpret_cast<cudaStream_t>(stream)));

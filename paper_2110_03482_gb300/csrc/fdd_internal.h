@@ -27,6 +27,9 @@ struct MacArgs {
   int n_chan;
   int n_bins;               // bins handled by this call (local indices 0 .. n_bins-1)
   int k_begin;              // absolute bin index of local bin 0 (phases use k_begin + k)
+  int k_step;               // tensor-core kernel only: phases use k_begin + k * k_step
+                            // (0 or 1: consecutive bins; G: one reference bin per
+                            // group of G bins, the groups' bins being the series)
   int n_series;
   int j_begin;              // first global trial index handled by this call
   int n_dm;                 // trials handled by this call
@@ -152,6 +155,34 @@ struct BinUntransposeArgs {
   int64_t in_bin_stride = 0;  // elements between bins of `in`; 0: n_series * n_dm
 };
 cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s);
+
+// The tensor-core kernel on bin-major spectra and output at the strides in a
+// (x_bin_stride, y_bin_stride > 0), with a.bin_absmax already holding the FP16
+// form's per-bin maxima: no scratch, one launch.
+cudaError_t launch_mac_tc_direct(const MacArgs& a, int precision, int n_sms, cudaStream_t s);
+
+// Spin-frequency-dependent DM grids (fdd_spin.cu; Sect. 2.3, Eqs. 8 and 9).
+struct SpinGeometry {
+  int G;             // bins per group (16 or 32)
+  double eps;        // largest relative DM contraction within a group
+  int k_min;         // first grouped bin: max(1, ceil((G - 1) / eps)), at most K
+  int j_lo;          // the scaled grid starts at trial j_lo of the plan's grid (<= 0)
+  int n_s;           // trials of the scaled grid, n_dm - j_lo
+  double dm0, ddm;   // the plan's grid
+  double dm0s;       // first DM of the scaled grid, dm0 + j_lo ddm
+};
+void spin_geometry(int64_t K, int n_dm, double dm0, double ddm, int G, double eps,
+                   SpinGeometry* out);
+// Scratch of launch_mac_spin: blocks of groups of at most 3 GiB.
+size_t spin_scratch_bytes(const SpinGeometry& sg, int n_chan, int64_t K);
+// Eq. 7 of one beam on the spin-frequency-dependent grids: a.X bins
+// innermost [chan][x_chan_stride], a.Y bins innermost (y_dm_stride), all K
+// = a.n_bins bins (k_begin 0), trials a.j_begin .. + a.n_dm of the plan's
+// grid; a.pc the plan's phase table (bins below k_min, on the FP32 tile
+// fp32_variant), pc_spin that of the scaled grid (first DM dm0s).
+cudaError_t launch_mac_spin(const MacArgs& a, const SpinGeometry& sg, const PhaseConst* pc_spin,
+                            int fp32_variant, int precision, int n_sms, void* scratch,
+                            size_t scratch_bytes, cudaStream_t s);
 
 // Allocation-failure injection (fdd_debug_fail_alloc): true when this device
 // allocation is to fail; every library allocator asks before cudaMalloc.

@@ -360,7 +360,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     uint32_t s = 0;
     bool ok = true;
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
-      const uint32_t ku = static_cast<uint32_t>(a.k_begin + k);  // absolute bin
+      // absolute bin of the phasors (groups of bins sharing a reference bin
+      // under spin-frequency-dependent grids step by the group size)
+      const uint32_t ku = static_cast<uint32_t>(a.k_begin + k * (a.k_step > 0 ? a.k_step : 1));
       const float sx = kPrec == kF16 ? f16_bin_scale(a.bin_absmax[k]) : 1.f;  // data scale
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
@@ -535,6 +537,14 @@ size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins) 
   if (kb > n_bins) kb = n_bins;
   return align_up(sizeof(unsigned int) * static_cast<size_t>(n_bins)) +
          per_bin * static_cast<size_t>(kb) + 2 * kScratchAlign;
+}
+
+cudaError_t launch_mac_tc_direct(const MacArgs& a, int precision, int n_sms, cudaStream_t s) {
+  if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
+  const int prec = tc_prec(precision);
+  if (prec < 0 || a.x_bin_stride <= 0 || a.y_bin_stride <= 0 || a.x_chan_stride != 1)
+    return cudaErrorInvalidValue;
+  return launch_mac_tc_block(a, prec, n_sms, s);
 }
 
 size_t mac_tc_min_scratch(int n_series, int n_chan, int n_dm, int64_t n_bins) {
