@@ -557,16 +557,17 @@ __global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* se
 // The complex multiply-accumulate y += z p needs four real products; with
 //   A += zr pr,  B += zi pi,  C += (zr + zi)(pr + pi)
 // accumulated instead, Re y = A - B and Im y = C - A - B at the end: three
-// real products per complex MAC (Gauss's three-multiplication form), the
-// sums zr + zi and pr + pi being formed once per phasor by the producers.
-// Its FP32 rounding is that of the four-product form to within a few
-// percent (every term is of the same size as a product of the four-product
-// form).  The tile: producer warp q evaluates, for bin q of the CTA's four
-// and each channel, the 64 Z_a = X Q_a and 32 P_b of a 2048-trial block (T =
-// 32), as planes zr, zi, zs and pr, pi, ps; consumer warps 2q and 2q + 1 own
-// the a's 0..31 and 32..63 of that bin, each lane a 4 x 8 tile of (a, b)
-// with the three accumulators as pairs along b: 48 paired FMAs per lane and
-// channel for 32 complex MACs.
+// real products per complex MAC (Gauss's three-multiplication form).  Its
+// FP32 rounding is that of the four-product form to within a few percent
+// (every term is of the size of a product of the four-product form).  The
+// tile: producer warp q evaluates, for bin q of the CTA's four and each
+// channel, the 64 Z_a = X Q_a and 32 P_b of a 2048-trial block (T = 32), as
+// planes zr, zi and pr, pi; consumer warps 2q and 2q + 1 own the a's 0..31
+// and 32..63 of that bin, each lane a 4 x 8 tile of (a, b) with the three
+// accumulators as pairs along b, the sums zr + zi and pr + pi formed in
+// registers after the loads (shared-memory traffic per lane as the
+// four-product form's, two floats per operand): 48 paired FMAs and 6 paired
+// adds per lane and channel for 32 complex MACs.
 template <int kCh, int kStages>
 struct G3 {
   static constexpr int kA = 64;                // a's per bin (Z_a)
@@ -576,7 +577,7 @@ struct G3 {
   static constexpr int kCons = 2 * kBins;      // consumer warps
   static constexpr int kProd = kBins;          // producer warps
   static constexpr int kThreads = 32 * (kCons + kProd);
-  static constexpr int kGFL = 3 * kA + 3 * kT;  // floats per (bin, channel): zr zi zs pr pi ps
+  static constexpr int kGFL = 2 * kA + 2 * kT;  // floats per (bin, channel): zr zi pr pi
   static constexpr int kStageFloats = kCh * kBins * kGFL;
   static constexpr size_t kBarBytes = (2 * kStages * 8 + 4 + 15) / 16 * 16;
   static constexpr size_t kSwapBytes = kBarBytes + sizeof(float) * size_t(kStages) * kStageFloats;
@@ -642,13 +643,10 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
           float* grp = st + ch * Ly::kBins * Ly::kGFL;
           grp[lane] = z0r;
           grp[Ly::kA + lane] = z0i;
-          grp[2 * Ly::kA + lane] = z0r + z0i;
           grp[32 + lane] = z1r;
           grp[Ly::kA + 32 + lane] = z1i;
-          grp[2 * Ly::kA + 32 + lane] = z1r + z1i;
-          grp[3 * Ly::kA + lane] = wp.x;
-          grp[3 * Ly::kA + Ly::kT + lane] = wp.y;
-          grp[3 * Ly::kA + 2 * Ly::kT + lane] = wp.x + wp.y;
+          grp[2 * Ly::kA + lane] = wp.x;
+          grp[2 * Ly::kA + Ly::kT + lane] = wp.y;
         }
       }
       if (!a.test_withhold) dev::mbar_arrive_warp(&full[s]);
@@ -678,23 +676,23 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
           const float* grp = st + ch * Ly::kBins * Ly::kGFL;
           const float4 zr = *reinterpret_cast<const float4*>(grp + 32 * h + 4 * ga);
           const float4 zi = *reinterpret_cast<const float4*>(grp + Ly::kA + 32 * h + 4 * ga);
-          const float4 zs = *reinterpret_cast<const float4*>(grp + 2 * Ly::kA + 32 * h + 4 * ga);
-          const float* pp = grp + 3 * Ly::kA + 8 * gb;
+          const float* pp = grp + 2 * Ly::kA + 8 * gb;
           const float4 pr0 = *reinterpret_cast<const float4*>(pp);
           const float4 pr1 = *reinterpret_cast<const float4*>(pp + 4);
           const float4 pi0 = *reinterpret_cast<const float4*>(pp + Ly::kT);
           const float4 pi1 = *reinterpret_cast<const float4*>(pp + Ly::kT + 4);
-          const float4 ps0 = *reinterpret_cast<const float4*>(pp + 2 * Ly::kT);
-          const float4 ps1 = *reinterpret_cast<const float4*>(pp + 2 * Ly::kT + 4);
           const float2 pr[4] = {make_float2(pr0.x, pr0.y), make_float2(pr0.z, pr0.w),
                                 make_float2(pr1.x, pr1.y), make_float2(pr1.z, pr1.w)};
           const float2 pi[4] = {make_float2(pi0.x, pi0.y), make_float2(pi0.z, pi0.w),
                                 make_float2(pi1.x, pi1.y), make_float2(pi1.z, pi1.w)};
-          const float2 ps[4] = {make_float2(ps0.x, ps0.y), make_float2(ps0.z, ps0.w),
-                                make_float2(ps1.x, ps1.y), make_float2(ps1.z, ps1.w)};
+          float2 ps[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) ps[m] = __fadd2_rn(pr[m], pi[m]);
+          const float2 zs01 = __fadd2_rn(make_float2(zr.x, zr.y), make_float2(zi.x, zi.y));
+          const float2 zs23 = __fadd2_rn(make_float2(zr.z, zr.w), make_float2(zi.z, zi.w));
           const float zrv[4] = {zr.x, zr.y, zr.z, zr.w};
           const float ziv[4] = {zi.x, zi.y, zi.z, zi.w};
-          const float zsv[4] = {zs.x, zs.y, zs.z, zs.w};
+          const float zsv[4] = {zs01.x, zs01.y, zs23.x, zs23.y};
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float2 r2 = make_float2(zrv[i], zrv[i]);

@@ -367,41 +367,42 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
-        PhaseConst pc_next = {0u, 0u, 0u, 0u};
-        float2 x_next[kBeamsPerWarp];
-        {
-          const int nu = lane;
-          if (nu < a.n_chan) pc_next = a.pc[nu];
+        // X and the phase constants run two tiles ahead (a tile's loads have
+        // two producer iterations to arrive)
+        auto load_pc = [&](int nn) {
+          return nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
+        };
+        auto load_x = [&](int nn, int m) {
+          const int bg = group * kBeams + pw + kProdWarps * m;
+          return (nn < a.n_chan && bg < a.n_series)
+                     ? __ldg(a.X + static_cast<int64_t>(k) * a.x_bin_stride +
+                             static_cast<int64_t>(bg) * a.x_series_stride +
+                             static_cast<int64_t>(nn) * a.x_chan_stride)
+                     : make_float2(0.f, 0.f);
+        };
+        PhaseConst pc_n1 = load_pc(lane), pc_n2 = load_pc(kKC + lane);
+        float2 x_n1[kBeamsPerWarp], x_n2[kBeamsPerWarp];
 #pragma unroll
-          for (int m = 0; m < kBeamsPerWarp; ++m) {
-            const int bg = group * kBeams + pw + kProdWarps * m;
-            x_next[m] = (nu < a.n_chan && bg < a.n_series)
-                            ? __ldg(a.X + static_cast<int64_t>(k) * a.x_bin_stride +
-                                    static_cast<int64_t>(bg) * a.x_series_stride +
-                                    static_cast<int64_t>(nu) * a.x_chan_stride)
-                            : make_float2(0.f, 0.f);
-          }
+        for (int m = 0; m < kBeamsPerWarp; ++m) {
+          x_n1[m] = load_x(lane, m);
+          x_n2[m] = load_x(kKC + lane, m);
         }
         for (int t = 0; t < n_tiles; ++t, ++s) {
           const int nu = t * kKC + lane;
           const bool nu_ok = nu < a.n_chan;
-          const PhaseConst pc = pc_next;
+          const PhaseConst pc = pc_n1;
           float2 x[kBeamsPerWarp];
 #pragma unroll
           for (int m = 0; m < kBeamsPerWarp; ++m)
-            x[m] = kPrec == kF16 ? make_float2(x_next[m].x * sx, x_next[m].y * sx) : x_next[m];
-          if (t + 1 < n_tiles) {  // prefetch the next tile
-            const int nn = nu + kKC;
-            pc_next = nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
+            x[m] = kPrec == kF16 ? make_float2(x_n1[m].x * sx, x_n1[m].y * sx) : x_n1[m];
+          pc_n1 = pc_n2;
 #pragma unroll
-            for (int m = 0; m < kBeamsPerWarp; ++m) {
-              const int bg = group * kBeams + pw + kProdWarps * m;
-              x_next[m] = (nn < a.n_chan && bg < a.n_series)
-                              ? __ldg(a.X + static_cast<int64_t>(k) * a.x_bin_stride +
-                                      static_cast<int64_t>(bg) * a.x_series_stride +
-                                      static_cast<int64_t>(nn) * a.x_chan_stride)
-                              : make_float2(0.f, 0.f);
-            }
+          for (int m = 0; m < kBeamsPerWarp; ++m) x_n1[m] = x_n2[m];
+          if (t + 2 < n_tiles) {  // prefetch the tile after next
+            const int nn = nu + 2 * kKC;
+            pc_n2 = load_pc(nn);
+#pragma unroll
+            for (int m = 0; m < kBeamsPerWarp; ++m) x_n2[m] = load_x(nn, m);
           }
           // phasors in registers before touching the stage (zero beyond n_chan)
           float2 r1 = make_float2(0.f, 0.f), pb = r1, r128 = r1, qa = r1, qb = r1;
