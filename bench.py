@@ -83,13 +83,14 @@ def parse_args():
                          "(one JSON line)")
     ap.add_argument("--batch-n-t-div", type=int, default=16,
                     help="divide the batch workload's beam lengths (device memory bound)")
-    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "bf16_hilo"],
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "bf16_hilo", "fp8"],
                     help="tensor-core form of the multi-beam workloads")
     ap.add_argument("--workspace-gib", type=float, default=200.0,
                     help="device workspace limit of the multi-beam plans (GiB)")
     ap.add_argument("--mac-sweep", default="",
-                    help="comma-separated FDD_MAC_* variants, by number or name, or tc / tc1 / tc16 for "
-                         "the tensor-core form in BF16 hi+lo / BF16 / FP16 (or 'all'): time the "
+                    help="comma-separated FDD_MAC_* variants, by number or name, or tc / tc1 / tc16 / "
+                         "tc8 for the tensor-core form in BF16 hi+lo / BF16 / FP16 / FP8 (or 'all'): "
+                         "time the "
                          "phase-rotate-and-sum kernel alone for each on one chunk of the "
                          "workload and print one JSON line per variant")
     return ap.parse_args()
@@ -674,7 +675,7 @@ def run_mac_sweep(args) -> None:
     fdd.build()
     w = workload_from_args(args)
     tc_prec = {"tc": fdd.FDD_PREC_BF16_HILO, "tc1": fdd.FDD_PREC_BF16,
-               "tc16": fdd.FDD_PREC_FP16}
+               "tc16": fdd.FDD_PREC_FP16, "tc8": fdd.FDD_PREC_FP8}
 
     def variant(v: str):
         if v in tc_prec:
@@ -736,7 +737,7 @@ def run_mac_sweep(args) -> None:
         extra = {"frac_bf16_peak_algorithmic": tf / bf16_peak,
                  "tensor_tflops_physical": (2 if v == "tc" else 1) * tf} if tc else {}
         print(json.dumps({"sweep": {"tc": "TC_hilo", "tc1": "TC_bf16",
-                                    "tc16": "TC_fp16"}.get(v, None) or
+                                    "tc16": "TC_fp16", "tc8": "TC_fp8"}.get(v, None) or
                           fdd.MAC_VARIANT_NAMES[v], "variant": v,
                           "ms_per_launch": ms, "beams": ns, "macs_per_s": tf * 1e12 / 8,
                           "tflops": tf, "frac_fp32_peak": tf / peak, "workload": w.name,
@@ -747,7 +748,7 @@ def run_mac_sweep(args) -> None:
               flush=True)
 
 
-TC_PREC = {"fp16": 3, "bf16": 2, "bf16_hilo": 1}  # FDD_PREC_* of the tensor-core forms
+TC_PREC = {"fp16": 3, "bf16": 2, "bf16_hilo": 1, "fp8": 4}  # FDD_PREC_* of the tensor-core forms
 RESIDENT_INPUT_BYTES = 100 << 30  # larger inputs stream from the generator
 
 

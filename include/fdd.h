@@ -98,6 +98,11 @@ typedef enum fdd_status {
 #define FDD_PREC_FP16 3      /* tensor cores with FP16 phasors and FP16 data, each
                                 bin's data scaled by a power of two into FP16's
                                 range (the tensor work of BF16, smaller error)   */
+#define FDD_PREC_FP8 4       /* tensor cores with FP8 E4M3 phasors and data (the
+                                8-bit direction of Sect. 5), per-bin data scaling
+                                as FP16, 64 channels per K stage; three mantissa
+                                bits give a relative error of a few percent, far
+                                above the 16-bit forms (measured, opt-in)        */
 
 typedef struct fdd_params {
   int32_t n_chan;         /* observing channels N_nu, >= 1                          */
@@ -498,7 +503,7 @@ typedef struct fdd_batch_info {
  * mac_variant 0 and autotune != 0 the candidate kernel tiles are timed on the
  * batch's own shapes and the fastest is kept (remembered per shape in the
  * process, and in the text file named by the FDD_AUTOTUNE_CACHE environment
- * variable when set); mac_variant 0 without autotune selects W12_8X8.
+ * variable when set); mac_variant 0 without autotune selects G12_4X8.
  * Allocates all device memory (and, while autotuning, a temporary output).
  * Layouts: the input is the beams' inputs concatenated in order (each
  * [n_t][n_chan] or [n_chan][n_t]); the output is, per beam in order,

@@ -41,6 +41,7 @@ FDD_PREC_FP32 = 0
 FDD_PREC_BF16_HILO = 1
 FDD_PREC_BF16 = 2
 FDD_PREC_FP16 = 3
+FDD_PREC_FP8 = 4
 MAC_VARIANT_NAMES = ["W12_8x8", "Q12_8x8", "Q_4x8", "Q_8x8_512", "Q_4x4", "G12_4x8"]
 for _i, _n in enumerate(MAC_VARIANT_NAMES):
     globals()["FDD_MAC_" + _n.upper()] = _i

@@ -348,7 +348,8 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   if (p->output != FDD_OUT_TIME && p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
     return fail(FDD_ERR_INVALID_ARG, "output %d unknown", p->output);
   if (p->precision != FDD_PREC_FP32 && p->precision != FDD_PREC_BF16_HILO &&
-      p->precision != FDD_PREC_BF16 && p->precision != FDD_PREC_FP16)
+      p->precision != FDD_PREC_BF16 && p->precision != FDD_PREC_FP16 &&
+      p->precision != FDD_PREC_FP8)
     return fail(FDD_ERR_INVALID_ARG, "precision %d unknown", p->precision);
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return fail(FDD_ERR_INVALID_ARG, "mac_variant %d outside [0, %d]", p->mac_variant,
@@ -891,7 +892,7 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
   const fdd_info& g = P->info;
   const int64_t rows = static_cast<int64_t>(p.n_beams) * p.n_chan;  // X_T row per bin
   unsigned int* absmax = reinterpret_cast<unsigned int*>(P->d_tcx);  // scratch head
-  const bool f16 = p.precision == FDD_PREC_FP16;
+  const bool f16 = p.precision == FDD_PREC_FP16 || p.precision == FDD_PREC_FP8;  // scaled
   const int dm_end = io.dm_first + io.n_dm;
   if (P->spin_on) return run_spin(P, io, s);
   for (int64_t c = 0; c < g.n_chunks; ++c) {

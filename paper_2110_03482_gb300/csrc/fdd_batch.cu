@@ -502,7 +502,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     if (tst != FDD_OK) return tst;
     cache_store(key, variant);
   }
-  if (variant < 0) variant = FDD_MAC_W12_8X8;
+  if (variant < 0) variant = FDD_MAC_G12_4X8;
   if ((st = use_variant(variant))) return st;
   B_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
   *out = guard.release();

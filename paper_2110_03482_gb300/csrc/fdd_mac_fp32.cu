@@ -849,19 +849,19 @@ VariantInfo variant_info(int v) {
 // Default tile for a trial count: the one with the least time for the padded
 // trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
 // measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
-// 131073 bins, full blocks): W12_8x8 0.623 (2048-trial blocks), Q_4x8 0.493
-// (1024), Q_8x8_512 0.415 (512), Q_4x4 0.347 (128).  (Q12_8x8, the 2048-trial
-// tile on the plain schedule, measured 49.5 ms against 43.7 for W12_8x8 on
-// the same launch.)
+// 131073 bins, full blocks): G12_4x8 0.650 (2048-trial blocks), Q_4x8 0.493
+// (1024), Q_8x8_512 0.415 (512), Q_4x4 0.347 (128).  (The four-product
+// warp-specialised tile W12_8x8 measured 0.622 on the same launch, Q12_8x8,
+// the 2048-trial tile on the plain schedule, 0.553.)
 int mac_variant_for(int n_dm) {
   struct Tile {
     int variant, block;
     double rate;
   };
   static const Tile tiles[] = {
-      {MAC_W12_8x8, 2048, 0.623}, {MAC_Q_4x8, 1024, 0.493}, {MAC_Q_8x8_512, 512, 0.415},
+      {MAC_G12_4x8, 2048, 0.650}, {MAC_Q_4x8, 1024, 0.493}, {MAC_Q_8x8_512, 512, 0.415},
       {MAC_Q_4x4, 128, 0.347}};
-  int best = MAC_W12_8x8;
+  int best = MAC_G12_4x8;
   double best_cost = 0.0;
   for (const Tile& t : tiles) {
     const double padded = static_cast<double>((n_dm + t.block - 1) / t.block) * t.block;

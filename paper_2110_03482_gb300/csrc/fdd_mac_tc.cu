@@ -43,6 +43,7 @@
 // drains its own MMAs (bounded), frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "fdd_device.cuh"
 #include "fdd_internal.h"
@@ -64,7 +65,7 @@ constexpr int kN = 256;                  // (a, beta) columns of each accumulato
 // kN / kBeams a's, i.e. kN / kBeams * kM trials.
 template <int kBeams>
 __host__ __device__ constexpr int dms_per_pass() { return kN / kBeams * kM; }
-constexpr int kKC = 32;                  // channels per stage
+constexpr int kKC = 32;                  // channels per stage of 16-bit operands
 constexpr int kProdWarps = 16;
 constexpr int kEpiWarps = 4;             // one per tensor-memory lane quarter
 constexpr int kThreads = 32 + 32 * kEpiWarps + 32 * kProdWarps;
@@ -96,18 +97,44 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 // Operand precisions of the kernel (from fdd_params.precision).
-enum TcPrec { kBf16HiLo = 0, kBf16 = 1, kF16 = 2 };
+enum TcPrec { kBf16HiLo = 0, kBf16 = 1, kF16 = 2, kF8 = 3 };
 
 // Instruction descriptor: D FP32, A and B both BF16 (format 1) or both FP16
-// (format 0), both K-major, N and M.
+// (format 0) under kind::f16, both E4M3 (format 0) under kind::f8f6f4; both
+// K-major, N and M.
 template <int kPrec>
 __host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | (kPrec == kF16 ? 0u : ((1u << 7) | (1u << 10))) |
+  return (1u << 4) | ((kPrec == kF16 || kPrec == kF8) ? 0u : ((1u << 7) | (1u << 10))) |
          (static_cast<uint32_t>(kN >> 3) << 17) | (static_cast<uint32_t>(kM >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Four bytes of one K-major row for kCpl channels: (re, im) of one channel in
+// the 16-bit types (re in the low half), or (re0, im0, re1, im1) of two
+// adjacent channels in FP8 E4M3 (re0 in the lowest byte).
+template <int kPrec>
+__device__ __forceinline__ uint32_t pack2(float x, float y);
+template <int kPrec, int kCpl>
+__device__ __forceinline__ uint32_t pack_word(const float2 (&v)[kCpl]) {
+  if constexpr (kPrec == kF8) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(v[0], __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(v[kCpl - 1], __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+  } else {
+    return pack2<kPrec>(v[0].x, v[0].y);
+  }
+}
+// (re, im) -> (re, -im) and -> (im, re) on every channel of a packed word.
+template <int kPrec>
+__device__ __forceinline__ constexpr uint32_t neg_im_mask() {
+  return kPrec == kF8 ? 0x80008000u : 0x80000000u;
+}
+template <int kPrec>
+__device__ __forceinline__ uint32_t swap_re_im(uint32_t w) {
+  return __byte_perm(w, 0, kPrec == kF8 ? 0x2301 : 0x1032);
 }
 
 // (x, y) rounded to the kernel's 16-bit operand type, x in the low half.
@@ -121,14 +148,17 @@ __device__ __forceinline__ uint32_t pack2(float x, float y) {
   }
 }
 
-// FP16 data scale of a bin whose largest |re| or |im| is m: with E the biased
-// exponent of m (m < 2^(E - 126)), the power of two 2^(140 - E), so that m
-// times it is below 2^14 and every component of Z = Q X (|Z| <= sqrt(2) m)
-// stays below 2^14.5, well inside FP16's range (65504).  Powers of two keep
+// Data scale of a bin whose largest |re| or |im| is m, for the operand types
+// of limited range: with E the biased exponent of m (m < 2^(E - 126)), the
+// power of two 2^(T + 126 - E), so that m times it is below 2^T and every
+// component of Z = Q X (|Z| <= sqrt(2) m) stays below 2^(T + 0.5): T = 14 for
+// FP16 (largest 65504), T = 8 for FP8 E4M3 (largest 448).  Powers of two keep
 // the scaling and its undoing exact.
-__device__ __forceinline__ float f16_bin_scale(float m) {
+template <int kPrec>
+__device__ __forceinline__ float bin_scale(float m) {
+  constexpr int kT = kPrec == kF8 ? 8 : 14;
   const int e = static_cast<int>((__float_as_uint(m) >> 23) & 0xFFu);
-  int f = 267 - e;  // biased exponent of 2^(140 - E)
+  int f = kT + 253 - e;  // biased exponent of 2^(T + 126 - E)
   f = f < 1 ? 1 : (f > 253 ? 253 : f);
   return __uint_as_float(static_cast<uint32_t>(f) << 23);
 }
@@ -154,22 +184,34 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// D (+)= A B^T for one K step of 16: M = 128, N = 256, 16-bit in, FP32 out.
+// D (+)= A B^T for one K step of 32 bytes: M = 128, N = 256, FP32 out; 16
+// elements of 16 bits (kind::f16) or 32 of FP8 E4M3 (kind::f8f6f4).
 template <int kPrec>
 __device__ __forceinline__ void mma16(uint32_t d, uint64_t adesc, uint64_t bdesc,
                                       uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(adesc), "l"(bdesc), "r"(idesc<kPrec>()), "r"(accum));
+  if constexpr (kPrec == kF8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(adesc), "l"(bdesc), "r"(idesc<kPrec>()), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(adesc), "l"(bdesc), "r"(idesc<kPrec>()), "r"(accum));
+  }
 }
 
 // kPrec: kBf16HiLo (phasors as BF16 hi + lo, four MMAs per K step), kBf16
-// (BF16 only) or kF16 (FP16 phasors and scaled FP16 data).
+// (BF16 only), kF16 (FP16 phasors and scaled FP16 data) or kF8 (FP8 E4M3
+// phasors and scaled E4M3 data, kind::f8f6f4, 64 channels per stage).
 template <int kPrec, int kBeams>
-__global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
+__global__ void __maxnreg__(96) mac_tc_kernel(const MacArgs a) {
   static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
   constexpr bool kHiLo = kPrec == kBf16HiLo;
+  constexpr bool kScaled = kPrec == kF16 || kPrec == kF8;  // per-bin data scale
+  constexpr int kCpl = kPrec == kF8 ? 2 : 1;               // channels per producer lane
+  constexpr int kKCp = kKC * kCpl;                         // channels per stage
   constexpr int kNA = kN / kBeams;            // a's per pass (8 or 16)
   constexpr int kDmsPass = dms_per_pass<kBeams>();
   constexpr int kStages = Ring<kHiLo>::kStages;
@@ -214,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
 
   const int n_groups = (a.n_series + kBeams - 1) / kBeams;
   const int n_pass = (a.n_dm + kDmsPass - 1) / kDmsPass;
-  const int n_tiles = (a.n_chan + kKC - 1) / kKC;
+  const int n_tiles = (a.n_chan + kKCp - 1) / kKCp;
   const int items_per_bin = n_groups * n_pass;
 
   if (warp == 0) {
@@ -288,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
       // FP16: undo the bin's data scale (a power of two, so exactly)
-      const float sy = kPrec == kF16 ? a.scale / f16_bin_scale(a.bin_absmax[k]) : a.scale;
+      const float sy = kScaled ? a.scale / bin_scale<kPrec>(a.bin_absmax[k]) : a.scale;
       const float2 sc = make_float2(sy, real_only ? 0.f : sy);
       const int64_t o_bin = static_cast<int64_t>(k) * a.y_bin_stride;
       for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
@@ -339,21 +381,24 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     }
   } else {
     // ------------------------------------------------------------ producers
-    // Producer warp pw (0..15) evaluates, for channel nu = tile*32 + lane:
+    // Producer warp pw (0..15) evaluates, for the channels nu = tile * kKCp +
+    // kCpl * lane + cl (cl < kCpl: one channel per lane for 16-bit operands,
+    // two adjacent ones for 8-bit, so every lane writes four bytes per row):
     //   P_b for the 8 rows b = 8 pw .. 8 pw + 7 (one direct phasor, then the
     //   recurrence P_{b+1} = P_b R with R = exp(2 pi i k v), at most 7 steps),
     //   stored as the A_re and A_im rows (hi, and lo = P - hi);
     //   Q_a for the pass's kNA a's as two chains of kNA / 2 (Q of each
     //   chain's first a direct, then Q_{a+1} = Q_a R^128),
     //   Z_a = Q_a X for the beams beta = pw (and pw + 16 in 32-beam groups).
-    // X and the phase constants of the next tile are loaded one stage ahead.
+    // X and the phase constants run two tiles ahead.
     const int pw = warp - 1 - kEpiWarps;           // 0..15
     constexpr int kRows = kM / kProdWarps;         // P rows per warp (8)
     constexpr int kBeamsPerWarp = kBeams / kProdWarps;  // 1 or 2
     constexpr int kHalfA = kNA / 2;                // a's per Q chain
     // Store offsets that do not change between stages (see sw128): the P
     // rows of this warp, and the B rows a_in * kBeams + pw + 16 m, whose
-    // position within an 8-row group is pw mod 8.
+    // position within an 8-row group is pw mod 8.  A lane's four bytes sit
+    // at the same place for either operand width.
     const uint32_t lane_chunk = static_cast<uint32_t>((lane >> 2) << 4);
     const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
     const uint32_t z_base = sw128(pw, 2 * lane);  // row pw < 16
@@ -363,12 +408,10 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       // absolute bin of the phasors (groups of bins sharing a reference bin
       // under spin-frequency-dependent grids step by the group size)
       const uint32_t ku = static_cast<uint32_t>(a.k_begin + k * (a.k_step > 0 ? a.k_step : 1));
-      const float sx = kPrec == kF16 ? f16_bin_scale(a.bin_absmax[k]) : 1.f;  // data scale
+      const float sx = kScaled ? bin_scale<kPrec>(a.bin_absmax[k]) : 1.f;  // data scale
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
-        // X and the phase constants run two tiles ahead (a tile's loads have
-        // two producer iterations to arrive)
         auto load_pc = [&](int nn) {
           return nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
         };
@@ -380,41 +423,55 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                              static_cast<int64_t>(nn) * a.x_chan_stride)
                      : make_float2(0.f, 0.f);
         };
-        PhaseConst pc_n1 = load_pc(lane), pc_n2 = load_pc(kKC + lane);
-        float2 x_n1[kBeamsPerWarp], x_n2[kBeamsPerWarp];
+        PhaseConst pc_n1[kCpl], pc_n2[kCpl];
+        float2 x_n1[kCpl][kBeamsPerWarp], x_n2[kCpl][kBeamsPerWarp];
 #pragma unroll
-        for (int m = 0; m < kBeamsPerWarp; ++m) {
-          x_n1[m] = load_x(lane, m);
-          x_n2[m] = load_x(kKC + lane, m);
+        for (int cl = 0; cl < kCpl; ++cl) {
+          pc_n1[cl] = load_pc(kCpl * lane + cl);
+          pc_n2[cl] = load_pc(kKCp + kCpl * lane + cl);
+#pragma unroll
+          for (int m = 0; m < kBeamsPerWarp; ++m) {
+            x_n1[cl][m] = load_x(kCpl * lane + cl, m);
+            x_n2[cl][m] = load_x(kKCp + kCpl * lane + cl, m);
+          }
         }
         for (int t = 0; t < n_tiles; ++t, ++s) {
-          const int nu = t * kKC + lane;
-          const bool nu_ok = nu < a.n_chan;
-          const PhaseConst pc = pc_n1;
-          float2 x[kBeamsPerWarp];
+          const int nu0 = t * kKCp + kCpl * lane;
+          PhaseConst pc[kCpl];
+          float2 x[kCpl][kBeamsPerWarp];
 #pragma unroll
-          for (int m = 0; m < kBeamsPerWarp; ++m)
-            x[m] = kPrec == kF16 ? make_float2(x_n1[m].x * sx, x_n1[m].y * sx) : x_n1[m];
-          pc_n1 = pc_n2;
+          for (int cl = 0; cl < kCpl; ++cl) {
+            pc[cl] = pc_n1[cl];
+            pc_n1[cl] = pc_n2[cl];
 #pragma unroll
-          for (int m = 0; m < kBeamsPerWarp; ++m) x_n1[m] = x_n2[m];
-          if (t + 2 < n_tiles) {  // prefetch the tile after next
-            const int nn = nu + 2 * kKC;
-            pc_n2 = load_pc(nn);
+            for (int m = 0; m < kBeamsPerWarp; ++m) {
+              x[cl][m] = kScaled ? make_float2(x_n1[cl][m].x * sx, x_n1[cl][m].y * sx)
+                                 : x_n1[cl][m];
+              x_n1[cl][m] = x_n2[cl][m];
+            }
+            if (t + 2 < n_tiles) {  // prefetch the tile after next
+              const int nn = nu0 + 2 * kKCp + cl;
+              pc_n2[cl] = load_pc(nn);
 #pragma unroll
-            for (int m = 0; m < kBeamsPerWarp; ++m) x_n2[m] = load_x(nn, m);
+              for (int m = 0; m < kBeamsPerWarp; ++m) x_n2[cl][m] = load_x(nn, m);
+            }
           }
           // phasors in registers before touching the stage (zero beyond n_chan)
-          float2 r1 = make_float2(0.f, 0.f), pb = r1, r128 = r1, qa = r1, qb = r1;
-          if (nu_ok) {
-            r1 = unit_phasor(top32_mul(ku, pc.v_lo, pc.v_hi));
-            pb = unit_phasor(top32_mul(ku * static_cast<uint32_t>(pw * kRows), pc.v_lo, pc.v_hi));
-            r128 = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kM), pc.v_lo, pc.v_hi));
-            const uint32_t ja = static_cast<uint32_t>(a.j_begin + j_pass);
-            const uint32_t ph_u = top32_mul(ku, pc.u_lo, pc.u_hi);
-            qa = unit_phasor(ph_u + top32_mul(ku * ja, pc.v_lo, pc.v_hi));
-            qb = unit_phasor(ph_u + top32_mul(ku * (ja + static_cast<uint32_t>(kHalfA * kM)),
-                                              pc.v_lo, pc.v_hi));
+          float2 r1[kCpl], pb[kCpl], r128[kCpl], qa[kCpl], qb[kCpl];
+#pragma unroll
+          for (int cl = 0; cl < kCpl; ++cl) {
+            r1[cl] = pb[cl] = r128[cl] = qa[cl] = qb[cl] = make_float2(0.f, 0.f);
+            if (nu0 + cl < a.n_chan) {
+              const PhaseConst& q = pc[cl];
+              r1[cl] = unit_phasor(top32_mul(ku, q.v_lo, q.v_hi));
+              pb[cl] = unit_phasor(top32_mul(ku * static_cast<uint32_t>(pw * kRows), q.v_lo, q.v_hi));
+              r128[cl] = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kM), q.v_lo, q.v_hi));
+              const uint32_t ja = static_cast<uint32_t>(a.j_begin + j_pass);
+              const uint32_t ph_u = top32_mul(ku, q.u_lo, q.u_hi);
+              qa[cl] = unit_phasor(ph_u + top32_mul(ku * ja, q.v_lo, q.v_hi));
+              qb[cl] = unit_phasor(ph_u + top32_mul(ku * (ja + static_cast<uint32_t>(kHalfA * kM)),
+                                                    q.v_lo, q.v_hi));
+            }
           }
           const uint32_t st = s % kStages;
           if (!__all_sync(0xffffffffu, mbar_wait(&empty[st], ((s / kStages) & 1) ^ 1, abort_flag))) {
@@ -423,46 +480,87 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           }
           unsigned char* stage = base + st * kStageBytes;
           // A rows b = 8 pw + i fill one 8-row swizzle group: the 16-byte chunk
-          // of column pair 2*lane is (lane/4) ^ i, the rest is a constant.
+          // of the lane's four bytes is (lane/4) ^ i, the rest is a constant.
 #pragma unroll
           for (int i = 0; i < kRows; ++i) {
-            const uint32_t hb = pack2<kPrec>(pb.x, pb.y);  // (pr, pi)
+            const uint32_t hb = pack_word<kPrec, kCpl>(pb);  // (pr, pi) per channel
             const uint32_t off = p_base + i * 128 + ((lane_chunk ^ (i << 4)));
-            *reinterpret_cast<uint32_t*>(stage + off) = hb ^ 0x80000000u;                  // (pr, -pi)
-            *reinterpret_cast<uint32_t*>(stage + kTileA + off) = __byte_perm(hb, 0, 0x1032);  // (pi, pr)
+            *reinterpret_cast<uint32_t*>(stage + off) = hb ^ neg_im_mask<kPrec>();       // (pr, -pi)
+            *reinterpret_cast<uint32_t*>(stage + kTileA + off) = swap_re_im<kPrec>(hb);  // (pi, pr)
             if (kHiLo) {
               // residual P - hi (the hi halves widened back to FP32)
               const float2 res = __ffma2_rn(make_float2(__uint_as_float(hb << 16),
                                                         __uint_as_float(hb & 0xFFFF0000u)),
-                                            make_float2(-1.f, -1.f), pb);
+                                            make_float2(-1.f, -1.f), pb[0]);
               const uint32_t lb = bf16x2_bits(__floats2bfloat162_rn(res.x, res.y));
               *reinterpret_cast<uint32_t*>(stage + 2 * kTileA + off) = lb ^ 0x80000000u;
               *reinterpret_cast<uint32_t*>(stage + 3 * kTileA + off) = __byte_perm(lb, 0, 0x1032);
             }
             // P <- P R as a paired multiply-add: (pr, pi) r1r + (-pi, pr) r1i
-            pb = __ffma2_rn(make_float2(-pb.y, pb.x), make_float2(r1.y, r1.y),
-                            __fmul2_rn(pb, make_float2(r1.x, r1.x)));
+#pragma unroll
+            for (int cl = 0; cl < kCpl; ++cl)
+              pb[cl] = __ffma2_rn(make_float2(-pb[cl].y, pb[cl].x), make_float2(r1[cl].y, r1[cl].y),
+                                  __fmul2_rn(pb[cl], make_float2(r1[cl].x, r1[cl].x)));
           }
           unsigned char* tb = stage + kBOff;
+          if constexpr (kPrec == kF16) {
+            // FP16: Z = X Q in paired half arithmetic, straight into the stored
+            // format: xr (qr, qi) + xi (-qi, qr), Q converted once per a
+            __half2 xr2[kBeamsPerWarp], xi2[kBeamsPerWarp];
+#pragma unroll
+            for (int m = 0; m < kBeamsPerWarp; ++m) {
+              xr2[m] = __float2half2_rn(x[0][m].x);
+              xi2[m] = __float2half2_rn(x[0][m].y);
+            }
+#pragma unroll
+            for (int al = 0; al < kHalfA; ++al) {
+              const __half2 qa2 = __floats2half2_rn(qa[0].x, qa[0].y);
+              const __half2 qas = __floats2half2_rn(-qa[0].y, qa[0].x);
+              const __half2 qb2 = __floats2half2_rn(qb[0].x, qb[0].y);
+              const __half2 qbs = __floats2half2_rn(-qb[0].y, qb[0].x);
+#pragma unroll
+              for (int m = 0; m < kBeamsPerWarp; ++m) {
+                const __half2 za = __hfma2(xr2[m], qa2, __hmul2(xi2[m], qas));
+                const __half2 zb = __hfma2(xr2[m], qb2, __hmul2(xi2[m], qbs));
+                const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
+                const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
+                *reinterpret_cast<__half2*>(tb + z_base + ra) = za;
+                *reinterpret_cast<__half2*>(tb + z_base + rb) = zb;
+              }
+              qa[0] = __ffma2_rn(make_float2(-qa[0].y, qa[0].x), make_float2(r128[0].y, r128[0].y),
+                                 __fmul2_rn(qa[0], make_float2(r128[0].x, r128[0].x)));
+              qb[0] = __ffma2_rn(make_float2(-qb[0].y, qb[0].x), make_float2(r128[0].y, r128[0].y),
+                                 __fmul2_rn(qb[0], make_float2(r128[0].x, r128[0].x)));
+            }
+          } else {
 #pragma unroll
           for (int al = 0; al < kHalfA; ++al) {
 #pragma unroll
             for (int m = 0; m < kBeamsPerWarp; ++m) {
               // Z = X Q as (xr, xr)(qr, qi) + (-xi, xi)(qi, qr), for a = al and al + kHalfA
-              const float2 za = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qa.y, qa.x),
-                                           __fmul2_rn(make_float2(x[m].x, x[m].x), qa));
-              const float2 zb = __ffma2_rn(make_float2(-x[m].y, x[m].y), make_float2(qb.y, qb.x),
-                                           __fmul2_rn(make_float2(x[m].x, x[m].x), qb));
+              float2 za[kCpl], zb[kCpl];
+#pragma unroll
+              for (int cl = 0; cl < kCpl; ++cl) {
+                const float2 xv = x[cl][m];
+                za[cl] = __ffma2_rn(make_float2(-xv.y, xv.y), make_float2(qa[cl].y, qa[cl].x),
+                                    __fmul2_rn(make_float2(xv.x, xv.x), qa[cl]));
+                zb[cl] = __ffma2_rn(make_float2(-xv.y, xv.y), make_float2(qb[cl].y, qb[cl].x),
+                                    __fmul2_rn(make_float2(xv.x, xv.x), qb[cl]));
+              }
               // row a_in * kBeams + pw + 16 m: z_base + (kBeams / 8 * a_in + 2 m) groups
               const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
               const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
-              *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack2<kPrec>(za.x, za.y);
-              *reinterpret_cast<uint32_t*>(tb + z_base + rb) = pack2<kPrec>(zb.x, zb.y);
+              *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack_word<kPrec, kCpl>(za);
+              *reinterpret_cast<uint32_t*>(tb + z_base + rb) = pack_word<kPrec, kCpl>(zb);
             }
-            qa = __ffma2_rn(make_float2(-qa.y, qa.x), make_float2(r128.y, r128.y),
-                            __fmul2_rn(qa, make_float2(r128.x, r128.x)));
-            qb = __ffma2_rn(make_float2(-qb.y, qb.x), make_float2(r128.y, r128.y),
-                            __fmul2_rn(qb, make_float2(r128.x, r128.x)));
+#pragma unroll
+            for (int cl = 0; cl < kCpl; ++cl) {
+              qa[cl] = __ffma2_rn(make_float2(-qa[cl].y, qa[cl].x), make_float2(r128[cl].y, r128[cl].y),
+                                  __fmul2_rn(qa[cl], make_float2(r128[cl].x, r128[cl].x)));
+              qb[cl] = __ffma2_rn(make_float2(-qb[cl].y, qb[cl].x), make_float2(r128[cl].y, r128[cl].y),
+                                  __fmul2_rn(qb[cl], make_float2(r128[cl].x, r128[cl].x)));
+            }
+          }
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           if (!a.test_withhold) mbar_arrive_warp(&full[st]);
@@ -498,6 +596,8 @@ cudaError_t mac_tc_prepare() {
   const void* fns[] = {reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 32>),
                        reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 32>),
                        reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 32>),
+                       reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 16>),
                        reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 16>),
                        reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 16>),
                        reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)};
@@ -526,6 +626,7 @@ int tc_prec(int precision) {
   return precision == FDD_PREC_BF16_HILO ? kBf16HiLo
          : precision == FDD_PREC_BF16    ? kBf16
          : precision == FDD_PREC_FP16    ? kF16
+         : precision == FDD_PREC_FP8     ? kF8
                                          : -1;
 }
 }  // namespace
@@ -570,7 +671,7 @@ cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* sc
   const size_t y_elem = a.out_kind == 2 ? sizeof(float) : sizeof(float2);
   cudaError_t e;
   if (x_in_place && y_in_place) {
-    if (prec == kF16 && !a.absmax_ready) {
+    if ((prec == kF16 || prec == kF8) && !a.absmax_ready) {
       BinAbsmaxArgs t{a.X, a.x_bin_stride, a.n_series * a.n_chan, a.n_bins, absmax};
       if ((e = launch_bin_absmax(t, s)) != cudaSuccess) return e;
     }
@@ -589,7 +690,8 @@ cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* sc
                                               a.n_chan;
   void* y_scratch = blk + align_up(x_block);
   const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
-  if (prec == kF16 && x_in_place && !a.absmax_ready) {
+  const bool scaled = prec == kF16 || prec == kF8;
+  if (scaled && x_in_place && !a.absmax_ready) {
     BinAbsmaxArgs t{a.X, a.x_bin_stride, a.n_series * a.n_chan, a.n_bins, absmax};
     if ((e = launch_bin_absmax(t, s)) != cudaSuccess) return e;
   }
@@ -602,12 +704,12 @@ cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* sc
     if (x_in_place) {
       c.X = a.X + k0 * a.x_bin_stride;
     } else {
-      if (prec == kF16) {
+      if (scaled) {
         e = cudaMemsetAsync(absmax + k0, 0, sizeof(unsigned int) * static_cast<size_t>(nb), s);
         if (e != cudaSuccess) return e;
       }
       BinTransposeArgs t{a.X, a.x_chan_stride, rows, k0, nb, x_scratch,
-                         prec == kF16 ? absmax + k0 : nullptr};
+                         scaled ? absmax + k0 : nullptr};
       if ((e = launch_bin_transpose(t, s)) != cudaSuccess) return e;
       c.X = x_scratch;
       c.x_bin_stride = rows;
@@ -645,9 +747,12 @@ static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cu
   else if (prec == kBf16)
     fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 16>)
              : reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 32>);
-  else
+  else if (prec == kF16)
     fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)
              : reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>);
+  else
+    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 16>)
+             : reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 32>);
   note_launches(1);
   return cudaLaunchKernel(fn, dim3(grid),
                           dim3(kThreads), params, mac_tc_smem_bytes(), s);

@@ -196,7 +196,7 @@ cudaError_t launch_mac_spin(const MacArgs& a, const SpinGeometry& sg, const Phas
   unsigned int* absmax = reinterpret_cast<unsigned int*>(p);
   p += align_up(sizeof(unsigned int) * static_cast<size_t>(kb) * G);
   unsigned int* gmax = reinterpret_cast<unsigned int*>(p);
-  const bool f16 = precision == FDD_PREC_FP16;
+  const bool f16 = precision == FDD_PREC_FP16 || precision == FDD_PREC_FP8;  // scaled data
   for (int64_t g0 = 0; g0 < n_g; g0 += kb) {
     const int nbg = static_cast<int>((n_g - g0) < kb ? (n_g - g0) : kb);
     const int64_t k_lo = sg.k_min + g0 * G;

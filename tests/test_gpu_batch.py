@@ -86,7 +86,7 @@ def test_batch_matches_oracle(output):
     xs = _inputs()
     with fdd.Batch(BEAMS, autotune=False, **_common(output)) as batch:
         assert batch.info["n_waves"] == 1
-        assert batch.info["mac_variant"] == fdd.FDD_MAC_W12_8X8
+        assert batch.info["mac_variant"] == fdd.FDD_MAC_G12_4X8
         # every beam's last block of <= 1024 trials runs on 128-trial blocks
         assert batch.info["tail_variant"] == fdd.FDD_MAC_Q_4X4
         assert batch.in_offsets == list(np.cumsum([0] + [b[0] * N_CHAN for b in BEAMS])[:-1])

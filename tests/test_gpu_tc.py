@@ -171,3 +171,38 @@ def test_tc_bin_windows_equal_the_whole_range(n_series):
         with pytest.raises(fdd.FddError) as e:
             plan.dedisperse_spectra_bins(dX, K, n_series, K - 2, 3, 0, n_dm, full, K)
         assert e.value.status == fdd.FDD_ERR_INVALID_ARG
+
+
+FP8_REL_L2 = 0.1  # E4M3: three mantissa bits, ~2^-4 per element (reported, not the 3e-3 gate)
+
+
+@pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
+    (32, 1024, 4096, 0.0, 0.5, 2048),  # the 32-beam tensor-core shape, 16 channel tiles of 64
+    (5, 70, 256, 0.0, 0.5, 300),       # partial groups, a ragged 64-channel tile
+])
+def test_fp8_form_error_is_measured(n_series, n_chan, L, dm0, ddm, n_dm):
+    """FP8 E4M3 phasors and data on kind::f8f6f4 (the 8-bit direction of Sect.
+    5): its rel-L2 against FP64 is measured and printed; it stays below 10 %
+    (the three mantissa bits give ~2^-4 per element) and above the 16-bit
+    forms' gate, which it does not meet."""
+    dms = dm0 + ddm * np.arange(n_dm)
+    w = _workload(n_chan, L, dms, n_series, band=(1250.0, 1550.0), t_samp=0.25e-3)
+    K = L // 2 + 1
+    rng = np.random.default_rng(n_chan)
+    X = rng.standard_normal((n_series, n_chan, K)) + 1j * rng.standard_normal((n_series, n_chan, K))
+    with fdd.Plan(**params_for(w, precision=fdd.FDD_PREC_FP8)) as plan:
+        dX = complex_to_device(X, plan.info["bin_pitch"])
+        dY = torch.empty((n_series, n_dm, K, 2), device="cuda")
+        plan.dedisperse_spectra(dX, plan.info["bin_pitch"], n_series, 0, n_dm, dY, K)
+        torch.cuda.synchronize()
+        plan.query()
+    Y = device_to_complex(dY, K)
+    bins = np.unique(np.concatenate([[0, 1, K - 1], rng.integers(2, K - 1, 5)]))
+    d = oracle.delays(w.channel_centres(), dms, w.t_samp_s)
+    errs = []
+    for b in range(min(n_series, 3)):
+        ref = oracle.fdd_bins(X[b][:, bins], bins, L, d)
+        errs.append(rel_l2(Y[b][:, bins], ref))
+    err = float(np.sqrt(np.mean(np.square(errs))))
+    print(f"FP8 E4M3 form: rel-L2 vs FP64 {err:.3e}")
+    assert TC_REL_L2 < err <= FP8_REL_L2
