@@ -375,7 +375,9 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     const int dms = fdd::mac_variant_trials_per_block(variant);
     const int tv = B->tail_variant;
     const int tail_dms = tv >= 0 ? fdd::mac_variant_trials_per_block(tv) : 0;
-    const bool tails = tv >= 0 && dms >= 2048 && tail_dms < dms;
+    // (the three-product tile runs a ragged last block of up to half its
+    // trials in the same launch, at half its work: no second launch)
+    const bool tails = tv >= 0 && dms >= 2048 && tail_dms < dms && variant != FDD_MAC_G12_4X8;
     for (auto& wv : B->waves) {
       wv.h_sets.assign(wv.count, fdd::BatchSet{});
       wv.h_tail.clear();

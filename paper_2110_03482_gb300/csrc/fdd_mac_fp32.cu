@@ -597,6 +597,10 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
   const int lane = threadIdx.x & 31;
   const int n_iter = (a.n_chan + kCh - 1) / kCh;
   const int jblk = dm_block * Ly::kDms;
+  // A ragged last block of at most half the trials needs only the a's 0..31:
+  // its second consumer warp of each bin and the producers' second Z skip
+  // their work (the stage handshake stays the same).
+  const bool half = a.n_dm - jblk <= Ly::kDms / 2;
   bool ok = true;
 
   if (warp >= Ly::kCons) {
@@ -635,16 +639,17 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
           const PhaseConst p = pcs[c];
           const uint32_t base = top32_mul(ku, p.u_lo, p.u_hi);
           const float2 w0 = unit_phasor(base + top32_mul(m_z0, p.v_lo, p.v_hi));
-          const float2 w1 = unit_phasor(base + top32_mul(m_z1, p.v_lo, p.v_hi));
           const float2 wp = unit_phasor(top32_mul(m_p, p.v_lo, p.v_hi));
           const float2 xv = x[ch];
           const float z0r = xv.x * w0.x - xv.y * w0.y, z0i = xv.x * w0.y + xv.y * w0.x;
-          const float z1r = xv.x * w1.x - xv.y * w1.y, z1i = xv.x * w1.y + xv.y * w1.x;
           float* grp = st + ch * Ly::kBins * Ly::kGFL;
           grp[lane] = z0r;
           grp[Ly::kA + lane] = z0i;
-          grp[32 + lane] = z1r;
-          grp[Ly::kA + 32 + lane] = z1i;
+          if (!half) {
+            const float2 w1 = unit_phasor(base + top32_mul(m_z1, p.v_lo, p.v_hi));
+            grp[32 + lane] = xv.x * w1.x - xv.y * w1.y;
+            grp[Ly::kA + 32 + lane] = xv.x * w1.y + xv.y * w1.x;
+          }
           grp[2 * Ly::kA + lane] = wp.x;
           grp[2 * Ly::kA + Ly::kT + lane] = wp.y;
         }
@@ -669,7 +674,7 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
       ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
       if (!ok) break;
       const float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
-      const int nc = a.n_chan - it * kCh;
+      const int nc = (half && h == 1) ? 0 : a.n_chan - it * kCh;
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         if (ch < nc) {
@@ -709,7 +714,7 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
       }
       dev::mbar_arrive_warp(&empty[s]);
     }
-    if (ok && k < a.n_bins) {
+    if (ok && k < a.n_bins && !(half && h == 1)) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {

@@ -202,11 +202,13 @@ __device__ __forceinline__ void mma16(uint32_t d, uint64_t adesc, uint64_t bdesc
   }
 }
 
+// 21 warps at one CTA per SM: one of the four schedulers holds six of them,
+// and a scheduler's 16384 registers cap the kernel at 80 per thread.
 // kPrec: kBf16HiLo (phasors as BF16 hi + lo, four MMAs per K step), kBf16
 // (BF16 only), kF16 (FP16 phasors and scaled FP16 data) or kF8 (FP8 E4M3
 // phasors and scaled E4M3 data, kind::f8f6f4, 64 channels per stage).
 template <int kPrec, int kBeams>
-__global__ void __maxnreg__(96) mac_tc_kernel(const MacArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
   constexpr bool kHiLo = kPrec == kBf16HiLo;
   constexpr bool kScaled = kPrec == kF16 || kPrec == kF8;  // per-bin data scale

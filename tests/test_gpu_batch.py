@@ -87,19 +87,23 @@ def test_batch_matches_oracle(output):
     with fdd.Batch(BEAMS, autotune=False, **_common(output)) as batch:
         assert batch.info["n_waves"] == 1
         assert batch.info["mac_variant"] == fdd.FDD_MAC_G12_4X8
-        # every beam's last block of <= 1024 trials runs on 128-trial blocks
-        assert batch.info["tail_variant"] == fdd.FDD_MAC_Q_4X4
+        # the three-product tile runs a beam's ragged last block (<= 1024
+        # trials) at half work inside the same persistent launch
+        assert batch.info["tail_variant"] == -1
         assert batch.in_offsets == list(np.cumsum([0] + [b[0] * N_CHAN for b in BEAMS])[:-1])
         o, _, _ = _run(batch, xs, output)
     _check(batch, o, _refs(xs), output)
 
 
-@pytest.mark.parametrize("variant", [fdd.FDD_MAC_Q12_8X8, fdd.FDD_MAC_Q_4X4])
+@pytest.mark.parametrize("variant", [fdd.FDD_MAC_W12_8X8, fdd.FDD_MAC_Q12_8X8, fdd.FDD_MAC_Q_4X4])
 def test_batch_other_tiles_match_oracle(variant):
     xs = _inputs()
     with fdd.Batch(BEAMS, autotune=False, mac_variant=variant + 1,
                    **_common(fdd.FDD_OUT_SPECTRA)) as batch:
         assert batch.info["mac_variant"] == variant
+        if variant == fdd.FDD_MAC_W12_8X8:
+            # its last blocks of <= 1024 trials go to a second launch on 128-trial blocks
+            assert batch.info["tail_variant"] == fdd.FDD_MAC_Q_4X4
         o, _, _ = _run(batch, xs, fdd.FDD_OUT_SPECTRA)
     _check(batch, o, _refs(xs), fdd.FDD_OUT_SPECTRA)
 
