@@ -1013,7 +1013,10 @@ def run_tc_workload(args) -> None:
 
 def run_batch(args) -> None:
     """Whole-batch throughput of the batching form (unpack, transforms and one
-    persistent phase-rotate-and-sum launch per wave, replayed as a CUDA graph)."""
+    persistent phase-rotate-and-sum launch per wave).  Resident when input and
+    output fit (replayed as a CUDA graph), else streamed: every beam's window
+    generated on the device by the source, every beam's output block handed
+    to a sink that counts it."""
     import torch
 
     import paper_2110_03482_gb300 as fdd
@@ -1027,29 +1030,50 @@ def run_batch(args) -> None:
     common = dict(n_chan=bw.n_chan, nu_lo_mhz=bw.nu_lo_mhz, dnu_mhz=bw.dnu_mhz,
                   t_samp_s=bw.t_samp_s, in_dtype=fdd.FDD_IN_F32, chunk_len=0,
                   output={"spectra": fdd.FDD_OUT_SPECTRA, "power": fdd.FDD_OUT_POWER}[bw.output],
-                  workspace_limit=64 << 30)
+                  workspace_limit=int(min(args.workspace_gib, 100.0) * (1 << 30)))
+    gen_kw = [synth.batch_beam_args(bw, desc, args.seed, b)[0] for b, desc in enumerate(beams)]
     t0 = time.perf_counter()
     with fdd.Batch(beams, autotune=True, **common) as batch:
         plan_s = time.perf_counter() - t0
         info = batch.info
-        # float32 N(0,1) noise with one dispersed pulse per beam, made on the
-        # device by the counter-based generator (beam by beam, in place)
-        d_in = torch.empty(info["in_elems"], dtype=torch.float32, device="cuda")
-        for b, desc in enumerate(beams):
-            kw, _ = synth.batch_beam_args(bw, desc, args.seed, b)
-            off = batch.in_offsets[b]
-            synth.gpu.filterbank(d_in[off: off + desc[0] * bw.n_chan], n_rows=desc[0], t0=0, **kw)
-        out = torch.empty(info["out_elems"] * (2 if bw.output == "spectra" else 1), device="cuda")
+        in_bytes = 4 * info["in_elems"]
+        out_bytes = int(info["out_bytes"])
+        resident = in_bytes + out_bytes <= RESIDENT_INPUT_BYTES
         stream = torch.cuda.current_stream()
+        s_handle = stream.cuda_stream
+        gen = synth.gpu.BeamWindows(gen_kw)
+        delivered = [0]
+        if resident:
+            # float32 N(0,1) noise with one dispersed pulse per beam, made on the
+            # device by the counter-based generator (beam by beam, in place)
+            d_in = torch.empty(info["in_elems"], dtype=torch.float32, device="cuda")
+            for b, desc in enumerate(beams):
+                gen.fill(b, d_in.data_ptr() + 4 * batch.in_offsets[b], 0, desc[0], s_handle)
+            out = torch.empty(info["out_elems"] * (2 if bw.output == "spectra" else 1),
+                              device="cuda")
+
+            def step():
+                batch.execute(d_in, out, stream)
+        else:
+            def source(beam, t_begin, n, d_window, ready, s):
+                gen.fill(beam, d_window, t_begin, n, s)
+
+            def sink(blk, s):
+                delivered[0] += blk["n_dm"] * blk["row_len"] * (8 if bw.output == "spectra" else 4)
+                return None
+
+            def step():
+                batch.execute_stream(source, sink, stream)
         for _ in range(max(args.warmup, 1)):
-            batch.execute(d_in, out, stream)
+            step()
         torch.cuda.synchronize()
+        delivered[0] = 0
         clocks = Clocks(gpu_uuid(torch.cuda.get_device_properties(0), 0))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            batch.execute(d_in, out, stream)
+            step()
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
@@ -1063,7 +1087,8 @@ def run_batch(args) -> None:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Philox4x32-10 noise + one dispersed pulse per beam, "
                     "generated on the device)",
-            "form": "batching (persistent launch per wave, CUDA graph, autotuned tile)",
+            "form": "batching (persistent launch per wave, autotuned tile)" +
+                    (", CUDA graph" if resident else ", streamed windows and output blocks"),
             "config": {"workload": bw.name, "beams": bw.n_beams, "n_chan": bw.n_chan,
                        "n_t_range": [min(n_ts), max(n_ts)], "n_t_divisor": args.batch_n_t_div,
                        "trials_range": [min(b[3] for b in beams), max(b[3] for b in beams)],
@@ -1072,7 +1097,11 @@ def run_batch(args) -> None:
                        "tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]],
                        "tail_tile": (fdd.MAC_VARIANT_NAMES[info["tail_variant"]]
                                      if info["tail_variant"] >= 0 else None),
-                       "autotune_ms": info["autotune_ms"], "plan_seconds": plan_s},
+                       "autotune_ms": info["autotune_ms"], "plan_seconds": plan_s,
+                       "input_bytes": in_bytes, "output_bytes": out_bytes,
+                       "io": "resident" if resident else
+                             "streamed (input windows generated per beam on the device; output "
+                             f"blocks counted: {delivered[0] // max(args.steps, 1)} B per step)"},
             "fp32_frac_whole_step": FLOPS_PER_MAC * macs / (ms / 1e3) / peak,
             "macs_per_step": macs, "clocks": clk}
     print(json.dumps(line), flush=True)

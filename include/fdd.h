@@ -531,6 +531,23 @@ fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offs
  */
 fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_stream_t stream);
 
+/*
+ * Execute the batch streamed (fdd_execute_stream's callbacks and contracts):
+ * the source fills one window per beam (t_begin 0, the beam's n_t samples,
+ * the common layout) through a ring of two windows of the longest beam, so
+ * the concatenated input never has to be on the device; per wave the
+ * persistent launch writes into one of two output slots of the wave's size,
+ * and the sink receives one block per beam (n_beams 1, chunk 0, dm_first 0,
+ * the beam's n_dm trials x n_bins, row_len = row_pitch = n_bins).  A sink
+ * that reads a wave's blocks on another stream returns a release event for
+ * its last block of the wave (an event recorded after all of them).  The
+ * first call allocates the rings and binds the work sets to them.  Not
+ * captured as a graph.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_ALLOC (first
+ * call), FDD_ERR_CUDA, FDD_ERR_CUFFT, a callback's own status.
+ */
+fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* source_user,
+                                    fdd_sink_fn sink, void* sink_user, fdd_stream_t stream);
+
 /* Release the batch plan (synchronises the device first).  NULL is ignored. */
 fdd_status fdd_batch_destroy(fdd_batch_t b);
 

@@ -55,7 +55,8 @@ EXPORTS = [
     "fdd_execute_host", "fdd_execute_stream", "fdd_dedisperse_spectra", "fdd_profile_enable",
     "fdd_profile_read",
     "fdd_destroy", "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
-    "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins", "fdd_tdd_execute",
+    "fdd_batch_execute", "fdd_batch_destroy", "fdd_batch_execute_stream",
+    "fdd_dedisperse_spectra_bins", "fdd_tdd_execute",
     "fdd_debug_stall_test", "fdd_debug_fail_alloc",
 ]
 FDD_STATIC_MAX_CHAN = 8192
@@ -253,6 +254,7 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.fdd_batch_execute.argtypes = [vp, vp, vp, vp]
         L.fdd_batch_destroy.argtypes = [vp]
+        L.fdd_batch_execute_stream.argtypes = [vp, SOURCE_FN, vp, SINK_FN, vp, vp]
         L.fdd_profile_enable.argtypes = [vp, i32]
         L.fdd_profile_read.argtypes = [vp, ctypes.POINTER(fdd_profile)]
         for name in ["fdd_plan_geometry", "fdd_plan", "fdd_query", "fdd_execute",
@@ -260,7 +262,8 @@ def lib() -> ctypes.CDLL:
                      "fdd_dedisperse_spectra",
                      "fdd_profile_enable", "fdd_profile_read", "fdd_destroy",
                      "fdd_dedisperse_spectra_static", "fdd_batch_plan", "fdd_batch_query",
-                     "fdd_batch_execute", "fdd_batch_destroy", "fdd_dedisperse_spectra_bins",
+                     "fdd_batch_execute", "fdd_batch_destroy", "fdd_batch_execute_stream",
+                     "fdd_dedisperse_spectra_bins",
                      "fdd_tdd_execute", "fdd_debug_stall_test", "fdd_debug_fail_alloc"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -388,6 +391,42 @@ def fdd_execute(plan: int, d_in, d_out, stream=None) -> None:
     _check(lib().fdd_execute(plan, _ptr(d_in), _ptr(d_out), _stream(stream)))
 
 
+def _callbacks(source, sink, err):
+    """ctypes callbacks around Python source / sink functions; exceptions are
+    collected in err and end the call."""
+    def _src(_user, beam, t_begin, n, d_window, ready, s):
+        try:
+            source(int(beam), int(t_begin), int(n), int(d_window), ready, s)
+            return FDD_OK
+        except BaseException as e:  # noqa: BLE001 -- re-raised by the caller
+            err.append(e)
+            return FDD_ERR_INVALID_ARG
+
+    def _snk(_user, blk, s):
+        try:
+            ev = sink(blk.contents.as_dict(), s)
+            blk.contents.release_event = ev
+            return FDD_OK
+        except BaseException as e:  # noqa: BLE001 -- re-raised by the caller
+            err.append(e)
+            return FDD_ERR_INVALID_ARG
+
+    c_src = SOURCE_FN(_src) if source is not None else ctypes.cast(None, SOURCE_FN)
+    return c_src, SINK_FN(_snk)
+
+
+def fdd_batch_execute_stream(batch: int, source, sink, stream=None) -> None:
+    """Streamed batch execute: ``source(beam, 0, n_t, d_window, ready_event,
+    stream)`` per beam, ``sink(block, stream)`` per beam's output block (see
+    fdd_execute_stream)."""
+    err = []
+    c_src, c_snk = _callbacks(source, sink, err)
+    status = lib().fdd_batch_execute_stream(batch, c_src, None, c_snk, None, _stream(stream))
+    if err:
+        raise err[0]
+    _check(status)
+
+
 def fdd_execute_stream(plan: int, source, sink, stream=None, d_in=None) -> None:
     """Streamed execute.  Input: ``d_in`` resident on the device (source None),
     or ``source(beam, t_begin, n_samples, d_window, ready_event, stream)``
@@ -397,26 +436,7 @@ def fdd_execute_stream(plan: int, source, sink, stream=None, d_in=None) -> None:
     returns the handle of a CUDA event recorded after those reads (else None).
     An exception in a callback ends the call and is raised here."""
     err = []
-
-    def _src(_user, beam, t_begin, n, d_window, ready, s):
-        try:
-            source(int(beam), int(t_begin), int(n), int(d_window), ready, s)
-            return FDD_OK
-        except BaseException as e:  # noqa: BLE001 -- re-raised below
-            err.append(e)
-            return FDD_ERR_INVALID_ARG
-
-    def _snk(_user, blk, s):
-        try:
-            ev = sink(blk.contents.as_dict(), s)
-            blk.contents.release_event = ev
-            return FDD_OK
-        except BaseException as e:  # noqa: BLE001 -- re-raised below
-            err.append(e)
-            return FDD_ERR_INVALID_ARG
-
-    c_src = SOURCE_FN(_src) if source is not None else ctypes.cast(None, SOURCE_FN)
-    c_snk = SINK_FN(_snk)
+    c_src, c_snk = _callbacks(source, sink, err)
     status = lib().fdd_execute_stream(plan, _ptr(d_in), c_src, None, c_snk, None,
                                       _stream(stream))
     if err:
@@ -512,6 +532,9 @@ class Batch:
 
     def execute(self, d_in, d_out, stream=None):
         fdd_batch_execute(self.handle, d_in, d_out, stream)
+
+    def execute_stream(self, source, sink, stream=None):
+        fdd_batch_execute_stream(self.handle, source, sink, stream)
 
     def close(self):
         if self.handle:

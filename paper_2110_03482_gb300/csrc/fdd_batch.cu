@@ -62,6 +62,17 @@ struct fdd_batch_s {
   void* d_fftwork = nullptr;
   size_t bytes_held = 0;
   std::map<int64_t, cufftHandle> r2c;  // by transform length
+  // streamed execute (fdd_batch_execute_stream, made on its first call): two
+  // input windows (the longest beam), and per wave two output slots (the
+  // wave's whole output) with the work sets bound to each
+  void* d_win[2] = {nullptr, nullptr};
+  void* d_wout[2] = {nullptr, nullptr};
+  size_t wout_bytes = 0;
+  std::vector<fdd::BatchSet*> d_sets_slot[2];
+  unsigned win_next = 0, out_next = 0;
+  bool win_used[2] = {false, false};
+  cudaEvent_t win_free[2] = {nullptr, nullptr};
+  void* out_release[2] = {nullptr, nullptr};
   // CUDA graph of the whole execute, for the buffers it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -95,6 +106,13 @@ void release(fdd_batch_s* B) {
   for (auto& w : B->waves) {
     if (w.d_sets) cudaFree(w.d_sets);
     if (w.d_tail) cudaFree(w.d_tail);
+  }
+  for (int k = 0; k < 2; ++k) {
+    for (fdd::BatchSet* p : B->d_sets_slot[k])
+      if (p) cudaFree(p);
+    if (B->d_win[k]) cudaFree(B->d_win[k]);
+    if (B->d_wout[k]) cudaFree(B->d_wout[k]);
+    if (B->win_free[k]) cudaEventDestroy(B->win_free[k]);
   }
   void* ptrs[] = {B->d_pc, B->d_xw, B->d_pool, B->d_counter, B->d_fftwork};
   for (void* q : ptrs)
@@ -473,21 +491,27 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
       for (size_t i = 0; i < w0.h_tail.size(); ++i)
         bind_set(B, w0m.h_tail[i], w0.tail_beam[i], scratch, origin);
       if ((tst = upload_wave(w0, nullptr))) break;
-      float ms = 0.f, tot = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaMemset(B->d_counter, 0, 2 * sizeof(unsigned long long));
-        cudaEventRecord(e0);
-        fdd::launch_mac_batch(w0.d_sets, w0.count, w0.n_items, B->d_counter, v, B->ctas,
-                              p->n_chan, nullptr);
-        if (w0.n_tail_items)
-          fdd::launch_mac_batch(w0.d_tail, static_cast<int>(w0.h_tail.size()), w0.n_tail_items,
-                                B->d_counter + 1, B->tail_variant, B->tail_ctas, p->n_chan,
-                                nullptr);
-        cudaEventRecord(e1);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep) tot = ms;  // the first launch is a warm-up
-      }
+      // Each launch times a bounded share of wave 0's items (eight rounds of
+      // the persistent grid rank the tiles whatever the wave's size), scaled
+      // to the whole wave: main launch plus, for a tile with one, tail launch.
+      auto timed = [&](fdd::BatchSet* sets, int n_sets, long long n_items, int tile, int ctas,
+                       unsigned long long* counter) -> double {
+        const long long part = std::min<long long>(n_items, 8LL * ctas);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch is a warm-up
+          cudaMemset(counter, 0, sizeof(unsigned long long));
+          cudaEventRecord(e0);
+          fdd::launch_mac_batch(sets, n_sets, part, counter, tile, ctas, p->n_chan, nullptr);
+          cudaEventRecord(e1);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        return static_cast<double>(ms) * static_cast<double>(n_items) / static_cast<double>(part);
+      };
+      double tot = timed(w0.d_sets, w0.count, w0.n_items, v, B->ctas, B->d_counter);
+      if (w0.n_tail_items)
+        tot += timed(w0.d_tail, static_cast<int>(w0.h_tail.size()), w0.n_tail_items,
+                     B->tail_variant, B->tail_ctas, B->d_counter + 1);
       if (cudaGetLastError() != cudaSuccess) {
         tst = report_error(FDD_ERR_CUDA, "autotune launch failed");
         break;
@@ -581,6 +605,102 @@ fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_s
     b->graph_out = d_out;
   }
   B_CUDA(cudaGraphLaunch(b->graph, s));
+  return FDD_OK;
+}
+
+fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* source_user,
+                                    fdd_sink_fn sink, void* sink_user, fdd_stream_t stream) {
+  using fdd::report_error;
+  if (!b) return report_error(FDD_ERR_INVALID_ARG, "batch is NULL");
+  if (!source || !sink) return report_error(FDD_ERR_INVALID_ARG, "NULL source or sink");
+  int dev = -1;
+  B_CUDA(cudaGetDevice(&dev));
+  if (dev != b->device)
+    return report_error(FDD_ERR_INVALID_ARG, "batch plan belongs to another device");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  fdd_status st;
+  const size_t esz = b->p.in_dtype == FDD_IN_U8 ? 1 : 4;
+  const size_t oesz = b->p.output == FDD_OUT_SPECTRA ? 8 : 4;
+  if (!b->d_win[0]) {
+    // rings: windows of the longest beam, output slots of the largest wave,
+    // and each wave's work sets bound to each output slot
+    int64_t nt_max = 0;
+    for (auto& d : b->beams) nt_max = std::max<int64_t>(nt_max, d.n_t);
+    size_t wmax = 0;
+    for (auto& w : b->waves) {
+      size_t o = 0;
+      for (int i = 0; i < w.count; ++i)
+        o += oesz * static_cast<size_t>(b->n_bins[w.first + i]) * b->beams[w.first + i].n_dm;
+      wmax = std::max(wmax, o);
+    }
+    b->wout_bytes = wmax;
+    for (int k = 0; k < 2; ++k) {
+      if ((st = alloc(b, &b->d_win[k], esz * static_cast<size_t>(b->p.n_chan) * nt_max)))
+        return st;
+      if ((st = alloc(b, &b->d_wout[k], wmax))) return st;
+      B_CUDA(cudaEventCreateWithFlags(&b->win_free[k], cudaEventDisableTiming));
+      for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+        auto& w = b->waves[wi];
+        const int64_t origin = b->out_off[w.first];
+        std::vector<fdd::BatchSet> sets = w.h_sets, tails = w.h_tail;
+        for (int i = 0; i < w.count; ++i) bind_set(b, sets[i], w.first + i, b->d_wout[k], origin);
+        for (size_t i = 0; i < tails.size(); ++i)
+          bind_set(b, tails[i], w.tail_beam[i], b->d_wout[k], origin);
+        fdd::BatchSet* d = nullptr;
+        const size_t n = sets.size() + tails.size();
+        if ((st = alloc(b, reinterpret_cast<void**>(&d), sizeof(fdd::BatchSet) * n))) return st;
+        b->d_sets_slot[k].push_back(d);
+        B_CUDA(cudaMemcpy(d, sets.data(), sizeof(fdd::BatchSet) * sets.size(),
+                          cudaMemcpyHostToDevice));
+        if (!tails.empty())
+          B_CUDA(cudaMemcpy(d + sets.size(), tails.data(), sizeof(fdd::BatchSet) * tails.size(),
+                            cudaMemcpyHostToDevice));
+      }
+    }
+  }
+  for (auto& kv : b->r2c) B_CUFFT(cufftSetStream(kv.second, s));
+  for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+    const auto& w = b->waves[wi];
+    for (int i = 0; i < w.count; ++i) {
+      const int bm = w.first + i;
+      const int slot = static_cast<int>(b->win_next++ & 1);
+      void* ready = b->win_used[slot] ? static_cast<void*>(b->win_free[slot]) : nullptr;
+      st = source(source_user, bm, 0, b->beams[bm].n_t, b->d_win[slot], ready, stream);
+      if (st != FDD_OK) return report_error(st, "the input source failed");
+      fdd::UnpackArgs ua{b->d_win[slot], b->p.in_dtype, b->p.in_layout, b->p.n_chan,
+                         b->beams[bm].n_t, 0, b->L[bm], b->d_xw, b->L[bm]};
+      B_CUDA(fdd::launch_unpack(ua, s));
+      B_CUDA(cudaEventRecord(b->win_free[slot], s));
+      b->win_used[slot] = true;
+      B_CUFFT(cufftExecR2C(b->r2c.at(b->L[bm]), b->d_xw,
+                           reinterpret_cast<cufftComplex*>(b->d_pool + b->spec_off[bm])));
+    }
+    const int k = static_cast<int>(b->out_next++ & 1);
+    if (b->out_release[k]) {  // the sink's reads of this slot's last wave
+      B_CUDA(cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(b->out_release[k]), 0));
+      b->out_release[k] = nullptr;
+    }
+    fdd::BatchSet* d_sets = b->d_sets_slot[k][wi];
+    B_CUDA(cudaMemsetAsync(b->d_counter + 2 * wi, 0, 2 * sizeof(unsigned long long), s));
+    B_CUDA(fdd::launch_mac_batch(d_sets, w.count, w.n_items, b->d_counter + 2 * wi, b->variant,
+                                 b->ctas, b->p.n_chan, s));
+    if (w.n_tail_items)
+      B_CUDA(fdd::launch_mac_batch(d_sets + w.count, static_cast<int>(w.h_tail.size()),
+                                   w.n_tail_items, b->d_counter + 2 * wi + 1, b->tail_variant,
+                                   b->tail_ctas, b->p.n_chan, s));
+    const int64_t origin = b->out_off[w.first];
+    void* release = nullptr;
+    for (int i = 0; i < w.count; ++i) {
+      const int bm = w.first + i;
+      fdd_block blk{bm, 1, 0, 0, b->beams[bm].n_dm,
+                    static_cast<char*>(b->d_wout[k]) + oesz * (b->out_off[bm] - origin),
+                    b->n_bins[bm], b->n_bins[bm], 0, nullptr};
+      st = sink(sink_user, &blk, stream);
+      if (st != FDD_OK) return report_error(st, "the output sink failed");
+      if (blk.release_event) release = blk.release_event;  // the wave's last one counts
+    }
+    b->out_release[k] = release;
+  }
   return FDD_OK;
 }
 

@@ -587,8 +587,11 @@ struct G3 {
 // local bin bin_tile * 4 and trials dm_block * 2048 + .. of one set of
 // spectra; ring stages and barrier phases continue from iteration it0.
 // Returns false after a timeout.
-template <int kCh, int kStages>
-__device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs, float* stages,
+// kHalf: a ragged last block of at most half the trials needs only the a's
+// 0..31: its second consumer warp of each bin and the producers' second Z
+// skip their work (the stage handshake stays the same).
+template <int kCh, int kStages, bool kHalf>
+__device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs, float* stages,
                                         uint64_t* full, uint64_t* empty,
                                         volatile int* abort_flag, int bin_tile, int dm_block,
                                         int series, uint32_t it0) {
@@ -597,10 +600,7 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
   const int lane = threadIdx.x & 31;
   const int n_iter = (a.n_chan + kCh - 1) / kCh;
   const int jblk = dm_block * Ly::kDms;
-  // A ragged last block of at most half the trials needs only the a's 0..31:
-  // its second consumer warp of each bin and the producers' second Z skip
-  // their work (the stage handshake stays the same).
-  const bool half = a.n_dm - jblk <= Ly::kDms / 2;
+  constexpr bool half = kHalf;
   bool ok = true;
 
   if (warp >= Ly::kCons) {
@@ -668,13 +668,22 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) A[i][m] = B[i][m] = C[i][m] = make_float2(0.f, 0.f);
-    for (int it = 0; it < n_iter; ++it) {
+    if (half && h == 1) {  // nothing to accumulate: keep the stage handshake
+      for (int it = 0; it < n_iter; ++it) {
+        const uint32_t g = it0 + it;
+        const int s = g % kStages;
+        ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
+        if (!ok) break;
+        dev::mbar_arrive_warp(&empty[s]);
+      }
+    }
+    for (int it = 0; it < n_iter && !(half && h == 1); ++it) {
       const uint32_t g = it0 + it;
       const int s = g % kStages;
       ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
       if (!ok) break;
       const float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
-      const int nc = (half && h == 1) ? 0 : a.n_chan - it * kCh;
+      const int nc = a.n_chan - it * kCh;
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         if (ch < nc) {
@@ -746,6 +755,18 @@ __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs,
     if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
   }
   return ok;
+}
+
+template <int kCh, int kStages>
+__device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs, float* stages,
+                                        uint64_t* full, uint64_t* empty,
+                                        volatile int* abort_flag, int bin_tile, int dm_block,
+                                        int series, uint32_t it0) {
+  if (a.n_dm - dm_block * G3<kCh, kStages>::kDms <= G3<kCh, kStages>::kDms / 2)
+    return g3_body<kCh, kStages, true>(a, pcs, stages, full, empty, abort_flag, bin_tile,
+                                       dm_block, series, it0);
+  return g3_body<kCh, kStages, false>(a, pcs, stages, full, empty, abort_flag, bin_tile,
+                                      dm_block, series, it0);
 }
 
 template <int kCh, int kStages>

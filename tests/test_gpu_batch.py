@@ -152,3 +152,42 @@ def test_batch_rejects_what_it_does_not_do():
     with pytest.raises(fdd.FddError) as e:
         fdd.Batch([(100, -1.0, 1.0, 4)], **_common(fdd.FDD_OUT_POWER))
     assert e.value.status == fdd.FDD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("variant,limit", [(0, 0), (fdd.FDD_MAC_W12_8X8 + 1, 0),
+                                           (fdd.FDD_MAC_Q_4X8 + 1, "waves")])
+def test_batch_streamed_equals_resident_execute(variant, limit):
+    """fdd_batch_execute_stream (a window per beam from the source, one block
+    per beam to the sink, output slots per wave) gives bit for bit what the
+    resident execute gives: the three-product tile, the warp-specialised tile
+    with its tail launch, and several waves."""
+    xs = _inputs()
+    kw = {}
+    if limit == "waves":
+        kw["workspace_limit"] = 4 * N_CHAN * 8192 + 16 * N_CHAN * len(BEAMS) + (64 << 20) + 1_700_000
+    with fdd.Batch(BEAMS, autotune=False, mac_variant=variant,
+                   **_common(fdd.FDD_OUT_POWER, **kw)) as batch:
+        if limit == "waves":
+            assert batch.info["n_waves"] == 3
+        ref, d_in, _ = _run(batch, xs, fdd.FDD_OUT_POWER)
+        got = torch.full((batch.info["out_elems"],), float("nan"), device="cuda")
+        seen = []
+
+        def source(beam, t0, n, d_window, ready, s):
+            assert t0 == 0 and n == BEAMS[beam][0]
+            fdd.memcpy_async(d_window, d_in.data_ptr() + 4 * batch.in_offsets[beam],
+                             4 * n * N_CHAN, s)
+
+        def sink(blk, s):
+            seen.append(blk["beam_first"])
+            b = blk["beam_first"]
+            fdd.memcpy_async(got.data_ptr() + 4 * batch.out_offsets[b], blk["d_data"],
+                             4 * blk["n_dm"] * blk["row_len"], s)
+            return None
+
+        for _ in range(2):  # the second call reuses the rings
+            seen.clear()
+            batch.execute_stream(source, sink, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert sorted(seen) == list(range(len(BEAMS)))
+            assert np.array_equal(got.cpu().numpy().astype(np.float64), ref)
