@@ -79,6 +79,7 @@ def test_32beam_full_size_time_output_sampled():
         torch.cuda.synchronize()
         plan.query()
         del d_in
+    torch.cuda.empty_cache()  # the next workload needs the device memory back
     assert len(got) == len(beams) * len(trials)
     d = oracle.delays(w.channel_centres(), w.dms()[trials], w.t_samp_s)
     K = (1 << 19) // 2 + 1
@@ -95,6 +96,7 @@ def test_32beam_full_size_time_output_sampled():
 
 
 def test_16beam_full_size_power_streamed_sampled():
+    torch.cuda.empty_cache()
     w = synth.WORKLOADS["fdd_16beam_4096ch_2p21t_8192dm_power"]
     gen = _beams(w)
     beams, chunks, trials = [0, 9], [0, 5], [0, 2047, 2048, 8191]
