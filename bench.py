@@ -770,26 +770,30 @@ def tc_workload_accuracy(fdd, w: synth.Workload, prec: int, seed: int, beams) ->
     rng = np.random.default_rng(seed)
     bins = np.unique(np.concatenate([[0, 1, geo.K - 1], rng.integers(2, geo.K - 1, 5)]))
     ref = oracle.fdd_bins(X[:, bins], bins, geo.L, d)
-    res = {}
-    with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA, n_beams=1,
-                         precision=prec, workspace_limit=8 << 30)) as plan:
-        nb = bins.size
-        host = np.zeros((1, w.n_chan, nb, 2), dtype=np.float32)
-        Xs = X[:, bins].astype(np.complex64)
-        host[0, :, :, 0] = Xs.real
-        host[0, :, :, 1] = Xs.imag
-        dX = torch.from_numpy(host).cuda()
-        got = np.zeros((w.n_dm, nb), dtype=np.complex128)
-        for q, k in enumerate(bins):  # bin windows of one bin (absolute phases)
-            dY = torch.empty((1, w.n_dm, 1, 2), device="cuda")
-            plan.dedisperse_spectra_bins(dX[:, :, q:q + 1].contiguous(), 1, 1, int(k), 1, 0,
-                                         w.n_dm, dY, 1)
-            y = dY.cpu().numpy().astype(np.float64)[0, :, 0]
-            got[:, q] = y[:, 0] + 1j * y[:, 1]
-    res["rel_l2_vs_oracle"] = _rel(got, ref)
-    res["rel_l2_vs_oracle_no_dc"] = _rel(got[:, bins > 0], ref[:, bins > 0])
+    res = {"by_form": {}}
+    nb = bins.size
+    host = np.zeros((1, w.n_chan, nb, 2), dtype=np.float32)
+    Xs = X[:, bins].astype(np.complex64)
+    host[0, :, :, 0] = Xs.real
+    host[0, :, :, 1] = Xs.imag
+    dX = torch.from_numpy(host).cuda()
+    for name, pr in sorted(TC_PREC.items(), key=lambda kv: kv[1] != prec):
+        with fdd.Plan(**dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA, n_beams=1,
+                             precision=pr, workspace_limit=8 << 30)) as plan:
+            got = np.zeros((w.n_dm, nb), dtype=np.complex128)
+            for q, k in enumerate(bins):  # bin windows of one bin (absolute phases)
+                dY = torch.empty((1, w.n_dm, 1, 2), device="cuda")
+                plan.dedisperse_spectra_bins(dX[:, :, q:q + 1].contiguous(), 1, 1, int(k), 1, 0,
+                                             w.n_dm, dY, 1)
+                y = dY.cpu().numpy().astype(np.float64)[0, :, 0]
+                got[:, q] = y[:, 0] + 1j * y[:, 1]
+        res["by_form"][name] = {"rel_l2_vs_oracle": _rel(got, ref),
+                                "rel_l2_vs_oracle_no_dc": _rel(got[:, bins > 0], ref[:, bins > 0])}
+        if pr == prec:
+            res.update(res["by_form"][name])
     res["sample"] = (f"beam 0, chunk 0: {bins.size} bins (DC, 1, Nyquist, 5 random) x "
-                     f"{w.n_dm} trials x {w.n_chan} channels, oracle FFT spectra in")
+                     f"{w.n_dm} trials x {w.n_chan} channels, oracle FFT spectra in; every "
+                     "tensor-core form")
     return res
 
 
@@ -903,25 +907,35 @@ def run_tc_workload(args) -> None:
             e = vp()
             rt.cudaEventCreateWithFlags(ctypes.byref(e), 2)
             return e.value
+        rt.cudaHostAlloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ctypes.c_uint]
+        rt.cudaFreeHost.argtypes = [vp]
+
+        def host_pinned(nbytes):  # page-locked, released explicitly below
+            p = vp()
+            if rt.cudaHostAlloc(ctypes.byref(p), nbytes, 0) != 0:
+                raise RuntimeError(f"cudaHostAlloc of {nbytes} bytes failed")
+            return p.value
         h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
         win_bytes = w.n_chan * int(info["fft_len"]) * esz
         if resident:
-            h_in = torch.empty(in_bytes, dtype=torch.uint8, pin_memory=True)
-            h_in.copy_(d_in)
+            h_in_ptr = host_pinned(in_bytes)
+            fdd.memcpy_async(h_in_ptr, d_in.data_ptr(), in_bytes, s_handle)
+            stream.synchronize()
             pool = None
         else:
-            pool_n = 4
-            h_in = torch.empty(pool_n * win_bytes, dtype=torch.uint8, pin_memory=True)
+            pool = 2  # distinct generated windows, reused cyclically
+            h_in_ptr = host_pinned(pool * win_bytes)
             tmp = torch.empty(win_bytes, dtype=torch.uint8, device="cuda")
-            for i in range(pool_n):  # distinct generated windows, reused cyclically
+            for i in range(pool):
                 beams.fill(i % w.n_beams, tmp.data_ptr(), 0,
                            min(int(info["fft_len"]), w.n_t), s_handle)
+                fdd.memcpy_async(h_in_ptr + i * win_bytes, tmp.data_ptr(), win_bytes, s_handle)
                 stream.synchronize()
-                h_in[i * win_bytes:(i + 1) * win_bytes].copy_(tmp)
             del tmp
-            pool = pool_n
         blk_max = max(1, int(info["stream_bytes"]) // 2 - win_bytes)
-        ring = [torch.empty(blk_max, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        # one host slot: the copies back run in order on one stream, and the
+        # host keeps nothing of a block once the next one arrives
+        ring_ptr = host_pinned(blk_max)
         ev_pool = [new_event() for _ in range(8)]
         state = {"win": 0, "blk": 0, "h2d": 0, "d2h": 0}
 
@@ -931,9 +945,9 @@ def run_tc_workload(args) -> None:
                 rt.cudaStreamWaitEvent(h2d.cuda_stream, ready, 0)
             nbytes = n * w.n_chan * esz
             if pool is None:
-                src = h_in.data_ptr() + (beam * w.n_t + t0) * w.n_chan * esz
+                src = h_in_ptr + (beam * w.n_t + t0) * w.n_chan * esz
             else:
-                src = h_in.data_ptr() + (state["win"] % pool) * win_bytes
+                src = h_in_ptr + (state["win"] % pool) * win_bytes
             fdd.memcpy_async(d_window, src, nbytes, h2d.cuda_stream)
             rt.cudaEventRecord(e_full, h2d.cuda_stream)
             rt.cudaStreamWaitEvent(s, e_full, 0)
@@ -947,7 +961,7 @@ def run_tc_workload(args) -> None:
             rt.cudaStreamWaitEvent(d2h.cuda_stream, e_done, 0)
             rows = blk["n_beams"] * blk["n_dm"]
             width = blk["row_len"] * out_esz
-            fdd.memcpy2d_async(ring[k].data_ptr(), width, blk["d_data"],
+            fdd.memcpy2d_async(ring_ptr, width, blk["d_data"],
                                blk["row_pitch"] * out_esz, width, rows, d2h.cuda_stream)
             rt.cudaEventRecord(e_rel, d2h.cuda_stream)
             state["blk"] += 1
@@ -978,10 +992,11 @@ def run_tc_workload(args) -> None:
                "input": ("whole input from pinned host memory" if pool is None else
                          f"every window from a pinned host pool of {pool} generated windows "
                          f"(the {in_bytes / 1e9:.0f} GB input exceeds host memory)"),
-               "output": "every output block to a pinned host ring of two blocks"}
+               "output": "every output block to a pinned host buffer (one block)"}
         for e in ev_pool:
             rt.cudaEventDestroy(e)
-        del h_in, ring
+        rt.cudaFreeHost(h_in_ptr)
+        rt.cudaFreeHost(ring_ptr)
     acc = tc_workload_accuracy(fdd, w, prec, args.seed, beams) if not args.no_cpu_baseline \
         else None
     cpu = None

@@ -684,28 +684,39 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
       if (!ok) break;
       const float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
       const int nc = a.n_chan - it * kCh;
+      // operands of channel ch + 1 are loaded before the products of ch
+      struct Ops {
+        float4 zr, zi, pr0, pr1, pi0, pi1;
+      };
+      auto load = [&](int ch) {
+        const float* grp = st + ch * Ly::kBins * Ly::kGFL;
+        const float* pp = grp + 2 * Ly::kA + 8 * gb;
+        Ops o;
+        o.zr = *reinterpret_cast<const float4*>(grp + 32 * h + 4 * ga);
+        o.zi = *reinterpret_cast<const float4*>(grp + Ly::kA + 32 * h + 4 * ga);
+        o.pr0 = *reinterpret_cast<const float4*>(pp);
+        o.pr1 = *reinterpret_cast<const float4*>(pp + 4);
+        o.pi0 = *reinterpret_cast<const float4*>(pp + Ly::kT);
+        o.pi1 = *reinterpret_cast<const float4*>(pp + Ly::kT + 4);
+        return o;
+      };
+      Ops cur = load(0);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         if (ch < nc) {
-          const float* grp = st + ch * Ly::kBins * Ly::kGFL;
-          const float4 zr = *reinterpret_cast<const float4*>(grp + 32 * h + 4 * ga);
-          const float4 zi = *reinterpret_cast<const float4*>(grp + Ly::kA + 32 * h + 4 * ga);
-          const float* pp = grp + 2 * Ly::kA + 8 * gb;
-          const float4 pr0 = *reinterpret_cast<const float4*>(pp);
-          const float4 pr1 = *reinterpret_cast<const float4*>(pp + 4);
-          const float4 pi0 = *reinterpret_cast<const float4*>(pp + Ly::kT);
-          const float4 pi1 = *reinterpret_cast<const float4*>(pp + Ly::kT + 4);
-          const float2 pr[4] = {make_float2(pr0.x, pr0.y), make_float2(pr0.z, pr0.w),
-                                make_float2(pr1.x, pr1.y), make_float2(pr1.z, pr1.w)};
-          const float2 pi[4] = {make_float2(pi0.x, pi0.y), make_float2(pi0.z, pi0.w),
-                                make_float2(pi1.x, pi1.y), make_float2(pi1.z, pi1.w)};
+          Ops nxt = cur;
+          if (ch + 1 < kCh && ch + 1 < nc) nxt = load(ch + 1);
+          const float2 pr[4] = {make_float2(cur.pr0.x, cur.pr0.y), make_float2(cur.pr0.z, cur.pr0.w),
+                                make_float2(cur.pr1.x, cur.pr1.y), make_float2(cur.pr1.z, cur.pr1.w)};
+          const float2 pi[4] = {make_float2(cur.pi0.x, cur.pi0.y), make_float2(cur.pi0.z, cur.pi0.w),
+                                make_float2(cur.pi1.x, cur.pi1.y), make_float2(cur.pi1.z, cur.pi1.w)};
           float2 ps[4];
 #pragma unroll
           for (int m = 0; m < 4; ++m) ps[m] = __fadd2_rn(pr[m], pi[m]);
-          const float2 zs01 = __fadd2_rn(make_float2(zr.x, zr.y), make_float2(zi.x, zi.y));
-          const float2 zs23 = __fadd2_rn(make_float2(zr.z, zr.w), make_float2(zi.z, zi.w));
-          const float zrv[4] = {zr.x, zr.y, zr.z, zr.w};
-          const float ziv[4] = {zi.x, zi.y, zi.z, zi.w};
+          const float2 zs01 = __fadd2_rn(make_float2(cur.zr.x, cur.zr.y), make_float2(cur.zi.x, cur.zi.y));
+          const float2 zs23 = __fadd2_rn(make_float2(cur.zr.z, cur.zr.w), make_float2(cur.zi.z, cur.zi.w));
+          const float zrv[4] = {cur.zr.x, cur.zr.y, cur.zr.z, cur.zr.w};
+          const float ziv[4] = {cur.zi.x, cur.zi.y, cur.zi.z, cur.zi.w};
           const float zsv[4] = {zs01.x, zs01.y, zs23.x, zs23.y};
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -719,6 +730,7 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
               C[i][m] = __ffma2_rn(s2, ps[m], C[i][m]);
             }
           }
+          cur = nxt;
         }
       }
       dev::mbar_arrive_warp(&empty[s]);
