@@ -74,6 +74,8 @@ def parse_args():
                     help="target wall time of the CPU-baseline sample")
     ap.add_argument("--n-t", type=int, default=0,
                     help="override samples per beam (smaller cases for profiler captures)")
+    ap.add_argument("--n-dm", type=int, default=0,
+                    help="override the workload's trial count (kernel sweeps)")
     ap.add_argument("--chunk-len", type=int, default=-1,
                     help="override the overlap-save chunk length")
     ap.add_argument("--mac-variant", type=int, default=0,
@@ -103,6 +105,8 @@ def workload_from_args(args) -> synth.Workload:
         kw["n_t"] = args.n_t
     if args.chunk_len >= 0:
         kw["chunk_len"] = args.chunk_len
+    if args.n_dm:
+        kw["n_dm"] = args.n_dm
     if kw:
         w = w.scaled(name=w.name + "_scaled", **kw)
     return w
@@ -997,13 +1001,17 @@ def run_tc_workload(args) -> None:
             rt.cudaEventDestroy(e)
         rt.cudaFreeHost(h_in_ptr)
         rt.cudaFreeHost(ring_ptr)
+    # the timed plan's workspace and the resident input go back before the
+    # accuracy plans are made
+    plan.close()
+    d_in = None
+    torch.cuda.empty_cache()
     acc = tc_workload_accuracy(fdd, w, prec, args.seed, beams) if not args.no_cpu_baseline \
         else None
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(w.scaled(n_beams=1), args.seed, args.cpu_seconds,
                            macs_step=macs_step)
-    plan.close()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision,

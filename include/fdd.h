@@ -458,16 +458,21 @@ fdd_status fdd_profile_read(fdd_plan_t plan, fdd_profile* out);
  * batch dimensions of Sect. 3 / Algorithm 1, and the autotuning suggested in
  * Sect. 5).  Every beam shares the channel set, sampling time, k_DM, nu_ref,
  * input type and layout of the common parameters; each has its own series
- * length and uniform trial grid.  Each beam's series is transformed whole
- * (L = next power of two >= n_t, as chunk_len 0), and the batch emits
- * spectra or |Y|^2 (output FDD_OUT_SPECTRA or FDD_OUT_POWER, FP32 form).
+ * length, uniform trial grid and chunk length: a beam is transformed whole
+ * (L = next power of two >= n_t, as chunk_len 0) or in overlap-save chunks
+ * of its own length (Sect. 2.2, as a plan with that chunk_len), and the
+ * batch emits spectra or |Y|^2 (output FDD_OUT_SPECTRA or FDD_OUT_POWER),
+ * in the FP32 form or on tensor cores (Sect. 5: beams that share their
+ * phasors make each bin a GEMM).
  * ---------------------------------------------------------------------- */
 typedef struct fdd_beam_desc {
-  int64_t n_t;      /* samples of this beam, >= 2                          */
-  double dm0;       /* first trial DM (pc cm^-3), >= 0                     */
-  double ddm;       /* trial step, >= 0                                    */
-  int32_t n_dm;     /* trials, >= 1                                        */
-  int32_t reserved; /* must be 0                                           */
+  int64_t n_t;       /* samples of this beam, >= 2                                  */
+  double dm0;        /* first trial DM (pc cm^-3), >= 0                             */
+  double ddm;        /* trial step, >= 0                                            */
+  int32_t n_dm;      /* trials, >= 1                                                */
+  int32_t chunk_len; /* 0: one transform of the whole series; else the overlap-save
+                        chunk length of this beam, a power of two above its largest
+                        delay (fdd_params.chunk_len's rules)                          */
 } fdd_beam_desc;
 
 typedef struct fdd_batch_s* fdd_batch_t;
@@ -477,15 +482,17 @@ typedef struct fdd_batch_info {
   int64_t out_elems;       /* elements of the concatenated output                */
   int64_t out_bytes;
   int64_t workspace_bytes; /* device bytes held by the batch plan                */
-  int64_t work_items;      /* (beam, bin tile, trial block) items per execute,
-                              tail items included                                */
+  int64_t work_items;      /* (beam, chunk, bin tile, trial block) items per
+                              execute, tail items included                       */
   int32_t n_waves;         /* waves (one or two persistent launches each)        */
   int32_t mac_variant;     /* kernel tile in use (FDD_MAC_*)                     */
   int32_t ctas;            /* CTAs of each persistent launch of that tile        */
   int32_t tail_variant;    /* tile of the ragged last trial blocks (FDD_MAC_*), or
-                              -1: with a 2048-trial tile, a beam's last block of
-                              1024 or fewer trials runs in a second persistent
-                              launch on this tile's 128-trial blocks            */
+                              -1 (none).  With the W12_8X8 tile a beam's last
+                              block of 1024 or fewer trials runs in a second
+                              persistent launch on this tile's 128-trial blocks;
+                              the G12_4X8 tile runs such a block in its own
+                              launch as wide items (eight bins x 1024 trials)  */
   double autotune_ms[FDD_MAC_VARIANTS]; /* timed candidates (ms), -1 if untimed */
 } fdd_batch_info;
 
@@ -493,23 +500,37 @@ typedef struct fdd_batch_info {
  * Plan a batch.  *p supplies the common fields (n_chan, nu_lo_mhz, dnu_mhz,
  * t_samp_s, k_dm, nu_ref_mhz, in_dtype, in_layout, output, precision,
  * workspace_limit, mac_variant); its n_t, dm_list, n_dm, n_beams are not
- * read and chunk_len must be 0.  beams[0 .. n_beams-1] describe the beams.
- * Beams are grouped in order into waves whose spectra (n_chan x (L/2+1 rounded
- * up to 64) complex each) fit in workspace_limit (default 16 GiB) minus the
+ * read and chunk_len must be 0 (each beam gives its own).  beams[0 ..
+ * n_beams-1] describe the beams.  Beams are grouped in order into waves
+ * whose spectra (n_chunks x n_chan x (L/2+1 rounded up to 64) complex each)
+ * fit in workspace_limit (default 16 GiB) minus the
  * fixed part (n_chan x max L floats of staging, the phase tables and a
  * 64 MiB reserve for the FFT work area);
  * each wave is one persistent launch of the phase-rotate-and-sum whose CTAs
- * take (beam, bin tile, trial block) work items from a counter.  With
+ * take (beam, chunk, bin tile, trial block) work items from a counter.  With
  * mac_variant 0 and autotune != 0 the candidate kernel tiles are timed on the
  * batch's own shapes and the fastest is kept (remembered per shape in the
  * process, and in the text file named by the FDD_AUTOTUNE_CACHE environment
  * variable when set); mac_variant 0 without autotune selects G12_4X8.
+ * With a tensor-core precision (FDD_PREC_BF16_HILO .. FDD_PREC_FP8) the
+ * beams are grouped by what their phasors share: whole-series beams by
+ * transform length and trial grid origin and step, chunked beams also by
+ * chunk length and trial count (which set the overlap); each group, sorted
+ * by trial count and cut into plans of up to 16 beams, runs as one
+ * tensor-core plan (fdd_plan with that precision) over its largest series
+ * and trial count, shorter beams reading zeros beyond their samples and
+ * keeping their own trials and chunks.  The plans are made here when their
+ * workspaces fit workspace_limit together, else each execute makes each plan
+ * for its turn and destroys it after (one at a time).  fdd_batch_info then
+ * gives mac_variant FDD_MAC_TC and n_waves the number of plans.
  * Allocates all device memory (and, while autotuning, a temporary output).
  * Layouts: the input is the beams' inputs concatenated in order (each
  * [n_t][n_chan] or [n_chan][n_t]); the output is, per beam in order,
- * [n_dm][L/2+1] complex (spectra) or float (power); fdd_batch_query gives the
- * offsets.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_UNSUPPORTED (time output,
- * chunking, non-FP32 precision, a tile without batched form), FDD_ERR_ALLOC,
+ * [n_chunks][n_dm][L/2+1] complex (spectra) or float (power), with n_chunks
+ * and L those fdd_plan_geometry gives for the beam's n_t and chunk_len
+ * (n_chunks 1 for a whole series); fdd_batch_query gives the offsets.
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_UNSUPPORTED (time output,
+ * fdd_params.chunk_len != 0, a tile without batched form), FDD_ERR_ALLOC,
  * FDD_ERR_CUDA, FDD_ERR_CUFFT.
  */
 fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32_t n_beams,
@@ -517,7 +538,9 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
 
 /* Sizes, waves, chosen tile and autotune timings; in_offsets / out_offsets
  * (arrays of n_beams, or NULL) receive each beam's element offset in the
- * concatenated input / output. */
+ * concatenated input / output.  Waits for the device; returns
+ * FDD_ERR_TIMEOUT (once, with *info filled) when a device-side wait of an
+ * execute since the last query timed out (its output is incomplete). */
 fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offsets,
                            int64_t* out_offsets);
 
@@ -527,7 +550,11 @@ fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offs
  * The sequence is captured once as a CUDA graph for a given (d_in, d_out)
  * pair and replayed on the stream by later calls with the same buffers; a
  * call with other buffers re-captures (synchronising the stream first).
- * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_CUDA, FDD_ERR_CUFFT.
+ * The tensor-core batch runs its plans streamed instead (fdd_execute_stream,
+ * windows copied from d_in, blocks copied into d_out), not as a graph; with
+ * plans made per execute it waits for the device after each.
+ * Errors: FDD_ERR_INVALID_ARG, FDD_ERR_ALLOC (plans made per execute),
+ * FDD_ERR_CUDA, FDD_ERR_CUFFT.
  */
 fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_stream_t stream);
 
@@ -537,13 +564,20 @@ fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_s
  * the common layout) through a ring of two windows of the longest beam, so
  * the concatenated input never has to be on the device; per wave the
  * persistent launch writes into one of two output slots of the wave's size,
- * and the sink receives one block per beam (n_beams 1, chunk 0, dm_first 0,
- * the beam's n_dm trials x n_bins, row_len = row_pitch = n_bins).  A sink
+ * and the sink receives one block per beam and chunk (n_beams 1, the chunk
+ * index, dm_first 0, the beam's n_dm trials x n_bins, row_len = row_pitch =
+ * n_bins).  A sink
  * that reads a wave's blocks on another stream returns a release event for
  * its last block of the wave (an event recorded after all of them).  The
  * first call allocates the rings and binds the work sets to them.  Not
- * captured as a graph.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_ALLOC (first
- * call), FDD_ERR_CUDA, FDD_ERR_CUFFT, a callback's own status.
+ * captured as a graph.  The tensor-core batch (time-major input only) calls
+ * the source per (beam, chunk) window of its plans (t_begin, n_samples within
+ * the beam's own samples) and the sink per (beam, chunk, block of trials) in
+ * each plan's block order; a sink reading on another stream returns, with
+ * the last block of each round of calls, an event recorded after its reads
+ * of every block so far.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_ALLOC (first
+ * call), FDD_ERR_UNSUPPORTED (tensor-core batch with channel-major input),
+ * FDD_ERR_CUDA, FDD_ERR_CUFFT, a callback's own status.
  */
 fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* source_user,
                                     fdd_sink_fn sink, void* sink_user, fdd_stream_t stream);

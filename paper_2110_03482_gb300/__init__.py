@@ -174,7 +174,7 @@ class fdd_beam_desc(ctypes.Structure):
         ("dm0", ctypes.c_double),
         ("ddm", ctypes.c_double),
         ("n_dm", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("chunk_len", ctypes.c_int32),
     ]
 
 
@@ -494,10 +494,12 @@ def fdd_dedisperse_spectra_static(params: Params, d_X, x_pitch: int, n_series: i
 
 
 def fdd_batch_plan(params: Params, beams, autotune: bool = True) -> int:
-    """beams: sequence of (n_t, dm0, ddm, n_dm)."""
+    """beams: sequence of (n_t, dm0, ddm, n_dm) or (n_t, dm0, ddm, n_dm, chunk_len)."""
     arr = (fdd_beam_desc * len(beams))()
-    for i, (n_t, dm0, ddm, n_dm) in enumerate(beams):
-        arr[i] = fdd_beam_desc(int(n_t), float(dm0), float(ddm), int(n_dm), 0)
+    for i, bm in enumerate(beams):
+        n_t, dm0, ddm, n_dm = bm[:4]
+        chunk = bm[4] if len(bm) > 4 else 0
+        arr[i] = fdd_beam_desc(int(n_t), float(dm0), float(ddm), int(n_dm), int(chunk))
     h = ctypes.c_void_p()
     _check(lib().fdd_batch_plan(ctypes.byref(params.c), arr, len(beams), 1 if autotune else 0,
                                 ctypes.byref(h)))

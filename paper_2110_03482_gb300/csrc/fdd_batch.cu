@@ -3,10 +3,11 @@
 // Algorithm 1 and the autotuning suggestion of Sect. 5).
 //
 // Beams are grouped into waves whose spectra fit the workspace.  For each
-// wave the beams are unpacked and transformed one by one (one cuFFT plan per
-// distinct transform length), then ONE persistent launch of the FP32
-// phase-rotate-and-sum serves the whole wave: its CTAs pull (beam, bin tile,
-// trial block) items from a counter.  The whole execute is captured once as a
+// wave the beams are unpacked and transformed one by one, whole or in their
+// own overlap-save chunks (one cuFFT plan per distinct transform length),
+// then ONE persistent launch of the FP32 phase-rotate-and-sum serves the
+// whole wave: its CTAs pull (beam, chunk, bin tile, trial block) items from a
+// counter.  The whole execute is captured once as a
 // CUDA graph and replayed.  At plan time an autotuner times the candidate
 // kernel tiles on the batch's real shapes and keeps the fastest.
 #include <cufft.h>
@@ -22,6 +23,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "fdd.h"
@@ -37,20 +39,21 @@ struct fdd_batch_s {
   int tail_variant = -1;  // tile of the ragged last trial blocks, -1: none
   int tail_ctas = 0;
   double tune_ms[FDD_MAC_VARIANTS];
-  // per beam
-  std::vector<int64_t> L, n_bins, pitch, in_off, out_off, spec_off;
+  // per beam (a chunk's spectra are n_chan x pitch, its output n_dm x n_bins)
+  std::vector<int64_t> L, n_bins, pitch, n_chunks, hop, in_off, out_off, spec_off;
   std::vector<int> wave_of;
   // per wave
   struct Wave {
-    int first = 0, count = 0;
+    int first = 0, count = 0;  // beams
     long long n_items = 0;
     fdd::BatchSet* d_sets = nullptr;
-    std::vector<fdd::BatchSet> h_sets;
+    std::vector<fdd::BatchSet> h_sets;   // one per (beam, chunk)
+    std::vector<int> set_beam, set_chunk;
     // ragged last trial blocks of 1024 or fewer trials, on the tail tile
     long long n_tail_items = 0;
     fdd::BatchSet* d_tail = nullptr;
     std::vector<fdd::BatchSet> h_tail;
-    std::vector<int> tail_beam;  // beam of each tail set
+    std::vector<int> tail_beam, tail_chunk;
   };
   std::vector<Wave> waves;
   int64_t in_elems = 0, out_elems = 0;
@@ -59,6 +62,8 @@ struct fdd_batch_s {
   float* d_xw = nullptr;            // [n_chan][L_max]
   float2* d_pool = nullptr;         // spectra of one wave
   unsigned long long* d_counter = nullptr;  // one per wave
+  int* d_status = nullptr;  // device-side timeouts of the persistent launches
+  fdd_status tc_status = FDD_OK;  // a timeout seen in a made-and-destroyed plan
   void* d_fftwork = nullptr;
   size_t bytes_held = 0;
   std::map<int64_t, cufftHandle> r2c;  // by transform length
@@ -73,6 +78,19 @@ struct fdd_batch_s {
   bool win_used[2] = {false, false};
   cudaEvent_t win_free[2] = {nullptr, nullptr};
   void* out_release[2] = {nullptr, nullptr};
+  // tensor-core form: beams grouped by what their phasors share (transform
+  // length, trial grid origin and step; with chunks also the trial count,
+  // which sets the overlap), one plan per group of up to 16 beams, run
+  // through fdd_execute_stream.  Plans are kept while their workspaces fit
+  // the limit together, else each is made for its turn and destroyed after.
+  struct TcGroup {
+    fdd_params q{};
+    std::vector<double> dms;
+    std::vector<int> beams;  // batch beams in the plan's beam order
+    fdd_plan_t plan = nullptr;
+  };
+  bool tc = false;
+  std::vector<TcGroup> tc_groups;
   // CUDA graph of the whole execute, for the buffers it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -100,6 +118,8 @@ namespace {
 
 void release(fdd_batch_s* B) {
   if (!B) return;
+  for (auto& g : B->tc_groups)
+    if (g.plan) fdd_destroy(g.plan);
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   for (auto& kv : B->r2c) cufftDestroy(kv.second);
@@ -114,7 +134,7 @@ void release(fdd_batch_s* B) {
     if (B->d_wout[k]) cudaFree(B->d_wout[k]);
     if (B->win_free[k]) cudaEventDestroy(B->win_free[k]);
   }
-  void* ptrs[] = {B->d_pc, B->d_xw, B->d_pool, B->d_counter, B->d_fftwork};
+  void* ptrs[] = {B->d_pc, B->d_xw, B->d_pool, B->d_counter, B->d_fftwork, B->d_status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete B;
@@ -135,24 +155,48 @@ fdd_status alloc(fdd_batch_s* B, void** p, size_t bytes) {
   return FDD_OK;
 }
 
-// Sets the output pointers of every work set for the given output buffer: a
-// set's row 0 is trial j_begin of its beam.
+// Output element of trial 0 of chunk c of beam b.
+int64_t chunk_out(const fdd_batch_s* B, int b, int64_t c) {
+  return B->out_off[b] + c * B->beams[b].n_dm * B->n_bins[b];
+}
+
+// Sets the output pointers of a work set for the given output buffer: a
+// set's row 0 is trial j_begin of its beam's chunk c.
 // (`origin`: output element at d_out, nonzero for a buffer that holds only
 // the beams from some beam on)
-void bind_set(const fdd_batch_s* B, fdd::BatchSet& bs, int b, void* d_out, int64_t origin = 0) {
+void bind_set(const fdd_batch_s* B, fdd::BatchSet& bs, int b, int c, void* d_out,
+              int64_t origin = 0) {
   fdd::MacArgs& m = bs.args;
-  const int64_t off = B->out_off[b] - origin + static_cast<int64_t>(m.j_begin) * B->n_bins[b];
+  const int64_t off = chunk_out(B, b, c) - origin + static_cast<int64_t>(m.j_begin) * B->n_bins[b];
   if (B->p.output == FDD_OUT_SPECTRA)
     m.Y = static_cast<float2*>(d_out) + off;
   else
     m.Y = static_cast<float*>(d_out) + off;
 }
 
+void bind_wave(const fdd_batch_s* B, std::vector<fdd::BatchSet>& sets,
+               std::vector<fdd::BatchSet>& tails, const fdd_batch_s::Wave& w, void* d_out,
+               int64_t origin) {
+  for (size_t i = 0; i < sets.size(); ++i)
+    bind_set(B, sets[i], w.set_beam[i], w.set_chunk[i], d_out, origin);
+  for (size_t i = 0; i < tails.size(); ++i)
+    bind_set(B, tails[i], w.tail_beam[i], w.tail_chunk[i], d_out, origin);
+}
+
 void bind_output(fdd_batch_s* B, void* d_out) {
-  for (auto& w : B->waves) {
-    for (int i = 0; i < w.count; ++i) bind_set(B, w.h_sets[i], w.first + i, d_out);
-    for (size_t i = 0; i < w.h_tail.size(); ++i) bind_set(B, w.h_tail[i], w.tail_beam[i], d_out);
-  }
+  for (auto& w : B->waves) bind_wave(B, w.h_sets, w.h_tail, w, d_out, 0);
+}
+
+// Unpack chunk c of beam b from its input and transform it into the pool.
+fdd_status transform_chunk(fdd_batch_s* B, const void* beam_in, int b, int64_t c,
+                           cudaStream_t s) {
+  fdd::UnpackArgs ua{beam_in, B->p.in_dtype, B->p.in_layout, B->p.n_chan, B->beams[b].n_t,
+                     c * B->hop[b], B->L[b], B->d_xw, B->L[b]};
+  B_CUDA(fdd::launch_unpack(ua, s));
+  B_CUFFT(cufftExecR2C(B->r2c.at(B->L[b]), B->d_xw,
+                       reinterpret_cast<cufftComplex*>(
+                           B->d_pool + B->spec_off[b] + c * B->p.n_chan * B->pitch[b])));
+  return FDD_OK;
 }
 
 // All work of one execute, issued on stream s (also used under capture).
@@ -163,16 +207,15 @@ fdd_status issue(fdd_batch_s* B, const void* d_in, cudaStream_t s) {
     const auto& w = B->waves[wi];
     for (int i = 0; i < w.count; ++i) {
       const int b = w.first + i;
-      fdd::UnpackArgs ua{static_cast<const char*>(d_in) + esz * B->in_off[b], B->p.in_dtype,
-                         B->p.in_layout, B->p.n_chan, B->beams[b].n_t, 0, B->L[b], B->d_xw,
-                         B->L[b]};
-      B_CUDA(fdd::launch_unpack(ua, s));
-      B_CUFFT(cufftExecR2C(B->r2c.at(B->L[b]), B->d_xw,
-                           reinterpret_cast<cufftComplex*>(B->d_pool + B->spec_off[b])));
+      for (int64_t c = 0; c < B->n_chunks[b]; ++c) {
+        const fdd_status st =
+            transform_chunk(B, static_cast<const char*>(d_in) + esz * B->in_off[b], b, c, s);
+        if (st != FDD_OK) return st;
+      }
     }
     B_CUDA(cudaMemsetAsync(B->d_counter + 2 * wi, 0, 2 * sizeof(unsigned long long), s));
-    B_CUDA(fdd::launch_mac_batch(w.d_sets, w.count, w.n_items, B->d_counter + 2 * wi,
-                                 B->variant, B->ctas, B->p.n_chan, s));
+    B_CUDA(fdd::launch_mac_batch(w.d_sets, static_cast<int>(w.h_sets.size()), w.n_items,
+                                 B->d_counter + 2 * wi, B->variant, B->ctas, B->p.n_chan, s));
     if (w.n_tail_items)
       B_CUDA(fdd::launch_mac_batch(w.d_tail, static_cast<int>(w.h_tail.size()), w.n_tail_items,
                                    B->d_counter + 2 * wi + 1, B->tail_variant, B->tail_ctas,
@@ -182,7 +225,7 @@ fdd_status issue(fdd_batch_s* B, const void* d_in, cudaStream_t s) {
 }
 
 fdd_status upload_wave(const fdd_batch_s::Wave& w, cudaStream_t s) {
-  B_CUDA(cudaMemcpyAsync(w.d_sets, w.h_sets.data(), sizeof(fdd::BatchSet) * w.count,
+  B_CUDA(cudaMemcpyAsync(w.d_sets, w.h_sets.data(), sizeof(fdd::BatchSet) * w.h_sets.size(),
                          cudaMemcpyHostToDevice, s));
   if (!w.h_tail.empty())
     B_CUDA(cudaMemcpyAsync(w.d_tail, w.h_tail.data(), sizeof(fdd::BatchSet) * w.h_tail.size(),
@@ -198,6 +241,188 @@ fdd_status upload_sets(fdd_batch_s* B, cudaStream_t s) {
   return FDD_OK;
 }
 
+// ------------------------------------------------ tensor-core batch
+// The callbacks of one group's fdd_execute_stream: windows come from the
+// resident input (d_in) or the caller's source, blocks go to the resident
+// output (d_out) or the caller's sink, one (beam, chunk) at a time.  A beam
+// shorter than the group's longest reads zeros beyond its own samples, which
+// is its own zero padding (whole series) or its own last chunks' zero fill;
+// chunks and trials beyond its own are dropped.
+struct TcCtx {
+  fdd_batch_s* B;
+  const fdd_batch_s::TcGroup* g;
+  const void* d_in;
+  void* d_out;
+  fdd_source_fn source;
+  void* source_user;
+  fdd_sink_fn sink;
+  void* sink_user;
+  fdd_status inner = FDD_OK;  // a callback's own failure
+};
+
+fdd_status tc_source(void* user, int32_t beam, int64_t t_begin, int64_t n, void* d_window,
+                     void* ready, fdd_stream_t stream) {
+  TcCtx* x = static_cast<TcCtx*>(user);
+  const fdd_batch_s* B = x->B;
+  const int bm = x->g->beams[beam];
+  const int64_t nc = B->p.n_chan;
+  const size_t esz = B->p.in_dtype == FDD_IN_U8 ? 1 : 4;
+  const bool tmaj = B->p.in_layout == FDD_LAYOUT_TIME_MAJOR;
+  const int64_t nb = std::max<int64_t>(0, std::min<int64_t>(n, B->beams[bm].n_t - t_begin));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* win = static_cast<char*>(d_window);
+  if (nb < n) {  // samples beyond the beam: zeros
+    cudaError_t e = cudaSuccess;
+    if (tmaj)
+      e = cudaMemsetAsync(win + esz * nb * nc, 0, esz * (n - nb) * nc, s);
+    else
+      e = cudaMemset2DAsync(win + esz * nb, esz * n, 0, esz * (n - nb), nc, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fdd::report_error(FDD_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  if (nb == 0) return FDD_OK;
+  if (x->d_in) {
+    const char* src = static_cast<const char*>(x->d_in) + esz * B->in_off[bm];
+    cudaError_t e;
+    if (tmaj)
+      e = cudaMemcpyAsync(win, src + esz * t_begin * nc, esz * nb * nc, cudaMemcpyDeviceToDevice,
+                          s);
+    else
+      e = cudaMemcpy2DAsync(win, esz * n, src + esz * t_begin, esz * B->beams[bm].n_t, esz * nb,
+                            nc, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fdd::report_error(FDD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return FDD_OK;
+  }
+  const fdd_status st = x->source(x->source_user, bm, t_begin, nb, d_window, ready, stream);
+  if (st != FDD_OK) x->inner = st;
+  return st;
+}
+
+fdd_status tc_sink(void* user, fdd_block* blk, fdd_stream_t stream) {
+  TcCtx* x = static_cast<TcCtx*>(user);
+  const fdd_batch_s* B = x->B;
+  const size_t esz = B->p.output == FDD_OUT_SPECTRA ? 8 : 4;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* release = nullptr;
+  for (int i = 0; i < blk->n_beams; ++i) {
+    const int bm = x->g->beams[blk->beam_first + i];
+    if (blk->chunk >= B->n_chunks[bm]) continue;
+    const int rows = std::min(blk->n_dm, B->beams[bm].n_dm - blk->dm_first);
+    if (rows <= 0) continue;
+    const char* src = static_cast<const char*>(blk->d_data) +
+                      esz * static_cast<size_t>(i) * blk->n_dm * blk->row_pitch;
+    if (x->d_out) {
+      const int64_t o = chunk_out(B, bm, blk->chunk) +
+                        static_cast<int64_t>(blk->dm_first) * B->n_bins[bm];
+      const cudaError_t e =
+          cudaMemcpyAsync(static_cast<char*>(x->d_out) + esz * o, src,
+                          esz * static_cast<size_t>(rows) * B->n_bins[bm],
+                          cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fdd::report_error(FDD_ERR_CUDA, cudaGetErrorString(e));
+      }
+      continue;
+    }
+    fdd_block ub{bm, 1, blk->chunk, blk->dm_first, rows, src, B->n_bins[bm], B->n_bins[bm], 0,
+                 nullptr};
+    const fdd_status st = x->sink(x->sink_user, &ub, stream);
+    if (st != FDD_OK) {
+      x->inner = st;
+      return st;
+    }
+    if (ub.release_event) release = ub.release_event;  // the last one counts
+  }
+  blk->release_event = release;
+  return FDD_OK;
+}
+
+fdd_status run_tc_batch(fdd_batch_s* B, TcCtx ctx, cudaStream_t s) {
+  for (auto& g : B->tc_groups) {
+    fdd_plan_t plan = g.plan;
+    fdd_status st;
+    if (!plan && (st = fdd_plan(&g.q, &plan)) != FDD_OK) return st;
+    ctx.g = &g;
+    st = fdd_execute_stream(plan, nullptr, tc_source, &ctx, tc_sink, &ctx,
+                            reinterpret_cast<fdd_stream_t>(s));
+    if (!g.plan) {
+      fdd_info gi;
+      if (st == FDD_OK && fdd_query(plan, &gi) == FDD_ERR_TIMEOUT) B->tc_status = FDD_ERR_TIMEOUT;
+      const fdd_status sd = fdd_destroy(plan);  // waits for the device
+      if (st == FDD_OK) st = sd;
+    }
+    if (st != FDD_OK) return ctx.inner != FDD_OK ? ctx.inner : st;
+  }
+  return FDD_OK;
+}
+
+// Groups and plans of the tensor-core form.
+fdd_status plan_tc_groups(fdd_batch_s* B, const fdd_params* p) {
+  // key: (transform length, chunk length, trial count for chunked beams,
+  // dm0, ddm); whole-series beams of one length share a group whatever
+  // their trial counts and lengths (the group runs to its largest)
+  std::map<std::tuple<int64_t, int32_t, int32_t, double, double>, std::vector<int>> keyed;
+  for (size_t b = 0; b < B->beams.size(); ++b) {
+    const fdd_beam_desc& d = B->beams[b];
+    keyed[std::make_tuple(B->L[b], d.chunk_len, d.chunk_len ? d.n_dm : 0, d.dm0, d.ddm)]
+        .push_back(static_cast<int>(b));
+  }
+  constexpr int kGroup = 16;  // beams per plan (the 16-beam tensor-core groups)
+  for (auto& kv : keyed) {
+    std::vector<int>& v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [&](int a, int c) {
+      return B->beams[a].n_dm != B->beams[c].n_dm ? B->beams[a].n_dm > B->beams[c].n_dm
+                                                  : B->beams[a].n_t > B->beams[c].n_t;
+    });
+    for (size_t i0 = 0; i0 < v.size(); i0 += kGroup) {
+      fdd_batch_s::TcGroup g;
+      g.beams.assign(v.begin() + i0, v.begin() + std::min(v.size(), i0 + kGroup));
+      int64_t n_t = 0;
+      int n_dm = 0;
+      for (int b : g.beams) {
+        n_t = std::max(n_t, B->beams[b].n_t);
+        n_dm = std::max(n_dm, B->beams[b].n_dm);
+      }
+      const fdd_beam_desc& d0 = B->beams[g.beams[0]];
+      g.dms.resize(n_dm);
+      for (int j = 0; j < n_dm; ++j) g.dms[j] = d0.dm0 + d0.ddm * j;
+      g.q = *p;
+      g.q.n_t = n_t;
+      g.q.n_beams = static_cast<int32_t>(g.beams.size());
+      g.q.dm_list = g.dms.data();
+      g.q.n_dm = n_dm;
+      g.q.chunk_len = d0.chunk_len;
+      g.q.mac_variant = 0;
+      B->tc_groups.push_back(std::move(g));
+    }
+  }
+  for (auto& g : B->tc_groups) g.q.dm_list = g.dms.data();  // after the moves
+  // keep every plan when their workspaces fit the limit together
+  const size_t limit = p->workspace_limit ? p->workspace_limit : (size_t(16) << 30);
+  size_t need = 0;
+  for (auto& g : B->tc_groups) {
+    fdd_info gi;
+    fdd_status st = fdd_plan_geometry(&g.q, &gi);
+    if (st != FDD_OK) return st;
+    need += static_cast<size_t>(gi.workspace_bytes + gi.stream_bytes);
+  }
+  if (need <= limit) {
+    for (auto& g : B->tc_groups) {
+      fdd_status st = fdd_plan(&g.q, &g.plan);
+      if (st != FDD_OK) return st;
+      fdd_info gi;
+      fdd_query(g.plan, &gi);
+      B->bytes_held += static_cast<size_t>(gi.workspace_bytes + gi.stream_bytes);
+    }
+  }
+  return FDD_OK;
+}
+
 // Autotune cache: shape signature -> variant, in process and optionally in a
 // text file named by FDD_AUTOTUNE_CACHE (one "signature variant" per line).
 std::mutex g_tune_mutex;
@@ -206,7 +431,8 @@ std::map<std::string, int> g_tune_cache;
 std::string signature(const fdd_batch_s* B) {
   std::string sig = "c" + std::to_string(B->p.n_chan) + "o" + std::to_string(B->p.output);
   for (size_t b = 0; b < B->beams.size(); ++b)
-    sig += "|" + std::to_string(B->L[b]) + "x" + std::to_string(B->beams[b].n_dm);
+    sig += "|" + std::to_string(B->L[b]) + "x" + std::to_string(B->beams[b].n_dm) + "x" +
+           std::to_string(B->n_chunks[b]);
   // keep the key short: hash the per-beam list
   unsigned long long h = 1469598103934665603ull;
   for (char c : sig) h = (h ^ static_cast<unsigned char>(c)) * 1099511628211ull;
@@ -257,10 +483,11 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   if (p->output != FDD_OUT_SPECTRA && p->output != FDD_OUT_POWER)
     return report_error(FDD_ERR_UNSUPPORTED,
                         "the batching form emits spectra or power (time output: per-beam plans)");
-  if (p->precision != FDD_PREC_FP32)
-    return report_error(FDD_ERR_UNSUPPORTED, "the batching form runs the FP32 form");
+  if (p->precision < FDD_PREC_FP32 || p->precision > FDD_PREC_FP8)
+    return report_error(FDD_ERR_INVALID_ARG, "unknown precision");
   if (p->chunk_len != 0)
-    return report_error(FDD_ERR_UNSUPPORTED, "the batching form transforms whole series (chunk_len 0)");
+    return report_error(FDD_ERR_UNSUPPORTED,
+                        "the batching form takes each beam's chunk length from its description");
   if (p->mac_variant < 0 || p->mac_variant > FDD_MAC_VARIANTS)
     return report_error(FDD_ERR_INVALID_ARG, "mac_variant out of range");
 
@@ -278,7 +505,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   for (int b = 0; b < n_beams; ++b) {
     const fdd_beam_desc& d = beams[b];
     if (d.n_dm < 1 || d.n_t < 2 || !(d.dm0 >= 0.0) || !(d.ddm >= 0.0) ||
-        !std::isfinite(d.dm0) || !std::isfinite(d.ddm) || d.reserved != 0)
+        !std::isfinite(d.dm0) || !std::isfinite(d.ddm) || d.chunk_len < 0)
       return report_error(FDD_ERR_INVALID_ARG, "invalid beam description");
     std::vector<double> dms(d.n_dm);
     for (int j = 0; j < d.n_dm; ++j) dms[j] = d.dm0 + d.ddm * j;
@@ -287,16 +514,19 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     q.n_beams = 1;
     q.dm_list = dms.data();
     q.n_dm = d.n_dm;
+    q.chunk_len = d.chunk_len;
     fdd_info g;
     fdd_status st = fdd_plan_geometry(&q, &g);
     if (st != FDD_OK) return st;
     B->L.push_back(g.fft_len);
     B->n_bins.push_back(g.n_bins);
     B->pitch.push_back(g.bin_pitch);
+    B->n_chunks.push_back(g.n_chunks);
+    B->hop.push_back(g.hop);
     B->in_off.push_back(in_acc);
     B->out_off.push_back(out_acc);
     in_acc += d.n_t * static_cast<int64_t>(p->n_chan);
-    out_acc += g.n_bins * static_cast<int64_t>(d.n_dm);
+    out_acc += g.n_chunks * g.n_bins * static_cast<int64_t>(d.n_dm);
     L_max = std::max(L_max, g.fft_len);
     fdd::CoreGeometry cg;
     if ((st = fdd::core_geometry(&q, &cg)) != FDD_OK) return st;
@@ -310,6 +540,16 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   B_CUDA(cudaGetDevice(&B->device));
   B_CUDA(cudaDeviceGetAttribute(&B->n_sms, cudaDevAttrMultiProcessorCount, B->device));
 
+  if (p->precision != FDD_PREC_FP32) {
+    B->tc = true;
+    B->variant = FDD_MAC_TC;
+    for (double& t : B->tune_ms) t = -1.0;
+    fdd_status st = plan_tc_groups(B, p);
+    if (st != FDD_OK) return st;
+    *out = guard.release();
+    return FDD_OK;
+  }
+
   // Waves: consecutive beams whose spectra fit the pool.
   const size_t limit = p->workspace_limit ? p->workspace_limit : (size_t(16) << 30);
   const size_t fixed = sizeof(float) * size_t(p->n_chan) * L_max +
@@ -319,7 +559,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   size_t pool_need = 0, cur = 0;
   fdd_batch_s::Wave w;
   for (int b = 0; b < n_beams; ++b) {
-    const size_t spec = sizeof(float2) * size_t(p->n_chan) * B->pitch[b];
+    const size_t spec = sizeof(float2) * size_t(p->n_chan) * B->pitch[b] * B->n_chunks[b];
     if (spec > pool_cap)
       return report_error(FDD_ERR_INVALID_ARG, "one beam's spectra exceed workspace_limit");
     if (cur + spec > pool_cap) {
@@ -346,6 +586,8 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   if ((st = alloc(B, reinterpret_cast<void**>(&B->d_counter),
                   2 * sizeof(unsigned long long) * B->waves.size())))
     return st;
+  if ((st = alloc(B, reinterpret_cast<void**>(&B->d_status), 256))) return st;
+  B_CUDA(cudaMemset(B->d_status, 0, 256));
   B_CUDA(cudaMemcpy(B->d_pc, pc.data(), sizeof(fdd::PhaseConst) * pc.size(),
                     cudaMemcpyHostToDevice));
 
@@ -371,9 +613,9 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
   // Work sets per wave (output pointers bound at execute).  With a tile of
   // 2048-trial blocks, a beam's last block of 1024 or fewer trials goes to the
   // tail tile's 128-trial blocks instead (less padding beyond the trial grid).
-  auto base_args = [&](int b) {
+  auto base_args = [&](int b, int64_t c) {
     fdd::MacArgs m{};
-    m.X = B->d_pool + B->spec_off[b];
+    m.X = B->d_pool + B->spec_off[b] + c * p->n_chan * B->pitch[b];
     m.x_series_stride = 0;
     m.x_chan_stride = B->pitch[b];
     m.pc = B->d_pc + static_cast<size_t>(b) * p->n_chan;
@@ -386,6 +628,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     m.scale = 1.0f;
     m.real_bin_a = -1;
     m.real_bin_b = -1;
+    m.status = B->d_status;
     return m;
   };
   auto build_sets = [&](int variant) -> fdd_status {
@@ -394,39 +637,57 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     const int tv = B->tail_variant;
     const int tail_dms = tv >= 0 ? fdd::mac_variant_trials_per_block(tv) : 0;
     // (the three-product tile runs a ragged last block of up to half its
-    // trials in the same launch, at half its work: no second launch)
+    // trials in the same launch, as wide items: no second launch)
     const bool tails = tv >= 0 && dms >= 2048 && tail_dms < dms && variant != FDD_MAC_G12_4X8;
     for (auto& wv : B->waves) {
-      wv.h_sets.assign(wv.count, fdd::BatchSet{});
+      wv.h_sets.clear();
+      wv.set_beam.clear();
+      wv.set_chunk.clear();
       wv.h_tail.clear();
       wv.tail_beam.clear();
+      wv.tail_chunk.clear();
       long long items = 0, t_items = 0;
       for (int i = 0; i < wv.count; ++i) {
         const int b = wv.first + i;
         const int n_dm = B->beams[b].n_dm;
         const int full = n_dm / dms, rem = n_dm % dms;
         const bool tail = tails && rem > 0 && rem <= dms / 2;
-        const int blocks = full + (rem > 0 && !tail ? 1 : 0);
-        fdd::BatchSet& bs = wv.h_sets[i];
-        bs.args = base_args(b);
-        bs.args.j_begin = 0;
-        bs.args.n_dm = tail ? full * dms : n_dm;
-        bs.n_bin_tiles = static_cast<int>((B->n_bins[b] + bins_per_cta - 1) / bins_per_cta);
-        bs.n_dm_blocks = blocks;
-        bs.item_begin = items;
-        items += static_cast<long long>(bs.n_bin_tiles) * blocks;
-        if (tail) {
-          fdd::BatchSet ts{};
-          ts.args = base_args(b);
-          ts.args.j_begin = full * dms;
-          ts.args.n_dm = rem;
-          const int tb = fdd::mac_variant_bins_per_cta(tv);
-          ts.n_bin_tiles = static_cast<int>((B->n_bins[b] + tb - 1) / tb);
-          ts.n_dm_blocks = (rem + tail_dms - 1) / tail_dms;
-          ts.item_begin = t_items;
-          t_items += static_cast<long long>(ts.n_bin_tiles) * ts.n_dm_blocks;
-          wv.h_tail.push_back(ts);
-          wv.tail_beam.push_back(b);
+        const bool wide = variant == FDD_MAC_G12_4X8 && rem > 0 && rem <= dms / 2;
+        const int blocks = full + (rem > 0 && !tail && !wide ? 1 : 0);
+        for (int64_t c = 0; c < B->n_chunks[b]; ++c) {
+          fdd::BatchSet bs{};
+          bs.args = base_args(b, c);
+          bs.args.j_begin = 0;
+          bs.args.n_dm = tail ? full * dms : n_dm;
+          bs.n_bin_tiles = static_cast<int>((B->n_bins[b] + bins_per_cta - 1) / bins_per_cta);
+          bs.n_dm_blocks = blocks;
+          bs.item_begin = items;
+          // the last block as wide items: 2x the bins and 1024 trials, or
+          // 4x the bins and 512
+          const int wf = rem <= dms / 4 ? 4 : 2;
+          bs.n_wide_tiles = wide ? static_cast<int>((B->n_bins[b] + wf * bins_per_cta - 1) /
+                                                    (wf * bins_per_cta))
+                                 : 0;
+          bs.j_wide = full * dms;
+          bs.wide_trials = dms / wf;
+          items += static_cast<long long>(bs.n_bin_tiles) * blocks + bs.n_wide_tiles;
+          wv.h_sets.push_back(bs);
+          wv.set_beam.push_back(b);
+          wv.set_chunk.push_back(static_cast<int>(c));
+          if (tail) {
+            fdd::BatchSet ts{};
+            ts.args = base_args(b, c);
+            ts.args.j_begin = full * dms;
+            ts.args.n_dm = rem;
+            const int tb = fdd::mac_variant_bins_per_cta(tv);
+            ts.n_bin_tiles = static_cast<int>((B->n_bins[b] + tb - 1) / tb);
+            ts.n_dm_blocks = (rem + tail_dms - 1) / tail_dms;
+            ts.item_begin = t_items;
+            t_items += static_cast<long long>(ts.n_bin_tiles) * ts.n_dm_blocks;
+            wv.h_tail.push_back(ts);
+            wv.tail_beam.push_back(b);
+            wv.tail_chunk.push_back(static_cast<int>(c));
+          }
         }
       }
       wv.n_items = items;
@@ -435,9 +696,11 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     return FDD_OK;
   };
   for (auto& wv : B->waves) {
-    if ((st = alloc(B, reinterpret_cast<void**>(&wv.d_sets), sizeof(fdd::BatchSet) * wv.count)))
+    int64_t n_sets = 0;
+    for (int i = 0; i < wv.count; ++i) n_sets += B->n_chunks[wv.first + i];
+    if ((st = alloc(B, reinterpret_cast<void**>(&wv.d_sets), sizeof(fdd::BatchSet) * n_sets)))
       return st;
-    if ((st = alloc(B, reinterpret_cast<void**>(&wv.d_tail), sizeof(fdd::BatchSet) * wv.count)))
+    if ((st = alloc(B, reinterpret_cast<void**>(&wv.d_tail), sizeof(fdd::BatchSet) * n_sets)))
       return st;
   }
   // the tail tile (128-trial blocks, four bins per warp)
@@ -472,9 +735,9 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     const int cands[] = {FDD_MAC_W12_8X8, FDD_MAC_G12_4X8, FDD_MAC_Q12_8X8, FDD_MAC_Q_4X8,
                          FDD_MAC_Q_4X4};
     const auto& w0 = B->waves[0];
-    int64_t w0_out = 0;
-    for (int i = 0; i < w0.count; ++i)
-      w0_out += B->n_bins[w0.first + i] * static_cast<int64_t>(B->beams[w0.first + i].n_dm);
+    const int64_t w0_out = (w0.first + w0.count < n_beams ? B->out_off[w0.first + w0.count]
+                                                           : B->out_elems) -
+                           B->out_off[w0.first];
     void* scratch = nullptr;
     B_CUDA(cudaMalloc(&scratch, (p->output == FDD_OUT_SPECTRA ? 8 : 4) * size_t(w0_out)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -486,10 +749,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
       if ((tst = use_variant(v))) break;
       // output of wave 0 into the scratch, laid out like the real output
       auto& w0m = B->waves[0];
-      const int64_t origin = B->out_off[w0.first];
-      for (int i = 0; i < w0.count; ++i) bind_set(B, w0m.h_sets[i], w0.first + i, scratch, origin);
-      for (size_t i = 0; i < w0.h_tail.size(); ++i)
-        bind_set(B, w0m.h_tail[i], w0.tail_beam[i], scratch, origin);
+      bind_wave(B, w0m.h_sets, w0m.h_tail, w0, scratch, B->out_off[w0.first]);
       if ((tst = upload_wave(w0, nullptr))) break;
       // Each launch times a bounded share of wave 0's items (eight rounds of
       // the persistent grid rank the tiles whatever the wave's size), scaled
@@ -508,7 +768,8 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
         }
         return static_cast<double>(ms) * static_cast<double>(n_items) / static_cast<double>(part);
       };
-      double tot = timed(w0.d_sets, w0.count, w0.n_items, v, B->ctas, B->d_counter);
+      double tot = timed(w0.d_sets, static_cast<int>(w0.h_sets.size()), w0.n_items, v, B->ctas,
+                         B->d_counter);
       if (w0.n_tail_items)
         tot += timed(w0.d_tail, static_cast<int>(w0.h_tail.size()), w0.n_tail_items,
                      B->tail_variant, B->tail_ctas, B->d_counter + 1);
@@ -543,7 +804,7 @@ fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offs
   info->out_elems = b->out_elems;
   info->out_bytes = b->out_elems * (b->p.output == FDD_OUT_SPECTRA ? 8 : 4);
   info->workspace_bytes = static_cast<int64_t>(b->bytes_held);
-  info->n_waves = static_cast<int32_t>(b->waves.size());
+  info->n_waves = static_cast<int32_t>(b->tc ? b->tc_groups.size() : b->waves.size());
   info->mac_variant = b->variant;
   long long items = 0;
   bool any_tail = false;
@@ -559,6 +820,22 @@ fdd_status fdd_batch_query(fdd_batch_t b, fdd_batch_info* info, int64_t* in_offs
     if (in_offsets) in_offsets[i] = b->in_off[i];
     if (out_offsets) out_offsets[i] = b->out_off[i];
   }
+  // a device-side wait that timed out since the last query, reported once
+  bool timeout = b->tc_status == FDD_ERR_TIMEOUT;
+  b->tc_status = FDD_OK;
+  for (auto& g : b->tc_groups) {
+    fdd_info gi;
+    if (g.plan && fdd_query(g.plan, &gi) == FDD_ERR_TIMEOUT) timeout = true;
+  }
+  if (b->d_status) {
+    int word = 0;
+    B_CUDA(cudaMemcpy(&word, b->d_status, sizeof word, cudaMemcpyDeviceToHost));
+    if (word != 0) {
+      B_CUDA(cudaMemset(b->d_status, 0, sizeof word));
+      timeout = true;
+    }
+  }
+  if (timeout) return fdd::report_error(FDD_ERR_TIMEOUT, "a device-side wait timed out");
   return FDD_OK;
 }
 
@@ -570,6 +847,8 @@ fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_s
   if (dev != b->device)
     return fdd::report_error(FDD_ERR_INVALID_ARG, "batch plan belongs to another device");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (b->tc) return run_tc_batch(b, TcCtx{b, nullptr, d_in, d_out, nullptr, nullptr, nullptr,
+                                          nullptr}, s);
   if (!b->graph || b->graph_in != d_in || b->graph_out != d_out) {
     // (Re)build the graph for these buffers: bind and upload the work sets,
     // then capture one execute on the plan's private stream.
@@ -618,6 +897,13 @@ fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* s
   if (dev != b->device)
     return report_error(FDD_ERR_INVALID_ARG, "batch plan belongs to another device");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (b->tc) {
+    if (b->p.in_layout != FDD_LAYOUT_TIME_MAJOR)
+      return report_error(FDD_ERR_UNSUPPORTED,
+                          "the streamed tensor-core batch takes time-major input");
+    return run_tc_batch(b, TcCtx{b, nullptr, nullptr, nullptr, source, source_user, sink,
+                                 sink_user}, s);
+  }
   fdd_status st;
   const size_t esz = b->p.in_dtype == FDD_IN_U8 ? 1 : 4;
   const size_t oesz = b->p.output == FDD_OUT_SPECTRA ? 8 : 4;
@@ -627,11 +913,11 @@ fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* s
     int64_t nt_max = 0;
     for (auto& d : b->beams) nt_max = std::max<int64_t>(nt_max, d.n_t);
     size_t wmax = 0;
-    for (auto& w : b->waves) {
-      size_t o = 0;
-      for (int i = 0; i < w.count; ++i)
-        o += oesz * static_cast<size_t>(b->n_bins[w.first + i]) * b->beams[w.first + i].n_dm;
-      wmax = std::max(wmax, o);
+    for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+      const auto& w = b->waves[wi];
+      const int64_t end = wi + 1 < b->waves.size() ? b->out_off[b->waves[wi + 1].first]
+                                                   : b->out_elems;
+      wmax = std::max(wmax, oesz * static_cast<size_t>(end - b->out_off[w.first]));
     }
     b->wout_bytes = wmax;
     for (int k = 0; k < 2; ++k) {
@@ -641,11 +927,8 @@ fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* s
       B_CUDA(cudaEventCreateWithFlags(&b->win_free[k], cudaEventDisableTiming));
       for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         auto& w = b->waves[wi];
-        const int64_t origin = b->out_off[w.first];
         std::vector<fdd::BatchSet> sets = w.h_sets, tails = w.h_tail;
-        for (int i = 0; i < w.count; ++i) bind_set(b, sets[i], w.first + i, b->d_wout[k], origin);
-        for (size_t i = 0; i < tails.size(); ++i)
-          bind_set(b, tails[i], w.tail_beam[i], b->d_wout[k], origin);
+        bind_wave(b, sets, tails, w, b->d_wout[k], b->out_off[w.first]);
         fdd::BatchSet* d = nullptr;
         const size_t n = sets.size() + tails.size();
         if ((st = alloc(b, reinterpret_cast<void**>(&d), sizeof(fdd::BatchSet) * n))) return st;
@@ -667,13 +950,10 @@ fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* s
       void* ready = b->win_used[slot] ? static_cast<void*>(b->win_free[slot]) : nullptr;
       st = source(source_user, bm, 0, b->beams[bm].n_t, b->d_win[slot], ready, stream);
       if (st != FDD_OK) return report_error(st, "the input source failed");
-      fdd::UnpackArgs ua{b->d_win[slot], b->p.in_dtype, b->p.in_layout, b->p.n_chan,
-                         b->beams[bm].n_t, 0, b->L[bm], b->d_xw, b->L[bm]};
-      B_CUDA(fdd::launch_unpack(ua, s));
+      for (int64_t c = 0; c < b->n_chunks[bm]; ++c)
+        if ((st = transform_chunk(b, b->d_win[slot], bm, c, s)) != FDD_OK) return st;
       B_CUDA(cudaEventRecord(b->win_free[slot], s));
       b->win_used[slot] = true;
-      B_CUFFT(cufftExecR2C(b->r2c.at(b->L[bm]), b->d_xw,
-                           reinterpret_cast<cufftComplex*>(b->d_pool + b->spec_off[bm])));
     }
     const int k = static_cast<int>(b->out_next++ & 1);
     if (b->out_release[k]) {  // the sink's reads of this slot's last wave
@@ -682,22 +962,25 @@ fdd_status fdd_batch_execute_stream(fdd_batch_t b, fdd_source_fn source, void* s
     }
     fdd::BatchSet* d_sets = b->d_sets_slot[k][wi];
     B_CUDA(cudaMemsetAsync(b->d_counter + 2 * wi, 0, 2 * sizeof(unsigned long long), s));
-    B_CUDA(fdd::launch_mac_batch(d_sets, w.count, w.n_items, b->d_counter + 2 * wi, b->variant,
+    const int n_sets = static_cast<int>(w.h_sets.size());
+    B_CUDA(fdd::launch_mac_batch(d_sets, n_sets, w.n_items, b->d_counter + 2 * wi, b->variant,
                                  b->ctas, b->p.n_chan, s));
     if (w.n_tail_items)
-      B_CUDA(fdd::launch_mac_batch(d_sets + w.count, static_cast<int>(w.h_tail.size()),
+      B_CUDA(fdd::launch_mac_batch(d_sets + n_sets, static_cast<int>(w.h_tail.size()),
                                    w.n_tail_items, b->d_counter + 2 * wi + 1, b->tail_variant,
                                    b->tail_ctas, b->p.n_chan, s));
     const int64_t origin = b->out_off[w.first];
     void* release = nullptr;
     for (int i = 0; i < w.count; ++i) {
       const int bm = w.first + i;
-      fdd_block blk{bm, 1, 0, 0, b->beams[bm].n_dm,
-                    static_cast<char*>(b->d_wout[k]) + oesz * (b->out_off[bm] - origin),
-                    b->n_bins[bm], b->n_bins[bm], 0, nullptr};
-      st = sink(sink_user, &blk, stream);
-      if (st != FDD_OK) return report_error(st, "the output sink failed");
-      if (blk.release_event) release = blk.release_event;  // the wave's last one counts
+      for (int64_t c = 0; c < b->n_chunks[bm]; ++c) {
+        fdd_block blk{bm, 1, c, 0, b->beams[bm].n_dm,
+                      static_cast<char*>(b->d_wout[k]) + oesz * (chunk_out(b, bm, c) - origin),
+                      b->n_bins[bm], b->n_bins[bm], 0, nullptr};
+        st = sink(sink_user, &blk, stream);
+        if (st != FDD_OK) return report_error(st, "the output sink failed");
+        if (blk.release_event) release = blk.release_event;  // the wave's last one counts
+      }
     }
     b->out_release[k] = release;
   }

@@ -578,7 +578,15 @@ struct G3 {
   static constexpr int kProd = kBins;          // producer warps
   static constexpr int kThreads = 32 * (kCons + kProd);
   static constexpr int kGFL = 2 * kA + 2 * kT;  // floats per (bin, channel): zr zi pr pi
-  static constexpr int kStageFloats = kCh * kBins * kGFL;
+  // wide items (a ragged remainder of at most 1024 or 512 trials): the a's
+  // 0 .. kAw - 1 (kAw 32 or 16) of 8 x 32 / kAw bins, zr zi (kAw each) and
+  // pr pi (32 each) per (bin, channel)
+  __host__ __device__ static constexpr int wide_bins(int aw) { return 8 * 32 / aw; }
+  __host__ __device__ static constexpr int wide_floats(int aw) { return 2 * aw + 2 * kT; }
+  static constexpr int kWideMax = wide_bins(16) * wide_floats(16) > wide_bins(32) * wide_floats(32)
+                                      ? wide_bins(16) * wide_floats(16)
+                                      : wide_bins(32) * wide_floats(32);
+  static constexpr int kStageFloats = kCh * (kBins * kGFL > kWideMax ? kBins * kGFL : kWideMax);
   static constexpr size_t kBarBytes = (2 * kStages * 8 + 4 + 15) / 16 * 16;
   static constexpr size_t kSwapBytes = kBarBytes + sizeof(float) * size_t(kStages) * kStageFloats;
 };
@@ -587,10 +595,7 @@ struct G3 {
 // local bin bin_tile * 4 and trials dm_block * 2048 + .. of one set of
 // spectra; ring stages and barrier phases continue from iteration it0.
 // Returns false after a timeout.
-// kHalf: a ragged last block of at most half the trials needs only the a's
-// 0..31: its second consumer warp of each bin and the producers' second Z
-// skip their work (the stage handshake stays the same).
-template <int kCh, int kStages, bool kHalf>
+template <int kCh, int kStages>
 __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs, float* stages,
                                         uint64_t* full, uint64_t* empty,
                                         volatile int* abort_flag, int bin_tile, int dm_block,
@@ -600,7 +605,6 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
   const int lane = threadIdx.x & 31;
   const int n_iter = (a.n_chan + kCh - 1) / kCh;
   const int jblk = dm_block * Ly::kDms;
-  constexpr bool half = kHalf;
   bool ok = true;
 
   if (warp >= Ly::kCons) {
@@ -609,9 +613,16 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
     const int k = bin_tile * Ly::kBins + q;
     const int kl = k < a.n_bins ? k : 0;          // idle bins evaluate local bin 0, unused
     const uint32_t ku = static_cast<uint32_t>(a.k_begin + kl);
-    const uint32_t m_z0 = ku * static_cast<uint32_t>(a.j_begin + jblk + lane * Ly::kT);
-    const uint32_t m_z1 = ku * static_cast<uint32_t>(a.j_begin + jblk + (lane + 32) * Ly::kT);
+    // Phases (units of 2^-32 cycle) of trial j0 + a T + b, j0 the block's
+    // first trial: Z_a takes k u + k j0 v + a (T k v) and P_b takes b k v.
+    // The lane-independent parts k u + k j0 v and 32 T k v of a channel are
+    // evaluated by one lane per channel and broadcast; a lane's own P phase
+    // (b = lane) gives its Z phases by a shift and an add (a T k v = T (a k
+    // v)), within 33 units of the exact phase.
+    const uint32_t m_j0 = ku * static_cast<uint32_t>(a.j_begin + jblk);
+    const uint32_t m_d = ku * static_cast<uint32_t>(32 * Ly::kT);
     const uint32_t m_p = ku * static_cast<uint32_t>(lane);
+    static_assert(Ly::kT == 32 && kCh <= 32 && (kCh & (kCh - 1)) == 0, "phase layout");
     const float2* xp = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
     const int64_t xs = a.x_chan_stride;
     float2 xn[kCh];
@@ -632,24 +643,39 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
                       dev::mbar_wait(&empty[s], ((g / kStages) & 1) ^ 1, abort_flag));
       if (!ok) break;
       float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
+      // lane l < kCh: the lane-independent phases of channel it kCh + l
+      uint32_t ph_a = 0, ph_d = 0;
+      {
+        const int c = it * kCh + (lane & (kCh - 1));
+        if (c < a.n_chan) {
+          const PhaseConst p = pcs[c];
+          ph_a = top32_mul(ku, p.u_lo, p.u_hi) + top32_mul(m_j0, p.v_lo, p.v_hi);
+          ph_d = top32_mul(m_d, p.v_lo, p.v_hi);
+        }
+      }
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         const int c = it * kCh + ch;
+        const uint32_t pa = __shfl_sync(0xffffffffu, ph_a, ch);
+        const uint32_t pd = __shfl_sync(0xffffffffu, ph_d, ch);
         if (c < a.n_chan) {
           const PhaseConst p = pcs[c];
-          const uint32_t base = top32_mul(ku, p.u_lo, p.u_hi);
-          const float2 w0 = unit_phasor(base + top32_mul(m_z0, p.v_lo, p.v_hi));
-          const float2 wp = unit_phasor(top32_mul(m_p, p.v_lo, p.v_hi));
+          const uint32_t pp = top32_mul(m_p, p.v_lo, p.v_hi);
+          const uint32_t pz0 = pa + (pp << 5);
+          const float2 w0 = unit_phasor(pz0);
+          const float2 w1 = unit_phasor(pz0 + pd);
+          const float2 wp = unit_phasor(pp);
+          // Z_lane and Z_lane+32 = X W as pairs
           const float2 xv = x[ch];
-          const float z0r = xv.x * w0.x - xv.y * w0.y, z0i = xv.x * w0.y + xv.y * w0.x;
+          const float2 cw = make_float2(w0.x, w1.x), sw = make_float2(w0.y, w1.y);
+          const float2 xr = make_float2(xv.x, xv.x);
+          const float2 zr = __ffma2_rn(xr, cw, __fmul2_rn(make_float2(-xv.y, -xv.y), sw));
+          const float2 zi = __ffma2_rn(xr, sw, __fmul2_rn(make_float2(xv.y, xv.y), cw));
           float* grp = st + ch * Ly::kBins * Ly::kGFL;
-          grp[lane] = z0r;
-          grp[Ly::kA + lane] = z0i;
-          if (!half) {
-            const float2 w1 = unit_phasor(base + top32_mul(m_z1, p.v_lo, p.v_hi));
-            grp[32 + lane] = xv.x * w1.x - xv.y * w1.y;
-            grp[Ly::kA + 32 + lane] = xv.x * w1.y + xv.y * w1.x;
-          }
+          grp[lane] = zr.x;
+          grp[Ly::kA + lane] = zi.x;
+          grp[32 + lane] = zr.y;
+          grp[Ly::kA + 32 + lane] = zi.y;
           grp[2 * Ly::kA + lane] = wp.x;
           grp[2 * Ly::kA + Ly::kT + lane] = wp.y;
         }
@@ -668,55 +694,35 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) A[i][m] = B[i][m] = C[i][m] = make_float2(0.f, 0.f);
-    if (half && h == 1) {  // nothing to accumulate: keep the stage handshake
-      for (int it = 0; it < n_iter; ++it) {
-        const uint32_t g = it0 + it;
-        const int s = g % kStages;
-        ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
-        if (!ok) break;
-        dev::mbar_arrive_warp(&empty[s]);
-      }
-    }
-    for (int it = 0; it < n_iter && !(half && h == 1); ++it) {
+    for (int it = 0; it < n_iter; ++it) {
       const uint32_t g = it0 + it;
       const int s = g % kStages;
       ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
       if (!ok) break;
       const float* st = stages + s * Ly::kStageFloats + q * Ly::kGFL;
       const int nc = a.n_chan - it * kCh;
-      // operands of channel ch + 1 are loaded before the products of ch
-      struct Ops {
-        float4 zr, zi, pr0, pr1, pi0, pi1;
-      };
-      auto load = [&](int ch) {
-        const float* grp = st + ch * Ly::kBins * Ly::kGFL;
-        const float* pp = grp + 2 * Ly::kA + 8 * gb;
-        Ops o;
-        o.zr = *reinterpret_cast<const float4*>(grp + 32 * h + 4 * ga);
-        o.zi = *reinterpret_cast<const float4*>(grp + Ly::kA + 32 * h + 4 * ga);
-        o.pr0 = *reinterpret_cast<const float4*>(pp);
-        o.pr1 = *reinterpret_cast<const float4*>(pp + 4);
-        o.pi0 = *reinterpret_cast<const float4*>(pp + Ly::kT);
-        o.pi1 = *reinterpret_cast<const float4*>(pp + Ly::kT + 4);
-        return o;
-      };
-      Ops cur = load(0);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         if (ch < nc) {
-          Ops nxt = cur;
-          if (ch + 1 < kCh && ch + 1 < nc) nxt = load(ch + 1);
-          const float2 pr[4] = {make_float2(cur.pr0.x, cur.pr0.y), make_float2(cur.pr0.z, cur.pr0.w),
-                                make_float2(cur.pr1.x, cur.pr1.y), make_float2(cur.pr1.z, cur.pr1.w)};
-          const float2 pi[4] = {make_float2(cur.pi0.x, cur.pi0.y), make_float2(cur.pi0.z, cur.pi0.w),
-                                make_float2(cur.pi1.x, cur.pi1.y), make_float2(cur.pi1.z, cur.pi1.w)};
+          const float* grp = st + ch * Ly::kBins * Ly::kGFL;
+          const float4 zr = *reinterpret_cast<const float4*>(grp + 32 * h + 4 * ga);
+          const float4 zi = *reinterpret_cast<const float4*>(grp + Ly::kA + 32 * h + 4 * ga);
+          const float* pp = grp + 2 * Ly::kA + 8 * gb;
+          const float4 pr0 = *reinterpret_cast<const float4*>(pp);
+          const float4 pr1 = *reinterpret_cast<const float4*>(pp + 4);
+          const float4 pi0 = *reinterpret_cast<const float4*>(pp + Ly::kT);
+          const float4 pi1 = *reinterpret_cast<const float4*>(pp + Ly::kT + 4);
+          const float2 pr[4] = {make_float2(pr0.x, pr0.y), make_float2(pr0.z, pr0.w),
+                                make_float2(pr1.x, pr1.y), make_float2(pr1.z, pr1.w)};
+          const float2 pi[4] = {make_float2(pi0.x, pi0.y), make_float2(pi0.z, pi0.w),
+                                make_float2(pi1.x, pi1.y), make_float2(pi1.z, pi1.w)};
           float2 ps[4];
 #pragma unroll
           for (int m = 0; m < 4; ++m) ps[m] = __fadd2_rn(pr[m], pi[m]);
-          const float2 zs01 = __fadd2_rn(make_float2(cur.zr.x, cur.zr.y), make_float2(cur.zi.x, cur.zi.y));
-          const float2 zs23 = __fadd2_rn(make_float2(cur.zr.z, cur.zr.w), make_float2(cur.zi.z, cur.zi.w));
-          const float zrv[4] = {cur.zr.x, cur.zr.y, cur.zr.z, cur.zr.w};
-          const float ziv[4] = {cur.zi.x, cur.zi.y, cur.zi.z, cur.zi.w};
+          const float2 zs01 = __fadd2_rn(make_float2(zr.x, zr.y), make_float2(zi.x, zi.y));
+          const float2 zs23 = __fadd2_rn(make_float2(zr.z, zr.w), make_float2(zi.z, zi.w));
+          const float zrv[4] = {zr.x, zr.y, zr.z, zr.w};
+          const float ziv[4] = {zi.x, zi.y, zi.z, zi.w};
           const float zsv[4] = {zs01.x, zs01.y, zs23.x, zs23.y};
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -730,12 +736,11 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
               C[i][m] = __ffma2_rn(s2, ps[m], C[i][m]);
             }
           }
-          cur = nxt;
         }
       }
       dev::mbar_arrive_warp(&empty[s]);
     }
-    if (ok && k < a.n_bins && !(half && h == 1)) {
+    if (ok && k < a.n_bins) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -769,16 +774,219 @@ __device__ __forceinline__ bool g3_body(const MacArgs& a, const PhaseConst* pcs,
   return ok;
 }
 
+// Wide item of the three-multiplication tile: a ragged remainder of at most
+// kAw x 32 trials (kAw = 32: 1024, kAw = 16: 512) from trial jw over the
+// CTA's 8 x 32 / kAw bins from bin_tile times that: consumer warp w owns
+// 32 / kAw of them (kAw / 4 x 4 lanes each, every lane busy), each lane a
+// 4 x 8 tile of (a, b) as in the full item; producer warp q evaluates, for its
+// quarter of the bins, P_b (b = lane) of each and the kAw Z_a of each (two per
+// lane).  Same stage ring and handshake as the full item.
+template <int kCh, int kStages, int kAw>
+__device__ __forceinline__ bool g3_wide_body(const MacArgs& a, const PhaseConst* pcs,
+                                             float* stages, uint64_t* full, uint64_t* empty,
+                                             volatile int* abort_flag, int bin_tile, int jw,
+                                             int series, uint32_t it0) {
+  using Ly = G3<kCh, kStages>;
+  constexpr int kNB = Ly::wide_bins(kAw);   // bins per CTA
+  constexpr int kW = Ly::wide_floats(kAw);  // floats per (bin, channel)
+  constexpr int kPB = kNB / Ly::kProd;      // bins per producer warp
+  constexpr int kLPB = kAw;                 // lanes per bin in a consumer warp (kAw/4 x 4)
+  static_assert(kAw == 32 || kAw == 16, "wide items of 1024 or 512 trials");
+  static_assert(kNB == Ly::kCons * 32 / kLPB && 2 * 32 == kPB * kAw, "wide layout");
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n_iter = (a.n_chan + kCh - 1) / kCh;
+  const int bin0 = bin_tile * kNB;
+  bool ok = true;
+
+  if (warp >= Ly::kCons) {
+    // ------------------------------------------------------------ producers
+    const int q = warp - Ly::kCons;
+    uint32_t ku[kPB], m_p[kPB];
+    const float2* xp[kPB];
+#pragma unroll
+    for (int r = 0; r < kPB; ++r) {
+      const int k = bin0 + q * kPB + r;
+      const int kl = k < a.n_bins ? k : 0;  // idle bins evaluate local bin 0, unused
+      ku[r] = static_cast<uint32_t>(a.k_begin + kl);
+      m_p[r] = ku[r] * static_cast<uint32_t>(lane);
+      xp[r] = a.X + static_cast<int64_t>(series) * a.x_series_stride + kl;
+    }
+    // the lane's two Z_a: a = lane mod kAw of the warp's bins 32 t / kAw + lane / kAw
+    // (bin t for kAw 32; bin 2 t + lane / 16 for kAw 16: chosen by selects)
+    const bool hi = kAw == 16 && lane >= 16;
+    uint32_t m_z[2], k_z[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int r0 = t * (32 / kAw);
+      k_z[t] = (kAw == 16 && hi) ? ku[(r0 + 1) % kPB] : ku[r0];
+      m_z[t] = k_z[t] * static_cast<uint32_t>(a.j_begin + jw + (lane % kAw) * Ly::kT);
+    }
+    const int64_t xs = a.x_chan_stride;
+    float2 xn[kPB][kCh];
+#pragma unroll
+    for (int r = 0; r < kPB; ++r)
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch)
+        xn[r][ch] = ch < a.n_chan ? __ldg(xp[r] + ch * xs) : make_float2(0.f, 0.f);
+    for (int it = 0; it < n_iter; ++it) {
+      const uint32_t g = it0 + it;
+      const int s = g % kStages;
+      float2 x[kPB][kCh];
+#pragma unroll
+      for (int r = 0; r < kPB; ++r)
+#pragma unroll
+        for (int ch = 0; ch < kCh; ++ch) {
+          x[r][ch] = xn[r][ch];
+          const int c = (it + 1) * kCh + ch;  // prefetch the next stage's X
+          xn[r][ch] = c < a.n_chan ? __ldg(xp[r] + c * xs) : make_float2(0.f, 0.f);
+        }
+      ok = __all_sync(0xffffffffu,
+                      dev::mbar_wait(&empty[s], ((g / kStages) & 1) ^ 1, abort_flag));
+      if (!ok) break;
+      float* st = stages + s * Ly::kStageFloats;
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) {
+        const int c = it * kCh + ch;
+        if (c < a.n_chan) {
+          const PhaseConst p = pcs[c];
+#pragma unroll
+          for (int r = 0; r < kPB; ++r) {
+            const float2 wp = unit_phasor(top32_mul(m_p[r], p.v_lo, p.v_hi));
+            float* grp = st + (ch * kNB + q * kPB + r) * kW;
+            grp[2 * kAw + lane] = wp.x;
+            grp[2 * kAw + 32 + lane] = wp.y;
+          }
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int r0 = t * (32 / kAw);
+            const int r = hi ? r0 + 1 : r0;
+            const float2 xv = (kAw == 16 && hi) ? x[(r0 + 1) % kPB][ch] : x[r0][ch];
+            const float2 w = unit_phasor(top32_mul(k_z[t], p.u_lo, p.u_hi) +
+                                         top32_mul(m_z[t], p.v_lo, p.v_hi));
+            float* grp = st + (ch * kNB + q * kPB + r) * kW;
+            const int ai = lane % kAw;
+            grp[ai] = xv.x * w.x - xv.y * w.y;
+            grp[kAw + ai] = xv.x * w.y + xv.y * w.x;
+          }
+        }
+      }
+      if (!a.test_withhold) dev::mbar_arrive_warp(&full[s]);
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int wb = warp * (32 / kLPB) + lane / kLPB;  // the lane's bin in the CTA
+    const int k = bin0 + wb;                          // local bin
+    const int ll = lane % kLPB;
+    const int ga = ll >> 2;  // a = 4 ga + i
+    const int gb = ll & 3;   // b = 8 gb + j
+    float2 A[4][4], B[4][4], C[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) A[i][m] = B[i][m] = C[i][m] = make_float2(0.f, 0.f);
+    for (int it = 0; it < n_iter; ++it) {
+      const uint32_t g = it0 + it;
+      const int s = g % kStages;
+      ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
+      if (!ok) break;
+      const int nc = a.n_chan - it * kCh;
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) {
+        if (ch < nc) {
+          const float* grp = stages + s * Ly::kStageFloats + (ch * kNB + wb) * kW;
+          const float4 zr = *reinterpret_cast<const float4*>(grp + 4 * ga);
+          const float4 zi = *reinterpret_cast<const float4*>(grp + kAw + 4 * ga);
+          const float4 pr0 = *reinterpret_cast<const float4*>(grp + 2 * kAw + 8 * gb);
+          const float4 pr1 = *reinterpret_cast<const float4*>(grp + 2 * kAw + 8 * gb + 4);
+          const float4 pi0 = *reinterpret_cast<const float4*>(grp + 2 * kAw + 32 + 8 * gb);
+          const float4 pi1 = *reinterpret_cast<const float4*>(grp + 2 * kAw + 32 + 8 * gb + 4);
+          const float2 pr[4] = {make_float2(pr0.x, pr0.y), make_float2(pr0.z, pr0.w),
+                                make_float2(pr1.x, pr1.y), make_float2(pr1.z, pr1.w)};
+          const float2 pi[4] = {make_float2(pi0.x, pi0.y), make_float2(pi0.z, pi0.w),
+                                make_float2(pi1.x, pi1.y), make_float2(pi1.z, pi1.w)};
+          float2 ps[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) ps[m] = __fadd2_rn(pr[m], pi[m]);
+          const float2 zs01 = __fadd2_rn(make_float2(zr.x, zr.y), make_float2(zi.x, zi.y));
+          const float2 zs23 = __fadd2_rn(make_float2(zr.z, zr.w), make_float2(zi.z, zi.w));
+          const float zrv[4] = {zr.x, zr.y, zr.z, zr.w};
+          const float ziv[4] = {zi.x, zi.y, zi.z, zi.w};
+          const float zsv[4] = {zs01.x, zs01.y, zs23.x, zs23.y};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 r2 = make_float2(zrv[i], zrv[i]);
+            const float2 i2 = make_float2(ziv[i], ziv[i]);
+            const float2 s2 = make_float2(zsv[i], zsv[i]);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              A[i][m] = __ffma2_rn(r2, pr[m], A[i][m]);
+              B[i][m] = __ffma2_rn(i2, pi[m], B[i][m]);
+              C[i][m] = __ffma2_rn(s2, ps[m], C[i][m]);
+            }
+          }
+        }
+      }
+      dev::mbar_arrive_warp(&empty[s]);
+    }
+    if (ok && k < a.n_bins) {
+      const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float av = e ? A[i][m].y : A[i][m].x;
+            const float bv = e ? B[i][m].y : B[i][m].x;
+            const float cv = e ? C[i][m].y : C[i][m].x;
+            const int jl = jw + (4 * ga + i) * Ly::kT + 8 * gb + 2 * m + e;
+            if (jl < a.n_dm) {
+              const float re = (av - bv) * a.scale;
+              const float im = real_only ? 0.f : (cv - av - bv) * a.scale;
+              const int64_t o = static_cast<int64_t>(series) * a.y_series_stride +
+                                static_cast<int64_t>(jl) * a.y_dm_stride + k;
+              if (a.out_kind == 2)
+                static_cast<float*>(a.Y)[o] = re * re + im * im;
+              else
+                static_cast<float2*>(a.Y)[o] = make_float2(re, im);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (!ok) {
+    *abort_flag = 1;
+    if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+  }
+  return ok;
+}
+
+// A grid item of the three-multiplication tile: a full item, or for a last
+// block of at most 1024 (512) trials a wide item over twice (four times) the
+// bins (the grid's bin tiles beyond the wide ones have nothing to do and
+// leave at once).
 template <int kCh, int kStages>
 __device__ __forceinline__ bool g3_item(const MacArgs& a, const PhaseConst* pcs, float* stages,
                                         uint64_t* full, uint64_t* empty,
                                         volatile int* abort_flag, int bin_tile, int dm_block,
                                         int series, uint32_t it0) {
-  if (a.n_dm - dm_block * G3<kCh, kStages>::kDms <= G3<kCh, kStages>::kDms / 2)
-    return g3_body<kCh, kStages, true>(a, pcs, stages, full, empty, abort_flag, bin_tile,
-                                       dm_block, series, it0);
-  return g3_body<kCh, kStages, false>(a, pcs, stages, full, empty, abort_flag, bin_tile,
-                                      dm_block, series, it0);
+  using Ly = G3<kCh, kStages>;
+  const int jblk = dm_block * Ly::kDms;
+  const int rem = a.n_dm - jblk;
+  if (rem <= Ly::kDms / 4) {
+    if (bin_tile * Ly::wide_bins(16) >= a.n_bins) return true;
+    return g3_wide_body<kCh, kStages, 16>(a, pcs, stages, full, empty, abort_flag, bin_tile,
+                                          jblk, series, it0);
+  }
+  if (rem <= Ly::kDms / 2) {
+    if (bin_tile * Ly::wide_bins(32) >= a.n_bins) return true;
+    return g3_wide_body<kCh, kStages, 32>(a, pcs, stages, full, empty, abort_flag, bin_tile,
+                                          jblk, series, it0);
+  }
+  return g3_body<kCh, kStages>(a, pcs, stages, full, empty, abort_flag, bin_tile, dm_block,
+                               series, it0);
 }
 
 template <int kCh, int kStages>
@@ -825,9 +1033,19 @@ __global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
     }
     __syncthreads();  // phase table ready; item_s read by every thread
     const long long local = item - bs.item_begin;
-    g3_item<kCh, kStages>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
-                          static_cast<int>(local / bs.n_dm_blocks),
-                          static_cast<int>(local % bs.n_dm_blocks), 0, it0);
+    const long long n_full = static_cast<long long>(bs.n_bin_tiles) * bs.n_dm_blocks;
+    if (local < n_full)
+      g3_body<kCh, kStages>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
+                            static_cast<int>(local / bs.n_dm_blocks),
+                            static_cast<int>(local % bs.n_dm_blocks), 0, it0);
+    else if (bs.wide_trials == 512)
+      g3_wide_body<kCh, kStages, 16>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty,
+                                     sm.abort_flag, static_cast<int>(local - n_full), bs.j_wide,
+                                     0, it0);
+    else
+      g3_wide_body<kCh, kStages, 32>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty,
+                                     sm.abort_flag, static_cast<int>(local - n_full), bs.j_wide,
+                                     0, it0);
     it0 += n_iter;
   }
 }
@@ -887,23 +1105,32 @@ VariantInfo variant_info(int v) {
 // Default tile for a trial count: the one with the least time for the padded
 // trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
 // measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
-// 131073 bins, full blocks): G12_4x8 0.650 (2048-trial blocks), Q_4x8 0.493
-// (1024), Q_8x8_512 0.415 (512), Q_4x4 0.347 (128).  (The four-product
-// warp-specialised tile W12_8x8 measured 0.622 on the same launch, Q12_8x8,
-// the 2048-trial tile on the plain schedule, 0.553.)
+// 131073 bins): G12_4x8 0.661 on full 2048-trial blocks, whose last block
+// runs as 1024-trial wide items at 0.578 (at most 1024 trials) or 512-trial
+// ones at 0.486 (at most 512); Q_4x8 0.493 (1024-trial blocks), Q_8x8_512
+// 0.415 (512), Q_4x4 0.347 (128).  (The four-product warp-specialised tile
+// W12_8x8 measured 0.621 on the same launch, Q12_8x8, the 2048-trial tile on
+// the plain schedule, 0.553.)
 int mac_variant_for(int n_dm) {
   struct Tile {
     int variant, block;
-    double rate;
+    double rate, wide_rate, narrow_rate;  // > 0: a last block of <= block / 2, / 4
   };
-  static const Tile tiles[] = {
-      {MAC_G12_4x8, 2048, 0.650}, {MAC_Q_4x8, 1024, 0.493}, {MAC_Q_8x8_512, 512, 0.415},
-      {MAC_Q_4x4, 128, 0.347}};
+  static const Tile tiles[] = {{MAC_G12_4x8, 2048, 0.661, 0.578, 0.486},
+                               {MAC_Q_4x8, 1024, 0.493, 0.0, 0.0},
+                               {MAC_Q_8x8_512, 512, 0.415, 0.0, 0.0},
+                               {MAC_Q_4x4, 128, 0.347, 0.0, 0.0}};
   int best = MAC_G12_4x8;
   double best_cost = 0.0;
   for (const Tile& t : tiles) {
-    const double padded = static_cast<double>((n_dm + t.block - 1) / t.block) * t.block;
-    const double cost = padded / t.rate;
+    const int full = n_dm / t.block, rem = n_dm % t.block;
+    double cost = full * t.block / t.rate;
+    if (rem > 0 && t.narrow_rate > 0.0 && rem <= t.block / 4)
+      cost += (t.block / 4) / t.narrow_rate;
+    else if (rem > 0 && t.wide_rate > 0.0 && rem <= t.block / 2)
+      cost += (t.block / 2) / t.wide_rate;
+    else if (rem > 0)
+      cost += t.block / t.rate;
     if (best_cost == 0.0 || cost < best_cost) {
       best = t.variant;
       best_cost = cost;

@@ -150,12 +150,13 @@ def test_variant_choice():
         assert fdd.fdd_plan_geometry(_params(w, mac_variant=v + 1))["mac_variant"] == v
     w2 = synth.WORKLOADS["fdd_1024ch_2p20t_2048dm"]
     assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_G12_4X8
-    # least padded-block time: 128-trial blocks up to 384 trials, 512-trial
-    # blocks to 512, 128 again to ~700, 1024 to 1024, 2048 from 1100 (measured
-    # tile rates 0.347 / 0.415 / 0.493 / 0.623)
-    for n, v in [(1, fdd.FDD_MAC_Q_4X4), (384, fdd.FDD_MAC_Q_4X4), (448, fdd.FDD_MAC_Q_8X8_512),
-                 (512, fdd.FDD_MAC_Q_8X8_512), (600, fdd.FDD_MAC_Q_4X4),
-                 (700, fdd.FDD_MAC_Q_4X8), (1024, fdd.FDD_MAC_Q_4X8),
+    # least padded-block time: 128-trial blocks up to 256 trials, the
+    # 2048-trial tile above (a last block of <= 512 or <= 1024 trials as
+    # 512- or 1024-trial wide items); measured rates 0.347 (128), 0.661
+    # (2048), wide 0.578, narrow 0.486
+    for n, v in [(1, fdd.FDD_MAC_Q_4X4), (256, fdd.FDD_MAC_Q_4X4), (384, fdd.FDD_MAC_G12_4X8),
+                 (448, fdd.FDD_MAC_G12_4X8), (512, fdd.FDD_MAC_G12_4X8),
+                 (600, fdd.FDD_MAC_G12_4X8), (1024, fdd.FDD_MAC_G12_4X8),
                  (1100, fdd.FDD_MAC_G12_4X8), (4096, fdd.FDD_MAC_G12_4X8)]:
         g = fdd.fdd_plan_geometry(_params(w2, dm_list=0.5 * np.arange(n)))
         assert g["mac_variant"] == v, (n, g["mac_variant"])

@@ -88,7 +88,7 @@ def test_batch_matches_oracle(output):
         assert batch.info["n_waves"] == 1
         assert batch.info["mac_variant"] == fdd.FDD_MAC_G12_4X8
         # the three-product tile runs a beam's ragged last block (<= 1024
-        # trials) at half work inside the same persistent launch
+        # trials) as wide items (eight bins, 1024 trials) in the same persistent launch
         assert batch.info["tail_variant"] == -1
         assert batch.in_offsets == list(np.cumsum([0] + [b[0] * N_CHAN for b in BEAMS])[:-1])
         o, _, _ = _run(batch, xs, output)
@@ -142,6 +142,67 @@ def test_batch_autotune_picks_a_timed_candidate():
     _check(batch, o, _refs(xs), fdd.FDD_OUT_POWER)
 
 
+# (n_t, dm0, ddm, n_dm, chunk_len): beams in overlap-save chunks of their own
+# lengths next to a whole-series beam (largest delays 131, 34, 533 and 607
+# samples), chunk counts 4, 1, 3 and 1
+CHUNKED = [(3000, 0.0, 1.0, 130, 1024), (1000, 2.0, 0.5, 64, 0), (5000, 0.0, 0.25, 2100, 2048),
+           (700, 0.0, 2.0, 300, 1024)]
+
+
+def _oracle_chunks(x, beam):
+    n_t, dm0, ddm, n_dm, chunk = beam
+    dnu = (BAND[1] - BAND[0]) / N_CHAN
+    nu = BAND[0] + 0.5 * dnu + dnu * np.arange(N_CHAN)
+    d = oracle.delays(nu, dm0 + ddm * np.arange(n_dm), T_SAMP)
+    geo = oracle.geometry(n_t, chunk, d)
+    return [oracle.fdd_bins(oracle.spectra(x.T.astype(np.float64), geo, c), np.arange(geo.K),
+                            geo.L, d) for c in range(geo.n_chunks)]
+
+
+@pytest.mark.parametrize("variant", [0, fdd.FDD_MAC_W12_8X8 + 1])
+def test_batch_chunked_beams_match_oracle(variant):
+    """Beams with their own overlap-save chunk lengths: every chunk of every
+    beam is a work set of the one persistent launch, output [chunk][dm][bin]
+    per beam, each chunk against the oracle's spectra of that chunk; the
+    streamed execute delivers one block per (beam, chunk) with the same bytes."""
+    rng = np.random.default_rng(33)
+    xs = [rng.standard_normal((b[0], N_CHAN)).astype(np.float32) for b in CHUNKED]
+    refs = [_oracle_chunks(x, b) for x, b in zip(xs, CHUNKED)]
+    assert [len(r) for r in refs] == [4, 1, 3, 1]
+    with fdd.Batch(CHUNKED, autotune=False, mac_variant=variant,
+                   **_common(fdd.FDD_OUT_POWER)) as batch:
+        assert batch.info["out_elems"] == sum(len(r) * r[0].size for r in refs)
+        d_in = torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
+        out = torch.zeros(batch.info["out_elems"], device="cuda")
+        batch.execute(d_in, out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.float64)
+        for i, ref in enumerate(refs):
+            for c, r in enumerate(ref):
+                off = batch.out_offsets[i] + c * r.size
+                got = o[off: off + r.size].reshape(r.shape)
+                assert rel_l2(got, np.abs(r) ** 2) <= 2 * FP32_REL_L2, (i, c)
+        got = torch.full_like(out, float("nan"))
+        seen = []
+
+        def source(beam, t0, n, d_window, ready, s):
+            fdd.memcpy_async(d_window, d_in.data_ptr() + 4 * batch.in_offsets[beam],
+                             4 * n * N_CHAN, s)
+
+        def sink(blk, s):
+            b, c = blk["beam_first"], blk["chunk"]
+            seen.append((b, c))
+            n = blk["n_dm"] * blk["row_len"]
+            fdd.memcpy_async(got.data_ptr() + 4 * (batch.out_offsets[b] + c * n), blk["d_data"],
+                             4 * n, s)
+            return None
+
+        batch.execute_stream(source, sink, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert seen == [(b, c) for b, r in enumerate(refs) for c in range(len(r))]
+        assert torch.equal(got, out)
+
+
 def test_batch_rejects_what_it_does_not_do():
     with pytest.raises(fdd.FddError) as e:
         fdd.Batch(BEAMS, **_common(fdd.FDD_OUT_TIME))
@@ -191,3 +252,81 @@ def test_batch_streamed_equals_resident_execute(variant, limit):
             torch.cuda.synchronize()
             assert sorted(seen) == list(range(len(BEAMS)))
             assert np.array_equal(got.cpu().numpy().astype(np.float64), ref)
+
+
+# (n_t, dm0, ddm, n_dm, chunk_len) for the tensor-core batch: three
+# whole-series beams of one transform length (4096) and trial grid with
+# uneven lengths and trial counts (one plan, run to 300 trials), a beam of
+# another length and grid (its own plan), and two chunked beams of one chunk
+# length and trial count with 3 and 2 chunks (one plan)
+TC_BEAMS = [(3000, 0.0, 1.0, 130, 0), (2500, 0.0, 1.0, 300, 0), (4000, 0.0, 1.0, 64, 0),
+            (1000, 2.0, 0.5, 64, 0), (5000, 0.0, 0.25, 2100, 2048),
+            (3500, 0.0, 0.25, 2100, 2048)]
+TC_REL = 3e-3  # accuracy gate of the tensor-core forms against the FP64 oracle
+
+
+def _tc_batch_run(batch, d_in, output):
+    n = batch.info["out_elems"]
+    out = torch.zeros((n, 2) if output == fdd.FDD_OUT_SPECTRA else (n,), device="cuda")
+    batch.execute(d_in, out)
+    torch.cuda.synchronize()
+    return out
+
+
+def _tc_check(batch, out, refs, output):
+    o = out.cpu().numpy().astype(np.float64)
+    if output == fdd.FDD_OUT_SPECTRA:
+        o = o[:, 0] + 1j * o[:, 1]
+    for i, ref in enumerate(refs):
+        for c, r in enumerate(ref):
+            off = batch.out_offsets[i] + c * r.size
+            got = o[off: off + r.size].reshape(r.shape)
+            want = r if output == fdd.FDD_OUT_SPECTRA else np.abs(r) ** 2
+            tol = TC_REL if output == fdd.FDD_OUT_SPECTRA else 2 * TC_REL
+            assert rel_l2(got, want) <= tol, (i, c, rel_l2(got, want))
+
+
+@pytest.mark.parametrize("output", [fdd.FDD_OUT_SPECTRA, fdd.FDD_OUT_POWER])
+def test_tensor_core_batch_matches_oracle(output):
+    """Beams grouped by shared phasors into FP16 tensor-core plans: every beam,
+    chunk and trial against the oracle; streamed, the same bytes; with plans
+    made per execute (a workspace limit below their sum), the oracle again."""
+    rng = np.random.default_rng(44)
+    xs = [rng.standard_normal((b[0], N_CHAN)).astype(np.float32) for b in TC_BEAMS]
+    refs = [_oracle_chunks(x, b) for x, b in zip(xs, TC_BEAMS)]
+    assert [len(r) for r in refs] == [1, 1, 1, 1, 3, 2]
+    d_in = torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
+    kw = _common(output, precision=fdd.FDD_PREC_FP16)
+    with fdd.Batch(TC_BEAMS, **kw) as batch:
+        assert batch.info["mac_variant"] == fdd.FDD_MAC_TC
+        assert batch.info["n_waves"] == 3  # plans
+        held = batch.info["workspace_bytes"]
+        assert held > 0  # kept between executes
+        out = _tc_batch_run(batch, d_in, output)
+        _tc_check(batch, out, refs, output)
+        # streamed: one block per (beam, chunk, block of trials)
+        got = torch.full_like(out, float("nan"))
+        esz = 8 if output == fdd.FDD_OUT_SPECTRA else 4
+
+        def source(beam, t0, n, d_window, ready, s):
+            assert 0 <= t0 and t0 + n <= TC_BEAMS[beam][0]
+            fdd.memcpy_async(d_window,
+                             d_in.data_ptr() + 4 * (batch.in_offsets[beam] + t0 * N_CHAN),
+                             4 * n * N_CHAN, s)
+
+        def sink(blk, s):
+            b, c = blk["beam_first"], blk["chunk"]
+            assert blk["dm_first"] + blk["n_dm"] <= TC_BEAMS[b][3]
+            K = blk["row_len"]
+            dst = batch.out_offsets[b] + (c * TC_BEAMS[b][3] + blk["dm_first"]) * K
+            fdd.memcpy_async(got.data_ptr() + esz * dst, blk["d_data"], esz * blk["n_dm"] * K, s)
+            return None
+
+        batch.execute_stream(source, sink, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert torch.equal(got, out)
+    # plans made for each execute (a limit below their sum, above each one's
+    # least workspace; their trial blocks may differ)
+    with fdd.Batch(TC_BEAMS, workspace_limit=held // 2, **kw) as batch:
+        assert batch.info["workspace_bytes"] == 0
+        _tc_check(batch, _tc_batch_run(batch, d_in, output), refs, output)

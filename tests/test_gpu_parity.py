@@ -50,6 +50,7 @@ KERNEL_CASES = [
     (37, 1024, 0.0, 1.0, 130, 1),     # 128-trial tile: 2 blocks, ragged; 513 bins ragged
     (64, 2048, 3.0, 0.5, 700, 2),     # 1024-trial tile, DM0 != 0, two series
     (16, 4096, 0.0, 0.25, 2100, 1),   # 2048-trial tile plus a ragged block
+    (12, 1024, 1.0, 0.3, 3500, 1),    # ragged 2048-trial block of more than 1024 trials
     (5, 64, 7.0, 0.0, 1, 1),          # one trial
     (1, 128, 0.0, 2.0, 3, 3),         # one channel
 ]
