@@ -67,6 +67,11 @@ def parse_args():
     ap.add_argument("--downsample-sweep", action="store_true",
                     help="time the workload's whole call at down-sampling factors 1, 2, 4, 8 "
                          "and print one JSON line per factor")
+    ap.add_argument("--spin-sweep", action="store_true",
+                    help="whole call in the FP32 form and with spin-frequency DM grids (FP16 "
+                         "tensor cores, groups of 16 and 32 bins), with the grids' error")
+    ap.add_argument("--spin-tol", type=float, default=0.01,
+                    help="with --spin-sweep: the largest DM contraction within a group")
     ap.add_argument("--crossover", action="store_true",
                     help="time Fourier- and time-domain dedispersion of the workload at "
                          "128..n_dm trials (one JSON line per trial count)")
@@ -83,6 +88,10 @@ def parse_args():
     ap.add_argument("--batch", default="",
                     help="time the batching form on a BATCH_WORKLOADS entry instead "
                          "(one JSON line)")
+    ap.add_argument("--batch-precision", default="fp32",
+                    choices=["fp32", "fp16", "bf16", "bf16_hilo", "fp8"],
+                    help="with --batch: the FP32 form (persistent launch per wave) or a "
+                         "tensor-core form (groups of beams sharing their phasors)")
     ap.add_argument("--batch-n-t-div", type=int, default=16,
                     help="divide the batch workload's beam lengths (device memory bound)")
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "bf16_hilo", "fp8"],
@@ -544,6 +553,71 @@ def run_downsample_sweep(args) -> None:
                               "macs_per_s": macs / (ms / 1e3), "time_over_f1": ms / ms1,
                               "tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]]}), flush=True)
             del out
+
+
+def run_spin_sweep(args) -> None:
+    """The workload's whole call (time output) in the FP32 form and with the
+    spin-frequency-dependent DM grids on FP16 tensor cores (Sect. 2.3; groups
+    of 16 and 32 bins at the given contraction tolerance), one JSON line
+    each, with the spin form's rel-L2 on sampled bins of chunk 0 against
+    Eq. 7 (the oracle's exact sum) and against the oracle's restatement of
+    the same approximation."""
+    import torch
+
+    import oracle
+    import paper_2110_03482_gb300 as fdd
+
+    fdd.build()
+    w = workload_from_args(args)
+    fb, _ = synth.filterbank(w, seed=args.seed)
+    d_in = torch.from_numpy(fb.reshape(-1)).cuda()
+    stream = torch.cuda.current_stream()
+    d, geo, X = oracle_sample_setup(w, args.seed)
+    rng = np.random.default_rng(args.seed)
+    bins = np.unique(np.concatenate([[1, geo.K // 2, geo.K - 1], rng.integers(2, geo.K - 1, 29)]))
+    ref = oracle.fdd_bins(X[:, bins], bins, geo.L, d)
+    ms_fp32 = None
+    for G in (0, 16, 32):
+        kw = dict(plan_params(w, fdd))
+        if G:
+            kw.update(precision=fdd.FDD_PREC_FP16, spin_group=G, spin_tol=args.spin_tol)
+        with fdd.Plan(**kw) as plan:
+            info = plan.info
+            out = torch.empty(info["out_elems"], dtype=torch.float32, device="cuda")
+            for _ in range(max(args.warmup, 1)):
+                plan.execute(d_in, out, stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                plan.execute(d_in, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            del out
+        ms_fp32 = ms if G == 0 else ms_fp32
+        line = {"spin_group": G, "workload": w.name, "ms_per_call": ms,
+                "macs_per_s": macs_per_beam(w, info) / (ms / 1e3),
+                "speedup_vs_fp32": ms_fp32 / ms}
+        if G:
+            # the dedispersed spectra of chunk 0 at the sampled bins
+            with fdd.Plan(**dict(kw, output=fdd.FDD_OUT_SPECTRA)) as plan:
+                sp = torch.empty(plan.info["out_elems"] * 2, dtype=torch.float32, device="cuda")
+                plan.execute(d_in, sp, stream)
+                torch.cuda.synchronize()
+                Y = sp.view(-1, 2)[: w.n_dm * geo.K].view(w.n_dm, geo.K, 2)
+                Yb = Y[:, torch.from_numpy(bins).cuda()].cpu().numpy().astype(np.float64)
+                got = Yb[..., 0] + 1j * Yb[..., 1]
+                del sp, Y
+            appr = oracle.fdd_bins_spin(X[:, bins], bins, geo.L, w.channel_centres(), w.dm0,
+                                        w.ddm, w.n_dm, w.t_samp_s, G, args.spin_tol)
+            line.update(spin_k_min=info["spin_k_min"], spin_tol=args.spin_tol,
+                        rel_l2_vs_eq7=_rel(got, ref), rel_l2_vs_restatement=_rel(got, appr),
+                        restatement_vs_eq7=_rel(appr, ref),
+                        sample=f"{bins.size} bins of chunk 0 (1, K/2, Nyquist, random), "
+                               f"all {w.n_dm} trials")
+        print(json.dumps(line), flush=True)
 
 
 def run_fdd(args, rank: int, world: int, dist) -> None:
@@ -1052,8 +1126,13 @@ def run_batch(args) -> None:
     beams = bw.beams(args.seed, n_t_div=args.batch_n_t_div)
     common = dict(n_chan=bw.n_chan, nu_lo_mhz=bw.nu_lo_mhz, dnu_mhz=bw.dnu_mhz,
                   t_samp_s=bw.t_samp_s, in_dtype=fdd.FDD_IN_F32, chunk_len=0,
-                  output={"spectra": fdd.FDD_OUT_SPECTRA, "power": fdd.FDD_OUT_POWER}[bw.output],
-                  workspace_limit=int(min(args.workspace_gib, 100.0) * (1 << 30)))
+                  output={"spectra": fdd.FDD_OUT_SPECTRA, "power": fdd.FDD_OUT_POWER}[bw.output])
+    tc = args.batch_precision != "fp32"
+    if tc:  # plans of up to 16 beams, each within the limit (streamed output)
+        common.update(precision=TC_PREC[args.batch_precision],
+                      workspace_limit=int(args.workspace_gib * (1 << 30)))
+    else:  # waves of spectra, leaving room for two output slots per wave
+        common.update(workspace_limit=int(min(args.workspace_gib, 100.0) * (1 << 30)))
     gen_kw = [synth.batch_beam_args(bw, desc, args.seed, b)[0] for b, desc in enumerate(beams)]
     t0 = time.perf_counter()
     with fdd.Batch(beams, autotune=True, **common) as batch:
@@ -1105,19 +1184,25 @@ def run_batch(args) -> None:
     props = torch.cuda.get_device_properties(0)
     peak = props.multi_processor_count * 128 * 2 * float(load_peaks().get("sm_max_mhz") or 2070) * 1e6
     n_ts = [b[0] for b in beams]
+    tc_peak = float(load_peaks().get("bf16_tflops_sustained") or 1700.0) * 1e12
     line = {"metric": METRIC, "value": macs / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.batch_precision if tc else "f32",
             "data": "synthetic (seeded Philox4x32-10 noise + one dispersed pulse per beam, "
                     "generated on the device)",
-            "form": "batching (persistent launch per wave, autotuned tile)" +
-                    (", CUDA graph" if resident else ", streamed windows and output blocks"),
+            "form": ("batching on tensor cores (beams grouped by shared phasors, one plan "
+                     "per group of up to 16 beams)" if tc else
+                     "batching (persistent launch per wave, autotuned tile)") +
+                    (", CUDA graph" if resident and not tc else
+                     ", streamed windows and output blocks"),
             "config": {"workload": bw.name, "beams": bw.n_beams, "n_chan": bw.n_chan,
                        "n_t_range": [min(n_ts), max(n_ts)], "n_t_divisor": args.batch_n_t_div,
                        "trials_range": [min(b[3] for b in beams), max(b[3] for b in beams)],
                        "output": bw.output, "waves": info["n_waves"],
                        "work_items": info["work_items"], "ctas": info["ctas"],
-                       "tile": fdd.MAC_VARIANT_NAMES[info["mac_variant"]],
+                       "tile": ("TC" if tc else fdd.MAC_VARIANT_NAMES[info["mac_variant"]]),
+                       "plans_resident": bool(tc and info["workspace_bytes"] > 0),
                        "tail_tile": (fdd.MAC_VARIANT_NAMES[info["tail_variant"]]
                                      if info["tail_variant"] >= 0 else None),
                        "autotune_ms": info["autotune_ms"], "plan_seconds": plan_s,
@@ -1126,6 +1211,8 @@ def run_batch(args) -> None:
                              "streamed (input windows generated per beam on the device; output "
                              f"blocks counted: {delivered[0] // max(args.steps, 1)} B per step)"},
             "fp32_frac_whole_step": FLOPS_PER_MAC * macs / (ms / 1e3) / peak,
+            "tensor_frac_whole_step": (FLOPS_PER_MAC * macs / (ms / 1e3) / tc_peak
+                                       if tc else None),
             "macs_per_step": macs, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -1150,6 +1237,9 @@ def main():
         return
     if args.downsample_sweep:
         run_downsample_sweep(args)
+        return
+    if args.spin_sweep:
+        run_spin_sweep(args)
         return
     if args.impl == "fdd" and synth.WORKLOADS[args.workload].n_beams > 1:
         run_tc_workload(args)

@@ -516,13 +516,18 @@ typedef struct fdd_batch_info {
  * beams are grouped by what their phasors share: whole-series beams by
  * transform length and trial grid origin and step, chunked beams also by
  * chunk length and trial count (which set the overlap); each group, sorted
- * by trial count and cut into plans of up to 16 beams, runs as one
+ * by trial count and cut into plans of up to 16 beams (fewer where such a
+ * plan, with its streaming rings, would exceed workspace_limit), runs as one
  * tensor-core plan (fdd_plan with that precision) over its largest series
  * and trial count, shorter beams reading zeros beyond their samples and
- * keeping their own trials and chunks.  The plans are made here when their
- * workspaces fit workspace_limit together, else each execute makes each plan
- * for its turn and destroys it after (one at a time).  fdd_batch_info then
- * gives mac_variant FDD_MAC_TC and n_waves the number of plans.
+ * keeping their own trials and chunks.  The plans are made here, each with
+ * its own workspace when those fit workspace_limit together, else all
+ * taking their per-call buffers (spectra, scratch, FFT work area, streaming
+ * rings) from one shared device block of the largest plan's size, which
+ * works because they run one after another; if even that block cannot be
+ * had, each execute makes each plan for its turn and destroys it after.
+ * fdd_batch_info then gives mac_variant FDD_MAC_TC and n_waves the number of
+ * plans.
  * Allocates all device memory (and, while autotuning, a temporary output).
  * Layouts: the input is the beams' inputs concatenated in order (each
  * [n_t][n_chan] or [n_chan][n_t]); the output is, per beam in order,

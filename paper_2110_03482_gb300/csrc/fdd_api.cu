@@ -70,6 +70,12 @@ struct fdd_plan_s {
   unsigned win_next = 0, blk_next = 0;
   bool win_used[2] = {false, false}, blk_used[2] = {false, false};
   void* blk_release[2] = {nullptr, nullptr};  // a sink's event per block slot
+  // Borrowed workspace (plans made by a tensor-core batch, which run one
+  // after another on one stream): per-call buffers come from [arena, arena +
+  // arena_bytes), bumped from its start; constants stay in the plan's own
+  // allocations.
+  char* arena = nullptr;
+  size_t arena_bytes = 0, arena_used = 0;
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t win_free[2] = {}, win_full[2] = {}, blk_free[2] = {}, blk_done[2] = {};
   cudaEvent_t pipe_start = nullptr, pipe_end = nullptr;
@@ -470,7 +476,9 @@ void release(fdd_plan_s* P) {
                   P->d_win[0], P->d_win[1], P->d_blk[0], P->d_blk[1], P->d_tcx, P->d_shift,
                   P->d_shift_base, P->d_tdd_x};
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q && !(P->arena && static_cast<char*>(q) >= P->arena &&
+               static_cast<char*>(q) < P->arena + P->arena_bytes))
+      cudaFree(q);
   for (cudaEvent_t e : P->prof_ev)
     if (e) cudaEventDestroy(e);
   cudaEvent_t pipe[] = {P->win_free[0], P->win_free[1], P->win_full[0], P->win_full[1],
@@ -502,6 +510,20 @@ fdd_status dev_alloc(fdd_plan_s* P, void** ptr, size_t bytes) {
     return fail(FDD_ERR_ALLOC, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
   }
   P->bytes_held += bytes;
+  return FDD_OK;
+}
+
+// A per-call buffer: from the borrowed workspace when the plan has one.
+fdd_status ws_alloc(fdd_plan_s* P, void** ptr, size_t bytes) {
+  if (!P->arena) return dev_alloc(P, ptr, bytes);
+  const size_t at = (P->arena_used + 255) / 256 * 256;
+  if (at + bytes > P->arena_bytes) {
+    *ptr = nullptr;
+    return fail(FDD_ERR_ALLOC, "borrowed workspace of %zu bytes too small (%zu more needed)",
+                P->arena_bytes, at + bytes - P->arena_bytes);
+  }
+  *ptr = P->arena + at;
+  P->arena_used = at + bytes;
   return FDD_OK;
 }
 
@@ -994,9 +1016,9 @@ fdd_status make_rings(fdd_plan_s* P, bool host) {
   const size_t esz = p.in_dtype == FDD_IN_U8 ? 1 : 4;
   for (int w = 0; w < 2; ++w) {
     if (!P->d_win[w] &&
-        (st = dev_alloc(P, &P->d_win[w], esz * static_cast<size_t>(p.n_chan) * g.fft_len)))
+        (st = ws_alloc(P, &P->d_win[w], esz * static_cast<size_t>(p.n_chan) * g.fft_len)))
       return st;
-    if (!P->d_blk[w] && (st = dev_alloc(P, &P->d_blk[w], P->blk_bytes))) return st;
+    if (!P->d_blk[w] && (st = ws_alloc(P, &P->d_blk[w], P->blk_bytes))) return st;
   }
   cudaEvent_t* evs[] = {&P->win_free[0], &P->win_free[1], &P->win_full[0], &P->win_full[1],
                         &P->blk_free[0], &P->blk_free[1], &P->blk_done[0], &P->blk_done[1],
@@ -1067,11 +1089,32 @@ fdd_status fdd_plan_geometry(const fdd_params* p, fdd_info* out) {
 }
 
 fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
+  return fdd::plan_create(p, nullptr, 0, out);
+}
+
+}  // extern "C"
+
+namespace fdd {
+
+fdd_status plan_drain(fdd_plan_t P, cudaStream_t s) {
+  for (int k = 0; k < 2; ++k) {
+    if (!P->blk_release[k]) continue;
+    FDD_CUDA(cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(P->blk_release[k]), 0));
+    P->blk_release[k] = nullptr;
+  }
+  return FDD_OK;
+}
+
+size_t plan_arena_used(fdd_plan_t P) { return P->arena_used; }
+
+fdd_status plan_create(const fdd_params* p, void* arena, size_t arena_bytes, fdd_plan_t* out) {
   if (!out) return fail(FDD_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   fdd_plan_s* P = new (std::nothrow) fdd_plan_s();
   if (!P) return fail(FDD_ERR_ALLOC, "host allocation failed");
   std::unique_ptr<fdd_plan_s, void (*)(fdd_plan_s*)> guard(P, release);
+  P->arena = static_cast<char*>(arena);
+  P->arena_bytes = arena ? arena_bytes : 0;
 
   fdd_status st = compute_plan(p, &P->info, &P->core);
   if (st != FDD_OK) return st;
@@ -1105,29 +1148,29 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_pc), sizeof(fdd::PhaseConst) * nc)))
     return st;
   if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_status), 256))) return st;
-  if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_xw), sizeof(float) * size_t(nc) * g.fft_len)))
+  if ((st = ws_alloc(P, reinterpret_cast<void**>(&P->d_xw), sizeof(float) * size_t(nc) * g.fft_len)))
     return st;
   const size_t sets = P->tc ? static_cast<size_t>(p->n_beams) : 1;
   if (P->tc) {
     P->tcx_bytes = fdd::mac_tc_scratch_bytes(p->n_beams, nc, p->n_dm, g.n_bins);
-    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_tcx), P->tcx_bytes))) return st;
+    if ((st = ws_alloc(P, reinterpret_cast<void**>(&P->d_tcx), P->tcx_bytes))) return st;
   }
-  if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_X),
-                      sizeof(float2) * size_t(nc) * g.bin_pitch * sets)))
+  if ((st = ws_alloc(P, reinterpret_cast<void**>(&P->d_X),
+                     sizeof(float2) * size_t(nc) * g.bin_pitch * sets)))
     return st;
-  if (P->tc && (st = dev_alloc(P, reinterpret_cast<void**>(&P->d_xb),
-                               sizeof(float2) * size_t(nc) * g.bin_pitch)))
+  if (P->tc && (st = ws_alloc(P, reinterpret_cast<void**>(&P->d_xb),
+                              sizeof(float2) * size_t(nc) * g.bin_pitch)))
     return st;
   if (P->tc && p->output == FDD_OUT_TIME &&
-      (st = dev_alloc(P, reinterpret_cast<void**>(&P->d_Yb),
-                      sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch)))
+      (st = ws_alloc(P, reinterpret_cast<void**>(&P->d_Yb),
+                     sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch)))
     return st;
   if (p->output == FDD_OUT_TIME) {
-    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_Y),
-                        sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch * sets)))
+    if ((st = ws_alloc(P, reinterpret_cast<void**>(&P->d_Y),
+                       sizeof(float2) * size_t(g.dm_batch) * g.bin_pitch * sets)))
       return st;
-    if ((st = dev_alloc(P, reinterpret_cast<void**>(&P->d_yt),
-                        sizeof(float) * size_t(g.dm_batch) * (g.fft_len / g.downsample))))
+    if ((st = ws_alloc(P, reinterpret_cast<void**>(&P->d_yt),
+                       sizeof(float) * size_t(g.dm_batch) * (g.fft_len / g.downsample))))
       return st;
   }
   FDD_CUDA(cudaMemcpy(P->d_pc, P->pc_host.data(), sizeof(fdd::PhaseConst) * nc,
@@ -1146,7 +1189,7 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
     FDD_CUDA(cudaMemcpy(P->d_pc_spin, pcs.data(), sizeof(fdd::PhaseConst) * nc,
                         cudaMemcpyHostToDevice));
     P->spin_scratch_bytes = fdd::spin_scratch_bytes(P->spin, nc, g.n_bins);
-    if ((st = dev_alloc(P, &P->d_spin_scratch, P->spin_scratch_bytes))) return st;
+    if ((st = ws_alloc(P, &P->d_spin_scratch, P->spin_scratch_bytes))) return st;
     P->spin_fp32_variant = fdd::mac_variant_for(p->n_dm);
     if (fdd::mac_smem_bytes(P->spin_fp32_variant, nc) > kMaxSmem)
       return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
@@ -1187,7 +1230,7 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   size_t w = w_r2c > w_c2r ? w_r2c : w_c2r;
   w = w > w_tail ? w : w_tail;
   if (w > 0) {
-    if ((st = dev_alloc(P, &P->d_fftwork, w))) return st;
+    if ((st = ws_alloc(P, &P->d_fftwork, w))) return st;
     FDD_CUFFT(cufftSetWorkArea(P->r2c, P->d_fftwork));
     if (P->has_c2r) FDD_CUFFT(cufftSetWorkArea(P->c2r, P->d_fftwork));
     if (P->has_c2r_tail) FDD_CUFFT(cufftSetWorkArea(P->c2r_tail, P->d_fftwork));
@@ -1201,6 +1244,10 @@ fdd_status fdd_plan(const fdd_params* p, fdd_plan_t* out) {
   *out = guard.release();
   return FDD_OK;
 }
+
+}  // namespace fdd
+
+extern "C" {
 
 fdd_status fdd_query(fdd_plan_t plan, fdd_info* out) {
   if (!plan || !out) return fail(FDD_ERR_INVALID_ARG, "NULL plan or info");

@@ -91,6 +91,10 @@ struct fdd_batch_s {
   };
   bool tc = false;
   std::vector<TcGroup> tc_groups;
+  // plans whose workspaces exceed the limit together share one block of the
+  // largest one's size for their per-call buffers (run one after another)
+  void* tc_arena = nullptr;
+  cudaEvent_t tc_ready = nullptr;  // recorded before each plan of a shared block
   // CUDA graph of the whole execute, for the buffers it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -120,6 +124,8 @@ void release(fdd_batch_s* B) {
   if (!B) return;
   for (auto& g : B->tc_groups)
     if (g.plan) fdd_destroy(g.plan);
+  if (B->tc_arena) cudaFree(B->tc_arena);
+  if (B->tc_ready) cudaEventDestroy(B->tc_ready);
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   for (auto& kv : B->r2c) cufftDestroy(kv.second);
@@ -258,6 +264,7 @@ struct TcCtx {
   fdd_sink_fn sink;
   void* sink_user;
   fdd_status inner = FDD_OK;  // a callback's own failure
+  void* arena_ready = nullptr;  // shared block: recorded before this plan's work
 };
 
 fdd_status tc_source(void* user, int32_t beam, int64_t t_begin, int64_t n, void* d_window,
@@ -298,6 +305,8 @@ fdd_status tc_source(void* user, int32_t beam, int64_t t_begin, int64_t n, void*
     }
     return FDD_OK;
   }
+  // (a window in a shared block may still hold an earlier plan's buffers)
+  if (!ready) ready = x->arena_ready;
   const fdd_status st = x->source(x->source_user, bm, t_begin, nb, d_window, ready, stream);
   if (st != FDD_OK) x->inner = st;
   return st;
@@ -348,8 +357,14 @@ fdd_status run_tc_batch(fdd_batch_s* B, TcCtx ctx, cudaStream_t s) {
     fdd_status st;
     if (!plan && (st = fdd_plan(&g.q, &plan)) != FDD_OK) return st;
     ctx.g = &g;
+    if (B->tc_arena) {
+      B_CUDA(cudaEventRecord(B->tc_ready, s));
+      ctx.arena_ready = B->tc_ready;
+    }
     st = fdd_execute_stream(plan, nullptr, tc_source, &ctx, tc_sink, &ctx,
                             reinterpret_cast<fdd_stream_t>(s));
+    // the next plan of a shared block starts after the sink's reads of this one's blocks
+    if (st == FDD_OK && B->tc_arena) st = fdd::plan_drain(plan, s);
     if (!g.plan) {
       fdd_info gi;
       if (st == FDD_OK && fdd_query(plan, &gi) == FDD_ERR_TIMEOUT) B->tc_status = FDD_ERR_TIMEOUT;
@@ -363,6 +378,7 @@ fdd_status run_tc_batch(fdd_batch_s* B, TcCtx ctx, cudaStream_t s) {
 
 // Groups and plans of the tensor-core form.
 fdd_status plan_tc_groups(fdd_batch_s* B, const fdd_params* p) {
+  using fdd::report_error;
   // key: (transform length, chunk length, trial count for chunked beams,
   // dm0, ddm); whole-series beams of one length share a group whatever
   // their trial counts and lengths (the group runs to its largest)
@@ -373,44 +389,60 @@ fdd_status plan_tc_groups(fdd_batch_s* B, const fdd_params* p) {
         .push_back(static_cast<int>(b));
   }
   constexpr int kGroup = 16;  // beams per plan (the 16-beam tensor-core groups)
+  const size_t limit = p->workspace_limit ? p->workspace_limit : (size_t(16) << 30);
+  auto with_margin = [](size_t bytes) { return bytes + bytes / 16 + (size_t(256) << 20); };
+  // a plan of beams v[i0 .. i0 + n - 1] and the device bytes it would hold
+  // with its streaming rings
+  auto make_group = [&](const std::vector<int>& v, size_t i0, size_t n,
+                        fdd_batch_s::TcGroup* g, size_t* bytes) -> fdd_status {
+    g->beams.assign(v.begin() + i0, v.begin() + i0 + n);
+    int64_t n_t = 0;
+    int n_dm = 0;
+    for (int b : g->beams) {
+      n_t = std::max(n_t, B->beams[b].n_t);
+      n_dm = std::max(n_dm, B->beams[b].n_dm);
+    }
+    const fdd_beam_desc& d0 = B->beams[g->beams[0]];
+    g->dms.resize(n_dm);
+    for (int j = 0; j < n_dm; ++j) g->dms[j] = d0.dm0 + d0.ddm * j;
+    g->q = *p;
+    g->q.n_t = n_t;
+    g->q.n_beams = static_cast<int32_t>(g->beams.size());
+    g->q.dm_list = g->dms.data();
+    g->q.n_dm = n_dm;
+    g->q.chunk_len = d0.chunk_len;
+    g->q.mac_variant = 0;
+    fdd_info gi;
+    const fdd_status st = fdd_plan_geometry(&g->q, &gi);
+    *bytes = st == FDD_OK ? static_cast<size_t>(gi.workspace_bytes + gi.stream_bytes) : 0;
+    return st;
+  };
+  size_t need = 0;
   for (auto& kv : keyed) {
     std::vector<int>& v = kv.second;
     std::stable_sort(v.begin(), v.end(), [&](int a, int c) {
       return B->beams[a].n_dm != B->beams[c].n_dm ? B->beams[a].n_dm > B->beams[c].n_dm
                                                   : B->beams[a].n_t > B->beams[c].n_t;
     });
-    for (size_t i0 = 0; i0 < v.size(); i0 += kGroup) {
+    for (size_t i0 = 0; i0 < v.size();) {
+      // up to 16 beams, fewer while the plan (with a margin for its FFT work
+      // area, which the estimate leaves out) would exceed the limit alone
+      size_t n = std::min<size_t>(kGroup, v.size() - i0), bytes = 0;
       fdd_batch_s::TcGroup g;
-      g.beams.assign(v.begin() + i0, v.begin() + std::min(v.size(), i0 + kGroup));
-      int64_t n_t = 0;
-      int n_dm = 0;
-      for (int b : g.beams) {
-        n_t = std::max(n_t, B->beams[b].n_t);
-        n_dm = std::max(n_dm, B->beams[b].n_dm);
-      }
-      const fdd_beam_desc& d0 = B->beams[g.beams[0]];
-      g.dms.resize(n_dm);
-      for (int j = 0; j < n_dm; ++j) g.dms[j] = d0.dm0 + d0.ddm * j;
-      g.q = *p;
-      g.q.n_t = n_t;
-      g.q.n_beams = static_cast<int32_t>(g.beams.size());
-      g.q.dm_list = g.dms.data();
-      g.q.n_dm = n_dm;
-      g.q.chunk_len = d0.chunk_len;
-      g.q.mac_variant = 0;
+      fdd_status st = make_group(v, i0, n, &g, &bytes);
+      while ((st != FDD_OK || with_margin(bytes) > limit) && n > 1)
+        st = make_group(v, i0, --n, &g, &bytes);
+      if (st != FDD_OK) return st;
+      if (bytes > limit)
+        return report_error(FDD_ERR_INVALID_ARG,
+                            "workspace_limit too small for one beam's tensor-core plan");
+      need += bytes;
       B->tc_groups.push_back(std::move(g));
+      i0 += n;
     }
   }
   for (auto& g : B->tc_groups) g.q.dm_list = g.dms.data();  // after the moves
-  // keep every plan when their workspaces fit the limit together
-  const size_t limit = p->workspace_limit ? p->workspace_limit : (size_t(16) << 30);
-  size_t need = 0;
-  for (auto& g : B->tc_groups) {
-    fdd_info gi;
-    fdd_status st = fdd_plan_geometry(&g.q, &gi);
-    if (st != FDD_OK) return st;
-    need += static_cast<size_t>(gi.workspace_bytes + gi.stream_bytes);
-  }
+  // keep every plan with its own workspace when they fit the limit together
   if (need <= limit) {
     for (auto& g : B->tc_groups) {
       fdd_status st = fdd_plan(&g.q, &g.plan);
@@ -419,6 +451,59 @@ fdd_status plan_tc_groups(fdd_batch_s* B, const fdd_params* p) {
       fdd_query(g.plan, &gi);
       B->bytes_held += static_cast<size_t>(gi.workspace_bytes + gi.stream_bytes);
     }
+    return FDD_OK;
+  }
+  // else one shared block for the per-call buffers, sized to the largest
+  // plan (estimated; the whole limit if that proves short)
+  size_t big = 0;
+  for (auto& g : B->tc_groups) {
+    fdd_info gi;
+    fdd_plan_geometry(&g.q, &gi);
+    big = std::max(big, static_cast<size_t>(gi.workspace_bytes + gi.stream_bytes));
+  }
+  size_t a = std::min(limit, with_margin(big));
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    fdd_status st = alloc(B, &B->tc_arena, a);
+    bool short_block = false;
+    for (size_t i = 0; st == FDD_OK && i < B->tc_groups.size(); ++i) {
+      auto& g = B->tc_groups[i];
+      st = fdd::plan_create(&g.q, B->tc_arena, a, &g.plan);
+      if (st == FDD_OK) {
+        fdd_info gi;
+        fdd_query(g.plan, &gi);
+        // the streaming rings come from the block at the first streamed call
+        if (fdd::plan_arena_used(g.plan) + 1024 + static_cast<size_t>(gi.stream_bytes) > a)
+          st = report_error(FDD_ERR_ALLOC, "shared workspace too small for the streaming rings");
+      }
+      short_block = st == FDD_ERR_ALLOC;
+    }
+    if (st == FDD_OK) {
+      for (auto& g : B->tc_groups) {  // the plans' own (constant) allocations
+        fdd_info gi;
+        fdd_query(g.plan, &gi);
+        B->bytes_held += static_cast<size_t>(gi.workspace_bytes);
+      }
+      break;
+    }
+    for (auto& g : B->tc_groups)
+      if (g.plan) {
+        fdd_destroy(g.plan);
+        g.plan = nullptr;
+      }
+    cudaFree(B->tc_arena);
+    B->bytes_held -= a;
+    B->tc_arena = nullptr;
+    if (!short_block || a >= limit || attempt == 1) {
+      // no shared block: each execute makes each plan for its turn
+      if (st != FDD_ERR_ALLOC) return st;
+      cudaGetLastError();
+      return FDD_OK;
+    }
+    a = limit;
+  }
+  if (cudaEventCreateWithFlags(&B->tc_ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return report_error(FDD_ERR_CUDA, "event creation failed");
   }
   return FDD_OK;
 }

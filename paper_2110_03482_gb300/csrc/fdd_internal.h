@@ -167,6 +167,18 @@ cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s);
 // form's per-bin maxima: no scratch, one launch.
 cudaError_t launch_mac_tc_direct(const MacArgs& a, int precision, int n_sms, cudaStream_t s);
 
+// A plan whose per-call buffers (spectra, scratch, transform staging, FFT
+// work area, streaming rings) are taken from a caller's device block
+// [arena, arena + arena_bytes) instead of its own allocations (arena NULL:
+// fdd_plan).  Plans sharing one block must run one after another on one
+// stream, each drained (plan_drain) before the next starts.
+fdd_status plan_create(const fdd_params* p, void* arena, size_t arena_bytes, fdd_plan_t* out);
+// Bytes of the borrowed block in use (after the first streamed call: with
+// its rings).
+size_t plan_arena_used(fdd_plan_t plan);
+// Make stream s wait for the sink release events the plan still holds.
+fdd_status plan_drain(fdd_plan_t plan, cudaStream_t s);
+
 // Spin-frequency-dependent DM grids (fdd_spin.cu; Sect. 2.3, Eqs. 8 and 9).
 struct SpinGeometry {
   int G;             // bins per group (16 or 32)

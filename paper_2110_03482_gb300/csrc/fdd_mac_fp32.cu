@@ -1034,16 +1034,19 @@ __global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
     __syncthreads();  // phase table ready; item_s read by every thread
     const long long local = item - bs.item_begin;
     const long long n_full = static_cast<long long>(bs.n_bin_tiles) * bs.n_dm_blocks;
+    // the set's arguments as a local copy: the item's loops then keep what
+    // they use in registers instead of re-reading the set after each store
+    const MacArgs args = bs.args;
     if (local < n_full)
-      g3_body<kCh, kStages>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
+      g3_body<kCh, kStages>(args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
                             static_cast<int>(local / bs.n_dm_blocks),
                             static_cast<int>(local % bs.n_dm_blocks), 0, it0);
     else if (bs.wide_trials == 512)
-      g3_wide_body<kCh, kStages, 16>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty,
+      g3_wide_body<kCh, kStages, 16>(args, sm.pcs, sm.stages, sm.full, sm.empty,
                                      sm.abort_flag, static_cast<int>(local - n_full), bs.j_wide,
                                      0, it0);
     else
-      g3_wide_body<kCh, kStages, 32>(bs.args, sm.pcs, sm.stages, sm.full, sm.empty,
+      g3_wide_body<kCh, kStages, 32>(args, sm.pcs, sm.stages, sm.full, sm.empty,
                                      sm.abort_flag, static_cast<int>(local - n_full), bs.j_wide,
                                      0, it0);
     it0 += n_iter;

@@ -325,8 +325,11 @@ def test_tensor_core_batch_matches_oracle(output):
         batch.execute_stream(source, sink, torch.cuda.current_stream())
         torch.cuda.synchronize()
         assert torch.equal(got, out)
-    # plans made for each execute (a limit below their sum, above each one's
-    # least workspace; their trial blocks may differ)
+    # a limit below the plans' sum, above each one's least workspace: the
+    # plans share one block for their per-call buffers (their trial blocks
+    # may differ); twice, the second call reusing the block
     with fdd.Batch(TC_BEAMS, workspace_limit=held // 2, **kw) as batch:
-        assert batch.info["workspace_bytes"] == 0
-        _tc_check(batch, _tc_batch_run(batch, d_in, output), refs, output)
+        assert 0 < batch.info["workspace_bytes"] < held
+        first = _tc_batch_run(batch, d_in, output)
+        _tc_check(batch, first, refs, output)
+        assert torch.equal(_tc_batch_run(batch, d_in, output), first)

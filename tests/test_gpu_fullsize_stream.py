@@ -145,3 +145,77 @@ def test_16beam_full_size_power_streamed_sampled():
                 err = rel_l2(p, ref[q])
                 print(f"16 beams, 4096 ch: beam {b} chunk {c} trial {j}: power rel-L2 {err:.2e}")
                 assert err <= 2 * TC_REL_L2, (b, c, j, err)
+
+
+@pytest.mark.parametrize("precision", [fdd.FDD_PREC_FP32, fdd.FDD_PREC_FP16], ids=["fp32", "fp16"])
+def test_96beam_full_size_batch_streamed_sampled(precision):
+    """The 96-beam batch at its full lengths (n_t up to ~2^20, 1536 channels,
+    512-4096 trials, |Y|^2), streamed as the benchmark runs it (every beam's
+    windows generated on the device, output blocks to a sink), in the FP32
+    form (persistent launch per wave) and on tensor cores (groups of beams
+    sharing their phasors): sampled bins of the longest, shortest, most- and
+    fewest-trial beams at four trials each, against the oracle."""
+    torch.cuda.empty_cache()
+    bw = synth.BATCH_WORKLOADS["fdd_96beam_1536ch_uneven"]
+    beams = bw.beams(SEED)
+    n_ts = np.array([b[0] for b in beams])
+    n_dms = np.array([b[3] for b in beams])
+    checked = sorted({int(np.argmin(n_ts)), int(np.argmax(n_ts)), int(np.argmax(n_dms)),
+                      int(np.argmin(n_dms))})
+    gen = synth.gpu.BeamWindows([synth.batch_beam_args(bw, desc, SEED, b)[0]
+                                 for b, desc in enumerate(beams)])
+    common = dict(n_chan=bw.n_chan, nu_lo_mhz=bw.nu_lo_mhz, dnu_mhz=bw.dnu_mhz,
+                  t_samp_s=bw.t_samp_s, in_dtype=fdd.FDD_IN_F32, chunk_len=0,
+                  output=fdd.FDD_OUT_POWER, precision=precision,
+                  workspace_limit=(200 << 30) if precision != fdd.FDD_PREC_FP32 else (100 << 30))
+    rng = np.random.default_rng(7)
+    picks = {}
+    for b in checked:
+        K = oracle.next_pow2(beams[b][0]) // 2 + 1
+        bins = np.unique(np.concatenate([[0, 1, K - 1], rng.integers(2, K - 1, 5)]))
+        trials = sorted({0, beams[b][3] // 2, beams[b][3] - 1, int(rng.integers(1, beams[b][3]))})
+        picks[b] = (K, bins, trials)
+    got = {}
+    with fdd.Batch(beams, autotune=False, **common) as batch:
+
+        def source(beam, t0, n, d_window, ready, s):
+            gen.fill(beam, d_window, t0, n, s)
+
+        def sink(blk, s):
+            b = blk["beam_first"]
+            if b not in picks:
+                return None
+            K, bins, trials = picks[b]
+            for j in trials:
+                r = j - blk["dm_first"]
+                if 0 <= r < blk["n_dm"]:
+                    row = torch.empty(K, dtype=torch.float32, device="cuda")
+                    fdd.memcpy_async(row.data_ptr(), blk["d_data"] + 4 * r * blk["row_pitch"],
+                                     4 * K, s)
+                    got[(b, j)] = row
+            return None
+
+        batch.execute_stream(source, sink, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        info = batch.info
+    torch.cuda.empty_cache()
+    assert len(got) == sum(len(p[2]) for p in picks.values())
+    errs = []
+    for b in checked:
+        n_t, dm0, ddm, n_dm = beams[b]
+        K, bins, trials = picks[b]
+        L = 2 * (K - 1)
+        x = np.zeros((bw.n_chan, L))
+        x[:, :n_t] = _host_rows(gen, b, 0, n_t, bw.n_chan).T
+        X = oracle.fft_r2c(x)[:, bins]
+        d = oracle.delays(bw.nu_lo_mhz + bw.dnu_mhz * np.arange(bw.n_chan),
+                          dm0 + ddm * np.array(trials, dtype=np.float64), bw.t_samp_s)
+        ref = np.abs(oracle.fdd_bins(X, bins, L, d)) ** 2
+        for q, j in enumerate(trials):
+            p = got[(b, j)].cpu().numpy().astype(np.float64)[bins]
+            errs.append(rel_l2(p, ref[q]))
+    tol = 2 * (1e-5 if precision == fdd.FDD_PREC_FP32 else TC_REL_L2)
+    print(f"96 uneven beams at full length ({'TC' if info['mac_variant'] == fdd.FDD_MAC_TC else 'FP32'}"
+          f", {info['n_waves']} waves/plans): power rel-L2 vs FP64 max {max(errs):.2e} "
+          f"over beams {checked}")
+    assert max(errs) <= tol
