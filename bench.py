@@ -43,7 +43,7 @@ UNIT = "phasor-MAC/s"
 DEFAULT_WORKLOAD = "fdd_1024ch_2p20t_2048dm"
 FLOPS_PER_MAC = 8
 MAC_SOURCE = os.path.join(ROOT, "paper_2110_03482_gb300", "csrc", "fdd_mac_fp32.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "mac_fp32_survey_1024ch_2048dm.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "mac_g12_survey_1024ch_2048dm.md")
 
 
 def parse_args():
@@ -1135,7 +1135,9 @@ def run_batch(args) -> None:
         common.update(workspace_limit=int(min(args.workspace_gib, 100.0) * (1 << 30)))
     gen_kw = [synth.batch_beam_args(bw, desc, args.seed, b)[0] for b, desc in enumerate(beams)]
     t0 = time.perf_counter()
-    with fdd.Batch(beams, autotune=True, **common) as batch:
+    # (--mac-variant pins the FP32 tile and skips the autotuner)
+    with fdd.Batch(beams, autotune=not args.mac_variant, mac_variant=args.mac_variant,
+                   **common) as batch:
         plan_s = time.perf_counter() - t0
         info = batch.info
         in_bytes = 4 * info["in_elems"]

@@ -737,8 +737,13 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
         const int n_dm = B->beams[b].n_dm;
         const int full = n_dm / dms, rem = n_dm % dms;
         const bool tail = tails && rem > 0 && rem <= dms / 2;
-        const bool wide = variant == FDD_MAC_G12_4X8 && rem > 0 && rem <= dms / 2;
-        const int blocks = full + (rem > 0 && !tail && !wide ? 1 : 0);
+        // the three-product tile's last trials as wide items: up to 512 one
+        // 512-trial item, up to 1024 one 1024-trial item, up to 1536 both
+        // (cheaper than a full block at the measured rates), else a full block
+        const bool g12 = variant == FDD_MAC_G12_4X8;
+        const bool wide = g12 && rem > dms / 4 && rem <= 3 * dms / 4;
+        const bool narrow = g12 && rem > 0 && (rem <= dms / 4 || (rem > dms / 2 && rem <= 3 * dms / 4));
+        const int blocks = full + (rem > 0 && !tail && !wide && !narrow ? 1 : 0);
         for (int64_t c = 0; c < B->n_chunks[b]; ++c) {
           fdd::BatchSet bs{};
           bs.args = base_args(b, c);
@@ -747,15 +752,16 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
           bs.n_bin_tiles = static_cast<int>((B->n_bins[b] + bins_per_cta - 1) / bins_per_cta);
           bs.n_dm_blocks = blocks;
           bs.item_begin = items;
-          // the last block as wide items: 2x the bins and 1024 trials, or
-          // 4x the bins and 512
-          const int wf = rem <= dms / 4 ? 4 : 2;
-          bs.n_wide_tiles = wide ? static_cast<int>((B->n_bins[b] + wf * bins_per_cta - 1) /
-                                                    (wf * bins_per_cta))
+          bs.n_wide_tiles = wide ? static_cast<int>((B->n_bins[b] + 2 * bins_per_cta - 1) /
+                                                    (2 * bins_per_cta))
                                  : 0;
           bs.j_wide = full * dms;
-          bs.wide_trials = dms / wf;
-          items += static_cast<long long>(bs.n_bin_tiles) * blocks + bs.n_wide_tiles;
+          bs.n_narrow_tiles = narrow ? static_cast<int>((B->n_bins[b] + 4 * bins_per_cta - 1) /
+                                                        (4 * bins_per_cta))
+                                     : 0;
+          bs.j_narrow = full * dms + (wide ? dms / 2 : 0);
+          items += static_cast<long long>(bs.n_bin_tiles) * blocks + bs.n_wide_tiles +
+                   bs.n_narrow_tiles;
           wv.h_sets.push_back(bs);
           wv.set_beam.push_back(b);
           wv.set_chunk.push_back(static_cast<int>(c));

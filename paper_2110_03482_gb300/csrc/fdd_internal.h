@@ -69,12 +69,13 @@ struct BatchSet {
   long long item_begin;  // first work item of this set
   int n_dm_blocks;       // trial blocks (items per bin tile)
   int n_bin_tiles;
-  // the three-product tile only: wide items (twice or four times the bins,
-  // wide_trials = 1024 or 512 trials from trial j_wide) numbered after the
-  // n_bin_tiles x n_dm_blocks ones
+  // the three-product tile only, numbered after the n_bin_tiles x
+  // n_dm_blocks items: wide items of 1024 trials (twice the bins) from trial
+  // j_wide, then wide items of 512 trials (four times the bins) from j_narrow
   int n_wide_tiles;
   int j_wide;
-  int wide_trials;
+  int n_narrow_tiles;
+  int j_narrow;
 };
 
 int mac_variant_for(int n_dm);

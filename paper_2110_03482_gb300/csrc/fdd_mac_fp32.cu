@@ -1041,14 +1041,15 @@ __global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
       g3_body<kCh, kStages>(args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
                             static_cast<int>(local / bs.n_dm_blocks),
                             static_cast<int>(local % bs.n_dm_blocks), 0, it0);
-    else if (bs.wide_trials == 512)
-      g3_wide_body<kCh, kStages, 16>(args, sm.pcs, sm.stages, sm.full, sm.empty,
-                                     sm.abort_flag, static_cast<int>(local - n_full), bs.j_wide,
-                                     0, it0);
-    else
+    else if (local < n_full + bs.n_wide_tiles)
       g3_wide_body<kCh, kStages, 32>(args, sm.pcs, sm.stages, sm.full, sm.empty,
                                      sm.abort_flag, static_cast<int>(local - n_full), bs.j_wide,
                                      0, it0);
+    else
+      g3_wide_body<kCh, kStages, 16>(args, sm.pcs, sm.stages, sm.full, sm.empty,
+                                     sm.abort_flag,
+                                     static_cast<int>(local - n_full - bs.n_wide_tiles),
+                                     bs.j_narrow, 0, it0);
     it0 += n_iter;
   }
 }

@@ -143,9 +143,10 @@ def test_batch_autotune_picks_a_timed_candidate():
 
 
 # (n_t, dm0, ddm, n_dm, chunk_len): beams in overlap-save chunks of their own
-# lengths next to a whole-series beam (largest delays 131, 34, 533 and 607
-# samples), chunk counts 4, 1, 3 and 1
-CHUNKED = [(3000, 0.0, 1.0, 130, 1024), (1000, 2.0, 0.5, 64, 0), (5000, 0.0, 0.25, 2100, 2048),
+# lengths next to a whole-series beam (largest delays 132, 34, 533 and 607
+# samples), chunk counts 4, 1, 3 and 1; the first beam's 1300 trials end in
+# a 1024-trial and a 512-trial wide item of the G12 tile
+CHUNKED = [(3000, 0.0, 0.1, 1300, 1024), (1000, 2.0, 0.5, 64, 0), (5000, 0.0, 0.25, 2100, 2048),
            (700, 0.0, 2.0, 300, 1024)]
 
 
