@@ -89,8 +89,12 @@ def test_stream_equals_device_execute(output, layout, n_beams, precision, n_dm, 
     if layout == fdd.FDD_LAYOUT_CHAN_MAJOR:
         fbs = [np.ascontiguousarray(f.T) for f in fbs]
     d_in = torch.from_numpy(np.ascontiguousarray(np.stack(fbs))).cuda()
+    # (FP32 under a limit: the 128-trial tile, whose blocks the limit splits
+    # into several; the default tile's blocks are 2048 trials)
+    tile = dict(mac_variant=fdd.FDD_MAC_Q_4X4 + 1) if precision == fdd.FDD_PREC_FP32 and limit \
+        else {}
     with fdd.Plan(**params_for(w, in_layout=layout, precision=precision,
-                               workspace_limit=limit)) as plan:
+                               workspace_limit=limit, **tile)) as plan:
         info = plan.info
         assert info["n_chunks"] >= 3
         shape = (info["out_elems"], 2) if output == "spectra" else (info["out_elems"],)
