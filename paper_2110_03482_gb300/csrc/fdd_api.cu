@@ -412,7 +412,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   }
   const bool tc = p->precision != FDD_PREC_FP32;
   g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
-                                                     : fdd::mac_variant_for(p->n_dm));
+                                                     : fdd::mac_variant_for(p->n_dm, nc));
   if (!tc && fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
     return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
 
@@ -1190,7 +1190,7 @@ fdd_status plan_create(const fdd_params* p, void* arena, size_t arena_bytes, fdd
                         cudaMemcpyHostToDevice));
     P->spin_scratch_bytes = fdd::spin_scratch_bytes(P->spin, nc, g.n_bins);
     if ((st = ws_alloc(P, &P->d_spin_scratch, P->spin_scratch_bytes))) return st;
-    P->spin_fp32_variant = fdd::mac_variant_for(p->n_dm);
+    P->spin_fp32_variant = fdd::mac_variant_for(p->n_dm, nc);
     if (fdd::mac_smem_bytes(P->spin_fp32_variant, nc) > kMaxSmem)
       return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
     FDD_CUDA(fdd::mac_prepare(P->spin_fp32_variant, nc));

@@ -805,6 +805,14 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     }
   }
 
+  auto tile_fits = [&](int v) {
+    if (fdd::mac_smem_bytes(v, p->n_chan) > 227 * 1024) return false;
+    if (fdd::mac_prepare(v, p->n_chan) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return fdd::mac_batch_ctas_per_sm(v, p->n_chan) >= 1;
+  };
   auto use_variant = [&](int v) -> fdd_status {
     B->variant = v;
     B_CUDA(fdd::mac_prepare(v, p->n_chan));
@@ -837,6 +845,7 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     double best = std::numeric_limits<double>::infinity();
     fdd_status tst = FDD_OK;
     for (int v : cands) {
+      if (!tile_fits(v)) continue;  // its shared memory does not hold the phase table
       if ((tst = use_variant(v))) break;
       // output of wave 0 into the scratch, laid out like the real output
       auto& w0m = B->waves[0];
@@ -880,7 +889,8 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     if (tst != FDD_OK) return tst;
     cache_store(key, variant);
   }
-  if (variant < 0) variant = FDD_MAC_G12_4X8;
+  if (variant < 0)  // G12, unless the channels' phase table leaves it no room
+    variant = tile_fits(FDD_MAC_G12_4X8) ? FDD_MAC_G12_4X8 : FDD_MAC_W12_8X8;
   if ((st = use_variant(variant))) return st;
   B_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
   *out = guard.release();

@@ -78,7 +78,9 @@ struct BatchSet {
   int j_narrow;
 };
 
-int mac_variant_for(int n_dm);
+// The FP32 tile with the least time for n_dm trials among those whose
+// shared memory holds n_chan channels' phase constants.
+int mac_variant_for(int n_dm, int n_chan);
 int mac_variant_bins_per_cta(int variant);
 bool mac_variant_batchable(int variant);
 // CTAs of the persistent batch kernel per SM (occupancy), 0 if unsupported.

@@ -567,7 +567,10 @@ __global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* se
 // accumulators as pairs along b, the sums zr + zi and pr + pi formed in
 // registers after the loads (shared-memory traffic per lane as the
 // four-product form's, two floats per operand): 48 paired FMAs and 6 paired
-// adds per lane and channel for 32 complex MACs.
+// adds per lane and channel for 32 complex MACs.  A stage carries kCh
+// channels (8 in use: against 4, half the barrier round trips per channel
+// and longer independent runs of loads and FMAs; 0.726 of the FP32 peak
+// against 0.661 on the same launch, with 2 or 4 stages within 1 %).
 template <int kCh, int kStages>
 struct G3 {
   static constexpr int kA = 64;                // a's per bin (Z_a)
@@ -1095,7 +1098,7 @@ VariantInfo info_g3() {
 
 VariantInfo variant_info(int v) {
   switch (v) {
-    case MAC_G12_4x8: return info_g3<4, 3>();
+    case MAC_G12_4x8: return info_g3<8, 3>();
     case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, 12>();
     case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>>();
     case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>>();
@@ -1109,24 +1112,25 @@ VariantInfo variant_info(int v) {
 // Default tile for a trial count: the one with the least time for the padded
 // trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
 // measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
-// 131073 bins): G12_4x8 0.661 on full 2048-trial blocks, whose last block
-// runs as 1024-trial wide items at 0.578 (at most 1024 trials) or 512-trial
-// ones at 0.486 (at most 512); Q_4x8 0.493 (1024-trial blocks), Q_8x8_512
+// 131073 bins): G12_4x8 0.726 on full 2048-trial blocks, whose last block
+// runs as 1024-trial wide items at 0.624 (at most 1024 trials) or 512-trial
+// ones at 0.504 (at most 512); Q_4x8 0.493 (1024-trial blocks), Q_8x8_512
 // 0.415 (512), Q_4x4 0.347 (128).  (The four-product warp-specialised tile
 // W12_8x8 measured 0.621 on the same launch, Q12_8x8, the 2048-trial tile on
 // the plain schedule, 0.553.)
-int mac_variant_for(int n_dm) {
+int mac_variant_for(int n_dm, int n_chan) {
   struct Tile {
     int variant, block;
     double rate, wide_rate, narrow_rate;  // > 0: a last block of <= block / 2, / 4
   };
-  static const Tile tiles[] = {{MAC_G12_4x8, 2048, 0.661, 0.578, 0.486},
+  static const Tile tiles[] = {{MAC_G12_4x8, 2048, 0.726, 0.624, 0.504},
                                {MAC_Q_4x8, 1024, 0.493, 0.0, 0.0},
                                {MAC_Q_8x8_512, 512, 0.415, 0.0, 0.0},
                                {MAC_Q_4x4, 128, 0.347, 0.0, 0.0}};
-  int best = MAC_G12_4x8;
+  int best = MAC_W12_8x8;  // (the smallest shared-memory need of the 2048-trial tiles)
   double best_cost = 0.0;
   for (const Tile& t : tiles) {
+    if (mac_smem_bytes(t.variant, n_chan) > 227 * 1024) continue;
     const int full = n_dm / t.block, rem = n_dm % t.block;
     double cost = full * t.block / t.rate;
     if (rem > 0 && t.narrow_rate > 0.0 && rem <= t.block / 4)

@@ -102,10 +102,19 @@ enum TcPrec { kBf16HiLo = 0, kBf16 = 1, kF16 = 2, kF8 = 3 };
 // Instruction descriptor: D FP32, A and B both BF16 (format 1) or both FP16
 // (format 0) under kind::f16, both E4M3 (format 0) under kind::f8f6f4; both
 // K-major, N and M.
+// n: the MMA's N, a multiple of 16 in [16, kN] (a pass's last a's may be
+// fewer than the kN / kBeams of a full pass).
 template <int kPrec>
-__host__ __device__ constexpr uint32_t idesc() {
+__host__ __device__ constexpr uint32_t idesc(int n = kN) {
   return (1u << 4) | ((kPrec == kF16 || kPrec == kF8) ? 0u : ((1u << 7) | (1u << 10))) |
-         (static_cast<uint32_t>(kN >> 3) << 17) | (static_cast<uint32_t>(kM >> 4) << 24);
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(kM >> 4) << 24);
+}
+
+// a's of the pass from trial j_pass: all kNA of a full pass, fewer (whole
+// a's of kM trials) where the trials end within it
+__device__ __forceinline__ int pass_as(int n_dm, int j_pass, int kNA) {
+  const int left = (n_dm - j_pass + kM - 1) / kM;
+  return left < kNA ? left : kNA;
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
@@ -188,17 +197,17 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (
 // elements of 16 bits (kind::f16) or 32 of FP8 E4M3 (kind::f8f6f4).
 template <int kPrec>
 __device__ __forceinline__ void mma16(uint32_t d, uint64_t adesc, uint64_t bdesc,
-                                      uint32_t accum) {
+                                      uint32_t accum, uint32_t id) {
   if constexpr (kPrec == kF8) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-        "l"(adesc), "l"(bdesc), "r"(idesc<kPrec>()), "r"(accum));
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accum));
   } else {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-        "l"(adesc), "l"(bdesc), "r"(idesc<kPrec>()), "r"(accum));
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accum));
   }
 }
 
@@ -274,6 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // N of this pass: its a's times the group's beams
+          const uint32_t id =
+              idesc<kPrec>(pass_as(a.n_dm, (it % n_pass) * kDmsPass, kNA) * kBeams);
           for (int t = 0; t < n_tiles; ++t, ++s) {
             const uint32_t st = s % kStages;
             if (!mbar_wait(&full[st], (s / kStages) & 1, abort_flag)) {
@@ -286,11 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t bd = smem_desc(stage + kBOff + kk * 32);
               const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
-              mma16<kPrec>(tmem, smem_desc(stage + kk * 32), bd, accum);               // re, hi
-              mma16<kPrec>(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum);  // im, hi
+              mma16<kPrec>(tmem, smem_desc(stage + kk * 32), bd, accum, id);               // re, hi
+              mma16<kPrec>(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum, id);  // im, hi
               if (kHiLo) {
-                mma16<kPrec>(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u);       // re, lo
-                mma16<kPrec>(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u);  // im, lo
+                mma16<kPrec>(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u, id);  // re, lo
+                mma16<kPrec>(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u,
+                             id);  // im, lo
               }
             }
             issued = true;
@@ -343,8 +356,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int n_cols = pass_as(a.n_dm, j_pass, kNA) * kBeams;  // columns this pass wrote
 #pragma unroll 1
-        for (int c0 = 0; c0 < kN; c0 += 16) {
+        for (int c0 = 0; c0 < n_cols; c0 += 16) {
           uint32_t re[16], im[16];
           tmem_ld16x2(t_lanes + c0, t_lanes + kN + c0, re, im);
           // the 16 columns share a_in = c0 / kBeams; beams beta0 .. beta0 + 15
@@ -414,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
+        const int n_a = pass_as(a.n_dm, j_pass, kNA);  // a's of this pass
         auto load_pc = [&](int nn) {
           return nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
         };
@@ -522,12 +537,18 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
               const __half2 qbs = __floats2half2_rn(-qb[0].y, qb[0].x);
 #pragma unroll
               for (int m = 0; m < kBeamsPerWarp; ++m) {
-                const __half2 za = __hfma2(xr2[m], qa2, __hmul2(xi2[m], qas));
-                const __half2 zb = __hfma2(xr2[m], qb2, __hmul2(xi2[m], qbs));
-                const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
-                const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
-                *reinterpret_cast<__half2*>(tb + z_base + ra) = za;
-                *reinterpret_cast<__half2*>(tb + z_base + rb) = zb;
+                // (a's beyond the pass's last one are not read by its MMAs)
+                if (al < n_a) {
+                  const __half2 za = __hfma2(xr2[m], qa2, __hmul2(xi2[m], qas));
+                  const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
+                  *reinterpret_cast<__half2*>(tb + z_base + ra) = za;
+                }
+                if (al + kHalfA < n_a) {
+                  const __half2 zb = __hfma2(xr2[m], qb2, __hmul2(xi2[m], qbs));
+                  const uint32_t rb =
+                      static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
+                  *reinterpret_cast<__half2*>(tb + z_base + rb) = zb;
+                }
               }
               qa[0] = __ffma2_rn(make_float2(-qa[0].y, qa[0].x), make_float2(r128[0].y, r128[0].y),
                                  __fmul2_rn(qa[0], make_float2(r128[0].x, r128[0].x)));
@@ -550,10 +571,12 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                                     __fmul2_rn(make_float2(xv.x, xv.x), qb[cl]));
               }
               // row a_in * kBeams + pw + 16 m: z_base + (kBeams / 8 * a_in + 2 m) groups
+              // (a's beyond the pass's last one are not read by its MMAs)
               const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
               const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
-              *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack_word<kPrec, kCpl>(za);
-              *reinterpret_cast<uint32_t*>(tb + z_base + rb) = pack_word<kPrec, kCpl>(zb);
+              if (al < n_a) *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack_word<kPrec, kCpl>(za);
+              if (al + kHalfA < n_a)
+                *reinterpret_cast<uint32_t*>(tb + z_base + rb) = pack_word<kPrec, kCpl>(zb);
             }
 #pragma unroll
             for (int cl = 0; cl < kCpl; ++cl) {

@@ -92,7 +92,7 @@ extern "C" fdd_status fdd_dedisperse_spectra_static(const fdd_params* p, const v
   if (x_pitch < g.n_bins || y_pitch < g.n_bins)
     return report_error(FDD_ERR_INVALID_ARG, "pitches must be >= n_bins");
 
-  const int variant = p->mac_variant ? p->mac_variant - 1 : fdd::mac_variant_for(p->n_dm);
+  const int variant = p->mac_variant ? p->mac_variant - 1 : fdd::mac_variant_for(p->n_dm, p->n_chan);
   if (fdd::mac_smem_bytes(variant, p->n_chan) > 227 * 1024)
     return report_error(FDD_ERR_UNSUPPORTED, "n_chan needs more shared memory than a CTA has");
 
