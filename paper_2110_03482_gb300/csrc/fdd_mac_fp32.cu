@@ -568,9 +568,11 @@ __global__ void __launch_bounds__(W * 32, 1) mac_batch_kernel(const BatchSet* se
 // registers after the loads (shared-memory traffic per lane as the
 // four-product form's, two floats per operand): 48 paired FMAs and 6 paired
 // adds per lane and channel for 32 complex MACs.  A stage carries kCh
-// channels (8 in use: against 4, half the barrier round trips per channel
-// and longer independent runs of loads and FMAs; 0.726 of the FP32 peak
-// against 0.661 on the same launch, with 2 or 4 stages within 1 %).
+// channels of full items (16 in use: against 4, a quarter of the barrier
+// round trips per channel and longer independent runs of loads and FMAs;
+// 0.661, 0.726 and 0.752 of the FP32 peak with 4, 8 and 16 channels on the
+// same launch) and kChWide = 8 of wide items, whose per-channel operands
+// are up to twice as large.
 template <int kCh, int kStages>
 struct G3 {
   static constexpr int kA = 64;                // a's per bin (Z_a)
@@ -589,7 +591,12 @@ struct G3 {
   static constexpr int kWideMax = wide_bins(16) * wide_floats(16) > wide_bins(32) * wide_floats(32)
                                       ? wide_bins(16) * wide_floats(16)
                                       : wide_bins(32) * wide_floats(32);
-  static constexpr int kStageFloats = kCh * (kBins * kGFL > kWideMax ? kBins * kGFL : kWideMax);
+  // channels per stage of the wide items (their per-channel operands are up
+  // to twice the full item's, so they fill a stage with fewer channels)
+  static constexpr int kChWide = kCh < 8 ? kCh : 8;
+  static constexpr int kStageFloats = kCh * kBins * kGFL > kChWide * kWideMax
+                                          ? kCh * kBins * kGFL
+                                          : kChWide * kWideMax;
   static constexpr size_t kBarBytes = (2 * kStages * 8 + 4 + 15) / 16 * 16;
   static constexpr size_t kSwapBytes = kBarBytes + sizeof(float) * size_t(kStages) * kStageFloats;
 };
@@ -790,6 +797,7 @@ __device__ __forceinline__ bool g3_wide_body(const MacArgs& a, const PhaseConst*
                                              volatile int* abort_flag, int bin_tile, int jw,
                                              int series, uint32_t it0) {
   using Ly = G3<kCh, kStages>;
+  constexpr int kC = Ly::kChWide;  // channels per stage
   constexpr int kNB = Ly::wide_bins(kAw);   // bins per CTA
   constexpr int kW = Ly::wide_floats(kAw);  // floats per (bin, channel)
   constexpr int kPB = kNB / Ly::kProd;      // bins per producer warp
@@ -798,7 +806,7 @@ __device__ __forceinline__ bool g3_wide_body(const MacArgs& a, const PhaseConst*
   static_assert(kNB == Ly::kCons * 32 / kLPB && 2 * 32 == kPB * kAw, "wide layout");
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_iter = (a.n_chan + kCh - 1) / kCh;
+  const int n_iter = (a.n_chan + kC - 1) / kC;
   const int bin0 = bin_tile * kNB;
   bool ok = true;
 
@@ -826,22 +834,22 @@ __device__ __forceinline__ bool g3_wide_body(const MacArgs& a, const PhaseConst*
       m_z[t] = k_z[t] * static_cast<uint32_t>(a.j_begin + jw + (lane % kAw) * Ly::kT);
     }
     const int64_t xs = a.x_chan_stride;
-    float2 xn[kPB][kCh];
+    float2 xn[kPB][kC];
 #pragma unroll
     for (int r = 0; r < kPB; ++r)
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch)
+      for (int ch = 0; ch < kC; ++ch)
         xn[r][ch] = ch < a.n_chan ? __ldg(xp[r] + ch * xs) : make_float2(0.f, 0.f);
     for (int it = 0; it < n_iter; ++it) {
       const uint32_t g = it0 + it;
       const int s = g % kStages;
-      float2 x[kPB][kCh];
+      float2 x[kPB][kC];
 #pragma unroll
       for (int r = 0; r < kPB; ++r)
 #pragma unroll
-        for (int ch = 0; ch < kCh; ++ch) {
+        for (int ch = 0; ch < kC; ++ch) {
           x[r][ch] = xn[r][ch];
-          const int c = (it + 1) * kCh + ch;  // prefetch the next stage's X
+          const int c = (it + 1) * kC + ch;  // prefetch the next stage's X
           xn[r][ch] = c < a.n_chan ? __ldg(xp[r] + c * xs) : make_float2(0.f, 0.f);
         }
       ok = __all_sync(0xffffffffu,
@@ -849,8 +857,8 @@ __device__ __forceinline__ bool g3_wide_body(const MacArgs& a, const PhaseConst*
       if (!ok) break;
       float* st = stages + s * Ly::kStageFloats;
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) {
-        const int c = it * kCh + ch;
+      for (int ch = 0; ch < kC; ++ch) {
+        const int c = it * kC + ch;
         if (c < a.n_chan) {
           const PhaseConst p = pcs[c];
 #pragma unroll
@@ -893,9 +901,9 @@ __device__ __forceinline__ bool g3_wide_body(const MacArgs& a, const PhaseConst*
       const int s = g % kStages;
       ok = __all_sync(0xffffffffu, dev::mbar_wait(&full[s], (g / kStages) & 1, abort_flag));
       if (!ok) break;
-      const int nc = a.n_chan - it * kCh;
+      const int nc = a.n_chan - it * kC;
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) {
+      for (int ch = 0; ch < kC; ++ch) {
         if (ch < nc) {
           const float* grp = stages + s * Ly::kStageFloats + (ch * kNB + wb) * kW;
           const float4 zr = *reinterpret_cast<const float4*>(grp + 4 * ga);
@@ -1019,6 +1027,8 @@ __global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
   int cur = -1;
   uint32_t it0 = 0;
   const uint32_t n_iter = static_cast<uint32_t>((n_chan + kCh - 1) / kCh);
+  const uint32_t n_iter_wide =
+      static_cast<uint32_t>((n_chan + Ly::kChWide - 1) / Ly::kChWide);
   while (true) {
     if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(counter, 1ull));
     __syncthreads();  // also: every stage of the previous item has been read
@@ -1040,7 +1050,8 @@ __global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
     // the set's arguments as a local copy: the item's loops then keep what
     // they use in registers instead of re-reading the set after each store
     const MacArgs args = bs.args;
-    if (local < n_full)
+    const bool full_item = local < n_full;
+    if (full_item)
       g3_body<kCh, kStages>(args, sm.pcs, sm.stages, sm.full, sm.empty, sm.abort_flag,
                             static_cast<int>(local / bs.n_dm_blocks),
                             static_cast<int>(local % bs.n_dm_blocks), 0, it0);
@@ -1053,7 +1064,7 @@ __global__ void __launch_bounds__(G3<kCh, kStages>::kThreads, 1)
                                      sm.abort_flag,
                                      static_cast<int>(local - n_full - bs.n_wide_tiles),
                                      bs.j_narrow, 0, it0);
-    it0 += n_iter;
+    it0 += full_item ? n_iter : n_iter_wide;  // stages this item used
   }
 }
 
@@ -1098,7 +1109,7 @@ VariantInfo info_g3() {
 
 VariantInfo variant_info(int v) {
   switch (v) {
-    case MAC_G12_4x8: return info_g3<8, 3>();
+    case MAC_G12_4x8: return info_g3<16, 3>();
     case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, 12>();
     case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>>();
     case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>>();
@@ -1112,9 +1123,9 @@ VariantInfo variant_info(int v) {
 // Default tile for a trial count: the one with the least time for the padded
 // trial blocks, ceil(n_dm / block) * block / rate, with each tile's rate
 // measured kernel-only on GB300 (fraction of the FP32 peak, 1024 channels,
-// 131073 bins): G12_4x8 0.726 on full 2048-trial blocks, whose last block
-// runs as 1024-trial wide items at 0.624 (at most 1024 trials) or 512-trial
-// ones at 0.504 (at most 512); Q_4x8 0.493 (1024-trial blocks), Q_8x8_512
+// 131073 bins): G12_4x8 0.752 on full 2048-trial blocks, whose last block
+// runs as 1024-trial wide items at 0.616 (at most 1024 trials) or 512-trial
+// ones at 0.510 (at most 512); Q_4x8 0.493 (1024-trial blocks), Q_8x8_512
 // 0.415 (512), Q_4x4 0.347 (128).  (The four-product warp-specialised tile
 // W12_8x8 measured 0.621 on the same launch, Q12_8x8, the 2048-trial tile on
 // the plain schedule, 0.553.)
@@ -1123,7 +1134,7 @@ int mac_variant_for(int n_dm, int n_chan) {
     int variant, block;
     double rate, wide_rate, narrow_rate;  // > 0: a last block of <= block / 2, / 4
   };
-  static const Tile tiles[] = {{MAC_G12_4x8, 2048, 0.726, 0.624, 0.504},
+  static const Tile tiles[] = {{MAC_G12_4x8, 2048, 0.752, 0.616, 0.510},
                                {MAC_Q_4x8, 1024, 0.493, 0.0, 0.0},
                                {MAC_Q_8x8_512, 512, 0.415, 0.0, 0.0},
                                {MAC_Q_4x4, 128, 0.347, 0.0, 0.0}};

@@ -152,8 +152,8 @@ def test_variant_choice():
     assert fdd.fdd_plan_geometry(_params(w2))["mac_variant"] == fdd.FDD_MAC_G12_4X8
     # least padded-block time: 128-trial blocks up to 256 trials, the
     # 2048-trial tile above (a last block of <= 512 or <= 1024 trials as
-    # 512- or 1024-trial wide items); measured rates 0.347 (128), 0.726
-    # (2048), wide 0.624, narrow 0.504
+    # 512- or 1024-trial wide items); measured rates 0.347 (128), 0.752
+    # (2048), wide 0.616, narrow 0.510
     for n, v in [(1, fdd.FDD_MAC_Q_4X4), (256, fdd.FDD_MAC_Q_4X4), (384, fdd.FDD_MAC_G12_4X8),
                  (448, fdd.FDD_MAC_G12_4X8), (512, fdd.FDD_MAC_G12_4X8),
                  (600, fdd.FDD_MAC_G12_4X8), (1024, fdd.FDD_MAC_G12_4X8),
