@@ -72,10 +72,14 @@ typedef enum fdd_status {
 /* Kernel tiles of the FP32 phase-rotate-and-sum (fdd_params.mac_variant - 1,
  * fdd_info.mac_variant).  All issue paired f32x2 FMAs on an A x B register
  * tile per lane (a warp covers 2048, 1024, 4 x 512 or 4 x 128 trials of its
- * bins); W12 splits phasor evaluation (4 warps) from the multiply-accumulates
- * (8 warps), the others let every warp do both. */
-#define FDD_MAC_W12_8X8 0   /* warp-specialised, 2048-trial blocks (default for
-                               large trial counts)                              */
+ * bins); W12 and G12 split phasor evaluation (4 warps) from the
+ * multiply-accumulates (8 warps), the others let every warp do both.  With
+ * mac_variant 0 a plan takes the tile with the least time for its trial
+ * count whose shared memory holds the channels' phase table: G12_4X8 from
+ * 257 trials, Q_4X4 below; above about 5300 channels G12_4X8 no longer fits
+ * and the fastest of the others that do is taken. */
+#define FDD_MAC_W12_8X8 0   /* warp-specialised, 2048-trial blocks, four real
+                               products per complex MAC                         */
 #define FDD_MAC_Q12_8X8 1   /* 2048-trial blocks, 12 warps, plain schedule       */
 #define FDD_MAC_Q_4X8 2     /* 1024-trial blocks                                 */
 #define FDD_MAC_Q_8X8_512 3 /* 8x8 lane tile, 8 lanes per bin, four bins per
@@ -84,7 +88,9 @@ typedef enum fdd_status {
                                blocks (small trial counts, ragged tails)        */
 #define FDD_MAC_G12_4X8 5   /* warp-specialised, 2048-trial blocks, three real
                                products per complex MAC (Gauss's form): 4 phasor
-                               warps feed 8 MAC warps, two per bin              */
+                               warps feed 8 MAC warps, two per bin; a last block
+                               of <= 1024 / <= 512 trials runs as wide items of
+                               8 / 16 bins (default from 257 trials)            */
 #define FDD_MAC_VARIANTS 6
 #define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
 
