@@ -889,8 +889,16 @@ fdd_status fdd_batch_plan(const fdd_params* p, const fdd_beam_desc* beams, int32
     if (tst != FDD_OK) return tst;
     cache_store(key, variant);
   }
-  if (variant < 0)  // G12, unless the channels' phase table leaves it no room
-    variant = tile_fits(FDD_MAC_G12_4X8) ? FDD_MAC_G12_4X8 : FDD_MAC_W12_8X8;
+  if (variant < 0) {  // G12, unless the channels' phase table leaves it no room
+    const int order[] = {FDD_MAC_G12_4X8, FDD_MAC_W12_8X8, FDD_MAC_Q12_8X8, FDD_MAC_Q_4X8,
+                         FDD_MAC_Q_8X8_512, FDD_MAC_Q_4X4};
+    for (int v : order)
+      if (tile_fits(v)) {
+        variant = v;
+        break;
+      }
+    if (variant < 0) return report_error(FDD_ERR_UNSUPPORTED, "no kernel tile fits an SM");
+  }
   if ((st = use_variant(variant))) return st;
   B_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
   *out = guard.release();

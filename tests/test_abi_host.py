@@ -160,6 +160,10 @@ def test_variant_choice():
                  (1100, fdd.FDD_MAC_G12_4X8), (4096, fdd.FDD_MAC_G12_4X8)]:
         g = fdd.fdd_plan_geometry(_params(w2, dm_list=0.5 * np.arange(n)))
         assert g["mac_variant"] == v, (n, g["mac_variant"])
+    # above ~5300 channels the G12 tile's ring leaves the phase table no room
+    # in a CTA's shared memory: the fastest tile that fits is taken
+    g = fdd.fdd_plan_geometry(_params(w2, n_chan=6000, dnu_mhz=0.05))
+    assert g["mac_variant"] not in (fdd.FDD_MAC_G12_4X8, fdd.FDD_MAC_TC)
 
 
 def test_tensor_core_form_geometry():

@@ -334,3 +334,32 @@ def test_tensor_core_batch_matches_oracle(output):
         first = _tc_batch_run(batch, d_in, output)
         _tc_check(batch, first, refs, output)
         assert torch.equal(_tc_batch_run(batch, d_in, output), first)
+
+
+def test_batch_many_channels_take_a_tile_that_fits():
+    """6000 channels: the G12 tile's ring leaves the phase table no room, so
+    the batch takes the next tile that fits one CTA per SM, and matches the
+    oracle."""
+    n_chan, beams = 6000, [(300, 0.0, 0.5, 64), (200, 1.0, 0.25, 40)]
+    lo, hi = 1200.0, 1500.0
+    dnu = (hi - lo) / n_chan
+    rng = np.random.default_rng(8)
+    xs = [rng.standard_normal((b[0], n_chan)).astype(np.float32) for b in beams]
+    with fdd.Batch(beams, autotune=False, n_chan=n_chan, nu_lo_mhz=lo + 0.5 * dnu,
+                   dnu_mhz=dnu, t_samp_s=T_SAMP, in_dtype=fdd.FDD_IN_F32,
+                   output=fdd.FDD_OUT_SPECTRA, chunk_len=0) as batch:
+        assert batch.info["mac_variant"] != fdd.FDD_MAC_G12_4X8
+        d_in = torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
+        out = torch.zeros((batch.info["out_elems"], 2), device="cuda")
+        batch.execute(d_in, out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.float64)
+        o = o[:, 0] + 1j * o[:, 1]
+        nu = lo + 0.5 * dnu + dnu * np.arange(n_chan)
+        for i, (x, (n_t, dm0, ddm, n_dm)) in enumerate(zip(xs, beams)):
+            d = oracle.delays(nu, dm0 + ddm * np.arange(n_dm), T_SAMP)
+            geo = oracle.geometry(n_t, 0, d)
+            ref = oracle.fdd_bins(oracle.spectra(x.T.astype(np.float64), geo, 0),
+                                  np.arange(geo.K), geo.L, d)
+            got = o[batch.out_offsets[i]: batch.out_offsets[i] + ref.size].reshape(ref.shape)
+            assert rel_l2(got, ref) <= FP32_REL_L2, (i, rel_l2(got, ref))
