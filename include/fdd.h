@@ -584,9 +584,12 @@ fdd_status fdd_batch_execute(fdd_batch_t b, const void* d_in, void* d_out, fdd_s
  * captured as a graph.  The tensor-core batch (time-major input only) calls
  * the source per (beam, chunk) window of its plans (t_begin, n_samples within
  * the beam's own samples) and the sink per (beam, chunk, block of trials) in
- * each plan's block order; a sink reading on another stream returns, with
- * the last block of each round of calls, an event recorded after its reads
- * of every block so far.  Errors: FDD_ERR_INVALID_ARG, FDD_ERR_ALLOC (first
+ * each plan's block order (the blocks of one plan block — same chunk and
+ * first trial, consecutive beams — come one after another); a sink reading
+ * on another stream may return a release event with any block, recorded
+ * after its reads of every block handed over so far: the last one returned
+ * within a plan block guards that plan block's device memory.  Errors:
+ * FDD_ERR_INVALID_ARG, FDD_ERR_ALLOC (first
  * call), FDD_ERR_UNSUPPORTED (tensor-core batch with channel-major input),
  * FDD_ERR_CUDA, FDD_ERR_CUFFT, a callback's own status.
  */
