@@ -76,8 +76,8 @@ typedef enum fdd_status {
  * multiply-accumulates (8 warps), the others let every warp do both.  With
  * mac_variant 0 a plan takes the tile with the least time for its trial
  * count whose shared memory holds the channels' phase table: G12_4X8 from
- * 257 trials, Q_4X4 below; above about 5300 channels G12_4X8 no longer fits
- * and the fastest of the others that do is taken. */
+ * 257 trials, Q_4X4 below; above 8381 channels G12_4X8 no longer fits and
+ * the fastest of the others that do is taken. */
 #define FDD_MAC_W12_8X8 0   /* warp-specialised, 2048-trial blocks, four real
                                products per complex MAC                         */
 #define FDD_MAC_Q12_8X8 1   /* 2048-trial blocks, 12 warps, plain schedule       */

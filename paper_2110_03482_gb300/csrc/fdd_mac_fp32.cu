@@ -1109,7 +1109,7 @@ VariantInfo info_g3() {
 
 VariantInfo variant_info(int v) {
   switch (v) {
-    case MAC_G12_4x8: return info_g3<16, 3>();
+    case MAC_G12_4x8: return info_g3<16, 2>();
     case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, 12>();
     case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>>();
     case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>>();
