@@ -1107,9 +1107,19 @@ VariantInfo info_g3() {
   return vi;
 }
 
-VariantInfo variant_info(int v) {
+// The G12 tile keeps three ring stages while the channels' phase table leaves
+// room for them in a CTA's 227 KB and drops to two beyond that (up to 8381
+// channels).  One plain launch runs as fast with two as with three; the
+// persistent batch kernel, whose items follow one another in the same ring,
+// lost 5 % with two.
+constexpr size_t kMaxSmem = 227 * 1024;
+
+VariantInfo variant_info(int v, int n_chan) {
   switch (v) {
-    case MAC_G12_4x8: return info_g3<16, 2>();
+    case MAC_G12_4x8:
+      return sizeof(PhaseConst) * static_cast<size_t>(n_chan) + G3<16, 3>::kSwapBytes <= kMaxSmem
+                 ? info_g3<16, 3>()
+                 : info_g3<16, 2>();
     case MAC_Q12_8x8: return info<G8x8, PackedCompact<G8x8>, 12>();
     case MAC_Q_4x8: return info<G4x8, PackedCompact<G4x8>>();
     case MAC_Q_8x8_512: return info<G8x8q, PackedCompact<G8x8q>>();
@@ -1141,7 +1151,7 @@ int mac_variant_for(int n_dm, int n_chan) {
   int best = MAC_W12_8x8;  // (the smallest shared-memory need of the 2048-trial tiles)
   double best_cost = 0.0;
   for (const Tile& t : tiles) {
-    if (mac_smem_bytes(t.variant, n_chan) > 227 * 1024) continue;
+    if (mac_smem_bytes(t.variant, n_chan) > kMaxSmem) continue;
     const int full = n_dm / t.block, rem = n_dm % t.block;
     double cost = full * t.block / t.rate;
     if (rem > 0 && t.narrow_rate > 0.0 && rem <= t.block / 4)
@@ -1158,26 +1168,26 @@ int mac_variant_for(int n_dm, int n_chan) {
   return best;
 }
 
-int mac_variant_trials_per_block(int variant) { return variant_info(variant).dms; }
+int mac_variant_trials_per_block(int variant) { return variant_info(variant, 1).dms; }
 
 size_t mac_smem_bytes(int variant, int n_chan) {
-  return sizeof(PhaseConst) * static_cast<size_t>(n_chan) + variant_info(variant).swap_bytes;
+  return sizeof(PhaseConst) * static_cast<size_t>(n_chan) + variant_info(variant, n_chan).swap_bytes;
 }
 
 cudaError_t mac_prepare(int variant, int n_chan) {
-  const VariantInfo vi = variant_info(variant);
+  const VariantInfo vi = variant_info(variant, n_chan);
   const int bytes = static_cast<int>(mac_smem_bytes(variant, n_chan));
   cudaError_t e = cudaFuncSetAttribute(vi.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess || !vi.batch_fn) return e;
   return cudaFuncSetAttribute(vi.batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-int mac_variant_bins_per_cta(int variant) { return variant_info(variant).bins(); }
+int mac_variant_bins_per_cta(int variant) { return variant_info(variant, 1).bins(); }
 
-bool mac_variant_batchable(int variant) { return variant_info(variant).batch_fn != nullptr; }
+bool mac_variant_batchable(int variant) { return variant_info(variant, 1).batch_fn != nullptr; }
 
 int mac_batch_ctas_per_sm(int variant, int n_chan) {
-  const VariantInfo vi = variant_info(variant);
+  const VariantInfo vi = variant_info(variant, n_chan);
   if (!vi.batch_fn) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vi.batch_fn, vi.warps * 32,
@@ -1192,7 +1202,7 @@ int mac_batch_ctas_per_sm(int variant, int n_chan) {
 cudaError_t launch_mac_batch(const BatchSet* d_sets, int n_sets, long long n_items,
                              unsigned long long* d_counter, int variant, int n_ctas, int n_chan,
                              cudaStream_t s) {
-  const VariantInfo vi = variant_info(variant);
+  const VariantInfo vi = variant_info(variant, n_chan);
   if (!vi.batch_fn) return cudaErrorInvalidValue;
   if (n_items <= 0) return cudaSuccess;
   void* params[] = {&d_sets, &n_sets, &n_items, &d_counter};
@@ -1203,7 +1213,7 @@ cudaError_t launch_mac_batch(const BatchSet* d_sets, int n_sets, long long n_ite
 
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
-  const VariantInfo vi = variant_info(variant);
+  const VariantInfo vi = variant_info(variant, a.n_chan);
   const int bins_per_cta = vi.bins();
   dim3 grid((a.n_bins + bins_per_cta - 1) / bins_per_cta, (a.n_dm + vi.dms - 1) / vi.dms,
             a.n_series);

@@ -160,9 +160,10 @@ def test_variant_choice():
                  (1100, fdd.FDD_MAC_G12_4X8), (4096, fdd.FDD_MAC_G12_4X8)]:
         g = fdd.fdd_plan_geometry(_params(w2, dm_list=0.5 * np.arange(n)))
         assert g["mac_variant"] == v, (n, g["mac_variant"])
-    # the G12 tile's two-stage ring (96 KB) leaves room for the phase table
-    # of 8381 channels (16 bytes each) in a CTA's 227 KB; above that the
-    # fastest tile that fits is taken
+    # the G12 tile's ring (three stages of 48 KB, two beyond about 5300
+    # channels) leaves room for the phase table of up to 8381 channels (16
+    # bytes each) in a CTA's 227 KB; above that the fastest tile that fits is
+    # taken
     g = fdd.fdd_plan_geometry(_params(w2, n_chan=8192, dnu_mhz=0.02, workspace_limit=200 << 30))
     assert g["mac_variant"] == fdd.FDD_MAC_G12_4X8
     g = fdd.fdd_plan_geometry(_params(w2, n_chan=9000, dnu_mhz=0.02, workspace_limit=200 << 30))

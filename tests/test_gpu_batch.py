@@ -337,10 +337,10 @@ def test_tensor_core_batch_matches_oracle(output):
 
 
 def test_batch_many_channels_take_a_tile_that_fits():
-    """6000 channels: the G12 tile's ring leaves the phase table no room, so
+    """9000 channels: the G12 tile's ring leaves the phase table no room, so
     the batch takes the next tile that fits one CTA per SM, and matches the
     oracle."""
-    n_chan, beams = 6000, [(300, 0.0, 0.5, 64), (200, 1.0, 0.25, 40)]
+    n_chan, beams = 9000, [(300, 0.0, 0.5, 64), (200, 1.0, 0.25, 40)]
     lo, hi = 1200.0, 1500.0
     dnu = (hi - lo) / n_chan
     rng = np.random.default_rng(8)
