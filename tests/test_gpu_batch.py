@@ -336,11 +336,12 @@ def test_tensor_core_batch_matches_oracle(output):
         assert torch.equal(_tc_batch_run(batch, d_in, output), first)
 
 
-def test_batch_many_channels_take_a_tile_that_fits():
-    """9000 channels: the G12 tile's ring leaves the phase table no room, so
-    the batch takes the next tile that fits one CTA per SM, and matches the
-    oracle."""
-    n_chan, beams = 9000, [(300, 0.0, 0.5, 64), (200, 1.0, 0.25, 40)]
+@pytest.mark.parametrize("n_chan", [6000, 9000])
+def test_batch_many_channels_take_a_tile_that_fits(n_chan):
+    """6000 channels: the G12 tile runs with a two-stage ring; 9000: its ring
+    leaves the phase table no room, so the batch takes the next tile that
+    fits one CTA per SM.  Both match the oracle."""
+    beams = [(300, 0.0, 0.5, 64), (200, 1.0, 0.25, 40)]
     lo, hi = 1200.0, 1500.0
     dnu = (hi - lo) / n_chan
     rng = np.random.default_rng(8)
@@ -348,7 +349,7 @@ def test_batch_many_channels_take_a_tile_that_fits():
     with fdd.Batch(beams, autotune=False, n_chan=n_chan, nu_lo_mhz=lo + 0.5 * dnu,
                    dnu_mhz=dnu, t_samp_s=T_SAMP, in_dtype=fdd.FDD_IN_F32,
                    output=fdd.FDD_OUT_SPECTRA, chunk_len=0) as batch:
-        assert batch.info["mac_variant"] != fdd.FDD_MAC_G12_4X8
+        assert (batch.info["mac_variant"] == fdd.FDD_MAC_G12_4X8) == (n_chan < 8382)
         d_in = torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
         out = torch.zeros((batch.info["out_elems"], 2), device="cuda")
         batch.execute(d_in, out)

@@ -89,6 +89,27 @@ def test_kernel_matches_oracle(n_chan, L, dm0, ddm, n_dm, n_series, variant):
         assert rel_l2(P[s], np.abs(ref) ** 2) <= 2 * FP32_REL_L2
 
 
+def test_kernel_g12_two_stage_ring():
+    """6000 channels: the G12 tile's phase table leaves room for two ring
+    stages only; full blocks, a wide last block and the oracle agree."""
+    n_chan, L, n_dm = 6000, 64, 2048 + 600
+    dms = 0.25 * np.arange(n_dm)
+    w = _small_workload(n_chan, L, dms, t_samp=2e-3)
+    rng = np.random.default_rng(61)
+    K = L // 2 + 1
+    X = rng.standard_normal((1, n_chan, K)) + 1j * rng.standard_normal((1, n_chan, K))
+    X = X.astype(np.complex64).astype(np.complex128)
+    with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA)) as plan:
+        assert plan.info["mac_variant"] == fdd.FDD_MAC_G12_4X8
+        dX = complex_to_device(X, K)
+        dY = torch.zeros((1, n_dm, K, 2), dtype=torch.float32, device="cuda")
+        plan.dedisperse_spectra(dX, K, 1, 0, n_dm, dY, K)
+        torch.cuda.synchronize()
+        Y = device_to_complex(dY, K)
+    ref = oracle.fdd_bins(X[0], np.arange(K), L, _oracle_delays(w))
+    assert rel_l2(Y[0], ref) <= FP32_REL_L2
+
+
 def test_kernel_dm_subrange_and_large_phases():
     """Survey-like phases (L = 2^18, trials 0..1023.5 at 64 us): sampled bins up
     to Nyquist, the full list and a sub-range starting mid-block."""
