@@ -432,9 +432,12 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
                   fixed + per_dm);
     const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
     if (fit < batch) {
+      // whole kernel passes (tensor cores) or trial blocks; below one pass,
+      // whole a's of the tensor-core tile, else whatever fits
       const int64_t blk = tc ? fdd::mac_tc_trials_per_pass(p->n_beams)
                              : fdd::mac_variant_trials_per_block(g->mac_variant);
-      batch = fit >= blk ? fit / blk * blk : fit;
+      const int64_t sub = tc ? fdd::mac_tc_trials_per_a() : blk;
+      batch = fit >= blk ? fit / blk * blk : fit >= sub ? fit / sub * sub : fit;
     }
     if (batch > 65535) batch = 65535 / 64 * 64;
   }

@@ -93,14 +93,18 @@ cudaError_t mac_prepare(int variant, int n_chan);  // kernel attributes (host, o
 cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s);
 size_t mac_smem_bytes(int variant, int n_chan);
 
-// Tensor-core phase-rotate-and-sum (fdd_mac_tc.cu): BF16 hi+lo (or BF16)
-// phasors, BF16 data, FP32 accumulation in tensor memory; one persistent CTA
-// per SM.
+// Tensor-core phase-rotate-and-sum (fdd_mac_tc.cu): 16-bit (or FP8)
+// phasors and data, FP32 accumulation in tensor memory; persistent pairs of
+// CTAs (one per SM), each pair on one bin at a time.
 size_t mac_tc_smem_bytes();
+// trials of one pass over the channels, and of one a (T = 256)
 int mac_tc_trials_per_pass(int n_series);
+int mac_tc_trials_per_a();
+// Sets the kernels' shared-memory limit and counts the pairs resident at once
+// on the current device (before the first call on it).
 cudaError_t mac_tc_prepare();
 // Beams per tensor-core group: 16 when a call has at most 16 series (then a
-// pass covers 2048 trials), else 32 (1024 trials per pass).
+// pass covers 4096 trials), else 32 (2048 trials per pass).
 int mac_tc_beams_per_group(int n_series);
 // The tensor-core kernel reads the spectra bin-major, X_T[k][series][chan]
 // (a 256-byte row per 32 channels of one beam), and writes Y bin-major,

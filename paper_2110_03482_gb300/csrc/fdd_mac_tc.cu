@@ -41,6 +41,8 @@
 // Barriers count warps (one arrive per warp).  Every wait is bounded: on
 // timeout the kernel records FDD_ERR_TIMEOUT in the status word, stops,
 // drains its own MMAs (bounded), frees its tensor memory and returns.
+#include <atomic>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -59,12 +61,16 @@ using dev::smem_u32;
 using dev::top32_mul;
 using dev::unit_phasor;
 
-constexpr int kM = 128;                  // trials b per a (T)
+constexpr int kM = 128;                  // trials b per CTA (tensor-memory lanes)
 constexpr int kN = 256;                  // (a, beta) columns of each accumulator
+// Trials per a: T = 128 for one CTA; a CTA pair (kPair, one MMA of M = 256
+// over both CTAs' tensor cores) takes T = 256, rows b < 128 in the first CTA.
+template <bool kPair>
+__host__ __device__ constexpr int trials_per_a() { return kPair ? 2 * kM : kM; }
 // Beams per group (kBeams, 16 or 32) is a template parameter: a pass covers
-// kN / kBeams a's, i.e. kN / kBeams * kM trials.
-template <int kBeams>
-__host__ __device__ constexpr int dms_per_pass() { return kN / kBeams * kM; }
+// kN / kBeams a's, i.e. kN / kBeams * T trials.
+template <int kBeams, bool kPair>
+__host__ __device__ constexpr int dms_per_pass() { return kN / kBeams * trials_per_a<kPair>(); }
 constexpr int kKC = 32;                  // channels per stage of 16-bit operands
 constexpr int kProdWarps = 16;
 constexpr int kEpiWarps = 4;             // one per tensor-memory lane quarter
@@ -103,17 +109,17 @@ enum TcPrec { kBf16HiLo = 0, kBf16 = 1, kF16 = 2, kF8 = 3 };
 // (format 0) under kind::f16, both E4M3 (format 0) under kind::f8f6f4; both
 // K-major, N and M.
 // n: the MMA's N, a multiple of 16 in [16, kN] (a pass's last a's may be
-// fewer than the kN / kBeams of a full pass).
+// fewer than the kN / kBeams of a full pass); m: 128, or 256 for a CTA pair.
 template <int kPrec>
-__host__ __device__ constexpr uint32_t idesc(int n = kN) {
+__host__ __device__ constexpr uint32_t idesc(int n, int m) {
   return (1u << 4) | ((kPrec == kF16 || kPrec == kF8) ? 0u : ((1u << 7) | (1u << 10))) |
-         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(kM >> 4) << 24);
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
 }
 
 // a's of the pass from trial j_pass: all kNA of a full pass, fewer (whole
-// a's of kM trials) where the trials end within it
-__device__ __forceinline__ int pass_as(int n_dm, int j_pass, int kNA) {
-  const int left = (n_dm - j_pass + kM - 1) / kM;
+// a's of kT trials) where the trials end within it
+__device__ __forceinline__ int pass_as(int n_dm, int j_pass, int kNA, int kT) {
+  const int left = (n_dm - j_pass + kT - 1) / kT;
   return left < kNA ? left : kNA;
 }
 
@@ -193,15 +199,28 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// D (+)= A B^T for one K step of 32 bytes: M = 128, N = 256, FP32 out; 16
-// elements of 16 bits (kind::f16) or 32 of FP8 E4M3 (kind::f8f6f4).
-template <int kPrec>
+// D (+)= A B^T for one K step of 32 bytes: M = 128 (256 over a CTA pair),
+// N up to 256, FP32 out; 16 elements of 16 bits (kind::f16) or 32 of FP8 E4M3
+// (kind::f8f6f4).  A CTA pair's MMA, issued by the first CTA, reads each
+// CTA's 128 rows of A and its N / 2 rows of B at the same shared-memory
+// offsets and writes each CTA's 128 rows of D into its own tensor memory.
+template <int kPrec, bool kPair>
 __device__ __forceinline__ void mma16(uint32_t d, uint64_t adesc, uint64_t bdesc,
                                       uint32_t accum, uint32_t id) {
-  if constexpr (kPrec == kF8) {
+  if constexpr (kPrec == kF8 && kPair) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accum));
+  } else if constexpr (kPrec == kF8) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accum));
+  } else if constexpr (kPair) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
         "l"(adesc), "l"(bdesc), "r"(id), "r"(accum));
   } else {
     asm volatile(
@@ -211,20 +230,125 @@ __device__ __forceinline__ void mma16(uint32_t d, uint64_t adesc, uint64_t bdesc
   }
 }
 
+// Completion of this thread's earlier MMAs arrives once on the barrier at
+// this shared-memory offset: in this CTA, or in both CTAs of a pair.
+template <bool kPair>
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  if constexpr (kPair) {
+    const uint16_t both = 3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(both)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+  }
+}
+
+// The same, arriving on this CTA's barrier only.
+template <bool kPair>
+__device__ __forceinline__ void mma_commit_one(uint64_t* bar) {
+  if constexpr (kPair) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+  } else {
+    mma_commit<false>(bar);
+  }
+}
+
+// ---- CTA pairs (clusters of two): rank, pair index, barriers in the first CTA
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Every thread of both CTAs: earlier accesses (release) before later ones
+// (acquire) of any thread of the pair.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// One arrive for the whole (converged) warp on the barrier at this offset in
+// the pair's first CTA (release at cluster scope).
+__device__ __forceinline__ void mbar_arrive_warp_first(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(smem_u32(bar)));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
+                 : "memory");
+  }
+}
+// Bounded wait at cluster scope (arrivals from the other CTA of the pair).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity,
+                                                  volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > dev::kWaitCycles) return false;
+  }
+}
+template <bool kPair>
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if constexpr (kPair)
+    return mbar_wait_cluster(bar, parity, abort_flag);
+  else
+    return mbar_wait(bar, parity, abort_flag);
+}
+template <bool kPair>
+__device__ __forceinline__ void arrive_warp(uint64_t* bar) {
+  if constexpr (kPair)
+    mbar_arrive_warp_first(bar);
+  else
+    mbar_arrive_warp(bar);
+}
+
 // 21 warps at one CTA per SM: one of the four schedulers holds six of them,
 // and a scheduler's 16384 registers cap the kernel at 80 per thread.
 // kPrec: kBf16HiLo (phasors as BF16 hi + lo, four MMAs per K step), kBf16
 // (BF16 only), kF16 (FP16 phasors and scaled FP16 data) or kF8 (FP8 E4M3
 // phasors and scaled E4M3 data, kind::f8f6f4, 64 channels per stage).
-template <int kPrec, int kBeams>
+// kPair: launched in clusters of two CTAs, each pair working on one bin at a
+// time with T = 256: the first CTA's MMA warp issues M = 256 MMAs over both
+// CTAs (rows b < 128 from the first CTA, the rest from the second), each CTA
+// builds its own 128 rows of P and half of the pass's Z columns (the first
+// or the second half of its a's), so a CTA builds a third fewer operand
+// values per MMA than alone; its producers and epilogue arrive on the first
+// CTA's barriers, and the MMAs' completion reaches both CTAs' barriers.
+template <int kPrec, int kBeams, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
   constexpr bool kHiLo = kPrec == kBf16HiLo;
   constexpr bool kScaled = kPrec == kF16 || kPrec == kF8;  // per-bin data scale
   constexpr int kCpl = kPrec == kF8 ? 2 : 1;               // channels per producer lane
   constexpr int kKCp = kKC * kCpl;                         // channels per stage
+  constexpr int kT = trials_per_a<kPair>();   // trials per a
   constexpr int kNA = kN / kBeams;            // a's per pass (8 or 16)
-  constexpr int kDmsPass = dms_per_pass<kBeams>();
+  constexpr int kNAc = kPair ? kNA / 2 : kNA;  // a's whose Z this CTA builds
+  constexpr int kDmsPass = dms_per_pass<kBeams, kPair>();
   constexpr int kStages = Ring<kHiLo>::kStages;
   constexpr uint32_t kStageBytes = Ring<kHiLo>::kStageBytes;
   constexpr uint32_t kBOff = Ring<kHiLo>::kBOff;
@@ -242,26 +366,39 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // this CTA's place in its pair (0 alone), the unit of bins and their count
+  const int rank = kPair ? static_cast<int>(cluster_rank()) : 0;
+  const int unit = kPair ? static_cast<int>(cluster_index()) : static_cast<int>(blockIdx.x);
+  const int n_units = kPair ? static_cast<int>(cluster_count()) : static_cast<int>(gridDim.x);
+  constexpr int kCtas = kPair ? 2 : 1;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&full[i], kProdWarps);  // one arrive per producer warp
+      mbar_init(&full[i], kCtas * kProdWarps);  // one arrive per producer warp of the pair
       mbar_init(&empty[i], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kEpiWarps);    // one arrive per epilogue warp
+    mbar_init(acc_empty, kCtas * kEpiWarps);    // one arrive per epilogue warp of the pair
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (kPair) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if constexpr (kPair) cluster_sync();  // both CTAs' barriers exist before any remote arrive
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -269,26 +406,31 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   const int n_pass = (a.n_dm + kDmsPass - 1) / kDmsPass;
   const int n_tiles = (a.n_chan + kKCp - 1) / kKCp;
   const int items_per_bin = n_groups * n_pass;
+  // a's of a pass with n_a of them: the MMA's (even for a pair, whose two
+  // CTAs hold half each) and, per CTA, how many and from which one it builds
+  auto mma_as = [&](int n_a) { return kPair ? (n_a + 1) & ~1 : n_a; };
+  auto cta_first_a = [&](int n_a) { return kPair ? rank * (mma_as(n_a) / 2) : 0; };
+  auto cta_as = [&](int n_a) { return kPair ? mma_as(n_a) / 2 : n_a; };
 
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && rank == 0) {
       uint32_t s = 0, p = 0;
       bool issued = false, ok = true;
-      for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
+      for (int k = unit; k < a.n_bins && ok; k += n_units) {
         for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
-          // the epilogue has read the previous pass out of tensor memory
-          if (!mbar_wait(acc_empty, (p & 1) ^ 1, abort_flag)) {
+          // the epilogue (of both CTAs) has read the previous pass out of tensor memory
+          if (!wait_bar<kPair>(acc_empty, (p & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           // N of this pass: its a's times the group's beams
-          const uint32_t id =
-              idesc<kPrec>(pass_as(a.n_dm, (it % n_pass) * kDmsPass, kNA) * kBeams);
+          const int n_a = pass_as(a.n_dm, (it % n_pass) * kDmsPass, kNA, kT);
+          const uint32_t id = idesc<kPrec>(mma_as(n_a) * kBeams, kCtas * kM);
           for (int t = 0; t < n_tiles; ++t, ++s) {
             const uint32_t st = s % kStages;
-            if (!mbar_wait(&full[st], (s / kStages) & 1, abort_flag)) {
+            if (!wait_bar<kPair>(&full[st], (s / kStages) & 1, abort_flag)) {
               ok = false;
               break;
             }
@@ -298,25 +440,21 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t bd = smem_desc(stage + kBOff + kk * 32);
               const uint32_t accum = (t > 0 || kk > 0) ? 1u : 0u;
-              mma16<kPrec>(tmem, smem_desc(stage + kk * 32), bd, accum, id);               // re, hi
-              mma16<kPrec>(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum, id);  // im, hi
+              mma16<kPrec, kPair>(tmem, smem_desc(stage + kk * 32), bd, accum, id);  // re, hi
+              mma16<kPrec, kPair>(tmem + kN, smem_desc(stage + kTileA + kk * 32), bd, accum,
+                                  id);  // im, hi
               if (kHiLo) {
-                mma16<kPrec>(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u, id);  // re, lo
-                mma16<kPrec>(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u,
-                             id);  // im, lo
+                mma16<kPrec, kPair>(tmem, smem_desc(stage + 2 * kTileA + kk * 32), bd, 1u,
+                                    id);  // re, lo
+                mma16<kPrec, kPair>(tmem + kN, smem_desc(stage + 3 * kTileA + kk * 32), bd, 1u,
+                                    id);  // im, lo
               }
             }
             issued = true;
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&empty[st]))
-                : "memory");
+            mma_commit<kPair>(&empty[st]);
           }
           if (!ok) break;
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(acc_full))
-              : "memory");
+          mma_commit<kPair>(acc_full);
         }
       }
       if (!ok) {
@@ -324,25 +462,22 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
         if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
       }
       if (issued) {  // drain this thread's MMAs before tensor memory is freed
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(drain))
-            : "memory");
+        mma_commit_one<kPair>(drain);
         volatile int never = 0;
         mbar_wait(drain, 0, &never);
       }
     }
   } else if (warp <= kEpiWarps) {
     // ------------------------------------------------------------ epilogue
-    // Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (trials b) of D_re
-    // and D_im, all 256 (a, beta) columns, and stores Y[k][beta][aT + b]:
-    // the warp's 32 lanes write 32 consecutive trials.
+    // Warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (trials b of this
+    // CTA) of D_re and D_im, all (a, beta) columns, and stores
+    // Y[k][beta][aT + b]: the warp's 32 lanes write 32 consecutive trials.
     const int quarter = warp & 3;  // the lanes this warp may read
-    const int b = quarter * 32 + lane;
+    const int b = rank * kM + quarter * 32 + lane;
     const uint32_t t_lanes = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     uint32_t p = 0;
     bool ok = true;
-    for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
+    for (int k = unit; k < a.n_bins && ok; k += n_units) {
       const bool real_only = (a.k_begin + k == a.real_bin_a) || (a.k_begin + k == a.real_bin_b);
       // FP16: undo the bin's data scale (a power of two, so exactly)
       const float sy = kScaled ? a.scale / bin_scale<kPrec>(a.bin_absmax[k]) : a.scale;
@@ -351,19 +486,20 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
-        if (!__all_sync(0xffffffffu, mbar_wait(acc_full, p & 1, abort_flag))) {
+        if (!__all_sync(0xffffffffu, wait_bar<kPair>(acc_full, p & 1, abort_flag))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int n_cols = pass_as(a.n_dm, j_pass, kNA) * kBeams;  // columns this pass wrote
+        // columns of the pass's a's that have trials
+        const int n_cols = pass_as(a.n_dm, j_pass, kNA, kT) * kBeams;
 #pragma unroll 1
         for (int c0 = 0; c0 < n_cols; c0 += 16) {
           uint32_t re[16], im[16];
           tmem_ld16x2(t_lanes + c0, t_lanes + kN + c0, re, im);
           // the 16 columns share a_in = c0 / kBeams; beams beta0 .. beta0 + 15
           const int bg0 = group * kBeams + c0 % kBeams;
-          const int jl = j_pass + (c0 / kBeams) * kM + b;
+          const int jl = j_pass + (c0 / kBeams) * kT + b;
           const int n_valid = a.n_series - bg0;  // beams of this chunk in range (may be <= 0)
           if (jl < a.n_dm && n_valid > 0) {
             const int64_t o0 = o_bin + static_cast<int64_t>(bg0) * a.y_series_stride +
@@ -388,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive_warp(acc_empty);
+        arrive_warp<kPair>(acc_empty);
       }
     }
     if (!ok) {
@@ -400,27 +536,28 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     // Producer warp pw (0..15) evaluates, for the channels nu = tile * kKCp +
     // kCpl * lane + cl (cl < kCpl: one channel per lane for 16-bit operands,
     // two adjacent ones for 8-bit, so every lane writes four bytes per row):
-    //   P_b for the 8 rows b = 8 pw .. 8 pw + 7 (one direct phasor, then the
-    //   recurrence P_{b+1} = P_b R with R = exp(2 pi i k v), at most 7 steps),
-    //   stored as the A_re and A_im rows (hi, and lo = P - hi);
-    //   Q_a for the pass's kNA a's as two chains of kNA / 2 (Q of each
-    //   chain's first a direct, then Q_{a+1} = Q_a R^128),
+    //   P_b for the 8 rows b = 128 rank + 8 pw .. + 7 (one direct phasor,
+    //   then the recurrence P_{b+1} = P_b R with R = exp(2 pi i k v), at most
+    //   7 steps), stored as the A_re and A_im rows (hi, and lo = P - hi);
+    //   Q_a for this CTA's a's of the pass as two chains (Q of each chain's
+    //   first a direct, then Q_{a+1} = Q_a R^T),
     //   Z_a = Q_a X for the beams beta = pw (and pw + 16 in 32-beam groups).
     // X and the phase constants run two tiles ahead.
     const int pw = warp - 1 - kEpiWarps;           // 0..15
     constexpr int kRows = kM / kProdWarps;         // P rows per warp (8)
     constexpr int kBeamsPerWarp = kBeams / kProdWarps;  // 1 or 2
-    constexpr int kHalfA = kNA / 2;                // a's per Q chain
+    constexpr int kHalfA = kNAc / 2;               // a's per Q chain
     // Store offsets that do not change between stages (see sw128): the P
-    // rows of this warp, and the B rows a_in * kBeams + pw + 16 m, whose
+    // rows of this warp, and the B rows a_local * kBeams + pw + 16 m, whose
     // position within an 8-row group is pw mod 8.  A lane's four bytes sit
     // at the same place for either operand width.
     const uint32_t lane_chunk = static_cast<uint32_t>((lane >> 2) << 4);
     const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
     const uint32_t z_base = sw128(pw, 2 * lane);  // row pw < 16
+    const uint32_t b_first = static_cast<uint32_t>(rank * kM + pw * kRows);  // first P row's b
     uint32_t s = 0;
     bool ok = true;
-    for (int k = blockIdx.x; k < a.n_bins && ok; k += gridDim.x) {
+    for (int k = unit; k < a.n_bins && ok; k += n_units) {
       // absolute bin of the phasors (groups of bins sharing a reference bin
       // under spin-frequency-dependent grids step by the group size)
       const uint32_t ku = static_cast<uint32_t>(a.k_begin + k * (a.k_step > 0 ? a.k_step : 1));
@@ -428,7 +565,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
       for (int it = 0; it < items_per_bin && ok; ++it) {
         const int group = it / n_pass;
         const int j_pass = (it % n_pass) * kDmsPass;
-        const int n_a = pass_as(a.n_dm, j_pass, kNA);  // a's of this pass
+        const int n_a = pass_as(a.n_dm, j_pass, kNA, kT);  // a's of this pass with trials
+        const int a_first = cta_first_a(n_a);              // this CTA's first a
+        const int n_mine = cta_as(n_a);                    // and its count
         auto load_pc = [&](int nn) {
           return nn < a.n_chan ? a.pc[nn] : PhaseConst{0u, 0u, 0u, 0u};
         };
@@ -440,6 +579,8 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                              static_cast<int64_t>(nn) * a.x_chan_stride)
                      : make_float2(0.f, 0.f);
         };
+        // a_local (< kNAc) is stored where this CTA holds it and it has trials
+        auto keep = [&](int a_local) { return a_local < n_mine && a_first + a_local < n_a; };
         PhaseConst pc_n1[kCpl], pc_n2[kCpl];
         float2 x_n1[kCpl][kBeamsPerWarp], x_n2[kCpl][kBeamsPerWarp];
 #pragma unroll
@@ -474,24 +615,26 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             }
           }
           // phasors in registers before touching the stage (zero beyond n_chan)
-          float2 r1[kCpl], pb[kCpl], r128[kCpl], qa[kCpl], qb[kCpl];
+          float2 r1[kCpl], pb[kCpl], rT[kCpl], qa[kCpl], qb[kCpl];
 #pragma unroll
           for (int cl = 0; cl < kCpl; ++cl) {
-            r1[cl] = pb[cl] = r128[cl] = qa[cl] = qb[cl] = make_float2(0.f, 0.f);
+            r1[cl] = pb[cl] = rT[cl] = qa[cl] = qb[cl] = make_float2(0.f, 0.f);
             if (nu0 + cl < a.n_chan) {
               const PhaseConst& q = pc[cl];
               r1[cl] = unit_phasor(top32_mul(ku, q.v_lo, q.v_hi));
-              pb[cl] = unit_phasor(top32_mul(ku * static_cast<uint32_t>(pw * kRows), q.v_lo, q.v_hi));
-              r128[cl] = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kM), q.v_lo, q.v_hi));
-              const uint32_t ja = static_cast<uint32_t>(a.j_begin + j_pass);
+              pb[cl] = unit_phasor(top32_mul(ku * b_first, q.v_lo, q.v_hi));
+              rT[cl] = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kT), q.v_lo, q.v_hi));
+              const uint32_t ja =
+                  static_cast<uint32_t>(a.j_begin + j_pass + a_first * kT);  // first a's trial
               const uint32_t ph_u = top32_mul(ku, q.u_lo, q.u_hi);
               qa[cl] = unit_phasor(ph_u + top32_mul(ku * ja, q.v_lo, q.v_hi));
-              qb[cl] = unit_phasor(ph_u + top32_mul(ku * (ja + static_cast<uint32_t>(kHalfA * kM)),
+              qb[cl] = unit_phasor(ph_u + top32_mul(ku * (ja + static_cast<uint32_t>(kHalfA * kT)),
                                                     q.v_lo, q.v_hi));
             }
           }
           const uint32_t st = s % kStages;
-          if (!__all_sync(0xffffffffu, mbar_wait(&empty[st], ((s / kStages) & 1) ^ 1, abort_flag))) {
+          if (!__all_sync(0xffffffffu,
+                          wait_bar<kPair>(&empty[st], ((s / kStages) & 1) ^ 1, abort_flag))) {
             ok = false;
             break;
           }
@@ -537,23 +680,23 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
               const __half2 qbs = __floats2half2_rn(-qb[0].y, qb[0].x);
 #pragma unroll
               for (int m = 0; m < kBeamsPerWarp; ++m) {
-                // (a's beyond the pass's last one are not read by its MMAs)
-                if (al < n_a) {
+                // (a's this CTA does not hold, or without trials, are not read by its MMAs)
+                if (keep(al)) {
                   const __half2 za = __hfma2(xr2[m], qa2, __hmul2(xi2[m], qas));
                   const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
                   *reinterpret_cast<__half2*>(tb + z_base + ra) = za;
                 }
-                if (al + kHalfA < n_a) {
+                if (keep(al + kHalfA)) {
                   const __half2 zb = __hfma2(xr2[m], qb2, __hmul2(xi2[m], qbs));
                   const uint32_t rb =
                       static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
                   *reinterpret_cast<__half2*>(tb + z_base + rb) = zb;
                 }
               }
-              qa[0] = __ffma2_rn(make_float2(-qa[0].y, qa[0].x), make_float2(r128[0].y, r128[0].y),
-                                 __fmul2_rn(qa[0], make_float2(r128[0].x, r128[0].x)));
-              qb[0] = __ffma2_rn(make_float2(-qb[0].y, qb[0].x), make_float2(r128[0].y, r128[0].y),
-                                 __fmul2_rn(qb[0], make_float2(r128[0].x, r128[0].x)));
+              qa[0] = __ffma2_rn(make_float2(-qa[0].y, qa[0].x), make_float2(rT[0].y, rT[0].y),
+                                 __fmul2_rn(qa[0], make_float2(rT[0].x, rT[0].x)));
+              qb[0] = __ffma2_rn(make_float2(-qb[0].y, qb[0].x), make_float2(rT[0].y, rT[0].y),
+                                 __fmul2_rn(qb[0], make_float2(rT[0].x, rT[0].x)));
             }
           } else {
 #pragma unroll
@@ -570,25 +713,30 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
                 zb[cl] = __ffma2_rn(make_float2(-xv.y, xv.y), make_float2(qb[cl].y, qb[cl].x),
                                     __fmul2_rn(make_float2(xv.x, xv.x), qb[cl]));
               }
-              // row a_in * kBeams + pw + 16 m: z_base + (kBeams / 8 * a_in + 2 m) groups
-              // (a's beyond the pass's last one are not read by its MMAs)
+              // row a_local * kBeams + pw + 16 m: z_base + (kBeams / 8 * a_local + 2 m) groups
+              // (a's this CTA does not hold, or without trials, are not read by its MMAs)
               const uint32_t ra = static_cast<uint32_t>((kBeams / 8 * al + 2 * m) * 1024);
               const uint32_t rb = static_cast<uint32_t>((kBeams / 8 * (al + kHalfA) + 2 * m) * 1024);
-              if (al < n_a) *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack_word<kPrec, kCpl>(za);
-              if (al + kHalfA < n_a)
+              if (keep(al)) *reinterpret_cast<uint32_t*>(tb + z_base + ra) = pack_word<kPrec, kCpl>(za);
+              if (keep(al + kHalfA))
                 *reinterpret_cast<uint32_t*>(tb + z_base + rb) = pack_word<kPrec, kCpl>(zb);
             }
 #pragma unroll
             for (int cl = 0; cl < kCpl; ++cl) {
-              qa[cl] = __ffma2_rn(make_float2(-qa[cl].y, qa[cl].x), make_float2(r128[cl].y, r128[cl].y),
-                                  __fmul2_rn(qa[cl], make_float2(r128[cl].x, r128[cl].x)));
-              qb[cl] = __ffma2_rn(make_float2(-qb[cl].y, qb[cl].x), make_float2(r128[cl].y, r128[cl].y),
-                                  __fmul2_rn(qb[cl], make_float2(r128[cl].x, r128[cl].x)));
+              qa[cl] = __ffma2_rn(make_float2(-qa[cl].y, qa[cl].x), make_float2(rT[cl].y, rT[cl].y),
+                                  __fmul2_rn(qa[cl], make_float2(rT[cl].x, rT[cl].x)));
+              qb[cl] = __ffma2_rn(make_float2(-qb[cl].y, qb[cl].x), make_float2(rT[cl].y, rT[cl].y),
+                                  __fmul2_rn(qb[cl], make_float2(rT[cl].x, rT[cl].x)));
             }
           }
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (!a.test_withhold) mbar_arrive_warp(&full[st]);
+          // this thread's stores before the MMAs' reads (async proxy), here
+          // or, for the second CTA of a pair, from the first CTA's MMA warp
+          if constexpr (kPair)
+            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+          else
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (!a.test_withhold) arrive_warp<kPair>(&full[st]);
         }
       }
     }
@@ -600,10 +748,17 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // a pair: the first CTA's MMAs have drained (its warp 0 waited above) and
+  // no thread of either CTA arrives remotely any more
+  if constexpr (kPair) cluster_sync();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols));
+    if constexpr (kPair)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols));
   }
 }
 
@@ -613,23 +768,70 @@ size_t mac_tc_smem_bytes() { return kRingBytes + 1024 + 128; }
 
 int mac_tc_beams_per_group(int n_series) { return n_series <= 16 ? 16 : 32; }
 
+// Calls run the CTA-pair form (trials per pass of its T = 256); the
+// one-CTA form only where no cluster of two fits the device.
 int mac_tc_trials_per_pass(int n_series) {
-  return mac_tc_beams_per_group(n_series) == 16 ? dms_per_pass<16>() : dms_per_pass<32>();
+  return mac_tc_beams_per_group(n_series) == 16 ? dms_per_pass<16, true>()
+                                                : dms_per_pass<32, true>();
 }
 
+int mac_tc_trials_per_a() { return trials_per_a<true>(); }
+
+namespace {
+template <int kPrec, int kBeams, bool kPair>
+const void* tc_fn() {
+  return reinterpret_cast<const void*>(&mac_tc_kernel<kPrec, kBeams, kPair>);
+}
+template <bool kPair>
+const void* tc_fn(int prec, bool g16) {
+  switch (prec) {
+    case kBf16HiLo: return g16 ? tc_fn<kBf16HiLo, 16, kPair>() : tc_fn<kBf16HiLo, 32, kPair>();
+    case kBf16: return g16 ? tc_fn<kBf16, 16, kPair>() : tc_fn<kBf16, 32, kPair>();
+    case kF16: return g16 ? tc_fn<kF16, 16, kPair>() : tc_fn<kF16, 32, kPair>();
+    default: return g16 ? tc_fn<kF8, 16, kPair>() : tc_fn<kF8, 32, kPair>();
+  }
+}
+cudaLaunchConfig_t pair_config(int n_pairs, cudaLaunchAttribute* attr, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * n_pairs);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = mac_tc_smem_bytes();
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+// Pairs resident at once per pair kernel (precision x group size), per device
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_pairs[kMaxDevices][8];
+}  // namespace
+
 cudaError_t mac_tc_prepare() {
-  const void* fns[] = {reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 32>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 32>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 32>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 16>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 16>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 16>),
-                       reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)};
-  for (const void* fn : fns) {
-    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(mac_tc_smem_bytes()));
-    if (e != cudaSuccess) return e;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  for (int prec = 0; prec < 4; ++prec) {
+    for (int g = 0; g < 2; ++g) {
+      for (const void* fn : {tc_fn<false>(prec, g == 1), tc_fn<true>(prec, g == 1)}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(mac_tc_smem_bytes()));
+        if (e != cudaSuccess) return e;
+      }
+      if (dev < kMaxDevices) {
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = pair_config(1, attr, nullptr);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_fn<true>(prec, g == 1), &cfg) != cudaSuccess) {
+          cudaGetLastError();
+          n = 0;
+        }
+        g_pairs[dev][prec * 2 + g].store(n);
+      }
+    }
   }
   return cudaSuccess;
 }
@@ -761,26 +963,25 @@ cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* sc
 }
 
 static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cudaStream_t s) {
-  const int grid = a.n_bins < n_sms ? a.n_bins : n_sms;
   MacArgs args = a;
   void* params[] = {&args};
   const bool g16 = mac_tc_beams_per_group(a.n_series) == 16;
-  const void* fn;
-  if (prec == kBf16HiLo)
-    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 16>)
-             : reinterpret_cast<const void*>(&mac_tc_kernel<kBf16HiLo, 32>);
-  else if (prec == kBf16)
-    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 16>)
-             : reinterpret_cast<const void*>(&mac_tc_kernel<kBf16, 32>);
-  else if (prec == kF16)
-    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 16>)
-             : reinterpret_cast<const void*>(&mac_tc_kernel<kF16, 32>);
-  else
-    fn = g16 ? reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 16>)
-             : reinterpret_cast<const void*>(&mac_tc_kernel<kF8, 32>);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // persistent pairs: as many as are resident at once, at most one per bin
+  int n_pairs = dev < kMaxDevices ? g_pairs[dev][prec * 2 + (g16 ? 1 : 0)].load() : 0;
+  if (n_pairs > n_sms / 2) n_pairs = n_sms / 2;
+  if (n_pairs > a.n_bins) n_pairs = a.n_bins;
   note_launches(1);
-  return cudaLaunchKernel(fn, dim3(grid),
-                          dim3(kThreads), params, mac_tc_smem_bytes(), s);
+  if (n_pairs >= 1) {
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = pair_config(n_pairs, attr, s);
+    return cudaLaunchKernelExC(&cfg, tc_fn<true>(prec, g16), params);
+  }
+  const int grid = a.n_bins < n_sms ? a.n_bins : n_sms;
+  return cudaLaunchKernel(tc_fn<false>(prec, g16), dim3(grid), dim3(kThreads), params,
+                          mac_tc_smem_bytes(), s);
 }
 
 }  // namespace fdd

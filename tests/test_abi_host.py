@@ -172,25 +172,30 @@ def test_variant_choice():
 
 def test_tensor_core_form_geometry():
     """The tensor-core form holds the spectra of every beam at once and batches
-    DMs in whole trial passes (1024 trials in 32-beam groups, 2048 in 16-beam
-    groups) when the workspace is bounded; below one pass, whatever fits."""
+    DMs in whole trial passes (2048 trials in 32-beam groups, 4096 in 16-beam
+    groups; T = 256 trials per a on a CTA pair) when the workspace is
+    bounded; below one pass, whole a's, and below one a whatever fits."""
     w = synth.WORKLOADS["fdd_32beam_1024ch_2p19t_4096dm"]
     g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
                                       workspace_limit=200 << 30))
     assert g["mac_variant"] == fdd.FDD_MAC_TC
-    assert g["dm_batch"] % 1024 == 0 and 0 < g["dm_batch"] <= 4096
+    assert g["dm_batch"] % 256 == 0 and 0 < g["dm_batch"] <= 4096
     spectra = 32 * 1024 * g["bin_pitch"] * 8
     assert spectra < g["workspace_bytes"] <= 200 << 30
     g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
                                       workspace_limit=120 << 30))
-    assert 512 < g["dm_batch"] < 1024 and g["workspace_bytes"] <= 120 << 30
+    assert g["dm_batch"] % 256 == 0 and 256 <= g["dm_batch"] < 2048
+    assert g["workspace_bytes"] <= 120 << 30
     g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
                                       workspace_limit=72 << 30))
-    assert 0 < g["dm_batch"] < 512 and g["workspace_bytes"] <= 72 << 30
-    # 16 beams: 2048-trial passes
+    assert 0 < g["dm_batch"] < 256 and g["workspace_bytes"] <= 72 << 30
+    # 16 beams: 4096-trial passes; 120 GiB holds 8 a's
     g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=fdd.FDD_PREC_BF16_HILO,
                                       workspace_limit=120 << 30))
     assert g["dm_batch"] == 2048 and g["workspace_bytes"] <= 120 << 30
+    g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=fdd.FDD_PREC_BF16_HILO,
+                                      workspace_limit=200 << 30))
+    assert g["dm_batch"] == 4096
 
 
 def test_geometry_edge_cases():
