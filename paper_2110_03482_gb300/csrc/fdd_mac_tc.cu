@@ -78,13 +78,14 @@ constexpr int kThreads = 32 + 32 * kEpiWarps + 32 * kProdWarps;
 constexpr uint32_t kTileA = kM * 64 * 2;  // 16 KB
 constexpr uint32_t kTileB = kN * 64 * 2;  // 32 KB
 constexpr uint32_t kRingBytes = 192 * 1024;
-// Stage layout: A_re hi, A_im hi (, A_re lo, A_im lo), then B.
-template <bool kHiLo>
+// Stage layout: A_re hi, A_im hi (, A_re lo, A_im lo), then B (a CTA of a
+// pair holds half of B's rows).
+template <bool kHiLo, bool kPair>
 struct Ring {
   static constexpr int kATiles = kHiLo ? 4 : 2;
   static constexpr uint32_t kBOff = kATiles * kTileA;
-  static constexpr uint32_t kStageBytes = kBOff + kTileB;       // 96 or 64 KB
-  static constexpr int kStages = kRingBytes / kStageBytes;      // 2 or 3
+  static constexpr uint32_t kStageBytes = kBOff + (kPair ? kTileB / 2 : kTileB);
+  static constexpr int kStages = kRingBytes / kStageBytes;  // 2 or 3; a pair 2 or 4
 };
 constexpr uint32_t kTmemCols = 2 * kN;   // D_re | D_im
 
@@ -283,17 +284,6 @@ __device__ __forceinline__ uint32_t cluster_count() {
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
 }
-// One arrive for the whole (converged) warp on the barrier at this offset in
-// the pair's first CTA (release at cluster scope).
-__device__ __forceinline__ void mbar_arrive_warp_first(uint64_t* bar) {
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) {
-    uint32_t remote;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(smem_u32(bar)));
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
-                 : "memory");
-  }
-}
 // Bounded wait at cluster scope (arrivals from the other CTA of the pair).
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity,
                                                   volatile int* abort_flag) {
@@ -318,13 +308,6 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
   else
     return mbar_wait(bar, parity, abort_flag);
 }
-template <bool kPair>
-__device__ __forceinline__ void arrive_warp(uint64_t* bar) {
-  if constexpr (kPair)
-    mbar_arrive_warp_first(bar);
-  else
-    mbar_arrive_warp(bar);
-}
 
 // 21 warps at one CTA per SM: one of the four schedulers holds six of them,
 // and a scheduler's 16384 registers cap the kernel at 80 per thread.
@@ -335,9 +318,12 @@ __device__ __forceinline__ void arrive_warp(uint64_t* bar) {
 // time with T = 256: the first CTA's MMA warp issues M = 256 MMAs over both
 // CTAs (rows b < 128 from the first CTA, the rest from the second), each CTA
 // builds its own 128 rows of P and half of the pass's Z columns (the first
-// or the second half of its a's), so a CTA builds a third fewer operand
-// values per MMA than alone; its producers and epilogue arrive on the first
-// CTA's barriers, and the MMAs' completion reaches both CTAs' barriers.
+// or the second half of its a's), so a CTA builds half the Z values per MMA
+// it would alone.  Producers and epilogue warps arrive on their own CTA's
+// barriers; in the second CTA one thread of warp 0 forwards each completed
+// stage and read-out to the first CTA's barriers (one cluster-scope release
+// per stage instead of one per producer warp, which cost more than the
+// pairing saved), and the MMAs' completion reaches both CTAs' barriers.
 template <int kPrec, int kBeams, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   static_assert(kBeams == 16 || kBeams == 32, "groups of 16 or 32 beams");
@@ -349,9 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   constexpr int kNA = kN / kBeams;            // a's per pass (8 or 16)
   constexpr int kNAc = kPair ? kNA / 2 : kNA;  // a's whose Z this CTA builds
   constexpr int kDmsPass = dms_per_pass<kBeams, kPair>();
-  constexpr int kStages = Ring<kHiLo>::kStages;
-  constexpr uint32_t kStageBytes = Ring<kHiLo>::kStageBytes;
-  constexpr uint32_t kBOff = Ring<kHiLo>::kBOff;
+  constexpr int kStages = Ring<kHiLo, kPair>::kStages;
+  constexpr uint32_t kStageBytes = Ring<kHiLo, kPair>::kStageBytes;
+  constexpr uint32_t kBOff = Ring<kHiLo, kPair>::kBOff;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -373,11 +359,13 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   constexpr int kCtas = kPair ? 2 : 1;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&full[i], kCtas * kProdWarps);  // one arrive per producer warp of the pair
+      // one arrive per producer warp; in a pair's first CTA one more from the
+      // second CTA's forwarder
+      mbar_init(&full[i], kProdWarps + (kPair && rank == 0 ? 1 : 0));
       mbar_init(&empty[i], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kCtas * kEpiWarps);    // one arrive per epilogue warp of the pair
+    mbar_init(acc_empty, kEpiWarps + (kPair && rank == 0 ? 1 : 0));  // likewise
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -466,6 +454,44 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
         volatile int never = 0;
         mbar_wait(drain, 0, &never);
       }
+    } else if (kPair && lane == 0) {
+      // forwarder of a pair's second CTA: each stage its producers filled and
+      // each pass its epilogue read out (their arrives, CTA scope) is passed
+      // on as one arrive on the first CTA's barrier at cluster scope, so that
+      // no producer or epilogue warp waits on a cluster-scope release of its
+      // own loads and stores in flight
+      uint32_t s = 0, p = 0;
+      bool ok = true;
+      auto forward = [&](uint64_t* bar) {
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(smem_u32(bar)));
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
+                     : "memory");
+      };
+      for (int k = unit; k < a.n_bins && ok; k += n_units) {
+        for (int it = 0; it < items_per_bin && ok; ++it, ++p) {
+          // the previous pass read out here (the first CTA's MMAs wait for it)
+          if (p > 0) {
+            if (!mbar_wait(acc_empty, (p - 1) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            forward(acc_empty);
+          }
+          for (int t = 0; t < n_tiles; ++t, ++s) {
+            const uint32_t st = s % kStages;
+            if (!mbar_wait(&full[st], (s / kStages) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            forward(&full[st]);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (a.status) atomicExch(a.status, FDD_ERR_TIMEOUT);
+      }
     }
   } else if (warp <= kEpiWarps) {
     // ------------------------------------------------------------ epilogue
@@ -524,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        arrive_warp<kPair>(acc_empty);
+        mbar_arrive_warp(acc_empty);  // (a pair's second CTA forwards it)
       }
     }
     if (!ok) {
@@ -730,13 +756,10 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
             }
           }
           }
-          // this thread's stores before the MMAs' reads (async proxy), here
-          // or, for the second CTA of a pair, from the first CTA's MMA warp
-          if constexpr (kPair)
-            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
-          else
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (!a.test_withhold) arrive_warp<kPair>(&full[st]);
+          // this thread's stores before the MMAs' reads (async proxy); the
+          // arrive is local (a pair's second CTA forwards the stage)
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (!a.test_withhold) mbar_arrive_warp(&full[st]);
         }
       }
     }
