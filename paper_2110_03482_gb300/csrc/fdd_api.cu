@@ -433,10 +433,12 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
     const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
     if (fit < batch) {
       // whole kernel passes (tensor cores) or trial blocks; below one pass,
-      // whole a's of the tensor-core tile, else whatever fits
+      // pairs of a's of the tensor-core tile (no padded a), else one a,
+      // else whatever fits
       const int64_t blk = tc ? fdd::mac_tc_trials_per_pass(p->n_beams)
                              : fdd::mac_variant_trials_per_block(g->mac_variant);
-      const int64_t sub = tc ? fdd::mac_tc_trials_per_a() : blk;
+      const int64_t ta = tc ? fdd::mac_tc_trials_per_a() : blk;
+      const int64_t sub = fit >= 2 * ta ? 2 * ta : ta;
       batch = fit >= blk ? fit / blk * blk : fit >= sub ? fit / sub * sub : fit;
     }
     if (batch > 65535) batch = 65535 / 64 * 64;
@@ -459,7 +461,9 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
                             : fdd::mac_variant_trials_per_block(g->mac_variant);
     const size_t cap = std::min<size_t>(size_t(4) << 30, limit / 4);
     int64_t bd = static_cast<int64_t>(cap / per_trial) / pass * pass;
-    if (bd < pass) bd = pass;
+    // at least one pass, or half of a tensor-core pass (one pass of the
+    // one-CTA form) where two blocks of a whole one would exceed half the limit
+    if (bd < pass) bd = (!tc || per_trial * static_cast<size_t>(pass) <= limit / 4) ? pass : pass / 2;
     if (bd > p->n_dm) bd = p->n_dm;
     g->block_dm = static_cast<int32_t>(bd);
     blk_bytes = per_trial * static_cast<size_t>(bd);
