@@ -92,7 +92,15 @@ typedef enum fdd_status {
                                of <= 1024 / <= 512 trials runs as wide items of
                                8 / 16 bins (default from 257 trials)            */
 #define FDD_MAC_VARIANTS 6
-#define FDD_MAC_TC 100     /* fdd_info.mac_variant of the tensor-core form       */
+#define FDD_MAC_TC 100      /* fdd_info.mac_variant of the tensor-core form: one
+                               CTA per SM, T = 128 trials per a (see below)      */
+#define FDD_MAC_TC_PAIR 101 /* the same on pairs of CTAs (two SMs, one MMA of
+                               M = 256, T = 256), each building half of the data
+                               operand: plans of more trials than one pass of
+                               the one-CTA form (1024 trials with more than 16
+                               beams, else 2048) whose streamed output blocks
+                               of one pair pass fit a quarter of workspace_limit
+                               (time output: whose DM batch is that long)      */
 
 /* fdd_params.precision */
 #define FDD_PREC_FP32 0      /* FP32 phasors and accumulation (CUDA cores)       */

@@ -47,6 +47,7 @@ for _i, _n in enumerate(MAC_VARIANT_NAMES):
     globals()["FDD_MAC_" + _n.upper()] = _i
 FDD_MAC_VARIANTS = len(MAC_VARIANT_NAMES)
 FDD_MAC_TC = 100
+FDD_MAC_TC_PAIR = 101
 
 # Every symbol include/fdd.h declares.
 EXPORTS = [

@@ -413,6 +413,11 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   const bool tc = p->precision != FDD_PREC_FP32;
   g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
                                                      : fdd::mac_variant_for(p->n_dm, nc));
+  // tensor cores: the CTA-pair form for calls of more trials than one pass
+  // of the one-CTA form (fewer leave the pair's larger T more phasor rows per
+  // output); a plan keeps one form, so its streamed and whole calls agree
+  bool pair = tc && p->spin_group == 0 &&
+              p->n_dm > fdd::mac_tc_trials_per_pass(p->n_beams, false);
   if (!tc && fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
     return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
 
@@ -432,17 +437,33 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
                   fixed + per_dm);
     const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
     if (fit < batch) {
-      // whole kernel passes (tensor cores) or trial blocks; below one pass,
-      // pairs of a's of the tensor-core tile (no padded a), else one a,
-      // else whatever fits
-      const int64_t blk = tc ? fdd::mac_tc_trials_per_pass(p->n_beams)
+      // whole kernel passes or trial blocks; below one pass of the CTA-pair
+      // form, pairs of its a's (no padded a) while that is more than one
+      // pass of the one-CTA form, else that form's whole passes, else
+      // whatever fits
+      const int64_t blk = tc ? fdd::mac_tc_trials_per_pass(p->n_beams, pair)
                              : fdd::mac_variant_trials_per_block(g->mac_variant);
-      const int64_t ta = tc ? fdd::mac_tc_trials_per_a() : blk;
-      const int64_t sub = fit >= 2 * ta ? 2 * ta : ta;
-      batch = fit >= blk ? fit / blk * blk : fit >= sub ? fit / sub * sub : fit;
+      batch = fit >= blk ? fit / blk * blk : fit;
+      if (pair && fit < blk) {
+        const int64_t two_a = 2 * fdd::mac_tc_trials_per_a(true);
+        const int64_t one = fdd::mac_tc_trials_per_pass(p->n_beams, false);
+        batch = fit / two_a * two_a;
+        if (batch <= one) {
+          pair = false;
+          batch = fit >= one ? fit / one * one : fit;
+        }
+      }
     }
     if (batch > 65535) batch = 65535 / 64 * 64;
+  } else if (pair) {
+    // streamed blocks are whole passes: the pair's only where two blocks of
+    // one pass stay within half the limit
+    const size_t per_trial = (p->output == FDD_OUT_SPECTRA ? 8 : 4) * spectra_sets *
+                             static_cast<size_t>(n_bins);
+    if (per_trial * static_cast<size_t>(fdd::mac_tc_trials_per_pass(p->n_beams, true)) > limit / 4)
+      pair = false;
   }
+  if (tc) g->mac_variant = pair ? FDD_MAC_TC_PAIR : FDD_MAC_TC;
   g->dm_batch = static_cast<int32_t>(batch);
   g->workspace_bytes = static_cast<int64_t>(fixed + per_dm * batch);
   // Streamed calls: output blocks of one beam's DM batch (time), or of
@@ -457,13 +478,11 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   } else {
     const size_t per_trial = (p->output == FDD_OUT_SPECTRA ? 8 : 4) * spectra_sets *
                              static_cast<size_t>(n_bins);
-    const int64_t pass = tc ? fdd::mac_tc_trials_per_pass(p->n_beams)
+    const int64_t pass = tc ? fdd::mac_tc_trials_per_pass(p->n_beams, pair)
                             : fdd::mac_variant_trials_per_block(g->mac_variant);
     const size_t cap = std::min<size_t>(size_t(4) << 30, limit / 4);
     int64_t bd = static_cast<int64_t>(cap / per_trial) / pass * pass;
-    // at least one pass, or half of a tensor-core pass (one pass of the
-    // one-CTA form) where two blocks of a whole one would exceed half the limit
-    if (bd < pass) bd = (!tc || per_trial * static_cast<size_t>(pass) <= limit / 4) ? pass : pass / 2;
+    if (bd < pass) bd = pass;
     if (bd > p->n_dm) bd = p->n_dm;
     g->block_dm = static_cast<int32_t>(bd);
     blk_bytes = per_trial * static_cast<size_t>(bd);
@@ -935,6 +954,7 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
       FDD_CUDA(fdd::launch_bin_transpose(t, s));
     }
     fdd::MacArgs m{};
+    m.tc_pair = P->info.mac_variant == FDD_MAC_TC_PAIR;
     m.X = P->d_X;
     m.x_bin_stride = rows;
     m.x_series_stride = p.n_chan;
@@ -1282,6 +1302,7 @@ fdd_status fdd_debug_stall_test(fdd_plan_t plan, fdd_stream_t stream) {
   void* y = nullptr;
   FDD_CUDA(cudaMalloc(&y, 64));
   fdd::MacArgs m{};
+  m.tc_pair = plan->info.mac_variant == FDD_MAC_TC_PAIR;
   m.X = plan->d_X;
   m.x_chan_stride = plan->info.bin_pitch;
   m.x_series_stride = plan->info.bin_pitch * plan->p.n_chan;
@@ -1410,6 +1431,7 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
   if (st != FDD_OK) return st;
   if ((st = need_uniform_grid(plan)) != FDD_OK) return st;
   fdd::MacArgs m{};
+  m.tc_pair = plan->info.mac_variant == FDD_MAC_TC_PAIR;
   m.X = static_cast<const float2*>(d_X);
   m.x_chan_stride = x_pitch;
   m.x_series_stride = x_pitch * plan->p.n_chan;

@@ -49,6 +49,7 @@ struct MacArgs {
                             // |re| or |im| of the spectra (sets that bin's data scale)
   int absmax_ready;         // tensor cores in FP16: the scratch already holds the
                             // per-bin maxima of these spectra (a later DM batch)
+  int tc_pair;              // tensor cores: the CTA-pair form (the plan's choice)
 };
 
 // Kernel variants of the FP32 phasor-MAC (see fdd_mac_fp32.cu and the
@@ -94,17 +95,18 @@ cudaError_t launch_mac_fp32(const MacArgs& a, int variant, cudaStream_t s);
 size_t mac_smem_bytes(int variant, int n_chan);
 
 // Tensor-core phase-rotate-and-sum (fdd_mac_tc.cu): 16-bit (or FP8)
-// phasors and data, FP32 accumulation in tensor memory; persistent pairs of
-// CTAs (one per SM), each pair on one bin at a time.
+// phasors and data, FP32 accumulation in tensor memory; persistent CTAs (one
+// per SM), alone or in pairs (one bin per pair at a time).
 size_t mac_tc_smem_bytes();
-// trials of one pass over the channels, and of one a (T = 256)
-int mac_tc_trials_per_pass(int n_series);
-int mac_tc_trials_per_a();
+// trials of one pass over the channels, and of one a (T = 128, or 256 for
+// the CTA-pair form)
+int mac_tc_trials_per_pass(int n_series, bool pair);
+int mac_tc_trials_per_a(bool pair);
 // Sets the kernels' shared-memory limit and counts the pairs resident at once
 // on the current device (before the first call on it).
 cudaError_t mac_tc_prepare();
 // Beams per tensor-core group: 16 when a call has at most 16 series (then a
-// pass covers 4096 trials), else 32 (2048 trials per pass).
+// pass covers 2048 trials, 4096 for a pair), else 32 (1024, 2048).
 int mac_tc_beams_per_group(int n_series);
 // The tensor-core kernel reads the spectra bin-major, X_T[k][series][chan]
 // (a 256-byte row per 32 channels of one beam), and writes Y bin-major,

@@ -791,16 +791,13 @@ size_t mac_tc_smem_bytes() { return kRingBytes + 1024 + 128; }
 
 int mac_tc_beams_per_group(int n_series) { return n_series <= 16 ? 16 : 32; }
 
-// Calls of more trials than one pass of the one-CTA form run the CTA-pair
-// form (passes of its T = 256; both forms' passes are whole pairs of its
-// a's); the others, and all where no cluster of two fits the device, the
-// one-CTA form.
-int mac_tc_trials_per_pass(int n_series) {
-  return mac_tc_beams_per_group(n_series) == 16 ? dms_per_pass<16, true>()
-                                                : dms_per_pass<32, true>();
+int mac_tc_trials_per_pass(int n_series, bool pair) {
+  const bool g16 = mac_tc_beams_per_group(n_series) == 16;
+  return pair ? (g16 ? dms_per_pass<16, true>() : dms_per_pass<32, true>())
+              : (g16 ? dms_per_pass<16, false>() : dms_per_pass<32, false>());
 }
 
-int mac_tc_trials_per_a() { return trials_per_a<true>(); }
+int mac_tc_trials_per_a(bool pair) { return pair ? trials_per_a<true>() : trials_per_a<false>(); }
 
 namespace {
 template <int kPrec, int kBeams, bool kPair>
@@ -994,11 +991,10 @@ static cudaError_t launch_mac_tc_block(const MacArgs& a, int prec, int n_sms, cu
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  // persistent pairs: as many as are resident at once, at most one per bin;
-  // only for calls of more than one pass of the one-CTA form (at most that
-  // many trials, the pair's larger T leaves more phasor rows per output)
+  // the CTA-pair form where the plan chose it: persistent pairs, as many as
+  // are resident at once, at most one per bin (none fit: the one-CTA form)
   int n_pairs = dev < kMaxDevices ? g_pairs[dev][prec * 2 + (g16 ? 1 : 0)].load() : 0;
-  if (a.n_dm <= (g16 ? dms_per_pass<16, false>() : dms_per_pass<32, false>())) n_pairs = 0;
+  if (!a.tc_pair) n_pairs = 0;
   if (n_pairs > n_sms / 2) n_pairs = n_sms / 2;
   if (n_pairs > a.n_bins) n_pairs = a.n_bins;
   note_launches(1);

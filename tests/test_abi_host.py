@@ -172,30 +172,44 @@ def test_variant_choice():
 
 def test_tensor_core_form_geometry():
     """The tensor-core form holds the spectra of every beam at once and batches
-    DMs in whole trial passes (2048 trials in 32-beam groups, 4096 in 16-beam
-    groups; T = 256 trials per a on a CTA pair) when the workspace is
-    bounded; below one pass, whole a's, and below one a whatever fits."""
+    DMs in whole trial passes when the workspace is bounded.  Plans of more
+    trials than one pass of the one-CTA form (1024 trials in 32-beam groups,
+    2048 in 16-beam groups) take the CTA-pair form (passes of 2048 / 4096,
+    T = 256 trials per a), with time output while its DM batch stays above
+    that one pass (below a pair pass: pairs of a's), with spectra or power
+    while two output blocks of one pair pass fit half the limit; below one
+    pass of the one-CTA form, whatever fits."""
     w = synth.WORKLOADS["fdd_32beam_1024ch_2p19t_4096dm"]
-    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
-                                      workspace_limit=200 << 30))
-    assert g["mac_variant"] == fdd.FDD_MAC_TC
-    assert g["dm_batch"] % 256 == 0 and 0 < g["dm_batch"] <= 4096
+    hilo = fdd.FDD_PREC_BF16_HILO
+    g = fdd.fdd_plan_geometry(_params(w, precision=hilo, workspace_limit=200 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC_PAIR
+    assert g["dm_batch"] == 1536  # 1941 fit: 6 a's of 256
     spectra = 32 * 1024 * g["bin_pitch"] * 8
     assert spectra < g["workspace_bytes"] <= 200 << 30
-    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
-                                      workspace_limit=120 << 30))
-    assert g["dm_batch"] % 256 == 0 and 256 <= g["dm_batch"] < 2048
-    assert g["workspace_bytes"] <= 120 << 30
-    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_BF16_HILO,
-                                      workspace_limit=72 << 30))
+    g = fdd.fdd_plan_geometry(_params(w, precision=hilo, workspace_limit=120 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC
+    assert 512 < g["dm_batch"] < 1024 and g["workspace_bytes"] <= 120 << 30
+    g = fdd.fdd_plan_geometry(_params(w, precision=hilo, workspace_limit=72 << 30))
     assert 0 < g["dm_batch"] < 256 and g["workspace_bytes"] <= 72 << 30
-    # 16 beams: 4096-trial passes; 120 GiB holds 8 a's
-    g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=fdd.FDD_PREC_BF16_HILO,
-                                      workspace_limit=120 << 30))
-    assert g["dm_batch"] == 2048 and g["workspace_bytes"] <= 120 << 30
-    g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=fdd.FDD_PREC_BF16_HILO,
+    # one pass of the one-CTA form: that form
+    g = fdd.fdd_plan_geometry(_params(w, precision=hilo, dm_list=0.5 * np.arange(1024),
                                       workspace_limit=200 << 30))
-    assert g["dm_batch"] == 4096
+    assert g["mac_variant"] == fdd.FDD_MAC_TC and g["dm_batch"] == 1024
+    # 16 beams: 4096-trial pair passes; 120 GiB holds 2048 trials, one
+    # one-CTA pass
+    g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=hilo, workspace_limit=120 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC
+    assert g["dm_batch"] == 2048 and g["workspace_bytes"] <= 120 << 30
+    g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=hilo, workspace_limit=200 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC_PAIR and g["dm_batch"] == 4096
+    # power of 32 beams: a pair pass's block (2048 x 32 x 262145 x 4 B) is
+    # above a quarter of 240 GiB, so the one-CTA form, blocks of its pass
+    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_FP16, output=fdd.FDD_OUT_POWER,
+                                      workspace_limit=240 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC and g["block_dm"] == 1024
+    g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_FP16, output=fdd.FDD_OUT_POWER,
+                                      workspace_limit=280 << 30))
+    assert g["mac_variant"] == fdd.FDD_MAC_TC_PAIR and g["block_dm"] == 2048
 
 
 def test_geometry_edge_cases():
