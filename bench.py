@@ -774,7 +774,8 @@ def run_mac_sweep(args) -> None:
         ns = w.n_beams if tc else 1
         kw = dict(plan_params(w, fdd), output=fdd.FDD_OUT_SPECTRA)
         if tc:
-            kw.update(precision=tc_prec[v], n_beams=ns)
+            kw.update(precision=tc_prec[v], n_beams=ns,
+                      workspace_limit=int(args.workspace_gib * (1 << 30)))
         else:
             kw.update(mac_variant=v + 1)
         with fdd.Plan(**kw) as plan:

@@ -96,11 +96,13 @@ typedef enum fdd_status {
                                CTA per SM, T = 128 trials per a (see below)      */
 #define FDD_MAC_TC_PAIR 101 /* the same on pairs of CTAs (two SMs, one MMA of
                                M = 256, T = 256), each building half of the data
-                               operand: plans of more trials than one pass of
-                               the one-CTA form (1024 trials with more than 16
-                               beams, else 2048) whose streamed output blocks
-                               of one pair pass fit a quarter of workspace_limit
-                               (time output: whose DM batch is that long)      */
+                               operand; a pass covers 2048 trials with more than
+                               16 beams, else 4096.  Plans whose calls end in a
+                               pass of this form that is full or more than half
+                               full take it: time output only in DM batches of
+                               whole passes, spectra and power only while an
+                               output block of one pass fits a quarter of
+                               workspace_limit                                 */
 
 /* fdd_params.precision */
 #define FDD_PREC_FP32 0      /* FP32 phasors and accumulation (CUDA cores)       */

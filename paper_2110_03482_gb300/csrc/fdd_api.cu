@@ -413,11 +413,19 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   const bool tc = p->precision != FDD_PREC_FP32;
   g->mac_variant = tc ? FDD_MAC_TC : (p->mac_variant ? p->mac_variant - 1
                                                      : fdd::mac_variant_for(p->n_dm, nc));
-  // tensor cores: the CTA-pair form for calls of more trials than one pass
-  // of the one-CTA form (fewer leave the pair's larger T more phasor rows per
-  // output); a plan keeps one form, so its streamed and whole calls agree
-  bool pair = tc && p->spin_group == 0 &&
-              p->n_dm > fdd::mac_tc_trials_per_pass(p->n_beams, false);
+  // tensor cores: the CTA-pair form where its passes are full enough.  A
+  // pass of either form costs a fixed part (the phasor rows P, evaluated per
+  // pass and CTA) plus a part per a (Z and the MMAs); measured on 32 beams x
+  // 1024 channels, the pair's pass (2048 trials) costs 375 + 12.2 per a of
+  // 256 trials, the one-CTA pass (1024 trials) 197 + 8.9 per a of 128: the
+  // pair wins on calls whose last pair pass is more than half full (or
+  // full).  A plan keeps one form, so its streamed and whole calls agree.
+  const int64_t pass2 = tc ? fdd::mac_tc_trials_per_pass(p->n_beams, true) : 0;
+  auto pair_wins = [&](int64_t n) {
+    const int64_t r = n % pass2;
+    return n > pass2 / 2 && (r == 0 || r > pass2 / 2);
+  };
+  bool pair = tc && p->spin_group == 0 && pair_wins(p->n_dm);
   if (!tc && fdd::mac_smem_bytes(g->mac_variant, nc) > kMaxSmem)
     return fail(FDD_ERR_UNSUPPORTED, "n_chan %d needs more shared memory than a CTA has", nc);
 
@@ -437,22 +445,13 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
                   fixed + per_dm);
     const int64_t fit = static_cast<int64_t>((limit - fixed) / per_dm);
     if (fit < batch) {
-      // whole kernel passes or trial blocks; below one pass of the CTA-pair
-      // form, pairs of its a's (no padded a) while that is more than one
-      // pass of the one-CTA form, else that form's whole passes, else
-      // whatever fits
+      // whole kernel passes or trial blocks, else whatever fits; the pair
+      // form only in batches of whole passes (partial ones lose to the
+      // one-CTA form's whole passes)
+      if (pair && fit < pass2) pair = false;
       const int64_t blk = tc ? fdd::mac_tc_trials_per_pass(p->n_beams, pair)
                              : fdd::mac_variant_trials_per_block(g->mac_variant);
       batch = fit >= blk ? fit / blk * blk : fit;
-      if (pair && fit < blk) {
-        const int64_t two_a = 2 * fdd::mac_tc_trials_per_a(true);
-        const int64_t one = fdd::mac_tc_trials_per_pass(p->n_beams, false);
-        batch = fit / two_a * two_a;
-        if (batch <= one) {
-          pair = false;
-          batch = fit >= one ? fit / one * one : fit;
-        }
-      }
     }
     if (batch > 65535) batch = 65535 / 64 * 64;
   } else if (pair) {
@@ -460,8 +459,7 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
     // one pass stay within half the limit
     const size_t per_trial = (p->output == FDD_OUT_SPECTRA ? 8 : 4) * spectra_sets *
                              static_cast<size_t>(n_bins);
-    if (per_trial * static_cast<size_t>(fdd::mac_tc_trials_per_pass(p->n_beams, true)) > limit / 4)
-      pair = false;
+    if (per_trial * static_cast<size_t>(pass2) > limit / 4) pair = false;
   }
   if (tc) g->mac_variant = pair ? FDD_MAC_TC_PAIR : FDD_MAC_TC;
   g->dm_batch = static_cast<int32_t>(batch);

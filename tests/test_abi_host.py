@@ -172,18 +172,17 @@ def test_variant_choice():
 
 def test_tensor_core_form_geometry():
     """The tensor-core form holds the spectra of every beam at once and batches
-    DMs in whole trial passes when the workspace is bounded.  Plans of more
-    trials than one pass of the one-CTA form (1024 trials in 32-beam groups,
-    2048 in 16-beam groups) take the CTA-pair form (passes of 2048 / 4096,
-    T = 256 trials per a), with time output while its DM batch stays above
-    that one pass (below a pair pass: pairs of a's), with spectra or power
-    while two output blocks of one pair pass fit half the limit; below one
-    pass of the one-CTA form, whatever fits."""
+    DMs in whole trial passes when the workspace is bounded (below one pass,
+    whatever fits).  Plans whose calls end in a pass of the CTA-pair form
+    (2048 trials in 32-beam groups, 4096 in 16-beam groups; T = 256 trials
+    per a) that is full or more than half full take that form: with time
+    output only in DM batches of whole pair passes, with spectra or power
+    only while two output blocks of one pair pass fit half the limit."""
     w = synth.WORKLOADS["fdd_32beam_1024ch_2p19t_4096dm"]
     hilo = fdd.FDD_PREC_BF16_HILO
     g = fdd.fdd_plan_geometry(_params(w, precision=hilo, workspace_limit=200 << 30))
-    assert g["mac_variant"] == fdd.FDD_MAC_TC_PAIR
-    assert g["dm_batch"] == 1536  # 1941 fit: 6 a's of 256
+    assert g["mac_variant"] == fdd.FDD_MAC_TC  # 1941 trials fit: one-CTA passes
+    assert g["dm_batch"] == 1024
     spectra = 32 * 1024 * g["bin_pitch"] * 8
     assert spectra < g["workspace_bytes"] <= 200 << 30
     g = fdd.fdd_plan_geometry(_params(w, precision=hilo, workspace_limit=120 << 30))
@@ -191,12 +190,19 @@ def test_tensor_core_form_geometry():
     assert 512 < g["dm_batch"] < 1024 and g["workspace_bytes"] <= 120 << 30
     g = fdd.fdd_plan_geometry(_params(w, precision=hilo, workspace_limit=72 << 30))
     assert 0 < g["dm_batch"] < 256 and g["workspace_bytes"] <= 72 << 30
-    # one pass of the one-CTA form: that form
-    g = fdd.fdd_plan_geometry(_params(w, precision=hilo, dm_list=0.5 * np.arange(1024),
-                                      workspace_limit=200 << 30))
-    assert g["mac_variant"] == fdd.FDD_MAC_TC and g["dm_batch"] == 1024
-    # 16 beams: 4096-trial pair passes; 120 GiB holds 2048 trials, one
-    # one-CTA pass
+    # the form by the pair's last pass: 1024 / 2560 / 3072 trials end in a
+    # pair pass at most half full, 1100 / 1536 / 2048 / 3584 / 4096 not
+    for n, v in [(1024, fdd.FDD_MAC_TC), (1100, fdd.FDD_MAC_TC_PAIR),
+                 (1536, fdd.FDD_MAC_TC_PAIR), (2048, fdd.FDD_MAC_TC_PAIR),
+                 (2560, fdd.FDD_MAC_TC), (3072, fdd.FDD_MAC_TC),
+                 (3584, fdd.FDD_MAC_TC_PAIR), (4096, fdd.FDD_MAC_TC_PAIR)]:
+        g = fdd.fdd_plan_geometry(_params(w, precision=fdd.FDD_PREC_FP16, n_t=4096,
+                                          output=fdd.FDD_OUT_SPECTRA,
+                                          dm_list=0.5 * np.arange(n),
+                                          workspace_limit=200 << 30))
+        assert g["mac_variant"] == v, (n, g["mac_variant"])
+    # 16 beams: 4096-trial pair passes; 120 GiB holds 2048 trials (one-CTA
+    # passes), 200 GiB all 4096
     g = fdd.fdd_plan_geometry(_params(w, n_beams=16, precision=hilo, workspace_limit=120 << 30))
     assert g["mac_variant"] == fdd.FDD_MAC_TC
     assert g["dm_batch"] == 2048 and g["workspace_bytes"] <= 120 << 30
