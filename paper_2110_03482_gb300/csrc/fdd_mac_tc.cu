@@ -347,8 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
   uint64_t* acc_full = bars + 2 * kStages;      // MMA commit -> epilogue
   uint64_t* acc_empty = acc_full + 1;           // epilogue -> MMA
   uint64_t* drain = acc_empty + 1;
-  uint64_t* tbar = drain + 1;                   // [2]  producers -> producers (phasor table)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tbar + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -368,8 +367,6 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpiWarps + (kPair && rank == 0 ? 1 : 0));  // likewise
     mbar_init(drain, 1);
-    mbar_init(&tbar[0], kProdWarps);
-    mbar_init(&tbar[1], kProdWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -584,55 +581,6 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
     const uint32_t p_base = static_cast<uint32_t>(pw * 1024 + (lane & 3) * 4);
     const uint32_t z_base = sw128(pw, 2 * lane);  // row pw < 16
     const uint32_t b_first = static_cast<uint32_t>(rank * kM + pw * kRows);  // first P row's b
-    // The phasors every producer warp needs for its lane's channel and that
-    // do not depend on the warp (R = exp(2 pi i k v), R^T and the first Q of
-    // each chain) come from a table in shared memory that all producer
-    // threads fill together, kTblG stages' channels at a time, one chunk
-    // ahead, in three buffers: a warp fills chunk g+1 once every warp has
-    // filled chunk g (barrier tbar[g & 1]), i.e. has begun chunk g-1, so no
-    // warp still reads chunk g-2's buffer.  (Each producer lane evaluated all
-    // of them for its channel before, every stage: sixteen times the same.)
-    constexpr int kTblG = 4;                       // stages per chunk
-    constexpr int kTblCh = kTblG * kKCp;           // channels per chunk
-    constexpr int kTblEntries = 4 * kTblCh;        // (R, R^T, Q_a0, Q_b0) per channel
-    static_assert(kTblEntries % (32 * kProdWarps) == 0, "whole entries per thread");
-    float2* tbl = reinterpret_cast<float2*>(base + kRingBytes + 128);  // [3][kTblEntries]
-    const int n_chunks_pass = (n_tiles + kTblG - 1) / kTblG;
-    const int my_bins = unit < a.n_bins ? (a.n_bins - unit + n_units - 1) / n_units : 0;
-    const long long n_chunks = static_cast<long long>(my_bins) * items_per_bin * n_chunks_pass;
-    auto fill = [&](long long g) {
-      const long long pass_i = g / n_chunks_pass;
-      const int c = static_cast<int>(g % n_chunks_pass);
-      const int kb = unit + static_cast<int>(pass_i / items_per_bin) * n_units;
-      const int jp = static_cast<int>(pass_i % items_per_bin) % n_pass * kDmsPass;
-      const uint32_t kuu = static_cast<uint32_t>(a.k_begin + kb * (a.k_step > 0 ? a.k_step : 1));
-      const uint32_t ja = static_cast<uint32_t>(
-          a.j_begin + jp + cta_first_a(pass_as(a.n_dm, jp, kNA, kT)) * kT);
-      float2* dst = tbl + (g % 3) * kTblEntries;
-#pragma unroll
-      for (int r = 0; r < kTblEntries / (32 * kProdWarps); ++r) {
-        const int e = (r * kProdWarps + pw) * 32 + lane;
-        const int nu = c * kTblCh + (e >> 2);
-        float2 v = make_float2(0.f, 0.f);
-        if (nu < a.n_chan) {
-          const PhaseConst q = a.pc[nu];
-          const int kind = e & 3;
-          const uint32_t mult = kind == 0   ? 1u
-                                : kind == 1 ? static_cast<uint32_t>(kT)
-                                            : ja + (kind == 3 ? static_cast<uint32_t>(kHalfA * kT) : 0u);
-          uint32_t ph = top32_mul(kuu * mult, q.v_lo, q.v_hi);
-          if (kind >= 2) ph += top32_mul(kuu, q.u_lo, q.u_hi);
-          v = unit_phasor(ph);
-        }
-        dst[e] = v;
-      }
-    };
-    if (n_chunks > 0) {
-      fill(0);
-      mbar_arrive_warp(&tbar[0]);
-    }
-    long long g = 0;          // chunk of the coming stage
-    const float2* tcur = tbl;  // its table
     uint32_t s = 0;
     bool ok = true;
     for (int k = unit; k < a.n_bins && ok; k += n_units) {
@@ -672,18 +620,6 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           }
         }
         for (int t = 0; t < n_tiles; ++t, ++s) {
-          if (t % kTblG == 0) {  // a new chunk: its table is complete, fill the next
-            if (!__all_sync(0xffffffffu, mbar_wait(&tbar[g & 1], (g >> 1) & 1, abort_flag))) {
-              ok = false;
-              break;
-            }
-            if (g + 1 < n_chunks) {
-              fill(g + 1);
-              mbar_arrive_warp(&tbar[(g + 1) & 1]);
-            }
-            tcur = tbl + (g % 3) * kTblEntries;
-            ++g;
-          }
           const int nu0 = t * kKCp + kCpl * lane;
           PhaseConst pc[kCpl];
           float2 x[kCpl][kBeamsPerWarp];
@@ -710,16 +646,16 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
           for (int cl = 0; cl < kCpl; ++cl) {
             r1[cl] = pb[cl] = rT[cl] = qa[cl] = qb[cl] = make_float2(0.f, 0.f);
             if (nu0 + cl < a.n_chan) {
-              // R, R^T, Q of the chains' first a's (this CTA's from a_first)
-              // from the table; P of this warp's first row directly
-              const float4* e4 = reinterpret_cast<const float4*>(
-                  tcur + 4 * ((t % kTblG) * kKCp + kCpl * lane + cl));
-              const float4 e0 = e4[0], e1 = e4[1];
-              r1[cl] = make_float2(e0.x, e0.y);
-              rT[cl] = make_float2(e0.z, e0.w);
-              qa[cl] = make_float2(e1.x, e1.y);
-              qb[cl] = make_float2(e1.z, e1.w);
-              pb[cl] = unit_phasor(top32_mul(ku * b_first, pc[cl].v_lo, pc[cl].v_hi));
+              const PhaseConst& q = pc[cl];
+              r1[cl] = unit_phasor(top32_mul(ku, q.v_lo, q.v_hi));
+              pb[cl] = unit_phasor(top32_mul(ku * b_first, q.v_lo, q.v_hi));
+              rT[cl] = unit_phasor(top32_mul(ku * static_cast<uint32_t>(kT), q.v_lo, q.v_hi));
+              const uint32_t ja =
+                  static_cast<uint32_t>(a.j_begin + j_pass + a_first * kT);  // first a's trial
+              const uint32_t ph_u = top32_mul(ku, q.u_lo, q.u_hi);
+              qa[cl] = unit_phasor(ph_u + top32_mul(ku * ja, q.v_lo, q.v_hi));
+              qb[cl] = unit_phasor(ph_u + top32_mul(ku * (ja + static_cast<uint32_t>(kHalfA * kT)),
+                                                    q.v_lo, q.v_hi));
             }
           }
           const uint32_t st = s % kStages;
@@ -851,9 +787,7 @@ __global__ void __launch_bounds__(kThreads, 1) mac_tc_kernel(const MacArgs a) {
 
 }  // namespace
 
-// ring, barriers (128 bytes), phasor table (3 chunks of 4 stages' channels x
-// 4 phasors: 24 KB for FP8's 64 channels per stage), alignment slack
-size_t mac_tc_smem_bytes() { return kRingBytes + 128 + 3 * 4 * (4 * 64) * sizeof(float2) + 1024; }
+size_t mac_tc_smem_bytes() { return kRingBytes + 1024 + 128; }
 
 int mac_tc_beams_per_group(int n_series) { return n_series <= 16 ? 16 : 32; }
 
