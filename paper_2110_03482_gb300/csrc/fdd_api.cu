@@ -77,9 +77,6 @@ struct fdd_plan_s {
   char* arena = nullptr;
   size_t arena_bytes = 0, arena_used = 0;
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  // tensor cores: the stream and events on which output blocks move to the
-  // caller's layout beside the next block's kernel
-  fdd::TcAux tc_aux;
   cudaEvent_t win_free[2] = {}, win_full[2] = {}, blk_free[2] = {}, blk_done[2] = {};
   cudaEvent_t pipe_start = nullptr, pipe_end = nullptr;
   // fdd_tdd_execute: rounded shift tables (relative to each block of trials'
@@ -513,11 +510,6 @@ void release(fdd_plan_s* P) {
                         P->pipe_start, P->pipe_end};
   for (cudaEvent_t e : pipe)
     if (e) cudaEventDestroy(e);
-  cudaEvent_t aux_ev[] = {P->tc_aux.fork, P->tc_aux.mac_done[0], P->tc_aux.mac_done[1],
-                          P->tc_aux.out_done[0], P->tc_aux.out_done[1]};
-  for (cudaEvent_t e : aux_ev)
-    if (e) cudaEventDestroy(e);
-  if (P->tc_aux.s) cudaStreamDestroy(P->tc_aux.s);
   if (P->h2d) cudaStreamDestroy(P->h2d);
   if (P->d2h) cudaStreamDestroy(P->d2h);
   delete P;
@@ -992,8 +984,7 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
         m.scale = whole_rows(P) ? static_cast<float>(1.0 / static_cast<double>(g.fft_len)) : 1.0f;
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
-          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s,
-                                      &P->tc_aux));
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s));
         }
         for (int b = 0; b < p.n_beams; ++b) {
           // this beam's trials with bins innermost, then its inverse transforms
@@ -1029,8 +1020,7 @@ fdd_status run_tc(fdd_plan_s* P, const Io& io, cudaStream_t s) {
         m.y_dm_stride = g.n_bins;
         {
           StageTimer t(P, FDD_STAGE_MAC, s);
-          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s,
-                                      &P->tc_aux));
+          FDD_CUDA(fdd::launch_mac_tc(m, p.precision, P->n_sms, P->d_tcx, P->tcx_bytes, s));
         }
         if (k >= 0) {
           fdd_block blk{0, p.n_beams, c, j0, nb, P->d_blk[k], g.n_bins, g.n_bins, 0, nullptr};
@@ -1169,13 +1159,8 @@ fdd_status plan_create(const fdd_params* p, void* arena, size_t arena_bytes, fdd
   fdd_info& g = P->info;
   P->tc = p->precision != FDD_PREC_FP32;
   FDD_CUDA(cudaDeviceGetAttribute(&P->n_sms, cudaDevAttrMultiProcessorCount, P->device));
-  if (P->tc) {
+  if (P->tc)
     FDD_CUDA(fdd::mac_tc_prepare());
-    FDD_CUDA(cudaStreamCreateWithFlags(&P->tc_aux.s, cudaStreamNonBlocking));
-    cudaEvent_t* aux_ev[] = {&P->tc_aux.fork, &P->tc_aux.mac_done[0], &P->tc_aux.mac_done[1],
-                             &P->tc_aux.out_done[0], &P->tc_aux.out_done[1]};
-    for (cudaEvent_t* e : aux_ev) FDD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-  }
   else
     FDD_CUDA(fdd::mac_prepare(g.mac_variant, p->n_chan));
 
@@ -1474,7 +1459,7 @@ fdd_status fdd_dedisperse_spectra_bins(fdd_plan_t plan, const void* d_X, int64_t
   } else if (plan->tc)
     FDD_CUDA(fdd::launch_mac_tc(m, plan->p.precision, plan->n_sms,
                                 plan->d_tcx, plan->tcx_bytes,
-                                reinterpret_cast<cudaStream_t>(stream), &plan->tc_aux));
+                                reinterpret_cast<cudaStream_t>(stream)));
   else
     FDD_CUDA(fdd::launch_mac_fp32(m, g.mac_variant, reinterpret_cast<cudaStream_t>(stream)));
   return FDD_OK;

@@ -125,18 +125,8 @@ int mac_tc_beams_per_group(int n_series);
 size_t mac_tc_scratch_bytes(int n_series, int n_chan, int n_dm, int64_t n_bins);
 size_t mac_tc_min_scratch(int n_series, int n_chan, int n_dm, int64_t n_bins);
 // precision: FDD_PREC_BF16_HILO, FDD_PREC_BF16 or FDD_PREC_FP16.
-// A second stream on which launch_mac_tc moves one block of bin-major output
-// to the caller's layout while the kernel computes the next block (forked
-// from and joined back to the calling stream by these events).
-struct TcAux {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, mac_done[2] = {nullptr, nullptr}, out_done[2] = {nullptr, nullptr};
-};
-// aux (may be NULL): with bin-major output moved to the caller's layout, the
-// blocks' moves run on aux->s overlapping the next blocks' kernels (two
-// output blocks in the scratch).
 cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
-                          size_t scratch_bytes, cudaStream_t s, const TcAux* aux = nullptr);
+                          size_t scratch_bytes, cudaStream_t s);
 
 // Bins k0 .. k0 + n_bins - 1 of `rows` complex rows of stride in_stride into
 // out[k][row] (bin-major), for the tensor-core kernel.
@@ -178,7 +168,6 @@ struct BinUntransposeArgs {
   int64_t out_series_stride;  // elements
   int64_t out_dm_stride;      // elements
   int64_t in_bin_stride = 0;  // elements between bins of `in`; 0: n_series * n_dm
-  int max_ctas = 0;           // > 0: at most this many CTAs (each loops over its tiles)
 };
 cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s);
 

@@ -905,7 +905,7 @@ size_t mac_tc_min_scratch(int n_series, int n_chan, int n_dm, int64_t n_bins) {
 }
 
 cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* scratch,
-                          size_t scratch_bytes, cudaStream_t s, const TcAux* aux) {
+                          size_t scratch_bytes, cudaStream_t s) {
   if (a.n_dm <= 0 || a.n_series <= 0 || a.n_bins <= 0) return cudaSuccess;
   const int prec = tc_prec(precision);
   if (prec < 0 || !scratch) return cudaErrorInvalidValue;
@@ -931,53 +931,21 @@ cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* sc
   const size_t per_bin =
       block_bytes_per_bin(x_in_place, y_in_place, a.n_series, a.n_chan, a.n_dm, y_elem);
   if (scratch_bytes < head + 2 * kScratchAlign) return cudaErrorInvalidValue;
-  int64_t kb = static_cast<int64_t>((scratch_bytes - head - 2 * kScratchAlign) / per_bin);
+  const int64_t kb = static_cast<int64_t>((scratch_bytes - head - 2 * kScratchAlign) / per_bin);
   if (kb < 1) return cudaErrorInvalidValue;
-  // Overlap: two output blocks in the scratch, at least four blocks per call,
-  // each a whole number of the kernel's persistent units where that allows
-  const size_t y_per_bin = y_elem * static_cast<size_t>(a.n_series) * a.n_dm;
-  const size_t x_per_bin = per_bin - (y_in_place ? 0 : y_per_bin);
-  bool overlap = aux && aux->s && !y_in_place;
-  if (overlap) {
-    int64_t kb2 = static_cast<int64_t>((scratch_bytes - head - 3 * kScratchAlign) /
-                                       (x_per_bin + 2 * y_per_bin));
-    const int64_t quarter = (a.n_bins + 3) / 4;
-    if (kb2 > quarter) kb2 = quarter;
-    const int64_t unit = n_sms / 2 > 0 ? n_sms / 2 : 1;
-    if (kb2 > unit) kb2 = kb2 / unit * unit;
-    if (kb2 < 1 || kb2 >= a.n_bins) {
-      overlap = false;
-    } else {
-      kb = kb2;
-    }
-  }
   char* blk = reinterpret_cast<char*>(scratch) + head;
   float2* x_scratch = reinterpret_cast<float2*>(blk);
   const size_t x_block = x_in_place ? 0 : sizeof(float2) * static_cast<size_t>(kb) * a.n_series *
                                               a.n_chan;
   void* y_scratch = blk + align_up(x_block);
-  void* y_slots[2] = {y_scratch,
-                      static_cast<char*>(y_scratch) + align_up(y_per_bin * static_cast<size_t>(kb))};
-  if (overlap) {  // the moves wait for everything before this call on s
-    if ((e = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(aux->s, aux->fork, 0)) != cudaSuccess) return e;
-  }
-  int64_t blk_i = 0;
   const int64_t rows = static_cast<int64_t>(a.n_series) * a.n_chan;
   const bool scaled = prec == kF16 || prec == kF8;
   if (scaled && x_in_place && !a.absmax_ready) {
     BinAbsmaxArgs t{a.X, a.x_bin_stride, a.n_series * a.n_chan, a.n_bins, absmax};
     if ((e = launch_bin_absmax(t, s)) != cudaSuccess) return e;
   }
-  for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb, ++blk_i) {
+  for (int64_t k0 = 0; k0 < a.n_bins; k0 += kb) {
     const int nb = static_cast<int>((a.n_bins - k0) < kb ? (a.n_bins - k0) : kb);
-    const int slot = static_cast<int>(blk_i & 1);
-    if (overlap) {
-      y_scratch = y_slots[slot];
-      // the move of the block two back has read this slot
-      if (blk_i >= 2 && (e = cudaStreamWaitEvent(s, aux->out_done[slot], 0)) != cudaSuccess)
-        return e;
-    }
     MacArgs c = a;
     c.n_bins = nb;
     c.k_begin = a.k_begin + static_cast<int>(k0);
@@ -1010,21 +978,8 @@ cudaError_t launch_mac_tc(const MacArgs& a, int precision, int n_sms, float2* sc
       BinUntransposeArgs u{y_scratch, static_cast<int>(y_elem), a.n_series, a.n_dm, nb,
                            static_cast<char*>(a.Y) + y_elem * static_cast<size_t>(k0),
                            a.y_series_stride, a.y_dm_stride};
-      if (overlap) {
-        // one small CTA per SM, beside the next block's kernel CTA there
-        u.max_ctas = n_sms;
-        if ((e = cudaEventRecord(aux->mac_done[slot], s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(aux->s, aux->mac_done[slot], 0)) != cudaSuccess) return e;
-        if ((e = launch_bin_untranspose(u, aux->s)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(aux->out_done[slot], aux->s)) != cudaSuccess) return e;
-      } else if ((e = launch_bin_untranspose(u, s)) != cudaSuccess) {
-        return e;
-      }
+      if ((e = launch_bin_untranspose(u, s)) != cudaSuccess) return e;
     }
-  }
-  if (overlap) {  // join: s waits for the last moves
-    for (int slot = 0; slot < 2 && slot < blk_i; ++slot)
-      if ((e = cudaStreamWaitEvent(s, aux->out_done[slot], 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

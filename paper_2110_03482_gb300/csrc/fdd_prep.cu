@@ -239,13 +239,7 @@ __global__ void __launch_bounds__(32 * kUntrRows) bin_untranspose_kernel(const T
 cudaError_t launch_bin_untranspose(const BinUntransposeArgs& a, cudaStream_t s) {
   if (a.n_bins <= 0 || a.n_dm <= 0 || a.n_series <= 0) return cudaSuccess;
   const int64_t tiles = static_cast<int64_t>(a.n_series) * ((a.n_dm + kTile - 1) / kTile);
-  int64_t gy = tiles < 65535 ? tiles : 65535;
-  const int gx = (a.n_bins + kTile - 1) / kTile;
-  if (a.max_ctas > 0) {  // (a bounded grid: each CTA loops over its (series, trial) tiles)
-    const int64_t cap = a.max_ctas / gx;
-    gy = cap < 1 ? 1 : (cap < gy ? cap : gy);
-  }
-  dim3 grid(gx, static_cast<unsigned>(gy));
+  dim3 grid((a.n_bins + kTile - 1) / kTile, static_cast<unsigned>(tiles < 65535 ? tiles : 65535));
   note_launches(1);
   const int64_t rows =
       a.in_bin_stride > 0 ? a.in_bin_stride : static_cast<int64_t>(a.n_series) * a.n_dm;
