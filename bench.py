@@ -1095,6 +1095,8 @@ def run_tc_workload(args) -> None:
             "config": dict(workload_config(w, info), beams_per_gpu=w.n_beams,
                            precision=args.precision, dm_batch=info["dm_batch"],
                            block_dm=info["block_dm"],
+                           tc_form=("CTA pairs" if info["mac_variant"] == fdd.FDD_MAC_TC_PAIR
+                                    else "one CTA per SM"),
                            input=("resident in HBM" if resident else
                                   "generated per (beam, chunk) window on the device "
                                   f"({in_bytes / 1e9:.0f} GB exceeds HBM)"),

@@ -93,7 +93,8 @@ typedef enum fdd_status {
                                8 / 16 bins (default from 257 trials)            */
 #define FDD_MAC_VARIANTS 6
 #define FDD_MAC_TC 100      /* fdd_info.mac_variant of the tensor-core form: one
-                               CTA per SM, T = 128 trials per a (see below)      */
+                               CTA per SM, a pass over the channels covering
+                               1024 trials with more than 16 beams, else 2048   */
 #define FDD_MAC_TC_PAIR 101 /* the same on pairs of CTAs (two SMs, one MMA of
                                M = 256, T = 256), each building half of the data
                                operand; a pass covers 2048 trials with more than
@@ -181,7 +182,8 @@ typedef struct fdd_info {
   double ddm;              /* DM step of the (uniform) trial list                  */
   int32_t dm_uniform;      /* 1 when the list is an arithmetic progression         */
   int32_t dm_batch;        /* trials per internal batch (bounded by workspace)     */
-  int32_t mac_variant;     /* phasor-MAC kernel tile chosen for this plan          */
+  int32_t mac_variant;     /* phasor-MAC kernel chosen for this plan: an FP32 tile
+                              (FDD_MAC_*) or FDD_MAC_TC / FDD_MAC_TC_PAIR         */
   int32_t downsample;      /* factor of the shortened inverse transform (1: none)    */
   int32_t block_dm;        /* trials per output block of the streamed calls        */
   int64_t stream_bytes;    /* device bytes the first streamed call adds to the plan
