@@ -47,12 +47,24 @@ PREC_NAMES = {fdd.FDD_PREC_BF16_HILO: "hi+lo", fdd.FDD_PREC_BF16: "bf16",
 
 @pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16,
                                        fdd.FDD_PREC_FP16], ids=["bf16_hilo", "bf16", "fp16"])
+def _pair_form(n_series, n_dm):
+    """The plans' rule: the CTA-pair form where the calls' last pair pass
+    (2048 trials with more than 16 series, else 4096) is full or more than
+    half full."""
+    p2 = 4096 if n_series <= 16 else 2048
+    r = n_dm % p2
+    return n_dm > p2 // 2 and (r == 0 or r > p2 // 2)
+
+
 @pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
-    (5, 40, 256, 0.0, 0.5, 2100),    # partial 16-beam group, ragged channel tile, 2 passes
-    (32, 64, 128, 3.0, 1.0, 1024),   # one full group, exactly one pass
-    (37, 33, 512, 0.0, 0.25, 300),   # two groups, one partial pass
-    (16, 64, 512, 1.0, 0.25, 2100),  # one full 16-beam group, 2048-trial passes, ragged
-    (33, 40, 256, 0.5, 0.5, 2200),   # 32-beam groups (one of 1 beam), 3 passes, ragged
+    (5, 40, 256, 0.0, 0.5, 2100),    # pair: partial 16-beam group, ragged channel tile,
+                                     # one pass of 9 a's (the second CTA's last a padded)
+    (32, 64, 128, 3.0, 1.0, 1024),   # one CTA per SM: one full group, exactly one pass
+    (37, 33, 512, 0.0, 0.25, 300),   # one CTA: two groups, one partial pass
+    (16, 64, 512, 1.0, 0.25, 2100),  # pair: one full 16-beam group, one pass of 9 a's
+    (33, 40, 256, 0.5, 0.5, 2200),   # one CTA: 32-beam groups (one of 1 beam), 3 passes
+    (40, 24, 128, 0.5, 0.5, 3300),   # pair: 32-beam groups (one of 8 beams), a full pass
+                                     # and one of 5 a's
     (1, 1, 64, 0.0, 1.0, 1),         # one series, one channel, one trial
     (2, 7, 32, 5.0, 0.1, 3),         # a few of everything, non-zero first trial
 ])
@@ -65,7 +77,8 @@ def test_tc_kernel_matches_oracle(n_series, n_chan, L, dm0, ddm, n_dm, precision
          1j * rng.standard_normal((n_series, n_chan, K))).astype(np.complex64).astype(np.complex128)
     xp, yp = K + 5, K + 2
     with fdd.Plan(**params_for(w, output=fdd.FDD_OUT_SPECTRA, precision=precision)) as plan:
-        assert plan.info["mac_variant"] in (fdd.FDD_MAC_TC, fdd.FDD_MAC_TC_PAIR)
+        assert plan.info["mac_variant"] == (fdd.FDD_MAC_TC_PAIR if _pair_form(n_series, n_dm)
+                                            else fdd.FDD_MAC_TC)
         dX = complex_to_device(X, xp)
         dY = torch.zeros((n_series, n_dm, yp, 2), dtype=torch.float32, device="cuda")
         plan.dedisperse_spectra(dX, xp, n_series, 0, n_dm, dY, yp)
