@@ -41,14 +41,23 @@ def _smoke_check(plan, w, fb):
     return rel_l2(out.cpu().numpy().reshape(w.n_dm, -1), ref)
 
 
-@pytest.mark.parametrize("precision,tol", [(fdd.FDD_PREC_FP32, FP32_REL_L2),
-                                           (fdd.FDD_PREC_BF16_HILO, 3e-3)],
-                         ids=["fp32", "tensor"])
-def test_stalled_producer_times_out_and_the_plan_recovers(precision, tol):
+@pytest.mark.parametrize("precision,tol,n_dm", [(fdd.FDD_PREC_FP32, FP32_REL_L2, 0),
+                                                (fdd.FDD_PREC_BF16_HILO, 3e-3, 0),
+                                                (fdd.FDD_PREC_FP16, 3e-3, 3000)],
+                         ids=["fp32", "tensor", "tensor_pair"])
+def test_stalled_producer_times_out_and_the_plan_recovers(precision, tol, n_dm):
+    """A kernel whose producers never announce a filled stage runs its waits
+    out, reports FDD_ERR_TIMEOUT once and leaves the context usable; the
+    third case is a plan of the CTA-pair form (3000 trials), whose second
+    CTA forwards its stages to the first."""
     w = synth.WORKLOADS["fdd_64ch_4096t_128dm"]
+    if n_dm:
+        w = w.scaled(n_dm=n_dm, ddm=0.01)
     fb, _ = synth.filterbank(w, seed=20211008)
     with fdd.Plan(**params_for(w, precision=precision)) as plan:
         assert plan.query()["n_bins"] == 2049
+        if n_dm:
+            assert plan.info["mac_variant"] == fdd.FDD_MAC_TC_PAIR
         t0 = time.perf_counter()
         plan.debug_stall_test()
         dt = time.perf_counter() - t0
