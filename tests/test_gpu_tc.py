@@ -45,8 +45,6 @@ PREC_NAMES = {fdd.FDD_PREC_BF16_HILO: "hi+lo", fdd.FDD_PREC_BF16: "bf16",
               fdd.FDD_PREC_FP16: "fp16"}
 
 
-@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16,
-                                       fdd.FDD_PREC_FP16], ids=["bf16_hilo", "bf16", "fp16"])
 def _pair_form(n_series, n_dm):
     """The plans' rule: the CTA-pair form where the calls' last pair pass
     (2048 trials with more than 16 series, else 4096) is full or more than
@@ -56,6 +54,8 @@ def _pair_form(n_series, n_dm):
     return n_dm > p2 // 2 and (r == 0 or r > p2 // 2)
 
 
+@pytest.mark.parametrize("precision", [fdd.FDD_PREC_BF16_HILO, fdd.FDD_PREC_BF16,
+                                       fdd.FDD_PREC_FP16], ids=["bf16_hilo", "bf16", "fp16"])
 @pytest.mark.parametrize("n_series,n_chan,L,dm0,ddm,n_dm", [
     (5, 40, 256, 0.0, 0.5, 2100),    # pair: partial 16-beam group, ragged channel tile,
                                      # one pass of 9 a's (the second CTA's last a padded)
