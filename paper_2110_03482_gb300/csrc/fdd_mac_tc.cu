@@ -2,9 +2,9 @@
 // for many beams sharing the same Fourier bins (the tensor-core and
 // phasor-reuse directions of Sect. 5 of the paper).
 //
-// With the trial index split j = aT + b (T = 128), the phasor of Eq. 4
-// factorises as W(aT + b) = Q_a P_b (see fdd_mac_fp32.cu), so for one bin k
-// and beams beta
+// With the trial index split j = aT + b (T = 128, or 256 on a CTA pair), the
+// phasor of Eq. 4 factorises as W(aT + b) = Q_a P_b (see fdd_mac_fp32.cu), so
+// for one bin k and beams beta
 //
 //   Y[aT + b][beta] = sum_nu P_b[nu] Z_a[nu][beta],   Z_a = Q_a X[nu][beta],
 //
@@ -19,11 +19,12 @@
 // step; or hi alone: two) or FP16 (two MMAs; each bin's data scaled by a power
 // of two so its largest component lands near 2^14, undone in the epilogue),
 // accumulation FP32 in tensor memory.  M = 128
-// trials b, N = 256 (a, beta) pairs (8 a's x 32 beams, or 16 a's x 16 beams
-// for calls with at most 16 series), K = 64 per stage (32 channels x
+// trials b per CTA, N = 256 (a, beta) pairs (8 a's x 32 beams, or 16 a's x 16
+// beams for calls with at most 16 series), K = 64 per stage (32 channels x
 // (re, im)).  D_re and D_im fill all 512 tensor-memory columns, so one pass
-// over the channels covers 1024 trials (2048 in 16-beam groups): every P tile
-// the producers build serves 256 output columns, and every Z value is
+// over the channels covers 1024 trials (2048 in 16-beam groups), twice that
+// on a CTA pair (M = 256 over two SMs, each CTA building half of B): every P
+// tile the producers build serves 256 output columns, and every Z value is
 // written to shared memory once.
 //
 // Warp specialisation: warp 0 allocates tensor memory and one of its threads
@@ -31,7 +32,8 @@
 // MUFU sin/cos and short recurrences, hi/lo split) and Z = Q X for each stage
 // straight into the 128-byte-swizzled K-major shared layout the MMA
 // descriptors address, through an mbarrier ring (2 stages of 96 KB with hi +
-// lo phasors, 3 of 64 KB without); 4 epilogue warps read the accumulators
+// lo phasors, 3 of 64 KB without; a pair's CTA holds half of B: 2 of 80 KB
+// or 4 of 48 KB); 4 epilogue warps read the accumulators
 // back (tcgen05.ld) and store them, while the producers already fill the ring
 // for the next pass.  The kernel writes Y bin-major, [bin][series][trial], so
 // each warp store covers 256 contiguous bytes; launch_mac_tc then moves it
