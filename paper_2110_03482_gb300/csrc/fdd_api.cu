@@ -416,8 +416,9 @@ fdd_status compute_plan(const fdd_params* p, fdd_info* g, fdd::CoreGeometry* cor
   // tensor cores: the CTA-pair form where its passes are full enough.  A
   // pass of either form costs a fixed part (the phasor rows P, evaluated per
   // pass and CTA) plus a part per a (Z and the MMAs); measured on 32 beams x
-  // 1024 channels, the pair's pass (2048 trials) costs 375 + 12.2 per a of
-  // 256 trials, the one-CTA pass (1024 trials) 197 + 8.9 per a of 128: the
+  // 1024 channels, in whole-GPU time per bin, the pair's pass (2048 trials)
+  // costs 375 ns + 12.2 ns per a of 256 trials, the one-CTA pass (1024
+  // trials) 197 ns + 8.9 ns per a of 128: the
   // pair wins on calls whose last pair pass is more than half full (or
   // full).  A plan keeps one form, so its streamed and whole calls agree.
   const int64_t pass2 = tc ? fdd::mac_tc_trials_per_pass(p->n_beams, true) : 0;
